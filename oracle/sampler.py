@@ -1,0 +1,116 @@
+"""Autoregressive statistics sampling with MU masking (Sec. II.C, Sec. III.C).
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+The tree is walked level by level (slot p = 0..n-1).  A node holds a prefix
+(slots < p) and the number of samples n_in that entered it; the root holds
+all N_s.  At each node the n_in samples are split among the four outcomes of
+slot p according to the masked conditional p~(v | v_<p), so that MU passes
+every sample to an allowed child and none is lost (Sec. III.C, Fig. 1C.iii);
+children with zero samples are dropped (Sec. II.C).  The leaves are the
+unique samples x^(l) with their occurrence numbers n^(l).
+
+Split rule (the paper fixes the distribution, a multinomial split, but not
+the procedure; reading): the node draws n_in uniforms u_i, i = 0..n_in-1,
+from Philox4x64-10 with counter (prefix, i >> 2, p, counter) and key
+(seed, 0), taking word i & 3 of each block; a uniform is the top 53 bits of
+the word times 2^-53.  Sample i goes to the first allowed outcome v with
+u_i < C_v, C_v the FP64 running sum of p~ over allowed outcomes in ascending
+v (the last allowed outcome if rounding leaves u_i >= C_last).  p~ is the
+softmax over allowed outcomes, evaluated in FP64 as exp(l_v - max) / sum.
+Children are emitted in ascending v, so the leaves come out in lexicographic
+order of (v_0, v_1, ..., v_{n-1}).
+
+Pins: sum of counts = N_s under MU, all leaves in the sector, and a
+chi-square test of the counts against N_s |psi(x)|^2 (tests/test_oracle_sampler.py).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .anqs import allowed_masks
+from .philox import philox4x64_np, uniform_from_word
+
+
+def split_probabilities(logits: np.ndarray, mask: np.ndarray) -> np.ndarray:
+    """p~ of one node from its 4 modulus logits and allowed mask (FP64)."""
+    l = np.asarray(logits, dtype=np.float64)
+    m = max(l[v] for v in range(4) if mask[v])
+    e = np.array([np.exp(l[v] - m) if mask[v] else 0.0 for v in range(4)])
+    s = 0.0
+    for v in range(4):
+        s += e[v]
+    return e / s
+
+
+def node_uniforms(prefix: int, count: int, p: int, seed: int, counter: int) -> np.ndarray:
+    i = np.arange(count, dtype=np.uint64)
+    blk = i >> np.uint64(2)
+    words = philox4x64_np(np.full_like(blk, np.uint64(prefix)), blk, np.full_like(blk, np.uint64(p)),
+                          np.full_like(blk, np.uint64(counter)), seed, 0)
+    w = np.stack(words, axis=1)[np.arange(count), (i & np.uint64(3)).astype(np.int64)]
+    return uniform_from_word(w)
+
+
+def split_node(probs: np.ndarray, mask, u: np.ndarray):
+    """Counts per outcome and the smallest |u - C_v| over the draws."""
+    C = np.zeros(4)
+    run = 0.0
+    allowed = [v for v in range(4) if mask[v]]
+    for v in range(4):
+        if mask[v]:
+            run += probs[v]
+        C[v] = run
+    out = np.full(len(u), allowed[-1], dtype=np.int64)
+    undecided = np.ones(len(u), dtype=bool)
+    for v in allowed:
+        hit = undecided & (u < C[v])
+        out[hit] = v
+        undecided &= ~hit
+    counts = np.bincount(out, minlength=4)
+    margin = np.inf
+    if len(u):
+        for v in allowed[:-1]:
+            margin = min(margin, float(np.min(np.abs(u - C[v]))))
+    return counts, margin
+
+
+def sample(model, isphys, n: int, n_samples: int, seed: int, counter: int = 0,
+           logits_fn=None):
+    """Unique samples and counts, in the tree's lexicographic order.
+
+    ``logits_fn(prefixes, p)`` may replace the network (returns [B, 4]
+    modulus logits); by default the model's slot outputs are used.
+    Returns (x uint64[N_unq], counts int64[N_unq], min_margin).
+    """
+    pre = np.zeros(1, dtype=np.uint64)
+    cnt = np.array([n_samples], dtype=np.int64)
+    margin = np.inf
+    for p in range(n):
+        if logits_fn is None:
+            L = model.slot_out(pre, p)[:, :4].detach().numpy()
+        else:
+            L = np.asarray(logits_fn(pre, p), dtype=np.float64)
+        M = allowed_masks(isphys, pre, n)[:, p]
+        new_pre, new_cnt = [], []
+        for k in range(len(pre)):
+            probs = split_probabilities(L[k], M[k])
+            u = node_uniforms(int(pre[k]), int(cnt[k]), p, seed, counter)
+            c, mg = split_node(probs, M[k], u)
+            margin = min(margin, mg)
+            for v in range(4):
+                if c[v] > 0:
+                    new_pre.append(int(pre[k]) | (v << (2 * p)))
+                    new_cnt.append(int(c[v]))
+        pre = np.array(new_pre, dtype=np.uint64)
+        cnt = np.array(new_cnt, dtype=np.int64)
+    return pre, cnt, margin
+
+
+def lexicographic_key(xs, n: int) -> np.ndarray:
+    """sum_p v_p 4^(n-1-p): ascending key = the tree's output order."""
+    xs = np.asarray(xs, dtype=np.uint64)
+    key = np.zeros(len(xs), dtype=np.uint64)
+    for p in range(n):
+        key = key * np.uint64(4) + ((xs >> np.uint64(2 * p)) & np.uint64(3))
+    return key

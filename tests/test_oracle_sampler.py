@@ -1,0 +1,54 @@
+"""Pins for the oracle's statistics sampler (MU)."""
+import numpy as np
+import pytest
+from scipy.stats import chi2
+
+from oracle.anqs import MLPAnsatz, TFAnsatz, log_psi
+from oracle.sampler import lexicographic_key, sample
+from oracle.sector import molecular_isphys, sector_states
+from synthetic import mlp_params, tf_params
+
+
+@pytest.mark.parametrize("kind", ["mlp", "tf"])
+def test_counts_match_born_distribution(kind):
+    n, na, nb = 4, 2, 2
+    if kind == "mlp":
+        model = MLPAnsatz(mlp_params(3, n, 32, 2, bias_std=0.7), n)
+    else:
+        model = TFAnsatz(tf_params(3, n, 8, 1, bias_std=0.3), n, 2)
+    ip = molecular_isphys(n, na, nb)
+    st = np.array(sector_states(n, na, nb), dtype=np.uint64)
+    la, _ = log_psi(model, ip, st)
+    prob = np.exp(2 * la.numpy())
+    Ns = 200_000
+    xs, cnt, _ = sample(model, ip, n, Ns, seed=11, counter=2)
+    assert cnt.sum() == Ns  # MU: no sample is lost (Sec. III.C)
+    assert set(xs.tolist()) <= set(st.tolist())
+    full = np.zeros(len(st))
+    full[np.searchsorted(st, xs)] = cnt
+    stat = ((full - Ns * prob) ** 2 / (Ns * prob)).sum()
+    assert stat < chi2.ppf(1 - 1e-6, len(st) - 1)
+
+
+def test_order_unique_and_deterministic():
+    n = 5
+    model = MLPAnsatz(mlp_params(2, n, 16, 2, bias_std=0.5), n)
+    ip = molecular_isphys(n, 3, 2)
+    a = sample(model, ip, n, 5000, seed=1)
+    b = sample(model, ip, n, 5000, seed=1)
+    c = sample(model, ip, n, 5000, seed=1, counter=1)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert not (np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1]))
+    key = lexicographic_key(a[0], n)
+    assert np.all(np.diff(key.astype(np.float64)) > 0)
+
+
+def test_single_sample_and_forced_path():
+    """N_s = 1 yields one leaf with count 1; a sector with a single
+    determinant (all orbitals filled) is always reached."""
+    n = 3
+    model = MLPAnsatz(mlp_params(0, n, 8, 2, bias_std=0.5), n)
+    xs, cnt, _ = sample(model, molecular_isphys(n, 1, 2), n, 1, seed=5)
+    assert len(xs) == 1 and cnt[0] == 1
+    xs, cnt, _ = sample(model, molecular_isphys(n, 3, 3), n, 777, seed=5)
+    assert xs.tolist() == [0b111111] and cnt.tolist() == [777]
