@@ -1,0 +1,260 @@
+/*
+ * anqs.h - C ABI of libanqs: the data-parallel hot path of symmetry-masked
+ * autoregressive variational Monte Carlo for second-quantised molecular
+ * Hamiltonians (Malyshev, Arrazola, Lvovsky, arXiv:2310.04166), on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Determinants are uint64 occupation strings.  Bit q is the occupation of
+ *   spin-orbital q = 2 p + s (spatial orbital p, s = 0 alpha, 1 beta): the
+ *   interleaved ordering of Appendix A (odd 1-based qubits carry spin up)
+ *   under the Jordan-Wigner encoding of Sec. IV.A.  The autoregressive unit
+ *   is the spatial orbital ("slot"): v_p = x_{2p} + 2 x_{2p+1} in {0..3}.
+ *   At most 32 spatial orbitals.
+ * - Every function returns ANQS_OK (0) or a negative ANQS_ERR_* code; the
+ *   message of the last error on the calling thread is available from
+ *   anqs_last_error().  Argument errors are detected on the host before any
+ *   work is queued.  Nothing in the library traps or asserts on the device.
+ * - Array arguments named *_dev are DEVICE pointers owned by the caller; the
+ *   library never frees or reallocates them.  Arguments named *_host are
+ *   host pointers, read before the call returns.
+ * - Calls that take a stream are asynchronous with respect to the host and
+ *   ordered on that stream (a cudaStream_t passed as void*, NULL = the
+ *   legacy default stream).  They allocate nothing: scratch memory comes
+ *   from the caller as (workspace_dev, workspace_bytes), sized by the
+ *   matching *_workspace_size() query, 256-byte aligned.
+ * - Handles (anqs_ham, anqs_model) are created on the current CUDA device,
+ *   own their device memory and are released by *_destroy.
+ *
+ * Network parameters (flat float32 arrays, device memory, caller-owned):
+ *   ANQS_MODEL_MLP  for each slot p = 0..n-1, for each layer k = 1..L+1:
+ *                   W_k [out][in] row-major (absent for k = 1, p = 0), b_k [out].
+ *                   Layer 1 maps the one-hot of v_<p (in = 4p, index 4q+v_q)
+ *                   to `width`, layers 2..L map width -> width (tanh after
+ *                   each hidden layer), the head maps width -> 8 outputs:
+ *                   modulus logits l_0..l_3, then phases phi_0..phi_3.
+ *   ANQS_MODEL_TF   tok[5][d] (rows 0..3 slot values, row 4 start token),
+ *                   pos[n][d], per layer: ln1_g[d] ln1_b[d] wq[d][d] bq[d]
+ *                   wk[d][d] bk[d] wv[d][d] bv[d] wo[d][d] bo[d] ln2_g[d]
+ *                   ln2_b[d] w1[4d][d] b1[4d] w2[d][4d] b2[d], then lnf_g[d]
+ *                   lnf_b[d] head_w[8][d] head_b[8].  Pre-LayerNorm (eps
+ *                   1e-5) causal blocks, ReLU FFN; position t reads the start
+ *                   token (t = 0) or v_{t-1} and outputs slot t's 8 values.
+ *   ANQS_MODEL_TABLE for each slot p: table_p[4^p][8], row = the prefix bits
+ *                   x & (4^p - 1).  n <= 11.
+ * Slot conditional (Appendix B.1, activation f3, with MU masking of
+ * Sec. III.C): |psi_p(v)|^2 = exp(l_v) / sum_{u allowed} exp(l_u) over the
+ * outcomes u that can still reach the (N_alpha, N_beta) sector, 0 for the
+ * others; arg psi_p(v) = phi_v.  log psi(x) = sum_p log psi_p(v_p | v_<p)
+ * (Eq. anqs_def).
+ */
+#ifndef ANQS_H
+#define ANQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ANQS_API __attribute__((visibility("default")))
+#else
+#define ANQS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ANQS_OK = 0,
+  ANQS_ERR_ARG = -1,         /* invalid argument (null pointer, size, mismatch) */
+  ANQS_ERR_CAPACITY = -2,    /* an output or workspace is too small */
+  ANQS_ERR_SECTOR = -3,      /* the requested sector is empty or invalid */
+  ANQS_ERR_CUDA = -4,        /* a CUDA runtime call failed (message has the name) */
+  ANQS_ERR_UNSUPPORTED = -5  /* configuration outside the supported range */
+};
+
+enum { ANQS_MODEL_MLP = 0, ANQS_MODEL_TF = 1, ANQS_MODEL_TABLE = 2 };
+
+/* Arithmetic form of a model's network evaluation.
+ * FP32: plain SIMT float32 kernels, every configuration evaluated over all
+ *       slots (no prefix reuse).
+ * BF16: tensor-core (tcgen05, TMEM accumulators) bfloat16 GEMMs with float32
+ *       accumulation, float32 activations/softmax/phase heads, and reuse of
+ *       the parent determinant's slots for its connected determinants. */
+enum { ANQS_FORM_FP32 = 0, ANQS_FORM_BF16 = 1 };
+
+typedef struct anqs_ham anqs_ham;
+typedef struct anqs_model anqs_model;
+
+typedef struct {
+  int32_t kind;      /* ANQS_MODEL_* */
+  int32_t form;      /* ANQS_FORM_* (TABLE: FP32 only) */
+  int32_t n_orb;     /* spatial orbitals n (slots), 1..32 */
+  int32_t width;     /* MLP: hidden width (multiple of 32, <= 256) */
+  int32_t n_hidden;  /* MLP: hidden layers L (1..8) */
+  int32_t d_model;   /* TF: model width d (multiple of 32, <= 256) */
+  int32_t n_heads;   /* TF: heads (d_model % n_heads == 0) */
+  int32_t n_layers;  /* TF: blocks */
+} anqs_model_desc;
+
+/* Library version string (static storage). */
+ANQS_API const char* anqs_version(void);
+
+/* Copy the last error message of the calling thread into buf (always
+ * NUL-terminated when len > 0).  Returns the code of that error. */
+ANQS_API int anqs_last_error(char* buf, size_t len);
+
+/* ---------------------------------------------------------------------------
+ * Hamiltonian and sector (Eq. sq_hamiltonian, Sec. IV.A; Alg. 1)
+ *
+ * H = E_nuc + sum_{pq,s} h_pq a+_{ps} a_{qs}
+ *           + 1/2 sum_{pqrs,s,t} g_pqrs a+_{ps} a+_{rt} a_{st} a_{qs}
+ * with real chemist-notation integrals g_pqrs = (pq|rs) (8-fold symmetric)
+ * and symmetric h.  The sector is fixed by N_alpha and N_beta, i.e. by the
+ * particle number and S_z of the reference determinant (Sec. IV.A,
+ * Appendix A).  At creation the library evaluates IsPhys (Algorithm 1) over
+ * the qubit tree with the additive n_e and S_z symmetries and stores, for
+ * every slot p and partial counts (a, b), the 4-bit mask of outcomes that
+ * still reach the sector.
+ *
+ * h_host: n*n doubles, row-major.  g_host: n^4 doubles, index
+ * ((p*n+q)*n+r)*n+s.  Copied to the current device; synchronous.
+ * Errors: ANQS_ERR_ARG (null, n outside 1..32), ANQS_ERR_SECTOR (N_alpha or
+ * N_beta outside 0..n), ANQS_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+ANQS_API int anqs_hamiltonian_create(anqs_ham** out, int n_orb, int n_alpha, int n_beta,
+                            const double* h_host, const double* g_host, double e_nuc);
+ANQS_API int anqs_hamiltonian_destroy(anqs_ham* ham);
+
+/* n_connected: off-diagonal determinants connected to every sector
+ * determinant by H (same for all of them):
+ *   Na(n-Na) + Nb(n-Nb) + C(Na,2)C(n-Na,2) + C(Nb,2)C(n-Nb,2) + Na(n-Na)Nb(n-Nb).
+ * sector_dim: C(n,Na) C(n,Nb) (saturated at UINT64_MAX).  Either may be NULL. */
+ANQS_API int anqs_hamiltonian_info(const anqs_ham* ham, uint64_t* n_connected, uint64_t* sector_dim);
+
+/* Slot mask table computed by IsPhys: out_host receives n*(Na+1)*(Nb+1)
+ * bytes, entry [(p*(Na+1)+a)*(Nb+1)+b] = bit v set when outcome v of slot p
+ * is allowed after a prefix holding a alpha and b beta electrons (0 when the
+ * prefix itself is unphysical).  len must be at least that size. */
+ANQS_API int anqs_hamiltonian_slot_masks(const anqs_ham* ham, uint8_t* out_host, size_t len);
+
+/* ---------------------------------------------------------------------------
+ * Connected set (Eq. local_energy_def: the x' with H_xx' != 0 by symmetry)
+ *
+ * For each of the n_x sector determinants x_dev[l], writes its K =
+ * n_connected off-diagonal connected determinants to xp_dev[l*K + k], the
+ * matrix elements <x'|H|x> (FP64, Slater-Condon rules, Jordan-Wigner signs)
+ * to hval_dev[l*K + k], and optionally the first slot in which x' differs
+ * from x to first_slot_dev[l*K + k] and the diagonal element <x|H|x> to
+ * hdiag_dev[l].  Order within a row, fixed and documented so that lists can
+ * be compared element by element: alpha singles, beta singles (each (I, A)
+ * ascending, spatial indices), alpha-alpha doubles, beta-beta doubles (each
+ * (I, J, A, B) lexicographic with I < J, A < B), alpha-beta doubles
+ * (I_a, A_a, I_b, A_b) lexicographic.  Zero elements are kept.
+ * A determinant outside the sector gets xp = x, hval = NaN, first_slot = 255
+ * and hdiag = NaN on its row (no error code: the check runs on the device).
+ * first_slot_dev and hdiag_dev may be NULL.  n_x may be 0.
+ * ------------------------------------------------------------------------- */
+ANQS_API int anqs_connected(const anqs_ham* ham, const uint64_t* x_dev, uint64_t n_x,
+                   uint64_t* xp_dev, double* hval_dev, uint8_t* first_slot_dev,
+                   double* hdiag_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Model (Eq. anqs_def; Appendix B.1; MU masking Sec. III.C)
+ * ------------------------------------------------------------------------- */
+/* Number of float32 parameters of a model description. */
+ANQS_API int anqs_model_param_count(const anqs_model_desc* desc, uint64_t* n_params);
+
+/* Creates a model over params_dev (n_params floats, caller-owned device
+ * memory that must outlive the model; the library keeps the pointer).  The
+ * BF16 form keeps packed bfloat16 copies of the weights: call
+ * anqs_model_sync() after changing params_dev.  Synchronous.
+ * Errors: ANQS_ERR_ARG, ANQS_ERR_UNSUPPORTED (sizes outside the ranges of
+ * anqs_model_desc), ANQS_ERR_CUDA. */
+ANQS_API int anqs_model_create(anqs_model** out, const anqs_model_desc* desc, const float* params_dev);
+ANQS_API int anqs_model_destroy(anqs_model* model);
+
+/* Re-derive the model's internal copies from params_dev, ordered on stream. */
+ANQS_API int anqs_model_sync(anqs_model* model, void* stream);
+
+/* log psi(x) for n_x determinants: log_abs_dev[l] = log|psi(x_l)|,
+ * phase_dev[l] = arg psi(x_l) (unwrapped sum of slot phases), float32.
+ * A determinant outside the sector has log_abs = -inf.  The model's n_orb
+ * must equal the Hamiltonian's. */
+ANQS_API int anqs_logpsi(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev,
+                uint64_t n_x, float* log_abs_dev, float* phase_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Masked autoregressive statistics sampling (Sec. II.C with MU, Sec. III.C)
+ *
+ * Walks the slot tree breadth first.  A node with n_in samples splits them
+ * among its allowed outcomes by n_in uniform draws u_i: sample i takes the
+ * first allowed v with u_i < C_v, C_v the FP64 running sum of the masked
+ * conditional over allowed outcomes in ascending v (the last allowed v if
+ * rounding leaves u_i >= C_last).  The masked conditional is evaluated in
+ * FP64 as exp(l_v - max) / sum from the network's float32 logits.  u_i comes
+ * from Philox4x64-10 (Salmon et al., SC'11) with counter (prefix, i >> 2,
+ * slot, counter) and key (seed, 0), word i & 3, top 53 bits times 2^-53.
+ * Children with zero samples are dropped; no sample is lost (MU), so the
+ * counts add up to n_samples.
+ *
+ * Output: *n_unique_dev (device uint64) = N_unq; x_out_dev[0..N_unq) the
+ * unique determinants in lexicographic order of (v_0, v_1, ..., v_{n-1}),
+ * n_out_dev their occurrence numbers.  cap must be at least
+ * min(n_samples, sector_dim) (checked on the host: ANQS_ERR_CAPACITY).
+ * n_samples >= 1.
+ * ------------------------------------------------------------------------- */
+ANQS_API int anqs_sample_workspace_size(const anqs_model* model, const anqs_ham* ham,
+                               uint64_t n_samples, size_t* bytes);
+ANQS_API int anqs_sample(const anqs_model* model, const anqs_ham* ham, uint64_t n_samples,
+                uint64_t seed, uint64_t counter, uint64_t* x_out_dev, uint64_t* n_out_dev,
+                uint64_t cap, uint64_t* n_unique_dev, void* workspace_dev,
+                size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Local energy and energy statistics (Eq. local_energy_def, Eq. energy_est)
+ *
+ * eloc[l] = H_xx + sum_k H_{x x'_k} exp(log psi(x'_k) - log psi(x)), complex,
+ * accumulated in FP64 over the K connected determinants of x = x_dev[l].
+ * If counts_dev is not NULL, stats_dev receives 4 doubles
+ *   (Re E, Im E, Var, S) with S = sum_l n_l, E = sum_l n_l eloc_l / S,
+ *   Var = sum_l n_l |eloc_l - E|^2 / S.
+ * n_x >= 1.  Workspace from anqs_local_energy_workspace_size(n_x).
+ * ------------------------------------------------------------------------- */
+ANQS_API int anqs_local_energy_workspace_size(const anqs_model* model, const anqs_ham* ham,
+                                     uint64_t n_x, size_t* bytes);
+ANQS_API int anqs_local_energy(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev,
+                      const uint64_t* counts_dev, uint64_t n_x, double* eloc_re_dev,
+                      double* eloc_im_dev, double* stats_dev, void* workspace_dev,
+                      size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * VMC gradient (Eq. grad_def)
+ *
+ * grad = 2 Re{ E[eloc d ln psi*] - E[eloc] E[d ln psi*] } with expectations
+ * weighted by n_l / S and eloc held fixed:
+ *   grad = sum_l (n_l/S) 2 [ Re(eloc_l - E) d log|psi(x_l)| + Im(eloc_l - E) d arg psi(x_l) ]
+ * with E = stats[0] + i stats[1] and S = stats[3] (as written by
+ * anqs_local_energy).  grad_dev: n_params floats, overwritten.
+ * Hand-written adjoint of the masked log psi (MLP and transformer).
+ * ------------------------------------------------------------------------- */
+ANQS_API int anqs_grad_workspace_size(const anqs_model* model, const anqs_ham* ham, uint64_t n_x,
+                             size_t* bytes);
+ANQS_API int anqs_grad(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev,
+              const uint64_t* counts_dev, uint64_t n_x, const double* eloc_re_dev,
+              const double* eloc_im_dev, const double* stats_dev, float* grad_dev,
+              void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Adjoint of the masked log psi (vector-Jacobian product): grad_dev
+ * (n_params floats, overwritten) = d/dtheta sum_l [cot_abs_dev[l] log|psi(x_l)|
+ * + cot_phase_dev[l] arg psi(x_l)].  anqs_grad is this product with the
+ * cotangents 2 (n_l/S) Re(eloc_l - E) and 2 (n_l/S) Im(eloc_l - E).
+ * No workspace. */
+ANQS_API int anqs_logpsi_vjp(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev, uint64_t n_x,
+                    const float* cot_abs_dev, const float* cot_phase_dev, float* grad_dev, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ANQS_H */

@@ -52,8 +52,9 @@ def node_uniforms(prefix: int, count: int, p: int, seed: int, counter: int) -> n
     return uniform_from_word(w)
 
 
-def split_node(probs: np.ndarray, mask, u: np.ndarray):
-    """Counts per outcome and the smallest |u - C_v| over the draws."""
+def split_node(probs: np.ndarray, mask, u: np.ndarray, tol: float = 0.0):
+    """Counts per outcome, the smallest |u - C_v| over the draws and the
+    number of draws closer than tol to a boundary C_v."""
     C = np.zeros(4)
     run = 0.0
     allowed = [v for v in range(4) if mask[v]]
@@ -69,23 +70,30 @@ def split_node(probs: np.ndarray, mask, u: np.ndarray):
         undecided &= ~hit
     counts = np.bincount(out, minlength=4)
     margin = np.inf
+    close = np.zeros(len(u), dtype=bool)
     if len(u):
         for v in allowed[:-1]:
-            margin = min(margin, float(np.min(np.abs(u - C[v]))))
-    return counts, margin
+            d = np.abs(u - C[v])
+            margin = min(margin, float(np.min(d)))
+            close |= d < tol
+    return counts, margin, int(close.sum())
 
 
 def sample(model, isphys, n: int, n_samples: int, seed: int, counter: int = 0,
-           logits_fn=None):
+           logits_fn=None, tol: float | None = None):
     """Unique samples and counts, in the tree's lexicographic order.
 
     ``logits_fn(prefixes, p)`` may replace the network (returns [B, 4]
     modulus logits); by default the model's slot outputs are used.
-    Returns (x uint64[N_unq], counts int64[N_unq], min_margin).
+    Returns (x uint64[N_unq], counts int64[N_unq], min_margin), plus the
+    number of draws within tol of a boundary when tol is given (draws that
+    a sampler with conditionals perturbed by less than tol may assign
+    differently).
     """
     pre = np.zeros(1, dtype=np.uint64)
     cnt = np.array([n_samples], dtype=np.int64)
     margin = np.inf
+    n_close = 0
     for p in range(n):
         if logits_fn is None:
             L = model.slot_out(pre, p)[:, :4].detach().numpy()
@@ -96,14 +104,17 @@ def sample(model, isphys, n: int, n_samples: int, seed: int, counter: int = 0,
         for k in range(len(pre)):
             probs = split_probabilities(L[k], M[k])
             u = node_uniforms(int(pre[k]), int(cnt[k]), p, seed, counter)
-            c, mg = split_node(probs, M[k], u)
+            c, mg, nc = split_node(probs, M[k], u, tol or 0.0)
             margin = min(margin, mg)
+            n_close += nc
             for v in range(4):
                 if c[v] > 0:
                     new_pre.append(int(pre[k]) | (v << (2 * p)))
                     new_cnt.append(int(c[v]))
         pre = np.array(new_pre, dtype=np.uint64)
         cnt = np.array(new_cnt, dtype=np.int64)
+    if tol is not None:
+        return pre, cnt, margin, n_close
     return pre, cnt, margin
 
 

@@ -1,0 +1,250 @@
+"""Symmetry-masked autoregressive VMC hot path on one GB300 (libanqs).
+
+Thin Python binding over the C ABI of ``include/anqs.h``: argument
+marshalling only.  PyTorch provides device memory and streams; every step of
+the computation runs in the library's CUDA kernels.  If ``lib/libanqs.so``
+has not been built, every call raises.
+
+    ham   = Hamiltonian(h, g, e_nuc, n_alpha, n_beta)
+    model = Model.mlp(n_orb, width, n_hidden, params_cuda_f32, form="bf16")
+    x, n  = sample(model, ham, n_samples, seed)
+    eloc_re, eloc_im, stats = local_energy(model, ham, x, n)
+    g     = grad(model, ham, x, n, eloc_re, eloc_im, stats)
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import AnqsError, ModelDesc, check
+
+__all__ = ["Hamiltonian", "Model", "connected", "logpsi", "logpsi_vjp", "sample", "sample_into",
+           "local_energy", "grad", "LogPsi", "AnqsError", "library_path"]
+
+
+def library_path() -> str:
+    return _lib.LIB_PATH
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _u64(t: torch.Tensor) -> torch.Tensor:
+    if t.dtype not in (torch.int64, torch.uint64):
+        raise TypeError("determinants and counts are 64-bit integer tensors")
+    return t.contiguous()
+
+
+class Hamiltonian:
+    """Integrals and (N_alpha, N_beta) sector on the current CUDA device."""
+
+    def __init__(self, h, g, e_nuc: float, n_alpha: int, n_beta: int):
+        lib = _lib.load()
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        n = h.shape[0]
+        if h.shape != (n, n) or g.shape != (n, n, n, n):
+            raise ValueError("h must be n x n and g n x n x n x n")
+        self.n, self.n_alpha, self.n_beta = n, n_alpha, n_beta
+        self.device = torch.cuda.current_device()
+        hp = C.c_void_p()
+        check(lib.anqs_hamiltonian_create(C.byref(hp), n, n_alpha, n_beta, h.ctypes.data, g.ctypes.data,
+                                          float(e_nuc)))
+        self._h = hp
+        k, d = C.c_uint64(), C.c_uint64()
+        check(lib.anqs_hamiltonian_info(hp, C.byref(k), C.byref(d)))
+        self.n_connected, self.sector_dim = k.value, d.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def slot_masks(self) -> np.ndarray:
+        out = np.zeros((self.n, self.n_alpha + 1, self.n_beta + 1), dtype=np.uint8)
+        check(_lib.load().anqs_hamiltonian_slot_masks(self._h, out.ctypes.data, out.nbytes))
+        return out
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib._lib is not None:
+            _lib._lib.anqs_hamiltonian_destroy(self._h)
+            self._h = None
+
+
+class Model:
+    """Autoregressive ansatz over caller-owned float32 CUDA parameters."""
+
+    def __init__(self, desc: ModelDesc, params: torch.Tensor):
+        lib = _lib.load()
+        if params.device.type != "cuda" or params.dtype != torch.float32 or not params.is_contiguous():
+            raise TypeError("params must be a contiguous float32 CUDA tensor")
+        n = C.c_uint64()
+        check(lib.anqs_model_param_count(C.byref(desc), C.byref(n)))
+        if params.numel() != n.value:
+            raise ValueError(f"expected {n.value} parameters, got {params.numel()}")
+        self.desc, self.params, self.n_params = desc, params, n.value
+        mp = C.c_void_p()
+        with torch.cuda.device(params.device):
+            check(lib.anqs_model_create(C.byref(mp), C.byref(desc), params.data_ptr()))
+        self._m = mp
+
+    @classmethod
+    def mlp(cls, n_orb, width, n_hidden, params, form="fp32"):
+        d = ModelDesc(_lib.ANQS_MODEL_MLP, _form(form), n_orb, width, n_hidden, 0, 0, 0)
+        return cls(d, params)
+
+    @classmethod
+    def transformer(cls, n_orb, d_model, n_heads, n_layers, params, form="fp32"):
+        d = ModelDesc(_lib.ANQS_MODEL_TF, _form(form), n_orb, 0, 0, d_model, n_heads, n_layers)
+        return cls(d, params)
+
+    @classmethod
+    def table(cls, n_orb, params):
+        d = ModelDesc(_lib.ANQS_MODEL_TABLE, _lib.ANQS_FORM_FP32, n_orb, 0, 0, 0, 0, 0)
+        return cls(d, params)
+
+    @property
+    def n_orb(self):
+        return self.desc.n_orb
+
+    def sync(self, stream=None):
+        """Refresh internal copies after params changed (BF16 packing)."""
+        check(_lib.load().anqs_model_sync(self._m, _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "_m", None) and _lib._lib is not None:
+            _lib._lib.anqs_model_destroy(self._m)
+            self._m = None
+
+
+def _form(f):
+    return {"fp32": _lib.ANQS_FORM_FP32, "bf16": _lib.ANQS_FORM_BF16}[f] if isinstance(f, str) else int(f)
+
+
+def _ws(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def connected(ham: Hamiltonian, x: torch.Tensor, stream=None):
+    """(xp [n_x, K], hval [n_x, K] f64, first_slot [n_x, K] u8, hdiag [n_x] f64)."""
+    x = _u64(x)
+    n_x, K = x.numel(), ham.n_connected
+    xp = torch.empty((n_x, K), dtype=torch.int64, device=x.device)
+    hv = torch.empty((n_x, K), dtype=torch.float64, device=x.device)
+    js = torch.empty((n_x, K), dtype=torch.uint8, device=x.device)
+    hd = torch.empty(n_x, dtype=torch.float64, device=x.device)
+    check(_lib.load().anqs_connected(ham.handle, x.data_ptr(), n_x, xp.data_ptr(), hv.data_ptr(), js.data_ptr(),
+                                     hd.data_ptr(), _stream(stream)))
+    return xp, hv, js, hd
+
+
+def logpsi(model: Model, ham: Hamiltonian, x: torch.Tensor, stream=None):
+    """(log|psi(x)|, arg psi(x)) as float32 tensors."""
+    x = _u64(x)
+    la = torch.empty(x.numel(), dtype=torch.float32, device=x.device)
+    ph = torch.empty_like(la)
+    check(_lib.load().anqs_logpsi(model._m, ham.handle, x.data_ptr(), x.numel(), la.data_ptr(), ph.data_ptr(),
+                                  _stream(stream)))
+    return la, ph
+
+
+def logpsi_vjp(model: Model, ham: Hamiltonian, x: torch.Tensor, cot_abs: torch.Tensor, cot_phase: torch.Tensor,
+               stream=None):
+    x = _u64(x)
+    g = torch.empty(model.n_params, dtype=torch.float32, device=x.device)
+    ca = cot_abs.to(torch.float32).contiguous()
+    cp = cot_phase.to(torch.float32).contiguous()
+    check(_lib.load().anqs_logpsi_vjp(model._m, ham.handle, x.data_ptr(), x.numel(), ca.data_ptr(), cp.data_ptr(),
+                                      g.data_ptr(), _stream(stream)))
+    return g
+
+
+class LogPsi(torch.autograd.Function):
+    """log|psi|, arg psi of determinants as a function of the flat parameters;
+    the backward pass is the library's hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, params, model, ham, x):
+        ctx.model, ctx.ham = model, ham
+        ctx.save_for_backward(x)
+        return logpsi(model, ham, x)
+
+    @staticmethod
+    def backward(ctx, g_abs, g_phase):
+        (x,) = ctx.saved_tensors
+        if g_abs is None:
+            g_abs = torch.zeros(x.numel(), device=x.device)
+        if g_phase is None:
+            g_phase = torch.zeros(x.numel(), device=x.device)
+        return logpsi_vjp(ctx.model, ctx.ham, x, g_abs, g_phase), None, None, None
+
+
+def sample_workspace_bytes(model: Model, ham: Hamiltonian, n_samples: int) -> int:
+    b = C.c_size_t()
+    check(_lib.load().anqs_sample_workspace_size(model._m, ham.handle, n_samples, C.byref(b)))
+    return b.value
+
+
+def sample_into(model, ham, n_samples, seed, counter, x_out, n_out, n_unique, workspace, stream=None):
+    """Asynchronous sampling into preallocated device buffers (no host sync)."""
+    check(_lib.load().anqs_sample(model._m, ham.handle, int(n_samples), int(seed) & (2**64 - 1),
+                                  int(counter) & (2**64 - 1), x_out.data_ptr(), n_out.data_ptr(), x_out.numel(),
+                                  n_unique.data_ptr(), workspace.data_ptr(), workspace.numel(), _stream(stream)))
+
+
+def sample(model: Model, ham: Hamiltonian, n_samples: int, seed: int, counter: int = 0, stream=None):
+    """Unique determinants and their counts (trimmed; synchronises once)."""
+    dev = model.params.device
+    cap = min(int(n_samples), ham.sector_dim)
+    x = torch.empty(cap, dtype=torch.int64, device=dev)
+    n = torch.empty(cap, dtype=torch.int64, device=dev)
+    nu = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = _ws(sample_workspace_bytes(model, ham, n_samples), dev)
+    sample_into(model, ham, n_samples, seed, counter, x, n, nu, ws, stream)
+    k = int(nu.item())
+    return x[:k], n[:k]
+
+
+def local_energy_workspace_bytes(model, ham, n_x) -> int:
+    b = C.c_size_t()
+    check(_lib.load().anqs_local_energy_workspace_size(model._m, ham.handle, n_x, C.byref(b)))
+    return b.value
+
+
+def local_energy(model: Model, ham: Hamiltonian, x: torch.Tensor, counts: torch.Tensor | None = None,
+                 workspace: torch.Tensor | None = None, stream=None):
+    """(eloc_re f64, eloc_im f64, stats f64[4] or None)."""
+    x = _u64(x)
+    n_x = x.numel()
+    ere = torch.empty(n_x, dtype=torch.float64, device=x.device)
+    eim = torch.empty_like(ere)
+    stats = torch.empty(4, dtype=torch.float64, device=x.device) if counts is not None else None
+    if workspace is None:
+        workspace = _ws(local_energy_workspace_bytes(model, ham, n_x), x.device)
+    cnt = _u64(counts) if counts is not None else None
+    check(_lib.load().anqs_local_energy(model._m, ham.handle, x.data_ptr(), _ptr(cnt), n_x, ere.data_ptr(),
+                                        eim.data_ptr(), _ptr(stats), workspace.data_ptr(), workspace.numel(),
+                                        _stream(stream)))
+    return ere, eim, stats
+
+
+def grad(model: Model, ham: Hamiltonian, x, counts, eloc_re, eloc_im, stats, workspace=None, stream=None):
+    """VMC gradient (float32, flat parameter layout)."""
+    x, counts = _u64(x), _u64(counts)
+    g = torch.empty(model.n_params, dtype=torch.float32, device=x.device)
+    if workspace is None:
+        b = C.c_size_t()
+        check(_lib.load().anqs_grad_workspace_size(model._m, ham.handle, x.numel(), C.byref(b)))
+        workspace = _ws(b.value, x.device)
+    check(_lib.load().anqs_grad(model._m, ham.handle, x.data_ptr(), counts.data_ptr(), x.numel(),
+                                eloc_re.data_ptr(), eloc_im.data_ptr(), stats.data_ptr(), g.data_ptr(),
+                                workspace.data_ptr(), workspace.numel(), _stream(stream)))
+    return g

@@ -1,0 +1,508 @@
+// C ABI entry points of libanqs: argument checks, handles, sector table,
+// workspace planning and the order of kernel launches for each call.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace anqs {
+
+static thread_local std::string g_msg;
+static thread_local int g_code = ANQS_OK;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_msg = buf;
+  g_code = code;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  const char* base = strrchr(file, '/');
+  return set_error(ANQS_ERR_CUDA, "%s failed: %s (%s:%d)", what, cudaGetErrorString(e),
+                   base ? base + 1 : file, line);
+}
+
+// ---------------------------------------------------------------------------
+// IsPhys (Algorithm 1) over the qubit tree for the additive symmetries n_e
+// and 2 S_z (Appendix A), memoised in a dense lookup keyed by (i, n_e, 2 S_z)
+// (Proposition 1).  Qubit i (1-based) adds n_e += x_i and 2 S_z += x_i for
+// odd i (spin up), -x_i for even i.  The target is the pair of the
+// reference determinant: (N_a + N_b, N_a - N_b).
+// ---------------------------------------------------------------------------
+struct IsPhysTable {
+  int N, ne_ref, sz_ref;
+  std::vector<int8_t> memo;  // -1 unknown, 0 false, 1 true
+  IsPhysTable(int n_qubits, int ne, int sz) : N(n_qubits), ne_ref(ne), sz_ref(sz) {
+    memo.assign(size_t(N + 2) * (N + 1) * (2 * N + 1), -1);
+  }
+  size_t key(int i, int ne, int sz) const {
+    return (size_t(i) * (N + 1) + ne) * (2 * N + 1) + (sz + N);
+  }
+  bool operator()(int i, int ne, int sz) {
+    int8_t& m = memo[key(i, ne, sz)];
+    if (m >= 0) return m != 0;
+    bool r;
+    if (i == N + 1) {
+      r = (ne == ne_ref && sz == sz_ref);
+    } else {
+      int dsz = (i % 2 == 1) ? 1 : -1;
+      r = (*this)(i + 1, ne, sz) || (*this)(i + 1, ne + 1, sz + dsz);
+    }
+    m = r ? 1 : 0;
+    return r;
+  }
+};
+
+static uint64_t sat_mul(uint64_t a, uint64_t b) {
+  if (a == 0 || b == 0) return 0;
+  if (a > UINT64_MAX / b) return UINT64_MAX;
+  return a * b;
+}
+static uint64_t sat_add(uint64_t a, uint64_t b) { return (a > UINT64_MAX - b) ? UINT64_MAX : a + b; }
+static uint64_t binom(int n, int k) {
+  if (k < 0 || k > n) return 0;
+  uint64_t r = 1;
+  for (int i = 1; i <= k; ++i) r = r * (n - k + i) / i;  // exact for n <= 64 here
+  return r;
+}
+
+static int check_stream_device(int device) {
+  int cur = -1;
+  ANQS_CUDA(cudaGetDevice(&cur));
+  if (cur != device)
+    return set_error(ANQS_ERR_ARG, "handle belongs to device %d but device %d is current", device, cur);
+  return ANQS_OK;
+}
+
+}  // namespace anqs
+
+namespace anqs {
+int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, float* la,
+                    float* ph, cudaStream_t s) {
+  switch (M->d.kind) {
+    case ANQS_MODEL_MLP:
+      return launch_mlp_fp32_logpsi(M->mlp, H->v, x, n_x, la, ph, s);
+    case ANQS_MODEL_TABLE:
+      return launch_table_logpsi(M, H->v, x, n_x, la, ph, s);
+    default:
+      return set_error(ANQS_ERR_UNSUPPORTED, "model kind %d not available in this build", M->d.kind);
+  }
+}
+}  // namespace anqs
+
+namespace anqs {
+// FP32 form: every connected determinant evaluated over all slots.
+static size_t eloc_plain_ws(const anqs_ham* H, uint64_t n_x, Arena& A, uint64_t** xp, double** hv,
+                            double** hd, float** la_x, float** ph_x, float** la_p, float** ph_p) {
+  uint64_t m = n_x * H->v.K;
+  *xp = A.take<uint64_t>(m);
+  *hv = A.take<double>(m);
+  *hd = A.take<double>(n_x);
+  *la_x = A.take<float>(n_x);
+  *ph_x = A.take<float>(n_x);
+  *la_p = A.take<float>(m);
+  *ph_p = A.take<float>(m);
+  return A.off;
+}
+}  // namespace anqs
+
+namespace anqs {
+static int vjp_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, const float* cl,
+                        const float* cp, float* grad, cudaStream_t s) {
+  if (M->d.kind == ANQS_MODEL_MLP) return launch_mlp_fp32_grad(M->mlp, H->v, x, n_x, cl, cp, grad, s);
+  return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not available in this build", M->d.kind);
+}
+}  // namespace anqs
+
+using namespace anqs;
+
+extern "C" {
+
+const char* anqs_version(void) { return "anqs 0.1 (sm_103a)"; }
+
+int anqs_last_error(char* buf, size_t len) {
+  if (buf && len) {
+    size_t k = g_msg.size() < len - 1 ? g_msg.size() : len - 1;
+    memcpy(buf, g_msg.data(), k);
+    buf[k] = 0;
+  }
+  return g_code;
+}
+
+int anqs_hamiltonian_create(anqs_ham** out, int n, int na, int nb, const double* h_host,
+                            const double* g_host, double e_nuc) {
+  if (!out || !h_host || !g_host) return set_error(ANQS_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (n < 1 || n > ANQS_MAX_ORB) return set_error(ANQS_ERR_ARG, "n_orb=%d outside 1..32", n);
+  if (na < 0 || na > n || nb < 0 || nb > n)
+    return set_error(ANQS_ERR_SECTOR, "N_alpha=%d, N_beta=%d outside 0..%d", na, nb, n);
+  anqs_ham* H = new anqs_ham();
+  ANQS_CUDA(cudaGetDevice(&H->device));
+  HamView& v = H->v;
+  v.n = n;
+  v.na = na;
+  v.nb = nb;
+  uint64_t nsa = uint64_t(na) * (n - na), nsb = uint64_t(nb) * (n - nb);
+  uint64_t ndaa = binom(na, 2) * binom(n - na, 2), ndbb = binom(nb, 2) * binom(n - nb, 2);
+  uint64_t ndab = nsa * nsb;
+  uint64_t K = nsa + nsb + ndaa + ndbb + ndab;
+  if (K > 0x7fffffffull) {
+    delete H;
+    return set_error(ANQS_ERR_UNSUPPORTED, "connected set of %llu exceeds 2^31", (unsigned long long)K);
+  }
+  v.nsa = uint32_t(nsa);
+  v.nsb = uint32_t(nsb);
+  v.ndaa = uint32_t(ndaa);
+  v.ndbb = uint32_t(ndbb);
+  v.ndab = uint32_t(ndab);
+  v.K = uint32_t(K);
+  v.e_nuc = e_nuc;
+  H->sector_dim = sat_mul(binom(n, na), binom(n, nb));
+
+  // slot masks from the qubit-level IsPhys
+  IsPhysTable ip(2 * n, na + nb, na - nb);
+  H->mask_host.assign(size_t(n) * (na + 1) * (nb + 1), 0);
+  for (int p = 0; p < n; ++p)
+    for (int a = 0; a <= na; ++a)
+      for (int b = 0; b <= nb; ++b) {
+        if (a > p || b > p) continue;
+        if (!ip(2 * p + 1, a + b, a - b)) continue;
+        uint8_t m = 0;
+        for (int u = 0; u < 4; ++u) {
+          int da = u & 1, db = u >> 1;
+          if (ip(2 * p + 3, a + b + da + db, a - b + da - db)) m |= uint8_t(1u << u);
+        }
+        H->mask_host[mask_index(v, p, a, b)] = m;
+      }
+  // physical prefixes per level (bounds the sampler's frontier)
+  H->phys_prefix.assign(n + 1, 0);
+  for (int p = 0; p <= n; ++p) {
+    uint64_t c = 0;
+    for (int a = 0; a <= std::min(p, na); ++a)
+      for (int b = 0; b <= std::min(p, nb); ++b)
+        if (ip(2 * p + 1, a + b, a - b)) c = sat_add(c, sat_mul(binom(p, a), binom(p, b)));
+    H->phys_prefix[p] = c;
+  }
+  if (H->phys_prefix[n] == 0) {
+    delete H;
+    return set_error(ANQS_ERR_SECTOR, "empty sector");
+  }
+
+  size_t hn = size_t(n) * n, gn = hn * hn;
+  if (cudaMalloc(&H->d_h, hn * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&H->d_g, gn * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&H->d_mask, H->mask_host.size()) != cudaSuccess) {
+    cudaGetLastError();
+    anqs_hamiltonian_destroy(H);
+    return set_error(ANQS_ERR_CUDA, "cudaMalloc failed for Hamiltonian tables");
+  }
+  ANQS_CUDA(cudaMemcpy(H->d_h, h_host, hn * sizeof(double), cudaMemcpyHostToDevice));
+  ANQS_CUDA(cudaMemcpy(H->d_g, g_host, gn * sizeof(double), cudaMemcpyHostToDevice));
+  ANQS_CUDA(cudaMemcpy(H->d_mask, H->mask_host.data(), H->mask_host.size(), cudaMemcpyHostToDevice));
+  v.h = H->d_h;
+  v.g = H->d_g;
+  v.mask = H->d_mask;
+  *out = H;
+  return ANQS_OK;
+}
+
+int anqs_hamiltonian_destroy(anqs_ham* H) {
+  if (!H) return ANQS_OK;
+  cudaFree(H->d_h);
+  cudaFree(H->d_g);
+  cudaFree(H->d_mask);
+  delete H;
+  return ANQS_OK;
+}
+
+int anqs_hamiltonian_info(const anqs_ham* H, uint64_t* n_connected, uint64_t* sector_dim) {
+  if (!H) return set_error(ANQS_ERR_ARG, "null Hamiltonian");
+  if (n_connected) *n_connected = H->v.K;
+  if (sector_dim) *sector_dim = H->sector_dim;
+  return ANQS_OK;
+}
+
+int anqs_hamiltonian_slot_masks(const anqs_ham* H, uint8_t* out, size_t len) {
+  if (!H || !out) return set_error(ANQS_ERR_ARG, "null argument");
+  if (len < H->mask_host.size())
+    return set_error(ANQS_ERR_CAPACITY, "need %zu bytes", H->mask_host.size());
+  memcpy(out, H->mask_host.data(), H->mask_host.size());
+  return ANQS_OK;
+}
+
+int anqs_connected(const anqs_ham* H, const uint64_t* x, uint64_t n_x, uint64_t* xp, double* hval,
+                   uint8_t* first_slot, double* hdiag, void* stream) {
+  if (!H) return set_error(ANQS_ERR_ARG, "null Hamiltonian");
+  if (n_x == 0) return ANQS_OK;
+  if (!x || !xp || !hval) return set_error(ANQS_ERR_ARG, "null array argument");
+  ANQS_TRY(check_stream_device(H->device));
+  return launch_connected(H->v, x, n_x, xp, hval, first_slot, hdiag, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// models
+// ---------------------------------------------------------------------------
+static int validate_desc(const anqs_model_desc* d) {
+  if (!d) return set_error(ANQS_ERR_ARG, "null model description");
+  if (d->n_orb < 1 || d->n_orb > ANQS_MAX_ORB) return set_error(ANQS_ERR_ARG, "n_orb=%d outside 1..32", d->n_orb);
+  if (d->form != ANQS_FORM_FP32 && d->form != ANQS_FORM_BF16)
+    return set_error(ANQS_ERR_ARG, "unknown form %d", d->form);
+  switch (d->kind) {
+    case ANQS_MODEL_MLP:
+      if (d->width != 64 && d->width != 128 && d->width != 256)
+        return set_error(ANQS_ERR_UNSUPPORTED, "MLP width %d not in {64,128,256}", d->width);
+      if (d->n_hidden < 1 || d->n_hidden > 8)
+        return set_error(ANQS_ERR_UNSUPPORTED, "MLP hidden layers %d outside 1..8", d->n_hidden);
+      return ANQS_OK;
+    case ANQS_MODEL_TF:
+      if (d->d_model < 32 || d->d_model > 256 || d->d_model % 32)
+        return set_error(ANQS_ERR_UNSUPPORTED, "d_model %d not a multiple of 32 in 32..256", d->d_model);
+      if (d->n_heads < 1 || d->d_model % d->n_heads)
+        return set_error(ANQS_ERR_UNSUPPORTED, "n_heads %d does not divide d_model", d->n_heads);
+      if (d->n_layers < 1 || d->n_layers > 16)
+        return set_error(ANQS_ERR_UNSUPPORTED, "n_layers %d outside 1..16", d->n_layers);
+      return ANQS_OK;
+    case ANQS_MODEL_TABLE:
+      if (d->n_orb > 11) return set_error(ANQS_ERR_UNSUPPORTED, "table model needs n_orb <= 11");
+      if (d->form != ANQS_FORM_FP32) return set_error(ANQS_ERR_UNSUPPORTED, "table model is FP32 only");
+      return ANQS_OK;
+  }
+  return set_error(ANQS_ERR_ARG, "unknown model kind %d", d->kind);
+}
+
+static uint64_t count_params(const anqs_model_desc* d) {
+  uint64_t n = d->n_orb;
+  if (d->kind == ANQS_MODEL_MLP) {
+    uint64_t w = d->width, t = 0;
+    for (uint64_t p = 0; p < n; ++p) t += 4 * p * w + w + (d->n_hidden - 1) * (w * w + w) + 8 * w + 8;
+    return t;
+  }
+  if (d->kind == ANQS_MODEL_TF) {
+    uint64_t D = d->d_model;
+    uint64_t per = 4 * D + 4 * (D * D + D) + 2 * (4 * D * D) + 4 * D + D;
+    return 5 * D + n * D + d->n_layers * per + 2 * D + 8 * D + 8;
+  }
+  uint64_t t = 0, r = 1;
+  for (uint64_t p = 0; p < n; ++p, r *= 4) t += 8 * r;
+  return t;
+}
+
+int anqs_model_param_count(const anqs_model_desc* d, uint64_t* n) {
+  ANQS_TRY(validate_desc(d));
+  if (!n) return set_error(ANQS_ERR_ARG, "null output");
+  *n = count_params(d);
+  return ANQS_OK;
+}
+
+int anqs_model_create(anqs_model** out, const anqs_model_desc* d, const float* params) {
+  if (!out) return set_error(ANQS_ERR_ARG, "null output");
+  *out = nullptr;
+  ANQS_TRY(validate_desc(d));
+  if (!params) return set_error(ANQS_ERR_ARG, "null parameters");
+  anqs_model* M = new anqs_model();
+  M->d = *d;
+  ANQS_CUDA(cudaGetDevice(&M->device));
+  M->params = params;
+  M->n_params = count_params(d);
+  M->packed = nullptr;
+  M->packed_bytes = 0;
+  if (d->kind == ANQS_MODEL_MLP) {
+    MlpView& v = M->mlp;
+    v.n = d->n_orb;
+    v.width = d->width;
+    v.n_hidden = d->n_hidden;
+    v.params = params;
+    uint64_t off = 0, w = d->width;
+    for (int p = 0; p <= d->n_orb; ++p) {
+      v.slot_off[p] = uint32_t(off);
+      off += 4 * uint64_t(p) * w + w + (d->n_hidden - 1) * (w * w + w) + 8 * w + 8;
+    }
+    if (M->n_params > 0xffffffffull) {
+      delete M;
+      return set_error(ANQS_ERR_UNSUPPORTED, "too many parameters");
+    }
+    if (d->form == ANQS_FORM_BF16) {
+      int r = mlp_tc_pack_alloc(M);
+      if (r != ANQS_OK) {
+        delete M;
+        return r;
+      }
+      r = mlp_tc_pack(M, 0);
+      if (r == ANQS_OK && cudaDeviceSynchronize() != cudaSuccess) r = set_error(ANQS_ERR_CUDA, "pack failed");
+      if (r != ANQS_OK) {
+        anqs_model_destroy(M);
+        return r;
+      }
+    }
+  } else if (d->kind == ANQS_MODEL_TF) {
+    M->tf.n = d->n_orb;
+    M->tf.d = d->d_model;
+    M->tf.H = d->n_heads;
+    M->tf.L = d->n_layers;
+    M->tf.params = params;
+  }
+  *out = M;
+  return ANQS_OK;
+}
+
+int anqs_model_destroy(anqs_model* M) {
+  if (!M) return ANQS_OK;
+  if (M->packed) cudaFree(M->packed);
+  delete M;
+  return ANQS_OK;
+}
+
+int anqs_model_sync(anqs_model* M, void* stream) {
+  if (!M) return set_error(ANQS_ERR_ARG, "null model");
+  ANQS_TRY(check_stream_device(M->device));
+  if (M->d.kind == ANQS_MODEL_MLP && M->d.form == ANQS_FORM_BF16) return mlp_tc_pack(M, (cudaStream_t)stream);
+  return ANQS_OK;
+}
+
+static int check_pair(const anqs_model* M, const anqs_ham* H) {
+  if (!M || !H) return set_error(ANQS_ERR_ARG, "null model or Hamiltonian");
+  if (M->d.n_orb != H->v.n)
+    return set_error(ANQS_ERR_ARG, "model has %d slots, Hamiltonian %d orbitals", M->d.n_orb, H->v.n);
+  if (M->device != H->device) return set_error(ANQS_ERR_ARG, "model and Hamiltonian on different devices");
+  return check_stream_device(M->device);
+}
+
+
+int anqs_logpsi(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, float* la,
+                float* ph, void* stream) {
+  ANQS_TRY(check_pair(M, H));
+  if (n_x == 0) return ANQS_OK;
+  if (!x || !la || !ph) return set_error(ANQS_ERR_ARG, "null array argument");
+  return logpsi_dispatch(M, H, x, n_x, la, ph, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// sampling
+// ---------------------------------------------------------------------------
+int anqs_sample_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, size_t* bytes) {
+  ANQS_TRY(check_pair(M, H));
+  if (!bytes) return set_error(ANQS_ERR_ARG, "null output");
+  if (n_samples == 0) return set_error(ANQS_ERR_ARG, "n_samples must be >= 1");
+  *bytes = sampler_workspace(H, n_samples);
+  return ANQS_OK;
+}
+
+int anqs_sample(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint64_t seed,
+                uint64_t counter, uint64_t* x_out, uint64_t* n_out, uint64_t cap, uint64_t* n_unique,
+                void* ws, size_t ws_bytes, void* stream) {
+  ANQS_TRY(check_pair(M, H));
+  if (n_samples == 0) return set_error(ANQS_ERR_ARG, "n_samples must be >= 1");
+  if (!x_out || !n_out || !n_unique) return set_error(ANQS_ERR_ARG, "null output");
+  uint64_t need = n_samples < H->sector_dim ? n_samples : H->sector_dim;
+  if (cap < need)
+    return set_error(ANQS_ERR_CAPACITY, "cap %llu < min(n_samples, sector_dim) = %llu",
+                     (unsigned long long)cap, (unsigned long long)need);
+  size_t wsn = sampler_workspace(H, n_samples);
+  if (ws_bytes < wsn || (wsn && !ws))
+    return set_error(ANQS_ERR_CAPACITY, "sampler workspace needs %zu bytes", wsn);
+  return run_sampler(M, H, n_samples, seed, counter, x_out, n_out, n_unique, ws, ws_bytes,
+                     (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// local energy
+// ---------------------------------------------------------------------------
+
+static bool uses_tc_eloc(const anqs_model* M) {
+  return M->d.kind == ANQS_MODEL_MLP && M->d.form == ANQS_FORM_BF16;
+}
+
+int anqs_local_energy_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_x, size_t* bytes) {
+  ANQS_TRY(check_pair(M, H));
+  if (!bytes) return set_error(ANQS_ERR_ARG, "null output");
+  if (uses_tc_eloc(M)) {
+    *bytes = eloc_tc_workspace(M, H, n_x);
+    return ANQS_OK;
+  }
+  Arena A(nullptr, 0);
+  uint64_t* a;
+  double *b, *c;
+  float *d, *e, *f, *g;
+  *bytes = eloc_plain_ws(H, n_x, A, &a, &b, &c, &d, &e, &f, &g);
+  return ANQS_OK;
+}
+
+int anqs_local_energy(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const uint64_t* counts,
+                      uint64_t n_x, double* ere, double* eim, double* stats, void* ws, size_t ws_bytes,
+                      void* stream) {
+  ANQS_TRY(check_pair(M, H));
+  if (n_x == 0) return set_error(ANQS_ERR_ARG, "n_x must be >= 1");
+  if (!x || !ere || !eim) return set_error(ANQS_ERR_ARG, "null array argument");
+  if (counts && !stats) return set_error(ANQS_ERR_ARG, "counts given without stats output");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (uses_tc_eloc(M)) {
+    size_t need = eloc_tc_workspace(M, H, n_x);
+    if (ws_bytes < need || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
+    ANQS_TRY(run_eloc_tc(M, H, x, n_x, ere, eim, ws, ws_bytes, s));
+  } else {
+    Arena A(ws, ws_bytes);
+    uint64_t* xp;
+    double *hv, *hd;
+    float *la_x, *ph_x, *la_p, *ph_p;
+    size_t need = eloc_plain_ws(H, n_x, A, &xp, &hv, &hd, &la_x, &ph_x, &la_p, &ph_p);
+    if (ws_bytes < need || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
+    ANQS_TRY(launch_connected(H->v, x, n_x, xp, hv, nullptr, hd, s));
+    ANQS_TRY(logpsi_dispatch(M, H, x, n_x, la_x, ph_x, s));
+    ANQS_TRY(logpsi_dispatch(M, H, xp, n_x * H->v.K, la_p, ph_p, s));
+    ANQS_TRY(launch_eloc_sum(H->v, n_x, hv, hd, la_x, ph_x, la_p, ph_p, ere, eim, s));
+  }
+  if (counts) ANQS_TRY(launch_stats(ere, eim, counts, n_x, stats, s));
+  return ANQS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gradient
+// ---------------------------------------------------------------------------
+
+int anqs_grad_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_x, size_t* bytes) {
+  ANQS_TRY(check_pair(M, H));
+  if (!bytes) return set_error(ANQS_ERR_ARG, "null output");
+  Arena A(nullptr, 0);
+  A.take<float>(n_x);
+  A.take<float>(n_x);
+  *bytes = A.off;
+  return ANQS_OK;
+}
+
+int anqs_grad(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const uint64_t* counts, uint64_t n_x,
+              const double* ere, const double* eim, const double* stats, float* grad, void* ws,
+              size_t ws_bytes, void* stream) {
+  ANQS_TRY(check_pair(M, H));
+  if (n_x == 0) return set_error(ANQS_ERR_ARG, "n_x must be >= 1");
+  if (!x || !counts || !ere || !eim || !stats || !grad) return set_error(ANQS_ERR_ARG, "null array argument");
+  Arena A(ws, ws_bytes);
+  float* cl = A.take<float>(n_x);
+  float* cp = A.take<float>(n_x);
+  if (!A.fits() || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", A.off);
+  cudaStream_t s = (cudaStream_t)stream;
+  ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));
+  ANQS_TRY(launch_grad_cotangents(ere, eim, counts, stats, n_x, cl, cp, s));
+  return vjp_dispatch(M, H, x, n_x, cl, cp, grad, s);
+}
+
+int anqs_logpsi_vjp(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, const float* cl,
+                    const float* cp, float* grad, void* stream) {
+  ANQS_TRY(check_pair(M, H));
+  if (!grad) return set_error(ANQS_ERR_ARG, "null gradient output");
+  cudaStream_t s = (cudaStream_t)stream;
+  ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));
+  if (n_x == 0) return ANQS_OK;
+  if (!x || !cl || !cp) return set_error(ANQS_ERR_ARG, "null array argument");
+  return vjp_dispatch(M, H, x, n_x, cl, cp, grad, s);
+}
+
+}  // extern "C"

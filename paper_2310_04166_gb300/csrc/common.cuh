@@ -1,0 +1,166 @@
+// Internal declarations shared by the libanqs translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+#include <vector>
+
+#include "anqs.h"
+
+#define ANQS_MAX_ORB 32
+
+namespace anqs {
+
+int set_error(int code, const char* fmt, ...);
+int cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+}  // namespace anqs
+
+#define ANQS_CUDA(call)                                                  \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return anqs::cuda_error(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define ANQS_LAUNCHED(what)                                              \
+  do {                                                                   \
+    cudaError_t e_ = cudaGetLastError();                                 \
+    if (e_ != cudaSuccess) return anqs::cuda_error(e_, what, __FILE__, __LINE__); \
+  } while (0)
+
+#define ANQS_TRY(expr)            \
+  do {                            \
+    int r_ = (expr);              \
+    if (r_ != ANQS_OK) return r_; \
+  } while (0)
+
+// Hamiltonian as seen by the kernels (passed by value).
+struct HamView {
+  int n, na, nb;
+  uint32_t nsa, nsb, ndaa, ndbb, ndab;  // sizes of the five excitation blocks
+  uint32_t K;                           // off-diagonal connected per determinant
+  double e_nuc;
+  const double* h;     // [n][n]
+  const double* g;     // [n][n][n][n] chemist notation
+  const uint8_t* mask; // [n][na+1][nb+1] allowed-outcome bits per slot and prefix counts
+};
+
+__host__ __device__ inline int mask_index(const HamView& hv, int p, int a, int b) {
+  return (p * (hv.na + 1) + a) * (hv.nb + 1) + b;
+}
+
+#ifdef __CUDACC__
+// Allowed-outcome bits of slot p after a prefix with a alpha and b beta
+// electrons (0 if the counts already leave the sector).
+__device__ __forceinline__ unsigned slot_mask(const HamView& hv, int p, int a, int b) {
+  if (a > hv.na || b > hv.nb) return 0u;
+  return hv.mask[mask_index(hv, p, a, b)];
+}
+#endif
+
+// MLP parameters as seen by the kernels.
+struct MlpView {
+  int n, width, n_hidden;
+  const float* params;
+  uint32_t slot_off[ANQS_MAX_ORB + 1];
+};
+
+// Transformer parameters as seen by the kernels.
+struct TfView {
+  int n, d, H, L;
+  const float* params;
+};
+
+// Bump allocator over a caller-provided workspace; with base == nullptr it
+// only measures.
+struct Arena {
+  char* base;
+  size_t off, cap;
+  explicit Arena(void* b, size_t c) : base(static_cast<char*>(b)), off(0), cap(c) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+  bool fits() const { return off <= cap; }
+};
+
+struct anqs_ham {
+  int device;
+  HamView v;
+  uint64_t sector_dim;
+  std::vector<uint8_t> mask_host;
+  std::vector<uint64_t> phys_prefix;  // [p] physical prefixes holding slots < p (saturated)
+  double* d_h;
+  double* d_g;
+  uint8_t* d_mask;
+};
+
+struct anqs_model {
+  anqs_model_desc d;
+  int device;
+  const float* params;
+  uint64_t n_params;
+  MlpView mlp;
+  TfView tf;
+  // BF16 form: packed weight images (see mlp_tc.cu)
+  void* packed;
+  size_t packed_bytes;
+  std::vector<uint64_t> pack_off;  // per slot byte offset of its image
+};
+
+// ---- launchers implemented in the kernel translation units ----
+namespace anqs {
+
+// connect.cu
+int launch_connected(const HamView& hv, const uint64_t* x, uint64_t n_x, uint64_t* xp, double* hval,
+                     uint8_t* first_slot, double* hdiag, cudaStream_t s);
+
+// mlp_fp32.cu
+int launch_mlp_fp32_logpsi(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x,
+                           float* la, float* ph, cudaStream_t s);
+int launch_mlp_fp32_slot_logits(const MlpView& m, int p, const uint64_t* prefixes,
+                                const uint64_t* n_rows_dev, uint64_t max_rows, float* out8,
+                                cudaStream_t s);
+int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x,
+                         const float* cot_la, const float* cot_ph, float* grad, cudaStream_t s);
+
+// table.cu
+int launch_table_logpsi(const anqs_model* md, const HamView& hv, const uint64_t* x, uint64_t n_x,
+                        float* la, float* ph, cudaStream_t s);
+int launch_table_slot_logits(const anqs_model* md, int p, const uint64_t* prefixes,
+                             const uint64_t* n_rows_dev, uint64_t max_rows, float* out8,
+                             cudaStream_t s);
+
+// eloc.cu
+int launch_eloc_sum(const HamView& hv, uint64_t n_x, const double* hval, const double* hdiag,
+                    const float* la_x, const float* ph_x, const float* la_p, const float* ph_p,
+                    double* ere, double* eim, cudaStream_t s);
+int launch_stats(const double* ere, const double* eim, const uint64_t* counts, uint64_t n_x,
+                 double* stats, cudaStream_t s);
+int launch_grad_cotangents(const double* ere, const double* eim, const uint64_t* counts,
+                           const double* stats, uint64_t n_x, float* cot_la, float* cot_ph,
+                           cudaStream_t s);
+
+// mlp_tc.cu (BF16 tensor-core form)
+int mlp_tc_pack_alloc(anqs_model* m);
+int mlp_tc_pack(anqs_model* m, cudaStream_t s);
+size_t eloc_tc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x);
+int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, double* ere,
+                double* eim, void* ws, size_t ws_bytes, cudaStream_t s);
+
+// api.cu
+int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, float* la,
+                    float* ph, cudaStream_t s);
+
+// sampler.cu
+size_t sampler_workspace(const anqs_ham* ham, uint64_t n_samples);
+int run_sampler(const anqs_model* md, const anqs_ham* ham, uint64_t n_samples, uint64_t seed,
+                uint64_t counter, uint64_t* x_out, uint64_t* n_out, uint64_t* n_unique, void* ws,
+                size_t ws_bytes, cudaStream_t s);
+
+}  // namespace anqs

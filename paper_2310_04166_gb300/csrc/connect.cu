@@ -1,0 +1,213 @@
+// Connected set of a determinant: single and double excitations that keep
+// N_alpha and N_beta, with Jordan-Wigner signs and Slater-Condon elements
+// (Eq. local_energy_def, Eq. sq_hamiltonian, Sec. IV.A).
+//
+// One thread per (determinant l, excitation k).  The excitation index k is
+// unranked directly into the fixed order (alpha singles, beta singles,
+// alpha-alpha doubles, beta-beta doubles, alpha-beta doubles), so that the
+// output needs no sort and every row has the same length K.  Integer work
+// (x', sign, first slot) is exact; matrix elements are FP64.
+#include "common.cuh"
+
+namespace anqs {
+namespace {
+
+__device__ __forceinline__ uint32_t spin_occ(uint64_t x, int s, int n) {
+  uint32_t m = 0;
+  for (int p = 0; p < n; ++p) m |= uint32_t((x >> (2 * p + s)) & 1ull) << p;
+  return m;
+}
+
+// position of the r-th (0-based) set bit of m
+__device__ __forceinline__ int nth_bit(uint32_t m, int r) {
+  for (int i = 0; i < r; ++i) m &= m - 1;
+  return __ffs(m) - 1;
+}
+
+// parity of the occupied spin-orbitals below q
+__device__ __forceinline__ int par_below(uint64_t x, int q) {
+  return __popcll(x & ((1ull << q) - 1ull)) & 1;
+}
+
+// unrank a pair (i < j) of an m-element list in lexicographic order
+__device__ __forceinline__ void unrank_pair(uint32_t idx, int m, int& i, int& j) {
+  i = 0;
+  while (idx >= uint32_t(m - 1 - i)) {
+    idx -= uint32_t(m - 1 - i);
+    ++i;
+  }
+  j = i + 1 + int(idx);
+}
+
+__device__ __forceinline__ double G(const HamView& hv, int p, int q, int r, int s) {
+  int n = hv.n;
+  return __ldg(hv.g + ((size_t(p) * n + q) * n + r) * n + s);
+}
+
+// <x|H|x> = E_nuc + sum_I h_ii + 1/2 sum_{I,J occ} ([II|JJ] - [IJ|JI])
+__device__ double diagonal_element(const HamView& hv, uint32_t oa, uint32_t ob) {
+  int n = hv.n;
+  double e = hv.e_nuc;
+  uint32_t occ[2] = {oa, ob};
+  for (int s = 0; s < 2; ++s)
+    for (uint32_t m = occ[s]; m; m &= m - 1) {
+      int i = __ffs(m) - 1;
+      e += __ldg(hv.h + i * n + i);
+    }
+  double c = 0.0, xch = 0.0;
+  for (int s = 0; s < 2; ++s)
+    for (uint32_t m = occ[s]; m; m &= m - 1) {
+      int i = __ffs(m) - 1;
+      for (int t = 0; t < 2; ++t)
+        for (uint32_t m2 = occ[t]; m2; m2 &= m2 - 1) {
+          int j = __ffs(m2) - 1;
+          c += G(hv, i, i, j, j);
+          if (s == t) xch += G(hv, i, j, j, i);
+        }
+    }
+  return e + 0.5 * (c - xch);
+}
+
+__global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, uint64_t n_x,
+                                 uint64_t* __restrict__ xp_out, double* __restrict__ h_out,
+                                 uint8_t* __restrict__ j_out) {
+  const uint64_t K = hv.K;
+  const uint64_t total = n_x * K;
+  const int n = hv.n;
+  for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < total;
+       t += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t l = t / K;
+    uint32_t k = uint32_t(t - l * K);
+    uint64_t x = __ldg(xs + l);
+    uint32_t oa = spin_occ(x, 0, n), ob = spin_occ(x, 1, n);
+    uint32_t full = (n == 32) ? 0xffffffffu : ((1u << n) - 1u);
+    bool ok = (__popc(oa) == hv.na) && (__popc(ob) == hv.nb) && (n == 32 || (x >> (2 * n)) == 0);
+    if (!ok) {
+      xp_out[t] = x;
+      h_out[t] = __longlong_as_double(0x7ff8000000000000ll);
+      if (j_out) j_out[t] = 255;
+      continue;
+    }
+    uint32_t va = full & ~oa, vb = full & ~ob;
+    uint64_t xn;
+    double val;
+    int jfirst;
+    if (k < hv.nsa + hv.nsb) {
+      // single I -> A of spin s: (h_ai + sum_{J occ} ([AI|JJ] - [AJ|JI])) <x'|a+_A a_I|x>
+      int s = k < hv.nsa ? 0 : 1;
+      uint32_t idx = s ? k - hv.nsa : k;
+      int nv = n - (s ? hv.nb : hv.na);
+      int i = nth_bit(s ? ob : oa, int(idx / nv));
+      int a = nth_bit(s ? vb : va, int(idx % nv));
+      int I = 2 * i + s, A = 2 * a + s;
+      xn = x ^ (1ull << I) ^ (1ull << A);
+      int lo = min(I, A), hi = max(I, A);
+      uint64_t between = ((1ull << hi) - 1ull) & ~((2ull << lo) - 1ull);
+      int sign = __popcll(x & between) & 1;
+      double v = __ldg(hv.h + a * n + i);
+      for (int t2 = 0; t2 < 2; ++t2)
+        for (uint32_t m = t2 ? ob : oa; m; m &= m - 1) {
+          int jj = __ffs(m) - 1;
+          v += G(hv, a, i, jj, jj);
+          if (t2 == s) v -= G(hv, a, jj, jj, i);
+        }
+      val = sign ? -v : v;
+      jfirst = min(i, a);
+    } else {
+      uint32_t r = k - hv.nsa - hv.nsb;
+      int I, J, A, B;
+      double v;
+      int i, j, a, b;
+      if (r < hv.ndaa + hv.ndbb) {
+        // same-spin double I<J -> A<B: [AI|BJ] - [AJ|BI]
+        int s = r < hv.ndaa ? 0 : 1;
+        uint32_t idx = s ? r - hv.ndaa : r;
+        int ne = s ? hv.nb : hv.na, nv = n - ne;
+        uint32_t nvp = uint32_t(nv) * (nv - 1) / 2;
+        int ri, rj, ra, rb;
+        unrank_pair(idx / nvp, ne, ri, rj);
+        unrank_pair(idx % nvp, nv, ra, rb);
+        uint32_t om = s ? ob : oa, vm = s ? vb : va;
+        i = nth_bit(om, ri);
+        j = nth_bit(om, rj);
+        a = nth_bit(vm, ra);
+        b = nth_bit(vm, rb);
+        I = 2 * i + s;
+        J = 2 * j + s;
+        A = 2 * a + s;
+        B = 2 * b + s;
+        v = G(hv, a, i, b, j) - G(hv, a, j, b, i);
+      } else {
+        // opposite-spin double (I_a, A_a, I_b, A_b): [AI|BJ] (exchange term vanishes by spin)
+        uint32_t idx = r - hv.ndaa - hv.ndbb;
+        int nva = n - hv.na, nvb = n - hv.nb;
+        int rab = int(idx % nvb);
+        idx /= nvb;
+        int rib = int(idx % hv.nb);
+        idx /= hv.nb;
+        int raa = int(idx % nva);
+        int ria = int(idx / nva);
+        i = nth_bit(oa, ria);
+        a = nth_bit(va, raa);
+        j = nth_bit(ob, rib);
+        b = nth_bit(vb, rab);
+        I = 2 * i;
+        A = 2 * a;
+        J = 2 * j + 1;
+        B = 2 * b + 1;
+        v = G(hv, a, i, b, j);
+      }
+      // sign of <x'| a+_A a+_B a_J a_I |x>, operators applied right to left
+      uint64_t y = x;
+      int sg = par_below(y, I);
+      y ^= 1ull << I;
+      sg ^= par_below(y, J);
+      y ^= 1ull << J;
+      sg ^= par_below(y, B);
+      y ^= 1ull << B;
+      sg ^= par_below(y, A);
+      y ^= 1ull << A;
+      xn = y;
+      val = sg ? -v : v;
+      jfirst = min(min(i, j), min(a, b));
+    }
+    xp_out[t] = xn;
+    h_out[t] = val;
+    if (j_out) j_out[t] = uint8_t(jfirst);
+  }
+}
+
+__global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, uint64_t n_x,
+                                double* __restrict__ hdiag) {
+  const int n = hv.n;
+  for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x;
+       l += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t x = __ldg(xs + l);
+    uint32_t oa = spin_occ(x, 0, n), ob = spin_occ(x, 1, n);
+    bool ok = (__popc(oa) == hv.na) && (__popc(ob) == hv.nb) && (n == 32 || (x >> (2 * n)) == 0);
+    hdiag[l] = ok ? diagonal_element(hv, oa, ob) : __longlong_as_double(0x7ff8000000000000ll);
+  }
+}
+
+}  // namespace
+
+int launch_connected(const HamView& hv, const uint64_t* x, uint64_t n_x, uint64_t* xp, double* hval,
+                     uint8_t* first_slot, double* hdiag, cudaStream_t s) {
+  const int threads = 256;
+  uint64_t total = n_x * hv.K;
+  if (total) {
+    uint64_t blocks = (total + threads - 1) / threads;
+    if (blocks > 152ull * 64) blocks = 152ull * 64;
+    connected_kernel<<<unsigned(blocks), threads, 0, s>>>(hv, x, n_x, xp, hval, first_slot);
+    ANQS_LAUNCHED("connected_kernel");
+  }
+  if (hdiag) {
+    uint64_t blocks = (n_x + threads - 1) / threads;
+    if (blocks > 152ull * 16) blocks = 152ull * 16;
+    diagonal_kernel<<<unsigned(blocks), threads, 0, s>>>(hv, x, n_x, hdiag);
+    ANQS_LAUNCHED("diagonal_kernel");
+  }
+  return ANQS_OK;
+}
+
+}  // namespace anqs

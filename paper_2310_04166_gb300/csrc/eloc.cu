@@ -1,0 +1,132 @@
+// Local-energy accumulation and count-weighted statistics in FP64
+// (Eq. local_energy_def, Eq. energy_est), and the per-sample cotangents of
+// the VMC gradient (Eq. grad_def).
+#include <cmath>
+
+#include "common.cuh"
+
+namespace anqs {
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// one warp per determinant: eloc = H_xx + sum_k H_k exp(dlog|psi| + i dphase)
+__global__ void eloc_sum_kernel(uint32_t K, uint64_t n_x, const double* __restrict__ hval,
+                                const double* __restrict__ hdiag, const float* __restrict__ la_x,
+                                const float* __restrict__ ph_x, const float* __restrict__ la_p,
+                                const float* __restrict__ ph_p, double* __restrict__ ere,
+                                double* __restrict__ eim) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+  for (uint64_t l = blockIdx.x * uint64_t(blockDim.x >> 5) + (threadIdx.x >> 5); l < n_x; l += warps) {
+    const double lx = la_x[l], px = ph_x[l];
+    double re = 0.0, im = 0.0;
+    const uint64_t base = l * K;
+    for (uint32_t k = lane; k < K; k += 32) {
+      double h = hval[base + k];
+      double r = exp(double(la_p[base + k]) - lx);
+      double s, c;
+      sincos(double(ph_p[base + k]) - px, &s, &c);
+      re = fma(h * r, c, re);
+      im = fma(h * r, s, im);
+    }
+    re = warp_sum(re);
+    im = warp_sum(im);
+    if (lane == 0) {
+      ere[l] = hdiag[l] + re;
+      eim[l] = im;
+    }
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (w == 0) {
+    t = lane < int(blockDim.x >> 5) ? red[lane] : 0.0;
+    t = warp_sum(t);
+    if (lane == 0) red[0] = t;
+  }
+  __syncthreads();
+  return red[0];
+}
+
+// single CTA: S, E (complex) then Var in a second pass
+__global__ void stats_kernel(const double* __restrict__ ere, const double* __restrict__ eim,
+                             const uint64_t* __restrict__ counts, uint64_t n_x, double* __restrict__ stats) {
+  __shared__ double red[32];
+  double s = 0.0, sr = 0.0, si = 0.0;
+  for (uint64_t l = threadIdx.x; l < n_x; l += blockDim.x) {
+    double w = double(counts[l]);
+    s += w;
+    sr = fma(w, ere[l], sr);
+    si = fma(w, eim[l], si);
+  }
+  s = block_sum(s, red);
+  sr = block_sum(sr, red);
+  si = block_sum(si, red);
+  const double Er = sr / s, Ei = si / s;
+  double v = 0.0;
+  for (uint64_t l = threadIdx.x; l < n_x; l += blockDim.x) {
+    double w = double(counts[l]);
+    double dr = ere[l] - Er, di = eim[l] - Ei;
+    v = fma(w, dr * dr + di * di, v);
+  }
+  v = block_sum(v, red);
+  if (threadIdx.x == 0) {
+    stats[0] = Er;
+    stats[1] = Ei;
+    stats[2] = v / s;
+    stats[3] = s;
+  }
+}
+
+// cot_la = 2 w Re(eloc - E), cot_ph = 2 w Im(eloc - E), w = n / S
+__global__ void cotangent_kernel(const double* __restrict__ ere, const double* __restrict__ eim,
+                                 const uint64_t* __restrict__ counts, const double* __restrict__ stats,
+                                 uint64_t n_x, float* __restrict__ cl, float* __restrict__ cp) {
+  const double Er = stats[0], Ei = stats[1], S = stats[3];
+  for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x; l += uint64_t(gridDim.x) * blockDim.x) {
+    double w = double(counts[l]) / S;
+    cl[l] = float(2.0 * w * (ere[l] - Er));
+    cp[l] = float(2.0 * w * (eim[l] - Ei));
+  }
+}
+
+}  // namespace
+
+int launch_eloc_sum(const HamView& hv, uint64_t n_x, const double* hval, const double* hdiag, const float* la_x,
+                    const float* ph_x, const float* la_p, const float* ph_p, double* ere, double* eim,
+                    cudaStream_t s) {
+  uint64_t blocks = (n_x + 7) / 8;  // 8 warps per CTA
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  eloc_sum_kernel<<<unsigned(blocks), 256, 0, s>>>(hv.K, n_x, hval, hdiag, la_x, ph_x, la_p, ph_p, ere, eim);
+  ANQS_LAUNCHED("eloc_sum_kernel");
+  return ANQS_OK;
+}
+
+int launch_stats(const double* ere, const double* eim, const uint64_t* counts, uint64_t n_x, double* stats,
+                 cudaStream_t s) {
+  stats_kernel<<<1, 1024, 0, s>>>(ere, eim, counts, n_x, stats);
+  ANQS_LAUNCHED("stats_kernel");
+  return ANQS_OK;
+}
+
+int launch_grad_cotangents(const double* ere, const double* eim, const uint64_t* counts, const double* stats,
+                           uint64_t n_x, float* cl, float* cp, cudaStream_t s) {
+  uint64_t blocks = (n_x + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  cotangent_kernel<<<unsigned(blocks), 256, 0, s>>>(ere, eim, counts, stats, n_x, cl, cp);
+  ANQS_LAUNCHED("cotangent_kernel");
+  return ANQS_OK;
+}
+
+}  // namespace anqs

@@ -1,0 +1,440 @@
+// Plain FP32 form of the per-slot MLP ansatz (SIMT, no tensor cores, no
+// prefix reuse): log psi of arbitrary determinants, slot logits for the
+// sampler, and the hand-written adjoint for the VMC gradient.
+//
+// Slot p's network (Appendix B.1 layout with one network per spatial
+// orbital): h_1 = tanh(b_1 + sum_{q<p} W_1[:, 4q + v_q]) (the one-hot input
+// is a column gather), h_k = tanh(W_k h_{k-1} + b_k) for k = 2..L, and the
+// head out = W_{L+1} h_L + b_{L+1} = (l_0..l_3, phi_0..phi_3).  The slot
+// conditional is the masked softmax of l over the allowed outcomes
+// (activation f3 of Appendix B.1 with MU masking, Sec. III.C).
+//
+// A CTA of 256 threads owns a tile of R = 32 rows; activations stay in
+// shared memory, weights stream through a padded shared-memory chunk.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace anqs {
+namespace {
+
+constexpr int R = 32;    // rows per CTA tile
+constexpr int NT = 256;  // threads per CTA
+constexpr int KC = 32;   // weight chunk depth
+
+struct MlpPtr {
+  const float* W1;  // [w][4p] (absent for p = 0)
+  const float* b1;  // [w]
+  const float* Wk;  // first hidden-to-hidden matrix
+  const float* Wh;  // head [8][w]
+  const float* bh;  // [8]
+};
+
+__device__ __forceinline__ MlpPtr slot_ptrs(const MlpView& m, int p) {
+  MlpPtr r;
+  const int w = m.width;
+  r.W1 = m.params + m.slot_off[p];
+  r.b1 = r.W1 + size_t(w) * 4 * p;
+  r.Wk = r.b1 + w;
+  r.Wh = r.Wk + size_t(m.n_hidden - 1) * (size_t(w) * w + w);
+  r.bh = r.Wh + 8 * w;
+  return r;
+}
+
+// out[r][c] = sum_k in[r][k] * B(k, c), B(k, c) = W[c][k] (forward) or W[k][c]
+// (adjoint).  Each warp owns R/8 rows, each lane W/32 columns.
+template <int W, bool ADJ>
+__device__ __forceinline__ void tile_gemm(const float* in, const float* __restrict__ Wg, float* ws,
+                                          float (&acc)[R / 8][W / 32]) {
+  constexpr int RPT = R / 8, CPT = W / 32;
+  const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < RPT; ++i)
+#pragma unroll
+    for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < W; k0 += KC) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < KC * W; idx += NT) {
+      int c, kk;
+      float val;
+      if (!ADJ) {
+        c = idx / KC;
+        kk = idx % KC;
+        val = __ldg(Wg + size_t(c) * W + k0 + kk);
+      } else {
+        kk = idx / W;
+        c = idx % W;
+        val = __ldg(Wg + size_t(k0 + kk) * W + c);
+      }
+      ws[kk * (W + 1) + c] = val;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      float a[RPT], b[CPT];
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) a[i] = in[(wg * RPT + i) * W + k0 + kk];
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) b[j] = ws[kk * (W + 1) + lane + 32 * j];
+#pragma unroll
+      for (int i = 0; i < RPT; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+  }
+}
+
+template <int W>
+struct Smem {
+  static constexpr size_t ws_floats = KC * (W + 1);
+  static size_t bytes(int n_act) { return (size_t(n_act) * R * W + ws_floats + R * 8) * sizeof(float); }
+};
+
+// Forward of slot p for the R rows whose determinants are xs[0..R) (rows
+// >= nrows are computed on garbage-free zeros and ignored).  act holds
+// n_keep activation buffers [R][W]: with n_keep == L every layer's output is
+// kept (for the adjoint), with n_keep == 2 they ping-pong.  Leaves the head
+// outputs in out8[R][8] and returns the index of the last hidden buffer.
+template <int W>
+__device__ int slot_forward(const MlpView& m, int p, const uint64_t* xs, int nrows, float* act, int n_keep,
+                            float* ws, float* out8) {
+  const MlpPtr P = slot_ptrs(m, p);
+  for (int idx = threadIdx.x; idx < R * W; idx += NT) {
+    int r = idx / W, o = idx % W;
+    float acc = __ldg(P.b1 + o);
+    if (r < nrows) {
+      uint64_t x = xs[r];
+      const float* wrow = P.W1 + size_t(o) * 4 * p;
+      for (int q = 0; q < p; ++q) acc += __ldg(wrow + 4 * q + int((x >> (2 * q)) & 3ull));
+    }
+    act[idx] = tanhf(acc);
+  }
+  int cur = 0;
+  const float* Wk = P.Wk;
+  constexpr int RPT = R / 8, CPT = W / 32;
+  const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
+  for (int k = 2; k <= m.n_hidden; ++k) {
+    const float* bk = Wk + size_t(W) * W;
+    float acc[RPT][CPT];
+    tile_gemm<W, false>(act + size_t(cur) * R * W, Wk, ws, acc);
+    int nxt = (n_keep == 2) ? (cur ^ 1) : (cur + 1);
+    float* o = act + size_t(nxt) * R * W;
+#pragma unroll
+    for (int i = 0; i < RPT; ++i)
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        int c = lane + 32 * j;
+        o[(wg * RPT + i) * W + c] = tanhf(acc[i][j] + __ldg(bk + c));
+      }
+    cur = nxt;
+    Wk = bk + W;
+  }
+  __syncthreads();
+  {
+    const float* h = act + size_t(cur) * R * W;
+    int r = threadIdx.x >> 3, o = threadIdx.x & 7;  // R * 8 == NT
+    float acc = __ldg(P.bh + o);
+    const float* wr = P.Wh + size_t(o) * W;
+    for (int k = 0; k < W; ++k) acc = fmaf(h[r * W + ((k + r) & (W - 1))], __ldg(wr + ((k + r) & (W - 1))), acc);
+    out8[r * 8 + o] = acc;
+  }
+  __syncthreads();
+  return cur;
+}
+
+// masked log-softmax term of the chosen outcome (FP32)
+__device__ __forceinline__ void slot_term(const float* o8, unsigned mask, int v, float& la, float& ph, bool& dead) {
+  if (!((mask >> v) & 1u)) {
+    dead = true;
+    return;
+  }
+  float mx = -INFINITY;
+  for (int u = 0; u < 4; ++u)
+    if ((mask >> u) & 1u) mx = fmaxf(mx, o8[u]);
+  float s = 0.f;
+  for (int u = 0; u < 4; ++u)
+    if ((mask >> u) & 1u) s += expf(o8[u] - mx);
+  la += 0.5f * (o8[v] - mx - logf(s));
+  ph += o8[4 + v];
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT) logpsi_kernel(MlpView m, HamView hv, const uint64_t* __restrict__ xs,
+                                                    uint64_t n_x, float* __restrict__ la_out,
+                                                    float* __restrict__ ph_out) {
+  extern __shared__ float smem[];
+  float* act = smem;
+  float* ws = act + 2 * R * W;
+  float* out8 = ws + Smem<W>::ws_floats;
+  __shared__ uint64_t xt[R];
+  __shared__ float la[R], ph[R];
+  __shared__ int ca[R], cb[R], dead[R];
+  const uint64_t n_tiles = (n_x + R - 1) / R;
+  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const uint64_t base = tile * R;
+    const int nrows = int(n_x - base < uint64_t(R) ? n_x - base : uint64_t(R));
+    if (threadIdx.x < R) {
+      xt[threadIdx.x] = threadIdx.x < nrows ? xs[base + threadIdx.x] : 0ull;
+      la[threadIdx.x] = 0.f;
+      ph[threadIdx.x] = 0.f;
+      ca[threadIdx.x] = cb[threadIdx.x] = dead[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (int p = 0; p < m.n; ++p) {
+      slot_forward<W>(m, p, xt, nrows, act, 2, ws, out8);
+      if (threadIdx.x < nrows) {
+        int r = threadIdx.x;
+        int v = int((xt[r] >> (2 * p)) & 3ull);
+        unsigned mk = slot_mask(hv, p, ca[r], cb[r]);
+        bool dd = dead[r];
+        slot_term(out8 + r * 8, mk, v, la[r], ph[r], dd);
+        dead[r] = dd;
+        ca[r] += v & 1;
+        cb[r] += v >> 1;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x < nrows) {
+      int r = threadIdx.x;
+      bool out_of_sector = dead[r] || (hv.n < 32 && (xt[r] >> (2 * hv.n)) != 0);
+      la_out[base + r] = out_of_sector ? -INFINITY : la[r];
+      ph_out[base + r] = ph[r];
+    }
+    __syncthreads();
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT) slot_logits_kernel(MlpView m, int p, const uint64_t* __restrict__ prefixes,
+                                                         const uint64_t* __restrict__ n_rows_dev,
+                                                         float* __restrict__ out) {
+  extern __shared__ float smem[];
+  float* act = smem;
+  float* ws = act + 2 * R * W;
+  float* out8 = ws + Smem<W>::ws_floats;
+  __shared__ uint64_t xt[R];
+  const uint64_t n_rows = *n_rows_dev;
+  const uint64_t n_tiles = (n_rows + R - 1) / R;
+  for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const uint64_t base = tile * R;
+    const int nrows = int(n_rows - base < uint64_t(R) ? n_rows - base : uint64_t(R));
+    if (threadIdx.x < R) xt[threadIdx.x] = threadIdx.x < nrows ? prefixes[base + threadIdx.x] : 0ull;
+    __syncthreads();
+    slot_forward<W>(m, p, xt, nrows, act, 2, ws, out8);
+    int r = threadIdx.x >> 3, o = threadIdx.x & 7;
+    if (r < nrows) out[(base + r) * 8 + o] = out8[r * 8 + o];
+    __syncthreads();
+  }
+}
+
+// Adjoint of sum_l [cot_la_l log|psi(x_l)| + cot_ph_l arg psi(x_l)] with
+// respect to slot p's parameters, for one tile of rows; partial sums over
+// the tile are added to grad with atomics.
+template <int W>
+__global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const uint64_t* __restrict__ xs,
+                                                  uint64_t n_x, const float* __restrict__ cot_la,
+                                                  const float* __restrict__ cot_ph, float* __restrict__ grad) {
+  extern __shared__ float smem[];
+  const int L = m.n_hidden;
+  float* act = smem;                       // L buffers [R][W]: h_1..h_L
+  float* ws = act + size_t(L) * R * W;     // weight chunk
+  float* out8 = ws + Smem<W>::ws_floats;   // head outputs, then their adjoint
+  float* dh = out8 + R * 8;                // [R][W] adjoint of the current layer output
+  __shared__ uint64_t xt[R];
+  __shared__ float cl[R], cp[R];
+  const int p = blockIdx.y;
+  const uint64_t base = uint64_t(blockIdx.x) * R;
+  if (base >= n_x) return;
+  const int nrows = int(n_x - base < uint64_t(R) ? n_x - base : uint64_t(R));
+  if (threadIdx.x < R) {
+    bool ok = threadIdx.x < nrows;
+    xt[threadIdx.x] = ok ? xs[base + threadIdx.x] : 0ull;
+    cl[threadIdx.x] = ok ? cot_la[base + threadIdx.x] : 0.f;
+    cp[threadIdx.x] = ok ? cot_ph[base + threadIdx.x] : 0.f;
+  }
+  __syncthreads();
+  const int last = slot_forward<W>(m, p, xt, nrows, act, L, ws, out8);
+  const MlpPtr P = slot_ptrs(m, p);
+  float* gbase = grad + (P.W1 - m.params);
+  // d out: d l_u = cot_la * 1/2 (delta_uv - p~_u) over allowed u, d phi_u = cot_ph delta_uv
+  if (threadIdx.x < R) {
+    int r = threadIdx.x;
+    float d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (r < nrows) {
+      uint64_t x = xt[r];
+      int a = 0, b = 0;
+      for (int q = 0; q < p; ++q) {
+        int vq = int((x >> (2 * q)) & 3ull);
+        a += vq & 1;
+        b += vq >> 1;
+      }
+      unsigned mk = slot_mask(hv, p, a, b);
+      int v = int((x >> (2 * p)) & 3ull);
+      if ((mk >> v) & 1u) {
+        const float* o8 = out8 + r * 8;
+        float mx = -INFINITY;
+        for (int u = 0; u < 4; ++u)
+          if ((mk >> u) & 1u) mx = fmaxf(mx, o8[u]);
+        float e[4], s = 0.f;
+        for (int u = 0; u < 4; ++u) {
+          e[u] = ((mk >> u) & 1u) ? expf(o8[u] - mx) : 0.f;
+          s += e[u];
+        }
+        for (int u = 0; u < 4; ++u) d[u] = 0.5f * cl[r] * ((u == v ? 1.f : 0.f) - e[u] / s);
+        d[4 + v] = cp[r];
+      }
+    }
+    for (int u = 0; u < 8; ++u) out8[r * 8 + u] = d[u];
+  }
+  __syncthreads();
+  // head: dW_h[o][k] += sum_r d[r][o] h_L[r][k]; db_h[o] += sum_r d[r][o]; dh_L = W_h^T d
+  {
+    const float* hL = act + size_t(last) * R * W;
+    float* gWh = gbase + (P.Wh - P.W1);
+    float* gbh = gbase + (P.bh - P.W1);
+    for (int idx = threadIdx.x; idx < 8 * W; idx += NT) {
+      int o = idx / W, k = idx % W;
+      float s = 0.f;
+      for (int r = 0; r < R; ++r) s = fmaf(out8[r * 8 + o], hL[r * W + k], s);
+      atomicAdd(gWh + idx, s);
+    }
+    if (threadIdx.x < 8) {
+      float s = 0.f;
+      for (int r = 0; r < R; ++r) s += out8[r * 8 + threadIdx.x];
+      atomicAdd(gbh + threadIdx.x, s);
+    }
+    for (int idx = threadIdx.x; idx < R * W; idx += NT) {
+      int r = idx / W, k = idx % W;
+      float s = 0.f;
+      for (int o = 0; o < 8; ++o) s = fmaf(__ldg(P.Wh + o * W + k), out8[r * 8 + o], s);
+      // through tanh: dz = dh (1 - h^2)
+      float hv_ = hL[idx];
+      dh[idx] = s * (1.f - hv_ * hv_);
+    }
+  }
+  __syncthreads();
+  // hidden layers L..2 (dh holds dz_k of layer k)
+  constexpr int RPT = R / 8, CPT = W / 32;
+  const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
+  for (int k = L; k >= 2; --k) {
+    const float* Wk = P.Wk + size_t(k - 2) * (size_t(W) * W + W);
+    float* gW = gbase + (Wk - P.W1);
+    float* gb = gW + size_t(W) * W;
+    const float* hprev = act + size_t(k - 2) * R * W;  // h_{k-1}
+    for (int idx = threadIdx.x; idx < W * W; idx += NT) {
+      int o = idx / W, i = idx % W;
+      float s = 0.f;
+      for (int r = 0; r < R; ++r) s = fmaf(dh[r * W + o], hprev[r * W + i], s);
+      atomicAdd(gW + idx, s);
+    }
+    for (int o = threadIdx.x; o < W; o += NT) {
+      float s = 0.f;
+      for (int r = 0; r < R; ++r) s += dh[r * W + o];
+      atomicAdd(gb + o, s);
+    }
+    float acc[RPT][CPT];
+    tile_gemm<W, true>(dh, Wk, ws, acc);  // dh_{k-1} = W_k^T dz_k
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < RPT; ++i)
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        int r = wg * RPT + i, c = lane + 32 * j;
+        float hv_ = hprev[r * W + c];
+        dh[r * W + c] = acc[i][j] * (1.f - hv_ * hv_);
+      }
+    __syncthreads();
+  }
+  // layer 1: dW_1[o][4q + v_q] += sum_r dz_1[r][o]; db_1 += sum_r dz_1
+  {
+    float* gW1 = gbase;
+    float* gb1 = gbase + size_t(W) * 4 * p;
+    for (int o = threadIdx.x; o < W; o += NT) {
+      float s = 0.f;
+      for (int r = 0; r < nrows; ++r) s += dh[r * W + o];
+      atomicAdd(gb1 + o, s);
+      for (int q = 0; q < p; ++q) {
+        float c4[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int r = 0; r < nrows; ++r) c4[int((xt[r] >> (2 * q)) & 3ull)] += dh[r * W + o];
+        for (int u = 0; u < 4; ++u)
+          if (c4[u] != 0.f) atomicAdd(gW1 + size_t(o) * 4 * p + 4 * q + u, c4[u]);
+      }
+    }
+  }
+}
+
+template <class F>
+int set_smem(F* f, size_t bytes) {
+  ANQS_CUDA(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes)));
+  return ANQS_OK;
+}
+
+unsigned grid_for(uint64_t tiles, unsigned cap) { return unsigned(tiles < cap ? (tiles ? tiles : 1) : cap); }
+
+template <int W>
+int logpsi_w(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la, float* ph,
+             cudaStream_t s) {
+  size_t sm = Smem<W>::bytes(2);
+  ANQS_TRY(set_smem(logpsi_kernel<W>, sm));
+  logpsi_kernel<W><<<grid_for((n_x + R - 1) / R, 152 * 8), NT, sm, s>>>(m, hv, x, n_x, la, ph);
+  ANQS_LAUNCHED("mlp logpsi_kernel");
+  return ANQS_OK;
+}
+
+template <int W>
+int logits_w(const MlpView& m, int p, const uint64_t* pre, const uint64_t* nr, uint64_t max_rows, float* out,
+             cudaStream_t s) {
+  size_t sm = Smem<W>::bytes(2);
+  ANQS_TRY(set_smem(slot_logits_kernel<W>, sm));
+  slot_logits_kernel<W><<<grid_for((max_rows + R - 1) / R, 152 * 8), NT, sm, s>>>(m, p, pre, nr, out);
+  ANQS_LAUNCHED("mlp slot_logits_kernel");
+  return ANQS_OK;
+}
+
+template <int W>
+int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x, const float* cl,
+           const float* cp, float* g, cudaStream_t s) {
+  size_t sm = Smem<W>::bytes(m.n_hidden + 1);
+  if (sm > 227 * 1024)
+    return set_error(ANQS_ERR_UNSUPPORTED, "FP32 MLP adjoint needs %zu bytes of shared memory", sm);
+  ANQS_TRY(set_smem(grad_kernel<W>, sm));
+  dim3 grid(unsigned((n_x + R - 1) / R), unsigned(m.n));
+  grad_kernel<W><<<grid, NT, sm, s>>>(m, hv, x, n_x, cl, cp, g);
+  ANQS_LAUNCHED("mlp grad_kernel");
+  return ANQS_OK;
+}
+
+}  // namespace
+
+int launch_mlp_fp32_logpsi(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la,
+                           float* ph, cudaStream_t s) {
+  switch (m.width) {
+    case 64: return logpsi_w<64>(m, hv, x, n_x, la, ph, s);
+    case 128: return logpsi_w<128>(m, hv, x, n_x, la, ph, s);
+    case 256: return logpsi_w<256>(m, hv, x, n_x, la, ph, s);
+  }
+  return set_error(ANQS_ERR_UNSUPPORTED, "width %d", m.width);
+}
+
+int launch_mlp_fp32_slot_logits(const MlpView& m, int p, const uint64_t* pre, const uint64_t* nr,
+                                uint64_t max_rows, float* out, cudaStream_t s) {
+  switch (m.width) {
+    case 64: return logits_w<64>(m, p, pre, nr, max_rows, out, s);
+    case 128: return logits_w<128>(m, p, pre, nr, max_rows, out, s);
+    case 256: return logits_w<256>(m, p, pre, nr, max_rows, out, s);
+  }
+  return set_error(ANQS_ERR_UNSUPPORTED, "width %d", m.width);
+}
+
+int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x, const float* cl,
+                         const float* cp, float* g, cudaStream_t s) {
+  if ((n_x + R - 1) / R > 0x7fffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "too many rows");
+  switch (m.width) {
+    case 64: return grad_w<64>(m, hv, x, n_x, cl, cp, g, s);
+    case 128: return grad_w<128>(m, hv, x, n_x, cl, cp, g, s);
+    case 256: return grad_w<256>(m, hv, x, n_x, cl, cp, g, s);
+  }
+  return set_error(ANQS_ERR_UNSUPPORTED, "width %d", m.width);
+}
+
+}  // namespace anqs

@@ -1,0 +1,381 @@
+// Masked autoregressive statistics sampling (Sec. II.C; MU, Sec. III.C).
+//
+// Breadth-first over the slot tree.  Level p holds the frontier of prefixes
+// (slots < p) with their sample counts.  Per level:
+//   1. the network's slot-p outputs for every frontier prefix;
+//   2. per node: allowed outcomes from the IsPhys slot mask, the masked
+//      conditional in FP64 and its running sums C_v;
+//   3. the node's n_in uniforms (Philox4x64-10, one block of four per
+//      thread; counter (prefix, i >> 2, p, counter), key (seed, 0)) are
+//      compared with C_v and the outcome counts are aggregated per warp
+//      segment before one atomic per (node, outcome);
+//   4. children with nonzero counts are compacted, in (node, outcome)
+//      order, into the next frontier (the last level writes the output).
+// Grids are sized from host-side bounds on the frontier (the number of
+// physical prefixes of each level, capped by N_s); the actual sizes stay on
+// the device so that the whole sequence can be captured in a CUDA graph.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace anqs {
+
+int logits_dispatch(const anqs_model* M, int p, const uint64_t* pre, const uint64_t* n_dev, uint64_t max_rows,
+                    float* out8, cudaStream_t s);
+
+namespace {
+
+constexpr int SCAN_T = 1024;      // threads per scan CTA
+constexpr int SCAN_ITEMS = 4;     // elements per thread
+constexpr int SCAN_CHUNK = SCAN_T * SCAN_ITEMS;
+
+struct Philox {
+  __device__ static void block(uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3, uint64_t k0, uint64_t k1,
+                               uint64_t out[4]) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+      if (r) {
+        k0 += W0;
+        k1 += W1;
+      }
+      uint64_t hi0 = __umul64hi(M0, c0), lo0 = M0 * c0;
+      uint64_t hi1 = __umul64hi(M1, c2), lo1 = M1 * c2;
+      uint64_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+      c0 = n0;
+      c1 = lo1;
+      c2 = n2;
+      c3 = lo0;
+    }
+    out[0] = c0;
+    out[1] = c1;
+    out[2] = c2;
+    out[3] = c3;
+  }
+};
+
+__global__ void init_kernel(uint64_t* pre, uint64_t* cnt, uint64_t* n_front, uint64_t n_samples) {
+  pre[0] = 0;
+  cnt[0] = n_samples;
+  n_front[0] = 1;
+}
+
+__device__ __forceinline__ int popc_alpha(uint64_t x, int p) {
+  uint64_t m = (p >= 32) ? ~0ull : ((1ull << (2 * p)) - 1ull);
+  return __popcll(x & m & 0x5555555555555555ull);
+}
+__device__ __forceinline__ int popc_beta(uint64_t x, int p) {
+  uint64_t m = (p >= 32) ? ~0ull : ((1ull << (2 * p)) - 1ull);
+  return __popcll(x & m & 0xAAAAAAAAAAAAAAAAull);
+}
+
+// per node: running sums of the masked conditional, draw-block counts
+__global__ void prep_kernel(HamView hv, int p, const uint64_t* __restrict__ pre, const uint64_t* __restrict__ cnt,
+                            const uint64_t* __restrict__ n_front, const float* __restrict__ logits,
+                            double* __restrict__ cdf, uint8_t* __restrict__ allowed, uint64_t* __restrict__ nblk,
+                            uint64_t* __restrict__ child) {
+  const uint64_t nf = *n_front;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < nf; i += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t x = pre[i];
+    unsigned mk = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p));
+    const float* l = logits + i * 8;
+    double m = -INFINITY;
+    for (int v = 0; v < 4; ++v)
+      if ((mk >> v) & 1u) m = fmax(m, double(l[v]));
+    double e[4], s = 0.0;
+    for (int v = 0; v < 4; ++v) {
+      e[v] = ((mk >> v) & 1u) ? exp(double(l[v]) - m) : 0.0;
+      s += e[v];
+    }
+    double run = 0.0;
+    for (int v = 0; v < 4; ++v) {
+      if ((mk >> v) & 1u) run += e[v] / s;
+      cdf[i * 4 + v] = run;
+      child[i * 4 + v] = 0;
+    }
+    allowed[i] = uint8_t(mk);
+    nblk[i] = (cnt[i] + 3) / 4;
+  }
+}
+
+// ---- exclusive scan of uint64 over a device-sized array -------------------
+__device__ __forceinline__ uint64_t warp_incl_scan(uint64_t v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint64_t t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// returns the exclusive prefix of v within the CTA, total in *tot
+__device__ uint64_t block_excl_scan(uint64_t v, uint64_t* sh, uint64_t* tot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t inc = warp_incl_scan(v);
+  __syncthreads();
+  if (lane == 31) sh[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint64_t t = lane < int(blockDim.x >> 5) ? sh[lane] : 0;
+    uint64_t ti = warp_incl_scan(t);
+    sh[lane] = ti - t;
+    if (lane == 31) sh[32] = ti;
+  }
+  __syncthreads();
+  *tot = sh[32];
+  return sh[w] + inc - v;
+}
+
+// in[i] for i < n (n = *n_dev * mult), partial sums per chunk
+__global__ void scan_reduce_kernel(const uint64_t* __restrict__ in, const uint64_t* __restrict__ n_dev,
+                                   uint64_t mult, uint64_t* __restrict__ partial) {
+  __shared__ uint64_t sh[33];
+  const uint64_t n = *n_dev * mult;
+  const uint64_t base = uint64_t(blockIdx.x) * SCAN_CHUNK;
+  uint64_t v = 0;
+  if (base < n)
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+      uint64_t i = base + uint64_t(k) * SCAN_T + threadIdx.x;
+      if (i < n) v += in[i];
+    }
+  uint64_t tot;
+  block_excl_scan(v, sh, &tot);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void scan_partials_kernel(uint64_t* __restrict__ partial, uint64_t n_part) {
+  __shared__ uint64_t sh[33];
+  uint64_t carry = 0;
+  for (uint64_t b = 0; b < n_part; b += SCAN_T) {
+    uint64_t i = b + threadIdx.x;
+    uint64_t v = i < n_part ? partial[i] : 0;
+    uint64_t tot;
+    uint64_t ex = block_excl_scan(v, sh, &tot);
+    if (i < n_part) partial[i] = carry + ex;
+    carry += tot;
+    __syncthreads();
+  }
+}
+
+// out[i] = exclusive prefix; out[n] = total; total also to *total_dev
+__global__ void scan_apply_kernel(const uint64_t* __restrict__ in, const uint64_t* __restrict__ n_dev,
+                                  uint64_t mult, const uint64_t* __restrict__ partial, uint64_t* __restrict__ out,
+                                  uint64_t* __restrict__ total_dev) {
+  __shared__ uint64_t sh[33];
+  const uint64_t n = *n_dev * mult;
+  const uint64_t base = uint64_t(blockIdx.x) * SCAN_CHUNK;
+  if (base > n) return;
+  // each thread owns SCAN_ITEMS consecutive elements
+  uint64_t loc[SCAN_ITEMS], s = 0;
+  const uint64_t first = base + uint64_t(threadIdx.x) * SCAN_ITEMS;
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    uint64_t i = first + k;
+    loc[k] = i < n ? in[i] : 0;
+    s += loc[k];
+  }
+  uint64_t tot;
+  uint64_t ex = block_excl_scan(s, sh, &tot) + partial[blockIdx.x];
+  for (int k = 0; k < SCAN_ITEMS; ++k) {
+    uint64_t i = first + k;
+    if (i < n) out[i] = ex;
+    if (i == n) {
+      out[n] = ex;
+      if (total_dev) *total_dev = ex;
+    }
+    ex += loc[k];
+  }
+}
+
+// ---- draws -----------------------------------------------------------------
+__global__ void draw_kernel(int p, uint64_t seed, uint64_t counter, const uint64_t* __restrict__ pre,
+                            const uint64_t* __restrict__ cnt, const uint64_t* __restrict__ n_front,
+                            const uint64_t* __restrict__ nblk_scan, const double* __restrict__ cdf,
+                            const uint8_t* __restrict__ allowed, uint64_t* __restrict__ child,
+                            uint64_t max_threads) {
+  const uint64_t nf = *n_front;
+  const uint64_t total = nblk_scan[nf];
+  const int lane = threadIdx.x & 31;
+  for (uint64_t t0 = blockIdx.x * uint64_t(blockDim.x); t0 < max_threads; t0 += uint64_t(gridDim.x) * blockDim.x) {
+    if (t0 >= total) break;
+    const uint64_t t = t0 + threadIdx.x;
+    int64_t node = -1;
+    uint32_t packed = 0;
+    if (t < total) {
+      // largest i with nblk_scan[i] <= t
+      uint64_t lo = 0, hi = nf - 1;
+      while (lo < hi) {
+        uint64_t mid = (lo + hi + 1) >> 1;
+        if (nblk_scan[mid] <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      node = int64_t(lo);
+      const uint64_t ib = t - nblk_scan[lo];
+      const uint64_t c = cnt[lo];
+      const uint64_t x = pre[lo];
+      uint64_t w[4];
+      Philox::block(x, ib, uint64_t(p), counter, seed, 0ull, w);
+      const unsigned mk = allowed[lo];
+      const double* C = cdf + lo * 4;
+      int last = 3;
+      while (last > 0 && !((mk >> last) & 1u)) --last;
+      for (int k = 0; k < 4; ++k) {
+        if (ib * 4 + k >= c) break;
+        double u = double(w[k] >> 11) * 0x1.0p-53;
+        int out = last;
+        for (int v = 0; v < 4; ++v)
+          if (((mk >> v) & 1u) && u < C[v]) {
+            out = v;
+            break;
+          }
+        packed += 1u << (8 * out);
+      }
+    }
+    // segmented sum over lanes with the same node (nodes are non-decreasing in t)
+    int64_t prev = __shfl_up_sync(0xffffffffu, node, 1);
+    unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != node);
+    int seg_start = 31 - __clz(heads & ((2u << lane) - 1u));
+    uint32_t v = packed;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t other = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane - o >= seg_start) v += other;
+    }
+    bool tail = (lane == 31) || ((heads >> (lane + 1)) & 1u);
+    if (tail && node >= 0)
+      for (int k = 0; k < 4; ++k) {
+        uint32_t ck = (v >> (8 * k)) & 0xffu;
+        if (ck) atomicAdd(reinterpret_cast<unsigned long long*>(child + node * 4 + k), (unsigned long long)ck);
+      }
+  }
+}
+
+__global__ void flag_kernel(const uint64_t* __restrict__ child, const uint64_t* __restrict__ n_front,
+                            uint64_t* __restrict__ flags) {
+  const uint64_t n4 = *n_front * 4;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n4; i += uint64_t(gridDim.x) * blockDim.x)
+    flags[i] = child[i] ? 1ull : 0ull;
+}
+
+__global__ void scatter_kernel(int p, const uint64_t* __restrict__ pre, const uint64_t* __restrict__ child,
+                               const uint64_t* __restrict__ n_front, const uint64_t* __restrict__ pos,
+                               uint64_t* __restrict__ pre_out, uint64_t* __restrict__ cnt_out) {
+  const uint64_t n4 = *n_front * 4;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n4; i += uint64_t(gridDim.x) * blockDim.x) {
+    uint64_t c = child[i];
+    if (c) {
+      uint64_t j = pos[i];
+      pre_out[j] = pre[i >> 2] | (uint64_t(i & 3) << (2 * p));
+      cnt_out[j] = c;
+    }
+  }
+}
+
+struct Plan {
+  uint64_t F;  // max frontier
+  uint64_t *pre[2], *cnt[2], *nblk, *nblk_scan, *child, *flags, *pos, *partial, *n_front;
+  float* logits;
+  double* cdf;
+  uint8_t* allowed;
+};
+
+uint64_t level_cap(const anqs_ham* H, uint64_t n_samples, int p) {
+  uint64_t c = H->phys_prefix[p];
+  return c < n_samples ? c : n_samples;
+}
+
+void plan_ws(const anqs_ham* H, uint64_t n_samples, Arena& A, Plan& P) {
+  uint64_t F = 1;
+  for (int p = 0; p <= H->v.n; ++p) F = std::max(F, level_cap(H, n_samples, p));
+  P.F = F;
+  for (int b = 0; b < 2; ++b) {
+    P.pre[b] = A.take<uint64_t>(F);
+    P.cnt[b] = A.take<uint64_t>(F);
+  }
+  P.logits = A.take<float>(F * 8);
+  P.cdf = A.take<double>(F * 4);
+  P.allowed = A.take<uint8_t>(F);
+  P.nblk = A.take<uint64_t>(F);
+  P.nblk_scan = A.take<uint64_t>(F + 1);
+  P.child = A.take<uint64_t>(F * 4);
+  P.flags = A.take<uint64_t>(F * 4);
+  P.pos = A.take<uint64_t>(F * 4 + 1);
+  P.partial = A.take<uint64_t>((F * 4 + 1) / SCAN_CHUNK + 2);
+  P.n_front = A.take<uint64_t>(2);
+}
+
+int scan(const uint64_t* in, const uint64_t* n_dev, uint64_t mult, uint64_t max_n, uint64_t* partial,
+         uint64_t* out, uint64_t* total_dev, cudaStream_t s) {
+  uint64_t chunks = max_n / SCAN_CHUNK + 1;  // covers index max_n (the total)
+  scan_reduce_kernel<<<unsigned(chunks), SCAN_T, 0, s>>>(in, n_dev, mult, partial);
+  ANQS_LAUNCHED("scan_reduce_kernel");
+  scan_partials_kernel<<<1, SCAN_T, 0, s>>>(partial, chunks);
+  ANQS_LAUNCHED("scan_partials_kernel");
+  scan_apply_kernel<<<unsigned(chunks), SCAN_T, 0, s>>>(in, n_dev, mult, partial, out, total_dev);
+  ANQS_LAUNCHED("scan_apply_kernel");
+  return ANQS_OK;
+}
+
+unsigned blocks_for(uint64_t n, int threads, uint64_t cap) {
+  uint64_t b = (n + threads - 1) / threads;
+  if (b > cap) b = cap;
+  return unsigned(b ? b : 1);
+}
+
+}  // namespace
+
+size_t sampler_workspace(const anqs_ham* H, uint64_t n_samples) {
+  Arena A(nullptr, 0);
+  Plan P;
+  plan_ws(H, n_samples, A, P);
+  return A.off;
+}
+
+int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint64_t seed, uint64_t counter,
+                uint64_t* x_out, uint64_t* n_out, uint64_t* n_unique, void* ws, size_t ws_bytes, cudaStream_t s) {
+  Arena A(ws, ws_bytes);
+  Plan P;
+  plan_ws(H, n_samples, A, P);
+  if (!A.fits()) return set_error(ANQS_ERR_CAPACITY, "sampler workspace needs %zu bytes", A.off);
+  const int n = H->v.n;
+  init_kernel<<<1, 1, 0, s>>>(P.pre[0], P.cnt[0], P.n_front, n_samples);
+  ANQS_LAUNCHED("sampler init_kernel");
+  for (int p = 0; p < n; ++p) {
+    const int cur = p & 1, nxt = cur ^ 1;
+    const uint64_t Fp = level_cap(H, n_samples, p);
+    uint64_t* nf = P.n_front + cur;
+    ANQS_TRY(logits_dispatch(M, p, P.pre[cur], nf, Fp, P.logits, s));
+    prep_kernel<<<blocks_for(Fp, 256, 152 * 8), 256, 0, s>>>(H->v, p, P.pre[cur], P.cnt[cur], nf, P.logits, P.cdf,
+                                                              P.allowed, P.nblk, P.child);
+    ANQS_LAUNCHED("sampler prep_kernel");
+    ANQS_TRY(scan(P.nblk, nf, 1, Fp, P.partial, P.nblk_scan, nullptr, s));
+    const uint64_t max_draw_threads = (n_samples + 3) / 4 + Fp;
+    draw_kernel<<<blocks_for(max_draw_threads, 256, 152 * 16), 256, 0, s>>>(
+        p, seed, counter, P.pre[cur], P.cnt[cur], nf, P.nblk_scan, P.cdf, P.allowed, P.child, max_draw_threads);
+    ANQS_LAUNCHED("sampler draw_kernel");
+    flag_kernel<<<blocks_for(Fp * 4, 256, 152 * 8), 256, 0, s>>>(P.child, nf, P.flags);
+    ANQS_LAUNCHED("sampler flag_kernel");
+    const bool last = (p == n - 1);
+    uint64_t* nf_next = last ? n_unique : P.n_front + nxt;
+    ANQS_TRY(scan(P.flags, nf, 4, Fp * 4, P.partial, P.pos, nf_next, s));
+    scatter_kernel<<<blocks_for(Fp * 4, 256, 152 * 8), 256, 0, s>>>(
+        p, P.pre[cur], P.child, nf, P.pos, last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt]);
+    ANQS_LAUNCHED("sampler scatter_kernel");
+  }
+  return ANQS_OK;
+}
+
+int logits_dispatch(const anqs_model* M, int p, const uint64_t* pre, const uint64_t* n_dev, uint64_t max_rows,
+                    float* out8, cudaStream_t s) {
+  switch (M->d.kind) {
+    case ANQS_MODEL_MLP:
+      return launch_mlp_fp32_slot_logits(M->mlp, p, pre, n_dev, max_rows, out8, s);
+    case ANQS_MODEL_TABLE:
+      return launch_table_slot_logits(M, p, pre, n_dev, max_rows, out8, s);
+    default:
+      return set_error(ANQS_ERR_UNSUPPORTED, "sampling for model kind %d not available in this build", M->d.kind);
+  }
+}
+
+}  // namespace anqs
