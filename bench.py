@@ -1,0 +1,373 @@
+"""Benchmark: local energies per second of the symmetry-masked autoregressive
+VMC hot path on one GB300 (or N independent replicas under torchrun).
+
+One step = one pass of the whole hot path over one batch of synthetic
+input: masked statistics sampling of N_s samples, the connected set and
+amplitudes of every unique sample, E_loc with the count-weighted energy
+statistics, and the VMC gradient.  Default workload: 7 spatial orbitals,
+N_a = N_b = 5 (14 qubits, 441 determinants: the H2O shape of the paper's
+Table I), synthetic integrals with 14 Cholesky vectors (seed 1), per-slot
+MLP with 3 hidden layers of width 128, N_s = 1e5.
+
+Prints one JSON line.  `value` = unique samples whose local energy was
+completed, per second of device time (max over ranks), inputs resident in
+HBM, L2 flushed between timed steps.  `e2e` = the same through the public
+API with host buffers: parameters copied host->device and energy statistics
+plus gradient copied back every step.  `--impl reference` times the FP64 CPU
+oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+METRIC = "local energies/sec at 1 GB300 (BF16 vs FP32 form), |dE| vs FP64 oracle (Ha)"
+UNIT = "local energies/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [t.strip() for t in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        return ws, rank, local, dist
+    return 1, 0, 0, None
+
+
+def _cpu_baseline(w, seconds=10.0, n_max=400):
+    """Time the FP64 oracle's local energy on a bounded prefix of the unique
+    samples of one oracle sampling pass (its own conditionals, same seed)."""
+    from oracle.anqs import MLPAnsatz, TFAnsatz
+    from oracle.hamiltonian import Hamiltonian as OHam
+    from oracle.sampler import sample as osample
+    from oracle.sector import molecular_isphys
+    from oracle.vmc import local_energy
+
+    oham = OHam(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    ip = molecular_isphys(w["n"], w["n_alpha"], w["n_beta"])
+    om = MLPAnsatz(w["params_struct"], w["n"]) if w["kind"] == "mlp" else \
+        TFAnsatz(w["params_struct"], w["n"], w["n_heads"])
+    xs, _, _ = osample(om, ip, w["n"], w["n_samples"], seed=12345)
+    done, t0 = 0, time.perf_counter()
+    k = 8
+    while done < min(n_max, len(xs)) and time.perf_counter() - t0 < seconds:
+        chunk = xs[done:done + k]
+        local_energy(om, ip, oham, chunk)
+        done += len(chunk)
+    dt = time.perf_counter() - t0
+    return {"value": done / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle local energy (connected set + log psi + sum) of the first {done} unique "
+                      f"samples of one N_s={w['n_samples']} sampling pass, {dt:.1f} s"}
+
+
+def _reference_arm(args, w, ws, rank):
+    if rank != 0:
+        return
+    steps = []
+    for _ in range(args.warmup):
+        _cpu_baseline(w, seconds=2.0, n_max=16)
+    for _ in range(args.steps):
+        steps.append(_cpu_baseline(w, seconds=8.0, n_max=200))
+    val = statistics.mean(s["value"] for s in steps)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 / val,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(w, args),
+            "cpu_baseline": {"kind": "oracle", "cores": steps[0]["cores"], "sample": steps[0]["sample"],
+                             "value": val, "unit": UNIT},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config(w, args):
+    net = (f"per-slot MLP {w['n_hidden']}x{w['width']}" if w["kind"] == "mlp"
+           else f"transformer d{w['d_model']} h{w['n_heads']} L{w['n_layers']}")
+    return {"workload": f"{args.workload}: n_orb={w['n']} N_a={w['n_alpha']} N_b={w['n_beta']} "
+                        f"({2 * w['n']} qubits), {w['n_chol']} Cholesky vectors seed {w['seed']}, {net}, "
+                        f"N_s={w['n_samples']}",
+            "form": args.form, "n_samples": w["n_samples"], "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single GPU"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default=os.environ.get("ANQS_BENCH_FORM", "bf16"), choices=["fp32", "bf16"])
+    ap.add_argument("--workload", default="h2o")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    from synthetic import workload
+    w = workload(args.workload)
+    ws, rank, local, dist = _dist()
+    if args.impl == "reference":
+        _reference_arm(args, w, ws, rank)
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import paper_2310_04166_gb300 as A
+    from paper_2310_04166_gb300 import _lib
+    lib = _lib.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    form = args.form
+    ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    params = torch.tensor(w["params"], device=dev)
+    try:
+        model = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form=form)
+    except A.AnqsError as e:
+        if form == "bf16" and "UNSUPPORTED" in str(e):
+            form = "fp32"
+            args.form = "fp32 (bf16 form unavailable in this build)"
+            model = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form="fp32")
+        else:
+            raise
+    Ns = w["n_samples"]
+    cap = min(Ns, ham.sector_dim)
+    x = torch.empty(cap, dtype=torch.int64, device=dev)
+    cnt = torch.empty(cap, dtype=torch.int64, device=dev)
+    nu = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws_s = A._ws(A.sample_workspace_bytes(model, ham, Ns), dev)
+    ws_e = A._ws(A.local_energy_workspace_bytes(model, ham, cap), dev)
+    ere = torch.empty(cap, dtype=torch.float64, device=dev)
+    eim = torch.empty_like(ere)
+    stats = torch.empty(4, dtype=torch.float64, device=dev)
+    g = torch.empty(model.n_params, dtype=torch.float32, device=dev)
+    import ctypes as C
+    gws_b = C.c_size_t()
+    _lib.check(lib.anqs_grad_workspace_size(model._m, ham.handle, cap, C.byref(gws_b)))
+    ws_g = A._ws(gws_b.value, dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    seed = 1234 + 7919 * rank
+
+    # N_unq varies per step and is only known on the device: one host read per
+    # step (outside the events) sizes the energy and gradient calls.
+    def run_step(counter, timed_events=None):
+        A.sample_into(model, ham, Ns, seed, counter, x, cnt, nu, ws_s)
+        k = int(nu.item())
+        if timed_events:
+            timed_events[1].record(stream)
+            timed_events[2].record(stream)
+        _lib.check(lib.anqs_local_energy(model._m, ham.handle, x.data_ptr(), cnt.data_ptr(), k, ere.data_ptr(),
+                                         eim.data_ptr(), stats.data_ptr(), ws_e.data_ptr(), ws_e.numel(),
+                                         stream.cuda_stream))
+        _lib.check(lib.anqs_grad(model._m, ham.handle, x.data_ptr(), cnt.data_ptr(), k, ere.data_ptr(),
+                                 eim.data_ptr(), stats.data_ptr(), g.data_ptr(), ws_g.data_ptr(), ws_g.numel(),
+                                 stream.cuda_stream))
+        return k
+
+    for i in range(args.warmup):
+        run_step(i)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    lib.anqs_profile_enable(1)
+    l0 = C.c_uint64()
+    lib.anqs_launch_count(C.byref(l0))
+    times, uniq = [], []
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e3 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            k = run_step(1000 + i, (e0, e1, e2))
+            e3.record(stream)
+            torch.cuda.synchronize()
+            # device time of the step: sampling (e0..e1) plus energy and
+            # gradient (e2..e3); the host read of N_unq between them is excluded
+            times.append(e0.elapsed_time(e1) + e2.elapsed_time(e3))
+            uniq.append(k)
+    l1 = C.c_uint64()
+    lib.anqs_launch_count(C.byref(l1))
+    prof = {}
+    for pid in range(64):
+        nm, n_l, ms = C.c_char_p(), C.c_uint64(), C.c_double()
+        if lib.anqs_profile_read(pid, C.byref(nm), C.byref(n_l), C.byref(ms)) != 0:
+            break
+        if n_l.value:
+            prof[nm.value.decode()] = (n_l.value, ms.value)
+    lib.anqs_profile_enable(0)
+
+    total_ms = sum(times)
+    total_u = sum(uniq)
+    t = torch.tensor([total_ms, float(total_u)], dtype=torch.float64, device=dev)
+    if dist:
+        tm = t.clone()
+        dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
+        dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
+        total_ms, total_u = float(tm[0]), float(t[1])
+    value = total_u / (total_ms / 1e3)
+
+    # end to end through the public API: host params in, host stats + gradient out
+    h_params = torch.tensor(w["params"]).pin_memory()
+    h_stats = torch.empty(4, dtype=torch.float64).pin_memory()
+    h_grad = torch.empty(model.n_params, dtype=torch.float32).pin_memory()
+    e2e_ms, e2e_u = 0.0, 0
+    for i in range(max(3, args.steps // 2)):
+        flush.fill_(i & 0xFF)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        params.copy_(h_params, non_blocking=True)
+        if form == "bf16":
+            model.sync()
+        xx, nn = A.sample(model, ham, Ns, seed, 5000 + i)
+        er, ei, st = A.local_energy(model, ham, xx, nn, workspace=ws_e)
+        gg = A.grad(model, ham, xx, nn, er, ei, st, workspace=ws_g)
+        h_stats.copy_(st, non_blocking=True)
+        h_grad.copy_(gg, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+        e2e_u += xx.numel()
+    e2e_val = e2e_u / (e2e_ms / 1e3)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel family
+    peaks, src = _peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (0, 0.0))
+    dname, (dl, dms) = dom
+    avg_ms = dms / max(dl, 1)
+    n_unq = total_u / args.steps
+    K = ham.n_connected
+    roof = _roofline(dname, dl, avg_ms, w, K, n_unq, args.steps, peaks, src)
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = _cpu_baseline(w)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16 GEMM / f32 heads / f64 E_loc" if form == "bf16" else "f32 network / f64 E_loc",
+            "data": "synthetic", "config": _config(w, args), "n_unique_per_step": n_unq,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(params.numel() * 4),
+                    "d2h_bytes_per_step": int(4 * 8 + model.n_params * 4 + 8)},
+            "gpu_launches": int(l1.value - l0.value),
+            "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in prof.items()},
+            "roofline": roof, "clocks": clk.summary()}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _roofline(name, launches, avg_ms, w, K, n_unq, steps, peaks, src):
+    """Algorithmic work per launch of the dominant kernel family over its
+    measured average duration.  FP32 SIMT network: FLOP of the network on
+    every configuration it evaluates (bound: FP32 ALU, peak = 152 SMs x 128
+    FMA/clk x 2 x max SM clock).  Otherwise bytes (HBM)."""
+    if avg_ms <= 0:
+        return None
+    n, W, L = w["n"], w.get("width", 0), w.get("n_hidden", 0)
+    flop_full = sum(2 * (4 * p * W + (L - 1) * W * W + 8 * W) for p in range(n))  # one configuration, all slots
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    if name == "mlp_fp32_logpsi_kernel":
+        # per step: unique samples and all their connected configurations, all slots
+        flops = flop_full * n_unq * (K + 1)
+        launches_per_step = launches / steps
+        ach = flops / launches_per_step / (avg_ms * 1e-3) / 1e12
+        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "note": f"FP32 FMA peak derived from 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz"}
+    return {"kernel": name, "bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None,
+            "traffic": None}
+
+
+if __name__ == "__main__":
+    main()

@@ -254,6 +254,21 @@ ANQS_API int anqs_grad(const anqs_model* model, const anqs_ham* ham, const uint6
 ANQS_API int anqs_logpsi_vjp(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev, uint64_t n_x,
                     const float* cot_abs_dev, const float* cot_phase_dev, float* grad_dev, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Instrumentation (no counterpart in the paper: measurement support)
+ *
+ * anqs_launch_count: number of CUDA kernels the library has launched in this
+ * process.  anqs_profile_enable(on): clears the totals and switches CUDA-event
+ * timing of the library's kernel families on or off (off by default; events
+ * are recorded on the launching stream; do not enable while capturing a
+ * graph).  anqs_profile_read(id, ...): waits for the recorded events and
+ * returns the family's name (static storage), launch count and summed
+ * device time in milliseconds; ids run from 0 until it returns ANQS_ERR_ARG.
+ * ------------------------------------------------------------------------- */
+ANQS_API int anqs_launch_count(uint64_t* n);
+ANQS_API int anqs_profile_enable(int on);
+ANQS_API int anqs_profile_read(int id, const char** name, uint64_t* launches, double* total_ms);
+
 #ifdef __cplusplus
 }
 #endif

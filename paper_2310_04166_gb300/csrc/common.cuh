@@ -15,6 +15,38 @@ namespace anqs {
 
 int set_error(int code, const char* fmt, ...);
 int cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void note_launch();
+
+// Kernel families timed by the optional event profiler (anqs_profile_*).
+enum ProfId {
+  PROF_CONNECT = 0,
+  PROF_DIAGONAL,
+  PROF_MLP_FP32_LOGPSI,
+  PROF_MLP_FP32_SLOT,
+  PROF_MLP_FP32_GRAD,
+  PROF_TABLE,
+  PROF_ELOC_SUM,
+  PROF_STATS,
+  PROF_COTANGENT,
+  PROF_SAMPLER,
+  PROF_TC_PARENT,
+  PROF_TC_SUFFIX,
+  PROF_TC_SORT,
+  PROF_TC_ELOC,
+  PROF_TC_SLOT,
+  PROF_TF,
+  PROF_COUNT
+};
+
+// Records a pair of CUDA events around the launches in its scope when the
+// profiler is on (no-op otherwise).
+struct ProfScope {
+  ProfScope(int id, cudaStream_t s);
+  ~ProfScope();
+  int id;
+  cudaStream_t stream;
+  cudaEvent_t start;
+};
 
 }  // namespace anqs
 
@@ -26,6 +58,7 @@ int cuda_error(cudaError_t e, const char* what, const char* file, int line);
 
 #define ANQS_LAUNCHED(what)                                              \
   do {                                                                   \
+    anqs::note_launch();                                                 \
     cudaError_t e_ = cudaGetLastError();                                 \
     if (e_ != cudaSuccess) return anqs::cuda_error(e_, what, __FILE__, __LINE__); \
   } while (0)

@@ -198,12 +198,14 @@ int launch_connected(const HamView& hv, const uint64_t* x, uint64_t n_x, uint64_
   if (total) {
     uint64_t blocks = (total + threads - 1) / threads;
     if (blocks > 152ull * 64) blocks = 152ull * 64;
+    ProfScope ps(PROF_CONNECT, s);
     connected_kernel<<<unsigned(blocks), threads, 0, s>>>(hv, x, n_x, xp, hval, first_slot);
     ANQS_LAUNCHED("connected_kernel");
   }
   if (hdiag) {
     uint64_t blocks = (n_x + threads - 1) / threads;
     if (blocks > 152ull * 16) blocks = 152ull * 16;
+    ProfScope ps(PROF_DIAGONAL, s);
     diagonal_kernel<<<unsigned(blocks), threads, 0, s>>>(hv, x, n_x, hdiag);
     ANQS_LAUNCHED("diagonal_kernel");
   }

@@ -108,6 +108,7 @@ int launch_eloc_sum(const HamView& hv, uint64_t n_x, const double* hval, const d
                     cudaStream_t s) {
   uint64_t blocks = (n_x + 7) / 8;  // 8 warps per CTA
   if (blocks > 152 * 16) blocks = 152 * 16;
+  ProfScope ps(PROF_ELOC_SUM, s);
   eloc_sum_kernel<<<unsigned(blocks), 256, 0, s>>>(hv.K, n_x, hval, hdiag, la_x, ph_x, la_p, ph_p, ere, eim);
   ANQS_LAUNCHED("eloc_sum_kernel");
   return ANQS_OK;
@@ -115,6 +116,7 @@ int launch_eloc_sum(const HamView& hv, uint64_t n_x, const double* hval, const d
 
 int launch_stats(const double* ere, const double* eim, const uint64_t* counts, uint64_t n_x, double* stats,
                  cudaStream_t s) {
+  ProfScope ps(PROF_STATS, s);
   stats_kernel<<<1, 1024, 0, s>>>(ere, eim, counts, n_x, stats);
   ANQS_LAUNCHED("stats_kernel");
   return ANQS_OK;
@@ -124,6 +126,7 @@ int launch_grad_cotangents(const double* ere, const double* eim, const uint64_t*
                            uint64_t n_x, float* cl, float* cp, cudaStream_t s) {
   uint64_t blocks = (n_x + 255) / 256;
   if (blocks > 152 * 8) blocks = 152 * 8;
+  ProfScope ps(PROF_COTANGENT, s);
   cotangent_kernel<<<unsigned(blocks), 256, 0, s>>>(ere, eim, counts, stats, n_x, cl, cp);
   ANQS_LAUNCHED("cotangent_kernel");
   return ANQS_OK;

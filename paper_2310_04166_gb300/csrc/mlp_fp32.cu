@@ -376,6 +376,7 @@ int logpsi_w(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_
              cudaStream_t s) {
   size_t sm = Smem<W>::bytes(2);
   ANQS_TRY(set_smem(logpsi_kernel<W>, sm));
+  ProfScope ps(PROF_MLP_FP32_LOGPSI, s);
   logpsi_kernel<W><<<grid_for((n_x + R - 1) / R, 152 * 8), NT, sm, s>>>(m, hv, x, n_x, la, ph);
   ANQS_LAUNCHED("mlp logpsi_kernel");
   return ANQS_OK;
@@ -386,6 +387,7 @@ int logits_w(const MlpView& m, int p, const uint64_t* pre, const uint64_t* nr, u
              cudaStream_t s) {
   size_t sm = Smem<W>::bytes(2);
   ANQS_TRY(set_smem(slot_logits_kernel<W>, sm));
+  ProfScope ps(PROF_MLP_FP32_SLOT, s);
   slot_logits_kernel<W><<<grid_for((max_rows + R - 1) / R, 152 * 8), NT, sm, s>>>(m, p, pre, nr, out);
   ANQS_LAUNCHED("mlp slot_logits_kernel");
   return ANQS_OK;
@@ -399,6 +401,7 @@ int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x,
     return set_error(ANQS_ERR_UNSUPPORTED, "FP32 MLP adjoint needs %zu bytes of shared memory", sm);
   ANQS_TRY(set_smem(grad_kernel<W>, sm));
   dim3 grid(unsigned((n_x + R - 1) / R), unsigned(m.n));
+  ProfScope ps(PROF_MLP_FP32_GRAD, s);
   grad_kernel<W><<<grid, NT, sm, s>>>(m, hv, x, n_x, cl, cp, g);
   ANQS_LAUNCHED("mlp grad_kernel");
   return ANQS_OK;

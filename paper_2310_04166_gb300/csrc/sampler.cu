@@ -339,13 +339,17 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
   plan_ws(H, n_samples, A, P);
   if (!A.fits()) return set_error(ANQS_ERR_CAPACITY, "sampler workspace needs %zu bytes", A.off);
   const int n = H->v.n;
-  init_kernel<<<1, 1, 0, s>>>(P.pre[0], P.cnt[0], P.n_front, n_samples);
-  ANQS_LAUNCHED("sampler init_kernel");
+  {
+    ProfScope ps(PROF_SAMPLER, s);
+    init_kernel<<<1, 1, 0, s>>>(P.pre[0], P.cnt[0], P.n_front, n_samples);
+    ANQS_LAUNCHED("sampler init_kernel");
+  }
   for (int p = 0; p < n; ++p) {
     const int cur = p & 1, nxt = cur ^ 1;
     const uint64_t Fp = level_cap(H, n_samples, p);
     uint64_t* nf = P.n_front + cur;
     ANQS_TRY(logits_dispatch(M, p, P.pre[cur], nf, Fp, P.logits, s));
+    ProfScope ps(PROF_SAMPLER, s);
     prep_kernel<<<blocks_for(Fp, 256, 152 * 8), 256, 0, s>>>(H->v, p, P.pre[cur], P.cnt[cur], nf, P.logits, P.cdf,
                                                               P.allowed, P.nblk, P.child);
     ANQS_LAUNCHED("sampler prep_kernel");

@@ -60,6 +60,7 @@ int launch_table_logpsi(const anqs_model* md, const HamView& hv, const uint64_t*
                         float* ph, cudaStream_t s) {
   uint64_t blocks = (n_x + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
+  ProfScope ps(PROF_TABLE, s);
   table_logpsi_kernel<<<unsigned(blocks), 256, 0, s>>>(md->params, md->d.n_orb, hv, x, n_x, la, ph);
   ANQS_LAUNCHED("table_logpsi_kernel");
   return ANQS_OK;
@@ -69,6 +70,7 @@ int launch_table_slot_logits(const anqs_model* md, int p, const uint64_t* pre, c
                              uint64_t max_rows, float* out, cudaStream_t s) {
   uint64_t blocks = (max_rows * 8 + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
+  ProfScope ps(PROF_TABLE, s);
   table_logits_kernel<<<unsigned(blocks ? blocks : 1), 256, 0, s>>>(md->params, p, pre, nr, out);
   ANQS_LAUNCHED("table_logits_kernel");
   return ANQS_OK;

@@ -106,7 +106,7 @@ def test_connected_bit_exact(name, n_check):
 
 def test_connected_out_of_sector_and_empty():
     w, ham, oham, ip = _problem("small")
-    xs = np.array([0b1111, 0b00001111 | (1 << 8)], dtype=np.uint64)  # wrong counts / bits beyond 2n
+    xs = np.array([0b0111, 0b00001111 | (1 << 8)], dtype=np.uint64)  # wrong counts / bits beyond 2n
     xp, hv, js, hd = A.connected(ham, _dev(xs))
     assert torch.isnan(hv).all() and (js == 255).all() and torch.isnan(hd).all()
     e = A.connected(ham, torch.zeros(0, dtype=torch.int64, device="cuda"))
@@ -270,7 +270,8 @@ def test_autograd_function_uses_library_adjoint():
     for t in ps:
         t.requires_grad_(True)
     ra, rp = log_psi(om, ip, st)
-    gs = torch.autograd.grad(ra.sum() + 0.5 * rp.sum(), ps)
-    ref = np.concatenate([t.reshape(-1).numpy() for t in gs])
+    gs = torch.autograd.grad(ra.sum() + 0.5 * rp.sum(), ps, allow_unused=True)
+    ref = np.concatenate([(g if g is not None else torch.zeros_like(t)).reshape(-1).numpy()
+                          for g, t in zip(gs, ps)])
     got = params.grad.cpu().numpy()
     assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
