@@ -255,6 +255,30 @@ ANQS_API int anqs_logpsi_vjp(const anqs_model* model, const anqs_ham* ham, const
                     const float* cot_abs_dev, const float* cot_phase_dev, float* grad_dev, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Local energy without caller workspace (the paper has no counterpart: this
+ * is an interface for callers that cannot allocate device memory)
+ *
+ * Same computation and outputs as anqs_local_energy for FP32-form MLP and
+ * table models, but the scratch memory lives in a fixed 16 MiB array inside
+ * the library (one per GPU that loads it, kept until the process exits)
+ * instead of a caller-provided workspace, and nothing is allocated.  Meant
+ * for callers that cannot hand out device memory at run time, e.g. plug-ins
+ * whose host application owns all device allocations, or loops that must not
+ * call cudaMalloc after start-up.
+ * - Needs n_x * n_connected * 24 + n_x * 16 bytes (plus alignment) to fit in
+ *   16 MiB; larger requests fail with ANQS_ERR_CAPACITY before any work is
+ *   queued.  Other forms and kinds: ANQS_ERR_UNSUPPORTED.
+ * - The first call on a device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ * - All calls on a device share the array: calls that may run concurrently
+ *   on the GPU race and must be ordered by the caller.  Every scratch
+ *   element is written before it is read, so no clearing is needed.
+ * ------------------------------------------------------------------------- */
+ANQS_API int anqs_local_energy_static(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev,
+                                      const uint64_t* counts_dev, uint64_t n_x, double* eloc_re_dev,
+                                      double* eloc_im_dev, double* stats_dev, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Instrumentation (no counterpart in the paper: measurement support)
  *
  * anqs_launch_count: number of CUDA kernels the library has launched in this

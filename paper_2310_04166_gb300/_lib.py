@@ -50,6 +50,7 @@ SIGNATURES = {
     "anqs_local_energy": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "anqs_grad_workspace_size": (C.c_int, [_VP, _VP, _U64, C.POINTER(_SZ)]),
     "anqs_grad": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "anqs_local_energy_static": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
     "anqs_launch_count": (C.c_int, [C.POINTER(_U64)]),
     "anqs_profile_enable": (C.c_int, [C.c_int]),
     "anqs_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_char_p), C.POINTER(_U64), C.POINTER(C.c_double)]),
