@@ -114,7 +114,7 @@ def _dist():
     return 1, 0, 0, None
 
 
-def _cpu_baseline(w, seconds=10.0, n_max=400):
+def _cpu_baseline(w, seconds=10.0, n_max=100000):
     """Time the FP64 oracle's local energy on a bounded prefix of the unique
     samples of one oracle sampling pass (its own conditionals, same seed)."""
     from oracle.anqs import MLPAnsatz, TFAnsatz
@@ -130,14 +130,15 @@ def _cpu_baseline(w, seconds=10.0, n_max=400):
     xs, _, _ = osample(om, ip, w["n"], w["n_samples"], seed=12345)
     done, t0 = 0, time.perf_counter()
     k = 8
-    while done < min(n_max, len(xs)) and time.perf_counter() - t0 < seconds:
-        chunk = xs[done:done + k]
+    while done < n_max and time.perf_counter() - t0 < seconds:
+        start = done % len(xs)
+        chunk = xs[start:start + k]
         local_energy(om, ip, oham, chunk)
         done += len(chunk)
     dt = time.perf_counter() - t0
     return {"value": done / dt, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle local energy (connected set + log psi + sum) of the first {done} unique "
-                      f"samples of one N_s={w['n_samples']} sampling pass, {dt:.1f} s"}
+            "sample": f"FP64 oracle local energy (connected set + log psi + sum) of {done} unique samples "
+                      f"(cycling over the {len(xs)} of one N_s={w['n_samples']} sampling pass), {dt:.1f} s"}
 
 
 def _reference_arm(args, w, ws, rank):
@@ -324,7 +325,8 @@ def main():
     avg_ms = dms / max(dl, 1)
     n_unq = total_u / args.steps
     K = ham.n_connected
-    roof = _roofline(dname, dl, avg_ms, w, K, n_unq, args.steps, peaks, src)
+    work = _tc_work(A, ham, model, w, x[:uniq[-1]]) if form == "bf16" else None
+    roof = _roofline(dname, dl, avg_ms, w, K, n_unq, args.steps, peaks, src, work)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -346,7 +348,27 @@ def main():
         dist.destroy_process_group()
 
 
-def _roofline(name, launches, avg_ms, w, K, n_unq, steps, peaks, src):
+def _tc_work(A, ham, model, w, x):
+    """Algorithmic FLOP per step of the BF16 kernel families for the sample set
+    x: suffix = sum over connected x' of the slots p > j(x'); parent = every
+    slot of every sample; slot (sampler) = every slot of every distinct prefix
+    of the leaves (the frontier of each level)."""
+    n, W, L = w["n"], w["width"], w["n_hidden"]
+    f = np.array([2 * (4 * p * W + (L - 1) * W * W + 8 * W) for p in range(n)], dtype=np.float64)
+    cf = np.concatenate([[0.0], np.cumsum(f)])  # cf[p] = sum_{q<p} f[q]
+    xp, hv, js, hd = A.connected(ham, x)
+    j = js.reshape(-1).cpu().numpy().astype(np.int64)
+    suffix = float((cf[n] - cf[j + 1]).sum())
+    parent = float(len(x) * cf[n])
+    xs = x.cpu().numpy().astype(np.uint64)
+    slot = 0.0
+    for p in range(n):
+        pre = np.unique(xs & np.uint64((1 << (2 * p)) - 1)) if p else np.zeros(1, np.uint64)
+        slot += len(pre) * f[p]
+    return {"mlp_tc_suffix_kernel": suffix, "mlp_tc_parent_kernel": parent, "mlp_tc_slot_kernel": slot}
+
+
+def _roofline(name, launches, avg_ms, w, K, n_unq, steps, peaks, src, work=None):
     """Algorithmic work per launch of the dominant kernel family over its
     measured average duration.  FP32 SIMT network: FLOP of the network on
     every configuration it evaluates (bound: FP32 ALU, peak = 152 SMs x 128
@@ -356,6 +378,14 @@ def _roofline(name, launches, avg_ms, w, K, n_unq, steps, peaks, src):
     n, W, L = w["n"], w.get("width", 0), w.get("n_hidden", 0)
     flop_full = sum(2 * (4 * p * W + (L - 1) * W * W + 8 * W) for p in range(n))  # one configuration, all slots
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    if name in ("mlp_tc_suffix_kernel", "mlp_tc_parent_kernel", "mlp_tc_slot_kernel") and work is not None:
+        flops = work[name] * steps
+        ach = flops / launches / (avg_ms * 1e-3) / 1e12
+        peak = peaks["bf16_tflops"]
+        return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "note": f"algorithmic FLOP with prefix reuse (bf16 GEMMs + f32 head, layer 1 as one-hot GEMM of "
+                        f"width 4p) / CUDA-event time; peak = {src} dense bf16 burst"}
     if name == "mlp_fp32_logpsi_kernel":
         # per step: unique samples and all their connected configurations, all slots
         flops = flop_full * n_unq * (K + 1)

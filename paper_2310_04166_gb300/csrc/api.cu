@@ -90,6 +90,7 @@ int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, u
                     float* ph, cudaStream_t s) {
   switch (M->d.kind) {
     case ANQS_MODEL_MLP:
+      if (M->d.form == ANQS_FORM_BF16) return launch_mlp_tc_logpsi(M, H->v, x, n_x, la, ph, s);
       return launch_mlp_fp32_logpsi(M->mlp, H->v, x, n_x, la, ph, s);
     case ANQS_MODEL_TABLE:
       return launch_table_logpsi(M, H->v, x, n_x, la, ph, s);

@@ -185,6 +185,11 @@ int mlp_tc_pack(anqs_model* m, cudaStream_t s);
 size_t eloc_tc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x);
 int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, double* ere,
                 double* eim, void* ws, size_t ws_bytes, cudaStream_t s);
+int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la,
+                         float* ph, cudaStream_t s);
+int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, const uint64_t* pre,
+                              const uint64_t* n_dev, uint64_t max_rows, float* out8, cudaStream_t s);
+int mlp_tc_status(const anqs_model* M, int* status);
 
 // api.cu
 int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, float* la,

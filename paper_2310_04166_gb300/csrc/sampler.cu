@@ -20,8 +20,8 @@
 
 namespace anqs {
 
-int logits_dispatch(const anqs_model* M, int p, const uint64_t* pre, const uint64_t* n_dev, uint64_t max_rows,
-                    float* out8, cudaStream_t s);
+int logits_dispatch(const anqs_model* M, const anqs_ham* H, int p, const uint64_t* pre, const uint64_t* n_dev,
+                    uint64_t max_rows, float* out8, cudaStream_t s);
 
 namespace {
 
@@ -348,7 +348,7 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
     const int cur = p & 1, nxt = cur ^ 1;
     const uint64_t Fp = level_cap(H, n_samples, p);
     uint64_t* nf = P.n_front + cur;
-    ANQS_TRY(logits_dispatch(M, p, P.pre[cur], nf, Fp, P.logits, s));
+    ANQS_TRY(logits_dispatch(M, H, p, P.pre[cur], nf, Fp, P.logits, s));
     ProfScope ps(PROF_SAMPLER, s);
     prep_kernel<<<blocks_for(Fp, 256, 152 * 8), 256, 0, s>>>(H->v, p, P.pre[cur], P.cnt[cur], nf, P.logits, P.cdf,
                                                               P.allowed, P.nblk, P.child);
@@ -370,10 +370,12 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
   return ANQS_OK;
 }
 
-int logits_dispatch(const anqs_model* M, int p, const uint64_t* pre, const uint64_t* n_dev, uint64_t max_rows,
-                    float* out8, cudaStream_t s) {
+int logits_dispatch(const anqs_model* M, const anqs_ham* H, int p, const uint64_t* pre, const uint64_t* n_dev,
+                    uint64_t max_rows, float* out8, cudaStream_t s) {
   switch (M->d.kind) {
     case ANQS_MODEL_MLP:
+      if (M->d.form == ANQS_FORM_BF16)
+        return launch_mlp_tc_slot_logits(M, H->v, p, pre, n_dev, max_rows, out8, s);
       return launch_mlp_fp32_slot_logits(M->mlp, p, pre, n_dev, max_rows, out8, s);
     case ANQS_MODEL_TABLE:
       return launch_table_slot_logits(M, p, pre, n_dev, max_rows, out8, s);
