@@ -179,6 +179,9 @@ def main():
     ap.add_argument("--form", default=os.environ.get("ANQS_BENCH_FORM", "bf16"), choices=["fp32", "bf16"])
     ap.add_argument("--workload", default="h2o")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="one FP32-form sampling pass, then one local-energy call in the chosen form "
+                         "(the launch sequence to capture with ncu), then exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -211,6 +214,14 @@ def main():
         else:
             raise
     Ns = w["n_samples"]
+    if args.kernel_case:
+        m32 = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form="fp32")
+        xk, nk = A.sample(m32, ham, Ns, seed=99)
+        ek = A.local_energy(model, ham, xk, nk)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": args.workload, "form": form, "n_unique": xk.numel(),
+                          "E": float(ek[2][0])}))
+        return
     cap = min(Ns, ham.sector_dim)
     x = torch.empty(cap, dtype=torch.int64, device=dev)
     cnt = torch.empty(cap, dtype=torch.int64, device=dev)
