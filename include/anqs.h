@@ -181,7 +181,9 @@ ANQS_API int anqs_model_sync(anqs_model* model, void* stream);
 /* log psi(x) for n_x determinants: log_abs_dev[l] = log|psi(x_l)|,
  * phase_dev[l] = arg psi(x_l) (unwrapped sum of slot phases), float32.
  * A determinant outside the sector has log_abs = -inf.  The model's n_orb
- * must equal the Hamiltonian's. */
+ * must equal the Hamiltonian's.  The BF16 form stages raw slot outputs in a
+ * scratch buffer owned by the model: calls on the same BF16 model must not
+ * run concurrently on different streams. */
 ANQS_API int anqs_logpsi(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev,
                 uint64_t n_x, float* log_abs_dev, float* phase_dev, void* stream);
 

@@ -316,6 +316,8 @@ int anqs_model_create(anqs_model** out, const anqs_model_desc* d, const float* p
   M->n_params = count_params(d);
   M->packed = nullptr;
   M->packed_bytes = 0;
+  M->tc_raw = nullptr;
+  M->tc_raw_rows = 0;
   if (d->kind == ANQS_MODEL_MLP) {
     MlpView& v = M->mlp;
     v.n = d->n_orb;
@@ -358,6 +360,7 @@ int anqs_model_create(anqs_model** out, const anqs_model_desc* d, const float* p
 int anqs_model_destroy(anqs_model* M) {
   if (!M) return ANQS_OK;
   if (M->packed) cudaFree(M->packed);
+  if (M->tc_raw) cudaFree(M->tc_raw);
   delete M;
   return ANQS_OK;
 }

@@ -144,6 +144,8 @@ struct anqs_model {
   void* packed;
   size_t packed_bytes;
   std::vector<uint64_t> pack_off;  // per slot byte offset of its image
+  float* tc_raw;                   // BF16 form: raw slot outputs of one chunk of anqs_logpsi rows
+  uint64_t tc_raw_rows;
 };
 
 // ---- launchers implemented in the kernel translation units ----

@@ -73,6 +73,8 @@ struct TcView {
   const unsigned char* img;   // packed images
   uint32_t img_off[ANQS_MAX_ORB + 1];
   uint32_t max_img;           // largest image (bytes)
+  uint32_t kmax;              // widest A operand (columns)
+  int nbuf;                   // weight-image buffers in shared memory (1 or 2)
   int* status;
 };
 
@@ -124,239 +126,395 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t phase) {
 }
 
 struct TileArgs {
-  // PARENT / LOGPSI / LOGITS: rows are x[0..n_rows); SUFFIX: rows perm[0..n_rows)
-  const uint64_t* x;
-  const uint64_t* n_rows_dev;  // LOGITS: device-side row count
+  const uint64_t* x;           // SLOTS: rows x[0..n_rows); SUFFIX: connected determinants
+  const uint64_t* n_rows_dev;  // SLOTS: device-side row count (or null: n_rows)
   uint64_t n_rows;
-  int p_single;                // LOGITS: the slot
+  int p_lo, p_hi;              // SLOTS: slots [p_lo, p_hi)
+  float* raw;                  // SLOTS output [row][p_hi - p_lo][8]
   // SUFFIX
   const uint32_t* perm;
   const uint8_t* js;
   const float* cache;          // [n_parents][n][CACHE_F]
   uint32_t K;
-  // outputs
   float* la;
   float* ph;
-  float* cache_out;            // PARENT
-  float* logits_out;           // LOGITS [n_rows][8]
 };
 
-template <int W, int MODE>
-__global__ void __launch_bounds__(MT, 1) mlp_tc_kernel(TcView tv, HamView hv, TileArgs ta) {
-  extern __shared__ __align__(1024) unsigned char smem[];
-  // [0, max_img): slot image; then the A tile (128 rows x max(W, k1) bf16)
-  unsigned char* s_img = smem;
-  unsigned char* s_a = smem + round_up(tv.max_img, 1024u);
-  __shared__ __align__(8) uint64_t s_bar[2];  // 0: weights, 1: mma
-  __shared__ uint32_t s_tmem;
-  __shared__ int s_jmin, s_abort;
+constexpr int NT = 2 * MT;   // two warpgroups
+constexpr int TPW = 4;       // SUFFIX: tiles per warpgroup per chunk
 
-  const int tid = threadIdx.x;
-  const int n = tv.n, L = tv.L;
-  const uint32_t bar_w = tc::smem_u32(&s_bar[0]), bar_m = tc::smem_u32(&s_bar[1]);
-  const uint32_t a_addr = tc::smem_u32(s_a), img_addr = tc::smem_u32(s_img);
-  constexpr uint32_t kCols = 2 * W;  // two accumulators
+struct Ctx {
+  const TcView* tv;
+  unsigned char* s_a;        // this warpgroup's A tile
+  uint32_t a_addr;
+  uint32_t tmem;             // this warpgroup's two accumulators
+  uint32_t lane_base;
+  uint32_t bar_m;            // this warpgroup's MMA barrier
+  int wg, t;
+};
+
+__device__ __forceinline__ void wg_sync(int wg) { asm volatile("bar.sync %0, 128;" ::"r"(1 + wg) : "memory"); }
+
+// Warpgroup barrier that also ANDs a flag over the 128 threads, so that a
+// bounded wait that gives up in some threads sends the whole warpgroup down
+// the same path.
+__device__ __forceinline__ bool wg_all(int wg, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred q, s;\n\t"
+      "setp.ne.u32 q, %1, 0;\n\t"
+      "bar.red.and.pred s, %2, 128, q;\n\t"
+      "selp.u32 %0, 1, 0, s;\n\t}\n"
+      : "=r"(r)
+      : "r"(uint32_t(v)), "r"(1 + wg)
+      : "memory");
+  return r != 0;
+}
+
+// All layers of slot p for the 128 rows of one tile (one warpgroup; row t =
+// thread t).  Returns false if a wait timed out.
+template <int W>
+__device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const SlotLayout& S, uint32_t img_addr,
+                          const unsigned char* img, float (&out)[8]) {
   constexpr uint32_t IDESC = tc::idesc_bf16_f32(MT, W);
-
-  if (tid == 0) {
-    tc::mbar_init(bar_w, 1);
-    tc::mbar_init(bar_m, 1);
-    tc::fence_mbar_init();
-    s_abort = 0;
+  const int L = c.tv->L;
+  // layer-1 input: one-hot of v_<p (K = k1 columns)
+  for (uint32_t k = 0; k < S.k1; k += 8) {
+    uint32_t w4[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint32_t lo = 0, hi = 0;
+      const uint32_t k0 = k + 2 * e, k1 = k0 + 1;
+      if (k0 < 4u * p && ((x >> (2 * (k0 >> 2))) & 3ull) == (k0 & 3u)) lo = 0x3F80u;
+      if (k1 < 4u * p && ((x >> (2 * (k1 >> 2))) & 3ull) == (k1 & 3u)) hi = 0x3F80u;
+      w4[e] = lo | (hi << 16);
+    }
+    *reinterpret_cast<uint4*>(c.s_a + tc::canon_off(c.t, k, S.k1)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
   }
-  if (tid < 32) {
-    tc::tmem_alloc(tc::smem_u32(&s_tmem), kCols);
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  wg_sync(c.wg);
+  const float* bias = reinterpret_cast<const float*>(img + S.bias);
+  const float* head = reinterpret_cast<const float*>(img + S.head);
+  const float* hbias = reinterpret_cast<const float*>(img + S.hbias);
+#pragma unroll
+  for (int o = 0; o < 8; ++o) out[o] = 0.f;
+  bool ok = true;
+  for (int layer = 0; layer < L; ++layer) {
+    const uint32_t K = layer == 0 ? S.k1 : uint32_t(W);
+    const uint32_t d_tmem = c.tmem + uint32_t(layer & 1) * W;
+    if (K > 0) {
+      if (c.t == 0) {
+        tc::fence_after_sync();
+        const uint32_t b_addr = img_addr + (layer == 0 ? S.w1 : S.wk + uint32_t(layer - 1) * W * W * 2u);
+#pragma unroll 1
+        for (uint32_t ks = 0; ks < K / 16; ++ks) {
+          const uint64_t ad = tc::sdesc(c.a_addr + ks * 256u, 128u, K * 16u);
+          const uint64_t bd = tc::sdesc(b_addr + ks * 256u, 128u, K * 16u);
+          tc::mma_bf16(d_tmem, ad, bd, IDESC, ks > 0 ? 1u : 0u);
+        }
+        tc::mma_commit(c.bar_m);
+      }
+      ok = wg_all(c.wg, wait_bar(c.bar_m, ph_m));
+      ph_m ^= 1;
+      if (!ok) return false;
+      tc::fence_after_sync();
+    }
+    const bool last = (layer == L - 1);
+    const float* b = bias + layer * W;
+#pragma unroll 1
+    for (int c0 = 0; c0 < W; c0 += 32) {
+      float v[32];
+      if (K > 0) {
+        tc::tmem_ld32(d_tmem + c.lane_base + uint32_t(c0), v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) v[i] = tc::tanh_fast(v[i] + b[c0 + i]);
+      if (!last) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          uint4 u;
+          u.x = tc::pack_bf16x2(v[8 * q + 0], v[8 * q + 1]);
+          u.y = tc::pack_bf16x2(v[8 * q + 2], v[8 * q + 3]);
+          u.z = tc::pack_bf16x2(v[8 * q + 4], v[8 * q + 5]);
+          u.w = tc::pack_bf16x2(v[8 * q + 6], v[8 * q + 7]);
+          *reinterpret_cast<uint4*>(c.s_a + tc::canon_off(c.t, c0 + 8 * q, W)) = u;
+        }
+      } else {
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+          const float4* hw = reinterpret_cast<const float4*>(head + o * W + c0);
+          float acc = out[o];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float4 h4 = hw[i];
+            acc = fmaf(h4.x, v[4 * i + 0], acc);
+            acc = fmaf(h4.y, v[4 * i + 1], acc);
+            acc = fmaf(h4.z, v[4 * i + 2], acc);
+            acc = fmaf(h4.w, v[4 * i + 3], acc);
+          }
+          out[o] = acc;
+        }
+      }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    wg_sync(c.wg);
+  }
+#pragma unroll
+  for (int o = 0; o < 8; ++o) out[o] += hbias[o];
+  return true;
+}
+
+// Shared set-up of both kernels: barriers and TMEM (4W columns: two
+// accumulators per warpgroup).
+template <int W>
+__device__ __forceinline__ void setup(uint64_t* bars, uint32_t* s_tmem, int* s_abort) {
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) tc::mbar_init(tc::smem_u32(&bars[i]), 1);
+    tc::fence_mbar_init();
+    *s_abort = 0;
+  }
+  if (threadIdx.x < 32) {
+    tc::tmem_alloc(tc::smem_u32(s_tmem), 4 * W);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  const uint32_t tmem = s_tmem;
-  const uint32_t lane_base = uint32_t(tid & ~31) << 16;  // warp w reads TMEM lanes 32w..32w+31
-  uint32_t ph_w = 0, ph_m = 0;
+}
 
-  const uint64_t n_rows = (MODE == MODE_LOGITS) ? *ta.n_rows_dev : ta.n_rows;
-  const uint64_t n_tiles = (n_rows + MT - 1) / MT;
-  for (uint64_t tile = blockIdx.x; tile < n_tiles && !s_abort; tile += gridDim.x) {
-    const uint64_t r = tile * MT + tid;
-    const bool valid = r < n_rows;
-    uint64_t x = 0;
-    int j = -1;
-    float la = 0.f, phs = 0.f;
-    uint64_t out_idx = r;
-    if (MODE == MODE_SUFFIX) {
-      if (valid) {
-        const uint32_t row = ta.perm[r];
-        out_idx = row;
-        x = ta.x[row];
-        j = ta.js[row];
-        const uint64_t parent = row / ta.K;
-        const float* c = ta.cache + (parent * n + j) * CACHE_F;
-        const int vj = int((x >> (2 * j)) & 3ull);
-        la = c[0] + c[2 + vj];
-        phs = c[1] + c[6 + vj];
-      } else {
-        j = n;  // no slots
-      }
-    } else if (valid) {
-      x = ta.x[r];
-    }
-    if (MODE == MODE_LOGITS) j = ta.p_single - 1;
-    if (tid == 0) s_jmin = n;
-    __syncthreads();
-    if (valid || MODE != MODE_SUFFIX) atomicMin(&s_jmin, j);
-    __syncthreads();
-    const int p0 = (MODE == MODE_LOGITS) ? ta.p_single : s_jmin + 1;
-    const int p1 = (MODE == MODE_LOGITS) ? ta.p_single + 1 : n;
-    bool dead = false;
-
-    for (int p = p0; p < p1; ++p) {
-      const SlotLayout S = slot_layout(p, W, L);
-      // weights of slot p (the previous slot's readers are done: barrier at loop end)
-      if (tid == 0) {
-        tc::mbar_arrive_expect_tx(bar_w, S.bytes);
-        tc::bulk_g2s(img_addr, tv.img + tv.img_off[p], S.bytes, bar_w);
-      }
-      // layer-1 input: one-hot of v_<p, K = k1 columns
-      for (uint32_t c = 0; c < S.k1; c += 8) {
-        uint32_t w4[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          uint32_t lo = 0, hi = 0;
-          const uint32_t k0 = c + 2 * e, k1 = k0 + 1;
-          if (k0 < 4u * p && ((x >> (2 * (k0 >> 2))) & 3ull) == (k0 & 3u)) lo = 0x3F80u;
-          if (k1 < 4u * p && ((x >> (2 * (k1 >> 2))) & 3ull) == (k1 & 3u)) hi = 0x3F80u;
-          w4[e] = lo | (hi << 16);
-        }
-        *reinterpret_cast<uint4*>(s_a + tc::canon_off(tid, c, S.k1)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
-      }
-      tc::fence_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      if (!wait_bar(bar_w, ph_w)) s_abort = 1;
-      ph_w ^= 1;
-      __syncthreads();
-      if (s_abort) break;
-      const float* bias = reinterpret_cast<const float*>(s_img + S.bias);
-      const float* head = reinterpret_cast<const float*>(s_img + S.head);
-      const float* hbias = reinterpret_cast<const float*>(s_img + S.hbias);
-      float out[8];
-#pragma unroll
-      for (int o = 0; o < 8; ++o) out[o] = 0.f;
-
-      bool aborted = false;
-      for (int layer = 0; layer < L; ++layer) {
-        const uint32_t K = layer == 0 ? S.k1 : uint32_t(W);
-        const uint32_t d_tmem = tmem + uint32_t(layer & 1) * W;
-        if (K > 0) {
-          if (tid == 0) {
-            tc::fence_after_sync();
-            const uint32_t b_addr = img_addr + (layer == 0 ? S.w1 : S.wk + uint32_t(layer - 1) * W * W * 2u);
-#pragma unroll 1
-            for (uint32_t ks = 0; ks < K / 16; ++ks) {
-              const uint64_t ad = tc::sdesc(a_addr + ks * 256u, 128u, K * 16u);
-              const uint64_t bd = tc::sdesc(b_addr + ks * 256u, 128u, K * 16u);
-              tc::mma_bf16(d_tmem, ad, bd, IDESC, ks > 0 ? 1u : 0u);
-            }
-            tc::mma_commit(bar_m);
-          }
-          if (!wait_bar(bar_m, ph_m)) s_abort = 1;
-          ph_m ^= 1;
-          __syncthreads();
-          if (s_abort) {
-            aborted = true;
-            break;
-          }
-          tc::fence_after_sync();
-        }
-        const bool last = (layer == L - 1);
-        const float* b = bias + layer * W;
-#pragma unroll 1
-        for (int c0 = 0; c0 < W; c0 += 32) {
-          float v[32];
-          if (K > 0) {
-            tc::tmem_ld32(d_tmem + lane_base + uint32_t(c0), v);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = 0.f;
-          }
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = tc::tanh_fast(v[i] + b[c0 + i]);
-          if (!last) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              uint4 u;
-              u.x = tc::pack_bf16x2(v[8 * q + 0], v[8 * q + 1]);
-              u.y = tc::pack_bf16x2(v[8 * q + 2], v[8 * q + 3]);
-              u.z = tc::pack_bf16x2(v[8 * q + 4], v[8 * q + 5]);
-              u.w = tc::pack_bf16x2(v[8 * q + 6], v[8 * q + 7]);
-              *reinterpret_cast<uint4*>(s_a + tc::canon_off(tid, c0 + 8 * q, W)) = u;
-            }
-          } else {
-#pragma unroll
-            for (int o = 0; o < 8; ++o) {
-              const float* hw = head + o * W + c0;
-              float acc = out[o];
-#pragma unroll
-              for (int i = 0; i < 32; ++i) acc = fmaf(hw[i], v[i], acc);
-              out[o] = acc;
-            }
-          }
-        }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-      }
-      if (aborted) break;
-#pragma unroll
-      for (int o = 0; o < 8; ++o) out[o] += hbias[o];
-
-      if (MODE == MODE_LOGITS) {
-        if (valid)
-#pragma unroll
-          for (int o = 0; o < 8; ++o) ta.logits_out[r * 8 + o] = out[o];
-      } else if (valid && j < p) {
-        // masked log-softmax of slot p for this row's prefix (f32)
-        const uint64_t pm = (p == 0) ? 0ull : ((1ull << (2 * p)) - 1ull);
-        const int a = __popcll(x & pm & 0x5555555555555555ull), bb = __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull);
-        const unsigned mk = slot_mask(hv, p, a, bb);
-        float mx = -INFINITY;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if ((mk >> u) & 1u) mx = fmaxf(mx, out[u]);
-        float s = 0.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if ((mk >> u) & 1u) s += __expf(out[u] - mx);
-        const float lse = mx + __logf(s);
-        const int v = int((x >> (2 * p)) & 3ull);
-        if (MODE == MODE_PARENT) {
-          float* c = ta.cache_out + (r * n + p) * CACHE_F;
-          c[0] = la;
-          c[1] = phs;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            c[2 + u] = ((mk >> u) & 1u) ? 0.5f * (out[u] - lse) : -INFINITY;
-            c[6 + u] = out[4 + u];
-          }
-        }
-        if (!((mk >> v) & 1u)) dead = true;
-        la += 0.5f * (out[v] - lse);
-        phs += out[4 + v];
-      }
-    }
-    if (MODE != MODE_LOGITS && valid) {
-      bool outside = dead || (n < 32 && (x >> (2 * n)) != 0);
-      ta.la[out_idx] = outside ? -INFINITY : la;
-      ta.ph[out_idx] = phs;
-    }
-    __syncthreads();
-  }
-  if (s_abort && tid == 0) atomicExch(tv.status, ST_TIMEOUT);
+template <int W>
+__device__ __forceinline__ void teardown(const TcView& tv, uint32_t tmem, int abort) {
+  if (abort && threadIdx.x == 0) atomicExch(tv.status, ST_TIMEOUT);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (tid < 32) tc::tmem_dealloc(tmem, kCols);
+  if (threadIdx.x < 32) tc::tmem_dealloc(tmem, 4 * W);
+}
+
+__device__ __forceinline__ void load_slot(const TcView& tv, int p, uint32_t dst, uint32_t bar, int W, int L) {
+  const SlotLayout S = slot_layout(p, W, L);
+  tc::mbar_arrive_expect_tx(bar, S.bytes);
+  tc::bulk_g2s(dst, tv.img + tv.img_off[p], S.bytes, bar);
+}
+
+// SLOTS: work item = (pair of 128-row tiles, slot p); writes the 8 raw
+// outputs of slot p for every row.
+template <int W>
+__global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs ta) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[4];  // 0,1: weights; 2,3: MMA per warpgroup
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  const int wg = threadIdx.x / MT, t = threadIdx.x % MT;
+  setup<W>(bars, &s_tmem, &s_abort);
+  const uint32_t img_stride = round_up(tv.max_img, 1024u);
+  unsigned char* s_img = smem;
+  Ctx c;
+  c.tv = &tv;
+  c.s_a = smem + img_stride * tv.nbuf + wg * (MT * tv.kmax * 2u);
+  c.a_addr = tc::smem_u32(c.s_a);
+  c.tmem = s_tmem + uint32_t(wg) * 2 * W;
+  c.lane_base = uint32_t(t & ~31) << 16;
+  c.bar_m = tc::smem_u32(&bars[2 + wg]);
+  c.wg = wg;
+  c.t = t;
+  const uint32_t bar_w = tc::smem_u32(&bars[0]);
+  uint32_t ph_w = 0, ph_m = 0;
+  const uint64_t n_rows = ta.n_rows_dev ? *ta.n_rows_dev : ta.n_rows;
+  const uint64_t n_pairs = (n_rows + 2 * MT - 1) / (2 * MT);
+  const int np = ta.p_hi - ta.p_lo;
+  const uint64_t n_items = n_pairs * uint64_t(np);
+  for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int p = ta.p_lo + int(it / n_pairs);
+    const uint64_t pair = it % n_pairs;
+    const SlotLayout S = slot_layout(p, W, tv.L);
+    if (threadIdx.x == 0) load_slot(tv, p, tc::smem_u32(s_img), bar_w, W, tv.L);
+    const uint64_t r = (pair * 2 + wg) * MT + t;
+    const bool valid = r < n_rows;
+    const uint64_t x = valid ? ta.x[r] : 0ull;
+    bool ok = __syncthreads_and(wait_bar(bar_w, ph_w));
+    ph_w ^= 1;
+    float out[8];
+    if (ok && (pair * 2 + wg) * MT < n_rows) ok = tile_slot<W>(c, ph_m, p, x, S, tc::smem_u32(s_img), s_img, out);
+    if (!ok) s_abort = 1;
+    if (ok && valid) {
+      float4* dst = reinterpret_cast<float4*>(ta.raw + (r * np + (p - ta.p_lo)) * 8);
+      dst[0] = make_float4(out[0], out[1], out[2], out[3]);
+      dst[1] = make_float4(out[4], out[5], out[6], out[7]);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    if (s_abort) break;
+  }
+  teardown<W>(tv, s_tmem, s_abort);
+}
+
+// SUFFIX: chunks of 2*TPW tiles per CTA (tiles b, b+G, ... of the rows
+// sorted by first differing slot), slot-outer so that each slot's weights are
+// loaded once per chunk; the next slot's image is prefetched when two
+// buffers fit.
+template <int W>
+__global__ void __launch_bounds__(NT, 1) mlp_tc_suffix_kernel(TcView tv, HamView hv, TileArgs ta) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  __shared__ int s_jmin[2 * TPW];
+  const int wg = threadIdx.x / MT, t = threadIdx.x % MT;
+  const int n = tv.n;
+  setup<W>(bars, &s_tmem, &s_abort);
+  const uint32_t img_stride = round_up(tv.max_img, 1024u);
+  Ctx c;
+  c.tv = &tv;
+  c.s_a = smem + img_stride * tv.nbuf + wg * (MT * tv.kmax * 2u);
+  c.a_addr = tc::smem_u32(c.s_a);
+  c.tmem = s_tmem + uint32_t(wg) * 2 * W;
+  c.lane_base = uint32_t(t & ~31) << 16;
+  c.bar_m = tc::smem_u32(&bars[2 + wg]);
+  c.wg = wg;
+  c.t = t;
+  uint32_t ph_w[2] = {0, 0}, ph_m = 0;
+  const uint64_t n_rows = ta.n_rows;
+  const uint64_t n_tiles = (n_rows + MT - 1) / MT;
+  const uint64_t G = gridDim.x;
+  for (uint64_t chunk = 0;; ++chunk) {
+    const uint64_t first = blockIdx.x + chunk * (2 * TPW) * G;
+    if (first >= n_tiles) break;
+    uint64_t x[TPW];
+    int j[TPW];
+    float la[TPW], phs[TPW];
+    uint32_t oi[TPW];
+    if (threadIdx.x < 2 * TPW) s_jmin[threadIdx.x] = n;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < TPW; ++q) {
+      const uint64_t tile = first + uint64_t(wg + 2 * q) * G;
+      const uint64_t r = tile * MT + t;
+      x[q] = 0;
+      j[q] = n;
+      la[q] = phs[q] = 0.f;
+      oi[q] = 0;
+      if (tile < n_tiles && r < n_rows) {
+        const uint32_t row = ta.perm[r];
+        oi[q] = row;
+        x[q] = ta.x[row];
+        j[q] = ta.js[row];
+        const float* cc = ta.cache + (uint64_t(row / ta.K) * n + j[q]) * CACHE_F;
+        const int vj = int((x[q] >> (2 * j[q])) & 3ull);
+        la[q] = cc[0] + cc[2 + vj];
+        phs[q] = cc[1] + cc[6 + vj];
+        atomicMin(&s_jmin[wg + 2 * q], j[q]);
+      }
+    }
+    __syncthreads();
+    int jlo = n;
+    for (int i = 0; i < 2 * TPW; ++i) jlo = min(jlo, s_jmin[i]);
+    const int p0 = jlo + 1;
+    const uint32_t img0 = tc::smem_u32(smem);
+    if (threadIdx.x == 0 && p0 < n) load_slot(tv, p0, img0, tc::smem_u32(&bars[0]), W, tv.L);
+    for (int p = p0; p < n; ++p) {
+      const int b = (tv.nbuf == 2) ? ((p - p0) & 1) : 0;
+      const uint32_t img_addr = img0 + uint32_t(b) * img_stride;
+      const unsigned char* img = smem + b * img_stride;
+      if (tv.nbuf == 2 && threadIdx.x == 0 && p + 1 < n)
+        load_slot(tv, p + 1, img0 + uint32_t(b ^ 1) * img_stride, tc::smem_u32(&bars[b ^ 1]), W, tv.L);
+      bool ok = __syncthreads_and(wait_bar(tc::smem_u32(&bars[b]), ph_w[b]));
+      ph_w[b] ^= 1;
+      const SlotLayout S = slot_layout(p, W, tv.L);
+#pragma unroll
+      for (int q = 0; q < TPW; ++q) {
+        if (!ok || s_jmin[wg + 2 * q] >= p) continue;  // uniform per warpgroup
+        float out[8];
+        ok = tile_slot<W>(c, ph_m, p, x[q], S, img_addr, img, out);
+        if (ok && j[q] < p) {
+          const uint64_t pm = (1ull << (2 * p)) - 1ull;
+          const int a = __popcll(x[q] & pm & 0x5555555555555555ull);
+          const int bb = __popcll(x[q] & pm & 0xAAAAAAAAAAAAAAAAull);
+          const unsigned mk = slot_mask(hv, p, a, bb);
+          float mx = -INFINITY;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if ((mk >> u) & 1u) mx = fmaxf(mx, out[u]);
+          float s = 0.f;
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if ((mk >> u) & 1u) s += __expf(out[u] - mx);
+          const int v = int((x[q] >> (2 * p)) & 3ull);
+          const float ov = (v == 0) ? out[0] : (v == 1) ? out[1] : (v == 2) ? out[2] : out[3];
+          const float pv = (v == 0) ? out[4] : (v == 1) ? out[5] : (v == 2) ? out[6] : out[7];
+          const float lse = mx + __logf(s);  // same expression order as finalize_kernel
+          la[q] += ((mk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY;
+          phs[q] += pv;
+        }
+      }
+      if (!ok) s_abort = 1;
+      tc::fence_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      if (s_abort) break;
+      if (tv.nbuf == 1 && threadIdx.x == 0 && p + 1 < n) load_slot(tv, p + 1, img0, tc::smem_u32(&bars[0]), W, tv.L);
+    }
+    if (s_abort) break;
+#pragma unroll
+    for (int q = 0; q < TPW; ++q) {
+      const uint64_t tile = first + uint64_t(wg + 2 * q) * G;
+      const uint64_t r = tile * MT + t;
+      if (tile < n_tiles && r < n_rows) {
+        ta.la[oi[q]] = la[q];
+        ta.ph[oi[q]] = phs[q];
+      }
+    }
+    __syncthreads();  // s_jmin is reset by the next chunk
+  }
+  teardown<W>(tv, s_tmem, s_abort);
+}
+
+// Per row: masked half-log-probabilities from the raw slot outputs, prefix
+// sums and log psi (and the parent cache when requested).
+__global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, uint64_t n_x,
+                                const float* __restrict__ raw, float* __restrict__ la_out, float* __restrict__ ph_out,
+                                float* __restrict__ cache) {
+  const int n = hv.n;
+  for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x; l += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t x = xs[l];
+    float la = 0.f, ph = 0.f;
+    bool dead = (n < 32) && ((x >> (2 * n)) != 0);
+    int a = 0, b = 0;
+    for (int p = 0; p < n; ++p) {
+      const float* o = raw + (l * n + p) * 8;
+      const unsigned mk = slot_mask(hv, p, a, b);
+      float mx = -INFINITY;
+      for (int u = 0; u < 4; ++u)
+        if ((mk >> u) & 1u) mx = fmaxf(mx, o[u]);
+      float s = 0.f;
+      for (int u = 0; u < 4; ++u)
+        if ((mk >> u) & 1u) s += __expf(o[u] - mx);
+      const float lse = mx + __logf(s);
+      if (cache) {
+        float* cc = cache + (l * n + p) * CACHE_F;
+        cc[0] = la;
+        cc[1] = ph;
+        for (int u = 0; u < 4; ++u) {
+          cc[2 + u] = ((mk >> u) & 1u) ? 0.5f * (o[u] - lse) : -INFINITY;
+          cc[6 + u] = o[4 + u];
+        }
+      }
+      const int v = int((x >> (2 * p)) & 3ull);
+      if (!((mk >> v) & 1u)) dead = true;
+      if (!dead) la += 0.5f * (o[v] - lse);
+      ph += o[4 + v];
+      a += v & 1;
+      b += v >> 1;
+    }
+    la_out[l] = dead ? -INFINITY : la;
+    ph_out[l] = ph;
+  }
 }
 
 // ---- sort of connected rows by first differing slot ---------------------------
@@ -398,6 +556,12 @@ int num_sms() {
   return g_num_sms;
 }
 
+constexpr size_t kSmemLimit = 227 * 1024;
+
+size_t smem_bytes(const TcView& tv, int nbuf) {
+  return size_t(round_up(tv.max_img, 1024u)) * nbuf + 2ull * MT * tv.kmax * 2u;
+}
+
 TcView make_view(const anqs_model* M) {
   TcView tv;
   tv.n = M->d.n_orb;
@@ -407,32 +571,49 @@ TcView make_view(const anqs_model* M) {
   tv.max_img = 0;
   for (int p = 0; p <= tv.n; ++p) tv.img_off[p] = uint32_t(M->pack_off[p]);
   for (int p = 0; p < tv.n; ++p) tv.max_img = std::max(tv.max_img, slot_layout(p, tv.W, tv.L).bytes);
+  tv.kmax = std::max<uint32_t>(tv.W, round_up(4u * (tv.n - 1), 16u));
+  tv.nbuf = smem_bytes(tv, 2) <= kSmemLimit ? 2 : 1;
   tv.status = reinterpret_cast<int*>(static_cast<unsigned char*>(M->packed) + M->pack_off[tv.n]);
   return tv;
 }
 
-size_t smem_bytes(const TcView& tv) {
-  uint32_t kmax = std::max<uint32_t>(tv.W, round_up(4u * (tv.n - 1), 16u));
-  return round_up(tv.max_img, 1024u) + size_t(MT) * kmax * 2u;
+template <int W>
+int launch_slots_w(const TcView& tv, const TileArgs& ta, uint64_t max_rows, cudaStream_t s) {
+  const size_t sm = smem_bytes(tv, 1);
+  const uint64_t items = (max_rows + 2 * MT - 1) / (2 * MT) * uint64_t(ta.p_hi - ta.p_lo);
+  const unsigned grid = unsigned(std::min<uint64_t>(items ? items : 1, uint64_t(num_sms())));
+  TcView v1 = tv;
+  v1.nbuf = 1;
+  ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_slots_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+  mlp_tc_slots_kernel<W><<<grid, NT, sm, s>>>(v1, ta);
+  ANQS_LAUNCHED("mlp_tc_slots_kernel");
+  return ANQS_OK;
 }
 
-template <int MODE>
-int launch_mode(const anqs_model* M, const HamView& hv, const TileArgs& ta, uint64_t max_rows, cudaStream_t s,
-                int prof) {
+int launch_slots(const anqs_model* M, const TileArgs& ta, uint64_t max_rows, cudaStream_t s, int prof) {
   TcView tv = make_view(M);
-  size_t sm = smem_bytes(tv);
-  if (sm > 227 * 1024) return set_error(ANQS_ERR_UNSUPPORTED, "BF16 MLP slot image needs %zu bytes of shared memory", sm);
-  uint64_t tiles = (max_rows + MT - 1) / MT;
-  unsigned grid = unsigned(std::min<uint64_t>(tiles ? tiles : 1, uint64_t(num_sms())));
+  if (smem_bytes(tv, 1) > kSmemLimit) return set_error(ANQS_ERR_UNSUPPORTED, "BF16 MLP slot image too large");
   ProfScope ps(prof, s);
-  if (tv.W == 128) {
-    ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_kernel<128, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-    mlp_tc_kernel<128, MODE><<<grid, MT, sm, s>>>(tv, hv, ta);
-  } else {
-    ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_kernel<64, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-    mlp_tc_kernel<64, MODE><<<grid, MT, sm, s>>>(tv, hv, ta);
-  }
-  ANQS_LAUNCHED("mlp_tc_kernel");
+  return tv.W == 128 ? launch_slots_w<128>(tv, ta, max_rows, s) : launch_slots_w<64>(tv, ta, max_rows, s);
+}
+
+template <int W>
+int launch_suffix_w(const TcView& tv, const HamView& hv, const TileArgs& ta, cudaStream_t s) {
+  const size_t sm = smem_bytes(tv, tv.nbuf);
+  const uint64_t tiles = (ta.n_rows + MT - 1) / MT;
+  const unsigned grid = unsigned(std::min<uint64_t>(tiles ? tiles : 1, uint64_t(num_sms())));
+  ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_suffix_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+  mlp_tc_suffix_kernel<W><<<grid, NT, sm, s>>>(tv, hv, ta);
+  ANQS_LAUNCHED("mlp_tc_suffix_kernel");
+  return ANQS_OK;
+}
+
+int launch_finalize(const HamView& hv, const uint64_t* x, uint64_t n_x, const float* raw, float* la, float* ph,
+                    float* cache, cudaStream_t s) {
+  uint64_t blocks = (n_x + 127) / 128;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  finalize_kernel<<<unsigned(blocks ? blocks : 1), 128, 0, s>>>(hv, x, n_x, raw, la, ph, cache);
+  ANQS_LAUNCHED("finalize_kernel");
   return ANQS_OK;
 }
 
@@ -441,7 +622,7 @@ struct ElocWs {
   double* hv;
   uint8_t* js;
   double* hd;
-  float *la_x, *ph_x, *cache, *la_p, *ph_p;
+  float *la_x, *ph_x, *raw, *cache, *la_p, *ph_p;
   uint32_t *perm, *hist, *cursor;
 };
 
@@ -453,6 +634,7 @@ size_t plan_eloc(const anqs_ham* H, uint64_t n_x, Arena& A, ElocWs& w) {
   w.hd = A.take<double>(n_x);
   w.la_x = A.take<float>(n_x);
   w.ph_x = A.take<float>(n_x);
+  w.raw = A.take<float>(n_x * H->v.n * 8);
   w.cache = A.take<float>(n_x * H->v.n * CACHE_F);
   w.la_p = A.take<float>(m);
   w.ph_p = A.take<float>(m);
@@ -481,10 +663,14 @@ int mlp_tc_pack_alloc(anqs_model* M) {
   tv.L = L;
   tv.max_img = 0;
   for (int p = 0; p < n; ++p) tv.max_img = std::max(tv.max_img, slot_layout(p, W, L).bytes);
-  if (smem_bytes(tv) > 227 * 1024)
-    return set_error(ANQS_ERR_UNSUPPORTED, "BF16 MLP slot image too large for shared memory (%zu bytes)", smem_bytes(tv));
+  tv.kmax = std::max<uint32_t>(W, round_up(4u * (n - 1), 16u));
+  if (smem_bytes(tv, 1) > kSmemLimit)
+    return set_error(ANQS_ERR_UNSUPPORTED, "BF16 MLP slot image too large for shared memory (%zu bytes)",
+                     smem_bytes(tv, 1));
   ANQS_CUDA(cudaMalloc(&M->packed, M->packed_bytes));
   ANQS_CUDA(cudaMemset(M->packed, 0, M->packed_bytes));
+  M->tc_raw_rows = 32768;
+  ANQS_CUDA(cudaMalloc(&M->tc_raw, M->tc_raw_rows * n * 8 * sizeof(float)));
   return ANQS_OK;
 }
 
@@ -504,27 +690,38 @@ int mlp_tc_status(const anqs_model* M, int* status) {
   return ANQS_OK;
 }
 
+// anqs_logpsi in the BF16 form: chunks of the model's scratch rows.
 int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la,
                          float* ph, cudaStream_t s) {
-  TileArgs ta{};
-  ta.x = x;
-  ta.n_rows = n_x;
-  ta.la = la;
-  ta.ph = ph;
-  return launch_mode<MODE_LOGPSI>(M, hv, ta, n_x, s, PROF_TC_PARENT);
+  for (uint64_t off = 0; off < n_x; off += M->tc_raw_rows) {
+    const uint64_t k = std::min<uint64_t>(M->tc_raw_rows, n_x - off);
+    TileArgs ta{};
+    ta.x = x + off;
+    ta.n_rows = k;
+    ta.p_lo = 0;
+    ta.p_hi = M->d.n_orb;
+    ta.raw = M->tc_raw;
+    ANQS_TRY(launch_slots(M, ta, k, s, PROF_TC_PARENT));
+    ProfScope ps(PROF_TC_PARENT, s);
+    ANQS_TRY(launch_finalize(hv, x + off, k, M->tc_raw, la + off, ph + off, nullptr, s));
+  }
+  return ANQS_OK;
 }
 
 int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, const uint64_t* pre,
                               const uint64_t* n_dev, uint64_t max_rows, float* out8, cudaStream_t s) {
+  (void)hv;
   TileArgs ta{};
   ta.x = pre;
   ta.n_rows_dev = n_dev;
-  ta.p_single = p;
-  ta.logits_out = out8;
-  return launch_mode<MODE_LOGITS>(M, hv, ta, max_rows, s, PROF_TC_SLOT);
+  ta.p_lo = p;
+  ta.p_hi = p + 1;
+  ta.raw = out8;
+  return launch_slots(M, ta, max_rows, s, PROF_TC_SLOT);
 }
 
 size_t eloc_tc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x) {
+  (void)M;
   Arena A(nullptr, 0);
   ElocWs w;
   return plan_eloc(H, n_x, A, w);
@@ -543,10 +740,12 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint6
     TileArgs ta{};
     ta.x = x;
     ta.n_rows = n_x;
-    ta.la = w.la_x;
-    ta.ph = w.ph_x;
-    ta.cache_out = w.cache;
-    ANQS_TRY(launch_mode<MODE_PARENT>(M, H->v, ta, n_x, s, PROF_TC_PARENT));
+    ta.p_lo = 0;
+    ta.p_hi = H->v.n;
+    ta.raw = w.raw;
+    ANQS_TRY(launch_slots(M, ta, n_x, s, PROF_TC_PARENT));
+    ProfScope ps(PROF_TC_PARENT, s);
+    ANQS_TRY(launch_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
   }
   {
     ProfScope ps(PROF_TC_SORT, s);
@@ -569,7 +768,9 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint6
     ta.K = uint32_t(K);
     ta.la = w.la_p;
     ta.ph = w.ph_p;
-    ANQS_TRY(launch_mode<MODE_SUFFIX>(M, H->v, ta, m, s, PROF_TC_SUFFIX));
+    TcView tv = make_view(M);
+    ProfScope ps(PROF_TC_SUFFIX, s);
+    ANQS_TRY(tv.W == 128 ? launch_suffix_w<128>(tv, H->v, ta, s) : launch_suffix_w<64>(tv, H->v, ta, s));
   }
   return launch_eloc_sum(H->v, n_x, w.hv, w.hd, w.la_x, w.ph_x, w.la_p, w.ph_p, ere, eim, s);
 }
