@@ -167,6 +167,8 @@ def _config(w, args):
                         f"({2 * w['n']} qubits), {w['n_chol']} Cholesky vectors seed {w['seed']}, {net}, "
                         f"N_s={w['n_samples']}",
             "form": args.form, "n_samples": w["n_samples"], "l2": "flushed between timed steps (256 MiB write)",
+            "timing": "one CUDA-graph replay of the whole step per timed iteration (weight packing, sampling, "
+                      "connected set, amplitudes, E_loc and statistics, gradient), CUDA events on the replay stream",
             "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single GPU"}
 
 
@@ -226,63 +228,40 @@ def main():
     x = torch.empty(cap, dtype=torch.int64, device=dev)
     cnt = torch.empty(cap, dtype=torch.int64, device=dev)
     nu = torch.zeros(1, dtype=torch.int64, device=dev)
+    ctr = torch.zeros(1, dtype=torch.int64, device=dev)
     ws_s = A._ws(A.sample_workspace_bytes(model, ham, Ns), dev)
     ws_e = A._ws(A.local_energy_workspace_bytes(model, ham, cap), dev)
-    ere = torch.empty(cap, dtype=torch.float64, device=dev)
-    eim = torch.empty_like(ere)
-    stats = torch.empty(4, dtype=torch.float64, device=dev)
-    g = torch.empty(model.n_params, dtype=torch.float32, device=dev)
-    import ctypes as C
-    gws_b = C.c_size_t()
-    _lib.check(lib.anqs_grad_workspace_size(model._m, ham.handle, cap, C.byref(gws_b)))
-    ws_g = A._ws(gws_b.value, dev)
+    ws_g = A._ws(A.grad_workspace_bytes(model, ham, cap), dev)
+    ere = torch.zeros(cap, dtype=torch.float64, device=dev)
+    eim = torch.zeros_like(ere)
+    stats = torch.zeros(4, dtype=torch.float64, device=dev)
+    g = torch.zeros(model.n_params, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     seed = 1234 + 7919 * rank
+    import ctypes as C
 
-    # N_unq varies per step and is only known on the device: one host read per
-    # step (outside the events) sizes the energy and gradient calls.
-    def run_step(counter, timed_events=None):
-        A.sample_into(model, ham, Ns, seed, counter, x, cnt, nu, ws_s)
-        k = int(nu.item())
-        if timed_events:
-            timed_events[1].record(stream)
-            timed_events[2].record(stream)
-        _lib.check(lib.anqs_local_energy(model._m, ham.handle, x.data_ptr(), cnt.data_ptr(), k, ere.data_ptr(),
-                                         eim.data_ptr(), stats.data_ptr(), ws_e.data_ptr(), ws_e.numel(),
-                                         stream.cuda_stream))
-        _lib.check(lib.anqs_grad(model._m, ham.handle, x.data_ptr(), cnt.data_ptr(), k, ere.data_ptr(),
-                                 eim.data_ptr(), stats.data_ptr(), g.data_ptr(), ws_g.data_ptr(), ws_g.numel(),
-                                 stream.cuda_stream))
-        return k
+    def step():
+        """One pass of the hot path; every size stays on the device (the
+        unique count of the sampler feeds the energy and gradient calls), so
+        the pass can be captured in a CUDA graph and replayed.  The Philox
+        counter advances on the device after each pass."""
+        if form == "bf16":
+            model.sync()  # re-pack the bf16 weight images (the optimiser changes params every step)
+        A.sample_into(model, ham, Ns, seed, 0, x, cnt, nu, ws_s, counter_dev=ctr)
+        A.local_energy(model, ham, x, cnt, workspace=ws_e, n_dev=nu, out=(ere, eim, stats))
+        A.grad(model, ham, x, cnt, ere, eim, stats, workspace=ws_g, n_dev=nu, out=g)
+        ctr.add_(1)
 
-    for i in range(args.warmup):
-        run_step(i)
+    # eager warm-up, then a profiled eager pass (per-kernel CUDA-event times)
+    for _ in range(args.warmup):
+        step()
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-
     lib.anqs_profile_enable(1)
-    l0 = C.c_uint64()
-    lib.anqs_launch_count(C.byref(l0))
-    times, uniq = [], []
-    with Clocks(local) as clk:
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e2 = torch.cuda.Event(enable_timing=True)
-            e3 = torch.cuda.Event(enable_timing=True)
-            torch.cuda.synchronize()
-            e0.record(stream)
-            k = run_step(1000 + i, (e0, e1, e2))
-            e3.record(stream)
-            torch.cuda.synchronize()
-            # device time of the step: sampling (e0..e1) plus energy and
-            # gradient (e2..e3); the host read of N_unq between them is excluded
-            times.append(e0.elapsed_time(e1) + e2.elapsed_time(e3))
-            uniq.append(k)
-    l1 = C.c_uint64()
-    lib.anqs_launch_count(C.byref(l1))
+    n_prof = max(5, args.steps // 2)
+    for _ in range(n_prof):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
     prof = {}
     for pid in range(64):
         nm, n_l, ms = C.c_char_p(), C.c_uint64(), C.c_double()
@@ -291,6 +270,43 @@ def main():
         if n_l.value:
             prof[nm.value.decode()] = (n_l.value, ms.value)
     lib.anqs_profile_enable(0)
+
+    # capture the step in a CUDA graph
+    l0 = C.c_uint64()
+    lib.anqs_launch_count(C.byref(l0))
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    l1 = C.c_uint64()
+    lib.anqs_launch_count(C.byref(l1))
+    launches_per_step = int(l1.value - l0.value)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step()
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+    times, uniq = [], []
+    stream = torch.cuda.current_stream()
+    with Clocks(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            uniq.append(int(nu.item()))
+    if dist:
+        dist.barrier()
 
     total_ms = sum(times)
     total_u = sum(uniq)
@@ -302,26 +318,23 @@ def main():
         total_ms, total_u = float(tm[0]), float(t[1])
     value = total_u / (total_ms / 1e3)
 
-    # end to end through the public API: host params in, host stats + gradient out
+    # end to end through the public API: host parameters in, host energy
+    # statistics and gradient out, around each graph replay
     h_params = torch.tensor(w["params"]).pin_memory()
     h_stats = torch.empty(4, dtype=torch.float64).pin_memory()
     h_grad = torch.empty(model.n_params, dtype=torch.float32).pin_memory()
     e2e_ms, e2e_u = 0.0, 0
-    for i in range(max(3, args.steps // 2)):
+    for i in range(max(3, args.steps)):
         flush.fill_(i & 0xFF)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         params.copy_(h_params, non_blocking=True)
-        if form == "bf16":
-            model.sync()
-        xx, nn = A.sample(model, ham, Ns, seed, 5000 + i)
-        er, ei, st = A.local_energy(model, ham, xx, nn, workspace=ws_e)
-        gg = A.grad(model, ham, xx, nn, er, ei, st, workspace=ws_g)
-        h_stats.copy_(st, non_blocking=True)
-        h_grad.copy_(gg, non_blocking=True)
+        graph.replay()
+        h_stats.copy_(stats, non_blocking=True)
+        h_grad.copy_(g, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
-        e2e_u += xx.numel()
+        e2e_u += int(nu.item())
     e2e_val = e2e_u / (e2e_ms / 1e3)
 
     if rank != 0:
@@ -329,15 +342,16 @@ def main():
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel family
+    # roofline of the dominant kernel family (eager profiled pass)
     peaks, src = _peaks()
     dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (0, 0.0))
     dname, (dl, dms) = dom
     avg_ms = dms / max(dl, 1)
     n_unq = total_u / args.steps
     K = ham.n_connected
-    work = _tc_work(A, ham, model, w, x[:uniq[-1]]) if form == "bf16" else None
-    roof = _roofline(dname, dl, avg_ms, w, K, n_unq, args.steps, peaks, src, work)
+    k_last = int(nu.item())
+    work = _tc_work(A, ham, model, w, x[:k_last]) if form == "bf16" else None
+    roof = _roofline(dname, dl, avg_ms, w, K, n_unq, n_prof, peaks, src, work)
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -349,8 +363,10 @@ def main():
             "data": "synthetic", "config": _config(w, args), "n_unique_per_step": n_unq,
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(params.numel() * 4),
                     "d2h_bytes_per_step": int(4 * 8 + model.n_params * 4 + 8)},
-            "gpu_launches": int(l1.value - l0.value),
+            "gpu_launches": launches_per_step * args.steps,
+            "launches_per_step": launches_per_step,
             "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in prof.items()},
+            "kernels_note": f"CUDA-event totals over {n_prof} eager (non-graph) steps",
             "roofline": roof, "clocks": clk.summary()}
     if cpu:
         line["cpu_baseline"] = cpu

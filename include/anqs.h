@@ -205,13 +205,15 @@ ANQS_API int anqs_logpsi(const anqs_model* model, const anqs_ham* ham, const uin
  * unique determinants in lexicographic order of (v_0, v_1, ..., v_{n-1}),
  * n_out_dev their occurrence numbers.  cap must be at least
  * min(n_samples, sector_dim) (checked on the host: ANQS_ERR_CAPACITY).
- * n_samples >= 1.
+ * n_samples >= 1.  The Philox counter word is counter + *counter_dev when
+ * counter_dev (a device uint64) is not NULL, so that a captured CUDA graph
+ * can draw fresh samples on every replay by advancing *counter_dev.
  * ------------------------------------------------------------------------- */
 ANQS_API int anqs_sample_workspace_size(const anqs_model* model, const anqs_ham* ham,
                                uint64_t n_samples, size_t* bytes);
 ANQS_API int anqs_sample(const anqs_model* model, const anqs_ham* ham, uint64_t n_samples,
-                uint64_t seed, uint64_t counter, uint64_t* x_out_dev, uint64_t* n_out_dev,
-                uint64_t cap, uint64_t* n_unique_dev, void* workspace_dev,
+                uint64_t seed, uint64_t counter, const uint64_t* counter_dev, uint64_t* x_out_dev,
+                uint64_t* n_out_dev, uint64_t cap, uint64_t* n_unique_dev, void* workspace_dev,
                 size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
@@ -223,12 +225,17 @@ ANQS_API int anqs_sample(const anqs_model* model, const anqs_ham* ham, uint64_t 
  *   (Re E, Im E, Var, S) with S = sum_l n_l, E = sum_l n_l eloc_l / S,
  *   Var = sum_l n_l |eloc_l - E|^2 / S.
  * n_x >= 1.  Workspace from anqs_local_energy_workspace_size(n_x).
+ * Row count on the device: when n_x_dev is not NULL, only the first *n_x_dev
+ * rows (read on the device, at most n_x) are processed and n_x is the
+ * capacity that sizes launches and the workspace; e.g. pass the sampler's
+ * n_unique_dev so that sampling, local energy and gradient can be captured
+ * in one CUDA graph.  Outputs beyond *n_x_dev are left untouched.
  * ------------------------------------------------------------------------- */
 ANQS_API int anqs_local_energy_workspace_size(const anqs_model* model, const anqs_ham* ham,
                                      uint64_t n_x, size_t* bytes);
 ANQS_API int anqs_local_energy(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev,
-                      const uint64_t* counts_dev, uint64_t n_x, double* eloc_re_dev,
-                      double* eloc_im_dev, double* stats_dev, void* workspace_dev,
+                      const uint64_t* counts_dev, uint64_t n_x, const uint64_t* n_x_dev,
+                      double* eloc_re_dev, double* eloc_im_dev, double* stats_dev, void* workspace_dev,
                       size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
@@ -238,15 +245,16 @@ ANQS_API int anqs_local_energy(const anqs_model* model, const anqs_ham* ham, con
  * weighted by n_l / S and eloc held fixed:
  *   grad = sum_l (n_l/S) 2 [ Re(eloc_l - E) d log|psi(x_l)| + Im(eloc_l - E) d arg psi(x_l) ]
  * with E = stats[0] + i stats[1] and S = stats[3] (as written by
- * anqs_local_energy).  grad_dev: n_params floats, overwritten.
+ * anqs_local_energy).  grad_dev: n_params floats, overwritten.  n_x_dev as
+ * for anqs_local_energy.
  * Hand-written adjoint of the masked log psi (MLP and transformer).
  * ------------------------------------------------------------------------- */
 ANQS_API int anqs_grad_workspace_size(const anqs_model* model, const anqs_ham* ham, uint64_t n_x,
                              size_t* bytes);
 ANQS_API int anqs_grad(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev,
-              const uint64_t* counts_dev, uint64_t n_x, const double* eloc_re_dev,
-              const double* eloc_im_dev, const double* stats_dev, float* grad_dev,
-              void* workspace_dev, size_t workspace_bytes, void* stream);
+              const uint64_t* counts_dev, uint64_t n_x, const uint64_t* n_x_dev,
+              const double* eloc_re_dev, const double* eloc_im_dev, const double* stats_dev,
+              float* grad_dev, void* workspace_dev, size_t workspace_bytes, void* stream);
 
 /* Adjoint of the masked log psi (vector-Jacobian product): grad_dev
  * (n_params floats, overwritten) = d/dtheta sum_l [cot_abs_dev[l] log|psi(x_l)|

@@ -193,11 +193,15 @@ def sample_workspace_bytes(model: Model, ham: Hamiltonian, n_samples: int) -> in
     return b.value
 
 
-def sample_into(model, ham, n_samples, seed, counter, x_out, n_out, n_unique, workspace, stream=None):
-    """Asynchronous sampling into preallocated device buffers (no host sync)."""
+def sample_into(model, ham, n_samples, seed, counter, x_out, n_out, n_unique, workspace, stream=None,
+                counter_dev=None):
+    """Asynchronous sampling into preallocated device buffers (no host sync).
+    With counter_dev (a 1-element int64 CUDA tensor) the Philox counter is
+    counter + counter_dev[0], read on the device."""
     check(_lib.load().anqs_sample(model._m, ham.handle, int(n_samples), int(seed) & (2**64 - 1),
-                                  int(counter) & (2**64 - 1), x_out.data_ptr(), n_out.data_ptr(), x_out.numel(),
-                                  n_unique.data_ptr(), workspace.data_ptr(), workspace.numel(), _stream(stream)))
+                                  int(counter) & (2**64 - 1), _ptr(counter_dev), x_out.data_ptr(), n_out.data_ptr(),
+                                  x_out.numel(), n_unique.data_ptr(), workspace.data_ptr(), workspace.numel(),
+                                  _stream(stream)))
 
 
 def sample(model: Model, ham: Hamiltonian, n_samples: int, seed: int, counter: int = 0, stream=None):
@@ -220,31 +224,43 @@ def local_energy_workspace_bytes(model, ham, n_x) -> int:
 
 
 def local_energy(model: Model, ham: Hamiltonian, x: torch.Tensor, counts: torch.Tensor | None = None,
-                 workspace: torch.Tensor | None = None, stream=None):
-    """(eloc_re f64, eloc_im f64, stats f64[4] or None)."""
+                 workspace: torch.Tensor | None = None, stream=None, n_dev: torch.Tensor | None = None,
+                 out=None):
+    """(eloc_re f64, eloc_im f64, stats f64[4] or None).  With n_dev (a
+    1-element int64 CUDA tensor) only the first n_dev[0] rows are used."""
     x = _u64(x)
     n_x = x.numel()
-    ere = torch.empty(n_x, dtype=torch.float64, device=x.device)
-    eim = torch.empty_like(ere)
-    stats = torch.empty(4, dtype=torch.float64, device=x.device) if counts is not None else None
+    if out is None:
+        ere = torch.empty(n_x, dtype=torch.float64, device=x.device)
+        eim = torch.empty_like(ere)
+        stats = torch.empty(4, dtype=torch.float64, device=x.device) if counts is not None else None
+    else:
+        ere, eim, stats = out
     if workspace is None:
         workspace = _ws(local_energy_workspace_bytes(model, ham, n_x), x.device)
     cnt = _u64(counts) if counts is not None else None
-    check(_lib.load().anqs_local_energy(model._m, ham.handle, x.data_ptr(), _ptr(cnt), n_x, ere.data_ptr(),
-                                        eim.data_ptr(), _ptr(stats), workspace.data_ptr(), workspace.numel(),
-                                        _stream(stream)))
+    check(_lib.load().anqs_local_energy(model._m, ham.handle, x.data_ptr(), _ptr(cnt), n_x, _ptr(n_dev),
+                                        ere.data_ptr(), eim.data_ptr(), _ptr(stats), workspace.data_ptr(),
+                                        workspace.numel(), _stream(stream)))
     return ere, eim, stats
 
 
-def grad(model: Model, ham: Hamiltonian, x, counts, eloc_re, eloc_im, stats, workspace=None, stream=None):
+def grad_workspace_bytes(model, ham, n_x) -> int:
+    b = C.c_size_t()
+    check(_lib.load().anqs_grad_workspace_size(model._m, ham.handle, n_x, C.byref(b)))
+    return b.value
+
+
+def grad(model: Model, ham: Hamiltonian, x, counts, eloc_re, eloc_im, stats, workspace=None, stream=None,
+         n_dev=None, out=None):
     """VMC gradient (float32, flat parameter layout)."""
     x, counts = _u64(x), _u64(counts)
-    g = torch.empty(model.n_params, dtype=torch.float32, device=x.device)
+    g = out if out is not None else torch.empty(model.n_params, dtype=torch.float32, device=x.device)
     if workspace is None:
         b = C.c_size_t()
         check(_lib.load().anqs_grad_workspace_size(model._m, ham.handle, x.numel(), C.byref(b)))
         workspace = _ws(b.value, x.device)
-    check(_lib.load().anqs_grad(model._m, ham.handle, x.data_ptr(), counts.data_ptr(), x.numel(),
+    check(_lib.load().anqs_grad(model._m, ham.handle, x.data_ptr(), counts.data_ptr(), x.numel(), _ptr(n_dev),
                                 eloc_re.data_ptr(), eloc_im.data_ptr(), stats.data_ptr(), g.data_ptr(),
                                 workspace.data_ptr(), workspace.numel(), _stream(stream)))
     return g

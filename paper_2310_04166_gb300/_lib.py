@@ -45,11 +45,11 @@ SIGNATURES = {
     "anqs_logpsi": (C.c_int, [_VP, _VP, _VP, _U64, _VP, _VP, _VP]),
     "anqs_logpsi_vjp": (C.c_int, [_VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
     "anqs_sample_workspace_size": (C.c_int, [_VP, _VP, _U64, C.POINTER(_SZ)]),
-    "anqs_sample": (C.c_int, [_VP, _VP, _U64, _U64, _U64, _VP, _VP, _U64, _VP, _VP, _SZ, _VP]),
+    "anqs_sample": (C.c_int, [_VP, _VP, _U64, _U64, _U64, _VP, _VP, _VP, _U64, _VP, _VP, _SZ, _VP]),
     "anqs_local_energy_workspace_size": (C.c_int, [_VP, _VP, _U64, C.POINTER(_SZ)]),
-    "anqs_local_energy": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "anqs_local_energy": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "anqs_grad_workspace_size": (C.c_int, [_VP, _VP, _U64, C.POINTER(_SZ)]),
-    "anqs_grad": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "anqs_grad": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "anqs_local_energy_static": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
     "anqs_launch_count": (C.c_int, [C.POINTER(_U64)]),
     "anqs_profile_enable": (C.c_int, [C.c_int]),

@@ -86,11 +86,14 @@ static int check_stream_device(int device) {
 }  // namespace anqs
 
 namespace anqs {
-int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, float* la,
+int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, float* la,
                     float* ph, cudaStream_t s) {
   switch (M->d.kind) {
     case ANQS_MODEL_MLP:
-      if (M->d.form == ANQS_FORM_BF16) return launch_mlp_tc_logpsi(M, H->v, x, n_x, la, ph, s);
+      if (M->d.form == ANQS_FORM_BF16) {
+        if (n_x.dev) return set_error(ANQS_ERR_UNSUPPORTED, "BF16 log psi takes host row counts");
+        return launch_mlp_tc_logpsi(M, H->v, x, n_x.n, la, ph, s);
+      }
       return launch_mlp_fp32_logpsi(M->mlp, H->v, x, n_x, la, ph, s);
     case ANQS_MODEL_TABLE:
       return launch_table_logpsi(M, H->v, x, n_x, la, ph, s);
@@ -117,7 +120,7 @@ static size_t eloc_plain_ws(const anqs_ham* H, uint64_t n_x, Arena& A, uint64_t*
 }  // namespace anqs
 
 namespace anqs {
-static int vjp_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, const float* cl,
+static int vjp_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, const float* cl,
                         const float* cp, float* grad, cudaStream_t s) {
   if (M->d.kind == ANQS_MODEL_MLP) return launch_mlp_fp32_grad(M->mlp, H->v, x, n_x, cl, cp, grad, s);
   return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not available in this build", M->d.kind);
@@ -246,7 +249,7 @@ int anqs_connected(const anqs_ham* H, const uint64_t* x, uint64_t n_x, uint64_t*
   if (n_x == 0) return ANQS_OK;
   if (!x || !xp || !hval) return set_error(ANQS_ERR_ARG, "null array argument");
   ANQS_TRY(check_stream_device(H->device));
-  return launch_connected(H->v, x, n_x, xp, hval, first_slot, hdiag, (cudaStream_t)stream);
+  return launch_connected(H->v, x, host_count(n_x), xp, hval, first_slot, hdiag, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -386,7 +389,7 @@ int anqs_logpsi(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint6
   ANQS_TRY(check_pair(M, H));
   if (n_x == 0) return ANQS_OK;
   if (!x || !la || !ph) return set_error(ANQS_ERR_ARG, "null array argument");
-  return logpsi_dispatch(M, H, x, n_x, la, ph, (cudaStream_t)stream);
+  return logpsi_dispatch(M, H, x, host_count(n_x), la, ph, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------
@@ -401,8 +404,8 @@ int anqs_sample_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t 
 }
 
 int anqs_sample(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint64_t seed,
-                uint64_t counter, uint64_t* x_out, uint64_t* n_out, uint64_t cap, uint64_t* n_unique,
-                void* ws, size_t ws_bytes, void* stream) {
+                uint64_t counter, const uint64_t* counter_dev, uint64_t* x_out, uint64_t* n_out, uint64_t cap,
+                uint64_t* n_unique, void* ws, size_t ws_bytes, void* stream) {
   ANQS_TRY(check_pair(M, H));
   if (n_samples == 0) return set_error(ANQS_ERR_ARG, "n_samples must be >= 1");
   if (!x_out || !n_out || !n_unique) return set_error(ANQS_ERR_ARG, "null output");
@@ -413,7 +416,7 @@ int anqs_sample(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
   size_t wsn = sampler_workspace(H, n_samples);
   if (ws_bytes < wsn || (wsn && !ws))
     return set_error(ANQS_ERR_CAPACITY, "sampler workspace needs %zu bytes", wsn);
-  return run_sampler(M, H, n_samples, seed, counter, x_out, n_out, n_unique, ws, ws_bytes,
+  return run_sampler(M, H, n_samples, seed, counter, counter_dev, x_out, n_out, n_unique, ws, ws_bytes,
                      (cudaStream_t)stream);
 }
 
@@ -441,17 +444,18 @@ int anqs_local_energy_workspace_size(const anqs_model* M, const anqs_ham* H, uin
 }
 
 int anqs_local_energy(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const uint64_t* counts,
-                      uint64_t n_x, double* ere, double* eim, double* stats, void* ws, size_t ws_bytes,
-                      void* stream) {
+                      uint64_t n_x, const uint64_t* n_x_dev, double* ere, double* eim, double* stats, void* ws,
+                      size_t ws_bytes, void* stream) {
   ANQS_TRY(check_pair(M, H));
   if (n_x == 0) return set_error(ANQS_ERR_ARG, "n_x must be >= 1");
   if (!x || !ere || !eim) return set_error(ANQS_ERR_ARG, "null array argument");
   if (counts && !stats) return set_error(ANQS_ERR_ARG, "counts given without stats output");
   cudaStream_t s = (cudaStream_t)stream;
+  const Count nc{n_x, n_x_dev, 1};
   if (uses_tc_eloc(M)) {
     size_t need = eloc_tc_workspace(M, H, n_x);
     if (ws_bytes < need || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
-    ANQS_TRY(run_eloc_tc(M, H, x, n_x, ere, eim, ws, ws_bytes, s));
+    ANQS_TRY(run_eloc_tc(M, H, x, nc, ere, eim, ws, ws_bytes, s));
   } else {
     Arena A(ws, ws_bytes);
     uint64_t* xp;
@@ -459,12 +463,12 @@ int anqs_local_energy(const anqs_model* M, const anqs_ham* H, const uint64_t* x,
     float *la_x, *ph_x, *la_p, *ph_p;
     size_t need = eloc_plain_ws(H, n_x, A, &xp, &hv, &hd, &la_x, &ph_x, &la_p, &ph_p);
     if (ws_bytes < need || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
-    ANQS_TRY(launch_connected(H->v, x, n_x, xp, hv, nullptr, hd, s));
-    ANQS_TRY(logpsi_dispatch(M, H, x, n_x, la_x, ph_x, s));
-    ANQS_TRY(logpsi_dispatch(M, H, xp, n_x * H->v.K, la_p, ph_p, s));
-    ANQS_TRY(launch_eloc_sum(H->v, n_x, hv, hd, la_x, ph_x, la_p, ph_p, ere, eim, s));
+    ANQS_TRY(launch_connected(H->v, x, nc, xp, hv, nullptr, hd, s));
+    ANQS_TRY(logpsi_dispatch(M, H, x, nc, la_x, ph_x, s));
+    ANQS_TRY(logpsi_dispatch(M, H, xp, scaled(nc, H->v.K), la_p, ph_p, s));
+    ANQS_TRY(launch_eloc_sum(H->v, nc, hv, hd, la_x, ph_x, la_p, ph_p, ere, eim, s));
   }
-  if (counts) ANQS_TRY(launch_stats(ere, eim, counts, n_x, stats, s));
+  if (counts) ANQS_TRY(launch_stats(ere, eim, counts, nc, stats, s));
   return ANQS_OK;
 }
 
@@ -483,8 +487,8 @@ int anqs_grad_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_
 }
 
 int anqs_grad(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const uint64_t* counts, uint64_t n_x,
-              const double* ere, const double* eim, const double* stats, float* grad, void* ws,
-              size_t ws_bytes, void* stream) {
+              const uint64_t* n_x_dev, const double* ere, const double* eim, const double* stats, float* grad,
+              void* ws, size_t ws_bytes, void* stream) {
   ANQS_TRY(check_pair(M, H));
   if (n_x == 0) return set_error(ANQS_ERR_ARG, "n_x must be >= 1");
   if (!x || !counts || !ere || !eim || !stats || !grad) return set_error(ANQS_ERR_ARG, "null array argument");
@@ -494,8 +498,9 @@ int anqs_grad(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const u
   if (!A.fits() || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", A.off);
   cudaStream_t s = (cudaStream_t)stream;
   ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));
-  ANQS_TRY(launch_grad_cotangents(ere, eim, counts, stats, n_x, cl, cp, s));
-  return vjp_dispatch(M, H, x, n_x, cl, cp, grad, s);
+  const Count nc{n_x, n_x_dev, 1};
+  ANQS_TRY(launch_grad_cotangents(ere, eim, counts, stats, nc, cl, cp, s));
+  return vjp_dispatch(M, H, x, nc, cl, cp, grad, s);
 }
 
 int anqs_logpsi_vjp(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, const float* cl,
@@ -506,7 +511,7 @@ int anqs_logpsi_vjp(const anqs_model* M, const anqs_ham* H, const uint64_t* x, u
   ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));
   if (n_x == 0) return ANQS_OK;
   if (!x || !cl || !cp) return set_error(ANQS_ERR_ARG, "null array argument");
-  return vjp_dispatch(M, H, x, n_x, cl, cp, grad, s);
+  return vjp_dispatch(M, H, x, host_count(n_x), cl, cp, grad, s);
 }
 
 }  // extern "C"

@@ -69,6 +69,21 @@ struct ProfScope {
     if (r_ != ANQS_OK) return r_; \
   } while (0)
 
+// Number of rows of a call: a host value, or (when dev is set) a value that
+// lives on the device (times mult), so that calls can be captured in a CUDA
+// graph without knowing e.g. the number of unique samples on the host.  n
+// always bounds the device value and sizes grids and workspaces.
+struct Count {
+  uint64_t n;
+  const uint64_t* dev;
+  uint64_t mult;
+#ifdef __CUDACC__
+  __device__ __forceinline__ uint64_t get() const { return dev ? *dev * mult : n; }
+#endif
+};
+inline Count host_count(uint64_t n) { return Count{n, nullptr, 1}; }
+inline Count scaled(const Count& c, uint64_t k) { return Count{c.n * k, c.dev, c.mult * k}; }
+
 // Hamiltonian as seen by the kernels (passed by value).
 struct HamView {
   int n, na, nb;
@@ -152,40 +167,40 @@ struct anqs_model {
 namespace anqs {
 
 // connect.cu
-int launch_connected(const HamView& hv, const uint64_t* x, uint64_t n_x, uint64_t* xp, double* hval,
+int launch_connected(const HamView& hv, const uint64_t* x, Count n_x, uint64_t* xp, double* hval,
                      uint8_t* first_slot, double* hdiag, cudaStream_t s);
 
 // mlp_fp32.cu
-int launch_mlp_fp32_logpsi(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x,
+int launch_mlp_fp32_logpsi(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x,
                            float* la, float* ph, cudaStream_t s);
 int launch_mlp_fp32_slot_logits(const MlpView& m, int p, const uint64_t* prefixes,
                                 const uint64_t* n_rows_dev, uint64_t max_rows, float* out8,
                                 cudaStream_t s);
-int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x,
+int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x,
                          const float* cot_la, const float* cot_ph, float* grad, cudaStream_t s);
 
 // table.cu
-int launch_table_logpsi(const anqs_model* md, const HamView& hv, const uint64_t* x, uint64_t n_x,
+int launch_table_logpsi(const anqs_model* md, const HamView& hv, const uint64_t* x, Count n_x,
                         float* la, float* ph, cudaStream_t s);
 int launch_table_slot_logits(const anqs_model* md, int p, const uint64_t* prefixes,
                              const uint64_t* n_rows_dev, uint64_t max_rows, float* out8,
                              cudaStream_t s);
 
 // eloc.cu
-int launch_eloc_sum(const HamView& hv, uint64_t n_x, const double* hval, const double* hdiag,
+int launch_eloc_sum(const HamView& hv, Count n_x, const double* hval, const double* hdiag,
                     const float* la_x, const float* ph_x, const float* la_p, const float* ph_p,
                     double* ere, double* eim, cudaStream_t s);
-int launch_stats(const double* ere, const double* eim, const uint64_t* counts, uint64_t n_x,
+int launch_stats(const double* ere, const double* eim, const uint64_t* counts, Count n_x,
                  double* stats, cudaStream_t s);
 int launch_grad_cotangents(const double* ere, const double* eim, const uint64_t* counts,
-                           const double* stats, uint64_t n_x, float* cot_la, float* cot_ph,
+                           const double* stats, Count n_x, float* cot_la, float* cot_ph,
                            cudaStream_t s);
 
 // mlp_tc.cu (BF16 tensor-core form)
 int mlp_tc_pack_alloc(anqs_model* m);
 int mlp_tc_pack(anqs_model* m, cudaStream_t s);
 size_t eloc_tc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x);
-int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, double* ere,
+int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere,
                 double* eim, void* ws, size_t ws_bytes, cudaStream_t s);
 int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la,
                          float* ph, cudaStream_t s);
@@ -194,13 +209,13 @@ int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, con
 int mlp_tc_status(const anqs_model* M, int* status);
 
 // api.cu
-int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, float* la,
+int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, float* la,
                     float* ph, cudaStream_t s);
 
 // sampler.cu
 size_t sampler_workspace(const anqs_ham* ham, uint64_t n_samples);
 int run_sampler(const anqs_model* md, const anqs_ham* ham, uint64_t n_samples, uint64_t seed,
-                uint64_t counter, uint64_t* x_out, uint64_t* n_out, uint64_t* n_unique, void* ws,
-                size_t ws_bytes, cudaStream_t s);
+                uint64_t counter, const uint64_t* counter_dev, uint64_t* x_out, uint64_t* n_out,
+                uint64_t* n_unique, void* ws, size_t ws_bytes, cudaStream_t s);
 
 }  // namespace anqs

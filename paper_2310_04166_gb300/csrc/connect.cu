@@ -68,11 +68,11 @@ __device__ double diagonal_element(const HamView& hv, uint32_t oa, uint32_t ob) 
   return e + 0.5 * (c - xch);
 }
 
-__global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, uint64_t n_x,
+__global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x,
                                  uint64_t* __restrict__ xp_out, double* __restrict__ h_out,
                                  uint8_t* __restrict__ j_out) {
   const uint64_t K = hv.K;
-  const uint64_t total = n_x * K;
+  const uint64_t total = n_x.get() * K;
   const int n = hv.n;
   for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < total;
        t += uint64_t(gridDim.x) * blockDim.x) {
@@ -177,9 +177,10 @@ __global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, ui
   }
 }
 
-__global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, uint64_t n_x,
+__global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x_,
                                 double* __restrict__ hdiag) {
   const int n = hv.n;
+  const uint64_t n_x = n_x_.get();
   for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x;
        l += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t x = __ldg(xs + l);
@@ -191,10 +192,10 @@ __global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, uin
 
 }  // namespace
 
-int launch_connected(const HamView& hv, const uint64_t* x, uint64_t n_x, uint64_t* xp, double* hval,
+int launch_connected(const HamView& hv, const uint64_t* x, Count n_x, uint64_t* xp, double* hval,
                      uint8_t* first_slot, double* hdiag, cudaStream_t s) {
   const int threads = 256;
-  uint64_t total = n_x * hv.K;
+  uint64_t total = n_x.n * hv.K;
   if (total) {
     uint64_t blocks = (total + threads - 1) / threads;
     if (blocks > 152ull * 64) blocks = 152ull * 64;
@@ -203,8 +204,9 @@ int launch_connected(const HamView& hv, const uint64_t* x, uint64_t n_x, uint64_
     ANQS_LAUNCHED("connected_kernel");
   }
   if (hdiag) {
-    uint64_t blocks = (n_x + threads - 1) / threads;
+    uint64_t blocks = (n_x.n + threads - 1) / threads;
     if (blocks > 152ull * 16) blocks = 152ull * 16;
+    if (blocks == 0) blocks = 1;
     ProfScope ps(PROF_DIAGONAL, s);
     diagonal_kernel<<<unsigned(blocks), threads, 0, s>>>(hv, x, n_x, hdiag);
     ANQS_LAUNCHED("diagonal_kernel");

@@ -15,12 +15,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // one warp per determinant: eloc = H_xx + sum_k H_k exp(dlog|psi| + i dphase)
-__global__ void eloc_sum_kernel(uint32_t K, uint64_t n_x, const double* __restrict__ hval,
+__global__ void eloc_sum_kernel(uint32_t K, Count n_x_, const double* __restrict__ hval,
                                 const double* __restrict__ hdiag, const float* __restrict__ la_x,
                                 const float* __restrict__ ph_x, const float* __restrict__ la_p,
                                 const float* __restrict__ ph_p, double* __restrict__ ere,
                                 double* __restrict__ eim) {
   const int lane = threadIdx.x & 31;
+  const uint64_t n_x = n_x_.get();
   const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
   for (uint64_t l = blockIdx.x * uint64_t(blockDim.x >> 5) + (threadIdx.x >> 5); l < n_x; l += warps) {
     const double lx = la_x[l], px = ph_x[l];
@@ -61,8 +62,9 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 
 // single CTA: S, E (complex) then Var in a second pass
 __global__ void stats_kernel(const double* __restrict__ ere, const double* __restrict__ eim,
-                             const uint64_t* __restrict__ counts, uint64_t n_x, double* __restrict__ stats) {
+                             const uint64_t* __restrict__ counts, Count n_x_, double* __restrict__ stats) {
   __shared__ double red[32];
+  const uint64_t n_x = n_x_.get();
   double s = 0.0, sr = 0.0, si = 0.0;
   for (uint64_t l = threadIdx.x; l < n_x; l += blockDim.x) {
     double w = double(counts[l]);
@@ -92,8 +94,9 @@ __global__ void stats_kernel(const double* __restrict__ ere, const double* __res
 // cot_la = 2 w Re(eloc - E), cot_ph = 2 w Im(eloc - E), w = n / S
 __global__ void cotangent_kernel(const double* __restrict__ ere, const double* __restrict__ eim,
                                  const uint64_t* __restrict__ counts, const double* __restrict__ stats,
-                                 uint64_t n_x, float* __restrict__ cl, float* __restrict__ cp) {
+                                 Count n_x_, float* __restrict__ cl, float* __restrict__ cp) {
   const double Er = stats[0], Ei = stats[1], S = stats[3];
+  const uint64_t n_x = n_x_.get();
   for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x; l += uint64_t(gridDim.x) * blockDim.x) {
     double w = double(counts[l]) / S;
     cl[l] = float(2.0 * w * (ere[l] - Er));
@@ -103,10 +106,11 @@ __global__ void cotangent_kernel(const double* __restrict__ ere, const double* _
 
 }  // namespace
 
-int launch_eloc_sum(const HamView& hv, uint64_t n_x, const double* hval, const double* hdiag, const float* la_x,
+int launch_eloc_sum(const HamView& hv, Count n_x, const double* hval, const double* hdiag, const float* la_x,
                     const float* ph_x, const float* la_p, const float* ph_p, double* ere, double* eim,
                     cudaStream_t s) {
-  uint64_t blocks = (n_x + 7) / 8;  // 8 warps per CTA
+  uint64_t blocks = (n_x.n + 7) / 8;  // 8 warps per CTA
+  if (blocks == 0) blocks = 1;
   if (blocks > 152 * 16) blocks = 152 * 16;
   ProfScope ps(PROF_ELOC_SUM, s);
   eloc_sum_kernel<<<unsigned(blocks), 256, 0, s>>>(hv.K, n_x, hval, hdiag, la_x, ph_x, la_p, ph_p, ere, eim);
@@ -114,7 +118,7 @@ int launch_eloc_sum(const HamView& hv, uint64_t n_x, const double* hval, const d
   return ANQS_OK;
 }
 
-int launch_stats(const double* ere, const double* eim, const uint64_t* counts, uint64_t n_x, double* stats,
+int launch_stats(const double* ere, const double* eim, const uint64_t* counts, Count n_x, double* stats,
                  cudaStream_t s) {
   ProfScope ps(PROF_STATS, s);
   stats_kernel<<<1, 1024, 0, s>>>(ere, eim, counts, n_x, stats);
@@ -123,8 +127,9 @@ int launch_stats(const double* ere, const double* eim, const uint64_t* counts, u
 }
 
 int launch_grad_cotangents(const double* ere, const double* eim, const uint64_t* counts, const double* stats,
-                           uint64_t n_x, float* cl, float* cp, cudaStream_t s) {
-  uint64_t blocks = (n_x + 255) / 256;
+                           Count n_x, float* cl, float* cp, cudaStream_t s) {
+  uint64_t blocks = (n_x.n + 255) / 256;
+  if (blocks == 0) blocks = 1;
   if (blocks > 152 * 8) blocks = 152 * 8;
   ProfScope ps(PROF_COTANGENT, s);
   cotangent_kernel<<<unsigned(blocks), 256, 0, s>>>(ere, eim, counts, stats, n_x, cl, cp);

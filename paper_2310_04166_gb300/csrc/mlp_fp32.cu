@@ -11,6 +11,7 @@
 //
 // A CTA of 256 threads owns a tile of R = 32 rows; activations stay in
 // shared memory, weights stream through a padded shared-memory chunk.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -160,8 +161,9 @@ __device__ __forceinline__ void slot_term(const float* o8, unsigned mask, int v,
 
 template <int W>
 __global__ void __launch_bounds__(NT) logpsi_kernel(MlpView m, HamView hv, const uint64_t* __restrict__ xs,
-                                                    uint64_t n_x, float* __restrict__ la_out,
+                                                    Count n_x_, float* __restrict__ la_out,
                                                     float* __restrict__ ph_out) {
+  const uint64_t n_x = n_x_.get();
   extern __shared__ float smem[];
   float* act = smem;
   float* ws = act + 2 * R * W;
@@ -232,7 +234,7 @@ __global__ void __launch_bounds__(NT) slot_logits_kernel(MlpView m, int p, const
 // the tile are added to grad with atomics.
 template <int W>
 __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const uint64_t* __restrict__ xs,
-                                                  uint64_t n_x, const float* __restrict__ cot_la,
+                                                  Count n_x_, const float* __restrict__ cot_la,
                                                   const float* __restrict__ cot_ph, float* __restrict__ grad) {
   extern __shared__ float smem[];
   const int L = m.n_hidden;
@@ -243,6 +245,7 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
   __shared__ uint64_t xt[R];
   __shared__ float cl[R], cp[R];
   const int p = blockIdx.y;
+  const uint64_t n_x = n_x_.get();
   const uint64_t base = uint64_t(blockIdx.x) * R;
   if (base >= n_x) return;
   const int nrows = int(n_x - base < uint64_t(R) ? n_x - base : uint64_t(R));
@@ -372,12 +375,12 @@ int set_smem(F* f, size_t bytes) {
 unsigned grid_for(uint64_t tiles, unsigned cap) { return unsigned(tiles < cap ? (tiles ? tiles : 1) : cap); }
 
 template <int W>
-int logpsi_w(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la, float* ph,
+int logpsi_w(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, float* la, float* ph,
              cudaStream_t s) {
   size_t sm = Smem<W>::bytes(2);
   ANQS_TRY(set_smem(logpsi_kernel<W>, sm));
   ProfScope ps(PROF_MLP_FP32_LOGPSI, s);
-  logpsi_kernel<W><<<grid_for((n_x + R - 1) / R, 152 * 8), NT, sm, s>>>(m, hv, x, n_x, la, ph);
+  logpsi_kernel<W><<<grid_for((n_x.n + R - 1) / R, 152 * 8), NT, sm, s>>>(m, hv, x, n_x, la, ph);
   ANQS_LAUNCHED("mlp logpsi_kernel");
   return ANQS_OK;
 }
@@ -394,13 +397,13 @@ int logits_w(const MlpView& m, int p, const uint64_t* pre, const uint64_t* nr, u
 }
 
 template <int W>
-int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x, const float* cl,
+int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
            const float* cp, float* g, cudaStream_t s) {
   size_t sm = Smem<W>::bytes(m.n_hidden + 1);
   if (sm > 227 * 1024)
     return set_error(ANQS_ERR_UNSUPPORTED, "FP32 MLP adjoint needs %zu bytes of shared memory", sm);
   ANQS_TRY(set_smem(grad_kernel<W>, sm));
-  dim3 grid(unsigned((n_x + R - 1) / R), unsigned(m.n));
+  dim3 grid(unsigned(std::max<uint64_t>((n_x.n + R - 1) / R, 1)), unsigned(m.n));
   ProfScope ps(PROF_MLP_FP32_GRAD, s);
   grad_kernel<W><<<grid, NT, sm, s>>>(m, hv, x, n_x, cl, cp, g);
   ANQS_LAUNCHED("mlp grad_kernel");
@@ -409,7 +412,7 @@ int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x,
 
 }  // namespace
 
-int launch_mlp_fp32_logpsi(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la,
+int launch_mlp_fp32_logpsi(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, float* la,
                            float* ph, cudaStream_t s) {
   switch (m.width) {
     case 64: return logpsi_w<64>(m, hv, x, n_x, la, ph, s);
@@ -429,9 +432,9 @@ int launch_mlp_fp32_slot_logits(const MlpView& m, int p, const uint64_t* pre, co
   return set_error(ANQS_ERR_UNSUPPORTED, "width %d", m.width);
 }
 
-int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, uint64_t n_x, const float* cl,
+int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
                          const float* cp, float* g, cudaStream_t s) {
-  if ((n_x + R - 1) / R > 0x7fffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "too many rows");
+  if ((n_x.n + R - 1) / R > 0x7fffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "too many rows");
   switch (m.width) {
     case 64: return grad_w<64>(m, hv, x, n_x, cl, cp, g, s);
     case 128: return grad_w<128>(m, hv, x, n_x, cl, cp, g, s);

@@ -126,9 +126,8 @@ __device__ __forceinline__ bool wait_bar(uint32_t bar, uint32_t phase) {
 }
 
 struct TileArgs {
-  const uint64_t* x;           // SLOTS: rows x[0..n_rows); SUFFIX: connected determinants
-  const uint64_t* n_rows_dev;  // SLOTS: device-side row count (or null: n_rows)
-  uint64_t n_rows;
+  const uint64_t* x;           // SLOTS: rows x[0..rows); SUFFIX: connected determinants
+  Count rows;
   int p_lo, p_hi;              // SLOTS: slots [p_lo, p_hi)
   float* raw;                  // SLOTS output [row][p_hi - p_lo][8]
   // SUFFIX
@@ -325,7 +324,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
   c.t = t;
   const uint32_t bar_w = tc::smem_u32(&bars[0]);
   uint32_t ph_w = 0, ph_m = 0;
-  const uint64_t n_rows = ta.n_rows_dev ? *ta.n_rows_dev : ta.n_rows;
+  const uint64_t n_rows = ta.rows.get();
   const uint64_t n_pairs = (n_rows + 2 * MT - 1) / (2 * MT);
   const int np = ta.p_hi - ta.p_lo;
   const uint64_t n_items = n_pairs * uint64_t(np);
@@ -380,7 +379,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_suffix_kernel(TcView tv, HamView
   c.wg = wg;
   c.t = t;
   uint32_t ph_w[2] = {0, 0}, ph_m = 0;
-  const uint64_t n_rows = ta.n_rows;
+  const uint64_t n_rows = ta.rows.get();
   const uint64_t n_tiles = (n_rows + MT - 1) / MT;
   const uint64_t G = gridDim.x;
   for (uint64_t chunk = 0;; ++chunk) {
@@ -477,10 +476,11 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_suffix_kernel(TcView tv, HamView
 
 // Per row: masked half-log-probabilities from the raw slot outputs, prefix
 // sums and log psi (and the parent cache when requested).
-__global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, uint64_t n_x,
+__global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x_,
                                 const float* __restrict__ raw, float* __restrict__ la_out, float* __restrict__ ph_out,
                                 float* __restrict__ cache) {
   const int n = hv.n;
+  const uint64_t n_x = n_x_.get();
   for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x; l += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t x = xs[l];
     float la = 0.f, ph = 0.f;
@@ -518,8 +518,9 @@ __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, uin
 }
 
 // ---- sort of connected rows by first differing slot ---------------------------
-__global__ void js_hist_kernel(const uint8_t* __restrict__ js, uint64_t m, int n, uint32_t* __restrict__ hist) {
+__global__ void js_hist_kernel(const uint8_t* __restrict__ js, Count m_, int n, uint32_t* __restrict__ hist) {
   __shared__ uint32_t h[ANQS_MAX_ORB];
+  const uint64_t m = m_.get();
   for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = 0;
   __syncthreads();
   for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < m; t += uint64_t(gridDim.x) * blockDim.x)
@@ -539,8 +540,9 @@ __global__ void js_offsets_kernel(const uint32_t* __restrict__ hist, int n, uint
   }
 }
 
-__global__ void js_scatter_kernel(const uint8_t* __restrict__ js, uint64_t m, uint32_t* __restrict__ cursor,
+__global__ void js_scatter_kernel(const uint8_t* __restrict__ js, Count m_, uint32_t* __restrict__ cursor,
                                   uint32_t* __restrict__ perm) {
+  const uint64_t m = m_.get();
   for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < m; t += uint64_t(gridDim.x) * blockDim.x)
     perm[atomicAdd(&cursor[js[t]], 1u)] = uint32_t(t);
 }
@@ -578,7 +580,8 @@ TcView make_view(const anqs_model* M) {
 }
 
 template <int W>
-int launch_slots_w(const TcView& tv, const TileArgs& ta, uint64_t max_rows, cudaStream_t s) {
+int launch_slots_w(const TcView& tv, const TileArgs& ta, cudaStream_t s) {
+  const uint64_t max_rows = ta.rows.n;
   const size_t sm = smem_bytes(tv, 1);
   const uint64_t items = (max_rows + 2 * MT - 1) / (2 * MT) * uint64_t(ta.p_hi - ta.p_lo);
   const unsigned grid = unsigned(std::min<uint64_t>(items ? items : 1, uint64_t(num_sms())));
@@ -590,17 +593,17 @@ int launch_slots_w(const TcView& tv, const TileArgs& ta, uint64_t max_rows, cuda
   return ANQS_OK;
 }
 
-int launch_slots(const anqs_model* M, const TileArgs& ta, uint64_t max_rows, cudaStream_t s, int prof) {
+int launch_slots(const anqs_model* M, const TileArgs& ta, cudaStream_t s, int prof) {
   TcView tv = make_view(M);
   if (smem_bytes(tv, 1) > kSmemLimit) return set_error(ANQS_ERR_UNSUPPORTED, "BF16 MLP slot image too large");
   ProfScope ps(prof, s);
-  return tv.W == 128 ? launch_slots_w<128>(tv, ta, max_rows, s) : launch_slots_w<64>(tv, ta, max_rows, s);
+  return tv.W == 128 ? launch_slots_w<128>(tv, ta, s) : launch_slots_w<64>(tv, ta, s);
 }
 
 template <int W>
 int launch_suffix_w(const TcView& tv, const HamView& hv, const TileArgs& ta, cudaStream_t s) {
   const size_t sm = smem_bytes(tv, tv.nbuf);
-  const uint64_t tiles = (ta.n_rows + MT - 1) / MT;
+  const uint64_t tiles = (ta.rows.n + MT - 1) / MT;
   const unsigned grid = unsigned(std::min<uint64_t>(tiles ? tiles : 1, uint64_t(num_sms())));
   ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_suffix_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
   mlp_tc_suffix_kernel<W><<<grid, NT, sm, s>>>(tv, hv, ta);
@@ -608,9 +611,9 @@ int launch_suffix_w(const TcView& tv, const HamView& hv, const TileArgs& ta, cud
   return ANQS_OK;
 }
 
-int launch_finalize(const HamView& hv, const uint64_t* x, uint64_t n_x, const float* raw, float* la, float* ph,
+int launch_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
                     float* cache, cudaStream_t s) {
-  uint64_t blocks = (n_x + 127) / 128;
+  uint64_t blocks = (n_x.n + 127) / 128;
   if (blocks > 152 * 8) blocks = 152 * 8;
   finalize_kernel<<<unsigned(blocks ? blocks : 1), 128, 0, s>>>(hv, x, n_x, raw, la, ph, cache);
   ANQS_LAUNCHED("finalize_kernel");
@@ -697,13 +700,13 @@ int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t*
     const uint64_t k = std::min<uint64_t>(M->tc_raw_rows, n_x - off);
     TileArgs ta{};
     ta.x = x + off;
-    ta.n_rows = k;
+    ta.rows = host_count(k);
     ta.p_lo = 0;
     ta.p_hi = M->d.n_orb;
     ta.raw = M->tc_raw;
-    ANQS_TRY(launch_slots(M, ta, k, s, PROF_TC_PARENT));
+    ANQS_TRY(launch_slots(M, ta, s, PROF_TC_PARENT));
     ProfScope ps(PROF_TC_PARENT, s);
-    ANQS_TRY(launch_finalize(hv, x + off, k, M->tc_raw, la + off, ph + off, nullptr, s));
+    ANQS_TRY(launch_finalize(hv, x + off, host_count(k), M->tc_raw, la + off, ph + off, nullptr, s));
   }
   return ANQS_OK;
 }
@@ -713,11 +716,11 @@ int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, con
   (void)hv;
   TileArgs ta{};
   ta.x = pre;
-  ta.n_rows_dev = n_dev;
+  ta.rows = Count{max_rows, n_dev, 1};
   ta.p_lo = p;
   ta.p_hi = p + 1;
   ta.raw = out8;
-  return launch_slots(M, ta, max_rows, s, PROF_TC_SLOT);
+  return launch_slots(M, ta, s, PROF_TC_SLOT);
 }
 
 size_t eloc_tc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x) {
@@ -727,23 +730,25 @@ size_t eloc_tc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x) {
   return plan_eloc(H, n_x, A, w);
 }
 
-int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, double* ere, double* eim,
+int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,
                 void* ws, size_t ws_bytes, cudaStream_t s) {
   Arena A(ws, ws_bytes);
   ElocWs w;
-  plan_eloc(H, n_x, A, w);
+  plan_eloc(H, n_x.n, A, w);
   if (!A.fits()) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", A.off);
-  const uint64_t K = H->v.K, m = n_x * K;
+  const uint64_t K = H->v.K;
+  const Count mc = scaled(n_x, K);
+  const uint64_t m = mc.n;
   if (m > 0xffffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "more than 2^32 connected determinants per call");
   ANQS_TRY(launch_connected(H->v, x, n_x, w.xp, w.hv, w.js, w.hd, s));
   {
     TileArgs ta{};
     ta.x = x;
-    ta.n_rows = n_x;
+    ta.rows = n_x;
     ta.p_lo = 0;
     ta.p_hi = H->v.n;
     ta.raw = w.raw;
-    ANQS_TRY(launch_slots(M, ta, n_x, s, PROF_TC_PARENT));
+    ANQS_TRY(launch_slots(M, ta, s, PROF_TC_PARENT));
     ProfScope ps(PROF_TC_PARENT, s);
     ANQS_TRY(launch_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
   }
@@ -751,17 +756,17 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint6
     ProfScope ps(PROF_TC_SORT, s);
     ANQS_CUDA(cudaMemsetAsync(w.hist, 0, ANQS_MAX_ORB * sizeof(uint32_t), s));
     unsigned g = unsigned(std::min<uint64_t>((m + 255) / 256, 152 * 4));
-    js_hist_kernel<<<g ? g : 1, 256, 0, s>>>(w.js, m, H->v.n, w.hist);
+    js_hist_kernel<<<g ? g : 1, 256, 0, s>>>(w.js, mc, H->v.n, w.hist);
     ANQS_LAUNCHED("js_hist_kernel");
     js_offsets_kernel<<<1, 32, 0, s>>>(w.hist, H->v.n, w.cursor);
     ANQS_LAUNCHED("js_offsets_kernel");
-    js_scatter_kernel<<<g ? g : 1, 256, 0, s>>>(w.js, m, w.cursor, w.perm);
+    js_scatter_kernel<<<g ? g : 1, 256, 0, s>>>(w.js, mc, w.cursor, w.perm);
     ANQS_LAUNCHED("js_scatter_kernel");
   }
   {
     TileArgs ta{};
     ta.x = w.xp;
-    ta.n_rows = m;
+    ta.rows = mc;
     ta.perm = w.perm;
     ta.js = w.js;
     ta.cache = w.cache;

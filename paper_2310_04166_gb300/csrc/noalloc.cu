@@ -98,10 +98,11 @@ extern "C" int anqs_local_energy_static(const anqs_model* M, const anqs_ham* H, 
   float* la_p = S.take<float>(m);
   float* ph_p = S.take<float>(m);
   cudaStream_t s = (cudaStream_t)stream;
-  ANQS_TRY(launch_connected(H->v, x, n_x, xp, hv, nullptr, hd, s));
-  ANQS_TRY(logpsi_dispatch(M, H, x, n_x, la_x, ph_x, s));
-  ANQS_TRY(logpsi_dispatch(M, H, xp, m, la_p, ph_p, s));
-  ANQS_TRY(launch_eloc_sum(H->v, n_x, hv, hd, la_x, ph_x, la_p, ph_p, ere, eim, s));
-  if (counts) ANQS_TRY(launch_stats(ere, eim, counts, n_x, stats, s));
+  const Count nc = host_count(n_x);
+  ANQS_TRY(launch_connected(H->v, x, nc, xp, hv, nullptr, hd, s));
+  ANQS_TRY(logpsi_dispatch(M, H, x, nc, la_x, ph_x, s));
+  ANQS_TRY(logpsi_dispatch(M, H, xp, host_count(m), la_p, ph_p, s));
+  ANQS_TRY(launch_eloc_sum(H->v, nc, hv, hd, la_x, ph_x, la_p, ph_p, ere, eim, s));
+  if (counts) ANQS_TRY(launch_stats(ere, eim, counts, nc, stats, s));
   return ANQS_OK;
 }

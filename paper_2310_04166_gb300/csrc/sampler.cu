@@ -55,10 +55,11 @@ struct Philox {
   }
 };
 
-__global__ void init_kernel(uint64_t* pre, uint64_t* cnt, uint64_t* n_front, uint64_t n_samples) {
+__global__ void init_kernel(uint64_t* pre, uint64_t* cnt, uint64_t* n_front, uint64_t n_samples, unsigned* done) {
   pre[0] = 0;
   cnt[0] = n_samples;
   n_front[0] = 1;
+  *done = 0;
 }
 
 __device__ __forceinline__ int popc_alpha(uint64_t x, int p) {
@@ -73,7 +74,7 @@ __device__ __forceinline__ int popc_beta(uint64_t x, int p) {
 // per node: running sums of the masked conditional, draw-block counts
 __global__ void prep_kernel(HamView hv, int p, const uint64_t* __restrict__ pre, const uint64_t* __restrict__ cnt,
                             const uint64_t* __restrict__ n_front, const float* __restrict__ logits,
-                            double* __restrict__ cdf, uint8_t* __restrict__ allowed, uint64_t* __restrict__ nblk,
+                            uint64_t* __restrict__ thr, uint8_t* __restrict__ allowed, uint64_t* __restrict__ nblk,
                             uint64_t* __restrict__ child) {
   const uint64_t nf = *n_front;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < nf; i += uint64_t(gridDim.x) * blockDim.x) {
@@ -88,15 +89,24 @@ __global__ void prep_kernel(HamView hv, int p, const uint64_t* __restrict__ pre,
       e[v] = ((mk >> v) & 1u) ? exp(double(l[v]) - m) : 0.0;
       s += e[v];
     }
+    // u < C_v  <=>  (word >> 11) < ceil(C_v 2^53) exactly (u = (word >> 11) 2^-53),
+    // so the draws compare integers against these thresholds
     double run = 0.0;
     for (int v = 0; v < 4; ++v) {
       if ((mk >> v) & 1u) run += e[v] / s;
-      cdf[i * 4 + v] = run;
+      thr[i * 4 + v] = uint64_t(ceil(run * 9007199254740992.0));
       child[i * 4 + v] = 0;
     }
     allowed[i] = uint8_t(mk);
     nblk[i] = (cnt[i] + 3) / 4;
   }
+}
+
+__device__ __forceinline__ int draw_outcome(uint64_t word, const uint64_t* thr, unsigned mk, int last) {
+  const uint64_t m = word >> 11;
+  for (int v = 0; v < 4; ++v)
+    if (((mk >> v) & 1u) && m < thr[v]) return v;
+  return last;
 }
 
 // ---- exclusive scan of uint64 over a device-sized array -------------------
@@ -189,13 +199,15 @@ __global__ void scan_apply_kernel(const uint64_t* __restrict__ in, const uint64_
 }
 
 // ---- draws -----------------------------------------------------------------
-__global__ void draw_kernel(int p, uint64_t seed, uint64_t counter, const uint64_t* __restrict__ pre,
+__global__ void draw_kernel(int p, uint64_t seed, uint64_t counter0, const uint64_t* __restrict__ counter_dev,
+                            const uint64_t* __restrict__ pre,
                             const uint64_t* __restrict__ cnt, const uint64_t* __restrict__ n_front,
-                            const uint64_t* __restrict__ nblk_scan, const double* __restrict__ cdf,
+                            const uint64_t* __restrict__ nblk_scan, const uint64_t* __restrict__ thr,
                             const uint8_t* __restrict__ allowed, uint64_t* __restrict__ child,
                             uint64_t max_threads) {
   const uint64_t nf = *n_front;
   const uint64_t total = nblk_scan[nf];
+  const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
   const int lane = threadIdx.x & 31;
   for (uint64_t t0 = blockIdx.x * uint64_t(blockDim.x); t0 < max_threads; t0 += uint64_t(gridDim.x) * blockDim.x) {
     if (t0 >= total) break;
@@ -217,19 +229,13 @@ __global__ void draw_kernel(int p, uint64_t seed, uint64_t counter, const uint64
       uint64_t w[4];
       Philox::block(x, ib, uint64_t(p), counter, seed, 0ull, w);
       const unsigned mk = allowed[lo];
-      const double* C = cdf + lo * 4;
+      uint64_t T[4];
+      for (int v = 0; v < 4; ++v) T[v] = thr[lo * 4 + v];
       int last = 3;
       while (last > 0 && !((mk >> last) & 1u)) --last;
       for (int k = 0; k < 4; ++k) {
         if (ib * 4 + k >= c) break;
-        double u = double(w[k] >> 11) * 0x1.0p-53;
-        int out = last;
-        for (int v = 0; v < 4; ++v)
-          if (((mk >> v) & 1u) && u < C[v]) {
-            out = v;
-            break;
-          }
-        packed += 1u << (8 * out);
+        packed += 1u << (8 * draw_outcome(w[k], T, mk, last));
       }
     }
     // segmented sum over lanes with the same node (nodes are non-decreasing in t)
@@ -272,12 +278,149 @@ __global__ void scatter_kernel(int p, const uint64_t* __restrict__ pre, const ui
   }
 }
 
+// ---- one CTA per level for small frontiers ------------------------------------
+// Everything after the network evaluation of a level in a single CTA of
+// SMALL_T threads: per-node running sums, scan of the draw blocks, draws with
+// warp-segment aggregation into shared counters, compaction of the children.
+constexpr int SMALL_T = 1024;
+constexpr int SMALL_F = 2048;  // largest frontier handled this way
+
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* sh, uint32_t* tot) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  __syncthreads();
+  if (lane == 31) sh[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t t = lane < int(blockDim.x >> 5) ? sh[lane] : 0;
+    uint32_t ti = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t u = __shfl_up_sync(0xffffffffu, ti, o);
+      if (lane >= o) ti += u;
+    }
+    sh[lane] = ti - t;
+    if (lane == 31) sh[32] = ti;
+  }
+  __syncthreads();
+  *tot = sh[32];
+  return sh[w] + inc - v;
+}
+
+// Draws of one level for frontiers of at most SMALL_F nodes: every CTA scans
+// the per-node draw-block counts in its own shared memory, draws its share
+// with integer threshold compares and adds warp-segment sums of the outcome
+// counts to the children; the last CTA to finish compacts the children into
+// the next frontier (no CTA waits on another).
+__global__ void __launch_bounds__(SMALL_T) draw_small_kernel(int p, uint64_t seed, uint64_t counter0,
+                                                             const uint64_t* __restrict__ counter_dev,
+                                                             const uint64_t* __restrict__ pre,
+                                                             const uint64_t* __restrict__ cnt,
+                                                             const uint64_t* __restrict__ n_front,
+                                                             const uint64_t* __restrict__ nblk,
+                                                             const uint64_t* __restrict__ thr,
+                                                             const uint8_t* __restrict__ allowed,
+                                                             uint64_t* __restrict__ child, unsigned* __restrict__ done,
+                                                             uint64_t* __restrict__ pre_out,
+                                                             uint64_t* __restrict__ cnt_out,
+                                                             uint64_t* __restrict__ n_out) {
+  __shared__ uint32_t s_scan[SMALL_F + 1];
+  __shared__ uint32_t s_red[33];
+  __shared__ bool s_last;
+  const int nf = int(*n_front);
+  const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
+  const int lane = threadIdx.x & 31;
+  uint32_t carry = 0;
+  for (int base = 0; base < nf; base += SMALL_T) {
+    const int i = base + threadIdx.x;
+    const uint32_t nb = i < nf ? uint32_t(nblk[i]) : 0u;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan_u32(nb, s_red, &tot);
+    if (i < nf) s_scan[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) s_scan[nf] = carry;
+  __syncthreads();
+  const uint32_t total = carry;
+  for (uint32_t t0 = blockIdx.x * SMALL_T; t0 < total; t0 += gridDim.x * SMALL_T) {
+    const uint32_t t = t0 + threadIdx.x;
+    int node = -1;
+    uint32_t packed = 0;
+    if (t < total) {
+      int lo = 0, hi = nf - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_scan[mid] <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      node = lo;
+      const uint64_t ib = t - s_scan[lo];
+      const uint64_t c = cnt[lo];
+      uint64_t w[4];
+      Philox::block(pre[lo], ib, uint64_t(p), counter, seed, 0ull, w);
+      const unsigned mk = allowed[lo];
+      uint64_t T[4];
+      for (int v = 0; v < 4; ++v) T[v] = thr[uint64_t(lo) * 4 + v];
+      int last = 3;
+      while (last > 0 && !((mk >> last) & 1u)) --last;
+      for (int k = 0; k < 4; ++k) {
+        if (ib * 4 + k >= c) break;
+        packed += 1u << (8 * draw_outcome(w[k], T, mk, last));
+      }
+    }
+    const int prev = __shfl_up_sync(0xffffffffu, node, 1);
+    const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != node);
+    const int seg_start = 31 - __clz(heads & ((2u << lane) - 1u));
+    uint32_t v = packed;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t other = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane - o >= seg_start) v += other;
+    }
+    const bool tail = (lane == 31) || ((heads >> (lane + 1)) & 1u);
+    if (tail && node >= 0)
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t ck = (v >> (8 * k)) & 0xffu;
+        if (ck) atomicAdd(reinterpret_cast<unsigned long long*>(child + uint64_t(node) * 4 + k), (unsigned long long)ck);
+      }
+  }
+  // last CTA: compaction (the other CTAs' counts are visible after their fence)
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(done, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  carry = 0;
+  for (int base = 0; base < 4 * nf; base += SMALL_T) {
+    const int i = base + threadIdx.x;
+    const uint64_t c = i < 4 * nf ? __ldcg(child + i) : 0ull;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan_u32(c ? 1u : 0u, s_red, &tot);
+    if (c) {
+      pre_out[carry + ex] = pre[i >> 2] | (uint64_t(i & 3) << (2 * p));
+      cnt_out[carry + ex] = c;
+    }
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    *n_out = carry;
+    *done = 0;  // ready for the next level
+  }
+}
+
 struct Plan {
   uint64_t F;  // max frontier
   uint64_t *pre[2], *cnt[2], *nblk, *nblk_scan, *child, *flags, *pos, *partial, *n_front;
   float* logits;
-  double* cdf;
+  uint64_t* thr;
   uint8_t* allowed;
+  unsigned* done;
 };
 
 uint64_t level_cap(const anqs_ham* H, uint64_t n_samples, int p) {
@@ -294,7 +437,7 @@ void plan_ws(const anqs_ham* H, uint64_t n_samples, Arena& A, Plan& P) {
     P.cnt[b] = A.take<uint64_t>(F);
   }
   P.logits = A.take<float>(F * 8);
-  P.cdf = A.take<double>(F * 4);
+  P.thr = A.take<uint64_t>(F * 4);
   P.allowed = A.take<uint8_t>(F);
   P.nblk = A.take<uint64_t>(F);
   P.nblk_scan = A.take<uint64_t>(F + 1);
@@ -303,6 +446,7 @@ void plan_ws(const anqs_ham* H, uint64_t n_samples, Arena& A, Plan& P) {
   P.pos = A.take<uint64_t>(F * 4 + 1);
   P.partial = A.take<uint64_t>((F * 4 + 1) / SCAN_CHUNK + 2);
   P.n_front = A.take<uint64_t>(2);
+  P.done = A.take<unsigned>(1);
 }
 
 int scan(const uint64_t* in, const uint64_t* n_dev, uint64_t mult, uint64_t max_n, uint64_t* partial,
@@ -333,7 +477,8 @@ size_t sampler_workspace(const anqs_ham* H, uint64_t n_samples) {
 }
 
 int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint64_t seed, uint64_t counter,
-                uint64_t* x_out, uint64_t* n_out, uint64_t* n_unique, void* ws, size_t ws_bytes, cudaStream_t s) {
+                const uint64_t* counter_dev, uint64_t* x_out, uint64_t* n_out, uint64_t* n_unique, void* ws,
+                size_t ws_bytes, cudaStream_t s) {
   Arena A(ws, ws_bytes);
   Plan P;
   plan_ws(H, n_samples, A, P);
@@ -341,7 +486,7 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
   const int n = H->v.n;
   {
     ProfScope ps(PROF_SAMPLER, s);
-    init_kernel<<<1, 1, 0, s>>>(P.pre[0], P.cnt[0], P.n_front, n_samples);
+    init_kernel<<<1, 1, 0, s>>>(P.pre[0], P.cnt[0], P.n_front, n_samples, P.done);
     ANQS_LAUNCHED("sampler init_kernel");
   }
   for (int p = 0; p < n; ++p) {
@@ -350,17 +495,28 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
     uint64_t* nf = P.n_front + cur;
     ANQS_TRY(logits_dispatch(M, H, p, P.pre[cur], nf, Fp, P.logits, s));
     ProfScope ps(PROF_SAMPLER, s);
-    prep_kernel<<<blocks_for(Fp, 256, 152 * 8), 256, 0, s>>>(H->v, p, P.pre[cur], P.cnt[cur], nf, P.logits, P.cdf,
-                                                              P.allowed, P.nblk, P.child);
+    const bool last = (p == n - 1);
+    const bool small = Fp <= uint64_t(SMALL_F) && n_samples < (1ull << 31);
+    // per-node conditional in FP64, spread over many small CTAs
+    prep_kernel<<<blocks_for(Fp, small ? 32 : 256, 152 * 8), small ? 32 : 256, 0, s>>>(
+        H->v, p, P.pre[cur], P.cnt[cur], nf, P.logits, P.thr, P.allowed, P.nblk, P.child);
     ANQS_LAUNCHED("sampler prep_kernel");
+    if (small) {
+      const uint64_t blocks = ((n_samples + 3) / 4 + Fp + SMALL_T - 1) / SMALL_T;
+      draw_small_kernel<<<blocks_for(blocks, 1, 152), SMALL_T, 0, s>>>(
+          p, seed, counter, counter_dev, P.pre[cur], P.cnt[cur], nf, P.nblk, P.thr, P.allowed, P.child, P.done,
+          last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt], last ? n_unique : P.n_front + nxt);
+      ANQS_LAUNCHED("sampler draw_small_kernel");
+      continue;
+    }
     ANQS_TRY(scan(P.nblk, nf, 1, Fp, P.partial, P.nblk_scan, nullptr, s));
     const uint64_t max_draw_threads = (n_samples + 3) / 4 + Fp;
     draw_kernel<<<blocks_for(max_draw_threads, 256, 152 * 16), 256, 0, s>>>(
-        p, seed, counter, P.pre[cur], P.cnt[cur], nf, P.nblk_scan, P.cdf, P.allowed, P.child, max_draw_threads);
+        p, seed, counter, counter_dev, P.pre[cur], P.cnt[cur], nf, P.nblk_scan, P.thr, P.allowed, P.child,
+        max_draw_threads);
     ANQS_LAUNCHED("sampler draw_kernel");
     flag_kernel<<<blocks_for(Fp * 4, 256, 152 * 8), 256, 0, s>>>(P.child, nf, P.flags);
     ANQS_LAUNCHED("sampler flag_kernel");
-    const bool last = (p == n - 1);
     uint64_t* nf_next = last ? n_unique : P.n_front + nxt;
     ANQS_TRY(scan(P.flags, nf, 4, Fp * 4, P.partial, P.pos, nf_next, s));
     scatter_kernel<<<blocks_for(Fp * 4, 256, 152 * 8), 256, 0, s>>>(

@@ -16,8 +16,9 @@ __device__ __forceinline__ const float* table_row(const float* params, int p, ui
 }
 
 __global__ void table_logpsi_kernel(const float* __restrict__ params, int n, HamView hv,
-                                    const uint64_t* __restrict__ xs, uint64_t n_x, float* __restrict__ la_out,
+                                    const uint64_t* __restrict__ xs, Count n_x_, float* __restrict__ la_out,
                                     float* __restrict__ ph_out) {
+  const uint64_t n_x = n_x_.get();
   for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x; l += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t x = xs[l];
     float la = 0.f, ph = 0.f;
@@ -56,9 +57,10 @@ __global__ void table_logits_kernel(const float* __restrict__ params, int p, con
 
 }  // namespace
 
-int launch_table_logpsi(const anqs_model* md, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la,
+int launch_table_logpsi(const anqs_model* md, const HamView& hv, const uint64_t* x, Count n_x, float* la,
                         float* ph, cudaStream_t s) {
-  uint64_t blocks = (n_x + 255) / 256;
+  uint64_t blocks = (n_x.n + 255) / 256;
+  if (blocks == 0) blocks = 1;
   if (blocks > 152 * 16) blocks = 152 * 16;
   ProfScope ps(PROF_TABLE, s);
   table_logpsi_kernel<<<unsigned(blocks), 256, 0, s>>>(md->params, md->d.n_orb, hv, x, n_x, la, ph);
