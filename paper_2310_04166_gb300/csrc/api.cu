@@ -121,8 +121,8 @@ static size_t eloc_plain_ws(const anqs_ham* H, uint64_t n_x, Arena& A, uint64_t*
 
 namespace anqs {
 static int vjp_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, const float* cl,
-                        const float* cp, float* grad, cudaStream_t s) {
-  if (M->d.kind == ANQS_MODEL_MLP) return launch_mlp_fp32_grad(M->mlp, H->v, x, n_x, cl, cp, grad, s);
+                        const float* cp, float* grad, float* part, cudaStream_t s) {
+  if (M->d.kind == ANQS_MODEL_MLP) return launch_mlp_fp32_grad(M->mlp, H->v, x, n_x, cl, cp, grad, part, s);
   return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not available in this build", M->d.kind);
 }
 }  // namespace anqs
@@ -482,6 +482,7 @@ int anqs_grad_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_
   Arena A(nullptr, 0);
   A.take<float>(n_x);
   A.take<float>(n_x);
+  if (M->d.kind == ANQS_MODEL_MLP) A.take<float>(mlp_fp32_grad_partial_floats(M->mlp, n_x));
   *bytes = A.off;
   return ANQS_OK;
 }
@@ -495,12 +496,13 @@ int anqs_grad(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const u
   Arena A(ws, ws_bytes);
   float* cl = A.take<float>(n_x);
   float* cp = A.take<float>(n_x);
+  float* part = (M->d.kind == ANQS_MODEL_MLP) ? A.take<float>(mlp_fp32_grad_partial_floats(M->mlp, n_x)) : nullptr;
   if (!A.fits() || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", A.off);
   cudaStream_t s = (cudaStream_t)stream;
-  ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));
+  if (!part) ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));
   const Count nc{n_x, n_x_dev, 1};
   ANQS_TRY(launch_grad_cotangents(ere, eim, counts, stats, nc, cl, cp, s));
-  return vjp_dispatch(M, H, x, nc, cl, cp, grad, s);
+  return vjp_dispatch(M, H, x, nc, cl, cp, grad, part, s);
 }
 
 int anqs_logpsi_vjp(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, const float* cl,
@@ -511,7 +513,7 @@ int anqs_logpsi_vjp(const anqs_model* M, const anqs_ham* H, const uint64_t* x, u
   ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));
   if (n_x == 0) return ANQS_OK;
   if (!x || !cl || !cp) return set_error(ANQS_ERR_ARG, "null array argument");
-  return vjp_dispatch(M, H, x, host_count(n_x), cl, cp, grad, s);
+  return vjp_dispatch(M, H, x, host_count(n_x), cl, cp, grad, nullptr, s);
 }
 
 }  // extern "C"

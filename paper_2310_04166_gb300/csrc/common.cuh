@@ -176,8 +176,11 @@ int launch_mlp_fp32_logpsi(const MlpView& m, const HamView& hv, const uint64_t* 
 int launch_mlp_fp32_slot_logits(const MlpView& m, int p, const uint64_t* prefixes,
                                 const uint64_t* n_rows_dev, uint64_t max_rows, float* out8,
                                 cudaStream_t s);
+// part: per-tile partial gradients (mlp_fp32_grad_partial_floats floats) or
+// null for atomic accumulation into grad (which must then be zeroed)
 int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x,
-                         const float* cot_la, const float* cot_ph, float* grad, cudaStream_t s);
+                         const float* cot_la, const float* cot_ph, float* grad, float* part, cudaStream_t s);
+size_t mlp_fp32_grad_partial_floats(const MlpView& m, uint64_t n_x);
 
 // table.cu
 int launch_table_logpsi(const anqs_model* md, const HamView& hv, const uint64_t* x, Count n_x,

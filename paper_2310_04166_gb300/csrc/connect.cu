@@ -44,30 +44,6 @@ __device__ __forceinline__ double G(const HamView& hv, int p, int q, int r, int 
   return __ldg(hv.g + ((size_t(p) * n + q) * n + r) * n + s);
 }
 
-// <x|H|x> = E_nuc + sum_I h_ii + 1/2 sum_{I,J occ} ([II|JJ] - [IJ|JI])
-__device__ double diagonal_element(const HamView& hv, uint32_t oa, uint32_t ob) {
-  int n = hv.n;
-  double e = hv.e_nuc;
-  uint32_t occ[2] = {oa, ob};
-  for (int s = 0; s < 2; ++s)
-    for (uint32_t m = occ[s]; m; m &= m - 1) {
-      int i = __ffs(m) - 1;
-      e += __ldg(hv.h + i * n + i);
-    }
-  double c = 0.0, xch = 0.0;
-  for (int s = 0; s < 2; ++s)
-    for (uint32_t m = occ[s]; m; m &= m - 1) {
-      int i = __ffs(m) - 1;
-      for (int t = 0; t < 2; ++t)
-        for (uint32_t m2 = occ[t]; m2; m2 &= m2 - 1) {
-          int j = __ffs(m2) - 1;
-          c += G(hv, i, i, j, j);
-          if (s == t) xch += G(hv, i, j, j, i);
-        }
-    }
-  return e + 0.5 * (c - xch);
-}
-
 __global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x,
                                  uint64_t* __restrict__ xp_out, double* __restrict__ h_out,
                                  uint8_t* __restrict__ j_out) {
@@ -177,16 +153,42 @@ __global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, Co
   }
 }
 
+// <x|H|x> = E_nuc + sum_I h_ii + 1/2 sum_{I,J occ} ([II|JJ] - [IJ|JI]).
+// One warp per determinant: lane i takes the occupied spin-orbital pairs
+// (I, J) with I*N_occ + J = i mod 32, then the FP64 partial sums are reduced.
 __global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x_,
                                 double* __restrict__ hdiag) {
   const int n = hv.n;
   const uint64_t n_x = n_x_.get();
-  for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x;
-       l += uint64_t(gridDim.x) * blockDim.x) {
-    uint64_t x = __ldg(xs + l);
-    uint32_t oa = spin_occ(x, 0, n), ob = spin_occ(x, 1, n);
-    bool ok = (__popc(oa) == hv.na) && (__popc(ob) == hv.nb) && (n == 32 || (x >> (2 * n)) == 0);
-    hdiag[l] = ok ? diagonal_element(hv, oa, ob) : __longlong_as_double(0x7ff8000000000000ll);
+  const int lane = threadIdx.x & 31;
+  const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+  for (uint64_t l = blockIdx.x * uint64_t(blockDim.x >> 5) + (threadIdx.x >> 5); l < n_x; l += warps) {
+    const uint64_t x = __ldg(xs + l);
+    const uint32_t oa = spin_occ(x, 0, n), ob = spin_occ(x, 1, n);
+    const bool ok = (__popc(oa) == hv.na) && (__popc(ob) == hv.nb) && (n == 32 || (x >> (2 * n)) == 0);
+    // occupied spin-orbitals as (spatial index, spin)
+    const int ne = hv.na + hv.nb;
+    double e = 0.0;
+    if (ok) {
+      for (int t = lane; t < ne * ne + ne; t += 32) {
+        if (t < ne * ne) {
+          const int I = t / ne, J = t % ne;
+          const int si = I < hv.na ? 0 : 1, sj = J < hv.na ? 0 : 1;
+          const int i = nth_bit(si ? ob : oa, si ? I - hv.na : I);
+          const int j = nth_bit(sj ? ob : oa, sj ? J - hv.na : J);
+          e += 0.5 * G(hv, i, i, j, j);
+          if (si == sj) e -= 0.5 * G(hv, i, j, j, i);
+        } else {
+          const int I = t - ne * ne;
+          const int si = I < hv.na ? 0 : 1;
+          const int i = nth_bit(si ? ob : oa, si ? I - hv.na : I);
+          e += __ldg(hv.h + i * n + i);
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+    if (lane == 0) hdiag[l] = ok ? hv.e_nuc + e : __longlong_as_double(0x7ff8000000000000ll);
   }
 }
 
@@ -204,7 +206,7 @@ int launch_connected(const HamView& hv, const uint64_t* x, Count n_x, uint64_t* 
     ANQS_LAUNCHED("connected_kernel");
   }
   if (hdiag) {
-    uint64_t blocks = (n_x.n + threads - 1) / threads;
+    uint64_t blocks = (n_x.n + 7) / 8;  // 8 warps per CTA
     if (blocks > 152ull * 16) blocks = 152ull * 16;
     if (blocks == 0) blocks = 1;
     ProfScope ps(PROF_DIAGONAL, s);

@@ -14,7 +14,10 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// one warp per determinant: eloc = H_xx + sum_k H_k exp(dlog|psi| + i dphase)
+// one warp per determinant: eloc = H_xx + sum_k H_k exp(dlog|psi| + i dphase).
+// The ratio psi(x')/psi(x) comes from float32 log-amplitudes, so it is formed
+// in float32 (expf, sincosf of the differences); the products with H and
+// their sum over the connected set are accumulated in FP64.
 __global__ void eloc_sum_kernel(uint32_t K, Count n_x_, const double* __restrict__ hval,
                                 const double* __restrict__ hdiag, const float* __restrict__ la_x,
                                 const float* __restrict__ ph_x, const float* __restrict__ la_p,
@@ -24,16 +27,17 @@ __global__ void eloc_sum_kernel(uint32_t K, Count n_x_, const double* __restrict
   const uint64_t n_x = n_x_.get();
   const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
   for (uint64_t l = blockIdx.x * uint64_t(blockDim.x >> 5) + (threadIdx.x >> 5); l < n_x; l += warps) {
-    const double lx = la_x[l], px = ph_x[l];
+    const float lx = la_x[l], px = ph_x[l];
     double re = 0.0, im = 0.0;
     const uint64_t base = l * K;
     for (uint32_t k = lane; k < K; k += 32) {
-      double h = hval[base + k];
-      double r = exp(double(la_p[base + k]) - lx);
-      double s, c;
-      sincos(double(ph_p[base + k]) - px, &s, &c);
-      re = fma(h * r, c, re);
-      im = fma(h * r, s, im);
+      const double h = hval[base + k];
+      const float r = expf(la_p[base + k] - lx);
+      float s, c;
+      sincosf(ph_p[base + k] - px, &s, &c);
+      const double hr = h * double(r);
+      re = fma(hr, double(c), re);
+      im = fma(hr, double(s), im);
     }
     re = warp_sum(re);
     im = warp_sum(im);

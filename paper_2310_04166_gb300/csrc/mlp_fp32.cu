@@ -232,10 +232,20 @@ __global__ void __launch_bounds__(NT) slot_logits_kernel(MlpView m, int p, const
 // Adjoint of sum_l [cot_la_l log|psi(x_l)| + cot_ph_l arg psi(x_l)] with
 // respect to slot p's parameters, for one tile of rows; partial sums over
 // the tile are added to grad with atomics.
-template <int W>
+// PARTIAL: each (tile, slot) CTA stores its sums, without atomics, into the
+// tile's own copy of the gradient (grad + tile * n_params); a second kernel
+// adds the copies.  Otherwise the sums go to grad with atomics.
+template <int W, bool PARTIAL>
+__device__ __forceinline__ void gacc(float* p, float v) {
+  if (PARTIAL) *p = v;
+  else atomicAdd(p, v);
+}
+
+template <int W, bool PARTIAL>
 __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const uint64_t* __restrict__ xs,
                                                   Count n_x_, const float* __restrict__ cot_la,
-                                                  const float* __restrict__ cot_ph, float* __restrict__ grad) {
+                                                  const float* __restrict__ cot_ph, float* __restrict__ grad,
+                                                  uint64_t n_params) {
   extern __shared__ float smem[];
   const int L = m.n_hidden;
   float* act = smem;                       // L buffers [R][W]: h_1..h_L
@@ -258,7 +268,7 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
   __syncthreads();
   const int last = slot_forward<W>(m, p, xt, nrows, act, L, ws, out8);
   const MlpPtr P = slot_ptrs(m, p);
-  float* gbase = grad + (P.W1 - m.params);
+  float* gbase = grad + (P.W1 - m.params) + (PARTIAL ? uint64_t(blockIdx.x) * n_params : 0ull);
   // d out: d l_u = cot_la * 1/2 (delta_uv - p~_u) over allowed u, d phi_u = cot_ph delta_uv
   if (threadIdx.x < R) {
     int r = threadIdx.x;
@@ -299,12 +309,12 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
       int o = idx / W, k = idx % W;
       float s = 0.f;
       for (int r = 0; r < R; ++r) s = fmaf(out8[r * 8 + o], hL[r * W + k], s);
-      atomicAdd(gWh + idx, s);
+      gacc<W, PARTIAL>(gWh + idx, s);
     }
     if (threadIdx.x < 8) {
       float s = 0.f;
       for (int r = 0; r < R; ++r) s += out8[r * 8 + threadIdx.x];
-      atomicAdd(gbh + threadIdx.x, s);
+      gacc<W, PARTIAL>(gbh + threadIdx.x, s);
     }
     for (int idx = threadIdx.x; idx < R * W; idx += NT) {
       int r = idx / W, k = idx % W;
@@ -328,12 +338,12 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
       int o = idx / W, i = idx % W;
       float s = 0.f;
       for (int r = 0; r < R; ++r) s = fmaf(dh[r * W + o], hprev[r * W + i], s);
-      atomicAdd(gW + idx, s);
+      gacc<W, PARTIAL>(gW + idx, s);
     }
     for (int o = threadIdx.x; o < W; o += NT) {
       float s = 0.f;
       for (int r = 0; r < R; ++r) s += dh[r * W + o];
-      atomicAdd(gb + o, s);
+      gacc<W, PARTIAL>(gb + o, s);
     }
     float acc[RPT][CPT];
     tile_gemm<W, true>(dh, Wk, ws, acc);  // dh_{k-1} = W_k^T dz_k
@@ -355,14 +365,26 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
     for (int o = threadIdx.x; o < W; o += NT) {
       float s = 0.f;
       for (int r = 0; r < nrows; ++r) s += dh[r * W + o];
-      atomicAdd(gb1 + o, s);
+      gacc<W, PARTIAL>(gb1 + o, s);
       for (int q = 0; q < p; ++q) {
         float c4[4] = {0.f, 0.f, 0.f, 0.f};
         for (int r = 0; r < nrows; ++r) c4[int((xt[r] >> (2 * q)) & 3ull)] += dh[r * W + o];
         for (int u = 0; u < 4; ++u)
-          if (c4[u] != 0.f) atomicAdd(gW1 + size_t(o) * 4 * p + 4 * q + u, c4[u]);
+          if (PARTIAL || c4[u] != 0.f) gacc<W, PARTIAL>(gW1 + size_t(o) * 4 * p + 4 * q + u, c4[u]);
       }
     }
+  }
+}
+
+// grad[i] = sum over the tiles of the per-tile copies (only tiles holding rows)
+__global__ void partial_sum_kernel(const float* __restrict__ part, Count n_x_, uint64_t n_params,
+                                   float* __restrict__ grad) {
+  const uint64_t tiles = (n_x_.get() + R - 1) / R;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n_params;
+       i += uint64_t(gridDim.x) * blockDim.x) {
+    float s = 0.f;
+    for (uint64_t t = 0; t < tiles; ++t) s += part[t * n_params + i];
+    grad[i] = s;
   }
 }
 
@@ -398,15 +420,24 @@ int logits_w(const MlpView& m, int p, const uint64_t* pre, const uint64_t* nr, u
 
 template <int W>
 int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
-           const float* cp, float* g, cudaStream_t s) {
+           const float* cp, float* g, float* part, uint64_t n_params, cudaStream_t s) {
   size_t sm = Smem<W>::bytes(m.n_hidden + 1);
   if (sm > 227 * 1024)
     return set_error(ANQS_ERR_UNSUPPORTED, "FP32 MLP adjoint needs %zu bytes of shared memory", sm);
-  ANQS_TRY(set_smem(grad_kernel<W>, sm));
   dim3 grid(unsigned(std::max<uint64_t>((n_x.n + R - 1) / R, 1)), unsigned(m.n));
   ProfScope ps(PROF_MLP_FP32_GRAD, s);
-  grad_kernel<W><<<grid, NT, sm, s>>>(m, hv, x, n_x, cl, cp, g);
-  ANQS_LAUNCHED("mlp grad_kernel");
+  if (part) {
+    ANQS_TRY(set_smem(grad_kernel<W, true>, sm));
+    grad_kernel<W, true><<<grid, NT, sm, s>>>(m, hv, x, n_x, cl, cp, part, n_params);
+    ANQS_LAUNCHED("mlp grad_kernel");
+    partial_sum_kernel<<<unsigned(std::min<uint64_t>((n_params + 255) / 256, 152 * 8)), 256, 0, s>>>(part, n_x,
+                                                                                                 n_params, g);
+    ANQS_LAUNCHED("mlp partial_sum_kernel");
+  } else {
+    ANQS_TRY(set_smem(grad_kernel<W, false>, sm));
+    grad_kernel<W, false><<<grid, NT, sm, s>>>(m, hv, x, n_x, cl, cp, g, n_params);
+    ANQS_LAUNCHED("mlp grad_kernel");
+  }
   return ANQS_OK;
 }
 
@@ -432,13 +463,18 @@ int launch_mlp_fp32_slot_logits(const MlpView& m, int p, const uint64_t* pre, co
   return set_error(ANQS_ERR_UNSUPPORTED, "width %d", m.width);
 }
 
+size_t mlp_fp32_grad_partial_floats(const MlpView& m, uint64_t n_x) {
+  return size_t((n_x + R - 1) / R) * m.slot_off[m.n];
+}
+
 int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
-                         const float* cp, float* g, cudaStream_t s) {
+                         const float* cp, float* g, float* part, cudaStream_t s) {
   if ((n_x.n + R - 1) / R > 0x7fffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "too many rows");
+  const uint64_t np = m.slot_off[m.n];
   switch (m.width) {
-    case 64: return grad_w<64>(m, hv, x, n_x, cl, cp, g, s);
-    case 128: return grad_w<128>(m, hv, x, n_x, cl, cp, g, s);
-    case 256: return grad_w<256>(m, hv, x, n_x, cl, cp, g, s);
+    case 64: return grad_w<64>(m, hv, x, n_x, cl, cp, g, part, np, s);
+    case 128: return grad_w<128>(m, hv, x, n_x, cl, cp, g, part, np, s);
+    case 256: return grad_w<256>(m, hv, x, n_x, cl, cp, g, part, np, s);
   }
   return set_error(ANQS_ERR_UNSUPPORTED, "width %d", m.width);
 }

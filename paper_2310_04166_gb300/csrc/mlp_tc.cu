@@ -543,8 +543,19 @@ __global__ void js_offsets_kernel(const uint32_t* __restrict__ hist, int n, uint
 __global__ void js_scatter_kernel(const uint8_t* __restrict__ js, Count m_, uint32_t* __restrict__ cursor,
                                   uint32_t* __restrict__ perm) {
   const uint64_t m = m_.get();
-  for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < m; t += uint64_t(gridDim.x) * blockDim.x)
-    perm[atomicAdd(&cursor[js[t]], 1u)] = uint32_t(t);
+  const int lane = threadIdx.x & 31;
+  for (uint64_t t0 = blockIdx.x * uint64_t(blockDim.x); t0 < m; t0 += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t t = t0 + threadIdx.x;
+    const int key = t < m ? int(js[t]) : -1;
+    // lanes with the same key reserve their slots with one atomic
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    uint32_t base = 0;
+    if (lane == leader && key >= 0) base = atomicAdd(&cursor[key], uint32_t(__popc(peers)));
+    base = __shfl_sync(peers, base, leader);
+    if (key >= 0) perm[base + rank] = uint32_t(t);
+  }
 }
 
 int g_num_sms = 0;

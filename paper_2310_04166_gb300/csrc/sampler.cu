@@ -55,11 +55,13 @@ struct Philox {
   }
 };
 
-__global__ void init_kernel(uint64_t* pre, uint64_t* cnt, uint64_t* n_front, uint64_t n_samples, unsigned* done) {
+__global__ void init_kernel(uint64_t* pre, uint64_t* cnt, uint64_t* n_front, uint64_t n_samples, unsigned* done,
+                            uint64_t* child) {
   pre[0] = 0;
   cnt[0] = n_samples;
   n_front[0] = 1;
   *done = 0;
+  for (int v = 0; v < 4; ++v) child[v] = 0;
 }
 
 __device__ __forceinline__ int popc_alpha(uint64_t x, int p) {
@@ -312,33 +314,39 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* sh
   return sh[w] + inc - v;
 }
 
-// Draws of one level for frontiers of at most SMALL_F nodes: every CTA scans
-// the per-node draw-block counts in its own shared memory, draws its share
-// with integer threshold compares and adds warp-segment sums of the outcome
-// counts to the children; the last CTA to finish compacts the children into
-// the next frontier (no CTA waits on another).
-__global__ void __launch_bounds__(SMALL_T) draw_small_kernel(int p, uint64_t seed, uint64_t counter0,
+// One level of the sampler for frontiers of at most SMALL_F nodes (after the
+// network has written the slot logits of every frontier prefix):
+//   - every CTA scans the per-node draw-block counts in its own shared memory;
+//   - for each window of SMALL_T draw blocks the CTA computes, for the nodes
+//     the window touches, the masked conditional in FP64 and the integer
+//     thresholds T_v = ceil(C_v 2^53) (u < C_v  <=>  (word >> 11) < T_v);
+//   - the draws compare Philox words with the thresholds and add
+//     warp-segment sums of the outcome counts to the children;
+//   - the last CTA to finish compacts the children, in (node, outcome)
+//     order, into the next frontier and clears the counters it used.
+// No CTA waits on another.
+__global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, uint64_t seed, uint64_t counter0,
                                                              const uint64_t* __restrict__ counter_dev,
                                                              const uint64_t* __restrict__ pre,
                                                              const uint64_t* __restrict__ cnt,
                                                              const uint64_t* __restrict__ n_front,
-                                                             const uint64_t* __restrict__ nblk,
-                                                             const uint64_t* __restrict__ thr,
-                                                             const uint8_t* __restrict__ allowed,
+                                                             const float* __restrict__ logits,
                                                              uint64_t* __restrict__ child, unsigned* __restrict__ done,
                                                              uint64_t* __restrict__ pre_out,
                                                              uint64_t* __restrict__ cnt_out,
                                                              uint64_t* __restrict__ n_out) {
   __shared__ uint32_t s_scan[SMALL_F + 1];
+  __shared__ uint64_t s_thr[SMALL_T][4];
+  __shared__ uint8_t s_mk[SMALL_T];
   __shared__ uint32_t s_red[33];
   __shared__ bool s_last;
   const int nf = int(*n_front);
-  const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
   const int lane = threadIdx.x & 31;
+  const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
   uint32_t carry = 0;
   for (int base = 0; base < nf; base += SMALL_T) {
     const int i = base + threadIdx.x;
-    const uint32_t nb = i < nf ? uint32_t(nblk[i]) : 0u;
+    const uint32_t nb = i < nf ? uint32_t((cnt[i] + 3) / 4) : 0u;
     uint32_t tot;
     const uint32_t ex = block_excl_scan_u32(nb, s_red, &tot);
     if (i < nf) s_scan[i] = carry + ex;
@@ -347,30 +355,56 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(int p, uint64_t see
   if (threadIdx.x == 0) s_scan[nf] = carry;
   __syncthreads();
   const uint32_t total = carry;
+  auto node_of = [&](uint32_t t) {
+    int lo = 0, hi = nf - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (s_scan[mid] <= t) lo = mid;
+      else hi = mid - 1;
+    }
+    return lo;
+  };
   for (uint32_t t0 = blockIdx.x * SMALL_T; t0 < total; t0 += gridDim.x * SMALL_T) {
+    const uint32_t t_end = min(total, t0 + SMALL_T);
+    const int n_lo = node_of(t0), n_hi = node_of(t_end - 1);
+    __syncthreads();  // previous window's thresholds are no longer read
+    if (threadIdx.x <= n_hi - n_lo) {
+      const int i = n_lo + threadIdx.x;
+      const uint64_t x = pre[i];
+      const unsigned mk = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p));
+      const float* l = logits + uint64_t(i) * 8;
+      double m = -INFINITY;
+      for (int v = 0; v < 4; ++v)
+        if ((mk >> v) & 1u) m = fmax(m, double(l[v]));
+      double e[4], s = 0.0;
+      for (int v = 0; v < 4; ++v) {
+        e[v] = ((mk >> v) & 1u) ? exp(double(l[v]) - m) : 0.0;
+        s += e[v];
+      }
+      double run = 0.0;
+      for (int v = 0; v < 4; ++v) {
+        if ((mk >> v) & 1u) run += e[v] / s;
+        s_thr[threadIdx.x][v] = uint64_t(ceil(run * 9007199254740992.0));
+      }
+      s_mk[threadIdx.x] = uint8_t(mk);
+    }
+    __syncthreads();
     const uint32_t t = t0 + threadIdx.x;
     int node = -1;
     uint32_t packed = 0;
-    if (t < total) {
-      int lo = 0, hi = nf - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_scan[mid] <= t) lo = mid;
-        else hi = mid - 1;
-      }
-      node = lo;
-      const uint64_t ib = t - s_scan[lo];
-      const uint64_t c = cnt[lo];
+    if (t < t_end) {
+      node = node_of(t);
+      const int li = node - n_lo;
+      const uint64_t ib = t - s_scan[node];
+      const uint64_t c = cnt[node];
       uint64_t w[4];
-      Philox::block(pre[lo], ib, uint64_t(p), counter, seed, 0ull, w);
-      const unsigned mk = allowed[lo];
-      uint64_t T[4];
-      for (int v = 0; v < 4; ++v) T[v] = thr[uint64_t(lo) * 4 + v];
+      Philox::block(pre[node], ib, uint64_t(p), counter, seed, 0ull, w);
+      const unsigned mk = s_mk[li];
       int last = 3;
       while (last > 0 && !((mk >> last) & 1u)) --last;
       for (int k = 0; k < 4; ++k) {
         if (ib * 4 + k >= c) break;
-        packed += 1u << (8 * draw_outcome(w[k], T, mk, last));
+        packed += 1u << (8 * draw_outcome(w[k], s_thr[li], mk, last));
       }
     }
     const int prev = __shfl_up_sync(0xffffffffu, node, 1);
@@ -408,9 +442,12 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(int p, uint64_t see
     }
     carry += tot;
   }
+  __syncthreads();
+  // clear the counters of the next level's nodes
+  for (uint32_t i = threadIdx.x; i < 4 * carry; i += SMALL_T) child[i] = 0;
   if (threadIdx.x == 0) {
     *n_out = carry;
-    *done = 0;  // ready for the next level
+    *done = 0;
   }
 }
 
@@ -486,9 +523,10 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
   const int n = H->v.n;
   {
     ProfScope ps(PROF_SAMPLER, s);
-    init_kernel<<<1, 1, 0, s>>>(P.pre[0], P.cnt[0], P.n_front, n_samples, P.done);
+    init_kernel<<<1, 1, 0, s>>>(P.pre[0], P.cnt[0], P.n_front, n_samples, P.done, P.child);
     ANQS_LAUNCHED("sampler init_kernel");
   }
+  bool prev_large = false;
   for (int p = 0; p < n; ++p) {
     const int cur = p & 1, nxt = cur ^ 1;
     const uint64_t Fp = level_cap(H, n_samples, p);
@@ -497,18 +535,22 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
     ProfScope ps(PROF_SAMPLER, s);
     const bool last = (p == n - 1);
     const bool small = Fp <= uint64_t(SMALL_F) && n_samples < (1ull << 31);
-    // per-node conditional in FP64, spread over many small CTAs
-    prep_kernel<<<blocks_for(Fp, small ? 32 : 256, 152 * 8), small ? 32 : 256, 0, s>>>(
-        H->v, p, P.pre[cur], P.cnt[cur], nf, P.logits, P.thr, P.allowed, P.nblk, P.child);
-    ANQS_LAUNCHED("sampler prep_kernel");
+    if (small && prev_large) {
+      // the multi-kernel path leaves its counters set; the small path expects them cleared
+      ANQS_CUDA(cudaMemsetAsync(P.child, 0, Fp * 4 * sizeof(uint64_t), s));
+    }
+    prev_large = !small;
     if (small) {
       const uint64_t blocks = ((n_samples + 3) / 4 + Fp + SMALL_T - 1) / SMALL_T;
       draw_small_kernel<<<blocks_for(blocks, 1, 152), SMALL_T, 0, s>>>(
-          p, seed, counter, counter_dev, P.pre[cur], P.cnt[cur], nf, P.nblk, P.thr, P.allowed, P.child, P.done,
+          H->v, p, seed, counter, counter_dev, P.pre[cur], P.cnt[cur], nf, P.logits, P.child, P.done,
           last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt], last ? n_unique : P.n_front + nxt);
       ANQS_LAUNCHED("sampler draw_small_kernel");
       continue;
     }
+    prep_kernel<<<blocks_for(Fp, 256, 152 * 8), 256, 0, s>>>(H->v, p, P.pre[cur], P.cnt[cur], nf, P.logits, P.thr,
+                                                              P.allowed, P.nblk, P.child);
+    ANQS_LAUNCHED("sampler prep_kernel");
     ANQS_TRY(scan(P.nblk, nf, 1, Fp, P.partial, P.nblk_scan, nullptr, s));
     const uint64_t max_draw_threads = (n_samples + 3) / 4 + Fp;
     draw_kernel<<<blocks_for(max_draw_threads, 256, 152 * 16), 256, 0, s>>>(
