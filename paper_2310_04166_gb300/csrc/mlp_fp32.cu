@@ -19,7 +19,8 @@
 namespace anqs {
 namespace {
 
-constexpr int R = 32;    // rows per CTA tile
+constexpr int R = 32;    // rows per CTA tile (log psi and slot logits)
+constexpr int RG = 16;   // rows per CTA tile of the adjoint (more CTAs for few samples)
 constexpr int NT = 256;  // threads per CTA
 constexpr int KC = 32;   // weight chunk depth
 
@@ -44,10 +45,10 @@ __device__ __forceinline__ MlpPtr slot_ptrs(const MlpView& m, int p) {
 
 // out[r][c] = sum_k in[r][k] * B(k, c), B(k, c) = W[c][k] (forward) or W[k][c]
 // (adjoint).  Each warp owns R/8 rows, each lane W/32 columns.
-template <int W, bool ADJ>
+template <int W, bool ADJ, int RR = R>
 __device__ __forceinline__ void tile_gemm(const float* in, const float* __restrict__ Wg, float* ws,
-                                          float (&acc)[R / 8][W / 32]) {
-  constexpr int RPT = R / 8, CPT = W / 32;
+                                          float (&acc)[RR / 8][W / 32]) {
+  constexpr int RPT = RR / 8, CPT = W / 32;
   const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < RPT; ++i)
@@ -85,10 +86,10 @@ __device__ __forceinline__ void tile_gemm(const float* in, const float* __restri
   }
 }
 
-template <int W>
+template <int W, int RR = R>
 struct Smem {
   static constexpr size_t ws_floats = KC * (W + 1);
-  static size_t bytes(int n_act) { return (size_t(n_act) * R * W + ws_floats + R * 8) * sizeof(float); }
+  static size_t bytes(int n_act) { return (size_t(n_act) * RR * W + ws_floats + RR * 8) * sizeof(float); }
 };
 
 // Forward of slot p for the R rows whose determinants are xs[0..R) (rows
@@ -96,11 +97,11 @@ struct Smem {
 // n_keep activation buffers [R][W]: with n_keep == L every layer's output is
 // kept (for the adjoint), with n_keep == 2 they ping-pong.  Leaves the head
 // outputs in out8[R][8] and returns the index of the last hidden buffer.
-template <int W>
+template <int W, int RR = R>
 __device__ int slot_forward(const MlpView& m, int p, const uint64_t* xs, int nrows, float* act, int n_keep,
                             float* ws, float* out8) {
   const MlpPtr P = slot_ptrs(m, p);
-  for (int idx = threadIdx.x; idx < R * W; idx += NT) {
+  for (int idx = threadIdx.x; idx < RR * W; idx += NT) {
     int r = idx / W, o = idx % W;
     float acc = __ldg(P.b1 + o);
     if (r < nrows) {
@@ -112,14 +113,14 @@ __device__ int slot_forward(const MlpView& m, int p, const uint64_t* xs, int nro
   }
   int cur = 0;
   const float* Wk = P.Wk;
-  constexpr int RPT = R / 8, CPT = W / 32;
+  constexpr int RPT = RR / 8, CPT = W / 32;
   const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
   for (int k = 2; k <= m.n_hidden; ++k) {
     const float* bk = Wk + size_t(W) * W;
     float acc[RPT][CPT];
-    tile_gemm<W, false>(act + size_t(cur) * R * W, Wk, ws, acc);
+    tile_gemm<W, false, RR>(act + size_t(cur) * RR * W, Wk, ws, acc);
     int nxt = (n_keep == 2) ? (cur ^ 1) : (cur + 1);
-    float* o = act + size_t(nxt) * R * W;
+    float* o = act + size_t(nxt) * RR * W;
 #pragma unroll
     for (int i = 0; i < RPT; ++i)
 #pragma unroll
@@ -132,12 +133,14 @@ __device__ int slot_forward(const MlpView& m, int p, const uint64_t* xs, int nro
   }
   __syncthreads();
   {
-    const float* h = act + size_t(cur) * R * W;
-    int r = threadIdx.x >> 3, o = threadIdx.x & 7;  // R * 8 == NT
-    float acc = __ldg(P.bh + o);
-    const float* wr = P.Wh + size_t(o) * W;
-    for (int k = 0; k < W; ++k) acc = fmaf(h[r * W + ((k + r) & (W - 1))], __ldg(wr + ((k + r) & (W - 1))), acc);
-    out8[r * 8 + o] = acc;
+    const float* h = act + size_t(cur) * RR * W;
+    int r = threadIdx.x >> 3, o = threadIdx.x & 7;
+    if (r < RR) {
+      float acc = __ldg(P.bh + o);
+      const float* wr = P.Wh + size_t(o) * W;
+      for (int k = 0; k < W; ++k) acc = fmaf(h[r * W + ((k + r) & (W - 1))], __ldg(wr + ((k + r) & (W - 1))), acc);
+      out8[r * 8 + o] = acc;
+    }
   }
   __syncthreads();
   return cur;
@@ -241,6 +244,58 @@ __device__ __forceinline__ void gacc(float* p, float v) {
   else atomicAdd(p, v);
 }
 
+// gW[o][i] (+)= sum_r dz[r][o] h[r][i] over the R rows of the tile, with
+// register blocking: a 16 x 16 grid of threads, each owning a block of
+// W/16 x W/16 outputs (W = 256 in two column halves), float4 shared loads.
+template <int W, bool PARTIAL, int RR>
+__device__ __forceinline__ void outer_accumulate(const float* dz, const float* h, float* gW) {
+  constexpr int B = (W >= 128) ? 8 : W / 16;  // outputs per thread along o and along i
+  constexpr int COLS = 16 * B;                 // columns covered per pass
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  for (int c0 = 0; c0 < W; c0 += COLS) {
+    float acc[B][B];
+#pragma unroll
+    for (int a = 0; a < B; ++a)
+#pragma unroll
+      for (int b = 0; b < B; ++b) acc[a][b] = 0.f;
+    const int o0 = ty * B * (W / (16 * B)), i0 = c0 + tx * B;
+    for (int ob = 0; ob < W / (16 * B); ++ob) {
+      const int oo = o0 + ob * B;
+      if (ob > 0) {
+#pragma unroll
+        for (int a = 0; a < B; ++a)
+#pragma unroll
+          for (int b = 0; b < B; ++b) acc[a][b] = 0.f;
+      }
+#pragma unroll 4
+      for (int r = 0; r < RR; ++r) {
+        float zo[B], hi[B];
+#pragma unroll
+        for (int a = 0; a < B; a += 4) {
+          const float4 z4 = *reinterpret_cast<const float4*>(dz + r * W + oo + a);
+          zo[a] = z4.x;
+          zo[a + 1] = z4.y;
+          zo[a + 2] = z4.z;
+          zo[a + 3] = z4.w;
+          const float4 h4 = *reinterpret_cast<const float4*>(h + r * W + i0 + a);
+          hi[a] = h4.x;
+          hi[a + 1] = h4.y;
+          hi[a + 2] = h4.z;
+          hi[a + 3] = h4.w;
+        }
+#pragma unroll
+        for (int a = 0; a < B; ++a)
+#pragma unroll
+          for (int b = 0; b < B; ++b) acc[a][b] = fmaf(zo[a], hi[b], acc[a][b]);
+      }
+#pragma unroll
+      for (int a = 0; a < B; ++a)
+#pragma unroll
+        for (int b = 0; b < B; ++b) gacc<W, PARTIAL>(gW + size_t(oo + a) * W + i0 + b, acc[a][b]);
+    }
+  }
+}
+
 template <int W, bool PARTIAL>
 __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const uint64_t* __restrict__ xs,
                                                   Count n_x_, const float* __restrict__ cot_la,
@@ -248,29 +303,29 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
                                                   uint64_t n_params) {
   extern __shared__ float smem[];
   const int L = m.n_hidden;
-  float* act = smem;                       // L buffers [R][W]: h_1..h_L
-  float* ws = act + size_t(L) * R * W;     // weight chunk
-  float* out8 = ws + Smem<W>::ws_floats;   // head outputs, then their adjoint
-  float* dh = out8 + R * 8;                // [R][W] adjoint of the current layer output
-  __shared__ uint64_t xt[R];
-  __shared__ float cl[R], cp[R];
+  float* act = smem;                       // L buffers [RG][W]: h_1..h_L
+  float* ws = act + size_t(L) * RG * W;     // weight chunk
+  float* out8 = ws + Smem<W, RG>::ws_floats;   // head outputs, then their adjoint
+  float* dh = out8 + RG * 8;                // [RG][W] adjoint of the current layer output
+  __shared__ uint64_t xt[RG];
+  __shared__ float cl[RG], cp[RG];
   const int p = blockIdx.y;
   const uint64_t n_x = n_x_.get();
-  const uint64_t base = uint64_t(blockIdx.x) * R;
+  const uint64_t base = uint64_t(blockIdx.x) * RG;
   if (base >= n_x) return;
-  const int nrows = int(n_x - base < uint64_t(R) ? n_x - base : uint64_t(R));
-  if (threadIdx.x < R) {
+  const int nrows = int(n_x - base < uint64_t(RG) ? n_x - base : uint64_t(RG));
+  if (threadIdx.x < RG) {
     bool ok = threadIdx.x < nrows;
     xt[threadIdx.x] = ok ? xs[base + threadIdx.x] : 0ull;
     cl[threadIdx.x] = ok ? cot_la[base + threadIdx.x] : 0.f;
     cp[threadIdx.x] = ok ? cot_ph[base + threadIdx.x] : 0.f;
   }
   __syncthreads();
-  const int last = slot_forward<W>(m, p, xt, nrows, act, L, ws, out8);
+  const int last = slot_forward<W, RG>(m, p, xt, nrows, act, L, ws, out8);
   const MlpPtr P = slot_ptrs(m, p);
   float* gbase = grad + (P.W1 - m.params) + (PARTIAL ? uint64_t(blockIdx.x) * n_params : 0ull);
   // d out: d l_u = cot_la * 1/2 (delta_uv - p~_u) over allowed u, d phi_u = cot_ph delta_uv
-  if (threadIdx.x < R) {
+  if (threadIdx.x < RG) {
     int r = threadIdx.x;
     float d[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     if (r < nrows) {
@@ -302,21 +357,21 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
   __syncthreads();
   // head: dW_h[o][k] += sum_r d[r][o] h_L[r][k]; db_h[o] += sum_r d[r][o]; dh_L = W_h^T d
   {
-    const float* hL = act + size_t(last) * R * W;
+    const float* hL = act + size_t(last) * RG * W;
     float* gWh = gbase + (P.Wh - P.W1);
     float* gbh = gbase + (P.bh - P.W1);
     for (int idx = threadIdx.x; idx < 8 * W; idx += NT) {
       int o = idx / W, k = idx % W;
       float s = 0.f;
-      for (int r = 0; r < R; ++r) s = fmaf(out8[r * 8 + o], hL[r * W + k], s);
+      for (int r = 0; r < RG; ++r) s = fmaf(out8[r * 8 + o], hL[r * W + k], s);
       gacc<W, PARTIAL>(gWh + idx, s);
     }
     if (threadIdx.x < 8) {
       float s = 0.f;
-      for (int r = 0; r < R; ++r) s += out8[r * 8 + threadIdx.x];
+      for (int r = 0; r < RG; ++r) s += out8[r * 8 + threadIdx.x];
       gacc<W, PARTIAL>(gbh + threadIdx.x, s);
     }
-    for (int idx = threadIdx.x; idx < R * W; idx += NT) {
+    for (int idx = threadIdx.x; idx < RG * W; idx += NT) {
       int r = idx / W, k = idx % W;
       float s = 0.f;
       for (int o = 0; o < 8; ++o) s = fmaf(__ldg(P.Wh + o * W + k), out8[r * 8 + o], s);
@@ -327,26 +382,21 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
   }
   __syncthreads();
   // hidden layers L..2 (dh holds dz_k of layer k)
-  constexpr int RPT = R / 8, CPT = W / 32;
+  constexpr int RPT = RG / 8, CPT = W / 32;
   const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
   for (int k = L; k >= 2; --k) {
     const float* Wk = P.Wk + size_t(k - 2) * (size_t(W) * W + W);
     float* gW = gbase + (Wk - P.W1);
     float* gb = gW + size_t(W) * W;
-    const float* hprev = act + size_t(k - 2) * R * W;  // h_{k-1}
-    for (int idx = threadIdx.x; idx < W * W; idx += NT) {
-      int o = idx / W, i = idx % W;
-      float s = 0.f;
-      for (int r = 0; r < R; ++r) s = fmaf(dh[r * W + o], hprev[r * W + i], s);
-      gacc<W, PARTIAL>(gW + idx, s);
-    }
+    const float* hprev = act + size_t(k - 2) * RG * W;  // h_{k-1}
+    outer_accumulate<W, PARTIAL, RG>(dh, hprev, gW);
     for (int o = threadIdx.x; o < W; o += NT) {
       float s = 0.f;
-      for (int r = 0; r < R; ++r) s += dh[r * W + o];
+      for (int r = 0; r < RG; ++r) s += dh[r * W + o];
       gacc<W, PARTIAL>(gb + o, s);
     }
     float acc[RPT][CPT];
-    tile_gemm<W, true>(dh, Wk, ws, acc);  // dh_{k-1} = W_k^T dz_k
+    tile_gemm<W, true, RG>(dh, Wk, ws, acc);  // dh_{k-1} = W_k^T dz_k
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < RPT; ++i)
@@ -379,7 +429,7 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
 // grad[i] = sum over the tiles of the per-tile copies (only tiles holding rows)
 __global__ void partial_sum_kernel(const float* __restrict__ part, Count n_x_, uint64_t n_params,
                                    float* __restrict__ grad) {
-  const uint64_t tiles = (n_x_.get() + R - 1) / R;
+  const uint64_t tiles = (n_x_.get() + RG - 1) / RG;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n_params;
        i += uint64_t(gridDim.x) * blockDim.x) {
     float s = 0.f;
@@ -421,10 +471,10 @@ int logits_w(const MlpView& m, int p, const uint64_t* pre, const uint64_t* nr, u
 template <int W>
 int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
            const float* cp, float* g, float* part, uint64_t n_params, cudaStream_t s) {
-  size_t sm = Smem<W>::bytes(m.n_hidden + 1);
+  size_t sm = Smem<W, RG>::bytes(m.n_hidden + 1);
   if (sm > 227 * 1024)
     return set_error(ANQS_ERR_UNSUPPORTED, "FP32 MLP adjoint needs %zu bytes of shared memory", sm);
-  dim3 grid(unsigned(std::max<uint64_t>((n_x.n + R - 1) / R, 1)), unsigned(m.n));
+  dim3 grid(unsigned(std::max<uint64_t>((n_x.n + RG - 1) / RG, 1)), unsigned(m.n));
   ProfScope ps(PROF_MLP_FP32_GRAD, s);
   if (part) {
     ANQS_TRY(set_smem(grad_kernel<W, true>, sm));
@@ -464,12 +514,12 @@ int launch_mlp_fp32_slot_logits(const MlpView& m, int p, const uint64_t* pre, co
 }
 
 size_t mlp_fp32_grad_partial_floats(const MlpView& m, uint64_t n_x) {
-  return size_t((n_x + R - 1) / R) * m.slot_off[m.n];
+  return size_t((n_x + RG - 1) / RG) * m.slot_off[m.n];
 }
 
 int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
                          const float* cp, float* g, float* part, cudaStream_t s) {
-  if ((n_x.n + R - 1) / R > 0x7fffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "too many rows");
+  if ((n_x.n + RG - 1) / RG > 0x7fffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "too many rows");
   const uint64_t np = m.slot_off[m.n];
   switch (m.width) {
     case 64: return grad_w<64>(m, hv, x, n_x, cl, cp, g, part, np, s);

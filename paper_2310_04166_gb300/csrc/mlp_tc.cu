@@ -19,7 +19,8 @@
 //   SUFFIX  rows = connected determinants x' (sorted by first differing slot
 //           j); log psi(x') = parent prefix up to j + parent slot-j term of
 //           v'_j + the network's slots p > j (Eq. anqs_def: slots <= j see
-//           the same prefix as in x).
+//           the same prefix as in x).  Weight-stationary: each CTA serves
+//           one slot for the whole launch.
 //   LOGPSI  rows = arbitrary determinants, all slots, log psi only.
 //   LOGITS  rows = sampler frontier prefixes, one slot, the 8 raw outputs.
 #include <cuda_bf16.h>
@@ -49,7 +50,7 @@ struct SlotLayout {
   uint32_t w1;      // layer-1 matrix [W][k1] bf16, canonical K-major
   uint32_t wk;      // hidden matrices [L-1][W][W] bf16, canonical, each W*W*2 bytes
   uint32_t bias;    // [L][W] f32
-  uint32_t head;    // [8][W] f32
+  uint32_t head;    // head [W][8] f32 (transposed: the 8 outputs of input k are adjacent)
   uint32_t hbias;   // [8] f32
   uint32_t bytes;   // total, multiple of 128
 };
@@ -108,8 +109,8 @@ __global__ void pack_kernel(MlpView m, TcView tv, unsigned char* img) {
       const float* bl = (l == 0) ? b1 : (Wk + size_t(l - 1) * (size_t(W) * W + W) + size_t(W) * W);
       reinterpret_cast<float*>(base + S.bias)[u] = bl[o];
     } else if (t < n1 + nk + uint32_t(L) * W + 8u * W) {
-      uint32_t u = t - n1 - nk - uint32_t(L) * W;
-      reinterpret_cast<float*>(base + S.head)[u] = Wh[u];
+      uint32_t u = t - n1 - nk - uint32_t(L) * W, o = u / W, k = u % W;
+      reinterpret_cast<float*>(base + S.head)[k * 8 + o] = Wh[o * W + k];
     } else {
       uint32_t u = t - n1 - nk - uint32_t(L) * W - 8u * W;
       reinterpret_cast<float*>(base + S.hbias)[u] = bh[u];
@@ -130,17 +131,10 @@ struct TileArgs {
   Count rows;
   int p_lo, p_hi;              // SLOTS: slots [p_lo, p_hi)
   float* raw;                  // SLOTS output [row][p_hi - p_lo][8]
-  // SUFFIX
-  const uint32_t* perm;
-  const uint8_t* js;
-  const float* cache;          // [n_parents][n][CACHE_F]
-  uint32_t K;
-  float* la;
-  float* ph;
 };
 
-constexpr int NT = 2 * MT;   // two warpgroups
-constexpr int TPW = 4;       // SUFFIX: tiles per warpgroup per chunk
+constexpr int NWG = 4;        // warpgroups per CTA, one 128-row tile each in flight
+constexpr int NT = NWG * MT;
 
 struct Ctx {
   const TcView* tv;
@@ -194,24 +188,22 @@ __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const
   tc::fence_before_sync();
   wg_sync(c.wg);
   const float* bias = reinterpret_cast<const float*>(img + S.bias);
-  const float* head = reinterpret_cast<const float*>(img + S.head);
+  const float4* head = reinterpret_cast<const float4*>(img + S.head);  // [W][8] as 2 float4 per input
   const float* hbias = reinterpret_cast<const float*>(img + S.hbias);
+  float acc[8];
 #pragma unroll
-  for (int o = 0; o < 8; ++o) out[o] = 0.f;
+  for (int o = 0; o < 8; ++o) acc[o] = 0.f;
   bool ok = true;
   for (int layer = 0; layer < L; ++layer) {
     const uint32_t K = layer == 0 ? S.k1 : uint32_t(W);
-    const uint32_t d_tmem = c.tmem + uint32_t(layer & 1) * W;
     if (K > 0) {
       if (c.t == 0) {
         tc::fence_after_sync();
         const uint32_t b_addr = img_addr + (layer == 0 ? S.w1 : S.wk + uint32_t(layer - 1) * W * W * 2u);
 #pragma unroll 1
-        for (uint32_t ks = 0; ks < K / 16; ++ks) {
-          const uint64_t ad = tc::sdesc(c.a_addr + ks * 256u, 128u, K * 16u);
-          const uint64_t bd = tc::sdesc(b_addr + ks * 256u, 128u, K * 16u);
-          tc::mma_bf16(d_tmem, ad, bd, IDESC, ks > 0 ? 1u : 0u);
-        }
+        for (uint32_t ks = 0; ks < K / 16; ++ks)
+          tc::mma_bf16(c.tmem, tc::sdesc(c.a_addr + ks * 256u, 128u, K * 16u),
+                       tc::sdesc(b_addr + ks * 256u, 128u, K * 16u), IDESC, ks > 0 ? 1u : 0u);
         tc::mma_commit(c.bar_m);
       }
       ok = wg_all(c.wg, wait_bar(c.bar_m, ph_m));
@@ -225,37 +217,35 @@ __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const
     for (int c0 = 0; c0 < W; c0 += 32) {
       float v[32];
       if (K > 0) {
-        tc::tmem_ld32(d_tmem + c.lane_base + uint32_t(c0), v);
+        tc::tmem_ld32(c.tmem + c.lane_base + uint32_t(c0), v);
       } else {
 #pragma unroll
         for (int i = 0; i < 32; ++i) v[i] = 0.f;
       }
 #pragma unroll
-      for (int i = 0; i < 32; ++i) v[i] = tc::tanh_fast(v[i] + b[c0 + i]);
+      for (int i = 0; i < 32; i += 2) {
+        const float2 bb = *reinterpret_cast<const float2*>(b + c0 + i);
+        tc::add_f32x2(v[i], v[i + 1], bb.x, bb.y, v[i], v[i + 1]);
+      }
       if (!last) {
+        // next GEMM operand: tanh on packed bf16 pairs
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          uint4 u;
-          u.x = tc::pack_bf16x2(v[8 * q + 0], v[8 * q + 1]);
-          u.y = tc::pack_bf16x2(v[8 * q + 2], v[8 * q + 3]);
-          u.z = tc::pack_bf16x2(v[8 * q + 4], v[8 * q + 5]);
-          u.w = tc::pack_bf16x2(v[8 * q + 6], v[8 * q + 7]);
-          *reinterpret_cast<uint4*>(c.s_a + tc::canon_off(c.t, c0 + 8 * q, W)) = u;
+          uint32_t u[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) u[e] = tc::tanh_bf16x2(tc::pack_bf16x2(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]));
+          *reinterpret_cast<uint4*>(c.s_a + tc::canon_off(c.t, c0 + 8 * q, W)) = make_uint4(u[0], u[1], u[2], u[3]);
         }
       } else {
+        // last hidden layer in f32 feeding the f32 head: acc[o] += head[k][o] h[k]
 #pragma unroll
-        for (int o = 0; o < 8; ++o) {
-          const float4* hw = reinterpret_cast<const float4*>(head + o * W + c0);
-          float acc = out[o];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float4 h4 = hw[i];
-            acc = fmaf(h4.x, v[4 * i + 0], acc);
-            acc = fmaf(h4.y, v[4 * i + 1], acc);
-            acc = fmaf(h4.z, v[4 * i + 2], acc);
-            acc = fmaf(h4.w, v[4 * i + 3], acc);
-          }
-          out[o] = acc;
+        for (int i = 0; i < 32; ++i) {
+          const float h = tc::tanh_fast(v[i]);
+          const float4 w0 = head[(c0 + i) * 2], w1 = head[(c0 + i) * 2 + 1];
+          tc::fma_f32x2(w0.x, w0.y, h, h, acc[0], acc[1], acc[0], acc[1]);
+          tc::fma_f32x2(w0.z, w0.w, h, h, acc[2], acc[3], acc[2], acc[3]);
+          tc::fma_f32x2(w1.x, w1.y, h, h, acc[4], acc[5], acc[4], acc[5]);
+          tc::fma_f32x2(w1.z, w1.w, h, h, acc[6], acc[7], acc[6], acc[7]);
         }
       }
     }
@@ -264,21 +254,21 @@ __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const
     wg_sync(c.wg);
   }
 #pragma unroll
-  for (int o = 0; o < 8; ++o) out[o] += hbias[o];
+  for (int o = 0; o < 8; ++o) out[o] = acc[o] + hbias[o];
   return true;
 }
 
-// Shared set-up of both kernels: barriers and TMEM (4W columns: two
-// accumulators per warpgroup).
+// Shared set-up of both kernels: barriers and TMEM (NWG*W columns: one
+// accumulator per warpgroup).
 template <int W>
 __device__ __forceinline__ void setup(uint64_t* bars, uint32_t* s_tmem, int* s_abort) {
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 4; ++i) tc::mbar_init(tc::smem_u32(&bars[i]), 1);
+    for (int i = 0; i < 2 + NWG; ++i) tc::mbar_init(tc::smem_u32(&bars[i]), 1);
     tc::fence_mbar_init();
     *s_abort = 0;
   }
   if (threadIdx.x < 32) {
-    tc::tmem_alloc(tc::smem_u32(s_tmem), 4 * W);
+    tc::tmem_alloc(tc::smem_u32(s_tmem), NWG * W);
     tc::tmem_relinquish();
   }
   tc::fence_before_sync();
@@ -292,7 +282,7 @@ __device__ __forceinline__ void teardown(const TcView& tv, uint32_t tmem, int ab
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (threadIdx.x < 32) tc::tmem_dealloc(tmem, 4 * W);
+  if (threadIdx.x < 32) tc::tmem_dealloc(tmem, NWG * W);
 }
 
 __device__ __forceinline__ void load_slot(const TcView& tv, int p, uint32_t dst, uint32_t bar, int W, int L) {
@@ -301,12 +291,12 @@ __device__ __forceinline__ void load_slot(const TcView& tv, int p, uint32_t dst,
   tc::bulk_g2s(dst, tv.img + tv.img_off[p], S.bytes, bar);
 }
 
-// SLOTS: work item = (pair of 128-row tiles, slot p); writes the 8 raw
+// SLOTS: work item = (group of NWG 128-row tiles, slot p); writes the 8 raw
 // outputs of slot p for every row.
 template <int W>
 __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs ta) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[4];  // 0,1: weights; 2,3: MMA per warpgroup
+  __shared__ __align__(8) uint64_t bars[2 + NWG];  // 0,1: weights; 2..: MMA per warpgroup
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   const int wg = threadIdx.x / MT, t = threadIdx.x % MT;
@@ -317,7 +307,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
   c.tv = &tv;
   c.s_a = smem + img_stride * tv.nbuf + wg * (MT * tv.kmax * 2u);
   c.a_addr = tc::smem_u32(c.s_a);
-  c.tmem = s_tmem + uint32_t(wg) * 2 * W;
+  c.tmem = s_tmem + uint32_t(wg) * W;
   c.lane_base = uint32_t(t & ~31) << 16;
   c.bar_m = tc::smem_u32(&bars[2 + wg]);
   c.wg = wg;
@@ -325,21 +315,21 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
   const uint32_t bar_w = tc::smem_u32(&bars[0]);
   uint32_t ph_w = 0, ph_m = 0;
   const uint64_t n_rows = ta.rows.get();
-  const uint64_t n_pairs = (n_rows + 2 * MT - 1) / (2 * MT);
+  const uint64_t n_groups = (n_rows + NWG * MT - 1) / (NWG * MT);
   const int np = ta.p_hi - ta.p_lo;
-  const uint64_t n_items = n_pairs * uint64_t(np);
+  const uint64_t n_items = n_groups * uint64_t(np);
   for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int p = ta.p_lo + int(it / n_pairs);
-    const uint64_t pair = it % n_pairs;
+    const int p = ta.p_lo + int(it / n_groups);
+    const uint64_t grp = it % n_groups;
     const SlotLayout S = slot_layout(p, W, tv.L);
     if (threadIdx.x == 0) load_slot(tv, p, tc::smem_u32(s_img), bar_w, W, tv.L);
-    const uint64_t r = (pair * 2 + wg) * MT + t;
+    const uint64_t r = (grp * NWG + wg) * MT + t;
     const bool valid = r < n_rows;
     const uint64_t x = valid ? ta.x[r] : 0ull;
     bool ok = __syncthreads_and(wait_bar(bar_w, ph_w));
     ph_w ^= 1;
     float out[8];
-    if (ok && (pair * 2 + wg) * MT < n_rows) ok = tile_slot<W>(c, ph_m, p, x, S, tc::smem_u32(s_img), s_img, out);
+    if (ok && (grp * NWG + wg) * MT < n_rows) ok = tile_slot<W>(c, ph_m, p, x, S, tc::smem_u32(s_img), s_img, out);
     if (!ok) s_abort = 1;
     if (ok && valid) {
       float4* dst = reinterpret_cast<float4*>(ta.raw + (r * np + (p - ta.p_lo)) * 8);
@@ -354,124 +344,146 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
   teardown<W>(tv, s_tmem, s_abort);
 }
 
-// SUFFIX: chunks of 2*TPW tiles per CTA (tiles b, b+G, ... of the rows
-// sorted by first differing slot), slot-outer so that each slot's weights are
-// loaded once per chunk; the next slot's image is prefetched when two
-// buffers fit.
+// SUFFIX (weight-stationary): the connected determinants sorted by first
+// differing slot j make, for every slot p, the rows that need slot p (those
+// with j < p) a prefix of the sorted order.  The grid is split among the
+// slots in proportion to their tiles; a CTA loads its slot's weight image
+// once and its warpgroups stream tiles of that slot independently (no
+// CTA-wide barrier in the loop).  Each (row, slot) term goes to T[row][p];
+// the local-energy kernel adds a row's terms to the parent's prefix.
 template <int W>
-__global__ void __launch_bounds__(NT, 1) mlp_tc_suffix_kernel(TcView tv, HamView hv, TileArgs ta) {
+__global__ void __launch_bounds__(NT, 1) mlp_tc_ws_kernel(TcView tv, HamView hv, const uint64_t* __restrict__ xp,
+                                                         const uint32_t* __restrict__ perm,
+                                                         const uint32_t* __restrict__ offsets,
+                                                         float2* __restrict__ T) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bars[4];
+  __shared__ __align__(8) uint64_t bars[2 + NWG];
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
-  __shared__ int s_jmin[2 * TPW];
   const int wg = threadIdx.x / MT, t = threadIdx.x % MT;
   const int n = tv.n;
   setup<W>(bars, &s_tmem, &s_abort);
   const uint32_t img_stride = round_up(tv.max_img, 1024u);
   Ctx c;
   c.tv = &tv;
-  c.s_a = smem + img_stride * tv.nbuf + wg * (MT * tv.kmax * 2u);
+  c.s_a = smem + img_stride + wg * (MT * tv.kmax * 2u);
   c.a_addr = tc::smem_u32(c.s_a);
-  c.tmem = s_tmem + uint32_t(wg) * 2 * W;
+  c.tmem = s_tmem + uint32_t(wg) * W;
   c.lane_base = uint32_t(t & ~31) << 16;
   c.bar_m = tc::smem_u32(&bars[2 + wg]);
   c.wg = wg;
   c.t = t;
-  uint32_t ph_w[2] = {0, 0}, ph_m = 0;
-  const uint64_t n_rows = ta.rows.get();
-  const uint64_t n_tiles = (n_rows + MT - 1) / MT;
-  const uint64_t G = gridDim.x;
-  for (uint64_t chunk = 0;; ++chunk) {
-    const uint64_t first = blockIdx.x + chunk * (2 * TPW) * G;
-    if (first >= n_tiles) break;
-    uint64_t x[TPW];
-    int j[TPW];
-    float la[TPW], phs[TPW];
-    uint32_t oi[TPW];
-    if (threadIdx.x < 2 * TPW) s_jmin[threadIdx.x] = n;
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < TPW; ++q) {
-      const uint64_t tile = first + uint64_t(wg + 2 * q) * G;
+  // partition of the grid among the slots (same result in every CTA)
+  uint64_t tiles[ANQS_MAX_ORB];
+  uint64_t total = 0;
+  int S = 0;
+  for (int p = 0; p < n; ++p) {
+    tiles[p] = (uint64_t(offsets[p]) + MT - 1) / MT;
+    total += tiles[p];
+    S += tiles[p] ? 1 : 0;
+  }
+  int my_p = -1;
+  uint64_t li = 0, gp = 0;
+  if (total) {
+    const uint64_t G = gridDim.x, spare = G > uint64_t(S) ? G - S : 0;
+    uint64_t start = 0;
+    for (int p = 0; p < n; ++p) {
+      if (!tiles[p]) continue;
+      const uint64_t g = 1 + spare * tiles[p] / total;
+      if (blockIdx.x >= start && blockIdx.x < start + g) {
+        my_p = p;
+        li = blockIdx.x - start;
+        gp = g;
+      }
+      start += g;
+    }
+  }
+  if (my_p >= 0) {
+    const int p = my_p;
+    const SlotLayout Sl = slot_layout(p, W, tv.L);
+    const uint32_t img_addr = tc::smem_u32(smem);
+    if (threadIdx.x == 0) load_slot(tv, p, img_addr, tc::smem_u32(&bars[0]), W, tv.L);
+    bool ok = __syncthreads_and(wait_bar(tc::smem_u32(&bars[0]), 0));
+    const uint64_t rows = offsets[p];
+    uint32_t ph_m = 0;
+    for (uint64_t tile = li + gp * wg; ok && tile < tiles[p]; tile += gp * NWG) {
       const uint64_t r = tile * MT + t;
-      x[q] = 0;
-      j[q] = n;
-      la[q] = phs[q] = 0.f;
-      oi[q] = 0;
-      if (tile < n_tiles && r < n_rows) {
-        const uint32_t row = ta.perm[r];
-        oi[q] = row;
-        x[q] = ta.x[row];
-        j[q] = ta.js[row];
-        const float* cc = ta.cache + (uint64_t(row / ta.K) * n + j[q]) * CACHE_F;
-        const int vj = int((x[q] >> (2 * j[q])) & 3ull);
-        la[q] = cc[0] + cc[2 + vj];
-        phs[q] = cc[1] + cc[6 + vj];
-        atomicMin(&s_jmin[wg + 2 * q], j[q]);
+      const bool valid = r < rows;
+      const uint32_t row = valid ? perm[r] : 0u;
+      const uint64_t x = valid ? xp[row] : 0ull;
+      float out[8];
+      ok = tile_slot<W>(c, ph_m, p, x, Sl, img_addr, smem, out);
+      if (ok && valid) {
+        const uint64_t pm = (1ull << (2 * p)) - 1ull;
+        const int a = __popcll(x & pm & 0x5555555555555555ull);
+        const int bb = __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull);
+        const unsigned mk = slot_mask(hv, p, a, bb);
+        float mx = -INFINITY;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if ((mk >> u) & 1u) mx = fmaxf(mx, out[u]);
+        float sum = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if ((mk >> u) & 1u) sum += __expf(out[u] - mx);
+        const int v = int((x >> (2 * p)) & 3ull);
+        const float ov = (v == 0) ? out[0] : (v == 1) ? out[1] : (v == 2) ? out[2] : out[3];
+        const float pv = (v == 0) ? out[4] : (v == 1) ? out[5] : (v == 2) ? out[6] : out[7];
+        const float lse = mx + __logf(sum);  // same expression order as finalize_kernel
+        T[uint64_t(row) * n + p] = make_float2(((mk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY, pv);
       }
     }
-    __syncthreads();
-    int jlo = n;
-    for (int i = 0; i < 2 * TPW; ++i) jlo = min(jlo, s_jmin[i]);
-    const int p0 = jlo + 1;
-    const uint32_t img0 = tc::smem_u32(smem);
-    if (threadIdx.x == 0 && p0 < n) load_slot(tv, p0, img0, tc::smem_u32(&bars[0]), W, tv.L);
-    for (int p = p0; p < n; ++p) {
-      const int b = (tv.nbuf == 2) ? ((p - p0) & 1) : 0;
-      const uint32_t img_addr = img0 + uint32_t(b) * img_stride;
-      const unsigned char* img = smem + b * img_stride;
-      if (tv.nbuf == 2 && threadIdx.x == 0 && p + 1 < n)
-        load_slot(tv, p + 1, img0 + uint32_t(b ^ 1) * img_stride, tc::smem_u32(&bars[b ^ 1]), W, tv.L);
-      bool ok = __syncthreads_and(wait_bar(tc::smem_u32(&bars[b]), ph_w[b]));
-      ph_w[b] ^= 1;
-      const SlotLayout S = slot_layout(p, W, tv.L);
-#pragma unroll
-      for (int q = 0; q < TPW; ++q) {
-        if (!ok || s_jmin[wg + 2 * q] >= p) continue;  // uniform per warpgroup
-        float out[8];
-        ok = tile_slot<W>(c, ph_m, p, x[q], S, img_addr, img, out);
-        if (ok && j[q] < p) {
-          const uint64_t pm = (1ull << (2 * p)) - 1ull;
-          const int a = __popcll(x[q] & pm & 0x5555555555555555ull);
-          const int bb = __popcll(x[q] & pm & 0xAAAAAAAAAAAAAAAAull);
-          const unsigned mk = slot_mask(hv, p, a, bb);
-          float mx = -INFINITY;
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if ((mk >> u) & 1u) mx = fmaxf(mx, out[u]);
-          float s = 0.f;
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if ((mk >> u) & 1u) s += __expf(out[u] - mx);
-          const int v = int((x[q] >> (2 * p)) & 3ull);
-          const float ov = (v == 0) ? out[0] : (v == 1) ? out[1] : (v == 2) ? out[2] : out[3];
-          const float pv = (v == 0) ? out[4] : (v == 1) ? out[5] : (v == 2) ? out[6] : out[7];
-          const float lse = mx + __logf(s);  // same expression order as finalize_kernel
-          la[q] += ((mk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY;
-          phs[q] += pv;
-        }
-      }
-      if (!ok) s_abort = 1;
-      tc::fence_async_smem();
-      tc::fence_before_sync();
-      __syncthreads();
-      if (s_abort) break;
-      if (tv.nbuf == 1 && threadIdx.x == 0 && p + 1 < n) load_slot(tv, p + 1, img0, tc::smem_u32(&bars[0]), W, tv.L);
-    }
-    if (s_abort) break;
-#pragma unroll
-    for (int q = 0; q < TPW; ++q) {
-      const uint64_t tile = first + uint64_t(wg + 2 * q) * G;
-      const uint64_t r = tile * MT + t;
-      if (tile < n_tiles && r < n_rows) {
-        ta.la[oi[q]] = la[q];
-        ta.ph[oi[q]] = phs[q];
-      }
-    }
-    __syncthreads();  // s_jmin is reset by the next chunk
+    if (!ok) s_abort = 1;
   }
   teardown<W>(tv, s_tmem, s_abort);
+}
+
+// One warp per parent x: log psi(x') = parent prefix up to slot j + parent
+// slot-j term of v'_j + the terms T[x'][p] of the slots p > j; then
+// E_loc(x) = H_xx + sum H_xx' exp(log psi(x') - log psi(x)) with the ratio in
+// float32 and the sum in FP64.
+__global__ void eloc_assemble_kernel(int n, uint32_t K, Count n_x_, const uint64_t* __restrict__ xp,
+                                     const uint8_t* __restrict__ js, const float* __restrict__ cache,
+                                     const float2* __restrict__ T, const double* __restrict__ hval,
+                                     const double* __restrict__ hdiag, const float* __restrict__ la_x,
+                                     const float* __restrict__ ph_x, double* __restrict__ ere,
+                                     double* __restrict__ eim) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t n_x = n_x_.get();
+  const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
+  for (uint64_t l = blockIdx.x * uint64_t(blockDim.x >> 5) + (threadIdx.x >> 5); l < n_x; l += warps) {
+    const float lx = la_x[l], px = ph_x[l];
+    double re = 0.0, im = 0.0;
+    for (uint32_t k = lane; k < K; k += 32) {
+      const uint64_t row = l * K + k;
+      const int j = js[row];
+      const uint64_t x = xp[row];
+      const float* cc = cache + (l * n + j) * CACHE_F;
+      const int vj = int((x >> (2 * j)) & 3ull);
+      float la = cc[0] + cc[2 + vj], ph = cc[1] + cc[6 + vj];
+      for (int p = j + 1; p < n; ++p) {
+        const float2 tv = T[row * n + p];
+        la += tv.x;
+        ph += tv.y;
+      }
+      const double h = hval[row];
+      const float r = expf(la - lx);
+      float s, co;
+      sincosf(ph - px, &s, &co);
+      const double hr = h * double(r);
+      re = fma(hr, double(co), re);
+      im = fma(hr, double(s), im);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, o);
+      im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0) {
+      ere[l] = hdiag[l] + re;
+      eim[l] = im;
+    }
+  }
 }
 
 // Per row: masked half-log-probabilities from the raw slot outputs, prefix
@@ -530,13 +542,17 @@ __global__ void js_hist_kernel(const uint8_t* __restrict__ js, Count m_, int n, 
     if (h[i]) atomicAdd(&hist[i], h[i]);
 }
 
-__global__ void js_offsets_kernel(const uint32_t* __restrict__ hist, int n, uint32_t* __restrict__ cursor) {
+// cursor[i] = offsets[i] = rows with first slot < i (exclusive prefix sums)
+__global__ void js_offsets_kernel(const uint32_t* __restrict__ hist, int n, uint32_t* __restrict__ cursor,
+                                  uint32_t* __restrict__ offsets) {
   if (threadIdx.x == 0) {
     uint32_t acc = 0;
     for (int i = 0; i < n; ++i) {
       cursor[i] = acc;
+      offsets[i] = acc;
       acc += hist[i];
     }
+    offsets[n] = acc;
   }
 }
 
@@ -572,7 +588,7 @@ int num_sms() {
 constexpr size_t kSmemLimit = 227 * 1024;
 
 size_t smem_bytes(const TcView& tv, int nbuf) {
-  return size_t(round_up(tv.max_img, 1024u)) * nbuf + 2ull * MT * tv.kmax * 2u;
+  return size_t(round_up(tv.max_img, 1024u)) * nbuf + size_t(NWG) * MT * tv.kmax * 2u;
 }
 
 TcView make_view(const anqs_model* M) {
@@ -594,7 +610,7 @@ template <int W>
 int launch_slots_w(const TcView& tv, const TileArgs& ta, cudaStream_t s) {
   const uint64_t max_rows = ta.rows.n;
   const size_t sm = smem_bytes(tv, 1);
-  const uint64_t items = (max_rows + 2 * MT - 1) / (2 * MT) * uint64_t(ta.p_hi - ta.p_lo);
+  const uint64_t items = (max_rows + NWG * MT - 1) / (NWG * MT) * uint64_t(ta.p_hi - ta.p_lo);
   const unsigned grid = unsigned(std::min<uint64_t>(items ? items : 1, uint64_t(num_sms())));
   TcView v1 = tv;
   v1.nbuf = 1;
@@ -611,17 +627,6 @@ int launch_slots(const anqs_model* M, const TileArgs& ta, cudaStream_t s, int pr
   return tv.W == 128 ? launch_slots_w<128>(tv, ta, s) : launch_slots_w<64>(tv, ta, s);
 }
 
-template <int W>
-int launch_suffix_w(const TcView& tv, const HamView& hv, const TileArgs& ta, cudaStream_t s) {
-  const size_t sm = smem_bytes(tv, tv.nbuf);
-  const uint64_t tiles = (ta.rows.n + MT - 1) / MT;
-  const unsigned grid = unsigned(std::min<uint64_t>(tiles ? tiles : 1, uint64_t(num_sms())));
-  ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_suffix_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-  mlp_tc_suffix_kernel<W><<<grid, NT, sm, s>>>(tv, hv, ta);
-  ANQS_LAUNCHED("mlp_tc_suffix_kernel");
-  return ANQS_OK;
-}
-
 int launch_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
                     float* cache, cudaStream_t s) {
   uint64_t blocks = (n_x.n + 127) / 128;
@@ -636,8 +641,9 @@ struct ElocWs {
   double* hv;
   uint8_t* js;
   double* hd;
-  float *la_x, *ph_x, *raw, *cache, *la_p, *ph_p;
-  uint32_t *perm, *hist, *cursor;
+  float *la_x, *ph_x, *raw, *cache;
+  float2* T;
+  uint32_t *perm, *hist, *cursor, *offsets;
 };
 
 size_t plan_eloc(const anqs_ham* H, uint64_t n_x, Arena& A, ElocWs& w) {
@@ -650,12 +656,22 @@ size_t plan_eloc(const anqs_ham* H, uint64_t n_x, Arena& A, ElocWs& w) {
   w.ph_x = A.take<float>(n_x);
   w.raw = A.take<float>(n_x * H->v.n * 8);
   w.cache = A.take<float>(n_x * H->v.n * CACHE_F);
-  w.la_p = A.take<float>(m);
-  w.ph_p = A.take<float>(m);
+  w.T = A.take<float2>(m * H->v.n);
   w.perm = A.take<uint32_t>(m);
   w.hist = A.take<uint32_t>(ANQS_MAX_ORB);
   w.cursor = A.take<uint32_t>(ANQS_MAX_ORB);
+  w.offsets = A.take<uint32_t>(ANQS_MAX_ORB + 1);
   return A.off;
+}
+
+template <int W>
+int launch_ws_w(const TcView& tv, const HamView& hv, const ElocWs& w, cudaStream_t s) {
+  const size_t sm = smem_bytes(tv, 1);
+  const unsigned grid = unsigned(std::max(num_sms(), tv.n));
+  ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_ws_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+  mlp_tc_ws_kernel<W><<<grid, NT, sm, s>>>(tv, hv, w.xp, w.perm, w.offsets, w.T);
+  ANQS_LAUNCHED("mlp_tc_ws_kernel");
+  return ANQS_OK;
 }
 
 }  // namespace
@@ -769,26 +785,26 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count
     unsigned g = unsigned(std::min<uint64_t>((m + 255) / 256, 152 * 4));
     js_hist_kernel<<<g ? g : 1, 256, 0, s>>>(w.js, mc, H->v.n, w.hist);
     ANQS_LAUNCHED("js_hist_kernel");
-    js_offsets_kernel<<<1, 32, 0, s>>>(w.hist, H->v.n, w.cursor);
+    js_offsets_kernel<<<1, 32, 0, s>>>(w.hist, H->v.n, w.cursor, w.offsets);
     ANQS_LAUNCHED("js_offsets_kernel");
     js_scatter_kernel<<<g ? g : 1, 256, 0, s>>>(w.js, mc, w.cursor, w.perm);
     ANQS_LAUNCHED("js_scatter_kernel");
   }
   {
-    TileArgs ta{};
-    ta.x = w.xp;
-    ta.rows = mc;
-    ta.perm = w.perm;
-    ta.js = w.js;
-    ta.cache = w.cache;
-    ta.K = uint32_t(K);
-    ta.la = w.la_p;
-    ta.ph = w.ph_p;
     TcView tv = make_view(M);
     ProfScope ps(PROF_TC_SUFFIX, s);
-    ANQS_TRY(tv.W == 128 ? launch_suffix_w<128>(tv, H->v, ta, s) : launch_suffix_w<64>(tv, H->v, ta, s));
+    ANQS_TRY(tv.W == 128 ? launch_ws_w<128>(tv, H->v, w, s) : launch_ws_w<64>(tv, H->v, w, s));
   }
-  return launch_eloc_sum(H->v, n_x, w.hv, w.hd, w.la_x, w.ph_x, w.la_p, w.ph_p, ere, eim, s);
+  {
+    ProfScope ps(PROF_TC_ELOC, s);
+    uint64_t blocks = (n_x.n + 7) / 8;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    eloc_assemble_kernel<<<unsigned(blocks ? blocks : 1), 256, 0, s>>>(H->v.n, uint32_t(K), n_x, w.xp, w.js,
+                                                                      w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x,
+                                                                      ere, eim);
+    ANQS_LAUNCHED("eloc_assemble_kernel");
+  }
+  return ANQS_OK;
 }
 
 }  // namespace anqs
