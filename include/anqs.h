@@ -192,10 +192,13 @@ ANQS_API int anqs_logpsi(const anqs_model* model, const anqs_ham* ham, const uin
  *
  * Walks the slot tree breadth first.  A node with n_in samples splits them
  * among its allowed outcomes by n_in uniform draws u_i: sample i takes the
- * first allowed v with u_i < C_v, C_v the FP64 running sum of the masked
+ * first allowed v with u_i < C_v, C_v the running sum of the masked
  * conditional over allowed outcomes in ascending v (the last allowed v if
- * rounding leaves u_i >= C_last).  The masked conditional is evaluated in
- * FP64 as exp(l_v - max) / sum from the network's float32 logits.  u_i comes
+ * rounding leaves u_i >= C_last).  The masked conditional is evaluated from
+ * the network's float32 logits in float32 by a fixed sequence of IEEE
+ * operations without fused multiply-adds: e_v = exp(l_v - max) by Cody-Waite
+ * reduction and a degree-7 Taylor polynomial, the sum over allowed v in
+ * ascending order, p_v = e_v / sum, C_v the running sum.  u_i comes
  * from Philox4x64-10 (Salmon et al., SC'11) with counter (prefix, i >> 2,
  * slot, counter) and key (seed, 0), word i & 3, top 53 bits times 2^-53.
  * Children with zero samples are dropped; no sample is lost (MU), so the

@@ -15,9 +15,16 @@ the procedure; reading): the node draws n_in uniforms u_i, i = 0..n_in-1,
 from Philox4x64-10 with counter (prefix, i >> 2, p, counter) and key
 (seed, 0), taking word i & 3 of each block; a uniform is the top 53 bits of
 the word times 2^-53.  Sample i goes to the first allowed outcome v with
-u_i < C_v, C_v the FP64 running sum of p~ over allowed outcomes in ascending
-v (the last allowed outcome if rounding leaves u_i >= C_last).  p~ is the
-softmax over allowed outcomes, evaluated in FP64 as exp(l_v - max) / sum.
+u_i < C_v, C_v the running sum of p~ over allowed outcomes in ascending v
+(the last allowed outcome if rounding leaves u_i >= C_last).  p~ is the
+softmax over allowed outcomes of the float32 logits, and it is evaluated in
+float32 by a fixed sequence of IEEE operations (reading: the precision in
+which the split decision is taken): e_v = exp(l_v - max) by Cody-Waite
+reduction with ln2 split in two parts and the degree-7 Taylor polynomial of
+e^r, s = sum of e_v in ascending v, p~_v = e_v / s, C_v = running sum.  The
+outcome is an integer decided by floating point, so both implementations
+take it in the same precision; the conditional's own error (about 1e-7
+relative) is far below sampling noise.
 Children are emitted in ascending v, so the leaves come out in lexicographic
 order of (v_0, v_1, ..., v_{n-1}).
 
@@ -32,15 +39,40 @@ from .anqs import allowed_masks
 from .philox import philox4x64_np, uniform_from_word
 
 
-def split_probabilities(logits: np.ndarray, mask: np.ndarray) -> np.ndarray:
-    """p~ of one node from its 4 modulus logits and allowed mask (FP64)."""
-    l = np.asarray(logits, dtype=np.float64)
+F32 = np.float32
+INV_LN2 = F32(1.44269502162933349609375)
+LN2_HI = F32(0.693145751953125)       # 16 significant bits: k * LN2_HI is exact
+LN2_LO = F32(1.428606765330187045e-06)
+TAYLOR = [F32(1.0), F32(1.0), F32(0.5), F32(1.0) / F32(6.0), F32(1.0) / F32(24.0), F32(1.0) / F32(120.0),
+          F32(1.0) / F32(720.0), F32(1.0) / F32(5040.0)]
+
+
+def exp_det(x) -> np.float32:
+    """e^x for float32 x <= 0: k = floor(x / ln2 + 1/2), r = x - k ln2 (two
+    parts), Horner on the degree-7 Taylor polynomial, times 2^k; every step a
+    single rounded float32 operation."""
+    x = F32(x)
+    if x < F32(-80.0):
+        return F32(0.0)
+    k = np.floor(F32(F32(x * INV_LN2) + F32(0.5)))
+    r = F32(F32(x - F32(k * LN2_HI)) - F32(k * LN2_LO))
+    q = TAYLOR[7]
+    for c in TAYLOR[6::-1]:
+        q = F32(F32(q * r) + c)
+    return F32(np.ldexp(q, int(k)))
+
+
+def split_probabilities(logits, mask) -> np.ndarray:
+    """p~ of one node from its 4 modulus logits (rounded to float32) and
+    allowed mask, in float32 (zero for masked outcomes)."""
+    l = np.asarray(logits, dtype=np.float64).astype(np.float32)
     m = max(l[v] for v in range(4) if mask[v])
-    e = np.array([np.exp(l[v] - m) if mask[v] else 0.0 for v in range(4)])
-    s = 0.0
+    e = [exp_det(F32(l[v] - m)) if mask[v] else F32(0.0) for v in range(4)]
+    s = F32(0.0)
     for v in range(4):
-        s += e[v]
-    return e / s
+        if mask[v]:
+            s = F32(s + e[v])
+    return np.array([F32(e[v] / s) if mask[v] else F32(0.0) for v in range(4)], dtype=np.float32)
 
 
 def node_uniforms(prefix: int, count: int, p: int, seed: int, counter: int) -> np.ndarray:
@@ -56,12 +88,12 @@ def split_node(probs: np.ndarray, mask, u: np.ndarray, tol: float = 0.0):
     """Counts per outcome, the smallest |u - C_v| over the draws and the
     number of draws closer than tol to a boundary C_v."""
     C = np.zeros(4)
-    run = 0.0
+    run = F32(0.0)
     allowed = [v for v in range(4) if mask[v]]
     for v in range(4):
         if mask[v]:
-            run += probs[v]
-        C[v] = run
+            run = F32(run + probs[v])
+        C[v] = float(run)
     out = np.full(len(u), allowed[-1], dtype=np.int64)
     undecided = np.ones(len(u), dtype=bool)
     for v in allowed:

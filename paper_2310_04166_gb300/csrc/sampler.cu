@@ -4,7 +4,8 @@
 // (slots < p) with their sample counts.  Per level:
 //   1. the network's slot-p outputs for every frontier prefix;
 //   2. per node: allowed outcomes from the IsPhys slot mask, the masked
-//      conditional in FP64 and its running sums C_v;
+//      conditional and its running sums C_v (float32 in a fixed order of IEEE
+//      operations, see split_thresholds);
 //   3. the node's n_in uniforms (Philox4x64-10, one block of four per
 //      thread; counter (prefix, i >> 2, p, counter), key (seed, 0)) are
 //      compared with C_v and the outcome counts are aggregated per warp
@@ -64,6 +65,59 @@ __global__ void init_kernel(uint64_t* pre, uint64_t* cnt, uint64_t* n_front, uin
   for (int v = 0; v < 4; ++v) child[v] = 0;
 }
 
+// ---- the split conditional, reproducible bit for bit -------------------------
+// exp(x) for x <= 0 in float32 from IEEE operations only, in a fixed order
+// and without fused multiply-adds: Cody-Waite reduction x = k ln2 + r (ln2
+// split into a 16-bit head and a tail) and the degree-7 Taylor polynomial of
+// e^r, |r| <= ln2/2 (truncation below 6e-9 relative).  The oracle evaluates
+// the same sequence with numpy float32.
+__device__ __forceinline__ float exp_det(float x) {
+  if (x < -80.f) return 0.f;
+  const float k = floorf(__fadd_rn(__fmul_rn(x, 1.44269502162933349609375f), 0.5f));
+  const float r = __fsub_rn(__fsub_rn(x, __fmul_rn(k, 0.693145751953125f)), __fmul_rn(k, 1.428606765330187045e-06f));
+  float q = 1.f / 5040.f;
+  q = __fadd_rn(__fmul_rn(q, r), 1.f / 720.f);
+  q = __fadd_rn(__fmul_rn(q, r), 1.f / 120.f);
+  q = __fadd_rn(__fmul_rn(q, r), 1.f / 24.f);
+  q = __fadd_rn(__fmul_rn(q, r), 1.f / 6.f);
+  q = __fadd_rn(__fmul_rn(q, r), 0.5f);
+  q = __fadd_rn(__fmul_rn(q, r), 1.f);
+  q = __fadd_rn(__fmul_rn(q, r), 1.f);
+  return ldexpf(q, int(k));
+}
+
+// ceil(C 2^53) for a float32 C in [0, 1], from its bits
+__device__ __forceinline__ uint64_t thr_from_float(float C) {
+  const uint32_t b = __float_as_uint(C);
+  const uint32_t e = (b >> 23) & 0xFFu, mant = b & 0x7FFFFFu;
+  if (e == 0) return mant ? 1ull : 0ull;  // subnormal: 0 < C 2^53 < 1
+  const uint64_t m24 = uint64_t(mant | 0x800000u);
+  if (e >= 97) return m24 << (e - 97);
+  const uint32_t sh = 97 - e;
+  if (sh >= 25) return 1ull;
+  return (m24 + (1ull << sh) - 1ull) >> sh;
+}
+
+// Thresholds T_v of one node: running sums C_v of the softmax of the
+// allowed logits (float32, fixed order), T_v = ceil(C_v 2^53), so that a
+// draw with word w goes to the first allowed v with (w >> 11) < T_v, i.e.
+// u = (w >> 11) 2^-53 < C_v.
+__device__ __forceinline__ void split_thresholds(const float* l, unsigned mk, uint64_t T[4]) {
+  float m = -INFINITY;
+  for (int v = 0; v < 4; ++v)
+    if ((mk >> v) & 1u) m = fmaxf(m, l[v]);
+  float e[4], s = 0.f;
+  for (int v = 0; v < 4; ++v) {
+    e[v] = ((mk >> v) & 1u) ? exp_det(__fsub_rn(l[v], m)) : 0.f;
+    if ((mk >> v) & 1u) s = __fadd_rn(s, e[v]);
+  }
+  float run = 0.f;
+  for (int v = 0; v < 4; ++v) {
+    if ((mk >> v) & 1u) run = __fadd_rn(run, __fdiv_rn(e[v], s));
+    T[v] = thr_from_float(run);
+  }
+}
+
 __device__ __forceinline__ int popc_alpha(uint64_t x, int p) {
   uint64_t m = (p >= 32) ? ~0ull : ((1ull << (2 * p)) - 1ull);
   return __popcll(x & m & 0x5555555555555555ull);
@@ -82,21 +136,10 @@ __global__ void prep_kernel(HamView hv, int p, const uint64_t* __restrict__ pre,
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < nf; i += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t x = pre[i];
     unsigned mk = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p));
-    const float* l = logits + i * 8;
-    double m = -INFINITY;
-    for (int v = 0; v < 4; ++v)
-      if ((mk >> v) & 1u) m = fmax(m, double(l[v]));
-    double e[4], s = 0.0;
+    uint64_t T[4];
+    split_thresholds(logits + i * 8, mk, T);
     for (int v = 0; v < 4; ++v) {
-      e[v] = ((mk >> v) & 1u) ? exp(double(l[v]) - m) : 0.0;
-      s += e[v];
-    }
-    // u < C_v  <=>  (word >> 11) < ceil(C_v 2^53) exactly (u = (word >> 11) 2^-53),
-    // so the draws compare integers against these thresholds
-    double run = 0.0;
-    for (int v = 0; v < 4; ++v) {
-      if ((mk >> v) & 1u) run += e[v] / s;
-      thr[i * 4 + v] = uint64_t(ceil(run * 9007199254740992.0));
+      thr[i * 4 + v] = T[v];
       child[i * 4 + v] = 0;
     }
     allowed[i] = uint8_t(mk);
@@ -318,8 +361,8 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* sh
 // network has written the slot logits of every frontier prefix):
 //   - every CTA scans the per-node draw-block counts in its own shared memory;
 //   - for each window of SMALL_T draw blocks the CTA computes, for the nodes
-//     the window touches, the masked conditional in FP64 and the integer
-//     thresholds T_v = ceil(C_v 2^53) (u < C_v  <=>  (word >> 11) < T_v);
+//     the window touches, the masked conditional (split_thresholds) and the
+//     integer thresholds T_v = ceil(C_v 2^53) (u < C_v <=> (word >> 11) < T_v);
 //   - the draws compare Philox words with the thresholds and add
 //     warp-segment sums of the outcome counts to the children;
 //   - the last CTA to finish compacts the children, in (node, outcome)
@@ -372,20 +415,7 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
       const int i = n_lo + threadIdx.x;
       const uint64_t x = pre[i];
       const unsigned mk = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p));
-      const float* l = logits + uint64_t(i) * 8;
-      double m = -INFINITY;
-      for (int v = 0; v < 4; ++v)
-        if ((mk >> v) & 1u) m = fmax(m, double(l[v]));
-      double e[4], s = 0.0;
-      for (int v = 0; v < 4; ++v) {
-        e[v] = ((mk >> v) & 1u) ? exp(double(l[v]) - m) : 0.0;
-        s += e[v];
-      }
-      double run = 0.0;
-      for (int v = 0; v < 4; ++v) {
-        if ((mk >> v) & 1u) run += e[v] / s;
-        s_thr[threadIdx.x][v] = uint64_t(ceil(run * 9007199254740992.0));
-      }
+      split_thresholds(logits + uint64_t(i) * 8, mk, s_thr[threadIdx.x]);
       s_mk[threadIdx.x] = uint8_t(mk);
     }
     __syncthreads();

@@ -52,3 +52,24 @@ def test_single_sample_and_forced_path():
     assert len(xs) == 1 and cnt[0] == 1
     xs, cnt, _ = sample(model, molecular_isphys(n, 3, 3), n, 777, seed=5)
     assert xs.tolist() == [0b111111] and cnt.tolist() == [777]
+
+
+def test_deterministic_exp_accuracy():
+    """exp_det is within one float32 ulp (2^-23 relative) of e^x on [-80, 0]
+    and exact at 0; the conditional it feeds sums to 1 to float32 rounding."""
+    import math
+    from oracle.sampler import exp_det, split_probabilities
+    assert exp_det(0.0) == 1.0
+    xs = np.concatenate([np.linspace(-80.0, 0.0, 4001), -np.logspace(-8, 1, 500)]).astype(np.float32)
+    rel = max(abs(float(exp_det(x)) - math.exp(float(x))) / math.exp(float(x)) for x in xs)
+    assert rel < 2.0 ** -23
+    rng = np.random.default_rng(0)
+    for _ in range(200):
+        l = rng.normal(0, 3, 4)
+        mask = rng.random(4) < 0.7
+        if not mask.any():
+            mask[rng.integers(4)] = True
+        p = split_probabilities(l, mask)
+        assert abs(float(p.sum()) - 1.0) < 4 * 2.0 ** -24 and np.all(p[~mask] == 0)
+        ref = np.where(mask, np.exp(l - l[mask].max()), 0.0)
+        assert np.abs(p - ref / ref.sum()).max() < 1e-6
