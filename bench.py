@@ -182,8 +182,8 @@ def main():
     ap.add_argument("--workload", default="h2o")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernel-case", action="store_true",
-                    help="one FP32-form sampling pass, then one local-energy call in the chosen form "
-                         "(the launch sequence to capture with ncu), then exit")
+                    help="one FP32-form sampling pass, then one local-energy and one gradient call in the "
+                         "chosen form (the launch sequence to capture with ncu), then exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -220,6 +220,7 @@ def main():
         m32 = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form="fp32")
         xk, nk = A.sample(m32, ham, Ns, seed=99)
         ek = A.local_energy(model, ham, xk, nk)
+        A.grad(model, ham, xk, nk, ek[0], ek[1], ek[2])
         torch.cuda.synchronize()
         print(json.dumps({"kernel_case": args.workload, "form": form, "n_unique": xk.numel(),
                           "E": float(ek[2][0])}))

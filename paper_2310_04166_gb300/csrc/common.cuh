@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cstddef>
+#include <utility>
 #include <vector>
 
 #include "anqs.h"
@@ -56,11 +57,32 @@ struct ProfScope {
     if (e_ != cudaSuccess) return anqs::cuda_error(e_, #call, __FILE__, __LINE__); \
   } while (0)
 
+#define ANQS_CUDA_LAUNCH(what, call)                                     \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return anqs::cuda_error(e_, what, __FILE__, __LINE__); \
+  } while (0)
+
 #define ANQS_LAUNCHED(what)                                              \
   do {                                                                   \
     anqs::note_launch();                                                 \
     cudaError_t e_ = cudaGetLastError();                                 \
     if (e_ != cudaSuccess) return anqs::cuda_error(e_, what, __FILE__, __LINE__); \
+  } while (0)
+
+// Programmatic dependent launch: every library kernel waits for the
+// previous kernel in the stream to complete (and its writes to be visible)
+// before it reads anything, and only then lets the next kernel be scheduled.
+// So the part of a kernel placed before ANQS_PDL_WAIT() (its prologue) runs
+// while the previous kernel may still execute, but after the kernel before
+// that has completed: a prologue may read data written two or more kernels
+// earlier (e.g. packed weights) and set up TMEM and shared memory.
+#define ANQS_PDL_TRIGGER() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
+#define ANQS_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
+#define ANQS_PDL_ENTRY() \
+  do {                   \
+    ANQS_PDL_WAIT();     \
+    ANQS_PDL_TRIGGER();  \
   } while (0)
 
 #define ANQS_TRY(expr)            \
@@ -165,6 +187,26 @@ struct anqs_model {
 
 // ---- launchers implemented in the kernel translation units ----
 namespace anqs {
+
+// Launch with the programmatic-stream-serialization attribute (see
+// ANQS_PDL_ENTRY); counts the launch and reports launch errors.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t stream,
+                            Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  note_launch();
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 
 // connect.cu
 int launch_connected(const HamView& hv, const uint64_t* x, Count n_x, uint64_t* xp, double* hval,

@@ -47,6 +47,7 @@ __device__ __forceinline__ double G(const HamView& hv, int p, int q, int r, int 
 __global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x,
                                  uint64_t* __restrict__ xp_out, double* __restrict__ h_out,
                                  uint8_t* __restrict__ j_out) {
+  ANQS_PDL_ENTRY();
   const uint64_t K = hv.K;
   const uint64_t total = n_x.get() * K;
   const int n = hv.n;
@@ -158,6 +159,7 @@ __global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, Co
 // (I, J) with I*N_occ + J = i mod 32, then the FP64 partial sums are reduced.
 __global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x_,
                                 double* __restrict__ hdiag) {
+  ANQS_PDL_ENTRY();
   const int n = hv.n;
   const uint64_t n_x = n_x_.get();
   const int lane = threadIdx.x & 31;
@@ -202,16 +204,14 @@ int launch_connected(const HamView& hv, const uint64_t* x, Count n_x, uint64_t* 
     uint64_t blocks = (total + threads - 1) / threads;
     if (blocks > 152ull * 64) blocks = 152ull * 64;
     ProfScope ps(PROF_CONNECT, s);
-    connected_kernel<<<unsigned(blocks), threads, 0, s>>>(hv, x, n_x, xp, hval, first_slot);
-    ANQS_LAUNCHED("connected_kernel");
+    ANQS_CUDA_LAUNCH("connected_kernel", launch_k(connected_kernel, dim3(unsigned(blocks)), dim3(threads), 0, s, hv, x, n_x, xp, hval, first_slot));
   }
   if (hdiag) {
     uint64_t blocks = (n_x.n + 7) / 8;  // 8 warps per CTA
     if (blocks > 152ull * 16) blocks = 152ull * 16;
     if (blocks == 0) blocks = 1;
     ProfScope ps(PROF_DIAGONAL, s);
-    diagonal_kernel<<<unsigned(blocks), threads, 0, s>>>(hv, x, n_x, hdiag);
-    ANQS_LAUNCHED("diagonal_kernel");
+    ANQS_CUDA_LAUNCH("diagonal_kernel", launch_k(diagonal_kernel, dim3(unsigned(blocks)), dim3(threads), 0, s, hv, x, n_x, hdiag));
   }
   return ANQS_OK;
 }

@@ -23,6 +23,7 @@ __global__ void eloc_sum_kernel(uint32_t K, Count n_x_, const double* __restrict
                                 const float* __restrict__ ph_x, const float* __restrict__ la_p,
                                 const float* __restrict__ ph_p, double* __restrict__ ere,
                                 double* __restrict__ eim) {
+  ANQS_PDL_ENTRY();
   const int lane = threadIdx.x & 31;
   const uint64_t n_x = n_x_.get();
   const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
@@ -67,6 +68,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // single CTA: S, E (complex) then Var in a second pass
 __global__ void stats_kernel(const double* __restrict__ ere, const double* __restrict__ eim,
                              const uint64_t* __restrict__ counts, Count n_x_, double* __restrict__ stats) {
+  ANQS_PDL_ENTRY();
   __shared__ double red[32];
   const uint64_t n_x = n_x_.get();
   double s = 0.0, sr = 0.0, si = 0.0;
@@ -99,6 +101,7 @@ __global__ void stats_kernel(const double* __restrict__ ere, const double* __res
 __global__ void cotangent_kernel(const double* __restrict__ ere, const double* __restrict__ eim,
                                  const uint64_t* __restrict__ counts, const double* __restrict__ stats,
                                  Count n_x_, float* __restrict__ cl, float* __restrict__ cp) {
+  ANQS_PDL_ENTRY();
   const double Er = stats[0], Ei = stats[1], S = stats[3];
   const uint64_t n_x = n_x_.get();
   for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x; l += uint64_t(gridDim.x) * blockDim.x) {
@@ -117,16 +120,14 @@ int launch_eloc_sum(const HamView& hv, Count n_x, const double* hval, const doub
   if (blocks == 0) blocks = 1;
   if (blocks > 152 * 16) blocks = 152 * 16;
   ProfScope ps(PROF_ELOC_SUM, s);
-  eloc_sum_kernel<<<unsigned(blocks), 256, 0, s>>>(hv.K, n_x, hval, hdiag, la_x, ph_x, la_p, ph_p, ere, eim);
-  ANQS_LAUNCHED("eloc_sum_kernel");
+  ANQS_CUDA_LAUNCH("eloc_sum_kernel", launch_k(eloc_sum_kernel, dim3(unsigned(blocks)), dim3(256), 0, s, hv.K, n_x, hval, hdiag, la_x, ph_x, la_p, ph_p, ere, eim));
   return ANQS_OK;
 }
 
 int launch_stats(const double* ere, const double* eim, const uint64_t* counts, Count n_x, double* stats,
                  cudaStream_t s) {
   ProfScope ps(PROF_STATS, s);
-  stats_kernel<<<1, 1024, 0, s>>>(ere, eim, counts, n_x, stats);
-  ANQS_LAUNCHED("stats_kernel");
+  ANQS_CUDA_LAUNCH("stats_kernel", launch_k(stats_kernel, dim3(1), dim3(1024), 0, s, ere, eim, counts, n_x, stats));
   return ANQS_OK;
 }
 
@@ -136,8 +137,7 @@ int launch_grad_cotangents(const double* ere, const double* eim, const uint64_t*
   if (blocks == 0) blocks = 1;
   if (blocks > 152 * 8) blocks = 152 * 8;
   ProfScope ps(PROF_COTANGENT, s);
-  cotangent_kernel<<<unsigned(blocks), 256, 0, s>>>(ere, eim, counts, stats, n_x, cl, cp);
-  ANQS_LAUNCHED("cotangent_kernel");
+  ANQS_CUDA_LAUNCH("cotangent_kernel", launch_k(cotangent_kernel, dim3(unsigned(blocks)), dim3(256), 0, s, ere, eim, counts, stats, n_x, cl, cp));
   return ANQS_OK;
 }
 

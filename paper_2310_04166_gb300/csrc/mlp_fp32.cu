@@ -166,6 +166,7 @@ template <int W>
 __global__ void __launch_bounds__(NT) logpsi_kernel(MlpView m, HamView hv, const uint64_t* __restrict__ xs,
                                                     Count n_x_, float* __restrict__ la_out,
                                                     float* __restrict__ ph_out) {
+  ANQS_PDL_ENTRY();
   const uint64_t n_x = n_x_.get();
   extern __shared__ float smem[];
   float* act = smem;
@@ -213,6 +214,7 @@ template <int W>
 __global__ void __launch_bounds__(NT) slot_logits_kernel(MlpView m, int p, const uint64_t* __restrict__ prefixes,
                                                          const uint64_t* __restrict__ n_rows_dev,
                                                          float* __restrict__ out) {
+  ANQS_PDL_ENTRY();
   extern __shared__ float smem[];
   float* act = smem;
   float* ws = act + 2 * R * W;
@@ -301,6 +303,7 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
                                                   Count n_x_, const float* __restrict__ cot_la,
                                                   const float* __restrict__ cot_ph, float* __restrict__ grad,
                                                   uint64_t n_params) {
+  ANQS_PDL_ENTRY();
   extern __shared__ float smem[];
   const int L = m.n_hidden;
   float* act = smem;                       // L buffers [RG][W]: h_1..h_L
@@ -429,6 +432,7 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
 // grad[i] = sum over the tiles of the per-tile copies (only tiles holding rows)
 __global__ void partial_sum_kernel(const float* __restrict__ part, Count n_x_, uint64_t n_params,
                                    float* __restrict__ grad) {
+  ANQS_PDL_ENTRY();
   const uint64_t tiles = (n_x_.get() + RG - 1) / RG;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n_params;
        i += uint64_t(gridDim.x) * blockDim.x) {
@@ -452,8 +456,7 @@ int logpsi_w(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, 
   size_t sm = Smem<W>::bytes(2);
   ANQS_TRY(set_smem(logpsi_kernel<W>, sm));
   ProfScope ps(PROF_MLP_FP32_LOGPSI, s);
-  logpsi_kernel<W><<<grid_for((n_x.n + R - 1) / R, 152 * 8), NT, sm, s>>>(m, hv, x, n_x, la, ph);
-  ANQS_LAUNCHED("mlp logpsi_kernel");
+  ANQS_CUDA_LAUNCH("mlp logpsi_kernel", launch_k(logpsi_kernel<W>, dim3(grid_for((n_x.n + R - 1) / R, 152 * 8)), dim3(NT), sm, s, m, hv, x, n_x, la, ph));
   return ANQS_OK;
 }
 
@@ -463,8 +466,7 @@ int logits_w(const MlpView& m, int p, const uint64_t* pre, const uint64_t* nr, u
   size_t sm = Smem<W>::bytes(2);
   ANQS_TRY(set_smem(slot_logits_kernel<W>, sm));
   ProfScope ps(PROF_MLP_FP32_SLOT, s);
-  slot_logits_kernel<W><<<grid_for((max_rows + R - 1) / R, 152 * 8), NT, sm, s>>>(m, p, pre, nr, out);
-  ANQS_LAUNCHED("mlp slot_logits_kernel");
+  ANQS_CUDA_LAUNCH("mlp slot_logits_kernel", launch_k(slot_logits_kernel<W>, dim3(grid_for((max_rows + R - 1) / R, 152 * 8)), dim3(NT), sm, s, m, p, pre, nr, out));
   return ANQS_OK;
 }
 
@@ -478,15 +480,11 @@ int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, co
   ProfScope ps(PROF_MLP_FP32_GRAD, s);
   if (part) {
     ANQS_TRY(set_smem(grad_kernel<W, true>, sm));
-    grad_kernel<W, true><<<grid, NT, sm, s>>>(m, hv, x, n_x, cl, cp, part, n_params);
-    ANQS_LAUNCHED("mlp grad_kernel");
-    partial_sum_kernel<<<unsigned(std::min<uint64_t>((n_params + 255) / 256, 152 * 8)), 256, 0, s>>>(part, n_x,
-                                                                                                 n_params, g);
-    ANQS_LAUNCHED("mlp partial_sum_kernel");
+    ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, true>, dim3(grid), dim3(NT), sm, s, m, hv, x, n_x, cl, cp, part, n_params));
+    ANQS_CUDA_LAUNCH("mlp partial_sum_kernel", launch_k(partial_sum_kernel, dim3(unsigned(std::min<uint64_t>((n_params + 255) / 256, 152 * 8))), dim3(256), 0, s, part, n_x, n_params, g));
   } else {
     ANQS_TRY(set_smem(grad_kernel<W, false>, sm));
-    grad_kernel<W, false><<<grid, NT, sm, s>>>(m, hv, x, n_x, cl, cp, g, n_params);
-    ANQS_LAUNCHED("mlp grad_kernel");
+    ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, false>, dim3(grid), dim3(NT), sm, s, m, hv, x, n_x, cl, cp, g, n_params));
   }
   return ANQS_OK;
 }

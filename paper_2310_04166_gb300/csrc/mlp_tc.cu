@@ -81,6 +81,7 @@ struct TcView {
 
 // ---- packing: f32 parameters -> per-slot bf16/f32 images --------------------
 __global__ void pack_kernel(MlpView m, TcView tv, unsigned char* img) {
+  ANQS_PDL_ENTRY();
   const int p = blockIdx.y;
   const int W = m.width, L = m.n_hidden;
   const SlotLayout S = slot_layout(p, W, L);
@@ -314,20 +315,39 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
   c.t = t;
   const uint32_t bar_w = tc::smem_u32(&bars[0]);
   uint32_t ph_w = 0, ph_m = 0;
+  const int np = ta.p_hi - ta.p_lo;
+  // A single-slot launch (one sampler level) fetches its weight image in the
+  // prologue: the packed images were written before the previous kernel.
+  int loaded = -1;     // slot whose image is in shared memory (or on its way)
+  bool pending = false;
+  if (np == 1) {
+    if (threadIdx.x == 0) load_slot(tv, ta.p_lo, tc::smem_u32(s_img), bar_w, W, tv.L);
+    loaded = ta.p_lo;
+    pending = true;
+  }
+  ANQS_PDL_WAIT();
+  ANQS_PDL_TRIGGER();
   const uint64_t n_rows = ta.rows.get();
   const uint64_t n_groups = (n_rows + NWG * MT - 1) / (NWG * MT);
-  const int np = ta.p_hi - ta.p_lo;
   const uint64_t n_items = n_groups * uint64_t(np);
   for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int p = ta.p_lo + int(it / n_groups);
     const uint64_t grp = it % n_groups;
     const SlotLayout S = slot_layout(p, W, tv.L);
-    if (threadIdx.x == 0) load_slot(tv, p, tc::smem_u32(s_img), bar_w, W, tv.L);
+    if (p != loaded) {
+      if (threadIdx.x == 0) load_slot(tv, p, tc::smem_u32(s_img), bar_w, W, tv.L);
+      loaded = p;
+      pending = true;
+    }
     const uint64_t r = (grp * NWG + wg) * MT + t;
     const bool valid = r < n_rows;
     const uint64_t x = valid ? ta.x[r] : 0ull;
-    bool ok = __syncthreads_and(wait_bar(bar_w, ph_w));
-    ph_w ^= 1;
+    bool ok = true;
+    if (pending) {
+      ok = __syncthreads_and(wait_bar(bar_w, ph_w));
+      ph_w ^= 1;
+      pending = false;
+    }
     float out[8];
     if (ok && (grp * NWG + wg) * MT < n_rows) ok = tile_slot<W>(c, ph_m, p, x, S, tc::smem_u32(s_img), s_img, out);
     if (!ok) s_abort = 1;
@@ -341,6 +361,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
     __syncthreads();
     if (s_abort) break;
   }
+  if (pending && !__syncthreads_and(wait_bar(bar_w, ph_w))) s_abort = 1;  // prefetched image not used
   teardown<W>(tv, s_tmem, s_abort);
 }
 
@@ -363,6 +384,8 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_ws_kernel(TcView tv, HamView hv,
   const int wg = threadIdx.x / MT, t = threadIdx.x % MT;
   const int n = tv.n;
   setup<W>(bars, &s_tmem, &s_abort);
+  ANQS_PDL_WAIT();
+  ANQS_PDL_TRIGGER();
   const uint32_t img_stride = round_up(tv.max_img, 1024u);
   Ctx c;
   c.tv = &tv;
@@ -448,6 +471,7 @@ __global__ void eloc_assemble_kernel(int n, uint32_t K, Count n_x_, const uint64
                                      const double* __restrict__ hdiag, const float* __restrict__ la_x,
                                      const float* __restrict__ ph_x, double* __restrict__ ere,
                                      double* __restrict__ eim) {
+  ANQS_PDL_ENTRY();
   const int lane = threadIdx.x & 31;
   const uint64_t n_x = n_x_.get();
   const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
@@ -491,6 +515,7 @@ __global__ void eloc_assemble_kernel(int n, uint32_t K, Count n_x_, const uint64
 __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x_,
                                 const float* __restrict__ raw, float* __restrict__ la_out, float* __restrict__ ph_out,
                                 float* __restrict__ cache) {
+  ANQS_PDL_ENTRY();
   const int n = hv.n;
   const uint64_t n_x = n_x_.get();
   for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x; l += uint64_t(gridDim.x) * blockDim.x) {
@@ -531,6 +556,7 @@ __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Cou
 
 // ---- sort of connected rows by first differing slot ---------------------------
 __global__ void js_hist_kernel(const uint8_t* __restrict__ js, Count m_, int n, uint32_t* __restrict__ hist) {
+  ANQS_PDL_ENTRY();
   __shared__ uint32_t h[ANQS_MAX_ORB];
   const uint64_t m = m_.get();
   for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = 0;
@@ -545,6 +571,7 @@ __global__ void js_hist_kernel(const uint8_t* __restrict__ js, Count m_, int n, 
 // cursor[i] = offsets[i] = rows with first slot < i (exclusive prefix sums)
 __global__ void js_offsets_kernel(const uint32_t* __restrict__ hist, int n, uint32_t* __restrict__ cursor,
                                   uint32_t* __restrict__ offsets) {
+  ANQS_PDL_ENTRY();
   if (threadIdx.x == 0) {
     uint32_t acc = 0;
     for (int i = 0; i < n; ++i) {
@@ -558,6 +585,7 @@ __global__ void js_offsets_kernel(const uint32_t* __restrict__ hist, int n, uint
 
 __global__ void js_scatter_kernel(const uint8_t* __restrict__ js, Count m_, uint32_t* __restrict__ cursor,
                                   uint32_t* __restrict__ perm) {
+  ANQS_PDL_ENTRY();
   const uint64_t m = m_.get();
   const int lane = threadIdx.x & 31;
   for (uint64_t t0 = blockIdx.x * uint64_t(blockDim.x); t0 < m; t0 += uint64_t(gridDim.x) * blockDim.x) {
@@ -615,8 +643,7 @@ int launch_slots_w(const TcView& tv, const TileArgs& ta, cudaStream_t s) {
   TcView v1 = tv;
   v1.nbuf = 1;
   ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_slots_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-  mlp_tc_slots_kernel<W><<<grid, NT, sm, s>>>(v1, ta);
-  ANQS_LAUNCHED("mlp_tc_slots_kernel");
+  ANQS_CUDA_LAUNCH("mlp_tc_slots_kernel", launch_k(mlp_tc_slots_kernel<W>, dim3(grid), dim3(NT), sm, s, v1, ta));
   return ANQS_OK;
 }
 
@@ -631,8 +658,7 @@ int launch_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float
                     float* cache, cudaStream_t s) {
   uint64_t blocks = (n_x.n + 127) / 128;
   if (blocks > 152 * 8) blocks = 152 * 8;
-  finalize_kernel<<<unsigned(blocks ? blocks : 1), 128, 0, s>>>(hv, x, n_x, raw, la, ph, cache);
-  ANQS_LAUNCHED("finalize_kernel");
+  ANQS_CUDA_LAUNCH("finalize_kernel", launch_k(finalize_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(128), 0, s, hv, x, n_x, raw, la, ph, cache));
   return ANQS_OK;
 }
 
@@ -669,8 +695,7 @@ int launch_ws_w(const TcView& tv, const HamView& hv, const ElocWs& w, cudaStream
   const size_t sm = smem_bytes(tv, 1);
   const unsigned grid = unsigned(std::max(num_sms(), tv.n));
   ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_ws_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-  mlp_tc_ws_kernel<W><<<grid, NT, sm, s>>>(tv, hv, w.xp, w.perm, w.offsets, w.T);
-  ANQS_LAUNCHED("mlp_tc_ws_kernel");
+  ANQS_CUDA_LAUNCH("mlp_tc_ws_kernel", launch_k(mlp_tc_ws_kernel<W>, dim3(grid), dim3(NT), sm, s, tv, hv, w.xp, w.perm, w.offsets, w.T));
   return ANQS_OK;
 }
 
@@ -707,8 +732,7 @@ int mlp_tc_pack_alloc(anqs_model* M) {
 int mlp_tc_pack(anqs_model* M, cudaStream_t s) {
   TcView tv = make_view(M);
   dim3 grid(64, unsigned(M->d.n_orb));
-  pack_kernel<<<grid, 256, 0, s>>>(M->mlp, tv, static_cast<unsigned char*>(M->packed));
-  ANQS_LAUNCHED("pack_kernel");
+  ANQS_CUDA_LAUNCH("pack_kernel", launch_k(pack_kernel, dim3(grid), dim3(256), 0, s, M->mlp, tv, static_cast<unsigned char*>(M->packed)));
   return ANQS_OK;
 }
 
@@ -783,12 +807,9 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count
     ProfScope ps(PROF_TC_SORT, s);
     ANQS_CUDA(cudaMemsetAsync(w.hist, 0, ANQS_MAX_ORB * sizeof(uint32_t), s));
     unsigned g = unsigned(std::min<uint64_t>((m + 255) / 256, 152 * 4));
-    js_hist_kernel<<<g ? g : 1, 256, 0, s>>>(w.js, mc, H->v.n, w.hist);
-    ANQS_LAUNCHED("js_hist_kernel");
-    js_offsets_kernel<<<1, 32, 0, s>>>(w.hist, H->v.n, w.cursor, w.offsets);
-    ANQS_LAUNCHED("js_offsets_kernel");
-    js_scatter_kernel<<<g ? g : 1, 256, 0, s>>>(w.js, mc, w.cursor, w.perm);
-    ANQS_LAUNCHED("js_scatter_kernel");
+    ANQS_CUDA_LAUNCH("js_hist_kernel", launch_k(js_hist_kernel, dim3(g ? g : 1), dim3(256), 0, s, w.js, mc, H->v.n, w.hist));
+    ANQS_CUDA_LAUNCH("js_offsets_kernel", launch_k(js_offsets_kernel, dim3(1), dim3(32), 0, s, w.hist, H->v.n, w.cursor, w.offsets));
+    ANQS_CUDA_LAUNCH("js_scatter_kernel", launch_k(js_scatter_kernel, dim3(g ? g : 1), dim3(256), 0, s, w.js, mc, w.cursor, w.perm));
   }
   {
     TcView tv = make_view(M);
@@ -799,10 +820,7 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count
     ProfScope ps(PROF_TC_ELOC, s);
     uint64_t blocks = (n_x.n + 7) / 8;
     if (blocks > 152 * 16) blocks = 152 * 16;
-    eloc_assemble_kernel<<<unsigned(blocks ? blocks : 1), 256, 0, s>>>(H->v.n, uint32_t(K), n_x, w.xp, w.js,
-                                                                      w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x,
-                                                                      ere, eim);
-    ANQS_LAUNCHED("eloc_assemble_kernel");
+    ANQS_CUDA_LAUNCH("eloc_assemble_kernel", launch_k(eloc_assemble_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(256), 0, s, H->v.n, uint32_t(K), n_x, w.xp, w.js, w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x, ere, eim));
   }
   return ANQS_OK;
 }

@@ -58,6 +58,7 @@ struct Philox {
 
 __global__ void init_kernel(uint64_t* pre, uint64_t* cnt, uint64_t* n_front, uint64_t n_samples, unsigned* done,
                             uint64_t* child) {
+  ANQS_PDL_ENTRY();
   pre[0] = 0;
   cnt[0] = n_samples;
   n_front[0] = 1;
@@ -132,6 +133,7 @@ __global__ void prep_kernel(HamView hv, int p, const uint64_t* __restrict__ pre,
                             const uint64_t* __restrict__ n_front, const float* __restrict__ logits,
                             uint64_t* __restrict__ thr, uint8_t* __restrict__ allowed, uint64_t* __restrict__ nblk,
                             uint64_t* __restrict__ child) {
+  ANQS_PDL_ENTRY();
   const uint64_t nf = *n_front;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < nf; i += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t x = pre[i];
@@ -186,6 +188,7 @@ __device__ uint64_t block_excl_scan(uint64_t v, uint64_t* sh, uint64_t* tot) {
 // in[i] for i < n (n = *n_dev * mult), partial sums per chunk
 __global__ void scan_reduce_kernel(const uint64_t* __restrict__ in, const uint64_t* __restrict__ n_dev,
                                    uint64_t mult, uint64_t* __restrict__ partial) {
+  ANQS_PDL_ENTRY();
   __shared__ uint64_t sh[33];
   const uint64_t n = *n_dev * mult;
   const uint64_t base = uint64_t(blockIdx.x) * SCAN_CHUNK;
@@ -201,6 +204,7 @@ __global__ void scan_reduce_kernel(const uint64_t* __restrict__ in, const uint64
 }
 
 __global__ void scan_partials_kernel(uint64_t* __restrict__ partial, uint64_t n_part) {
+  ANQS_PDL_ENTRY();
   __shared__ uint64_t sh[33];
   uint64_t carry = 0;
   for (uint64_t b = 0; b < n_part; b += SCAN_T) {
@@ -218,6 +222,7 @@ __global__ void scan_partials_kernel(uint64_t* __restrict__ partial, uint64_t n_
 __global__ void scan_apply_kernel(const uint64_t* __restrict__ in, const uint64_t* __restrict__ n_dev,
                                   uint64_t mult, const uint64_t* __restrict__ partial, uint64_t* __restrict__ out,
                                   uint64_t* __restrict__ total_dev) {
+  ANQS_PDL_ENTRY();
   __shared__ uint64_t sh[33];
   const uint64_t n = *n_dev * mult;
   const uint64_t base = uint64_t(blockIdx.x) * SCAN_CHUNK;
@@ -250,6 +255,7 @@ __global__ void draw_kernel(int p, uint64_t seed, uint64_t counter0, const uint6
                             const uint64_t* __restrict__ nblk_scan, const uint64_t* __restrict__ thr,
                             const uint8_t* __restrict__ allowed, uint64_t* __restrict__ child,
                             uint64_t max_threads) {
+  ANQS_PDL_ENTRY();
   const uint64_t nf = *n_front;
   const uint64_t total = nblk_scan[nf];
   const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
@@ -304,6 +310,7 @@ __global__ void draw_kernel(int p, uint64_t seed, uint64_t counter0, const uint6
 
 __global__ void flag_kernel(const uint64_t* __restrict__ child, const uint64_t* __restrict__ n_front,
                             uint64_t* __restrict__ flags) {
+  ANQS_PDL_ENTRY();
   const uint64_t n4 = *n_front * 4;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n4; i += uint64_t(gridDim.x) * blockDim.x)
     flags[i] = child[i] ? 1ull : 0ull;
@@ -312,6 +319,7 @@ __global__ void flag_kernel(const uint64_t* __restrict__ child, const uint64_t* 
 __global__ void scatter_kernel(int p, const uint64_t* __restrict__ pre, const uint64_t* __restrict__ child,
                                const uint64_t* __restrict__ n_front, const uint64_t* __restrict__ pos,
                                uint64_t* __restrict__ pre_out, uint64_t* __restrict__ cnt_out) {
+  ANQS_PDL_ENTRY();
   const uint64_t n4 = *n_front * 4;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n4; i += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t c = child[i];
@@ -329,6 +337,7 @@ __global__ void scatter_kernel(int p, const uint64_t* __restrict__ pre, const ui
 // warp-segment aggregation into shared counters, compaction of the children.
 constexpr int SMALL_T = 1024;
 constexpr int SMALL_F = 2048;  // largest frontier handled this way
+constexpr size_t SMALL_DYN = size_t(SMALL_T) * 48;  // thresholds and window counts
 
 __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* sh, uint32_t* tot) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -378,8 +387,11 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
                                                              uint64_t* __restrict__ pre_out,
                                                              uint64_t* __restrict__ cnt_out,
                                                              uint64_t* __restrict__ n_out) {
+  ANQS_PDL_ENTRY();
   __shared__ uint32_t s_scan[SMALL_F + 1];
-  __shared__ uint64_t s_thr[SMALL_T][4];
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  uint64_t(*s_thr)[4] = reinterpret_cast<uint64_t(*)[4]>(s_dyn);                  // SMALL_T x 4
+  uint32_t(*s_cnt)[4] = reinterpret_cast<uint32_t(*)[4]>(s_dyn + SMALL_T * 32);   // window outcome counts
   __shared__ uint8_t s_mk[SMALL_T];
   __shared__ uint32_t s_red[33];
   __shared__ bool s_last;
@@ -413,6 +425,7 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
     __syncthreads();  // previous window's thresholds are no longer read
     if (threadIdx.x <= n_hi - n_lo) {
       const int i = n_lo + threadIdx.x;
+      for (int v = 0; v < 4; ++v) s_cnt[threadIdx.x][v] = 0;
       const uint64_t x = pre[i];
       const unsigned mk = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p));
       split_thresholds(logits + uint64_t(i) * 8, mk, s_thr[threadIdx.x]);
@@ -450,7 +463,16 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
     if (tail && node >= 0)
       for (int k = 0; k < 4; ++k) {
         const uint32_t ck = (v >> (8 * k)) & 0xffu;
-        if (ck) atomicAdd(reinterpret_cast<unsigned long long*>(child + uint64_t(node) * 4 + k), (unsigned long long)ck);
+        if (ck) atomicAdd(&s_cnt[node - n_lo][k], ck);
+      }
+    __syncthreads();
+    // one global atomic per (node, outcome) and window
+    if (threadIdx.x <= n_hi - n_lo)
+      for (int k = 0; k < 4; ++k) {
+        const uint32_t ck = s_cnt[threadIdx.x][k];
+        if (ck)
+          atomicAdd(reinterpret_cast<unsigned long long*>(child + uint64_t(n_lo + threadIdx.x) * 4 + k),
+                    (unsigned long long)ck);
       }
   }
   // last CTA: compaction (the other CTAs' counts are visible after their fence)
@@ -519,12 +541,9 @@ void plan_ws(const anqs_ham* H, uint64_t n_samples, Arena& A, Plan& P) {
 int scan(const uint64_t* in, const uint64_t* n_dev, uint64_t mult, uint64_t max_n, uint64_t* partial,
          uint64_t* out, uint64_t* total_dev, cudaStream_t s) {
   uint64_t chunks = max_n / SCAN_CHUNK + 1;  // covers index max_n (the total)
-  scan_reduce_kernel<<<unsigned(chunks), SCAN_T, 0, s>>>(in, n_dev, mult, partial);
-  ANQS_LAUNCHED("scan_reduce_kernel");
-  scan_partials_kernel<<<1, SCAN_T, 0, s>>>(partial, chunks);
-  ANQS_LAUNCHED("scan_partials_kernel");
-  scan_apply_kernel<<<unsigned(chunks), SCAN_T, 0, s>>>(in, n_dev, mult, partial, out, total_dev);
-  ANQS_LAUNCHED("scan_apply_kernel");
+  ANQS_CUDA_LAUNCH("scan_reduce_kernel", launch_k(scan_reduce_kernel, dim3(unsigned(chunks)), dim3(SCAN_T), 0, s, in, n_dev, mult, partial));
+  ANQS_CUDA_LAUNCH("scan_partials_kernel", launch_k(scan_partials_kernel, dim3(1), dim3(SCAN_T), 0, s, partial, chunks));
+  ANQS_CUDA_LAUNCH("scan_apply_kernel", launch_k(scan_apply_kernel, dim3(unsigned(chunks)), dim3(SCAN_T), 0, s, in, n_dev, mult, partial, out, total_dev));
   return ANQS_OK;
 }
 
@@ -553,8 +572,7 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
   const int n = H->v.n;
   {
     ProfScope ps(PROF_SAMPLER, s);
-    init_kernel<<<1, 1, 0, s>>>(P.pre[0], P.cnt[0], P.n_front, n_samples, P.done, P.child);
-    ANQS_LAUNCHED("sampler init_kernel");
+    ANQS_CUDA_LAUNCH("sampler init_kernel", launch_k(init_kernel, dim3(1), dim3(1), 0, s, P.pre[0], P.cnt[0], P.n_front, n_samples, P.done, P.child));
   }
   bool prev_large = false;
   for (int p = 0; p < n; ++p) {
@@ -572,28 +590,18 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
     prev_large = !small;
     if (small) {
       const uint64_t blocks = ((n_samples + 3) / 4 + Fp + SMALL_T - 1) / SMALL_T;
-      draw_small_kernel<<<blocks_for(blocks, 1, 152), SMALL_T, 0, s>>>(
-          H->v, p, seed, counter, counter_dev, P.pre[cur], P.cnt[cur], nf, P.logits, P.child, P.done,
-          last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt], last ? n_unique : P.n_front + nxt);
-      ANQS_LAUNCHED("sampler draw_small_kernel");
+      ANQS_CUDA(cudaFuncSetAttribute(draw_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMALL_DYN)));
+      ANQS_CUDA_LAUNCH("sampler draw_small_kernel", launch_k(draw_small_kernel, dim3(blocks_for(blocks, 1, 152)), dim3(SMALL_T), SMALL_DYN, s, H->v, p, seed, counter, counter_dev, P.pre[cur], P.cnt[cur], nf, P.logits, P.child, P.done, last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt], last ? n_unique : P.n_front + nxt));
       continue;
     }
-    prep_kernel<<<blocks_for(Fp, 256, 152 * 8), 256, 0, s>>>(H->v, p, P.pre[cur], P.cnt[cur], nf, P.logits, P.thr,
-                                                              P.allowed, P.nblk, P.child);
-    ANQS_LAUNCHED("sampler prep_kernel");
+    ANQS_CUDA_LAUNCH("sampler prep_kernel", launch_k(prep_kernel, dim3(blocks_for(Fp, 256, 152 * 8)), dim3(256), 0, s, H->v, p, P.pre[cur], P.cnt[cur], nf, P.logits, P.thr, P.allowed, P.nblk, P.child));
     ANQS_TRY(scan(P.nblk, nf, 1, Fp, P.partial, P.nblk_scan, nullptr, s));
     const uint64_t max_draw_threads = (n_samples + 3) / 4 + Fp;
-    draw_kernel<<<blocks_for(max_draw_threads, 256, 152 * 16), 256, 0, s>>>(
-        p, seed, counter, counter_dev, P.pre[cur], P.cnt[cur], nf, P.nblk_scan, P.thr, P.allowed, P.child,
-        max_draw_threads);
-    ANQS_LAUNCHED("sampler draw_kernel");
-    flag_kernel<<<blocks_for(Fp * 4, 256, 152 * 8), 256, 0, s>>>(P.child, nf, P.flags);
-    ANQS_LAUNCHED("sampler flag_kernel");
+    ANQS_CUDA_LAUNCH("sampler draw_kernel", launch_k(draw_kernel, dim3(blocks_for(max_draw_threads, 256, 152 * 16)), dim3(256), 0, s, p, seed, counter, counter_dev, P.pre[cur], P.cnt[cur], nf, P.nblk_scan, P.thr, P.allowed, P.child, max_draw_threads));
+    ANQS_CUDA_LAUNCH("sampler flag_kernel", launch_k(flag_kernel, dim3(blocks_for(Fp * 4, 256, 152 * 8)), dim3(256), 0, s, P.child, nf, P.flags));
     uint64_t* nf_next = last ? n_unique : P.n_front + nxt;
     ANQS_TRY(scan(P.flags, nf, 4, Fp * 4, P.partial, P.pos, nf_next, s));
-    scatter_kernel<<<blocks_for(Fp * 4, 256, 152 * 8), 256, 0, s>>>(
-        p, P.pre[cur], P.child, nf, P.pos, last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt]);
-    ANQS_LAUNCHED("sampler scatter_kernel");
+    ANQS_CUDA_LAUNCH("sampler scatter_kernel", launch_k(scatter_kernel, dim3(blocks_for(Fp * 4, 256, 152 * 8)), dim3(256), 0, s, p, P.pre[cur], P.child, nf, P.pos, last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt]));
   }
   return ANQS_OK;
 }

@@ -18,6 +18,7 @@ __device__ __forceinline__ const float* table_row(const float* params, int p, ui
 __global__ void table_logpsi_kernel(const float* __restrict__ params, int n, HamView hv,
                                     const uint64_t* __restrict__ xs, Count n_x_, float* __restrict__ la_out,
                                     float* __restrict__ ph_out) {
+  ANQS_PDL_ENTRY();
   const uint64_t n_x = n_x_.get();
   for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x; l += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t x = xs[l];
@@ -50,6 +51,7 @@ __global__ void table_logpsi_kernel(const float* __restrict__ params, int n, Ham
 
 __global__ void table_logits_kernel(const float* __restrict__ params, int p, const uint64_t* __restrict__ pre,
                                     const uint64_t* __restrict__ n_rows_dev, float* __restrict__ out) {
+  ANQS_PDL_ENTRY();
   const uint64_t n = *n_rows_dev;
   for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < n * 8; t += uint64_t(gridDim.x) * blockDim.x)
     out[t] = table_row(params, p, pre[t / 8])[t % 8];
@@ -63,8 +65,7 @@ int launch_table_logpsi(const anqs_model* md, const HamView& hv, const uint64_t*
   if (blocks == 0) blocks = 1;
   if (blocks > 152 * 16) blocks = 152 * 16;
   ProfScope ps(PROF_TABLE, s);
-  table_logpsi_kernel<<<unsigned(blocks), 256, 0, s>>>(md->params, md->d.n_orb, hv, x, n_x, la, ph);
-  ANQS_LAUNCHED("table_logpsi_kernel");
+  ANQS_CUDA_LAUNCH("table_logpsi_kernel", launch_k(table_logpsi_kernel, dim3(unsigned(blocks)), dim3(256), 0, s, md->params, md->d.n_orb, hv, x, n_x, la, ph));
   return ANQS_OK;
 }
 
@@ -73,8 +74,7 @@ int launch_table_slot_logits(const anqs_model* md, int p, const uint64_t* pre, c
   uint64_t blocks = (max_rows * 8 + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   ProfScope ps(PROF_TABLE, s);
-  table_logits_kernel<<<unsigned(blocks ? blocks : 1), 256, 0, s>>>(md->params, p, pre, nr, out);
-  ANQS_LAUNCHED("table_logits_kernel");
+  ANQS_CUDA_LAUNCH("table_logits_kernel", launch_k(table_logits_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(256), 0, s, md->params, p, pre, nr, out));
   return ANQS_OK;
 }
 
