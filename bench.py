@@ -343,16 +343,13 @@ def main():
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel family (eager profiled pass)
+    # rooflines of the kernel families (eager profiled pass)
     peaks, src = _peaks()
-    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else ("none", (0, 0.0))
-    dname, (dl, dms) = dom
-    avg_ms = dms / max(dl, 1)
     n_unq = total_u / args.steps
-    K = ham.n_connected
     k_last = int(nu.item())
-    work = _tc_work(A, ham, model, w, x[:k_last]) if form == "bf16" else None
-    roof = _roofline(dname, dl, avg_ms, w, K, n_unq, n_prof, peaks, src, work)
+    work = _tc_work(A, ham, model, w, x[:k_last])
+    roof, roofs = _rooflines(prof, work, n_prof, peaks, src)
+    top = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -368,7 +365,7 @@ def main():
             "launches_per_step": launches_per_step,
             "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in prof.items()},
             "kernels_note": f"CUDA-event totals over {n_prof} eager (non-graph) steps",
-            "roofline": roof, "clocks": clk.summary()}
+            "roofline": roof, "rooflines": roofs, "top_kernel_family": top, "clocks": clk.summary()}
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -377,10 +374,15 @@ def main():
 
 
 def _tc_work(A, ham, model, w, x):
-    """Algorithmic FLOP per step of the BF16 kernel families for the sample set
-    x: suffix = sum over connected x' of the slots p > j(x'); parent = every
-    slot of every sample; slot (sampler) = every slot of every distinct prefix
-    of the leaves (the frontier of each level)."""
+    """Algorithmic work per step for the sample set x.
+
+    FLOP of one slot-p evaluation f(p) = 2 (4p W + (L-1) W^2 + 8 W).
+    suffix = sum over connected x' of f(p) for the slots p > j(x'); parent =
+    every slot of every sample; slot (sampler) = every slot of every distinct
+    prefix of the leaves (the frontier of each level); grad = 3 x parent (the
+    forward recomputed plus the two adjoint products); eloc bytes = per
+    connected x': x' 8 + j 1 + H 8 + parent cache 8 + one 8-byte term per
+    slot p > j."""
     n, W, L = w["n"], w["width"], w["n_hidden"]
     f = np.array([2 * (4 * p * W + (L - 1) * W * W + 8 * W) for p in range(n)], dtype=np.float64)
     cf = np.concatenate([[0.0], np.cumsum(f)])  # cf[p] = sum_{q<p} f[q]
@@ -393,38 +395,40 @@ def _tc_work(A, ham, model, w, x):
     for p in range(n):
         pre = np.unique(xs & np.uint64((1 << (2 * p)) - 1)) if p else np.zeros(1, np.uint64)
         slot += len(pre) * f[p]
-    return {"mlp_tc_suffix_kernel": suffix, "mlp_tc_parent_kernel": parent, "mlp_tc_slot_kernel": slot}
+    eloc_bytes = float((8 + 1 + 8 + 8 + 8 * (n - 1 - j)).sum())
+    return {"mlp_tc_suffix_kernel": suffix, "mlp_tc_parent_kernel": parent, "mlp_tc_slot_kernel": slot,
+            "mlp_fp32_grad_kernel": 3.0 * parent, "eloc_assemble_kernel": eloc_bytes,
+            "connected_kernel": float(len(j) * (8 + 8 + 1) + len(x) * 8)}
 
 
-def _roofline(name, launches, avg_ms, w, K, n_unq, steps, peaks, src, work=None):
-    """Algorithmic work per launch of the dominant kernel family over its
-    measured average duration.  FP32 SIMT network: FLOP of the network on
-    every configuration it evaluates (bound: FP32 ALU, peak = 152 SMs x 128
-    FMA/clk x 2 x max SM clock).  Otherwise bytes (HBM)."""
-    if avg_ms <= 0:
-        return None
-    n, W, L = w["n"], w.get("width", 0), w.get("n_hidden", 0)
-    flop_full = sum(2 * (4 * p * W + (L - 1) * W * W + 8 * W) for p in range(n))  # one configuration, all slots
+def _rooflines(prof, work, steps, peaks, src):
+    """Roofline of every kernel family with a defined bound (work per step x
+    steps / total event time) and the dominant one by time."""
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    if name in ("mlp_tc_suffix_kernel", "mlp_tc_parent_kernel", "mlp_tc_slot_kernel") and work is not None:
-        flops = work[name] * steps
-        ach = flops / launches / (avg_ms * 1e-3) / 1e12
-        peak = peaks["bf16_tflops"]
-        return {"kernel": name, "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "note": f"algorithmic FLOP with prefix reuse (bf16 GEMMs + f32 head, layer 1 as one-hot GEMM of "
-                        f"width 4p) / CUDA-event time; peak = {src} dense bf16 burst"}
-    if name == "mlp_fp32_logpsi_kernel":
-        # per step: unique samples and all their connected configurations, all slots
-        flops = flop_full * n_unq * (K + 1)
-        launches_per_step = launches / steps
-        ach = flops / launches_per_step / (avg_ms * 1e-3) / 1e12
-        peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "note": f"FP32 FMA peak derived from 152 SMs x 128 lanes x 2 x {sm_mhz:.0f} MHz"}
-    return {"kernel": name, "bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None,
-            "traffic": None}
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    out = {}
+    for name, (launches, ms) in prof.items():
+        if name not in work or ms <= 0:
+            continue
+        per_launch = work[name] * steps / launches
+        avg_s = ms / launches * 1e-3
+        if name.startswith("mlp_tc_"):
+            bound, unit, peak = "tensor", "TFLOP/s", peaks["bf16_tflops"]
+            ach = per_launch / avg_s / 1e12
+            note = f"dense bf16 {src} burst peak; FLOP with prefix reuse"
+        elif name == "mlp_fp32_grad_kernel":
+            bound, unit, peak = "alu", "TFLOP/s", fp32_peak
+            ach = per_launch / avg_s / 1e12
+            note = f"FP32 SIMT peak derived: 152 SMs x 128 FMA lanes x 2 x {sm_mhz:.0f} MHz"
+        else:
+            bound, unit, peak = "hbm", "GB/s", peaks["hbm_gbs"]
+            ach = per_launch / avg_s / 1e9
+            note = f"{src} copy bandwidth; algorithmic bytes"
+        out[name] = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+                     "frac": ach / peak, "traffic": None, "avg_launch_us": avg_s * 1e6,
+                     "work_per_launch": per_launch, "note": note}
+    dominant = max(out.values(), key=lambda r: prof[r["kernel"]][1]) if out else None
+    return dominant, out
 
 
 if __name__ == "__main__":

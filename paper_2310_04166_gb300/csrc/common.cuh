@@ -36,6 +36,9 @@ enum ProfId {
   PROF_TC_ELOC,
   PROF_TC_SLOT,
   PROF_TF,
+  PROF_TC_FINALIZE,
+  PROF_GRAD_REDUCE,
+  PROF_SAMPLER_NET_FP32,
   PROF_COUNT
 };
 

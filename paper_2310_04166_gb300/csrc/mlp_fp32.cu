@@ -477,14 +477,22 @@ int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, co
   if (sm > 227 * 1024)
     return set_error(ANQS_ERR_UNSUPPORTED, "FP32 MLP adjoint needs %zu bytes of shared memory", sm);
   dim3 grid(unsigned(std::max<uint64_t>((n_x.n + RG - 1) / RG, 1)), unsigned(m.n));
-  ProfScope ps(PROF_MLP_FP32_GRAD, s);
   if (part) {
     ANQS_TRY(set_smem(grad_kernel<W, true>, sm));
-    ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, true>, dim3(grid), dim3(NT), sm, s, m, hv, x, n_x, cl, cp, part, n_params));
-    ANQS_CUDA_LAUNCH("mlp partial_sum_kernel", launch_k(partial_sum_kernel, dim3(unsigned(std::min<uint64_t>((n_params + 255) / 256, 152 * 8))), dim3(256), 0, s, part, n_x, n_params, g));
+    {
+      ProfScope ps(PROF_MLP_FP32_GRAD, s);
+      ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, true>, dim3(grid), dim3(NT), sm, s, m, hv, x, n_x,
+                                                   cl, cp, part, n_params));
+    }
+    ProfScope ps(PROF_GRAD_REDUCE, s);
+    ANQS_CUDA_LAUNCH("mlp partial_sum_kernel",
+                     launch_k(partial_sum_kernel, dim3(unsigned(std::min<uint64_t>((n_params + 255) / 256, 152 * 8))),
+                              dim3(256), 0, s, part, n_x, n_params, g));
   } else {
     ANQS_TRY(set_smem(grad_kernel<W, false>, sm));
-    ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, false>, dim3(grid), dim3(NT), sm, s, m, hv, x, n_x, cl, cp, g, n_params));
+    ProfScope ps(PROF_MLP_FP32_GRAD, s);
+    ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, false>, dim3(grid), dim3(NT), sm, s, m, hv, x, n_x, cl,
+                                                 cp, g, n_params));
   }
   return ANQS_OK;
 }

@@ -756,7 +756,7 @@ int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t*
     ta.p_hi = M->d.n_orb;
     ta.raw = M->tc_raw;
     ANQS_TRY(launch_slots(M, ta, s, PROF_TC_PARENT));
-    ProfScope ps(PROF_TC_PARENT, s);
+    ProfScope ps(PROF_TC_FINALIZE, s);
     ANQS_TRY(launch_finalize(hv, x + off, host_count(k), M->tc_raw, la + off, ph + off, nullptr, s));
   }
   return ANQS_OK;
@@ -800,7 +800,7 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count
     ta.p_hi = H->v.n;
     ta.raw = w.raw;
     ANQS_TRY(launch_slots(M, ta, s, PROF_TC_PARENT));
-    ProfScope ps(PROF_TC_PARENT, s);
+    ProfScope ps(PROF_TC_FINALIZE, s);
     ANQS_TRY(launch_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
   }
   {
