@@ -1,5 +1,7 @@
 """Benchmark: local energies per second of the symmetry-masked autoregressive
-VMC hot path on one GB300 (or N independent replicas under torchrun).
+VMC hot path on one GB300 (under torchrun: N data-parallel ranks, one per
+GPU, each with its own sample set, exchanging energy statistics and
+gradients).
 
 One step = one pass of the whole hot path over one batch of synthetic
 input: masked statistics sampling of N_s samples, the connected set and
@@ -62,19 +64,24 @@ class Clocks:
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.perf_counter()  # the sampler is running before the region starts
+            while not self.lines and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.01)
         except OSError:
             self.proc = None
+        self.t_begin = time.perf_counter()
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *a):
+        self.t_end = time.perf_counter()
         if self.proc:
             self.proc.terminate()
             try:
@@ -85,7 +92,10 @@ class Clocks:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        inside = [ln for t, ln in self.lines if self.t_begin <= t <= self.t_end]
+        if not inside:  # region shorter than the sampling period: the first sample after its start
+            inside = [ln for t, ln in self.lines if t >= self.t_begin][:1]
+        for ln in inside:
             f = [t.strip() for t in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -107,7 +117,7 @@ def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
-    if ws > 1:
+    if "WORLD_SIZE" in os.environ and "MASTER_ADDR" in os.environ:  # launched by torchrun
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
         return ws, rank, local, dist
@@ -169,13 +179,14 @@ def _config(w, args):
             "form": args.form, "n_samples": w["n_samples"], "l2": "flushed between timed steps (256 MiB write)",
             "timing": "one CUDA-graph replay of the whole step per timed iteration (weight packing, sampling, "
                       "connected set, amplitudes, E_loc and statistics, gradient), CUDA events on the replay stream",
-            "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single GPU"}
+            "parallelism": (f"dp{args.gpus}: per-rank sample sets (seed per rank), statistics all-gather + "
+                            "gradient all-reduce per step" if args.gpus > 1 else "single GPU")}
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default=os.environ.get("ANQS_BENCH_FORM", "bf16"), choices=["fp32", "bf16"])
@@ -241,17 +252,32 @@ def main():
     seed = 1234 + 7919 * rank
     import ctypes as C
 
+    stats_g = torch.zeros(4, dtype=torch.float64, device=dev)
+
+    def step_a():
+        if form == "bf16":
+            model.sync()  # re-pack the bf16 weight images (the optimiser changes params every step)
+        A.sample_into(model, ham, Ns, seed, 0, x, cnt, nu, ws_s, counter_dev=ctr)
+        A.local_energy(model, ham, x, cnt, workspace=ws_e, n_dev=nu, out=(ere, eim, stats))
+
+    def step_b(st):
+        A.grad(model, ham, x, cnt, ere, eim, st, workspace=ws_g, n_dev=nu, out=g)
+        ctr.add_(1)
+
     def step():
         """One pass of the hot path; every size stays on the device (the
         unique count of the sampler feeds the energy and gradient calls), so
         the pass can be captured in a CUDA graph and replayed.  The Philox
         counter advances on the device after each pass."""
-        if form == "bf16":
-            model.sync()  # re-pack the bf16 weight images (the optimiser changes params every step)
-        A.sample_into(model, ham, Ns, seed, 0, x, cnt, nu, ws_s, counter_dev=ctr)
-        A.local_energy(model, ham, x, cnt, workspace=ws_e, n_dev=nu, out=(ere, eim, stats))
-        A.grad(model, ham, x, cnt, ere, eim, stats, workspace=ws_g, n_dev=nu, out=g)
-        ctr.add_(1)
+        step_a()
+        step_b(stats)
+
+    def exchange():
+        """Data-parallel exchange (one process per GPU, each with its own
+        sample set): gather the ranks' statistics, combine them on the device,
+        and after the gradient pass sum the gradients."""
+        from paper_2310_04166_gb300.dist import exchange_stats
+        A.stats_combine(exchange_stats(stats), out=stats_g)
 
     # eager warm-up, then a profiled eager pass (per-kernel CUDA-event times)
     for _ in range(args.warmup):
@@ -283,9 +309,26 @@ def main():
     l1 = C.c_uint64()
     lib.anqs_launch_count(C.byref(l1))
     launches_per_step = int(l1.value - l0.value)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        step()
+    if dist:
+        # two graphs around the exchange (the collectives run eagerly)
+        from paper_2310_04166_gb300.dist import reduce_grad
+        ga, gb = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(ga):
+            step_a()
+        with torch.cuda.graph(gb):
+            step_b(stats_g)
+
+        class _Pair:
+            def replay(self):
+                ga.replay()
+                exchange()
+                gb.replay()
+                reduce_grad(g)
+        graph = _Pair()
+    else:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
     for _ in range(args.warmup):
         graph.replay()
     torch.cuda.synchronize()
@@ -331,7 +374,7 @@ def main():
         t0 = time.perf_counter()
         params.copy_(h_params, non_blocking=True)
         graph.replay()
-        h_stats.copy_(stats, non_blocking=True)
+        h_stats.copy_(stats_g if dist else stats, non_blocking=True)
         h_grad.copy_(g, non_blocking=True)
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3

@@ -219,6 +219,32 @@ ANQS_API int anqs_sample(const anqs_model* model, const anqs_ham* ham, uint64_t 
                 uint64_t* n_out_dev, uint64_t cap, uint64_t* n_unique_dev, void* workspace_dev,
                 size_t workspace_bytes, void* stream);
 
+/* One rank's share of the same sampling pass on `world` GPUs (the data-
+ * parallel split of the tree: subtrees are independent).  Every rank walks
+ * levels 0..split_level-1 exactly as anqs_sample does; the level-split_level
+ * frontier (the output when split_level = n_orb) is then reduced to its
+ * nodes i with i % world == rank, and the walk continues from those.  The
+ * draws of a node depend only on its prefix, so the union over the ranks of
+ * their outputs is exactly the output of anqs_sample with the same seed and
+ * counter, and the counts add up to n_samples.  Energy statistics and
+ * gradients of the shards combine by sums over the ranks (the host-side
+ * exchange: S, S E, S (Var + |E|^2) and the gradient; anqs_grad takes the
+ * combined stats).  Arguments otherwise as anqs_sample. */
+ANQS_API int anqs_sample_shard(const anqs_model* model, const anqs_ham* ham, uint64_t n_samples, uint64_t seed,
+                               uint64_t counter, const uint64_t* counter_dev, int rank, int world, int split_level,
+                               uint64_t* x_out_dev, uint64_t* n_out_dev, uint64_t cap, uint64_t* n_unique_dev,
+                               void* workspace_dev, size_t workspace_bytes, void* stream);
+
+/* Energy statistics of the union of `world` disjoint sample sets (the
+ * estimator of Eq. energy_est over all ranks' samples) from each set's
+ * statistics: stats_in_dev [world][4] (layout of anqs_local_energy's stats),
+ * stats_out_dev [4]:  S = sum S_r,  E = sum S_r E_r / S,
+ * Var = sum S_r (Var_r + |E_r - E|^2) / S; sets with S_r = 0 (an empty
+ * shard, whose E_r is 0/0) are skipped.  FP64, one thread; stats_in_dev
+ * and stats_out_dev may not overlap.  ANQS_ERR_ARG for world < 1 or null
+ * pointers. */
+ANQS_API int anqs_stats_combine(const double* stats_in_dev, int world, double* stats_out_dev, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Local energy and energy statistics (Eq. local_energy_def, Eq. energy_est)
  *

@@ -112,8 +112,14 @@ def split_node(probs: np.ndarray, mask, u: np.ndarray, tol: float = 0.0):
 
 
 def sample(model, isphys, n: int, n_samples: int, seed: int, counter: int = 0,
-           logits_fn=None, tol: float | None = None):
+           logits_fn=None, tol: float | None = None, shard=None):
     """Unique samples and counts, in the tree's lexicographic order.
+
+    ``shard = (rank, world, level)`` keeps, of the frontier reached after
+    ``level`` slots (the leaves when level = n), the nodes i with
+    i % world == rank, and walks on from those only: the subtrees below a
+    node are independent (Sec. II.C), so the union over the ranks is the
+    unsharded result.
 
     ``logits_fn(prefixes, p)`` may replace the network (returns [B, 4]
     modulus logits); by default the model's slot outputs are used.
@@ -126,7 +132,14 @@ def sample(model, isphys, n: int, n_samples: int, seed: int, counter: int = 0,
     cnt = np.array([n_samples], dtype=np.int64)
     margin = np.inf
     n_close = 0
+    def keep(pre, cnt, p):
+        if shard is None or shard[1] <= 1 or shard[2] != p:
+            return pre, cnt
+        sel = np.arange(len(pre)) % shard[1] == shard[0]
+        return pre[sel], cnt[sel]
+
     for p in range(n):
+        pre, cnt = keep(pre, cnt, p)
         if logits_fn is None:
             L = model.slot_out(pre, p)[:, :4].detach().numpy()
         else:
@@ -145,6 +158,7 @@ def sample(model, isphys, n: int, n_samples: int, seed: int, counter: int = 0,
                     new_cnt.append(int(c[v]))
         pre = np.array(new_pre, dtype=np.uint64)
         cnt = np.array(new_cnt, dtype=np.int64)
+    pre, cnt = keep(pre, cnt, n)
     if tol is not None:
         return pre, cnt, margin, n_close
     return pre, cnt, margin

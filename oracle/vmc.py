@@ -68,6 +68,20 @@ def energy_stats(eloc, counts):
     return np.array([E.real, E.imag, var, S])
 
 
+def combine_stats(stats_list):
+    """Statistics of the union of disjoint sample sets from the statistics of
+    each (the estimator of Eq. energy_est over all samples): S = sum S_r,
+    E = sum S_r E_r / S, Var = sum S_r (Var_r + |E_r - E|^2) / S.  Empty
+    sets (S_r = 0) contribute nothing."""
+    st = np.asarray(stats_list, dtype=np.float64).reshape(-1, 4)
+    st = st[st[:, 3] > 0]
+    S = st[:, 3].sum()
+    Er = (st[:, 3] * st[:, 0]).sum() / S
+    Ei = (st[:, 3] * st[:, 1]).sum() / S
+    var = (st[:, 3] * (st[:, 2] + (st[:, 0] - Er) ** 2 + (st[:, 1] - Ei) ** 2)).sum() / S
+    return np.array([Er, Ei, var, S])
+
+
 def gradient(model, isphys, xs, counts, eloc, stats=None):
     """VMC gradient (Eq. grad_def) with respect to model.parameters(), FP64."""
     xs = np.asarray(xs, dtype=np.uint64)

@@ -217,6 +217,40 @@ def sample(model: Model, ham: Hamiltonian, n_samples: int, seed: int, counter: i
     return x[:k], n[:k]
 
 
+def sample_shard_into(model, ham, n_samples, seed, counter, rank, world, split_level, x_out, n_out, n_unique,
+                      workspace, stream=None, counter_dev=None):
+    """This rank's share of sample_into's pass: the level-``split_level``
+    frontier is split round-robin over ``world`` ranks (asynchronous)."""
+    check(_lib.load().anqs_sample_shard(model._m, ham.handle, int(n_samples), int(seed) & (2**64 - 1),
+                                        int(counter) & (2**64 - 1), _ptr(counter_dev), int(rank), int(world),
+                                        int(split_level), x_out.data_ptr(), n_out.data_ptr(), x_out.numel(),
+                                        n_unique.data_ptr(), workspace.data_ptr(), workspace.numel(),
+                                        _stream(stream)))
+
+
+def sample_shard(model, ham, n_samples, seed, rank, world, split_level, counter=0, stream=None):
+    """Unique determinants and counts of this rank's share (synchronises once)."""
+    dev = model.params.device
+    cap = min(int(n_samples), ham.sector_dim)
+    x = torch.empty(cap, dtype=torch.int64, device=dev)
+    n = torch.empty(cap, dtype=torch.int64, device=dev)
+    nu = torch.zeros(1, dtype=torch.int64, device=dev)
+    ws = _ws(sample_workspace_bytes(model, ham, n_samples), dev)
+    sample_shard_into(model, ham, n_samples, seed, counter, rank, world, split_level, x, n, nu, ws, stream)
+    k = int(nu.item())
+    return x[:k], n[:k]
+
+
+def stats_combine(stats_all: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Statistics of the union of disjoint sample sets; stats_all f64 [world, 4]
+    on the device."""
+    stats_all = stats_all.contiguous()
+    out = out if out is not None else torch.empty(4, dtype=torch.float64, device=stats_all.device)
+    check(_lib.load().anqs_stats_combine(stats_all.data_ptr(), stats_all.numel() // 4, out.data_ptr(),
+                                         _stream(stream)))
+    return out
+
+
 def local_energy_workspace_bytes(model, ham, n_x) -> int:
     b = C.c_size_t()
     check(_lib.load().anqs_local_energy_workspace_size(model._m, ham.handle, n_x, C.byref(b)))

@@ -420,6 +420,32 @@ int anqs_sample(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
                      (cudaStream_t)stream);
 }
 
+int anqs_sample_shard(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint64_t seed, uint64_t counter,
+                      const uint64_t* counter_dev, int rank, int world, int split_level, uint64_t* x_out,
+                      uint64_t* n_out, uint64_t cap, uint64_t* n_unique, void* ws, size_t ws_bytes, void* stream) {
+  ANQS_TRY(check_pair(M, H));
+  if (world < 1 || rank < 0 || rank >= world) return set_error(ANQS_ERR_ARG, "rank %d of world %d", rank, world);
+  if (split_level < 0 || split_level > H->v.n)
+    return set_error(ANQS_ERR_ARG, "split level %d outside 0..%d", split_level, H->v.n);
+  if (n_samples == 0) return set_error(ANQS_ERR_ARG, "n_samples must be >= 1");
+  if (!x_out || !n_out || !n_unique) return set_error(ANQS_ERR_ARG, "null output");
+  uint64_t need = n_samples < H->sector_dim ? n_samples : H->sector_dim;
+  if (cap < need)
+    return set_error(ANQS_ERR_CAPACITY, "cap %llu < min(n_samples, sector_dim) = %llu",
+                     (unsigned long long)cap, (unsigned long long)need);
+  size_t wsn = sampler_workspace(H, n_samples);
+  if (ws_bytes < wsn || (wsn && !ws))
+    return set_error(ANQS_ERR_CAPACITY, "sampler workspace needs %zu bytes", wsn);
+  return run_sampler(M, H, n_samples, seed, counter, counter_dev, x_out, n_out, n_unique, ws, ws_bytes,
+                     (cudaStream_t)stream, rank, world, split_level);
+}
+
+int anqs_stats_combine(const double* stats_in, int world, double* stats_out, void* stream) {
+  if (world < 1) return set_error(ANQS_ERR_ARG, "world %d < 1", world);
+  if (!stats_in || !stats_out) return set_error(ANQS_ERR_ARG, "null stats");
+  return launch_stats_combine(stats_in, world, stats_out, (cudaStream_t)stream);
+}
+
 // ---------------------------------------------------------------------------
 // local energy
 // ---------------------------------------------------------------------------

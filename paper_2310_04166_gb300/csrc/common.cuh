@@ -238,6 +238,7 @@ int launch_table_slot_logits(const anqs_model* md, int p, const uint64_t* prefix
 int launch_eloc_sum(const HamView& hv, Count n_x, const double* hval, const double* hdiag,
                     const float* la_x, const float* ph_x, const float* la_p, const float* ph_p,
                     double* ere, double* eim, cudaStream_t s);
+int launch_stats_combine(const double* in, int world, double* out, cudaStream_t s);
 int launch_stats(const double* ere, const double* eim, const uint64_t* counts, Count n_x,
                  double* stats, cudaStream_t s);
 int launch_grad_cotangents(const double* ere, const double* eim, const uint64_t* counts,
@@ -264,6 +265,7 @@ int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, C
 size_t sampler_workspace(const anqs_ham* ham, uint64_t n_samples);
 int run_sampler(const anqs_model* md, const anqs_ham* ham, uint64_t n_samples, uint64_t seed,
                 uint64_t counter, const uint64_t* counter_dev, uint64_t* x_out, uint64_t* n_out,
-                uint64_t* n_unique, void* ws, size_t ws_bytes, cudaStream_t s);
+                uint64_t* n_unique, void* ws, size_t ws_bytes, cudaStream_t s, int rank = 0, int world = 1,
+                int split_level = 0);
 
 }  // namespace anqs

@@ -111,7 +111,40 @@ __global__ void cotangent_kernel(const double* __restrict__ ere, const double* _
   }
 }
 
+// statistics of the union of `world` disjoint sample sets (law of total
+// variance); one thread, world is small.  Empty sets (S_r = 0, whose E_r is
+// 0/0) are skipped.
+__global__ void stats_combine_kernel(const double* __restrict__ in, int world, double* __restrict__ out) {
+  ANQS_PDL_ENTRY();
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double s = 0.0, sr = 0.0, si = 0.0;
+  for (int r = 0; r < world; ++r) {
+    const double w = in[4 * r + 3];
+    if (!(w > 0.0)) continue;
+    s += w;
+    sr = fma(w, in[4 * r + 0], sr);
+    si = fma(w, in[4 * r + 1], si);
+  }
+  const double Er = sr / s, Ei = si / s;
+  double v = 0.0;
+  for (int r = 0; r < world; ++r) {
+    if (!(in[4 * r + 3] > 0.0)) continue;
+    const double dr = in[4 * r + 0] - Er, di = in[4 * r + 1] - Ei;
+    v = fma(in[4 * r + 3], in[4 * r + 2] + dr * dr + di * di, v);
+  }
+  out[0] = Er;
+  out[1] = Ei;
+  out[2] = v / s;
+  out[3] = s;
+}
+
 }  // namespace
+
+int launch_stats_combine(const double* in, int world, double* out, cudaStream_t s) {
+  ProfScope ps(PROF_STATS, s);
+  ANQS_CUDA_LAUNCH("stats_combine_kernel", launch_k(stats_combine_kernel, dim3(1), dim3(32), 0, s, in, world, out));
+  return ANQS_OK;
+}
 
 int launch_eloc_sum(const HamView& hv, Count n_x, const double* hval, const double* hdiag, const float* la_x,
                     const float* ph_x, const float* la_p, const float* ph_p, double* ere, double* eim,

@@ -503,6 +503,31 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
   }
 }
 
+// Keeps the nodes i with i % world == rank of a device-sized list, in order
+// and in place (one CTA, chunk by chunk: each chunk is read before any of
+// its compacted entries is written).
+__global__ void __launch_bounds__(SMALL_T) shard_kernel(uint64_t* __restrict__ pre, uint64_t* __restrict__ cnt,
+                                                        uint64_t* __restrict__ n_list, int rank, int world) {
+  ANQS_PDL_ENTRY();
+  __shared__ uint32_t s_red[33];
+  const uint64_t nf = *n_list;
+  uint64_t carry = 0;
+  for (uint64_t base = 0; base < nf; base += SMALL_T) {
+    const uint64_t i = base + threadIdx.x;
+    const bool keep = i < nf && (i % uint64_t(world)) == uint64_t(rank);
+    const uint64_t x = keep ? pre[i] : 0ull, c = keep ? cnt[i] : 0ull;
+    uint32_t tot;
+    const uint32_t ex = block_excl_scan_u32(keep ? 1u : 0u, s_red, &tot);  // synchronises the CTA
+    if (keep) {
+      pre[carry + ex] = x;
+      cnt[carry + ex] = c;
+    }
+    carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *n_list = carry;
+}
+
 struct Plan {
   uint64_t F;  // max frontier
   uint64_t *pre[2], *cnt[2], *nblk, *nblk_scan, *child, *flags, *pos, *partial, *n_front;
@@ -564,7 +589,7 @@ size_t sampler_workspace(const anqs_ham* H, uint64_t n_samples) {
 
 int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint64_t seed, uint64_t counter,
                 const uint64_t* counter_dev, uint64_t* x_out, uint64_t* n_out, uint64_t* n_unique, void* ws,
-                size_t ws_bytes, cudaStream_t s) {
+                size_t ws_bytes, cudaStream_t s, int rank, int world, int split_level) {
   Arena A(ws, ws_bytes);
   Plan P;
   plan_ws(H, n_samples, A, P);
@@ -579,6 +604,12 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
     const int cur = p & 1, nxt = cur ^ 1;
     const uint64_t Fp = level_cap(H, n_samples, p);
     uint64_t* nf = P.n_front + cur;
+    if (world > 1 && p == split_level) {
+      // shard: this rank continues from its share of the level-p frontier
+      ProfScope ps(PROF_SAMPLER, s);
+      ANQS_CUDA_LAUNCH("sampler shard_kernel",
+                       launch_k(shard_kernel, dim3(1), dim3(SMALL_T), 0, s, P.pre[cur], P.cnt[cur], nf, rank, world));
+    }
     ANQS_TRY(logits_dispatch(M, H, p, P.pre[cur], nf, Fp, P.logits, s));
     ProfScope ps(PROF_SAMPLER, s);
     const bool last = (p == n - 1);
@@ -602,6 +633,11 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
     uint64_t* nf_next = last ? n_unique : P.n_front + nxt;
     ANQS_TRY(scan(P.flags, nf, 4, Fp * 4, P.partial, P.pos, nf_next, s));
     ANQS_CUDA_LAUNCH("sampler scatter_kernel", launch_k(scatter_kernel, dim3(blocks_for(Fp * 4, 256, 152 * 8)), dim3(256), 0, s, p, P.pre[cur], P.child, nf, P.pos, last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt]));
+  }
+  if (world > 1 && split_level == n) {
+    ProfScope ps(PROF_SAMPLER, s);
+    ANQS_CUDA_LAUNCH("sampler shard_kernel",
+                     launch_k(shard_kernel, dim3(1), dim3(SMALL_T), 0, s, x_out, n_out, n_unique, rank, world));
   }
   return ANQS_OK;
 }

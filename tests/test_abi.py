@@ -74,3 +74,10 @@ def test_invalid_descriptions_rejected_on_host(lib):
 def test_null_arguments_rejected(lib):
     assert lib.anqs_hamiltonian_create(None, 4, 2, 2, None, None, 0.0) == -1
     assert lib.anqs_connected(None, None, 0, None, None, None, None, None) == -1
+
+
+def test_shard_and_combine_arguments_rejected_on_host(lib):
+    assert lib.anqs_stats_combine(None, 1, None, None) == -1
+    buf = C.create_string_buffer(8 * 8)
+    assert lib.anqs_stats_combine(buf, 0, buf, None) == -1
+    assert lib.anqs_sample_shard(None, None, 10, 0, 0, None, 0, 2, 1, None, None, 0, None, None, 0, None) == -1
