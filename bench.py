@@ -13,7 +13,11 @@ MLP with 3 hidden layers of width 128, N_s = 1e5.
 
 Prints one JSON line.  `value` = unique samples whose local energy was
 completed, per second of device time (max over ranks), inputs resident in
-HBM, L2 flushed between timed steps.  `e2e` = the same through the public
+HBM, L2 flushed between timed steps, for the chosen form (--form, default
+BF16 tensor-core network); `forms` reports both forms timed the same way in
+the same run (plain FP32 SIMT network and BF16), their ratio, and for each
+the |E_gpu - E_oracle| of the count-weighted energy on that form's last
+sample set against the FP64 oracle (evaluated in the CPU-baseline leg).  `e2e` = the same through the public
 API with host buffers: parameters copied host->device and energy statistics
 plus gradient copied back every step.  `--impl reference` times the FP64 CPU
 oracle on the same workload.
@@ -124,22 +128,50 @@ def _dist():
     return 1, 0, 0, None
 
 
-def _cpu_baseline(w, seconds=10.0, n_max=100000):
-    """Time the FP64 oracle's local energy on a bounded prefix of the unique
-    samples of one oracle sampling pass (its own conditionals, same seed)."""
+def _cpu_baseline(w, sets=None, seconds=10.0, n_max=100000):
+    """Time the FP64 oracle's local energy on the host cores.
+
+    With ``sets`` ({form: {"x", "cnt", "stats"}}: the unique samples, counts
+    and GPU statistics of a form's last timed step) the oracle evaluates
+    those samples, a whole set when it fits in ``seconds`` per set, and
+    reports |E_gpu - E_oracle| of the count-weighted energy on the same
+    samples; otherwise it cycles over the unique samples of one oracle
+    sampling pass.  The value is unique samples per second over all the
+    oracle's work."""
     from oracle.anqs import MLPAnsatz, TFAnsatz
     from oracle.hamiltonian import Hamiltonian as OHam
     from oracle.sampler import sample as osample
     from oracle.sector import molecular_isphys
-    from oracle.vmc import local_energy
+    from oracle.vmc import energy_stats, local_energy
 
     oham = OHam(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
     ip = molecular_isphys(w["n"], w["n_alpha"], w["n_beta"])
     om = MLPAnsatz(w["params_struct"], w["n"]) if w["kind"] == "mlp" else \
         TFAnsatz(w["params_struct"], w["n"], w["n_heads"])
+    k = 8
+    if sets:
+        done, busy, delta, notes = 0, 0.0, {}, []
+        for form, st in sets.items():
+            xs = st["x"].cpu().numpy().astype(np.uint64)
+            es, t0 = [], time.perf_counter()
+            for a in range(0, len(xs), k):
+                if time.perf_counter() - t0 > seconds or done >= n_max:
+                    break
+                es.append(local_energy(om, ip, oham, xs[a:a + k]))
+            dt = time.perf_counter() - t0
+            m = sum(len(e) for e in es)
+            done, busy = done + m, busy + dt
+            notes.append(f"{m} of the {len(xs)} unique samples of the {form} form's last step")
+            if m == len(xs):
+                ref = energy_stats(np.concatenate(es), st["cnt"])
+                delta[form] = {"E_oracle_ha": float(ref[0]), "abs_dE_ha": abs(float(st["stats"][0]) - ref[0])}
+            else:
+                delta[form] = {"abs_dE_ha": None, "note": "oracle did not finish the set in the time bound"}
+        return {"value": done / busy, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+                "sample": "FP64 oracle local energy (connected set + log psi + sum) of " + "; ".join(notes) +
+                          f", {busy:.1f} s", "delta_E": delta}
     xs, _, _ = osample(om, ip, w["n"], w["n_samples"], seed=12345)
     done, t0 = 0, time.perf_counter()
-    k = 8
     while done < n_max and time.perf_counter() - t0 < seconds:
         start = done % len(xs)
         chunk = xs[start:start + k]
@@ -183,76 +215,31 @@ def _config(w, args):
                             "gradient all-reduce per step" if args.gpus > 1 else "single GPU")}
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default=os.environ.get("ANQS_BENCH_FORM", "bf16"), choices=["fp32", "bf16"])
-    ap.add_argument("--workload", default="h2o")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--kernel-case", action="store_true",
-                    help="one FP32-form sampling pass, then one local-energy and one gradient call in the "
-                         "chosen form (the launch sequence to capture with ncu), then exit")
-    args = ap.parse_args()
-    args.warmup = max(args.warmup, 3)
+# DRAM bytes per launch from one ncu capture of the same kernel build and
+# workload (`ncu --set full -k regex:<kernel> -c 1 python bench.py
+# --kernel-case`, h2o, BF16 form): dram__bytes_read.sum + dram__bytes_write.sum
+TRAFFIC = {("h2o", "bf16"): {"mlp_fp32_grad_kernel": 1163776 + 135680, "mlp_tc_suffix_kernel": 1240064,
+                             "eloc_assemble_kernel": 4650240, "connected_kernel": 49920}}
 
-    from synthetic import workload
-    w = workload(args.workload)
-    ws, rank, local, dist = _dist()
-    if args.impl == "reference":
-        _reference_arm(args, w, ws, rank)
-        if dist:
-            dist.destroy_process_group()
-        return
 
-    import paper_2310_04166_gb300 as A
-    from paper_2310_04166_gb300 import _lib
-    lib = _lib.load()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream()
-
-    form = args.form
-    ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
-    params = torch.tensor(w["params"], device=dev)
-    try:
-        model = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form=form)
-    except A.AnqsError as e:
-        if form == "bf16" and "UNSUPPORTED" in str(e):
-            form = "fp32"
-            args.form = "fp32 (bf16 form unavailable in this build)"
-            model = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form="fp32")
-        else:
-            raise
+def _run_form(A, lib, args, w, form, ham, params, dev, rank, dist, stream_clocks):
+    """Graph-captured timing of one form: returns throughput, end-to-end
+    throughput, the eager per-kernel profile and the last step's sample set
+    with its statistics."""
+    import ctypes as C
+    model = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form=form)
     Ns = w["n_samples"]
-    if args.kernel_case:
-        m32 = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form="fp32")
-        xk, nk = A.sample(m32, ham, Ns, seed=99)
-        ek = A.local_energy(model, ham, xk, nk)
-        A.grad(model, ham, xk, nk, ek[0], ek[1], ek[2])
-        torch.cuda.synchronize()
-        print(json.dumps({"kernel_case": args.workload, "form": form, "n_unique": xk.numel(),
-                          "E": float(ek[2][0])}))
-        return
     cap = min(Ns, ham.sector_dim)
-    x = torch.empty(cap, dtype=torch.int64, device=dev)
-    cnt = torch.empty(cap, dtype=torch.int64, device=dev)
-    nu = torch.zeros(1, dtype=torch.int64, device=dev)
-    ctr = torch.zeros(1, dtype=torch.int64, device=dev)
+    i64, f64 = dict(dtype=torch.int64, device=dev), dict(dtype=torch.float64, device=dev)
+    x, cnt, nu, ctr = torch.empty(cap, **i64), torch.empty(cap, **i64), torch.zeros(1, **i64), torch.zeros(1, **i64)
     ws_s = A._ws(A.sample_workspace_bytes(model, ham, Ns), dev)
     ws_e = A._ws(A.local_energy_workspace_bytes(model, ham, cap), dev)
     ws_g = A._ws(A.grad_workspace_bytes(model, ham, cap), dev)
-    ere = torch.zeros(cap, dtype=torch.float64, device=dev)
-    eim = torch.zeros_like(ere)
-    stats = torch.zeros(4, dtype=torch.float64, device=dev)
+    ere, eim, stats, stats_g = torch.zeros(cap, **f64), torch.zeros(cap, **f64), torch.zeros(4, **f64), \
+        torch.zeros(4, **f64)
     g = torch.zeros(model.n_params, dtype=torch.float32, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     seed = 1234 + 7919 * rank
-    import ctypes as C
-
-    stats_g = torch.zeros(4, dtype=torch.float64, device=dev)
 
     def step_a():
         if form == "bf16":
@@ -274,8 +261,8 @@ def main():
 
     def exchange():
         """Data-parallel exchange (one process per GPU, each with its own
-        sample set): gather the ranks' statistics, combine them on the device,
-        and after the gradient pass sum the gradients."""
+        sample set): gather the ranks' statistics and combine them on the
+        device; the gradients are summed after the gradient pass."""
         from paper_2310_04166_gb300.dist import exchange_stats
         A.stats_combine(exchange_stats(stats), out=stats_g)
 
@@ -284,7 +271,7 @@ def main():
         step()
     torch.cuda.synchronize()
     lib.anqs_profile_enable(1)
-    n_prof = max(5, args.steps // 2)
+    n_prof = max(5, min(args.steps // 2, 200))
     for _ in range(n_prof):
         flush.fill_(1)
         step()
@@ -337,7 +324,7 @@ def main():
 
     times, uniq = [], []
     stream = torch.cuda.current_stream()
-    with Clocks(local) as clk:
+    with Clocks(torch.cuda.current_device()) as clk:
         for i in range(args.steps):
             flush.fill_(i & 0xFF)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -351,20 +338,20 @@ def main():
             uniq.append(int(nu.item()))
     if dist:
         dist.barrier()
-
-    total_ms = sum(times)
-    total_u = sum(uniq)
-    t = torch.tensor([total_ms, float(total_u)], dtype=torch.float64, device=dev)
+    total_ms, total_u = sum(times), sum(uniq)
     if dist:
+        t = torch.tensor([total_ms, float(total_u)], dtype=torch.float64, device=dev)
         tm = t.clone()
         dist.all_reduce(tm[:1], op=dist.ReduceOp.MAX)
         dist.all_reduce(t[1:], op=dist.ReduceOp.SUM)
         total_ms, total_u = float(tm[0]), float(t[1])
     value = total_u / (total_ms / 1e3)
+    k_last = int(nu.item())
+    last = {"x": x[:k_last].clone(), "cnt": cnt[:k_last].cpu().numpy(), "stats": stats.cpu().numpy().copy()}
 
     # end to end through the public API: host parameters in, host energy
     # statistics and gradient out, around each graph replay
-    h_params = torch.tensor(w["params"]).pin_memory()
+    h_params = params.detach().cpu().pin_memory()
     h_stats = torch.empty(4, dtype=torch.float64).pin_memory()
     h_grad = torch.empty(model.n_params, dtype=torch.float32).pin_memory()
     e2e_ms, e2e_u = 0.0, 0
@@ -379,36 +366,94 @@ def main():
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_u += int(nu.item())
-    e2e_val = e2e_u / (e2e_ms / 1e3)
+    return {"model": model, "value": value, "ms_per_step": total_ms / args.steps, "n_unique": total_u / args.steps,
+            "e2e": {"value": e2e_u / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(params.numel() * 4),
+                    "d2h_bytes_per_step": int(4 * 8 + model.n_params * 4 + 8)},
+            "launches_per_step": launches_per_step, "prof": prof, "n_prof": n_prof, "last": last,
+            "clocks": clk.summary()}
 
-    if rank != 0:
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default=os.environ.get("ANQS_BENCH_FORM", "bf16"), choices=["fp32", "bf16"])
+    ap.add_argument("--workload", default="h2o")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--one-form", action="store_true", help="time only --form (default: both forms)")
+    ap.add_argument("--kernel-case", action="store_true",
+                    help="one FP32-form sampling pass, then one local-energy and one gradient call in the "
+                         "chosen form (the launch sequence to capture with ncu), then exit")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    from synthetic import workload
+    w = workload(args.workload)
+    ws, rank, local, dist = _dist()
+    if args.impl == "reference":
+        _reference_arm(args, w, ws, rank)
         if dist:
             dist.destroy_process_group()
         return
 
+    import paper_2310_04166_gb300 as A
+    from paper_2310_04166_gb300 import _lib
+    lib = _lib.load()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    params = torch.tensor(w["params"], device=dev)
+    form = args.form
+    if args.kernel_case:
+        model = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form=form)
+        m32 = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form="fp32")
+        xk, nk = A.sample(m32, ham, w["n_samples"], seed=99)
+        ek = A.local_energy(model, ham, xk, nk)
+        A.grad(model, ham, xk, nk, ek[0], ek[1], ek[2])
+        torch.cuda.synchronize()
+        print(json.dumps({"kernel_case": args.workload, "form": form, "n_unique": xk.numel(),
+                          "E": float(ek[2][0])}))
+        return
+
+    runs = {form: _run_form(A, lib, args, w, form, ham, params, dev, rank, dist, True)}
+    if not args.one_form:
+        other = "fp32" if form == "bf16" else "bf16"
+        runs[other] = _run_form(A, lib, args, w, other, ham, params, dev, rank, dist, True)
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    r = runs[form]
+
     # rooflines of the kernel families (eager profiled pass)
     peaks, src = _peaks()
-    n_unq = total_u / args.steps
-    k_last = int(nu.item())
-    work = _tc_work(A, ham, model, w, x[:k_last])
-    roof, roofs = _rooflines(prof, work, n_prof, peaks, src)
-    top = max(prof.items(), key=lambda kv: kv[1][1])[0] if prof else None
+    work = _tc_work(A, ham, r["model"], w, r["last"]["x"])
+    roof, roofs = _rooflines(r["prof"], work, r["n_prof"], peaks, src, TRAFFIC.get((args.workload, form), {}))
+    top = max(r["prof"].items(), key=lambda kv: kv[1][1])[0] if r["prof"] else None
 
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = _cpu_baseline(w)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        cpu = _cpu_baseline(w, {f: v["last"] for f, v in runs.items()})
+    forms = {f: {"value": v["value"], "ms_per_step": v["ms_per_step"], "e2e": v["e2e"]["value"],
+                 "n_unique_per_step": v["n_unique"], "E_ha": float(v["last"]["stats"][0])} for f, v in runs.items()}
+    if cpu:
+        for f, d in cpu.pop("delta_E", {}).items():
+            forms[f].update(d)
+    if "fp32" in runs and "bf16" in runs:
+        forms["bf16_over_fp32"] = runs["bf16"]["value"] / runs["fp32"]["value"]
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16 GEMM / f32 heads / f64 E_loc" if form == "bf16" else "f32 network / f64 E_loc",
-            "data": "synthetic", "config": _config(w, args), "n_unique_per_step": n_unq,
-            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(params.numel() * 4),
-                    "d2h_bytes_per_step": int(4 * 8 + model.n_params * 4 + 8)},
-            "gpu_launches": launches_per_step * args.steps,
-            "launches_per_step": launches_per_step,
-            "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in prof.items()},
-            "kernels_note": f"CUDA-event totals over {n_prof} eager (non-graph) steps",
-            "roofline": roof, "rooflines": roofs, "top_kernel_family": top, "clocks": clk.summary()}
+            "data": "synthetic", "config": _config(w, args), "n_unique_per_step": r["n_unique"],
+            "e2e": r["e2e"], "forms": forms,
+            "gpu_launches": r["launches_per_step"] * args.steps,
+            "launches_per_step": r["launches_per_step"],
+            "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 4)} for k, v in r["prof"].items()},
+            "kernels_note": f"CUDA-event totals over {r['n_prof']} eager (non-graph) steps",
+            "roofline": roof, "rooflines": roofs, "top_kernel_family": top, "clocks": r["clocks"]}
     if cpu:
         line["cpu_baseline"] = cpu
     print(json.dumps(line), flush=True)
@@ -444,7 +489,7 @@ def _tc_work(A, ham, model, w, x):
             "connected_kernel": float(len(j) * (8 + 8 + 1) + len(x) * 8)}
 
 
-def _rooflines(prof, work, steps, peaks, src):
+def _rooflines(prof, work, steps, peaks, src, traffic):
     """Roofline of every kernel family with a defined bound (work per step x
     steps / total event time) and the dominant one by time."""
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
@@ -468,7 +513,7 @@ def _rooflines(prof, work, steps, peaks, src):
             ach = per_launch / avg_s / 1e9
             note = f"{src} copy bandwidth; algorithmic bytes"
         out[name] = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
-                     "frac": ach / peak, "traffic": None, "avg_launch_us": avg_s * 1e6,
+                     "frac": ach / peak, "traffic": traffic.get(name), "avg_launch_us": avg_s * 1e6,
                      "work_per_launch": per_launch, "note": note}
     dominant = max(out.values(), key=lambda r: prof[r["kernel"]][1]) if out else None
     return dominant, out
