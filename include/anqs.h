@@ -93,7 +93,7 @@ typedef struct {
   int32_t n_orb;     /* spatial orbitals n (slots), 1..32 */
   int32_t width;     /* MLP: hidden width (multiple of 32, <= 256) */
   int32_t n_hidden;  /* MLP: hidden layers L (1..8) */
-  int32_t d_model;   /* TF: model width d (multiple of 32, <= 256) */
+  int32_t d_model;   /* TF: model width d in {32, 64, 128, 256} */
   int32_t n_heads;   /* TF: heads (d_model % n_heads == 0) */
   int32_t n_layers;  /* TF: blocks */
 } anqs_model_desc;

@@ -95,6 +95,8 @@ int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, C
         return launch_mlp_tc_logpsi(M, H->v, x, n_x.n, la, ph, s);
       }
       return launch_mlp_fp32_logpsi(M->mlp, H->v, x, n_x, la, ph, s);
+    case ANQS_MODEL_TF:
+      return launch_tf_fp32_logpsi(M->tf, H->v, x, n_x, la, ph, s);
     case ANQS_MODEL_TABLE:
       return launch_table_logpsi(M, H->v, x, n_x, la, ph, s);
     default:
@@ -268,8 +270,8 @@ static int validate_desc(const anqs_model_desc* d) {
         return set_error(ANQS_ERR_UNSUPPORTED, "MLP hidden layers %d outside 1..8", d->n_hidden);
       return ANQS_OK;
     case ANQS_MODEL_TF:
-      if (d->d_model < 32 || d->d_model > 256 || d->d_model % 32)
-        return set_error(ANQS_ERR_UNSUPPORTED, "d_model %d not a multiple of 32 in 32..256", d->d_model);
+      if (d->d_model != 32 && d->d_model != 64 && d->d_model != 128 && d->d_model != 256)
+        return set_error(ANQS_ERR_UNSUPPORTED, "d_model %d not in {32,64,128,256}", d->d_model);
       if (d->n_heads < 1 || d->d_model % d->n_heads)
         return set_error(ANQS_ERR_UNSUPPORTED, "n_heads %d does not divide d_model", d->n_heads);
       if (d->n_layers < 1 || d->n_layers > 16)
@@ -312,6 +314,8 @@ int anqs_model_create(anqs_model** out, const anqs_model_desc* d, const float* p
   *out = nullptr;
   ANQS_TRY(validate_desc(d));
   if (!params) return set_error(ANQS_ERR_ARG, "null parameters");
+  if (d->kind == ANQS_MODEL_TF && d->form == ANQS_FORM_BF16)
+    return set_error(ANQS_ERR_UNSUPPORTED, "transformer BF16 form not built");
   anqs_model* M = new anqs_model();
   M->d = *d;
   ANQS_CUDA(cudaGetDevice(&M->device));

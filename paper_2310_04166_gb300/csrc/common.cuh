@@ -228,6 +228,10 @@ int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x,
 size_t mlp_fp32_grad_partial_floats(const MlpView& m, uint64_t n_x);
 
 // table.cu
+int launch_tf_fp32_logpsi(const TfView& m, const HamView& hv, const uint64_t* x, Count n_x, float* la, float* ph,
+                          cudaStream_t s);
+int launch_tf_fp32_slot_logits(const TfView& m, int p, const uint64_t* pre, const uint64_t* nr, uint64_t max_rows,
+                               float* out, cudaStream_t s);
 int launch_table_logpsi(const anqs_model* md, const HamView& hv, const uint64_t* x, Count n_x,
                         float* la, float* ph, cudaStream_t s);
 int launch_table_slot_logits(const anqs_model* md, int p, const uint64_t* prefixes,

@@ -649,6 +649,8 @@ int logits_dispatch(const anqs_model* M, const anqs_ham* H, int p, const uint64_
       if (M->d.form == ANQS_FORM_BF16)
         return launch_mlp_tc_slot_logits(M, H->v, p, pre, n_dev, max_rows, out8, s);
       return launch_mlp_fp32_slot_logits(M->mlp, p, pre, n_dev, max_rows, out8, s);
+    case ANQS_MODEL_TF:
+      return launch_tf_fp32_slot_logits(M->tf, p, pre, n_dev, max_rows, out8, s);
     case ANQS_MODEL_TABLE:
       return launch_table_slot_logits(M, p, pre, n_dev, max_rows, out8, s);
     default:

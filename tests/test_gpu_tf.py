@@ -1,0 +1,136 @@
+"""GPU parity of the causal-transformer ansatz, FP32 form (SIMT), against the
+FP64 oracle.
+
+The FP32 forward carries a relative rounding error of a few float32 ulp per
+operation through LayerNorm, attention and the FFN; over L blocks and n
+slot terms the log-amplitude moves by much less than TOL = 1e-4 (the
+measured error is ~1e-6).  A local energy then moves by at most
+sum_k |H_k psi(x'_k)/psi(x)| (e^{2 TOL} - 1), evaluated per sample from the
+oracle's own terms; the sampler may send a draw another way only when it
+falls within the conditional's FP32 error of a boundary (counted by the
+oracle with tol = 1e-5).
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle.anqs import TFAnsatz, log_psi
+from oracle.hamiltonian import Hamiltonian as OHam
+from oracle.sampler import lexicographic_key, sample as osample
+from oracle.sector import molecular_isphys, sector_states
+from oracle.vmc import energy_stats, local_energy
+from synthetic import flatten_tf, integrals, tf_params, workload
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def A():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2310_04166_gb300 as mod
+    from paper_2310_04166_gb300 import _lib
+    _lib.load()
+    return mod
+
+
+def _dev(a):
+    return torch.tensor(np.asarray(a).astype(np.int64), device="cuda")
+
+
+def _custom(A, n, na, nb, d, H, L, seed):
+    P = tf_params(seed, n, d, L, bias_std=0.2)
+    h, g, e = integrals(seed, n, n)
+    ham = A.Hamiltonian(h, g, e, na, nb)
+    model = A.Model.transformer(n, d, H, L, torch.tensor(flatten_tf(P), device="cuda"))
+    return ham, model, TFAnsatz(P, n, H), molecular_isphys(n, na, nb), OHam(h, g, e, na, nb)
+
+
+def _n2(A):
+    w = workload("n2", bias_std=0.2)
+    ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    model = A.Model.transformer(w["n"], w["d_model"], w["n_heads"], w["n_layers"],
+                                torch.tensor(w["params"], device="cuda"))
+    om = TFAnsatz(w["params_struct"], w["n"], w["n_heads"])
+    ip = molecular_isphys(w["n"], w["n_alpha"], w["n_beta"])
+    oham = OHam(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    return w, ham, model, om, ip, oham
+
+
+@pytest.mark.parametrize("n,na,nb,d,H,L", [(4, 2, 2, 32, 2, 1), (5, 2, 3, 64, 4, 2), (6, 3, 3, 128, 8, 2),
+                                           (5, 2, 2, 256, 4, 1)])
+def test_tf_logpsi_fp32_every_width(A, n, na, nb, d, H, L):
+    ham, model, om, ip, _ = _custom(A, n, na, nb, d, H, L, seed=n + d)
+    st = np.array(sector_states(n, na, nb), dtype=np.uint64)
+    la, ph = A.logpsi(model, ham, _dev(st))
+    rla, rph = log_psi(om, ip, st)
+    assert np.abs(la.cpu().numpy() - rla.numpy()).max() < TOL
+    assert np.abs(ph.cpu().numpy() - rph.numpy()).max() < TOL
+    bad = np.array([0, int(st[0]) ^ 1], dtype=np.uint64)
+    assert torch.isneginf(A.logpsi(model, ham, _dev(bad))[0]).all()
+
+
+def test_tf_logpsi_fp32_n2_whole_sector(A):
+    w, ham, model, om, ip, _ = _n2(A)
+    st = np.array(sector_states(w["n"], w["n_alpha"], w["n_beta"]), dtype=np.uint64)
+    la, ph = A.logpsi(model, ham, _dev(st))
+    rla, rph = log_psi(om, ip, st)
+    assert np.abs(la.cpu().numpy() - rla.numpy()).max() < TOL
+    assert np.abs(ph.cpu().numpy() - rph.numpy()).max() < TOL
+    # normalised on the sector
+    assert abs(np.exp(2 * la.double().cpu().numpy()).sum() - 1.0) < 1e-4
+
+
+def test_tf_logpsi_fp32_large_shape(A):
+    """26 slots, d 128, 8 heads, 4 blocks: two sequences per tile."""
+    w = workload("large", bias_std=0.2)
+    ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    model = A.Model.transformer(w["n"], w["d_model"], w["n_heads"], w["n_layers"],
+                                torch.tensor(w["params"], device="cuda"))
+    om = TFAnsatz(w["params_struct"], w["n"], w["n_heads"])
+    ip = molecular_isphys(w["n"], w["n_alpha"], w["n_beta"])
+    x, _ = A.sample(model, ham, 2000, seed=1)
+    xs = x.cpu().numpy().astype(np.uint64)[:97]
+    la, ph = A.logpsi(model, ham, _dev(xs))
+    rla, rph = log_psi(om, ip, xs)
+    assert np.abs(la.cpu().numpy() - rla.numpy()).max() < TOL
+    assert np.abs(ph.cpu().numpy() - rph.numpy()).max() < TOL
+
+
+def test_tf_sampler_fp32_n2(A):
+    w, ham, model, om, ip, _ = _n2(A)
+    Ns = 100_000
+    x, c = A.sample(model, ham, Ns, seed=3, counter=2)
+    x, c = x.cpu().numpy().astype(np.uint64), c.cpu().numpy()
+    ox, on, _, n_close = osample(om, ip, w["n"], Ns, seed=3, counter=2, tol=1e-5)
+    assert c.sum() == Ns
+    allx = np.union1d(ox, x)
+    a = np.zeros(len(allx), np.int64)
+    b = np.zeros(len(allx), np.int64)
+    a[np.searchsorted(allx, ox)] = on
+    b[np.searchsorted(allx, x)] = c
+    assert np.abs(a - b).sum() <= 2 * n_close
+    assert np.all(np.diff(lexicographic_key(x, w["n"]).astype(np.float64)) > 0)
+
+
+def test_tf_local_energy_fp32_n2(A):
+    w, ham, model, om, ip, oham = _n2(A)
+    ox, on, _ = osample(om, ip, w["n"], 20_000, seed=9)
+    keep = np.argsort(-on, kind="stable")[:96]  # the most frequent samples (bounded oracle work)
+    ox, on = ox[keep], on[keep]
+    ere, eim, stats = A.local_energy(model, ham, _dev(ox), _dev(on))
+    e_ref = local_energy(om, ip, oham, ox)
+    la, _ = log_psi(om, ip, ox)
+    lists = [oham.connected(int(v)) for v in ox]
+    K = len(lists[0])
+    xs = np.array([t[0] for L in lists for t in L], dtype=np.uint64)
+    hv = np.array([t[1] for L in lists for t in L]).reshape(-1, K)
+    lp, _ = log_psi(om, ip, xs)
+    r = np.exp(lp.numpy().reshape(-1, K) - la.numpy()[:, None])
+    bound = (np.abs(hv) * r).sum(1) * (np.exp(2 * TOL) - 1)
+    err = np.abs((ere.cpu().numpy() - e_ref.real) + 1j * (eim.cpu().numpy() - e_ref.imag))
+    assert np.all(err <= bound), (err / bound).max()
+    s_ref = energy_stats(e_ref, on)
+    wts = on / on.sum()
+    assert abs(stats.cpu().numpy()[0] - s_ref[0]) <= (wts * err).sum() + 1e-12
