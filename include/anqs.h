@@ -289,9 +289,14 @@ ANQS_API int anqs_grad(const anqs_model* model, const anqs_ham* ham, const uint6
  * (n_params floats, overwritten) = d/dtheta sum_l [cot_abs_dev[l] log|psi(x_l)|
  * + cot_phase_dev[l] arg psi(x_l)].  anqs_grad is this product with the
  * cotangents 2 (n_l/S) Re(eloc_l - E) and 2 (n_l/S) Im(eloc_l - E).
- * No workspace. */
+ * The transformer's adjoint keeps every forward activation of the n_x
+ * determinants in the workspace (anqs_logpsi_vjp_workspace_size); the MLP's
+ * needs none (workspace may be null). */
+ANQS_API int anqs_logpsi_vjp_workspace_size(const anqs_model* model, const anqs_ham* ham, uint64_t n_x,
+                                            size_t* bytes);
 ANQS_API int anqs_logpsi_vjp(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev, uint64_t n_x,
-                    const float* cot_abs_dev, const float* cot_phase_dev, float* grad_dev, void* stream);
+                    const float* cot_abs_dev, const float* cot_phase_dev, float* grad_dev, void* workspace_dev,
+                    size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
  * Local energy without caller workspace (the paper has no counterpart: this

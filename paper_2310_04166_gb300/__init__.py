@@ -162,8 +162,11 @@ def logpsi_vjp(model: Model, ham: Hamiltonian, x: torch.Tensor, cot_abs: torch.T
     g = torch.empty(model.n_params, dtype=torch.float32, device=x.device)
     ca = cot_abs.to(torch.float32).contiguous()
     cp = cot_phase.to(torch.float32).contiguous()
+    b = C.c_size_t()
+    check(_lib.load().anqs_logpsi_vjp_workspace_size(model._m, ham.handle, x.numel(), C.byref(b)))
+    ws = _ws(b.value, x.device) if b.value else None
     check(_lib.load().anqs_logpsi_vjp(model._m, ham.handle, x.data_ptr(), x.numel(), ca.data_ptr(), cp.data_ptr(),
-                                      g.data_ptr(), _stream(stream)))
+                                      g.data_ptr(), _ptr(ws), b.value, _stream(stream)))
     return g
 
 

@@ -43,7 +43,8 @@ SIGNATURES = {
     "anqs_model_destroy": (C.c_int, [_VP]),
     "anqs_model_sync": (C.c_int, [_VP, _VP]),
     "anqs_logpsi": (C.c_int, [_VP, _VP, _VP, _U64, _VP, _VP, _VP]),
-    "anqs_logpsi_vjp": (C.c_int, [_VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
+    "anqs_logpsi_vjp": (C.c_int, [_VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _SZ, _VP]),
+    "anqs_logpsi_vjp_workspace_size": (C.c_int, [_VP, _VP, _U64, C.POINTER(_SZ)]),
     "anqs_sample_workspace_size": (C.c_int, [_VP, _VP, _U64, C.POINTER(_SZ)]),
     "anqs_sample": (C.c_int, [_VP, _VP, _U64, _U64, _U64, _VP, _VP, _VP, _U64, _VP, _VP, _SZ, _VP]),
 "anqs_sample_shard": (C.c_int, [_VP, _VP, _U64, _U64, _U64, _VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _U64, _VP,

@@ -123,8 +123,9 @@ static size_t eloc_plain_ws(const anqs_ham* H, uint64_t n_x, Arena& A, uint64_t*
 
 namespace anqs {
 static int vjp_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, const float* cl,
-                        const float* cp, float* grad, float* part, cudaStream_t s) {
+                        const float* cp, float* grad, float* part, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (M->d.kind == ANQS_MODEL_MLP) return launch_mlp_fp32_grad(M->mlp, H->v, x, n_x, cl, cp, grad, part, s);
+  if (M->d.kind == ANQS_MODEL_TF) return launch_tf_fp32_grad(M->tf, H->v, x, n_x, cl, cp, grad, ws, ws_bytes, s);
   return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not available in this build", M->d.kind);
 }
 }  // namespace anqs
@@ -513,6 +514,7 @@ int anqs_grad_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_
   A.take<float>(n_x);
   A.take<float>(n_x);
   if (M->d.kind == ANQS_MODEL_MLP) A.take<float>(mlp_fp32_grad_partial_floats(M->mlp, n_x));
+  if (M->d.kind == ANQS_MODEL_TF) A.take<char>(tf_grad_workspace(M->tf, n_x));
   *bytes = A.off;
   return ANQS_OK;
 }
@@ -527,23 +529,34 @@ int anqs_grad(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const u
   float* cl = A.take<float>(n_x);
   float* cp = A.take<float>(n_x);
   float* part = (M->d.kind == ANQS_MODEL_MLP) ? A.take<float>(mlp_fp32_grad_partial_floats(M->mlp, n_x)) : nullptr;
+  const size_t tfb = (M->d.kind == ANQS_MODEL_TF) ? tf_grad_workspace(M->tf, n_x) : 0;
+  void* tfws = tfb ? A.take<char>(tfb) : nullptr;
   if (!A.fits() || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", A.off);
   cudaStream_t s = (cudaStream_t)stream;
   if (!part) ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));
   const Count nc{n_x, n_x_dev, 1};
   ANQS_TRY(launch_grad_cotangents(ere, eim, counts, stats, nc, cl, cp, s));
-  return vjp_dispatch(M, H, x, nc, cl, cp, grad, part, s);
+  return vjp_dispatch(M, H, x, nc, cl, cp, grad, part, tfws, tfb, s);
+}
+
+int anqs_logpsi_vjp_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_x, size_t* bytes) {
+  ANQS_TRY(check_pair(M, H));
+  if (!bytes) return set_error(ANQS_ERR_ARG, "null output");
+  *bytes = (M->d.kind == ANQS_MODEL_TF) ? tf_grad_workspace(M->tf, n_x) : 0;
+  return ANQS_OK;
 }
 
 int anqs_logpsi_vjp(const anqs_model* M, const anqs_ham* H, const uint64_t* x, uint64_t n_x, const float* cl,
-                    const float* cp, float* grad, void* stream) {
+                    const float* cp, float* grad, void* ws, size_t ws_bytes, void* stream) {
   ANQS_TRY(check_pair(M, H));
   if (!grad) return set_error(ANQS_ERR_ARG, "null gradient output");
+  if (n_x && (!x || !cl || !cp)) return set_error(ANQS_ERR_ARG, "null array argument");
+  const size_t need = (M->d.kind == ANQS_MODEL_TF) ? tf_grad_workspace(M->tf, n_x) : 0;
+  if (ws_bytes < need || (need && !ws)) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
   cudaStream_t s = (cudaStream_t)stream;
   ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));
   if (n_x == 0) return ANQS_OK;
-  if (!x || !cl || !cp) return set_error(ANQS_ERR_ARG, "null array argument");
-  return vjp_dispatch(M, H, x, host_count(n_x), cl, cp, grad, nullptr, s);
+  return vjp_dispatch(M, H, x, host_count(n_x), cl, cp, grad, nullptr, ws, ws_bytes, s);
 }
 
 }  // extern "C"

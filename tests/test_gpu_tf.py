@@ -134,3 +134,110 @@ def test_tf_local_energy_fp32_n2(A):
     s_ref = energy_stats(e_ref, on)
     wts = on / on.sum()
     assert abs(stats.cpu().numpy()[0] - s_ref[0]) <= (wts * err).sum() + 1e-12
+
+
+# ---------------------------------------------------------------------------
+# adjoint (FP32): the VJP of the masked log psi against the FP64 oracle's
+# autograd, for arbitrary cotangents and through anqs_grad (Eq. grad_def)
+# ---------------------------------------------------------------------------
+def _flat_grad(gs):
+    return np.concatenate([t.reshape(-1).numpy() for t in gs])
+
+
+@pytest.mark.parametrize("n,na,nb,d,H,L", [(4, 2, 2, 32, 2, 1), (5, 2, 3, 64, 4, 2), (6, 3, 3, 128, 8, 2),
+                                           (5, 2, 2, 256, 4, 1)])
+def test_tf_logpsi_vjp_every_width(A, n, na, nb, d, H, L):
+    ham, model, om, ip, _ = _custom(A, n, na, nb, d, H, L, seed=n + d)
+    st = np.array(sector_states(n, na, nb), dtype=np.uint64)
+    rng = np.random.default_rng(d)
+    ca, cp = rng.normal(size=len(st)), rng.normal(size=len(st))
+    g = A.logpsi_vjp(model, ham, _dev(st), torch.tensor(ca, device="cuda"), torch.tensor(cp, device="cuda"))
+    ps = om.parameters()
+    for t in ps:
+        t.requires_grad_(True)
+    la, ph = log_psi(om, ip, st)
+    ref = _flat_grad(torch.autograd.grad((torch.tensor(ca) * la).sum() + (torch.tensor(cp) * ph).sum(), ps))
+    for t in ps:
+        t.requires_grad_(False)
+    got = g.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel < 1e-4, rel
+
+
+def test_tf_grad_n2_against_oracle(A):
+    """anqs_grad on sampled unique determinants with given local energies
+    (any values: the gradient is linear in the cotangents they define)."""
+    from oracle.vmc import gradient
+    w, ham, model, om, ip, oham = _n2(A)
+    x, c = A.sample(model, ham, 50_000, seed=12)
+    xs, cs = x.cpu().numpy().astype(np.uint64), c.cpu().numpy()
+    rng = np.random.default_rng(3)
+    e = rng.normal(-10, 1, len(xs)) + 1j * rng.normal(0, 0.1, len(xs))
+    st = energy_stats(e, cs)
+    g = A.grad(model, ham, x, c, torch.tensor(e.real, device="cuda"), torch.tensor(e.imag, device="cuda"),
+               torch.tensor(st, device="cuda")).cpu().numpy().astype(np.float64)
+    ref = _flat_grad(gradient(om, ip, xs, cs, e, st))
+    rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    assert rel < 1e-4, rel
+
+
+def test_tf_grad_large_central_differences(A):
+    """26 slots, d 128, 8 heads, 4 blocks: the library gradient of
+    L = sum_l [c_l log|psi(x_l)| + c'_l arg psi(x_l)] against FP64 central
+    differences of the oracle's L (step 1e-4) on 16 random parameters, and
+    against the oracle's FP64 gradient."""
+    w = workload("large", bias_std=0.2)
+    ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    params = torch.tensor(w["params"], device="cuda")
+    model = A.Model.transformer(w["n"], w["d_model"], w["n_heads"], w["n_layers"], params)
+    om = TFAnsatz(w["params_struct"], w["n"], w["n_heads"])
+    ip = molecular_isphys(w["n"], w["n_alpha"], w["n_beta"])
+    x, _ = A.sample(model, ham, 4000, seed=2)
+    xs = x.cpu().numpy().astype(np.uint64)[:64]
+    rng = np.random.default_rng(4)
+    ca, cp = rng.normal(size=len(xs)), rng.normal(size=len(xs))
+    g = A.logpsi_vjp(model, ham, _dev(xs), torch.tensor(ca, device="cuda"),
+                     torch.tensor(cp, device="cuda")).cpu().numpy().astype(np.float64)
+    ps = om.parameters()
+    for t in ps:
+        t.requires_grad_(True)
+    la, ph = log_psi(om, ip, xs)
+    ref = _flat_grad(torch.autograd.grad((torch.tensor(ca) * la).sum() + (torch.tensor(cp) * ph).sum(), ps))
+    for t in ps:
+        t.requires_grad_(False)
+    assert np.linalg.norm(g - ref) / np.linalg.norm(ref) < 1e-4
+    sizes = [t.numel() for t in ps]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    hstep = 1e-4
+
+    def loss():
+        a, b = log_psi(om, ip, xs)
+        return float((torch.tensor(ca) * a).sum() + (torch.tensor(cp) * b).sum())
+
+    # L is piecewise smooth (ReLU in the FFN): a parameter is used only if L
+    # is smooth over the stencil, i.e. the central differences with steps h
+    # and h/2 agree to their FP64 rounding (~1e-16 |L| / h); a ReLU kink
+    # within the stencil makes them differ by O(1e-4)
+    checked, tried = 0, 0
+    for i in rng.permutation(offs[-1]):
+        if checked == 16:
+            break
+        tried += 1
+        k = int(np.searchsorted(offs, i, side="right") - 1)
+        flat = ps[k].view(-1)
+        j = int(i - offs[k])
+        old = float(flat[j])
+        f = {}
+        for k2 in (-1.0, -0.5, 0.5, 1.0):
+            flat[j] = old + k2 * hstep
+            f[k2] = loss()
+        flat[j] = old
+        fd_h = (f[1.0] - f[-1.0]) / (2 * hstep)
+        fd_h2 = (f[0.5] - f[-0.5]) / hstep
+        if abs(fd_h - fd_h2) > 1e-7 * max(1.0, abs(fd_h2)):
+            continue
+        checked += 1
+        fd = (4 * fd_h2 - fd_h) / 3
+        assert abs(g[i] - fd) <= 1e-4 * max(1.0, abs(fd)) + 1e-4 * np.linalg.norm(ref) / np.sqrt(len(ref)), \
+            (i, g[i], fd, ref[i])
+    assert checked == 16 and tried < 64, (checked, tried)
