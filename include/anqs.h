@@ -245,6 +245,12 @@ ANQS_API int anqs_sample_shard(const anqs_model* model, const anqs_ham* ham, uin
  * pointers. */
 ANQS_API int anqs_stats_combine(const double* stats_in_dev, int world, double* stats_out_dev, void* stream);
 
+/* Device-side status of the model's BF16 tensor-core kernels (synchronous):
+ * 0, or 1 when a bounded wait inside a kernel (weight copy or MMA completion,
+ * 2 s each) gave up since the model was created; the kernel then stopped and
+ * the outputs of that call are invalid.  Always 0 for the FP32 forms. */
+ANQS_API int anqs_model_status(const anqs_model* model, int* status);
+
 /* ---------------------------------------------------------------------------
  * Local energy and energy statistics (Eq. local_energy_def, Eq. energy_est)
  *

@@ -115,6 +115,12 @@ class Model:
     def n_orb(self):
         return self.desc.n_orb
 
+    def status(self) -> int:
+        """0, or 1 if a bounded wait in a tensor-core kernel gave up (synchronous)."""
+        v = C.c_int()
+        check(_lib.load().anqs_model_status(self._m, C.byref(v)))
+        return v.value
+
     def sync(self, stream=None):
         """Refresh internal copies after params changed (BF16 packing)."""
         check(_lib.load().anqs_model_sync(self._m, _stream(stream)))

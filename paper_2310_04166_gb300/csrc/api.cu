@@ -96,6 +96,10 @@ int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, C
       }
       return launch_mlp_fp32_logpsi(M->mlp, H->v, x, n_x, la, ph, s);
     case ANQS_MODEL_TF:
+      if (M->d.form == ANQS_FORM_BF16) {
+        if (n_x.dev) return set_error(ANQS_ERR_UNSUPPORTED, "BF16 log psi takes host row counts");
+        return launch_tf_tc_logpsi(M, H->v, x, n_x.n, la, ph, s);
+      }
       return launch_tf_fp32_logpsi(M->tf, H->v, x, n_x, la, ph, s);
     case ANQS_MODEL_TABLE:
       return launch_table_logpsi(M, H->v, x, n_x, la, ph, s);
@@ -315,8 +319,6 @@ int anqs_model_create(anqs_model** out, const anqs_model_desc* d, const float* p
   *out = nullptr;
   ANQS_TRY(validate_desc(d));
   if (!params) return set_error(ANQS_ERR_ARG, "null parameters");
-  if (d->kind == ANQS_MODEL_TF && d->form == ANQS_FORM_BF16)
-    return set_error(ANQS_ERR_UNSUPPORTED, "transformer BF16 form not built");
   anqs_model* M = new anqs_model();
   M->d = *d;
   ANQS_CUDA(cudaGetDevice(&M->device));
@@ -360,6 +362,15 @@ int anqs_model_create(anqs_model** out, const anqs_model_desc* d, const float* p
     M->tf.H = d->n_heads;
     M->tf.L = d->n_layers;
     M->tf.params = params;
+    if (d->form == ANQS_FORM_BF16) {
+      int r = tf_tc_pack_alloc(M);
+      if (r == ANQS_OK) r = tf_tc_pack(M, 0);
+      if (r == ANQS_OK && cudaDeviceSynchronize() != cudaSuccess) r = set_error(ANQS_ERR_CUDA, "pack failed");
+      if (r != ANQS_OK) {
+        anqs_model_destroy(M);
+        return r;
+      }
+    }
   }
   *out = M;
   return ANQS_OK;
@@ -377,7 +388,16 @@ int anqs_model_sync(anqs_model* M, void* stream) {
   if (!M) return set_error(ANQS_ERR_ARG, "null model");
   ANQS_TRY(check_stream_device(M->device));
   if (M->d.kind == ANQS_MODEL_MLP && M->d.form == ANQS_FORM_BF16) return mlp_tc_pack(M, (cudaStream_t)stream);
+  if (M->d.kind == ANQS_MODEL_TF && M->d.form == ANQS_FORM_BF16) return tf_tc_pack(M, (cudaStream_t)stream);
   return ANQS_OK;
+}
+
+int anqs_model_status(const anqs_model* M, int* status) {
+  if (!M || !status) return set_error(ANQS_ERR_ARG, "null argument");
+  *status = 0;
+  if (M->d.form != ANQS_FORM_BF16) return ANQS_OK;
+  ANQS_TRY(check_stream_device(M->device));
+  return M->d.kind == ANQS_MODEL_TF ? tf_tc_status(M, status) : mlp_tc_status(M, status);
 }
 
 static int check_pair(const anqs_model* M, const anqs_ham* H) {
@@ -455,15 +475,17 @@ int anqs_stats_combine(const double* stats_in, int world, double* stats_out, voi
 // local energy
 // ---------------------------------------------------------------------------
 
-static bool uses_tc_eloc(const anqs_model* M) {
-  return M->d.kind == ANQS_MODEL_MLP && M->d.form == ANQS_FORM_BF16;
+static bool uses_tc_eloc(const anqs_model* M) { return M->d.form == ANQS_FORM_BF16; }
+
+static size_t tc_eloc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x) {
+  return M->d.kind == ANQS_MODEL_TF ? tf_tc_eloc_workspace(M, H, n_x) : eloc_tc_workspace(M, H, n_x);
 }
 
 int anqs_local_energy_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_x, size_t* bytes) {
   ANQS_TRY(check_pair(M, H));
   if (!bytes) return set_error(ANQS_ERR_ARG, "null output");
   if (uses_tc_eloc(M)) {
-    *bytes = eloc_tc_workspace(M, H, n_x);
+    *bytes = tc_eloc_workspace(M, H, n_x);
     return ANQS_OK;
   }
   Arena A(nullptr, 0);
@@ -484,9 +506,10 @@ int anqs_local_energy(const anqs_model* M, const anqs_ham* H, const uint64_t* x,
   cudaStream_t s = (cudaStream_t)stream;
   const Count nc{n_x, n_x_dev, 1};
   if (uses_tc_eloc(M)) {
-    size_t need = eloc_tc_workspace(M, H, n_x);
+    size_t need = tc_eloc_workspace(M, H, n_x);
     if (ws_bytes < need || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
-    ANQS_TRY(run_eloc_tc(M, H, x, nc, ere, eim, ws, ws_bytes, s));
+    if (M->d.kind == ANQS_MODEL_TF) ANQS_TRY(run_eloc_tf_tc(M, H, x, nc, ere, eim, ws, ws_bytes, s));
+    else ANQS_TRY(run_eloc_tc(M, H, x, nc, ere, eim, ws, ws_bytes, s));
   } else {
     Arena A(ws, ws_bytes);
     uint64_t* xp;

@@ -263,6 +263,26 @@ int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t*
 int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, const uint64_t* pre,
                               const uint64_t* n_dev, uint64_t max_rows, float* out8, cudaStream_t s);
 int mlp_tc_status(const anqs_model* M, int* status);
+// pieces of the tensor-core local-energy pipeline shared by the MLP and transformer forms
+constexpr int TC_CACHE_F = 10;  // floats per (parent, slot): prefix la, ph, 4 masked terms, 4 phases
+int launch_tc_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
+                       float* cache, cudaStream_t s);
+int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* hist, uint32_t* cursor, uint32_t* offsets,
+                   uint32_t* perm, cudaStream_t s);
+int launch_eloc_assemble(int n, uint32_t K, Count n_x, const uint64_t* xp, const uint8_t* js, const float* cache,
+                         const float2* T, const double* hval, const double* hdiag, const float* la_x,
+                         const float* ph_x, double* ere, double* eim, cudaStream_t s);
+// BF16 transformer form
+int tf_tc_pack_alloc(anqs_model* m);
+int tf_tc_pack(anqs_model* m, cudaStream_t s);
+int tf_tc_status(const anqs_model* M, int* status);
+size_t tf_tc_eloc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x);
+int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,
+                   void* ws, size_t ws_bytes, cudaStream_t s);
+int launch_tf_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la,
+                        float* ph, cudaStream_t s);
+int launch_tf_tc_slot_logits(const anqs_model* M, int p, const uint64_t* pre, const uint64_t* n_dev,
+                             uint64_t max_rows, float* out8, cudaStream_t s);
 
 // api.cu
 int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, float* la,

@@ -774,6 +774,30 @@ int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, con
   return launch_slots(M, ta, s, PROF_TC_SLOT);
 }
 
+int launch_tc_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
+                       float* cache, cudaStream_t s) {
+  return launch_finalize(hv, x, n_x, raw, la, ph, cache, s);
+}
+
+int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* hist, uint32_t* cursor, uint32_t* offsets,
+                   uint32_t* perm, cudaStream_t s) {
+  ANQS_CUDA(cudaMemsetAsync(hist, 0, ANQS_MAX_ORB * sizeof(uint32_t), s));
+  const unsigned g = unsigned(std::min<uint64_t>((mc.n + 255) / 256, 152 * 4));
+  ANQS_CUDA_LAUNCH("js_hist_kernel", launch_k(js_hist_kernel, dim3(g ? g : 1), dim3(256), 0, s, js, mc, n, hist));
+  ANQS_CUDA_LAUNCH("js_offsets_kernel", launch_k(js_offsets_kernel, dim3(1), dim3(32), 0, s, hist, n, cursor, offsets));
+  ANQS_CUDA_LAUNCH("js_scatter_kernel", launch_k(js_scatter_kernel, dim3(g ? g : 1), dim3(256), 0, s, js, mc, cursor, perm));
+  return ANQS_OK;
+}
+
+int launch_eloc_assemble(int n, uint32_t K, Count n_x, const uint64_t* xp, const uint8_t* js, const float* cache,
+                         const float2* T, const double* hval, const double* hdiag, const float* la_x,
+                         const float* ph_x, double* ere, double* eim, cudaStream_t s) {
+  uint64_t blocks = (n_x.n + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  ANQS_CUDA_LAUNCH("eloc_assemble_kernel", launch_k(eloc_assemble_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(256), 0, s, n, K, n_x, xp, js, cache, T, hval, hdiag, la_x, ph_x, ere, eim));
+  return ANQS_OK;
+}
+
 size_t eloc_tc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x) {
   (void)M;
   Arena A(nullptr, 0);

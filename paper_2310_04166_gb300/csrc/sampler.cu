@@ -650,6 +650,7 @@ int logits_dispatch(const anqs_model* M, const anqs_ham* H, int p, const uint64_
         return launch_mlp_tc_slot_logits(M, H->v, p, pre, n_dev, max_rows, out8, s);
       return launch_mlp_fp32_slot_logits(M->mlp, p, pre, n_dev, max_rows, out8, s);
     case ANQS_MODEL_TF:
+      if (M->d.form == ANQS_FORM_BF16) return launch_tf_tc_slot_logits(M, p, pre, n_dev, max_rows, out8, s);
       return launch_tf_fp32_slot_logits(M->tf, p, pre, n_dev, max_rows, out8, s);
     case ANQS_MODEL_TABLE:
       return launch_table_slot_logits(M, p, pre, n_dev, max_rows, out8, s);
