@@ -222,12 +222,18 @@ TRAFFIC = {("h2o", "bf16"): {"mlp_fp32_grad_kernel": 1163776 + 135680, "mlp_tc_s
                              "eloc_assemble_kernel": 4650240, "connected_kernel": 49920}}
 
 
+def _make_model(A, w, params, form):
+    if w["kind"] == "mlp":
+        return A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form=form)
+    return A.Model.transformer(w["n"], w["d_model"], w["n_heads"], w["n_layers"], params, form=form)
+
+
 def _run_form(A, lib, args, w, form, ham, params, dev, rank, dist, stream_clocks):
     """Graph-captured timing of one form: returns throughput, end-to-end
     throughput, the eager per-kernel profile and the last step's sample set
     with its statistics."""
     import ctypes as C
-    model = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form=form)
+    model = _make_model(A, w, params, form)
     Ns = w["n_samples"]
     cap = min(Ns, ham.sector_dim)
     i64, f64 = dict(dtype=torch.int64, device=dev), dict(dtype=torch.float64, device=dev)
@@ -407,8 +413,8 @@ def main():
     params = torch.tensor(w["params"], device=dev)
     form = args.form
     if args.kernel_case:
-        model = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form=form)
-        m32 = A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form="fp32")
+        model = _make_model(A, w, params, form)
+        m32 = _make_model(A, w, params, "fp32")
         xk, nk = A.sample(m32, ham, w["n_samples"], seed=99)
         ek = A.local_energy(model, ham, xk, nk)
         A.grad(model, ham, xk, nk, ek[0], ek[1], ek[2])
@@ -461,6 +467,32 @@ def main():
         dist.destroy_process_group()
 
 
+def _tf_work(A, ham, w, x):
+    """Algorithmic FLOP per step of the transformer families for the sample
+    set x.  One (sequence, position t) row costs f(t) = L (24 d^2 + 4 (t+1) d)
+    + 16 d: the q|k|v, output and FFN projections, the attention scores and
+    weighted sum over the t+1 keys, and the head.  suffix = positions > j(x')
+    of every connected x'; parent = every position of every sample; slot
+    (sampler) = positions 0..p of every distinct prefix at level p; grad =
+    3 x parent (forward plus the two products of the adjoint)."""
+    n, d, L = w["n"], w["d_model"], w["n_layers"]
+    f = np.array([L * (24 * d * d + 4 * (t + 1) * d) + 16 * d for t in range(n)], dtype=np.float64)
+    cf = np.concatenate([[0.0], np.cumsum(f)])
+    xp, hv, js, hd = A.connected(ham, x)
+    j = js.reshape(-1).cpu().numpy().astype(np.int64)
+    suffix = float((cf[n] - cf[j + 1]).sum())
+    parent = float(len(x) * cf[n])
+    xs = x.cpu().numpy().astype(np.uint64)
+    slot = 0.0
+    for p in range(n):
+        pre = np.unique(xs & np.uint64((1 << (2 * p)) - 1)) if p else np.zeros(1, np.uint64)
+        slot += len(pre) * cf[p + 1]
+    eloc_bytes = float((8 + 1 + 8 + 8 + 8 * (n - 1 - j)).sum())
+    return {"tf_tc_suffix_kernel": suffix, "tf_tc_parent_kernel": parent, "tf_tc_slot_kernel": slot,
+            "tf_fp32_kernel": len(j) * cf[n] + parent + slot, "tf_fp32_grad_kernels": 3.0 * parent,
+            "eloc_assemble_kernel": eloc_bytes, "connected_kernel": float(len(j) * (8 + 8 + 1) + len(x) * 8)}
+
+
 def _tc_work(A, ham, model, w, x):
     """Algorithmic work per step for the sample set x.
 
@@ -471,6 +503,8 @@ def _tc_work(A, ham, model, w, x):
     forward recomputed plus the two adjoint products); eloc bytes = per
     connected x': x' 8 + j 1 + H 8 + parent cache 8 + one 8-byte term per
     slot p > j."""
+    if w["kind"] != "mlp":
+        return _tf_work(A, ham, w, x)
     n, W, L = w["n"], w["width"], w["n_hidden"]
     f = np.array([2 * (4 * p * W + (L - 1) * W * W + 8 * W) for p in range(n)], dtype=np.float64)
     cf = np.concatenate([[0.0], np.cumsum(f)])  # cf[p] = sum_{q<p} f[q]
@@ -500,11 +534,11 @@ def _rooflines(prof, work, steps, peaks, src, traffic):
             continue
         per_launch = work[name] * steps / launches
         avg_s = ms / launches * 1e-3
-        if name.startswith("mlp_tc_"):
+        if name.startswith(("mlp_tc_", "tf_tc_")):
             bound, unit, peak = "tensor", "TFLOP/s", peaks["bf16_tflops"]
             ach = per_launch / avg_s / 1e12
             note = f"dense bf16 {src} burst peak; FLOP with prefix reuse"
-        elif name == "mlp_fp32_grad_kernel":
+        elif name in ("mlp_fp32_grad_kernel", "tf_fp32_grad_kernels", "tf_fp32_kernel"):
             bound, unit, peak = "alu", "TFLOP/s", fp32_peak
             ach = per_launch / avg_s / 1e12
             note = f"FP32 SIMT peak derived: 152 SMs x 128 FMA lanes x 2 x {sm_mhz:.0f} MHz"

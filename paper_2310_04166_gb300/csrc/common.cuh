@@ -39,6 +39,10 @@ enum ProfId {
   PROF_TC_FINALIZE,
   PROF_GRAD_REDUCE,
   PROF_SAMPLER_NET_FP32,
+  PROF_TF_GRAD,
+  PROF_TF_TC_PARENT,
+  PROF_TF_TC_SUFFIX,
+  PROF_TF_TC_SLOT,
   PROF_COUNT
 };
 

@@ -525,7 +525,7 @@ int run(const TfView& m, const HamView& hv, const uint64_t* x, Count nx, const f
   const uint64_t R = rows.n;
   const Count kD = host_count(D), k4D = host_count(4 * D), k8 = host_count(8);
   const float* P = m.params;
-  ProfScope ps(PROF_TF, s);
+  ProfScope ps(PROF_TF_GRAD, s);
   const unsigned eg = grid_for(R * D, 256, 152 * 16), lg = grid_for(R * 32, 256, 152 * 16);
   ANQS_CUDA_LAUNCH("tf embed_kernel", launch_k(embed_kernel, dim3(eg), dim3(256), 0, s, m, x, rows, a.H[0]));
   for (int l = 0; l < L; ++l) {

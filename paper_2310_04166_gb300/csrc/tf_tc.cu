@@ -594,7 +594,7 @@ int sms() {
   return g_sms;
 }
 
-int launch(const anqs_model* M, Args a, uint64_t max_tiles, cudaStream_t s) {
+int launch(const anqs_model* M, Args a, uint64_t max_tiles, int prof, cudaStream_t s) {
   a.img = static_cast<const unsigned char*>(M->packed);
   a.params = M->params;
   a.n = M->d.n_orb;
@@ -603,7 +603,7 @@ int launch(const anqs_model* M, Args a, uint64_t max_tiles, cudaStream_t s) {
   const uint64_t pairs = (max_tiles + 1) / 2;
   const unsigned grid = unsigned(std::max<uint64_t>(1, std::min<uint64_t>(pairs, uint64_t(sms()))));
   const int dh = D / M->d.n_heads;
-  ProfScope ps(PROF_TF, s);
+  ProfScope ps(prof, s);
   if (dh == 16) {
     ANQS_CUDA(cudaFuncSetAttribute(tf_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMEM_BYTES)));
     ANQS_CUDA_LAUNCH("tf_tc_kernel", launch_k(tf_tc_kernel<16>, dim3(grid), dim3(NT), SMEM_BYTES, s, a));
@@ -692,7 +692,7 @@ int launch_tf_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t* 
   for (uint64_t off = 0; off < n_x; off += M->tc_raw_rows) {
     const uint64_t k = std::min<uint64_t>(M->tc_raw_rows, n_x - off);
     Args a = full_args(x + off, host_count(k), n, 0, M->tc_raw, nullptr, hv);
-    ANQS_TRY(launch(M, a, (k + MT / n - 1) / (MT / n), s));
+    ANQS_TRY(launch(M, a, (k + MT / n - 1) / (MT / n), PROF_TF_TC_PARENT, s));
     ProfScope ps(PROF_TC_FINALIZE, s);
     ANQS_TRY(launch_tc_finalize(hv, x + off, host_count(k), M->tc_raw, la + off, ph + off, nullptr, s));
   }
@@ -704,7 +704,7 @@ int launch_tf_tc_slot_logits(const anqs_model* M, int p, const uint64_t* pre, co
   HamView hv{};
   Args a = full_args(pre, Count{max_rows, n_dev, 1}, p + 1, 1, out8, nullptr, hv);
   const uint64_t S = MT / (p + 1);
-  return launch(M, a, (max_rows + S - 1) / S, s);
+  return launch(M, a, (max_rows + S - 1) / S, PROF_TF_TC_SLOT, s);
 }
 
 size_t tf_tc_eloc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x) {
@@ -726,7 +726,7 @@ int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Co
   ANQS_TRY(launch_connected(H->v, x, n_x, w.xp, w.hv, w.js, w.hd, s));
   {
     Args a = full_args(x, n_x, n, 0, w.raw, w.kv, H->v);
-    ANQS_TRY(launch(M, a, (n_x.n + MT / n - 1) / (MT / n), s));
+    ANQS_TRY(launch(M, a, (n_x.n + MT / n - 1) / (MT / n), PROF_TF_TC_PARENT, s));
     ProfScope ps(PROF_TC_FINALIZE, s);
     ANQS_TRY(launch_tc_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
   }
@@ -746,7 +746,7 @@ int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Co
     a.T = w.T;
     uint64_t tiles = 0;  // upper bound over the groups
     for (int j = 0; j + 1 < n; ++j) tiles += mc.n / uint64_t(MT / (n - 1 - j)) + 1;
-    ANQS_TRY(launch(M, a, tiles, s));
+    ANQS_TRY(launch(M, a, tiles, PROF_TF_TC_SUFFIX, s));
   }
   {
     ProfScope ps(PROF_TC_ELOC, s);
