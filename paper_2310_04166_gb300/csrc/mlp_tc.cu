@@ -48,6 +48,8 @@ enum { ST_TIMEOUT = 1 };
 struct SlotLayout {
   uint32_t k1;      // padded input width of layer 1 (multiple of 16, 0 for slot 0)
   uint32_t w1;      // layer-1 matrix [W][k1] bf16, canonical K-major
+  uint32_t w1lo;    // its rounding residual W1 - bf16(W1), same layout, or 0 bytes when the split is
+                    // off (the one-hot input is exact, so hi + lo makes layer 1 exact to 2^-16 relative)
   uint32_t wk;      // hidden matrices [L-1][W][W] bf16, canonical, each W*W*2 bytes
   uint32_t bias;    // [L][W] f32
   uint32_t head;    // head [W][8] f32 (transposed: the 8 outputs of input k are adjacent)
@@ -57,11 +59,12 @@ struct SlotLayout {
 
 __host__ __device__ inline uint32_t round_up(uint32_t a, uint32_t b) { return (a + b - 1) / b * b; }
 
-__host__ __device__ inline SlotLayout slot_layout(int p, int W, int L) {
+__host__ __device__ inline SlotLayout slot_layout(int p, int W, int L, int lo) {
   SlotLayout s;
   s.k1 = round_up(4u * p, 16u);
   s.w1 = 0;
-  s.wk = round_up(s.w1 + uint32_t(W) * s.k1 * 2u, 128u);
+  s.w1lo = round_up(s.w1 + uint32_t(W) * s.k1 * 2u, 128u);
+  s.wk = round_up(s.w1lo + (lo ? uint32_t(W) * s.k1 * 2u : 0u), 128u);
   s.bias = round_up(s.wk + uint32_t(L - 1) * W * W * 2u, 128u);
   s.head = round_up(s.bias + uint32_t(L) * W * 4u, 128u);
   s.hbias = round_up(s.head + 8u * W * 4u, 128u);
@@ -69,8 +72,18 @@ __host__ __device__ inline SlotLayout slot_layout(int p, int W, int L) {
   return s;
 }
 
+// The layer-1 split is on when the largest slot image with it still fits in
+// shared memory next to the warpgroups' A tiles (n <= 11 at width 128).
+constexpr int kNwg = 4;
+__host__ __device__ inline int use_w1_split(int n, int W, int L) {
+  const uint32_t kmax = uint32_t(W) > round_up(4u * (n - 1), 16u) ? uint32_t(W) : round_up(4u * (n - 1), 16u);
+  const uint32_t img = round_up(slot_layout(n - 1, W, L, 1).bytes, 1024u);
+  return img + uint32_t(kNwg) * 128u * kmax * 2u <= 227u * 1024u ? 1 : 0;
+}
+
 struct TcView {
   int n, W, L;
+  int lo;                     // layer-1 hi/lo split on (use_w1_split)
   const unsigned char* img;   // packed images
   uint32_t img_off[ANQS_MAX_ORB + 1];
   uint32_t max_img;           // largest image (bytes)
@@ -84,7 +97,7 @@ __global__ void pack_kernel(MlpView m, TcView tv, unsigned char* img) {
   ANQS_PDL_ENTRY();
   const int p = blockIdx.y;
   const int W = m.width, L = m.n_hidden;
-  const SlotLayout S = slot_layout(p, W, L);
+  const SlotLayout S = slot_layout(p, W, L, tv.lo);
   unsigned char* base = img + tv.img_off[p];
   const float* W1 = m.params + m.slot_off[p];
   const float* b1 = W1 + size_t(W) * 4 * p;
@@ -98,8 +111,11 @@ __global__ void pack_kernel(MlpView m, TcView tv, unsigned char* img) {
     if (t < n1) {
       uint32_t r = t / S.k1, k = t % S.k1;
       float v = (k < 4u * p) ? W1[size_t(r) * 4 * p + k] : 0.f;
-      *reinterpret_cast<uint16_t*>(base + S.w1 + tc::canon_off(r, k, S.k1)) =
-          __bfloat16_as_ushort(__float2bfloat16_rn(v));
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      *reinterpret_cast<uint16_t*>(base + S.w1 + tc::canon_off(r, k, S.k1)) = __bfloat16_as_ushort(hi);
+      if (tv.lo)
+        *reinterpret_cast<uint16_t*>(base + S.w1lo + tc::canon_off(r, k, S.k1)) =
+            __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(hi)));
     } else if (t < n1 + nk) {
       uint32_t u = t - n1, l = u / (W * W), e = u % (W * W), r = e / W, k = e % W;
       float v = Wk[size_t(l) * (size_t(W) * W + W) + size_t(r) * W + k];
@@ -134,7 +150,7 @@ struct TileArgs {
   float* raw;                  // SLOTS output [row][p_hi - p_lo][8]
 };
 
-constexpr int NWG = 4;        // warpgroups per CTA, one 128-row tile each in flight
+constexpr int NWG = kNwg;     // warpgroups per CTA, one 128-row tile each in flight
 constexpr int NT = NWG * MT;
 
 struct Ctx {
@@ -205,6 +221,12 @@ __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const
         for (uint32_t ks = 0; ks < K / 16; ++ks)
           tc::mma_bf16(c.tmem, tc::sdesc(c.a_addr + ks * 256u, 128u, K * 16u),
                        tc::sdesc(b_addr + ks * 256u, 128u, K * 16u), IDESC, ks > 0 ? 1u : 0u);
+        if (layer == 0 && c.tv->lo) {  // + one-hot x (W1 - bf16(W1))
+#pragma unroll 1
+          for (uint32_t ks = 0; ks < K / 16; ++ks)
+            tc::mma_bf16(c.tmem, tc::sdesc(c.a_addr + ks * 256u, 128u, K * 16u),
+                         tc::sdesc(img_addr + S.w1lo + ks * 256u, 128u, K * 16u), IDESC, 1u);
+        }
         tc::mma_commit(c.bar_m);
       }
       ok = wg_all(c.wg, wait_bar(c.bar_m, ph_m));
@@ -229,12 +251,14 @@ __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const
         tc::add_f32x2(v[i], v[i + 1], bb.x, bb.y, v[i], v[i + 1]);
       }
       if (!last) {
-        // next GEMM operand: tanh on packed bf16 pairs
+        // next GEMM operand: f32 tanh, rounded to bf16 (a bf16x2 tanh would add
+        // its own approximation error to the bf16 rounding)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           uint32_t u[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) u[e] = tc::tanh_bf16x2(tc::pack_bf16x2(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]));
+          for (int e = 0; e < 4; ++e)
+            u[e] = tc::pack_bf16x2(tc::tanh_fast(v[8 * q + 2 * e]), tc::tanh_fast(v[8 * q + 2 * e + 1]));
           *reinterpret_cast<uint4*>(c.s_a + tc::canon_off(c.t, c0 + 8 * q, W)) = make_uint4(u[0], u[1], u[2], u[3]);
         }
       } else {
@@ -287,7 +311,7 @@ __device__ __forceinline__ void teardown(const TcView& tv, uint32_t tmem, int ab
 }
 
 __device__ __forceinline__ void load_slot(const TcView& tv, int p, uint32_t dst, uint32_t bar, int W, int L) {
-  const SlotLayout S = slot_layout(p, W, L);
+  const SlotLayout S = slot_layout(p, W, L, tv.lo);
   tc::mbar_arrive_expect_tx(bar, S.bytes);
   tc::bulk_g2s(dst, tv.img + tv.img_off[p], S.bytes, bar);
 }
@@ -333,7 +357,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
   for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int p = ta.p_lo + int(it / n_groups);
     const uint64_t grp = it % n_groups;
-    const SlotLayout S = slot_layout(p, W, tv.L);
+    const SlotLayout S = slot_layout(p, W, tv.L, tv.lo);
     if (p != loaded) {
       if (threadIdx.x == 0) load_slot(tv, p, tc::smem_u32(s_img), bar_w, W, tv.L);
       loaded = p;
@@ -423,7 +447,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_ws_kernel(TcView tv, HamView hv,
   }
   if (my_p >= 0) {
     const int p = my_p;
-    const SlotLayout Sl = slot_layout(p, W, tv.L);
+    const SlotLayout Sl = slot_layout(p, W, tv.L, tv.lo);
     const uint32_t img_addr = tc::smem_u32(smem);
     if (threadIdx.x == 0) load_slot(tv, p, img_addr, tc::smem_u32(&bars[0]), W, tv.L);
     bool ok = __syncthreads_and(wait_bar(tc::smem_u32(&bars[0]), 0));
@@ -624,10 +648,11 @@ TcView make_view(const anqs_model* M) {
   tv.n = M->d.n_orb;
   tv.W = M->d.width;
   tv.L = M->d.n_hidden;
+  tv.lo = use_w1_split(tv.n, tv.W, tv.L);
   tv.img = static_cast<const unsigned char*>(M->packed);
   tv.max_img = 0;
   for (int p = 0; p <= tv.n; ++p) tv.img_off[p] = uint32_t(M->pack_off[p]);
-  for (int p = 0; p < tv.n; ++p) tv.max_img = std::max(tv.max_img, slot_layout(p, tv.W, tv.L).bytes);
+  for (int p = 0; p < tv.n; ++p) tv.max_img = std::max(tv.max_img, slot_layout(p, tv.W, tv.L, tv.lo).bytes);
   tv.kmax = std::max<uint32_t>(tv.W, round_up(4u * (tv.n - 1), 16u));
   tv.nbuf = smem_bytes(tv, 2) <= kSmemLimit ? 2 : 1;
   tv.status = reinterpret_cast<int*>(static_cast<unsigned char*>(M->packed) + M->pack_off[tv.n]);
@@ -704,11 +729,12 @@ int launch_ws_w(const TcView& tv, const HamView& hv, const ElocWs& w, cudaStream
 int mlp_tc_pack_alloc(anqs_model* M) {
   const int n = M->d.n_orb, W = M->d.width, L = M->d.n_hidden;
   if (W != 64 && W != 128) return set_error(ANQS_ERR_UNSUPPORTED, "BF16 MLP form supports width 64 or 128");
+  const int lo = use_w1_split(n, W, L);
   M->pack_off.assign(n + 1, 0);
   uint64_t off = 0;
   for (int p = 0; p < n; ++p) {
     M->pack_off[p] = off;
-    off += slot_layout(p, W, L).bytes;
+    off += slot_layout(p, W, L, lo).bytes;
   }
   M->pack_off[n] = off;  // status word after the images
   M->packed_bytes = off + 256;
@@ -716,8 +742,9 @@ int mlp_tc_pack_alloc(anqs_model* M) {
   tv.n = n;
   tv.W = W;
   tv.L = L;
+  tv.lo = lo;
   tv.max_img = 0;
-  for (int p = 0; p < n; ++p) tv.max_img = std::max(tv.max_img, slot_layout(p, W, L).bytes);
+  for (int p = 0; p < n; ++p) tv.max_img = std::max(tv.max_img, slot_layout(p, W, L, lo).bytes);
   tv.kmax = std::max<uint32_t>(W, round_up(4u * (n - 1), 16u));
   if (smem_bytes(tv, 1) > kSmemLimit)
     return set_error(ANQS_ERR_UNSUPPORTED, "BF16 MLP slot image too large for shared memory (%zu bytes)",

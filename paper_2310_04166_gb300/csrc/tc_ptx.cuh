@@ -181,13 +181,6 @@ __device__ __forceinline__ void fma_f32x2(float a0, float a1, float b0, float b1
       : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
 }
 
-// tanh on two packed bf16 values (one MUFU operation for both)
-__device__ __forceinline__ uint32_t tanh_bf16x2(uint32_t x) {
-  uint32_t y;
-  asm("tanh.approx.bf16x2 %0, %1;" : "=r"(y) : "r"(x));
-  return y;
-}
-
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   uint32_t r;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
