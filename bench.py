@@ -379,6 +379,77 @@ def _run_form(A, lib, args, w, form, ham, params, dev, rank, dist, stream_clocks
             "clocks": clk.summary()}
 
 
+def _batch32(args, dev):
+    """32 independent problems (seeds 100..131, n in [6, 14], MLP 3x128 each,
+    N_s = 1e5 each): the BF16 form with all passes in one CUDA graph (one
+    stream per problem) against the plain FP32 form run as 32 separate
+    eager passes one after the other.  Prints one JSON line."""
+    import paper_2310_04166_gb300 as A
+    from paper_2310_04166_gb300.batch import BatchedStep, Problem
+    from synthetic import batch32_problem, flatten_mlp, mlp_params
+    specs = [batch32_problem(k) for k in range(32)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def build(form):
+        out = []
+        for k, p in enumerate(specs):
+            ham = A.Hamiltonian(p["h"], p["g"], p["e_nuc"], p["n_alpha"], p["n_beta"])
+            params = torch.tensor(flatten_mlp(mlp_params(p["seed"], p["n"], p["width"], p["n_hidden"])), device=dev)
+            model = A.Model.mlp(p["n"], p["width"], p["n_hidden"], params, form=form)
+            out.append(Problem(ham, model, p["n_samples"], 1234 + k))
+        return out
+
+    def timed(run, problems, steps):
+        times, uniq = [], 0
+        stream = torch.cuda.current_stream()
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            uniq += int(torch.stack([p.nu for p in problems]).sum().item())
+        return uniq / (sum(times) / 1e3), sum(times) / steps, uniq / steps
+
+    res = {}
+    probs = build("bf16")
+    bs = BatchedStep(probs)
+    for _ in range(args.warmup):
+        bs.eager()
+    bs.capture()
+    for _ in range(args.warmup):
+        bs.replay()
+    with Clocks(torch.cuda.current_device()) as clk:
+        res["bf16"] = timed(bs.replay, probs, args.steps)
+    del bs, probs
+    torch.cuda.empty_cache()
+    probs = build("fp32")
+
+    def plain():
+        for p in probs:
+            p.step()
+    for _ in range(args.warmup):
+        plain()
+    res["fp32"] = timed(plain, probs, args.steps)
+    line = {"metric": METRIC, "value": res["bf16"][0], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["bf16"][1], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16 GEMM / f32 heads / f64 E_loc", "data": "synthetic",
+            "config": {"workload": "batch32: 32 problems, seeds 100..131, n in [6, 14], N_a = N_b in [1, n-1], "
+                                   "2n Cholesky vectors, per-slot MLP 3x128 each, N_s = 1e5 each",
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "timing": "bf16: one CUDA-graph replay of all 32 passes (one stream per problem); "
+                                 "fp32: 32 eager passes one after the other"},
+            "n_unique_per_step": res["bf16"][2],
+            "forms": {"bf16_batched_graph": {"value": res["bf16"][0], "ms_per_step": res["bf16"][1]},
+                      "fp32_separate": {"value": res["fp32"][0], "ms_per_step": res["fp32"][1]},
+                      "bf16_over_fp32": res["bf16"][0] / res["fp32"][0]},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -396,7 +467,7 @@ def main():
     args.warmup = max(args.warmup, 3)
 
     from synthetic import workload
-    w = workload(args.workload)
+    w = workload("h2o" if args.workload == "batch32" else args.workload)
     ws, rank, local, dist = _dist()
     if args.impl == "reference":
         _reference_arm(args, w, ws, rank)
@@ -409,6 +480,9 @@ def main():
     lib = _lib.load()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload == "batch32":
+        _batch32(args, dev)
+        return
     ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
     params = torch.tensor(w["params"], device=dev)
     form = args.form
