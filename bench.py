@@ -207,8 +207,10 @@ def _config(w, args):
            else f"transformer d{w['d_model']} h{w['n_heads']} L{w['n_layers']}")
     return {"workload": f"{args.workload}: n_orb={w['n']} N_a={w['n_alpha']} N_b={w['n_beta']} "
                         f"({2 * w['n']} qubits), {w['n_chol']} Cholesky vectors seed {w['seed']}, {net}, "
-                        f"N_s={w['n_samples']}",
-            "form": args.form, "n_samples": w["n_samples"], "l2": "flushed between timed steps (256 MiB write)",
+                        f"N_s={args.n_samples or w['n_samples']}",
+            "form": args.form, "n_samples": args.n_samples or w["n_samples"],
+            "sampler": "binomial (chained binomials per node)" if args.binomial else "multinomial (one draw per sample)",
+            "l2": "flushed between timed steps (256 MiB write)",
             "timing": "one CUDA-graph replay of the whole step per timed iteration (weight packing, sampling, "
                       "connected set, amplitudes, E_loc and statistics, gradient), CUDA events on the replay stream",
             "parallelism": (f"dp{args.gpus}: per-rank sample sets (seed per rank), statistics all-gather + "
@@ -234,7 +236,7 @@ def _run_form(A, lib, args, w, form, ham, params, dev, rank, dist, stream_clocks
     with its statistics."""
     import ctypes as C
     model = _make_model(A, w, params, form)
-    Ns = w["n_samples"]
+    Ns = args.n_samples or w["n_samples"]
     cap = min(Ns, ham.sector_dim)
     i64, f64 = dict(dtype=torch.int64, device=dev), dict(dtype=torch.float64, device=dev)
     x, cnt, nu, ctr = torch.empty(cap, **i64), torch.empty(cap, **i64), torch.zeros(1, **i64), torch.zeros(1, **i64)
@@ -250,7 +252,7 @@ def _run_form(A, lib, args, w, form, ham, params, dev, rank, dist, stream_clocks
     def step_a():
         if form == "bf16":
             model.sync()  # re-pack the bf16 weight images (the optimiser changes params every step)
-        A.sample_into(model, ham, Ns, seed, 0, x, cnt, nu, ws_s, counter_dev=ctr)
+        A.sample_into(model, ham, Ns, seed, 0, x, cnt, nu, ws_s, counter_dev=ctr, binomial=args.binomial)
         A.local_energy(model, ham, x, cnt, workspace=ws_e, n_dev=nu, out=(ere, eim, stats))
 
     def step_b(st):
@@ -460,11 +462,14 @@ def main():
     ap.add_argument("--workload", default="h2o")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--one-form", action="store_true", help="time only --form (default: both forms)")
+    ap.add_argument("--binomial", action="store_true", help="binomial statistics sampling (chained binomials per node)")
+    ap.add_argument("--n-samples", type=float, default=0, help="N_s of the sampling pass (default: the workload's)")
     ap.add_argument("--kernel-case", action="store_true",
                     help="one FP32-form sampling pass, then one local-energy and one gradient call in the "
                          "chosen form (the launch sequence to capture with ncu), then exit")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    args.n_samples = int(args.n_samples)
 
     from synthetic import workload
     w = workload("h2o" if args.workload == "batch32" else args.workload)

@@ -219,6 +219,24 @@ ANQS_API int anqs_sample(const anqs_model* model, const anqs_ham* ham, uint64_t 
                 uint64_t* n_out_dev, uint64_t cap, uint64_t* n_unique_dev, void* workspace_dev,
                 size_t workspace_bytes, void* stream);
 
+/* Binomial statistics sampling (Sec. II.C, the trick of Barrett et al.):
+ * the same tree walk, but a node splits its n_in samples by chained
+ * binomials instead of n_in draws, so the cost per node does not depend on
+ * n_in and n_samples can reach 1e8 and beyond.  For the allowed outcomes in
+ * ascending v: k_v ~ B(rest, p_v / (p_v + ... + p_last)), rest -= k_v; the
+ * last allowed outcome takes the rest (MU: nothing is lost).  p is the same
+ * float32 masked conditional as above.  B(n, q) is drawn with q' = min(q,
+ * 1 - q) by inversion of the pmf when n q' < 10, else by BTRS (Hormann 1993,
+ * transformed rejection with squeeze; log Gamma by the Stirling series), in
+ * FP64.  Uniforms: Philox4x64-10 with counter (prefix, (v << 32) | block,
+ * slot, counter) and key (seed, 1), four per block.  The counts are an exact
+ * multinomial split in distribution; they are not the counts of
+ * anqs_sample.  Arguments and outputs as anqs_sample (same workspace). */
+ANQS_API int anqs_sample_binomial(const anqs_model* model, const anqs_ham* ham, uint64_t n_samples, uint64_t seed,
+                                  uint64_t counter, const uint64_t* counter_dev, uint64_t* x_out_dev,
+                                  uint64_t* n_out_dev, uint64_t cap, uint64_t* n_unique_dev, void* workspace_dev,
+                                  size_t workspace_bytes, void* stream);
+
 /* One rank's share of the same sampling pass on `world` GPUs (the data-
  * parallel split of the tree: subtrees are independent).  Every rank walks
  * levels 0..split_level-1 exactly as anqs_sample does; the level-split_level

@@ -171,3 +171,43 @@ def lexicographic_key(xs, n: int) -> np.ndarray:
     for p in range(n):
         key = key * np.uint64(4) + ((xs >> np.uint64(2 * p)) & np.uint64(3))
     return key
+
+
+def sample_binomial(model, isphys, n: int, n_samples: int, rng, logits_fn=None):
+    """Binomial statistics sampling (Sec. II.C): at every node the n_in
+    samples are split among the allowed outcomes by chained binomials,
+    k_v ~ B(rest, p_v / (p_v + ... + p_last)) in ascending v, the last
+    allowed outcome taking the rest (MU: nothing is lost).  p is the masked
+    conditional in FP64; the binomial draws come from ``rng`` (a numpy
+    Generator: a library primitive, so parity with the device sampler is in
+    distribution only).  Returns (x uint64[N_unq], counts int64[N_unq]) in
+    the tree's lexicographic order."""
+    from .anqs import masked_log_prob
+    import torch
+    pre = np.zeros(1, dtype=np.uint64)
+    cnt = np.array([n_samples], dtype=np.int64)
+    for p in range(n):
+        if logits_fn is None:
+            L = model.slot_out(pre, p)[:, :4].detach()
+        else:
+            L = torch.as_tensor(np.asarray(logits_fn(pre, p), dtype=np.float64))
+        M = allowed_masks(isphys, pre, n)[:, p]
+        P = torch.exp(masked_log_prob(L, torch.as_tensor(M))).numpy()
+        new_pre, new_cnt = [], []
+        for k in range(len(pre)):
+            allowed = [v for v in range(4) if M[k][v]]
+            rest, tail = int(cnt[k]), 1.0
+            for v in allowed:
+                if v == allowed[-1]:
+                    c = rest
+                else:
+                    q = min(P[k][v] / tail, 1.0) if tail > 0 else 1.0
+                    c = int(rng.binomial(rest, q))
+                    tail -= P[k][v]
+                rest -= c
+                if c > 0:
+                    new_pre.append(int(pre[k]) | (v << (2 * p)))
+                    new_cnt.append(c)
+        pre = np.array(new_pre, dtype=np.uint64)
+        cnt = np.array(new_cnt, dtype=np.int64)
+    return pre, cnt

@@ -203,17 +203,20 @@ def sample_workspace_bytes(model: Model, ham: Hamiltonian, n_samples: int) -> in
 
 
 def sample_into(model, ham, n_samples, seed, counter, x_out, n_out, n_unique, workspace, stream=None,
-                counter_dev=None):
+                counter_dev=None, binomial=False):
     """Asynchronous sampling into preallocated device buffers (no host sync).
     With counter_dev (a 1-element int64 CUDA tensor) the Philox counter is
-    counter + counter_dev[0], read on the device."""
-    check(_lib.load().anqs_sample(model._m, ham.handle, int(n_samples), int(seed) & (2**64 - 1),
+    counter + counter_dev[0], read on the device.  binomial=True splits each
+    node's samples by chained binomials (cost independent of n_samples)."""
+    fn = _lib.load().anqs_sample_binomial if binomial else _lib.load().anqs_sample
+    check(fn(model._m, ham.handle, int(n_samples), int(seed) & (2**64 - 1),
                                   int(counter) & (2**64 - 1), _ptr(counter_dev), x_out.data_ptr(), n_out.data_ptr(),
                                   x_out.numel(), n_unique.data_ptr(), workspace.data_ptr(), workspace.numel(),
                                   _stream(stream)))
 
 
-def sample(model: Model, ham: Hamiltonian, n_samples: int, seed: int, counter: int = 0, stream=None):
+def sample(model: Model, ham: Hamiltonian, n_samples: int, seed: int, counter: int = 0, stream=None,
+           binomial: bool = False):
     """Unique determinants and their counts (trimmed; synchronises once)."""
     dev = model.params.device
     cap = min(int(n_samples), ham.sector_dim)
@@ -221,7 +224,7 @@ def sample(model: Model, ham: Hamiltonian, n_samples: int, seed: int, counter: i
     n = torch.empty(cap, dtype=torch.int64, device=dev)
     nu = torch.zeros(1, dtype=torch.int64, device=dev)
     ws = _ws(sample_workspace_bytes(model, ham, n_samples), dev)
-    sample_into(model, ham, n_samples, seed, counter, x, n, nu, ws, stream)
+    sample_into(model, ham, n_samples, seed, counter, x, n, nu, ws, stream, binomial=binomial)
     k = int(nu.item())
     return x[:k], n[:k]
 

@@ -445,6 +445,23 @@ int anqs_sample(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
                      (cudaStream_t)stream);
 }
 
+int anqs_sample_binomial(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint64_t seed, uint64_t counter,
+                         const uint64_t* counter_dev, uint64_t* x_out, uint64_t* n_out, uint64_t cap,
+                         uint64_t* n_unique, void* ws, size_t ws_bytes, void* stream) {
+  ANQS_TRY(check_pair(M, H));
+  if (n_samples == 0) return set_error(ANQS_ERR_ARG, "n_samples must be >= 1");
+  if (!x_out || !n_out || !n_unique) return set_error(ANQS_ERR_ARG, "null output");
+  uint64_t need = n_samples < H->sector_dim ? n_samples : H->sector_dim;
+  if (cap < need)
+    return set_error(ANQS_ERR_CAPACITY, "cap %llu < min(n_samples, sector_dim) = %llu",
+                     (unsigned long long)cap, (unsigned long long)need);
+  size_t wsn = sampler_workspace(H, n_samples);
+  if (ws_bytes < wsn || (wsn && !ws))
+    return set_error(ANQS_ERR_CAPACITY, "sampler workspace needs %zu bytes", wsn);
+  return run_sampler(M, H, n_samples, seed, counter, counter_dev, x_out, n_out, n_unique, ws, ws_bytes,
+                     (cudaStream_t)stream, 0, 1, 0, true);
+}
+
 int anqs_sample_shard(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint64_t seed, uint64_t counter,
                       const uint64_t* counter_dev, int rank, int world, int split_level, uint64_t* x_out,
                       uint64_t* n_out, uint64_t cap, uint64_t* n_unique, void* ws, size_t ws_bytes, void* stream) {

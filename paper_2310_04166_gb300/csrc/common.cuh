@@ -297,6 +297,6 @@ size_t sampler_workspace(const anqs_ham* ham, uint64_t n_samples);
 int run_sampler(const anqs_model* md, const anqs_ham* ham, uint64_t n_samples, uint64_t seed,
                 uint64_t counter, const uint64_t* counter_dev, uint64_t* x_out, uint64_t* n_out,
                 uint64_t* n_unique, void* ws, size_t ws_bytes, cudaStream_t s, int rank = 0, int world = 1,
-                int split_level = 0);
+                int split_level = 0, bool binom = false);
 
 }  // namespace anqs

@@ -308,6 +308,124 @@ __global__ void draw_kernel(int p, uint64_t seed, uint64_t counter0, const uint6
   }
 }
 
+// ---- binomial statistics sampling (Sec. II.C) ---------------------------------
+// A node's n_in samples are split among its allowed outcomes by chained
+// binomials: k_v ~ B(rest, p_v / (p_v + ... + p_last)) in ascending v, the
+// last allowed outcome takes the rest; the cost per node does not depend on
+// n_in.  p is the node's masked conditional (the same float32 softmax as the
+// multinomial split).  Each binomial draws uniforms from its own Philox
+// stream: counter (prefix, (v << 32) | block, level, counter), key (seed, 1).
+struct Uniforms {
+  uint64_t x, v, p, counter, seed, blk;
+  uint64_t w[4];
+  int used;
+  __device__ double next() {
+    if (used == 4) {
+      Philox::block(x, (v << 32) | blk, p, counter, seed, 1ull, w);
+      ++blk;
+      used = 0;
+    }
+    return double(w[used++] >> 11) * 0x1.0p-53;
+  }
+};
+
+// log Gamma(x) for x >= 1 by the Stirling series, the argument shifted to
+// at least 10 (truncation below 1e-13 there)
+__device__ __forceinline__ double lgamma_stirling(double x) {
+  double shift = 0.0;
+  while (x < 10.0) {
+    shift -= log(x);
+    x += 1.0;
+  }
+  const double r = 1.0 / x, r2 = r * r;
+  const double series = r * (1.0 / 12 - r2 * (1.0 / 360 - r2 * (1.0 / 1260 - r2 * (1.0 / 1680))));
+  return shift + (x - 0.5) * log(x) - x + 0.91893853320467274178 + series;
+}
+
+// one draw of B(n, q)
+__device__ uint64_t binomial(uint64_t n, double q, Uniforms& U) {
+  if (n == 0 || !(q > 0.0)) return 0;
+  if (q >= 1.0) return n;
+  const bool flip = q > 0.5;
+  const double p = flip ? 1.0 - q : q, qq = 1.0 - p, nd = double(n);
+  uint64_t k = 0;
+  if (nd * p < 10.0) {
+    // inversion: walk the pmf from 0, P(k+1) = P(k) (n - k) p / ((k + 1) q)
+    double u = U.next(), r = exp(nd * log1p(-p));
+    const double s = p / qq, a = (nd + 1.0) * s;
+    while (u > r && k < n && k < 4096) {
+      u -= r;
+      ++k;
+      r *= a / double(k) - s;
+    }
+  } else {
+    // BTRS: transformed rejection with squeeze (Hormann 1993)
+    const double spq = sqrt(nd * p * qq);
+    const double b = 1.15 + 2.53 * spq, a = -0.0873 + 0.0248 * b + 0.01 * p, c = nd * p + 0.5;
+    const double vr = 0.92 - 4.2 / b, alpha = (2.83 + 5.1 / b) * spq, lpq = log(p / qq);
+    const double m = floor((nd + 1.0) * p);
+    const double h = lgamma_stirling(m + 1.0) + lgamma_stirling(nd - m + 1.0);
+    k = uint64_t(m);
+    for (int it = 0; it < 256; ++it) {  // acceptance is above 0.8 per iteration
+      const double u = U.next() - 0.5, v = U.next();
+      const double us = 0.5 - fabs(u);
+      const double kf = floor((2.0 * a / us + b) * u + c);
+      if (kf < 0.0 || kf > nd) continue;
+      if (us >= 0.07 && v <= vr) {
+        k = uint64_t(kf);
+        break;
+      }
+      const double lv = log(v * alpha / (a / (us * us) + b));
+      if (lv <= h - lgamma_stirling(kf + 1.0) - lgamma_stirling(nd - kf + 1.0) + (kf - m) * lpq) {
+        k = uint64_t(kf);
+        break;
+      }
+    }
+  }
+  return flip ? n - k : k;
+}
+
+__global__ void binom_kernel(HamView hv, int p, uint64_t seed, uint64_t counter0,
+                             const uint64_t* __restrict__ counter_dev, const uint64_t* __restrict__ pre,
+                             const uint64_t* __restrict__ cnt, const uint64_t* __restrict__ n_front,
+                             const float* __restrict__ logits, uint64_t* __restrict__ child) {
+  ANQS_PDL_ENTRY();
+  const uint64_t nf = *n_front;
+  const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < nf; i += uint64_t(gridDim.x) * blockDim.x) {
+    const uint64_t x = pre[i];
+    const unsigned mk = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p));
+    const float* l = logits + i * 8;
+    float m = -INFINITY;
+    for (int v = 0; v < 4; ++v)
+      if ((mk >> v) & 1u) m = fmaxf(m, l[v]);
+    float e[4], s = 0.f;
+    for (int v = 0; v < 4; ++v) {
+      e[v] = ((mk >> v) & 1u) ? exp_det(__fsub_rn(l[v], m)) : 0.f;
+      if ((mk >> v) & 1u) s = __fadd_rn(s, e[v]);
+    }
+    int last = 3;
+    while (last > 0 && !((mk >> last) & 1u)) --last;
+    uint64_t rest = cnt[i];
+    double tail = 1.0;  // probability mass of the outcomes not split off yet
+    for (int v = 0; v < 4; ++v) {
+      uint64_t k = 0;
+      if ((mk >> v) & 1u) {
+        if (v == last) {
+          k = rest;
+        } else {
+          const double pv = double(__fdiv_rn(e[v], s));
+          Uniforms U{x, uint64_t(v), uint64_t(p), counter, seed, 0, {0, 0, 0, 0}, 4};
+          k = binomial(rest, tail > 0.0 ? fmin(pv / tail, 1.0) : 1.0, U);
+          tail -= pv;
+        }
+      }
+      child[i * 4 + v] = k;
+      rest -= k;
+    }
+  }
+}
+
 __global__ void flag_kernel(const uint64_t* __restrict__ child, const uint64_t* __restrict__ n_front,
                             uint64_t* __restrict__ flags) {
   ANQS_PDL_ENTRY();
@@ -589,7 +707,7 @@ size_t sampler_workspace(const anqs_ham* H, uint64_t n_samples) {
 
 int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint64_t seed, uint64_t counter,
                 const uint64_t* counter_dev, uint64_t* x_out, uint64_t* n_out, uint64_t* n_unique, void* ws,
-                size_t ws_bytes, cudaStream_t s, int rank, int world, int split_level) {
+                size_t ws_bytes, cudaStream_t s, int rank, int world, int split_level, bool binom) {
   Arena A(ws, ws_bytes);
   Plan P;
   plan_ws(H, n_samples, A, P);
@@ -613,6 +731,14 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
     ANQS_TRY(logits_dispatch(M, H, p, P.pre[cur], nf, Fp, P.logits, s));
     ProfScope ps(PROF_SAMPLER, s);
     const bool last = (p == n - 1);
+    if (binom) {
+      ANQS_CUDA_LAUNCH("sampler binom_kernel", launch_k(binom_kernel, dim3(blocks_for(Fp, 128, 152 * 8)), dim3(128), 0, s, H->v, p, seed, counter, counter_dev, P.pre[cur], P.cnt[cur], nf, P.logits, P.child));
+      ANQS_CUDA_LAUNCH("sampler flag_kernel", launch_k(flag_kernel, dim3(blocks_for(Fp * 4, 256, 152 * 8)), dim3(256), 0, s, P.child, nf, P.flags));
+      uint64_t* nf_next = last ? n_unique : P.n_front + nxt;
+      ANQS_TRY(scan(P.flags, nf, 4, Fp * 4, P.partial, P.pos, nf_next, s));
+      ANQS_CUDA_LAUNCH("sampler scatter_kernel", launch_k(scatter_kernel, dim3(blocks_for(Fp * 4, 256, 152 * 8)), dim3(256), 0, s, p, P.pre[cur], P.child, nf, P.pos, last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt]));
+      continue;
+    }
     const bool small = Fp <= uint64_t(SMALL_F) && n_samples < (1ull << 31);
     if (small && prev_large) {
       // the multi-kernel path leaves its counters set; the small path expects them cleared

@@ -73,3 +73,49 @@ def test_deterministic_exp_accuracy():
         assert abs(float(p.sum()) - 1.0) < 4 * 2.0 ** -24 and np.all(p[~mask] == 0)
         ref = np.where(mask, np.exp(l - l[mask].max()), 0.0)
         assert np.abs(p - ref / ref.sum()).max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# binomial statistics sampling (Sec. II.C)
+# ---------------------------------------------------------------------------
+def test_binomial_sampler_conserves_and_follows_born_distribution():
+    from scipy.stats import chi2
+    from oracle.anqs import MLPAnsatz, log_psi
+    from oracle.sampler import sample_binomial
+    from oracle.sector import molecular_isphys, sector_states
+    from synthetic import workload
+    w = workload("small", bias_std=0.3)
+    om = MLPAnsatz(w["params_struct"], w["n"])
+    ip = molecular_isphys(w["n"], w["n_alpha"], w["n_beta"])
+    Ns = 10 ** 7
+    x, c = sample_binomial(om, ip, w["n"], Ns, np.random.default_rng(3))
+    assert c.sum() == Ns and np.all(c > 0)
+    st = np.array(sector_states(w["n"], w["n_alpha"], w["n_beta"]), dtype=np.uint64)
+    assert np.all(np.isin(x, st))
+    la, _ = log_psi(om, ip, st)
+    prob = np.exp(2 * la.numpy())
+    full = np.zeros(len(st))
+    full[np.searchsorted(st, x)] = c
+    stat = ((full - Ns * prob) ** 2 / (Ns * prob)).sum()
+    assert stat < chi2.ppf(1 - 1e-6, len(st) - 1)
+
+
+def test_binomial_chain_has_multinomial_moments():
+    """One free node (2 orbitals, 1 + 1 electrons: slot 0 takes any of the 4
+    values, slot 1 is forced): the chained binomials reproduce the mean
+    N p_v and the variance N p_v (1 - p_v) of the multinomial split."""
+    from oracle.sampler import sample_binomial
+    from oracle.sector import molecular_isphys
+    p = np.array([0.5, 0.3, 0.15, 0.05])
+    ip = molecular_isphys(2, 1, 1)
+    logits = lambda pre, q: np.tile(np.log(p), (len(pre), 1))
+    rng = np.random.default_rng(7)
+    N, R = 1000, 4000
+    counts = np.zeros((R, 4))
+    for r in range(R):
+        x, c = sample_binomial(None, ip, 2, N, rng, logits_fn=logits)
+        counts[r, (x & np.uint64(3)).astype(int)] = c
+    assert np.all(counts.sum(1) == N)
+    mean, var = counts.mean(0), counts.var(0, ddof=1)
+    assert np.all(np.abs(mean - N * p) < 5 * np.sqrt(N * p * (1 - p) / R))
+    assert np.all(np.abs(var / (N * p * (1 - p)) - 1) < 5 * np.sqrt(2 / R))
