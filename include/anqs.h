@@ -127,6 +127,19 @@ ANQS_API int anqs_hamiltonian_create(anqs_ham** out, int n_orb, int n_alpha, int
                             const double* h_host, const double* g_host, double e_nuc);
 ANQS_API int anqs_hamiltonian_destroy(anqs_ham* ham);
 
+/* Pruning strategy of unphysical subtrees (Sec. III.C, Fig. 1C): MU-d with
+ * d = du_levels, i.e. MU on the first n_orb - d slots and DU on the last d
+ * (slot levels of this build's 4-way tree).  d = 0 (the default) is MU:
+ * conditionals are renormalised over the allowed outcomes and no sample is
+ * lost.  d = n_orb is DU: on a DU level the conditional is the network's
+ * softmax over all four outcomes, and samples drawn into an unphysical child
+ * are discarded, so the counts may add up to less than n_samples; amplitudes
+ * of sector determinants use the same unmasked conditionals on those levels
+ * (log psi of a determinant outside the sector stays -inf).  Applies to
+ * every later call with this Hamiltonian (sampling, log psi, local energy,
+ * gradient).  ANQS_ERR_ARG unless 0 <= du_levels <= n_orb. */
+ANQS_API int anqs_hamiltonian_set_pruning(anqs_ham* ham, int du_levels);
+
 /* n_connected: off-diagonal determinants connected to every sector
  * determinant by H (same for all of them):
  *   Na(n-Na) + Nb(n-Nb) + C(Na,2)C(n-Na,2) + C(Nb,2)C(n-Nb,2) + Na(n-Na)Nb(n-Nb).

@@ -93,13 +93,27 @@ def masked_log_prob(logits: torch.Tensor, mask: torch.Tensor) -> torch.Tensor:
     return lm - lse
 
 
-def log_psi_from_logits(out: torch.Tensor, xs, mask: np.ndarray, forced_phase_zero: bool = False):
+def norm_masks(mask: np.ndarray, du_levels: int = 0) -> np.ndarray:
+    """Outcomes over which each slot's conditional is normalised under the
+    MU-d strategy (Sec. III.C): the physical ones on the first n - d slots
+    (MU), all four on the last d (DU, where samples sent to an unphysical
+    child are discarded).  d = 0 is MU, d = n is DU."""
+    nm = np.array(mask, dtype=bool, copy=True)
+    if du_levels > 0:
+        nm[:, nm.shape[1] - du_levels:, :] = True
+    return nm
+
+
+def log_psi_from_logits(out: torch.Tensor, xs, mask: np.ndarray, forced_phase_zero: bool = False,
+                        du_levels: int = 0):
     """out: [B, n, 8] network outputs per slot.  Returns (log|psi|, phase)
-    as FP64 tensors: log|psi| = sum_p 1/2 log p~_p(v_p), phase = sum_p phi_p(v_p)."""
+    as FP64 tensors: log|psi| = sum_p 1/2 log p~_p(v_p), phase = sum_p phi_p(v_p),
+    with p~ normalised as norm_masks says and zero for unphysical v_p."""
     n = out.shape[1]
     v = torch.as_tensor(slot_values(xs, n))
     m = torch.as_tensor(mask)
-    lp = masked_log_prob(out[..., :4], m)
+    lp = masked_log_prob(out[..., :4], torch.as_tensor(norm_masks(mask, du_levels)))
+    lp = torch.where(m, lp, torch.full_like(lp, -math.inf))
     lp_sel = torch.gather(lp, 2, v[..., None])[..., 0]
     ph_sel = torch.gather(out[..., 4:], 2, v[..., None])[..., 0]
     if forced_phase_zero:
@@ -238,11 +252,12 @@ def table_from_state(states, amps, n: int, floor: float = -1e30):
     return tables
 
 
-def log_psi(model, isphys: IsPhys, xs, forced_phase_zero: bool = False):
-    """(log|psi(x)|, arg psi(x)) in FP64 for a batch of determinants."""
+def log_psi(model, isphys: IsPhys, xs, forced_phase_zero: bool = False, du_levels: int = 0):
+    """(log|psi(x)|, arg psi(x)) in FP64 for a batch of determinants (MU-d
+    strategy with d = du_levels; 0 = MU)."""
     xs = np.asarray(xs, dtype=np.uint64)
     mask = allowed_masks(isphys, xs, model.n)
-    return log_psi_from_logits(model.outputs(xs), xs, mask, forced_phase_zero)
+    return log_psi_from_logits(model.outputs(xs), xs, mask, forced_phase_zero, du_levels)
 
 
 def conditionals(model, isphys: IsPhys, prefixes, p: int):

@@ -112,8 +112,12 @@ def split_node(probs: np.ndarray, mask, u: np.ndarray, tol: float = 0.0):
 
 
 def sample(model, isphys, n: int, n_samples: int, seed: int, counter: int = 0,
-           logits_fn=None, tol: float | None = None, shard=None):
+           logits_fn=None, tol: float | None = None, shard=None, du_levels: int = 0):
     """Unique samples and counts, in the tree's lexicographic order.
+
+    ``du_levels = d`` selects the MU-d strategy (Sec. III.C): on the last d
+    slots the split uses the conditional over all four outcomes and the
+    samples drawn into an unphysical child are discarded (d = 0: MU).
 
     ``shard = (rank, world, level)`` keeps, of the frontier reached after
     ``level`` slots (the leaves when level = n), the nodes i with
@@ -145,11 +149,13 @@ def sample(model, isphys, n: int, n_samples: int, seed: int, counter: int = 0,
         else:
             L = np.asarray(logits_fn(pre, p), dtype=np.float64)
         M = allowed_masks(isphys, pre, n)[:, p]
+        NM = M if p < n - du_levels else np.ones_like(M)
         new_pre, new_cnt = [], []
         for k in range(len(pre)):
-            probs = split_probabilities(L[k], M[k])
+            probs = split_probabilities(L[k], NM[k])
             u = node_uniforms(int(pre[k]), int(cnt[k]), p, seed, counter)
-            c, mg, nc = split_node(probs, M[k], u, tol or 0.0)
+            c, mg, nc = split_node(probs, NM[k], u, tol or 0.0)
+            c = np.where(M[k], c, 0)  # DU levels: samples of unphysical children are lost
             margin = min(margin, mg)
             n_close += nc
             for v in range(4):
@@ -173,7 +179,7 @@ def lexicographic_key(xs, n: int) -> np.ndarray:
     return key
 
 
-def sample_binomial(model, isphys, n: int, n_samples: int, rng, logits_fn=None):
+def sample_binomial(model, isphys, n: int, n_samples: int, rng, logits_fn=None, du_levels: int = 0):
     """Binomial statistics sampling (Sec. II.C): at every node the n_in
     samples are split among the allowed outcomes by chained binomials,
     k_v ~ B(rest, p_v / (p_v + ... + p_last)) in ascending v, the last
@@ -192,10 +198,11 @@ def sample_binomial(model, isphys, n: int, n_samples: int, rng, logits_fn=None):
         else:
             L = torch.as_tensor(np.asarray(logits_fn(pre, p), dtype=np.float64))
         M = allowed_masks(isphys, pre, n)[:, p]
-        P = torch.exp(masked_log_prob(L, torch.as_tensor(M))).numpy()
+        NM = M if p < n - du_levels else np.ones_like(M)
+        P = torch.exp(masked_log_prob(L, torch.as_tensor(NM))).numpy()
         new_pre, new_cnt = [], []
         for k in range(len(pre)):
-            allowed = [v for v in range(4) if M[k][v]]
+            allowed = [v for v in range(4) if NM[k][v]]
             rest, tail = int(cnt[k]), 1.0
             for v in allowed:
                 if v == allowed[-1]:
@@ -205,7 +212,7 @@ def sample_binomial(model, isphys, n: int, n_samples: int, rng, logits_fn=None):
                     c = int(rng.binomial(rest, q))
                     tail -= P[k][v]
                 rest -= c
-                if c > 0:
+                if c > 0 and M[k][v]:
                     new_pre.append(int(pre[k]) | (v << (2 * p)))
                     new_cnt.append(c)
         pre = np.array(new_pre, dtype=np.uint64)

@@ -33,7 +33,7 @@ def connected_lists(ham, xs):
     return [ham.connected(int(x)) for x in xs], np.array([ham.diagonal(int(x)) for x in xs])
 
 
-def local_energy(model, isphys, ham, xs, lists=None, diag=None):
+def local_energy(model, isphys, ham, xs, lists=None, diag=None, du_levels: int = 0):
     """Complex E_loc per unique sample, FP64."""
     xs = np.asarray(xs, dtype=np.uint64)
     if lists is None:
@@ -42,8 +42,9 @@ def local_energy(model, isphys, ham, xs, lists=None, diag=None):
     flat_h = np.array([v for L in lists for _, v, _ in L], dtype=np.float64)
     sizes = [len(L) for L in lists]
     with torch.no_grad():
-        la, ph = log_psi(model, isphys, xs)
-        la_p, ph_p = log_psi(model, isphys, flat_x) if len(flat_x) else (torch.zeros(0), torch.zeros(0))
+        la, ph = log_psi(model, isphys, xs, du_levels=du_levels)
+        la_p, ph_p = (log_psi(model, isphys, flat_x, du_levels=du_levels) if len(flat_x)
+                      else (torch.zeros(0), torch.zeros(0)))
     la, ph, la_p, ph_p = (t.numpy() for t in (la, ph, la_p, ph_p))
     e = np.zeros(len(xs), dtype=np.complex128)
     off = 0
@@ -82,7 +83,7 @@ def combine_stats(stats_list):
     return np.array([Er, Ei, var, S])
 
 
-def gradient(model, isphys, xs, counts, eloc, stats=None):
+def gradient(model, isphys, xs, counts, eloc, stats=None, du_levels: int = 0):
     """VMC gradient (Eq. grad_def) with respect to model.parameters(), FP64."""
     xs = np.asarray(xs, dtype=np.uint64)
     if stats is None:
@@ -94,7 +95,7 @@ def gradient(model, isphys, xs, counts, eloc, stats=None):
     for t in params:
         t.requires_grad_(True)
         t.grad = None
-    la, ph = log_psi(model, isphys, xs)
+    la, ph = log_psi(model, isphys, xs, du_levels=du_levels)
     L = (torch.as_tensor(2.0 * w * dre) * la).sum() + (torch.as_tensor(2.0 * w * dim) * ph).sum()
     grads = torch.autograd.grad(L, params, allow_unused=True)
     for t in params:

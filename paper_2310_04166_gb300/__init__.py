@@ -68,6 +68,11 @@ class Hamiltonian:
     def handle(self):
         return self._h
 
+    def set_pruning(self, du_levels: int) -> "Hamiltonian":
+        """MU-d (Sec. III.C): MU on the first n_orb - du_levels slots, DU on the rest."""
+        check(_lib.load().anqs_hamiltonian_set_pruning(self._h, int(du_levels)))
+        return self
+
     def slot_masks(self) -> np.ndarray:
         out = np.zeros((self.n, self.n_alpha + 1, self.n_beta + 1), dtype=np.uint8)
         check(_lib.load().anqs_hamiltonian_slot_masks(self._h, out.ctypes.data, out.nbytes))

@@ -222,7 +222,16 @@ int anqs_hamiltonian_create(anqs_ham** out, int n, int na, int nb, const double*
   v.h = H->d_h;
   v.g = H->d_g;
   v.mask = H->d_mask;
+  v.mu_lv = n;
   *out = H;
+  return ANQS_OK;
+}
+
+int anqs_hamiltonian_set_pruning(anqs_ham* H, int du_levels) {
+  if (!H) return set_error(ANQS_ERR_ARG, "null Hamiltonian");
+  if (du_levels < 0 || du_levels > H->v.n)
+    return set_error(ANQS_ERR_ARG, "du_levels %d outside 0..%d", du_levels, H->v.n);
+  H->v.mu_lv = H->v.n - du_levels;
   return ANQS_OK;
 }
 

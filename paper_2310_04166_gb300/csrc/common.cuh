@@ -122,6 +122,7 @@ struct HamView {
   const double* h;     // [n][n]
   const double* g;     // [n][n][n][n] chemist notation
   const uint8_t* mask; // [n][na+1][nb+1] allowed-outcome bits per slot and prefix counts
+  int mu_lv;           // slots p < mu_lv are masked (MU), slots p >= mu_lv discard (DU): MU-d, d = n - mu_lv
 };
 
 __host__ __device__ inline int mask_index(const HamView& hv, int p, int a, int b) {
@@ -134,6 +135,13 @@ __host__ __device__ inline int mask_index(const HamView& hv, int p, int a, int b
 __device__ __forceinline__ unsigned slot_mask(const HamView& hv, int p, int a, int b) {
   if (a > hv.na || b > hv.nb) return 0u;
   return hv.mask[mask_index(hv, p, a, b)];
+}
+
+// Outcomes over which slot p's conditional is normalised (Sec. III.C): the
+// allowed ones on MU levels (p < mu_lv), all four on DU levels, where samples
+// that go to an unphysical child are discarded.
+__device__ __forceinline__ unsigned norm_mask(const HamView& hv, int p, unsigned phys) {
+  return p < hv.mu_lv ? phys : 0xFu;
 }
 #endif
 

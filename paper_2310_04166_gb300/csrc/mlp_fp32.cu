@@ -146,9 +146,12 @@ __device__ int slot_forward(const MlpView& m, int p, const uint64_t* xs, int nro
   return cur;
 }
 
-// masked log-softmax term of the chosen outcome (FP32)
-__device__ __forceinline__ void slot_term(const float* o8, unsigned mask, int v, float& la, float& ph, bool& dead) {
-  if (!((mask >> v) & 1u)) {
+// log-softmax term of the chosen outcome (FP32): normalised over nm, zero
+// amplitude (dead) when v is not physical
+__device__ __forceinline__ void slot_term(const float* o8, unsigned nm, unsigned phys, int v, float& la, float& ph,
+                                          bool& dead) {
+  const unsigned mask = nm;
+  if (!((phys >> v) & 1u)) {
     dead = true;
     return;
   }
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(NT) logpsi_kernel(MlpView m, HamView hv, const
         int v = int((xt[r] >> (2 * p)) & 3ull);
         unsigned mk = slot_mask(hv, p, ca[r], cb[r]);
         bool dd = dead[r];
-        slot_term(out8 + r * 8, mk, v, la[r], ph[r], dd);
+        slot_term(out8 + r * 8, norm_mask(hv, p, mk), mk, v, la[r], ph[r], dd);
         dead[r] = dd;
         ca[r] += v & 1;
         cb[r] += v >> 1;
@@ -339,9 +342,9 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
         a += vq & 1;
         b += vq >> 1;
       }
-      unsigned mk = slot_mask(hv, p, a, b);
+      const unsigned pm = slot_mask(hv, p, a, b), mk = norm_mask(hv, p, pm);
       int v = int((x >> (2 * p)) & 3ull);
-      if ((mk >> v) & 1u) {
+      if ((pm >> v) & 1u) {
         const float* o8 = out8 + r * 8;
         float mx = -INFINITY;
         for (int u = 0; u < 4; ++u)

@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_ws_kernel(TcView tv, HamView hv,
         const uint64_t pm = (1ull << (2 * p)) - 1ull;
         const int a = __popcll(x & pm & 0x5555555555555555ull);
         const int bb = __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull);
-        const unsigned mk = slot_mask(hv, p, a, bb);
+        const unsigned pmk = slot_mask(hv, p, a, bb), mk = norm_mask(hv, p, pmk);
         float mx = -INFINITY;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -477,7 +477,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_ws_kernel(TcView tv, HamView hv,
         const float ov = (v == 0) ? out[0] : (v == 1) ? out[1] : (v == 2) ? out[2] : out[3];
         const float pv = (v == 0) ? out[4] : (v == 1) ? out[5] : (v == 2) ? out[6] : out[7];
         const float lse = mx + __logf(sum);  // same expression order as finalize_kernel
-        T[uint64_t(row) * n + p] = make_float2(((mk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY, pv);
+        T[uint64_t(row) * n + p] = make_float2(((pmk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY, pv);
       }
     }
     if (!ok) s_abort = 1;
@@ -549,7 +549,7 @@ __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Cou
     int a = 0, b = 0;
     for (int p = 0; p < n; ++p) {
       const float* o = raw + (l * n + p) * 8;
-      const unsigned mk = slot_mask(hv, p, a, b);
+      const unsigned pmk = slot_mask(hv, p, a, b), mk = norm_mask(hv, p, pmk);
       float mx = -INFINITY;
       for (int u = 0; u < 4; ++u)
         if ((mk >> u) & 1u) mx = fmaxf(mx, o[u]);
@@ -562,12 +562,12 @@ __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Cou
         cc[0] = la;
         cc[1] = ph;
         for (int u = 0; u < 4; ++u) {
-          cc[2 + u] = ((mk >> u) & 1u) ? 0.5f * (o[u] - lse) : -INFINITY;
+          cc[2 + u] = ((pmk >> u) & 1u) ? 0.5f * (o[u] - lse) : -INFINITY;
           cc[6 + u] = o[4 + u];
         }
       }
       const int v = int((x >> (2 * p)) & 3ull);
-      if (!((mk >> v) & 1u)) dead = true;
+      if (!((pmk >> v) & 1u)) dead = true;
       if (!dead) la += 0.5f * (o[v] - lse);
       ph += o[4 + v];
       a += v & 1;

@@ -137,14 +137,14 @@ __global__ void prep_kernel(HamView hv, int p, const uint64_t* __restrict__ pre,
   const uint64_t nf = *n_front;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < nf; i += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t x = pre[i];
-    unsigned mk = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p));
+    const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p)), mk = norm_mask(hv, p, pm);
     uint64_t T[4];
     split_thresholds(logits + i * 8, mk, T);
     for (int v = 0; v < 4; ++v) {
       thr[i * 4 + v] = T[v];
       child[i * 4 + v] = 0;
     }
-    allowed[i] = uint8_t(mk);
+    allowed[i] = uint8_t(mk | (pm << 4));  // low: normalised outcomes, high: physical ones
     nblk[i] = (cnt[i] + 3) / 4;
   }
 }
@@ -279,14 +279,15 @@ __global__ void draw_kernel(int p, uint64_t seed, uint64_t counter0, const uint6
       const uint64_t x = pre[lo];
       uint64_t w[4];
       Philox::block(x, ib, uint64_t(p), counter, seed, 0ull, w);
-      const unsigned mk = allowed[lo];
+      const unsigned mk = allowed[lo] & 0xFu, pm = allowed[lo] >> 4;
       uint64_t T[4];
       for (int v = 0; v < 4; ++v) T[v] = thr[lo * 4 + v];
       int last = 3;
       while (last > 0 && !((mk >> last) & 1u)) --last;
       for (int k = 0; k < 4; ++k) {
         if (ib * 4 + k >= c) break;
-        packed += 1u << (8 * draw_outcome(w[k], T, mk, last));
+        const int v = draw_outcome(w[k], T, mk, last);
+        if ((pm >> v) & 1u) packed += 1u << (8 * v);  // DU levels: a draw to an unphysical child is lost
       }
     }
     // segmented sum over lanes with the same node (nodes are non-decreasing in t)
@@ -394,7 +395,7 @@ __global__ void binom_kernel(HamView hv, int p, uint64_t seed, uint64_t counter0
   const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < nf; i += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t x = pre[i];
-    const unsigned mk = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p));
+    const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p)), mk = norm_mask(hv, p, pm);
     const float* l = logits + i * 8;
     float m = -INFINITY;
     for (int v = 0; v < 4; ++v)
@@ -420,7 +421,7 @@ __global__ void binom_kernel(HamView hv, int p, uint64_t seed, uint64_t counter0
           tail -= pv;
         }
       }
-      child[i * 4 + v] = k;
+      child[i * 4 + v] = ((pm >> v) & 1u) ? k : 0ull;  // DU levels: samples of unphysical children are lost
       rest -= k;
     }
   }
@@ -545,9 +546,9 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
       const int i = n_lo + threadIdx.x;
       for (int v = 0; v < 4; ++v) s_cnt[threadIdx.x][v] = 0;
       const uint64_t x = pre[i];
-      const unsigned mk = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p));
+      const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p)), mk = norm_mask(hv, p, pm);
       split_thresholds(logits + uint64_t(i) * 8, mk, s_thr[threadIdx.x]);
-      s_mk[threadIdx.x] = uint8_t(mk);
+      s_mk[threadIdx.x] = uint8_t(mk | (pm << 4));
     }
     __syncthreads();
     const uint32_t t = t0 + threadIdx.x;
@@ -560,12 +561,13 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
       const uint64_t c = cnt[node];
       uint64_t w[4];
       Philox::block(pre[node], ib, uint64_t(p), counter, seed, 0ull, w);
-      const unsigned mk = s_mk[li];
+      const unsigned mk = s_mk[li] & 0xFu, pm = s_mk[li] >> 4;
       int last = 3;
       while (last > 0 && !((mk >> last) & 1u)) --last;
       for (int k = 0; k < 4; ++k) {
         if (ib * 4 + k >= c) break;
-        packed += 1u << (8 * draw_outcome(w[k], s_thr[li], mk, last));
+        const int v = draw_outcome(w[k], s_thr[li], mk, last);
+        if ((pm >> v) & 1u) packed += 1u << (8 * v);
       }
     }
     const int prev = __shfl_up_sync(0xffffffffu, node, 1);

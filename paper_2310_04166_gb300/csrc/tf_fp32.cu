@@ -237,9 +237,12 @@ __device__ void tile_forward(const TfView& m, const uint64_t* xs, int S, int T, 
   __syncthreads();
 }
 
-// masked log-softmax term of the chosen outcome (FP32), as for the MLP
-__device__ __forceinline__ void slot_term(const float* o8, unsigned mask, int v, float& la, float& ph, bool& dead) {
-  if (!((mask >> v) & 1u)) {
+// log-softmax term of the chosen outcome (FP32), as for the MLP: normalised
+// over nm, dead when v is not physical
+__device__ __forceinline__ void slot_term(const float* o8, unsigned nm, unsigned phys, int v, float& la, float& ph,
+                                          bool& dead) {
+  const unsigned mask = nm;
+  if (!((phys >> v) & 1u)) {
     dead = true;
     return;
   }
@@ -279,7 +282,8 @@ __global__ void __launch_bounds__(NT, 1) tf_logpsi_kernel(TfView m, HamView hv, 
       int ca = 0, cb = 0;
       for (int p = 0; p < T; ++p) {
         const int v = int((x >> (2 * p)) & 3ull);
-        slot_term(out8 + (s * T + p) * 8, slot_mask(hv, p, ca, cb), v, la, ph, dead);
+        const unsigned pm = slot_mask(hv, p, ca, cb);
+        slot_term(out8 + (s * T + p) * 8, norm_mask(hv, p, pm), pm, v, la, ph, dead);
         ca += v & 1;
         cb += v >> 1;
       }

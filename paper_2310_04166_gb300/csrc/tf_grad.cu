@@ -361,7 +361,7 @@ __global__ void head_dout_kernel(HamView hv, const uint64_t* __restrict__ x, Cou
     ca = cb = 0;
     for (int p = 0; p < n; ++p) {
       const int v = int((xs >> (2 * p)) & 3ull);
-      const unsigned mk = slot_mask(hv, p, ca, cb);
+      const unsigned mk = norm_mask(hv, p, slot_mask(hv, p, ca, cb));
       const float* o = out8 + (s * n + p) * 8;
       float* d = dout8 + (s * n + p) * 8;
       float mx = -INFINITY;

@@ -553,8 +553,9 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
           }
         } else {
           const uint64_t pm = (1ull << (2 * pos)) - 1ull;
-          const unsigned mk = slot_mask(a.hv, pos, __popcll(x & pm & 0x5555555555555555ull),
-                                        __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull));
+          const unsigned pmk = slot_mask(a.hv, pos, __popcll(x & pm & 0x5555555555555555ull),
+                                         __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull));
+          const unsigned mk = norm_mask(a.hv, pos, pmk);
           float mx = -INFINITY;
 #pragma unroll
           for (int u = 0; u < 4; ++u)
@@ -567,7 +568,7 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
           const float ov = (v == 0) ? out[0] : (v == 1) ? out[1] : (v == 2) ? out[2] : out[3];
           const float pv = (v == 0) ? out[4] : (v == 1) ? out[5] : (v == 2) ? out[6] : out[7];
           const float lse = mx + __logf(sum);
-          a.T[seq * n + pos] = make_float2(((mk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY, pv);
+          a.T[seq * n + pos] = make_float2(((pmk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY, pv);
         }
       }
     }
