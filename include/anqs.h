@@ -140,16 +140,34 @@ ANQS_API int anqs_hamiltonian_destroy(anqs_ham* ham);
  * gradient).  ANQS_ERR_ARG unless 0 <= du_levels <= n_orb. */
 ANQS_API int anqs_hamiltonian_set_pruning(anqs_ham* ham, int du_levels);
 
+/* Z2 symmetries of H (Sec. IV.A: Pauli-Z strings that commute with H, such
+ * as the images of the abelian point-group operations under the
+ * Jordan-Wigner transform).  qubit_masks[j] (host) has bit q set when
+ * symmetry j acts with Z on qubit q = 2p + sigma.  The target eigenvalues
+ * are those of the reference determinant (the lowest N_alpha alpha and
+ * N_beta beta orbitals occupied); IsPhys (Algorithm 1) then masks every
+ * outcome that cannot reach them, on top of the electron counts, so the
+ * sampler, the amplitudes and the sector dimension all refer to the smaller
+ * sector.  The caller guarantees that the strings commute with H (the
+ * connected set is not filtered: an excitation that changes a parity has
+ * H_xx' = 0 and psi(x') = 0).  0 <= nz <= 4 (nz = 0 removes them); each mask
+ * within the 2 n_orb qubits.  ANQS_ERR_SECTOR (and no change) when the
+ * resulting sector is empty. */
+ANQS_API int anqs_hamiltonian_set_z2(anqs_ham* ham, int nz, const uint64_t* qubit_masks);
+
 /* n_connected: off-diagonal determinants connected to every sector
  * determinant by H (same for all of them):
  *   Na(n-Na) + Nb(n-Nb) + C(Na,2)C(n-Na,2) + C(Nb,2)C(n-Nb,2) + Na(n-Na)Nb(n-Nb).
- * sector_dim: C(n,Na) C(n,Nb) (saturated at UINT64_MAX).  Either may be NULL. */
+ * sector_dim: the number of determinants in the sector (C(n,Na) C(n,Nb)
+ * without Z2 symmetries; saturated at UINT64_MAX).  Either may be NULL. */
 ANQS_API int anqs_hamiltonian_info(const anqs_ham* ham, uint64_t* n_connected, uint64_t* sector_dim);
 
-/* Slot mask table computed by IsPhys: out_host receives n*(Na+1)*(Nb+1)
- * bytes, entry [(p*(Na+1)+a)*(Nb+1)+b] = bit v set when outcome v of slot p
- * is allowed after a prefix holding a alpha and b beta electrons (0 when the
- * prefix itself is unphysical).  len must be at least that size. */
+/* Slot mask table computed by IsPhys: out_host receives
+ * n*(Na+1)*(Nb+1)*2^nz bytes (nz = number of Z2 symmetries set), entry
+ * [((p*(Na+1)+a)*(Nb+1)+b)*2^nz+z] = bit v set when outcome v of slot p is
+ * allowed after a prefix holding a alpha and b beta electrons whose Z2
+ * parities are the bits of z (0 when the prefix itself is unphysical).  len
+ * must be at least that size. */
 ANQS_API int anqs_hamiltonian_slot_masks(const anqs_ham* ham, uint8_t* out_host, size_t len);
 
 /* ---------------------------------------------------------------------------

@@ -18,7 +18,9 @@ def sector_basis(n: int, n_alpha: int, n_beta: int) -> np.ndarray:
 
 
 def ground_state(ham, states, dense_limit: int = 3000):
-    """(E_0, c) of the sector Hamiltonian built from the connected lists."""
+    """(E_0, c) of the sector Hamiltonian built from the connected lists.
+    ``states`` may be a symmetry sector inside the (N_a, N_b) one, provided H
+    has no element leading out of it."""
     states = [int(s) for s in states]
     idx = {x: k for k, x in enumerate(states)}
     rows, cols, vals = [], [], []
@@ -27,6 +29,12 @@ def ground_state(ham, states, dense_limit: int = 3000):
         cols.append(k)
         vals.append(ham.diagonal(x))
         for xp, v, _ in ham.connected(x):
+            if xp not in idx:
+                # a symmetry sector smaller than the (N_a, N_b) sector (Z2,
+                # Sec. IV.A): H must not connect it to the rest
+                if v != 0.0:
+                    raise ValueError(f"H connects {x} to {xp} outside the given states")
+                continue
             rows.append(idx[xp])
             cols.append(k)
             vals.append(v)

@@ -54,7 +54,7 @@ class Hamiltonian:
         n = h.shape[0]
         if h.shape != (n, n) or g.shape != (n, n, n, n):
             raise ValueError("h must be n x n and g n x n x n x n")
-        self.n, self.n_alpha, self.n_beta = n, n_alpha, n_beta
+        self.n, self.n_alpha, self.n_beta, self.nz = n, n_alpha, n_beta, 0
         self.device = torch.cuda.current_device()
         hp = C.c_void_p()
         check(lib.anqs_hamiltonian_create(C.byref(hp), n, n_alpha, n_beta, h.ctypes.data, g.ctypes.data,
@@ -73,8 +73,20 @@ class Hamiltonian:
         check(_lib.load().anqs_hamiltonian_set_pruning(self._h, int(du_levels)))
         return self
 
+    def set_z2(self, qubit_masks) -> "Hamiltonian":
+        """Z2 symmetries (Pauli-Z strings commuting with H), one qubit mask each."""
+        m = np.ascontiguousarray(np.asarray(qubit_masks, dtype=np.uint64))
+        check(_lib.load().anqs_hamiltonian_set_z2(self._h, len(m), m.ctypes.data if len(m) else None))
+        self.nz = len(m)
+        info_k, info_d = C.c_uint64(), C.c_uint64()
+        check(_lib.load().anqs_hamiltonian_info(self._h, C.byref(info_k), C.byref(info_d)))
+        self.sector_dim = info_d.value
+        return self
+
     def slot_masks(self) -> np.ndarray:
-        out = np.zeros((self.n, self.n_alpha + 1, self.n_beta + 1), dtype=np.uint8)
+        """[n][N_a + 1][N_b + 1] (or [...][2^nz] with Z2 symmetries) outcome bits."""
+        shape = (self.n, self.n_alpha + 1, self.n_beta + 1) + ((1 << self.nz,) if self.nz else ())
+        out = np.zeros(shape, dtype=np.uint8)
         check(_lib.load().anqs_hamiltonian_slot_masks(self._h, out.ctypes.data, out.nbytes))
         return out
 

@@ -32,30 +32,39 @@ int cuda_error(cudaError_t e, const char* what, const char* file, int line) {
 }
 
 // ---------------------------------------------------------------------------
-// IsPhys (Algorithm 1) over the qubit tree for the additive symmetries n_e
-// and 2 S_z (Appendix A), memoised in a dense lookup keyed by (i, n_e, 2 S_z)
-// (Proposition 1).  Qubit i (1-based) adds n_e += x_i and 2 S_z += x_i for
-// odd i (spin up), -x_i for even i.  The target is the pair of the
-// reference determinant: (N_a + N_b, N_a - N_b).
+// IsPhys (Algorithm 1) over the qubit tree, memoised in a dense lookup keyed
+// by (i, n_e, 2 S_z, z) (Proposition 1).  Qubit i (1-based) adds n_e += x_i
+// and 2 S_z += x_i for odd i (spin up), -x_i for even i (Appendix A, additive
+// symmetries); each Z2 symmetry (a Pauli-Z string, Sec. IV.A, multiplicative)
+// multiplies its eigenvalue by (-1)^x_i on the qubits of its support, kept
+// here as parity bit j of z.  The target is the eigenvalue vector of the
+// reference determinant.
 // ---------------------------------------------------------------------------
 struct IsPhysTable {
-  int N, ne_ref, sz_ref;
+  int N, ne_ref, sz_ref, z_ref, nz;
+  const uint64_t* zm;
   std::vector<int8_t> memo;  // -1 unknown, 0 false, 1 true
-  IsPhysTable(int n_qubits, int ne, int sz) : N(n_qubits), ne_ref(ne), sz_ref(sz) {
-    memo.assign(size_t(N + 2) * (N + 1) * (2 * N + 1), -1);
+  IsPhysTable(int n_qubits, int ne, int sz, int nz_, const uint64_t* zmask, int zref)
+      : N(n_qubits), ne_ref(ne), sz_ref(sz), z_ref(zref), nz(nz_), zm(zmask) {
+    memo.assign(size_t(N + 2) * (N + 1) * (2 * N + 1) << nz, -1);
   }
-  size_t key(int i, int ne, int sz) const {
-    return (size_t(i) * (N + 1) + ne) * (2 * N + 1) + (sz + N);
+  size_t key(int i, int ne, int sz, int z) const {
+    return (((size_t(i) * (N + 1) + ne) * (2 * N + 1) + (sz + N)) << nz) + z;
   }
-  bool operator()(int i, int ne, int sz) {
-    int8_t& m = memo[key(i, ne, sz)];
+  int flip(int i) const {  // parity bits flipped by x_i = 1
+    int f = 0;
+    for (int j = 0; j < nz; ++j) f |= int((zm[j] >> (i - 1)) & 1ull) << j;
+    return f;
+  }
+  bool operator()(int i, int ne, int sz, int z) {
+    int8_t& m = memo[key(i, ne, sz, z)];
     if (m >= 0) return m != 0;
     bool r;
     if (i == N + 1) {
-      r = (ne == ne_ref && sz == sz_ref);
+      r = (ne == ne_ref && sz == sz_ref && z == z_ref);
     } else {
       int dsz = (i % 2 == 1) ? 1 : -1;
-      r = (*this)(i + 1, ne, sz) || (*this)(i + 1, ne + 1, sz + dsz);
+      r = (*this)(i + 1, ne, sz, z) || (*this)(i + 1, ne + 1, sz + dsz, z ^ flip(i));
     }
     m = r ? 1 : 0;
     return r;
@@ -136,6 +145,68 @@ static int vjp_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* 
 
 using namespace anqs;
 
+// Slot masks, physical-prefix counts per level and the sector dimension from
+// IsPhys; the prefix counts come from a forward count of the qubit strings
+// reaching each state (saturating).
+static int build_sector(anqs_ham* H) {
+  HamView& v = H->v;
+  const int n = v.n, na = v.na, nb = v.nb, N = 2 * n, nz = v.nz, Z = 1 << nz;
+  int zref = 0;  // reference determinant: the lowest N_a alpha and N_b beta orbitals
+  for (int j = 0; j < nz; ++j) {
+    uint64_t ref = 0;
+    for (int p = 0; p < na; ++p) ref |= 1ull << (2 * p);
+    for (int p = 0; p < nb; ++p) ref |= 1ull << (2 * p + 1);
+    zref |= (__builtin_popcountll(ref & v.zmask[j]) & 1) << j;
+  }
+  IsPhysTable ip(N, na + nb, na - nb, nz, v.zmask, zref);
+  H->mask_host.assign(size_t(n) * (na + 1) * (nb + 1) * Z, 0);
+  for (int p = 0; p < n; ++p)
+    for (int a = 0; a <= na; ++a)
+      for (int b = 0; b <= nb; ++b)
+        for (int z = 0; z < Z; ++z) {
+          if (a > p || b > p) continue;
+          if (!ip(2 * p + 1, a + b, a - b, z)) continue;
+          uint8_t m = 0;
+          for (int u = 0; u < 4; ++u) {
+            const int da = u & 1, db = u >> 1;
+            const int z2 = z ^ (da ? ip.flip(2 * p + 1) : 0) ^ (db ? ip.flip(2 * p + 2) : 0);
+            if (ip(2 * p + 3, a + b + da + db, a - b + da - db, z2)) m |= uint8_t(1u << u);
+          }
+          H->mask_host[mask_index(v, p, a, b, z)] = m;
+        }
+  // forward counts of the (a, b, z) states over slot levels
+  std::vector<uint64_t> cur(size_t(na + 1) * (nb + 1) * Z, 0), nxt;
+  auto at = [&](int a, int b, int z) { return (size_t(a) * (nb + 1) + b) * Z + z; };
+  cur[at(0, 0, 0)] = 1;
+  H->phys_prefix.assign(n + 1, 0);
+  for (int p = 0; p <= n; ++p) {
+    uint64_t c = 0;
+    for (int a = 0; a <= na; ++a)
+      for (int b = 0; b <= nb; ++b)
+        for (int z = 0; z < Z; ++z)
+          if (cur[at(a, b, z)] && ip(2 * p + 1, a + b, a - b, z)) c = sat_add(c, cur[at(a, b, z)]);
+    H->phys_prefix[p] = c;
+    if (p == n) break;
+    nxt.assign(cur.size(), 0);
+    for (int a = 0; a <= na; ++a)
+      for (int b = 0; b <= nb; ++b)
+        for (int z = 0; z < Z; ++z) {
+          const uint64_t w = cur[at(a, b, z)];
+          if (!w) continue;
+          for (int u = 0; u < 4; ++u) {
+            const int a2 = a + (u & 1), b2 = b + (u >> 1);
+            if (a2 > na || b2 > nb) continue;
+            const int z2 = z ^ ((u & 1) ? ip.flip(2 * p + 1) : 0) ^ ((u >> 1) ? ip.flip(2 * p + 2) : 0);
+            nxt[at(a2, b2, z2)] = sat_add(nxt[at(a2, b2, z2)], w);
+          }
+        }
+    cur.swap(nxt);
+  }
+  H->sector_dim = H->phys_prefix[n];
+  if (H->sector_dim == 0) return set_error(ANQS_ERR_SECTOR, "empty sector");
+  return ANQS_OK;
+}
+
 extern "C" {
 
 const char* anqs_version(void) { return "anqs 0.1 (sm_103a)"; }
@@ -177,35 +248,11 @@ int anqs_hamiltonian_create(anqs_ham** out, int n, int na, int nb, const double*
   v.ndab = uint32_t(ndab);
   v.K = uint32_t(K);
   v.e_nuc = e_nuc;
-  H->sector_dim = sat_mul(binom(n, na), binom(n, nb));
-
-  // slot masks from the qubit-level IsPhys
-  IsPhysTable ip(2 * n, na + nb, na - nb);
-  H->mask_host.assign(size_t(n) * (na + 1) * (nb + 1), 0);
-  for (int p = 0; p < n; ++p)
-    for (int a = 0; a <= na; ++a)
-      for (int b = 0; b <= nb; ++b) {
-        if (a > p || b > p) continue;
-        if (!ip(2 * p + 1, a + b, a - b)) continue;
-        uint8_t m = 0;
-        for (int u = 0; u < 4; ++u) {
-          int da = u & 1, db = u >> 1;
-          if (ip(2 * p + 3, a + b + da + db, a - b + da - db)) m |= uint8_t(1u << u);
-        }
-        H->mask_host[mask_index(v, p, a, b)] = m;
-      }
-  // physical prefixes per level (bounds the sampler's frontier)
-  H->phys_prefix.assign(n + 1, 0);
-  for (int p = 0; p <= n; ++p) {
-    uint64_t c = 0;
-    for (int a = 0; a <= std::min(p, na); ++a)
-      for (int b = 0; b <= std::min(p, nb); ++b)
-        if (ip(2 * p + 1, a + b, a - b)) c = sat_add(c, sat_mul(binom(p, a), binom(p, b)));
-    H->phys_prefix[p] = c;
-  }
-  if (H->phys_prefix[n] == 0) {
+  v.mu_lv = n;
+  v.nz = 0;
+  if (build_sector(H) != ANQS_OK) {
     delete H;
-    return set_error(ANQS_ERR_SECTOR, "empty sector");
+    return ANQS_ERR_SECTOR;
   }
 
   size_t hn = size_t(n) * n, gn = hn * hn;
@@ -224,6 +271,38 @@ int anqs_hamiltonian_create(anqs_ham** out, int n, int na, int nb, const double*
   v.mask = H->d_mask;
   v.mu_lv = n;
   *out = H;
+  return ANQS_OK;
+}
+
+int anqs_hamiltonian_set_z2(anqs_ham* H, int nz, const uint64_t* qubit_masks) {
+  if (!H) return set_error(ANQS_ERR_ARG, "null Hamiltonian");
+  if (nz < 0 || nz > 4) return set_error(ANQS_ERR_ARG, "nz %d outside 0..4", nz);
+  if (nz && !qubit_masks) return set_error(ANQS_ERR_ARG, "null qubit masks");
+  const int n = H->v.n;
+  const uint64_t all = n >= 32 ? ~0ull : ((1ull << (2 * n)) - 1ull);
+  for (int j = 0; j < nz; ++j)
+    if (qubit_masks[j] & ~all) return set_error(ANQS_ERR_ARG, "Z2 mask %d reaches beyond qubit %d", j, 2 * n - 1);
+  ANQS_TRY(check_stream_device(H->device));
+  anqs_ham saved = *H;
+  H->v.nz = nz;
+  for (int j = 0; j < 4; ++j) H->v.zmask[j] = j < nz ? qubit_masks[j] : 0ull;
+  if (build_sector(H) != ANQS_OK) {
+    const int code = g_code;
+    std::string msg = g_msg;
+    H->v = saved.v;
+    H->mask_host = saved.mask_host;
+    H->phys_prefix = saved.phys_prefix;
+    H->sector_dim = saved.sector_dim;
+    set_error(code, "%s", msg.c_str());
+    return code;
+  }
+  uint8_t* d = nullptr;
+  ANQS_CUDA(cudaDeviceSynchronize());  // earlier work may still read the old table
+  ANQS_CUDA(cudaMalloc(&d, H->mask_host.size()));
+  ANQS_CUDA(cudaMemcpy(d, H->mask_host.data(), H->mask_host.size(), cudaMemcpyHostToDevice));
+  cudaFree(H->d_mask);
+  H->d_mask = d;
+  H->v.mask = d;
   return ANQS_OK;
 }
 

@@ -123,18 +123,28 @@ struct HamView {
   const double* g;     // [n][n][n][n] chemist notation
   const uint8_t* mask; // [n][na+1][nb+1] allowed-outcome bits per slot and prefix counts
   int mu_lv;           // slots p < mu_lv are masked (MU), slots p >= mu_lv discard (DU): MU-d, d = n - mu_lv
+  int nz;              // Z2 symmetries (Pauli-Z strings commuting with H), 0..ANQS_MAX_Z2
+  uint64_t zmask[4];   // their qubit supports (bit q = qubit q)
 };
 
-__host__ __device__ inline int mask_index(const HamView& hv, int p, int a, int b) {
-  return (p * (hv.na + 1) + a) * (hv.nb + 1) + b;
+// slot mask table entry of (slot p, a alpha and b beta electrons, Z2 parity
+// bits z of the prefix)
+__host__ __device__ inline int mask_index(const HamView& hv, int p, int a, int b, int z = 0) {
+  return ((p * (hv.na + 1) + a) * (hv.nb + 1) + b) * (1 << hv.nz) + z;
 }
 
 #ifdef __CUDACC__
-// Allowed-outcome bits of slot p after a prefix with a alpha and b beta
-// electrons (0 if the counts already leave the sector).
-__device__ __forceinline__ unsigned slot_mask(const HamView& hv, int p, int a, int b) {
+// Allowed-outcome bits of slot p after the prefix (slots < p) of x holding a
+// alpha and b beta electrons (0 if the counts already leave the sector); the
+// Z2 parities of the prefix select the entry when Z2 symmetries are set.
+__device__ __forceinline__ unsigned slot_mask(const HamView& hv, int p, int a, int b, uint64_t x) {
   if (a > hv.na || b > hv.nb) return 0u;
-  return hv.mask[mask_index(hv, p, a, b)];
+  int z = 0;
+  if (hv.nz) {
+    const uint64_t pm = p >= 32 ? ~0ull : ((1ull << (2 * p)) - 1ull);
+    for (int j = 0; j < hv.nz; ++j) z |= (__popcll(x & pm & hv.zmask[j]) & 1) << j;
+  }
+  return hv.mask[mask_index(hv, p, a, b, z)];
 }
 
 // Outcomes over which slot p's conditional is normalised (Sec. III.C): the

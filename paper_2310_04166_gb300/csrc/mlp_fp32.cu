@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(NT) logpsi_kernel(MlpView m, HamView hv, const
       if (threadIdx.x < nrows) {
         int r = threadIdx.x;
         int v = int((xt[r] >> (2 * p)) & 3ull);
-        unsigned mk = slot_mask(hv, p, ca[r], cb[r]);
+        unsigned mk = slot_mask(hv, p, ca[r], cb[r], xt[r]);
         bool dd = dead[r];
         slot_term(out8 + r * 8, norm_mask(hv, p, mk), mk, v, la[r], ph[r], dd);
         dead[r] = dd;
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
         a += vq & 1;
         b += vq >> 1;
       }
-      const unsigned pm = slot_mask(hv, p, a, b), mk = norm_mask(hv, p, pm);
+      const unsigned pm = slot_mask(hv, p, a, b, x), mk = norm_mask(hv, p, pm);
       int v = int((x >> (2 * p)) & 3ull);
       if ((pm >> v) & 1u) {
         const float* o8 = out8 + r * 8;

@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_ws_kernel(TcView tv, HamView hv,
         const uint64_t pm = (1ull << (2 * p)) - 1ull;
         const int a = __popcll(x & pm & 0x5555555555555555ull);
         const int bb = __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull);
-        const unsigned pmk = slot_mask(hv, p, a, bb), mk = norm_mask(hv, p, pmk);
+        const unsigned pmk = slot_mask(hv, p, a, bb, x), mk = norm_mask(hv, p, pmk);
         float mx = -INFINITY;
 #pragma unroll
         for (int u = 0; u < 4; ++u)
@@ -549,7 +549,7 @@ __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Cou
     int a = 0, b = 0;
     for (int p = 0; p < n; ++p) {
       const float* o = raw + (l * n + p) * 8;
-      const unsigned pmk = slot_mask(hv, p, a, b), mk = norm_mask(hv, p, pmk);
+      const unsigned pmk = slot_mask(hv, p, a, b, x), mk = norm_mask(hv, p, pmk);
       float mx = -INFINITY;
       for (int u = 0; u < 4; ++u)
         if ((mk >> u) & 1u) mx = fmaxf(mx, o[u]);

@@ -137,7 +137,7 @@ __global__ void prep_kernel(HamView hv, int p, const uint64_t* __restrict__ pre,
   const uint64_t nf = *n_front;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < nf; i += uint64_t(gridDim.x) * blockDim.x) {
     uint64_t x = pre[i];
-    const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p)), mk = norm_mask(hv, p, pm);
+    const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p), x), mk = norm_mask(hv, p, pm);
     uint64_t T[4];
     split_thresholds(logits + i * 8, mk, T);
     for (int v = 0; v < 4; ++v) {
@@ -395,7 +395,7 @@ __global__ void binom_kernel(HamView hv, int p, uint64_t seed, uint64_t counter0
   const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < nf; i += uint64_t(gridDim.x) * blockDim.x) {
     const uint64_t x = pre[i];
-    const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p)), mk = norm_mask(hv, p, pm);
+    const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p), x), mk = norm_mask(hv, p, pm);
     const float* l = logits + i * 8;
     float m = -INFINITY;
     for (int v = 0; v < 4; ++v)
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
       const int i = n_lo + threadIdx.x;
       for (int v = 0; v < 4; ++v) s_cnt[threadIdx.x][v] = 0;
       const uint64_t x = pre[i];
-      const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p)), mk = norm_mask(hv, p, pm);
+      const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p), x), mk = norm_mask(hv, p, pm);
       split_thresholds(logits + uint64_t(i) * 8, mk, s_thr[threadIdx.x]);
       s_mk[threadIdx.x] = uint8_t(mk | (pm << 4));
     }

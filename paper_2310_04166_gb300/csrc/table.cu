@@ -28,7 +28,7 @@ __global__ void table_logpsi_kernel(const float* __restrict__ params, int n, Ham
     for (int p = 0; p < n && !dead; ++p) {
       const float* o8 = table_row(params, p, x);
       int v = int((x >> (2 * p)) & 3ull);
-      const unsigned pm = slot_mask(hv, p, a, b), mk = norm_mask(hv, p, pm);
+      const unsigned pm = slot_mask(hv, p, a, b, x), mk = norm_mask(hv, p, pm);
       if (!((pm >> v) & 1u)) {
         dead = true;
         break;

@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(NT, 1) tf_logpsi_kernel(TfView m, HamView hv, 
       int ca = 0, cb = 0;
       for (int p = 0; p < T; ++p) {
         const int v = int((x >> (2 * p)) & 3ull);
-        const unsigned pm = slot_mask(hv, p, ca, cb);
+        const unsigned pm = slot_mask(hv, p, ca, cb, x);
         slot_term(out8 + (s * T + p) * 8, norm_mask(hv, p, pm), pm, v, la, ph, dead);
         ca += v & 1;
         cb += v >> 1;

@@ -354,14 +354,14 @@ __global__ void head_dout_kernel(HamView hv, const uint64_t* __restrict__ x, Cou
     int ca = 0, cb = 0;
     for (int p = 0; p < n; ++p) {
       const int v = int((xs >> (2 * p)) & 3ull);
-      if (!((slot_mask(hv, p, ca, cb) >> v) & 1u)) dead = true;
+      if (!((slot_mask(hv, p, ca, cb, xs) >> v) & 1u)) dead = true;
       ca += v & 1;
       cb += v >> 1;
     }
     ca = cb = 0;
     for (int p = 0; p < n; ++p) {
       const int v = int((xs >> (2 * p)) & 3ull);
-      const unsigned mk = norm_mask(hv, p, slot_mask(hv, p, ca, cb));
+      const unsigned mk = norm_mask(hv, p, slot_mask(hv, p, ca, cb, xs));
       const float* o = out8 + (s * n + p) * 8;
       float* d = dout8 + (s * n + p) * 8;
       float mx = -INFINITY;

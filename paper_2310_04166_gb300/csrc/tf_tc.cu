@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
         } else {
           const uint64_t pm = (1ull << (2 * pos)) - 1ull;
           const unsigned pmk = slot_mask(a.hv, pos, __popcll(x & pm & 0x5555555555555555ull),
-                                         __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull));
+                                         __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull), x);
           const unsigned mk = norm_mask(a.hv, pos, pmk);
           float mx = -INFINITY;
 #pragma unroll

@@ -58,6 +58,43 @@ def integrals(seed: int, n: int, n_chol: int, rng: np.random.Generator | None = 
     return h, g, 0.0
 
 
+def integrals_z2(seed: int, n: int, n_chol: int, labels):
+    """Integrals with planted abelian point-group symmetry: orbital p carries
+    the irrep label labels[p] in [0, 2^k) (irrep product = XOR).  Drawn as
+    `integrals`, then h_pq is kept only within one irrep and each Cholesky
+    factor B^L, of irrep L mod 2^k, only where labels[p] ^ labels[q] equals
+    it, so that g_pqrs vanishes unless the four labels XOR to zero.  Under the
+    Jordan-Wigner transform every bit j of the labels gives a Z2 symmetry:
+    the Pauli-Z string on both spin-qubits of the orbitals with bit j set
+    (`z2_qubit_masks`)."""
+    labels = np.asarray(labels, dtype=np.int64)
+    k = max(1, int(labels.max()).bit_length())
+    rng = np.random.default_rng(seed)
+    h = np.zeros((n, n))
+    h[np.diag_indices(n)] = np.linspace(-2.0, 1.0, n)
+    iu = np.triu_indices(n, 1)
+    h[iu] = rng.normal(0.0, 0.05, size=len(iu[0]))
+    h[(iu[1], iu[0])] = h[iu]
+    h[labels[:, None] != labels[None, :]] = 0.0
+    iu0 = np.triu_indices(n, 0)
+    g = np.zeros((n, n, n, n))
+    for L in range(n_chol):
+        B = np.zeros((n, n))
+        B[iu0] = rng.normal(0.0, 0.1, size=len(iu0[0]))
+        B[(iu0[1], iu0[0])] = B[iu0]
+        B[(labels[:, None] ^ labels[None, :]) != (L % (1 << k))] = 0.0
+        g += np.einsum("pq,rs->pqrs", B, B)
+    return h, g, 0.0
+
+
+def z2_qubit_masks(labels):
+    """Qubit supports of the Z2 symmetries of `integrals_z2` (bit q = qubit
+    q = 2p + sigma): one per bit of the irrep labels."""
+    labels = [int(v) for v in labels]
+    k = max(1, max(labels).bit_length())
+    return [sum(3 << (2 * p) for p, v in enumerate(labels) if (v >> j) & 1) for j in range(k)]
+
+
 # ----------------------------------------------------------------------------
 # network parameters
 # ----------------------------------------------------------------------------
