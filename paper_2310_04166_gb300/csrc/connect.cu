@@ -44,15 +44,15 @@ __device__ __forceinline__ double G(const HamView& hv, int p, int q, int r, int 
   return __ldg(hv.g + ((size_t(p) * n + q) * n + r) * n + s);
 }
 
-__global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x,
-                                 uint64_t* __restrict__ xp_out, double* __restrict__ h_out,
-                                 uint8_t* __restrict__ j_out) {
-  ANQS_PDL_ENTRY();
+// blocks bid = 0..nb-1 of a grid-stride loop over the (sample, excitation)
+// pairs
+__device__ __forceinline__ void connected_body(const HamView& hv, const uint64_t* __restrict__ xs, Count n_x,
+                                               uint64_t* __restrict__ xp_out, double* __restrict__ h_out,
+                                               uint8_t* __restrict__ j_out, uint64_t bid, uint64_t nb) {
   const uint64_t K = hv.K;
   const uint64_t total = n_x.get() * K;
   const int n = hv.n;
-  for (uint64_t t = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; t < total;
-       t += uint64_t(gridDim.x) * blockDim.x) {
+  for (uint64_t t = bid * blockDim.x + threadIdx.x; t < total; t += nb * blockDim.x) {
     uint64_t l = t / K;
     uint32_t k = uint32_t(t - l * K);
     uint64_t x = __ldg(xs + l);
@@ -154,17 +154,24 @@ __global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, Co
   }
 }
 
+__global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x,
+                                 uint64_t* __restrict__ xp_out, double* __restrict__ h_out,
+                                 uint8_t* __restrict__ j_out) {
+  ANQS_PDL_ENTRY();
+  connected_body(hv, xs, n_x, xp_out, h_out, j_out, blockIdx.x, gridDim.x);
+}
+
 // <x|H|x> = E_nuc + sum_I h_ii + 1/2 sum_{I,J occ} ([II|JJ] - [IJ|JI]).
 // One warp per determinant: lane i takes the occupied spin-orbital pairs
 // (I, J) with I*N_occ + J = i mod 32, then the FP64 partial sums are reduced.
-__global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x_,
-                                double* __restrict__ hdiag) {
-  ANQS_PDL_ENTRY();
+// one warp per sample, blocks bid = 0..nb-1
+__device__ __forceinline__ void diagonal_body(const HamView& hv, const uint64_t* __restrict__ xs, Count n_x_,
+                                              double* __restrict__ hdiag, uint64_t bid, uint64_t nb) {
   const int n = hv.n;
   const uint64_t n_x = n_x_.get();
   const int lane = threadIdx.x & 31;
-  const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
-  for (uint64_t l = blockIdx.x * uint64_t(blockDim.x >> 5) + (threadIdx.x >> 5); l < n_x; l += warps) {
+  const uint64_t warps = nb * (blockDim.x >> 5);
+  for (uint64_t l = bid * (blockDim.x >> 5) + (threadIdx.x >> 5); l < n_x; l += warps) {
     const uint64_t x = __ldg(xs + l);
     const uint32_t oa = spin_occ(x, 0, n), ob = spin_occ(x, 1, n);
     const bool ok = (__popc(oa) == hv.na) && (__popc(ob) == hv.nb) && (n == 32 || (x >> (2 * n)) == 0);
@@ -194,12 +201,35 @@ __global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, Cou
   }
 }
 
+__global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x, double* __restrict__ hdiag) {
+  ANQS_PDL_ENTRY();
+  diagonal_body(hv, xs, n_x, hdiag, blockIdx.x, gridDim.x);
+}
+
+// the connected set on blocks [0, nb_c) and the diagonal on the rest, in one
+// launch
+__global__ void connected_diag_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x,
+                                      uint64_t* __restrict__ xp_out, double* __restrict__ h_out,
+                                      uint8_t* __restrict__ j_out, double* __restrict__ hdiag, unsigned nb_c) {
+  ANQS_PDL_ENTRY();
+  if (blockIdx.x < nb_c) connected_body(hv, xs, n_x, xp_out, h_out, j_out, blockIdx.x, nb_c);
+  else diagonal_body(hv, xs, n_x, hdiag, blockIdx.x - nb_c, gridDim.x - nb_c);
+}
+
 }  // namespace
 
 int launch_connected(const HamView& hv, const uint64_t* x, Count n_x, uint64_t* xp, double* hval,
                      uint8_t* first_slot, double* hdiag, cudaStream_t s) {
   const int threads = 256;
   uint64_t total = n_x.n * hv.K;
+  if (total && hdiag) {
+    uint64_t bc = (total + threads - 1) / threads, bd = (n_x.n + 7) / 8;
+    if (bc > 152ull * 64) bc = 152ull * 64;
+    if (bd > 152ull * 16) bd = 152ull * 16;
+    ProfScope ps(PROF_CONNECT, s);
+    ANQS_CUDA_LAUNCH("connected_diag_kernel", launch_k(connected_diag_kernel, dim3(unsigned(bc + bd)), dim3(threads), 0, s, hv, x, n_x, xp, hval, first_slot, hdiag, unsigned(bc)));
+    return ANQS_OK;
+  }
   if (total) {
     uint64_t blocks = (total + threads - 1) / threads;
     if (blocks > 152ull * 64) blocks = 152ull * 64;

@@ -20,7 +20,8 @@ namespace anqs {
 namespace {
 
 constexpr int R = 32;    // rows per CTA tile (log psi and slot logits)
-constexpr int RG = 16;   // rows per CTA tile of the adjoint (more CTAs for few samples)
+// rows per CTA tile of the adjoint: the smallest of 16, 24, 32 whose tiles fit
+// in one wave of CTAs (rg_for)
 constexpr int NT = 256;  // threads per CTA
 constexpr int KC = 32;   // weight chunk depth
 
@@ -44,16 +45,36 @@ __device__ __forceinline__ MlpPtr slot_ptrs(const MlpView& m, int p) {
 }
 
 // out[r][c] = sum_k in[r][k] * B(k, c), B(k, c) = W[c][k] (forward) or W[k][c]
-// (adjoint).  Each warp owns R/8 rows, each lane W/32 columns.
+// (adjoint).  Each warp owns R/8 rows, each lane W/32 columns.  With wres
+// the matrix is already resident in shared memory (row stride W + 1, so
+// that both access patterns are free of bank conflicts) and no chunk is
+// staged; otherwise 32-row chunks of W stream through ws.
 template <int W, bool ADJ, int RR = R>
 __device__ __forceinline__ void tile_gemm(const float* in, const float* __restrict__ Wg, float* ws,
-                                          float (&acc)[RR / 8][W / 32]) {
+                                          float (&acc)[RR / 8][W / 32], const float* wres = nullptr) {
   constexpr int RPT = RR / 8, CPT = W / 32;
   const int lane = threadIdx.x & 31, wg = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < RPT; ++i)
 #pragma unroll
     for (int j = 0; j < CPT; ++j) acc[i][j] = 0.f;
+  if (wres) {
+    __syncthreads();  // `in` was written by other threads
+#pragma unroll 4
+    for (int k = 0; k < W; ++k) {
+      float a[RPT], b[CPT];
+#pragma unroll
+      for (int i = 0; i < RPT; ++i) a[i] = in[(wg * RPT + i) * W + k];
+#pragma unroll
+      for (int j = 0; j < CPT; ++j)
+        b[j] = ADJ ? wres[k * (W + 1) + lane + 32 * j] : wres[(lane + 32 * j) * (W + 1) + k];
+#pragma unroll
+      for (int i = 0; i < RPT; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    return;
+  }
   for (int k0 = 0; k0 < W; k0 += KC) {
     __syncthreads();
     for (int idx = threadIdx.x; idx < KC * W; idx += NT) {
@@ -99,7 +120,7 @@ struct Smem {
 // outputs in out8[R][8] and returns the index of the last hidden buffer.
 template <int W, int RR = R>
 __device__ int slot_forward(const MlpView& m, int p, const uint64_t* xs, int nrows, float* act, int n_keep,
-                            float* ws, float* out8) {
+                            float* ws, float* out8, const float* wres = nullptr) {
   const MlpPtr P = slot_ptrs(m, p);
   for (int idx = threadIdx.x; idx < RR * W; idx += NT) {
     int r = idx / W, o = idx % W;
@@ -118,7 +139,8 @@ __device__ int slot_forward(const MlpView& m, int p, const uint64_t* xs, int nro
   for (int k = 2; k <= m.n_hidden; ++k) {
     const float* bk = Wk + size_t(W) * W;
     float acc[RPT][CPT];
-    tile_gemm<W, false, RR>(act + size_t(cur) * RR * W, Wk, ws, acc);
+    tile_gemm<W, false, RR>(act + size_t(cur) * RR * W, Wk, ws, acc,
+                            wres ? wres + size_t(k - 2) * W * (W + 1) : nullptr);
     int nxt = (n_keep == 2) ? (cur ^ 1) : (cur + 1);
     float* o = act + size_t(nxt) * RR * W;
 #pragma unroll
@@ -301,7 +323,7 @@ __device__ __forceinline__ void outer_accumulate(const float* dz, const float* h
   }
 }
 
-template <int W, bool PARTIAL>
+template <int W, int RG, bool PARTIAL, bool RESIDENT>
 __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const uint64_t* __restrict__ xs,
                                                   Count n_x_, const float* __restrict__ cot_la,
                                                   const float* __restrict__ cot_ph, float* __restrict__ grad,
@@ -327,7 +349,17 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
     cp[threadIdx.x] = ok ? cot_ph[base + threadIdx.x] : 0.f;
   }
   __syncthreads();
-  const int last = slot_forward<W, RG>(m, p, xt, nrows, act, L, ws, out8);
+  // hidden matrices of slot p resident in shared memory (row stride W + 1)
+  float* wres = RESIDENT ? dh + RG * W : nullptr;
+  if (RESIDENT) {
+    const MlpPtr Pw = slot_ptrs(m, p);
+    for (int l = 0; l < L - 1; ++l) {
+      const float* src = Pw.Wk + size_t(l) * (size_t(W) * W + W);
+      float* dst = wres + size_t(l) * W * (W + 1);
+      for (int idx = threadIdx.x; idx < W * W; idx += NT) dst[(idx / W) * (W + 1) + idx % W] = __ldg(src + idx);
+    }
+  }
+  const int last = slot_forward<W, RG>(m, p, xt, nrows, act, L, ws, out8, wres);
   const MlpPtr P = slot_ptrs(m, p);
   float* gbase = grad + (P.W1 - m.params) + (PARTIAL ? uint64_t(blockIdx.x) * n_params : 0ull);
   // d out: d l_u = cot_la * 1/2 (delta_uv - p~_u) over allowed u, d phi_u = cot_ph delta_uv
@@ -402,7 +434,7 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
       gacc<W, PARTIAL>(gb + o, s);
     }
     float acc[RPT][CPT];
-    tile_gemm<W, true, RG>(dh, Wk, ws, acc);  // dh_{k-1} = W_k^T dz_k
+    tile_gemm<W, true, RG>(dh, Wk, ws, acc, RESIDENT ? wres + size_t(k - 2) * W * (W + 1) : nullptr);  // W_k^T dz_k
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < RPT; ++i)
@@ -433,16 +465,24 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
 }
 
 // grad[i] = sum over the tiles of the per-tile copies (only tiles holding rows)
-__global__ void partial_sum_kernel(const float* __restrict__ part, Count n_x_, uint64_t n_params,
+__global__ void partial_sum_kernel(const float* __restrict__ part, Count n_x_, uint64_t n_params, int rg,
                                    float* __restrict__ grad) {
   ANQS_PDL_ENTRY();
-  const uint64_t tiles = (n_x_.get() + RG - 1) / RG;
+  const uint64_t tiles = (n_x_.get() + rg - 1) / rg;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n_params;
        i += uint64_t(gridDim.x) * blockDim.x) {
     float s = 0.f;
     for (uint64_t t = 0; t < tiles; ++t) s += part[t * n_params + i];
     grad[i] = s;
   }
+}
+
+// the smallest tile height (16, 24 or 32 rows) whose tiles of all slots fit
+// in one wave of (one per SM) CTAs, else 32
+int rg_for(const MlpView& m, uint64_t n_x) {
+  for (int rg : {16, 24})
+    if (((n_x + rg - 1) / rg) * uint64_t(m.n) <= 152) return rg;
+  return 32;
 }
 
 template <class F>
@@ -473,31 +513,51 @@ int logits_w(const MlpView& m, int p, const uint64_t* pre, const uint64_t* nr, u
   return ANQS_OK;
 }
 
-template <int W>
-int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
-           const float* cp, float* g, float* part, uint64_t n_params, cudaStream_t s) {
-  size_t sm = Smem<W, RG>::bytes(m.n_hidden + 1);
-  if (sm > 227 * 1024)
-    return set_error(ANQS_ERR_UNSUPPORTED, "FP32 MLP adjoint needs %zu bytes of shared memory", sm);
+template <int W, int RG, bool RES>
+int grad_launch(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
+                const float* cp, float* g, float* part, uint64_t n_params, size_t sm, cudaStream_t s) {
   dim3 grid(unsigned(std::max<uint64_t>((n_x.n + RG - 1) / RG, 1)), unsigned(m.n));
   if (part) {
-    ANQS_TRY(set_smem(grad_kernel<W, true>, sm));
+    ANQS_TRY(set_smem(grad_kernel<W, RG, true, RES>, sm));
     {
       ProfScope ps(PROF_MLP_FP32_GRAD, s);
-      ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, true>, dim3(grid), dim3(NT), sm, s, m, hv, x, n_x,
-                                                   cl, cp, part, n_params));
+      ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, RG, true, RES>, dim3(grid), dim3(NT), sm, s, m, hv,
+                                                   x, n_x, cl, cp, part, n_params));
     }
     ProfScope ps(PROF_GRAD_REDUCE, s);
     ANQS_CUDA_LAUNCH("mlp partial_sum_kernel",
                      launch_k(partial_sum_kernel, dim3(unsigned(std::min<uint64_t>((n_params + 255) / 256, 152 * 8))),
-                              dim3(256), 0, s, part, n_x, n_params, g));
+                              dim3(256), 0, s, part, n_x, n_params, RG, g));
   } else {
-    ANQS_TRY(set_smem(grad_kernel<W, false>, sm));
+    ANQS_TRY(set_smem(grad_kernel<W, RG, false, RES>, sm));
     ProfScope ps(PROF_MLP_FP32_GRAD, s);
-    ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, false>, dim3(grid), dim3(NT), sm, s, m, hv, x, n_x, cl,
-                                                 cp, g, n_params));
+    ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, RG, false, RES>, dim3(grid), dim3(NT), sm, s, m, hv,
+                                                 x, n_x, cl, cp, g, n_params));
   }
   return ANQS_OK;
+}
+
+// The slot's hidden matrices stay in shared memory when they fit next to the
+// activations (widths 64 and 128); otherwise they stream in chunks.
+template <int W, int RG>
+int grad_rg(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
+            const float* cp, float* g, float* part, uint64_t n_params, cudaStream_t s) {
+  const size_t sm = Smem<W, RG>::bytes(m.n_hidden + 1);
+  const size_t res = sm + size_t(m.n_hidden - 1) * W * (W + 1) * sizeof(float);
+  if (res <= 227 * 1024) return grad_launch<W, RG, true>(m, hv, x, n_x, cl, cp, g, part, n_params, res, s);
+  if (sm > 227 * 1024)
+    return set_error(ANQS_ERR_UNSUPPORTED, "FP32 MLP adjoint needs %zu bytes of shared memory", sm);
+  return grad_launch<W, RG, false>(m, hv, x, n_x, cl, cp, g, part, n_params, sm, s);
+}
+
+template <int W>
+int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
+           const float* cp, float* g, float* part, uint64_t n_params, cudaStream_t s) {
+  switch (rg_for(m, n_x.n)) {
+    case 16: return grad_rg<W, 16>(m, hv, x, n_x, cl, cp, g, part, n_params, s);
+    case 24: return grad_rg<W, 24>(m, hv, x, n_x, cl, cp, g, part, n_params, s);
+  }
+  return grad_rg<W, 32>(m, hv, x, n_x, cl, cp, g, part, n_params, s);
 }
 
 }  // namespace
@@ -523,12 +583,13 @@ int launch_mlp_fp32_slot_logits(const MlpView& m, int p, const uint64_t* pre, co
 }
 
 size_t mlp_fp32_grad_partial_floats(const MlpView& m, uint64_t n_x) {
-  return size_t((n_x + RG - 1) / RG) * m.slot_off[m.n];
+  const int rg = rg_for(m, n_x);
+  return size_t((n_x + rg - 1) / rg) * m.slot_off[m.n];
 }
 
 int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
                          const float* cp, float* g, float* part, cudaStream_t s) {
-  if ((n_x.n + RG - 1) / RG > 0x7fffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "too many rows");
+  if ((n_x.n + 15) / 16 > 0x7fffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "too many rows");
   const uint64_t np = m.slot_off[m.n];
   switch (m.width) {
     case 64: return grad_w<64>(m, hv, x, n_x, cl, cp, g, part, np, s);

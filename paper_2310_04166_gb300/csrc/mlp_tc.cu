@@ -148,6 +148,7 @@ struct TileArgs {
   Count rows;
   int p_lo, p_hi;              // SLOTS: slots [p_lo, p_hi)
   float* raw;                  // SLOTS output [row][p_hi - p_lo][8]
+  int tpi;                     // SLOTS: 128-row tiles per work item (1..NWG; warpgroups >= tpi idle)
 };
 
 constexpr int NWG = kNwg;     // warpgroups per CTA, one 128-row tile each in flight
@@ -352,7 +353,8 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
   ANQS_PDL_WAIT();
   ANQS_PDL_TRIGGER();
   const uint64_t n_rows = ta.rows.get();
-  const uint64_t n_groups = (n_rows + NWG * MT - 1) / (NWG * MT);
+  const int tpi = ta.tpi;
+  const uint64_t n_groups = (n_rows + uint64_t(tpi) * MT - 1) / (uint64_t(tpi) * MT);
   const uint64_t n_items = n_groups * uint64_t(np);
   for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int p = ta.p_lo + int(it / n_groups);
@@ -363,8 +365,8 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
       loaded = p;
       pending = true;
     }
-    const uint64_t r = (grp * NWG + wg) * MT + t;
-    const bool valid = r < n_rows;
+    const uint64_t r = (grp * tpi + wg) * MT + t;
+    const bool valid = wg < tpi && r < n_rows;
     const uint64_t x = valid ? ta.x[r] : 0ull;
     bool ok = true;
     if (pending) {
@@ -373,7 +375,8 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
       pending = false;
     }
     float out[8];
-    if (ok && (grp * NWG + wg) * MT < n_rows) ok = tile_slot<W>(c, ph_m, p, x, S, tc::smem_u32(s_img), s_img, out);
+    if (ok && wg < tpi && (grp * tpi + wg) * MT < n_rows)
+      ok = tile_slot<W>(c, ph_m, p, x, S, tc::smem_u32(s_img), s_img, out);
     if (!ok) s_abort = 1;
     if (ok && valid) {
       float4* dst = reinterpret_cast<float4*>(ta.raw + (r * np + (p - ta.p_lo)) * 8);
@@ -626,6 +629,44 @@ __global__ void js_scatter_kernel(const uint8_t* __restrict__ js, Count m_, uint
   }
 }
 
+// All three steps in one CTA for up to JS_SMALL rows: histogram in shared
+// memory, offsets (offsets[n] = rows), scatter with warp-aggregated shared
+// atomics.
+constexpr uint64_t JS_SMALL = 8192;
+__global__ void __launch_bounds__(1024) js_sort_small_kernel(const uint8_t* __restrict__ js, Count m_, int n,
+                                                             uint32_t* __restrict__ offsets,
+                                                             uint32_t* __restrict__ perm) {
+  ANQS_PDL_ENTRY();
+  __shared__ uint32_t h[ANQS_MAX_ORB], cur[ANQS_MAX_ORB];
+  const uint64_t m = m_.get();
+  const int lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = 0;
+  __syncthreads();
+  for (uint64_t t = threadIdx.x; t < m; t += blockDim.x) atomicAdd(&h[js[t]], 1u);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t acc = 0;
+    for (int i = 0; i < n; ++i) {
+      cur[i] = acc;
+      offsets[i] = acc;
+      acc += h[i];
+    }
+    offsets[n] = acc;
+  }
+  __syncthreads();
+  for (uint64_t t0 = 0; t0 < m; t0 += blockDim.x) {
+    const uint64_t t = t0 + threadIdx.x;
+    const int key = t < m ? int(js[t]) : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int leader = __ffs(peers) - 1;
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    uint32_t base = 0;
+    if (lane == leader && key >= 0) base = atomicAdd(&cur[key], uint32_t(__popc(peers)));
+    base = __shfl_sync(peers, base, leader);
+    if (key >= 0) perm[base + rank] = uint32_t(t);
+  }
+}
+
 int g_num_sms = 0;
 
 int num_sms() {
@@ -663,12 +704,17 @@ template <int W>
 int launch_slots_w(const TcView& tv, const TileArgs& ta, cudaStream_t s) {
   const uint64_t max_rows = ta.rows.n;
   const size_t sm = smem_bytes(tv, 1);
-  const uint64_t items = (max_rows + NWG * MT - 1) / (NWG * MT) * uint64_t(ta.p_hi - ta.p_lo);
+  // one 128-row tile per CTA (its warpgroup alone on the SM) while the
+  // tiles of all slots fit in one wave, else NWG tiles per CTA
+  const uint64_t np = uint64_t(ta.p_hi - ta.p_lo), tiles = (max_rows + MT - 1) / MT;
+  TileArgs a = ta;
+  a.tpi = tiles * np <= uint64_t(num_sms()) ? 1 : NWG;
+  const uint64_t items = (max_rows + uint64_t(a.tpi) * MT - 1) / (uint64_t(a.tpi) * MT) * np;
   const unsigned grid = unsigned(std::min<uint64_t>(items ? items : 1, uint64_t(num_sms())));
   TcView v1 = tv;
   v1.nbuf = 1;
   ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_slots_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
-  ANQS_CUDA_LAUNCH("mlp_tc_slots_kernel", launch_k(mlp_tc_slots_kernel<W>, dim3(grid), dim3(NT), sm, s, v1, ta));
+  ANQS_CUDA_LAUNCH("mlp_tc_slots_kernel", launch_k(mlp_tc_slots_kernel<W>, dim3(grid), dim3(NT), sm, s, v1, a));
   return ANQS_OK;
 }
 
@@ -808,6 +854,10 @@ int launch_tc_finalize(const HamView& hv, const uint64_t* x, Count n_x, const fl
 
 int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* hist, uint32_t* cursor, uint32_t* offsets,
                    uint32_t* perm, cudaStream_t s) {
+  if (mc.n <= JS_SMALL) {
+    ANQS_CUDA_LAUNCH("js_sort_small_kernel", launch_k(js_sort_small_kernel, dim3(1), dim3(1024), 0, s, js, mc, n, offsets, perm));
+    return ANQS_OK;
+  }
   ANQS_CUDA(cudaMemsetAsync(hist, 0, ANQS_MAX_ORB * sizeof(uint32_t), s));
   const unsigned g = unsigned(std::min<uint64_t>((mc.n + 255) / 256, 152 * 4));
   ANQS_CUDA_LAUNCH("js_hist_kernel", launch_k(js_hist_kernel, dim3(g ? g : 1), dim3(256), 0, s, js, mc, n, hist));
@@ -856,11 +906,7 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count
   }
   {
     ProfScope ps(PROF_TC_SORT, s);
-    ANQS_CUDA(cudaMemsetAsync(w.hist, 0, ANQS_MAX_ORB * sizeof(uint32_t), s));
-    unsigned g = unsigned(std::min<uint64_t>((m + 255) / 256, 152 * 4));
-    ANQS_CUDA_LAUNCH("js_hist_kernel", launch_k(js_hist_kernel, dim3(g ? g : 1), dim3(256), 0, s, w.js, mc, H->v.n, w.hist));
-    ANQS_CUDA_LAUNCH("js_offsets_kernel", launch_k(js_offsets_kernel, dim3(1), dim3(32), 0, s, w.hist, H->v.n, w.cursor, w.offsets));
-    ANQS_CUDA_LAUNCH("js_scatter_kernel", launch_k(js_scatter_kernel, dim3(g ? g : 1), dim3(256), 0, s, w.js, mc, w.cursor, w.perm));
+    ANQS_TRY(launch_js_sort(w.js, mc, H->v.n, w.hist, w.cursor, w.offsets, w.perm, s));
   }
   {
     TcView tv = make_view(M);

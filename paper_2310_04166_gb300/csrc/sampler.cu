@@ -454,7 +454,7 @@ __global__ void scatter_kernel(int p, const uint64_t* __restrict__ pre, const ui
 // Everything after the network evaluation of a level in a single CTA of
 // SMALL_T threads: per-node running sums, scan of the draw blocks, draws with
 // warp-segment aggregation into shared counters, compaction of the children.
-constexpr int SMALL_T = 1024;
+constexpr int SMALL_T = 256;
 constexpr int SMALL_F = 2048;  // largest frontier handled this way
 constexpr size_t SMALL_DYN = size_t(SMALL_T) * 48;  // thresholds and window counts
 
