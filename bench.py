@@ -220,8 +220,9 @@ def _config(w, args):
 # DRAM bytes per launch from one ncu capture of the same kernel build and
 # workload (`ncu --set full -k regex:<kernel> -c 1 python bench.py
 # --kernel-case`, h2o, BF16 form): dram__bytes_read.sum + dram__bytes_write.sum
-TRAFFIC = {("h2o", "bf16"): {"mlp_fp32_grad_kernel": 1163776 + 135680, "mlp_tc_suffix_kernel": 1240064,
-                             "eloc_assemble_kernel": 4650240, "connected_kernel": 49920}}
+TRAFFIC = {("h2o", "bf16"): {"mlp_fp32_grad_kernel": 1093120 + 44032, "mlp_tc_suffix_kernel": 1280768 + 5888,
+                             "mlp_tc_parent_kernel": 591616, "eloc_assemble_kernel": 4650496,
+                             "connected_kernel": 64256}}
 
 
 def _make_model(A, w, params, form):
