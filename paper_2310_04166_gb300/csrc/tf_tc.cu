@@ -382,14 +382,16 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
           const uint4* kp;
           if (u < tl.t0) kp = reinterpret_cast<const uint4*>(pkv + size_t(u) * (2 * D));
           else kp = reinterpret_cast<const uint4*>(sKV + (row0 + u - tl.t0) * KV_STRIDE);
-          float sc = 0.f;
+          // score as two interleaved partial sums (packed f32x2 FMAs)
+          float s0 = 0.f, s1 = 0.f;
 #pragma unroll
           for (int e8 = 0; e8 < DH; e8 += 8) {
             float kf[8];
             bf16x8_to_f32(kp[(hd * DH + e8) / 8], kf);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) sc = fmaf(q[e8 + e], kf[e], sc);
+            for (int e = 0; e < 8; e += 2) tc::fma_f32x2(q[e8 + e], q[e8 + e + 1], kf[e], kf[e + 1], s0, s1, s0, s1);
           }
+          const float sc = s0 + s1;
           const float mn = fmaxf(m, sc);
           const float corr = __expf(m - mn), p = __expf(sc - mn);
           lsum = fmaf(lsum, corr, p);
@@ -398,7 +400,11 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
             float vf[8];
             bf16x8_to_f32(kp[(D + hd * DH + e8) / 8], vf);
 #pragma unroll
-            for (int e = 0; e < 8; ++e) acc[e8 + e] = fmaf(acc[e8 + e], corr, p * vf[e]);
+            for (int e = 0; e < 8; e += 2) {  // acc = acc corr + p v, two elements per instruction
+              float p0, p1;
+              tc::fma_f32x2(p, p, vf[e], vf[e + 1], 0.f, 0.f, p0, p1);
+              tc::fma_f32x2(acc[e8 + e], acc[e8 + e + 1], corr, corr, p0, p1, acc[e8 + e], acc[e8 + e + 1]);
+            }
           }
           m = mn;
         }
