@@ -14,8 +14,9 @@ modulus and keeps the phases of the allowed outcomes (the paper's binary
 example fixes the single allowed amplitude to 1; with ``forced_phase_zero`` a
 slot with exactly one allowed outcome gets phase 0 instead).
 
-Networks (readings, the paper's own ansatz is the per-qubit NADE of Appendix
-B.1):
+Networks (the paper's own ansatz, the per-qubit complex NADE of Appendix
+B.1, and readings):
+* per-qubit NADE (NADEAnsatz): see its docstring.
 * per-slot MLP: slot p reads the one-hot of v_<p (4p inputs), tanh hidden
   layers, 8 outputs; slot 0 has no input (first layer = bias).
 * causal transformer: token t is the start token (t = 0) or v_{t-1}, plus a
@@ -210,6 +211,85 @@ class TFAnsatz:
 
     def slot_out(self, xs, p: int) -> torch.Tensor:
         return self.outputs(xs, upto=p + 1)[:, p]
+
+
+def leaky_relu(x):
+    """LeReLU of Appendix B.1, read as the usual leaky ReLU: x for x >= 0,
+    0.01 x otherwise (the printed "-0.01 x" would make the function
+    non-monotonic; reading)."""
+    return torch.where(x >= 0, x, 0.01 * x)
+
+
+class NADEAnsatz:
+    """The paper's own ansatz (Appendix B.1): one complex MLP per qubit
+    i = 1..N (here 0-based, i = 0..2n-1) reading the i previous bits, with
+    f1 = tanh (complex), f2 = LeReLU(Re z) + i LeReLU(Im z), and f3(z) =
+    z - 1/2 LSE(2 Re z) over its two outputs, so that
+    log psi_i(x_i | x_<i) = f3(z)_{x_i}.
+
+    The slot formulation of this build groups qubits 2p (alpha) and 2p + 1
+    (beta): the slot conditional of v = a + 2b is psi_{2p}(a) psi_{2p+1}(b | a).
+    MU masking acts on each qubit's binary conditional (Sec. III.C): the
+    allowed values of qubit 2p are those a with some allowed (a, b) in the
+    slot, those of qubit 2p+1 the b with (a, b) allowed; the modulus is
+    renormalised over them and the phases kept (reading 4).  On the DU slots
+    of an MU-d strategy no value is masked.  slot_out returns the 8 slot
+    values l_v = log |psi_slot(v)|^2 and phi_v = arg psi_slot(v) (-inf for
+    masked v), which are already normalised, so the slot-level machinery
+    (masked log-softmax, sampler) reproduces them.
+    """
+
+    def __init__(self, qubits, n: int, isphys: IsPhys, du_levels: int = 0):
+        self.n, self.isphys, self.du_levels = n, isphys, du_levels
+        self.q = [[(torch.tensor(a.real, dtype=DT), torch.tensor(a.imag, dtype=DT)) for a in arrs] for arrs in qubits]
+
+    def parameters(self):
+        return [t for arrs in self.q for pair in arrs for t in pair]
+
+    def _qubit(self, i: int, bits: torch.Tensor) -> torch.Tensor:
+        """log psi_i(0), log psi_i(1) (complex, unmasked) for bits [B, i]."""
+        (W1r, W1i), (b1r, b1i), (W2r, W2i), (b2r, b2i), (W3r, W3i), (b3r, b3i) = self.q[i]
+        W1, b1 = torch.complex(W1r, W1i), torch.complex(b1r, b1i)
+        W2, b2 = torch.complex(W2r, W2i), torch.complex(b2r, b2i)
+        W3, b3 = torch.complex(W3r, W3i), torch.complex(b3r, b3i)
+        B = bits.shape[0]
+        z = b1.expand(B, -1) + (bits.to(torch.complex128) @ W1.T if i > 0 else 0)
+        h = torch.tanh(z)
+        z = h @ W2.T + b2
+        h = torch.complex(leaky_relu(z.real), leaky_relu(z.imag))
+        z = h @ W3.T + b3
+        return z - 0.5 * torch.logsumexp(2 * z.real, dim=-1, keepdim=True)
+
+    @staticmethod
+    def _mask(lq: torch.Tensor, allowed: torch.Tensor) -> torch.Tensor:
+        """Renormalise the modulus over the allowed values, keep the phases."""
+        neg = torch.full_like(lq.real, -math.inf)
+        re = torch.where(allowed, lq.real, neg)
+        lse = 0.5 * torch.logsumexp(2 * re, dim=-1, keepdim=True)
+        lse = torch.where(torch.isfinite(lse), lse, torch.zeros_like(lse))
+        return torch.complex(re - lse, lq.imag)
+
+    def slot_out(self, xs, p: int) -> torch.Tensor:
+        xs = np.asarray(xs, dtype=np.uint64)
+        B = len(xs)
+        bits = torch.tensor(np.stack([((xs >> np.uint64(q)) & np.uint64(1)).astype(np.float64)
+                                      for q in range(2 * p)], axis=1) if p > 0 else np.zeros((B, 0)), dtype=DT)
+        lq0 = self._qubit(2 * p, bits)
+        lq1 = [self._qubit(2 * p + 1, torch.cat([bits, torch.full((B, 1), float(a), dtype=DT)], 1)) for a in (0, 1)]
+        if p < self.n - self.du_levels:
+            m = torch.as_tensor(allowed_masks(self.isphys, xs, self.n)[:, p])  # [B, 4], v = a + 2b
+            lq0 = self._mask(lq0, torch.stack([m[:, 0] | m[:, 2], m[:, 1] | m[:, 3]], 1))
+            lq1 = [self._mask(lq1[a], torch.stack([m[:, a], m[:, a + 2]], 1)) for a in (0, 1)]
+        out = torch.zeros((B, 8), dtype=DT)
+        for v in range(4):
+            a, b = v & 1, v >> 1
+            lv = lq0[:, a] + lq1[a][:, b]
+            out[:, v] = 2 * lv.real
+            out[:, 4 + v] = lv.imag
+        return out
+
+    def outputs(self, xs) -> torch.Tensor:
+        return torch.stack([self.slot_out(xs, p) for p in range(self.n)], dim=1)
 
 
 class TableAnsatz:

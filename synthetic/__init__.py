@@ -265,6 +265,48 @@ def tf_param_count(n: int, d: int, n_layers: int) -> int:
     return 5 * d + n * d + n_layers * per_layer + 2 * d + N_OUT * d + N_OUT
 
 
+def nade_params(seed: int, n: int, width: int = 64, bias_std: float = 0.0):
+    """Per-qubit NADE weights (Appendix B.1): one complex MLP per qubit
+    i = 0..2n-1 (0-based) reading the i previous bits, two hidden layers of
+    `width`, 2 complex outputs.  Per qubit: (W1 [w][i], b1 [w], W2 [w][w],
+    b2 [w], W3 [2][w], b3 [2]) as complex128 arrays holding float32-
+    representable parts; real and imaginary parts of a matrix with fan-in f
+    ~ N(0, 1/(2 f)) each, biases ~ N(0, bias_std^2) each part."""
+    rng = np.random.default_rng(3000 + seed)
+
+    def cplx(shape, std):
+        if std == 0.0 or 0 in shape:
+            return np.zeros(shape, dtype=np.complex128)
+        re = rng.normal(0.0, std, shape).astype(np.float32).astype(np.float64)
+        im = rng.normal(0.0, std, shape).astype(np.float32).astype(np.float64)
+        return re + 1j * im
+
+    qubits = []
+    for i in range(2 * n):
+        W1 = cplx((width, i), 1.0 / np.sqrt(2 * max(i, 1)))
+        b1 = cplx((width,), bias_std)
+        W2 = cplx((width, width), 1.0 / np.sqrt(2 * width))
+        b2 = cplx((width,), bias_std)
+        W3 = cplx((2, width), 1.0 / np.sqrt(2 * width))
+        b3 = cplx((2,), bias_std)
+        qubits.append((W1, b1, W2, b2, W3, b3))
+    return qubits
+
+
+def flatten_nade(qubits) -> np.ndarray:
+    """Flat float32 layout of anqs.h: per qubit W1, b1, W2, b2, W3, b3, each
+    row-major with (re, im) interleaved."""
+    parts = []
+    for arrs in qubits:
+        for a in arrs:
+            parts.append(np.stack([a.real, a.imag], axis=-1).reshape(-1))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def nade_param_count(n: int, width: int) -> int:
+    return sum(2 * (width * i + width + width * width + width + 2 * width + 2) for i in range(2 * n))
+
+
 # ----------------------------------------------------------------------------
 # workloads
 # ----------------------------------------------------------------------------
