@@ -43,6 +43,20 @@
  *                   token (t = 0) or v_{t-1} and outputs slot t's 8 values.
  *   ANQS_MODEL_TABLE for each slot p: table_p[4^p][8], row = the prefix bits
  *                   x & (4^p - 1).  n <= 11.
+ *   ANQS_MODEL_NADE the per-qubit complex NADE of Appendix B.1 (FP32 form
+ *                   only, width in {32, 64, 128}; no adjoint: anqs_grad and
+ *                   anqs_logpsi_vjp return ANQS_ERR_UNSUPPORTED).  For each
+ *                   qubit i = 0..2n-1 (q = 2p + sigma, alpha first): W1
+ *                   [w][i], b1 [w], W2 [w][w], b2 [w], W3 [2][w], b3 [2],
+ *                   complex, row-major, each entry (re, im) interleaved.
+ *                   z1 = W1 x_<i + b1, h1 = tanh(z1) (complex), z2 = W2 h1 +
+ *                   b2, h2 = LeReLU(Re z2) + i LeReLU(Im z2) (slope 0.01
+ *                   below zero), z3 = W3 h2 + b3, f3(z3) = z3 - LSE(2 Re
+ *                   z3) / 2 = (log psi_i(0), log psi_i(1)).  Slot p's values
+ *                   are l_v = 2 Re, phi_v = Im of log psi_2p(a) + log
+ *                   psi_2p+1(b | a), v = a + 2b; on MU slots each qubit's
+ *                   modulus is first renormalised over the values with an
+ *                   allowed slot outcome (b given a for qubit 2p+1).
  * Slot conditional (Appendix B.1, activation f3, with MU masking of
  * Sec. III.C): |psi_p(v)|^2 = exp(l_v) / sum_{u allowed} exp(l_u) over the
  * outcomes u that can still reach the (N_alpha, N_beta) sector, 0 for the
@@ -74,7 +88,7 @@ enum {
   ANQS_ERR_UNSUPPORTED = -5  /* configuration outside the supported range */
 };
 
-enum { ANQS_MODEL_MLP = 0, ANQS_MODEL_TF = 1, ANQS_MODEL_TABLE = 2 };
+enum { ANQS_MODEL_MLP = 0, ANQS_MODEL_TF = 1, ANQS_MODEL_TABLE = 2, ANQS_MODEL_NADE = 3 };
 
 /* Arithmetic form of a model's network evaluation.
  * FP32: plain SIMT float32 kernels, every configuration evaluated over all
@@ -91,7 +105,7 @@ typedef struct {
   int32_t kind;      /* ANQS_MODEL_* */
   int32_t form;      /* ANQS_FORM_* (TABLE: FP32 only) */
   int32_t n_orb;     /* spatial orbitals n (slots), 1..32 */
-  int32_t width;     /* MLP: hidden width (multiple of 32, <= 256) */
+  int32_t width;     /* MLP: hidden width in {64, 128, 256}; NADE: in {32, 64, 128} */
   int32_t n_hidden;  /* MLP: hidden layers L (1..8) */
   int32_t d_model;   /* TF: model width d in {32, 64, 128, 256} */
   int32_t n_heads;   /* TF: heads (d_model % n_heads == 0) */
@@ -331,7 +345,8 @@ ANQS_API int anqs_local_energy(const anqs_model* model, const anqs_ham* ham, con
  * with E = stats[0] + i stats[1] and S = stats[3] (as written by
  * anqs_local_energy).  grad_dev: n_params floats, overwritten.  n_x_dev as
  * for anqs_local_energy.
- * Hand-written adjoint of the masked log psi (MLP and transformer).
+ * Hand-written adjoint of the masked log psi (MLP and transformer); other
+ * model kinds return ANQS_ERR_UNSUPPORTED before anything is queued.
  * ------------------------------------------------------------------------- */
 ANQS_API int anqs_grad_workspace_size(const anqs_model* model, const anqs_ham* ham, uint64_t n_x,
                              size_t* bytes);

@@ -128,6 +128,12 @@ class Model:
         d = ModelDesc(_lib.ANQS_MODEL_TABLE, _lib.ANQS_FORM_FP32, n_orb, 0, 0, 0, 0, 0)
         return cls(d, params)
 
+    @classmethod
+    def nade(cls, n_orb, width, params):
+        """Per-qubit complex NADE of Appendix B.1 (FP32; no adjoint)."""
+        d = ModelDesc(_lib.ANQS_MODEL_NADE, _lib.ANQS_FORM_FP32, n_orb, width, 0, 0, 0, 0)
+        return cls(d, params)
+
     @property
     def n_orb(self):
         return self.desc.n_orb

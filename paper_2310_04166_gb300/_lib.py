@@ -8,7 +8,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "lib", "libanqs.so")
 
 ANQS_OK = 0
-ANQS_MODEL_MLP, ANQS_MODEL_TF, ANQS_MODEL_TABLE = 0, 1, 2
+ANQS_MODEL_MLP, ANQS_MODEL_TF, ANQS_MODEL_TABLE, ANQS_MODEL_NADE = 0, 1, 2, 3
 ANQS_FORM_FP32, ANQS_FORM_BF16 = 0, 1
 ERRORS = {-1: "ANQS_ERR_ARG", -2: "ANQS_ERR_CAPACITY", -3: "ANQS_ERR_SECTOR", -4: "ANQS_ERR_CUDA",
           -5: "ANQS_ERR_UNSUPPORTED"}

@@ -112,6 +112,8 @@ int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, C
       return launch_tf_fp32_logpsi(M->tf, H->v, x, n_x, la, ph, s);
     case ANQS_MODEL_TABLE:
       return launch_table_logpsi(M, H->v, x, n_x, la, ph, s);
+    case ANQS_MODEL_NADE:
+      return launch_nade_logpsi(M->nade, H->v, x, n_x, la, ph, s);
     default:
       return set_error(ANQS_ERR_UNSUPPORTED, "model kind %d not available in this build", M->d.kind);
   }
@@ -135,6 +137,12 @@ static size_t eloc_plain_ws(const anqs_ham* H, uint64_t n_x, Arena& A, uint64_t*
 }  // namespace anqs
 
 namespace anqs {
+// model kinds with a hand-written adjoint
+static int check_adjoint(const anqs_model* M) {
+  if (M->d.kind == ANQS_MODEL_MLP || M->d.kind == ANQS_MODEL_TF) return ANQS_OK;
+  return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not available in this build", M->d.kind);
+}
+
 static int vjp_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, const float* cl,
                         const float* cp, float* grad, float* part, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (M->d.kind == ANQS_MODEL_MLP) return launch_mlp_fp32_grad(M->mlp, H->v, x, n_x, cl, cp, grad, part, s);
@@ -374,9 +382,17 @@ static int validate_desc(const anqs_model_desc* d) {
       if (d->n_orb > 11) return set_error(ANQS_ERR_UNSUPPORTED, "table model needs n_orb <= 11");
       if (d->form != ANQS_FORM_FP32) return set_error(ANQS_ERR_UNSUPPORTED, "table model is FP32 only");
       return ANQS_OK;
+    case ANQS_MODEL_NADE:
+      if (d->width != 32 && d->width != 64 && d->width != 128)
+        return set_error(ANQS_ERR_UNSUPPORTED, "NADE width %d not in {32,64,128}", d->width);
+      if (d->form != ANQS_FORM_FP32) return set_error(ANQS_ERR_UNSUPPORTED, "NADE model is FP32 only");
+      return ANQS_OK;
   }
   return set_error(ANQS_ERR_ARG, "unknown model kind %d", d->kind);
 }
+
+// floats of qubit i's block: complex W1 [w][i], b1 [w], W2 [w][w], b2 [w], W3 [2][w], b3 [2]
+static uint64_t nade_qubit_floats(uint64_t w, uint64_t i) { return 2 * (w * i + w + w * w + w + 2 * w + 2); }
 
 static uint64_t count_params(const anqs_model_desc* d) {
   uint64_t n = d->n_orb;
@@ -389,6 +405,11 @@ static uint64_t count_params(const anqs_model_desc* d) {
     uint64_t D = d->d_model;
     uint64_t per = 4 * D + 4 * (D * D + D) + 2 * (4 * D * D) + 4 * D + D;
     return 5 * D + n * D + d->n_layers * per + 2 * D + 8 * D + 8;
+  }
+  if (d->kind == ANQS_MODEL_NADE) {
+    uint64_t t = 0;
+    for (uint64_t i = 0; i < 2 * n; ++i) t += nade_qubit_floats(d->width, i);
+    return t;
   }
   uint64_t t = 0, r = 1;
   for (uint64_t p = 0; p < n; ++p, r *= 4) t += 8 * r;
@@ -443,6 +464,16 @@ int anqs_model_create(anqs_model** out, const anqs_model_desc* d, const float* p
         anqs_model_destroy(M);
         return r;
       }
+    }
+  } else if (d->kind == ANQS_MODEL_NADE) {
+    NadeView& v = M->nade;
+    v.n = d->n_orb;
+    v.w = d->width;
+    v.params = params;
+    uint64_t off = 0;
+    for (int i = 0; i < 2 * d->n_orb; ++i) {
+      v.qoff[i] = uint32_t(off);
+      off += nade_qubit_floats(d->width, i);
     }
   } else if (d->kind == ANQS_MODEL_TF) {
     M->tf.n = d->n_orb;
@@ -653,6 +684,7 @@ int anqs_grad(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const u
   ANQS_TRY(check_pair(M, H));
   if (n_x == 0) return set_error(ANQS_ERR_ARG, "n_x must be >= 1");
   if (!x || !counts || !ere || !eim || !stats || !grad) return set_error(ANQS_ERR_ARG, "null array argument");
+  ANQS_TRY(check_adjoint(M));
   Arena A(ws, ws_bytes);
   float* cl = A.take<float>(n_x);
   float* cp = A.take<float>(n_x);
@@ -679,6 +711,7 @@ int anqs_logpsi_vjp(const anqs_model* M, const anqs_ham* H, const uint64_t* x, u
   ANQS_TRY(check_pair(M, H));
   if (!grad) return set_error(ANQS_ERR_ARG, "null gradient output");
   if (n_x && (!x || !cl || !cp)) return set_error(ANQS_ERR_ARG, "null array argument");
+  ANQS_TRY(check_adjoint(M));
   const size_t need = (M->d.kind == ANQS_MODEL_TF) ? tf_grad_workspace(M->tf, n_x) : 0;
   if (ws_bytes < need || (need && !ws)) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
   cudaStream_t s = (cudaStream_t)stream;

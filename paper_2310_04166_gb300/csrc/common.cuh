@@ -43,6 +43,7 @@ enum ProfId {
   PROF_TF_TC_PARENT,
   PROF_TF_TC_SUFFIX,
   PROF_TF_TC_SLOT,
+  PROF_NADE,
   PROF_COUNT
 };
 
@@ -168,6 +169,14 @@ struct TfView {
   const float* params;
 };
 
+// Per-qubit NADE parameters as seen by the kernels: qubit i's block
+// (W1, b1, W2, b2, W3, b3, complex interleaved) starts at params + qoff[i].
+struct NadeView {
+  int n, w;
+  const float* params;
+  uint32_t qoff[2 * ANQS_MAX_ORB];
+};
+
 // Bump allocator over a caller-provided workspace; with base == nullptr it
 // only measures.
 struct Arena {
@@ -202,6 +211,7 @@ struct anqs_model {
   uint64_t n_params;
   MlpView mlp;
   TfView tf;
+  NadeView nade;
   // BF16 form: packed weight images (see mlp_tc.cu)
   void* packed;
   size_t packed_bytes;
@@ -305,6 +315,12 @@ int launch_tf_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t* 
                         float* ph, cudaStream_t s);
 int launch_tf_tc_slot_logits(const anqs_model* M, int p, const uint64_t* pre, const uint64_t* n_dev,
                              uint64_t max_rows, float* out8, cudaStream_t s);
+
+// nade.cu (per-qubit NADE, FP32)
+int launch_nade_logpsi(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, float* la, float* ph,
+                       cudaStream_t s);
+int launch_nade_slot_logits(const NadeView& m, const HamView& hv, int p, const uint64_t* pre, const uint64_t* n_dev,
+                            uint64_t max_rows, float* out8, cudaStream_t s);
 
 // api.cu
 int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, float* la,

@@ -30,7 +30,8 @@ const char* kNames[PROF_COUNT] = {
     "cotangent_kernel",       "sampler_draw_kernels", "mlp_tc_parent_kernel",   "mlp_tc_suffix_kernel",
     "tc_sort_kernels",        "eloc_assemble_kernel", "mlp_tc_slot_kernel",     "tf_fp32_kernel",
     "finalize_kernel",        "grad_partial_sum_kernel", "unused",              "tf_fp32_grad_kernels",
-    "tf_tc_parent_kernel",    "tf_tc_suffix_kernel",  "tf_tc_slot_kernel"};
+    "tf_tc_parent_kernel",    "tf_tc_suffix_kernel",  "tf_tc_slot_kernel",
+    "nade_kernel"};
 
 cudaEvent_t get_event() {
   if (!g_pool.empty()) {

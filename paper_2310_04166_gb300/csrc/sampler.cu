@@ -782,6 +782,8 @@ int logits_dispatch(const anqs_model* M, const anqs_ham* H, int p, const uint64_
       return launch_tf_fp32_slot_logits(M->tf, p, pre, n_dev, max_rows, out8, s);
     case ANQS_MODEL_TABLE:
       return launch_table_slot_logits(M, p, pre, n_dev, max_rows, out8, s);
+    case ANQS_MODEL_NADE:
+      return launch_nade_slot_logits(M->nade, H->v, p, pre, n_dev, max_rows, out8, s);
     default:
       return set_error(ANQS_ERR_UNSUPPORTED, "sampling for model kind %d not available in this build", M->d.kind);
   }
