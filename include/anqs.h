@@ -44,8 +44,7 @@
  *   ANQS_MODEL_TABLE for each slot p: table_p[4^p][8], row = the prefix bits
  *                   x & (4^p - 1).  n <= 11.
  *   ANQS_MODEL_NADE the per-qubit complex NADE of Appendix B.1 (FP32 form
- *                   only, width in {32, 64, 128}; no adjoint: anqs_grad and
- *                   anqs_logpsi_vjp return ANQS_ERR_UNSUPPORTED).  For each
+ *                   only, width in {32, 64, 128}, n_orb <= 32).  For each
  *                   qubit i = 0..2n-1 (q = 2p + sigma, alpha first): W1
  *                   [w][i], b1 [w], W2 [w][w], b2 [w], W3 [2][w], b3 [2],
  *                   complex, row-major, each entry (re, im) interleaved.
@@ -345,8 +344,8 @@ ANQS_API int anqs_local_energy(const anqs_model* model, const anqs_ham* ham, con
  * with E = stats[0] + i stats[1] and S = stats[3] (as written by
  * anqs_local_energy).  grad_dev: n_params floats, overwritten.  n_x_dev as
  * for anqs_local_energy.
- * Hand-written adjoint of the masked log psi (MLP and transformer); other
- * model kinds return ANQS_ERR_UNSUPPORTED before anything is queued.
+ * Hand-written adjoint of the masked log psi (MLP, transformer, NADE); the
+ * table model returns ANQS_ERR_UNSUPPORTED before anything is queued.
  * ------------------------------------------------------------------------- */
 ANQS_API int anqs_grad_workspace_size(const anqs_model* model, const anqs_ham* ham, uint64_t n_x,
                              size_t* bytes);

@@ -130,7 +130,7 @@ class Model:
 
     @classmethod
     def nade(cls, n_orb, width, params):
-        """Per-qubit complex NADE of Appendix B.1 (FP32; no adjoint)."""
+        """Per-qubit complex NADE of Appendix B.1 (FP32 form)."""
         d = ModelDesc(_lib.ANQS_MODEL_NADE, _lib.ANQS_FORM_FP32, n_orb, width, 0, 0, 0, 0)
         return cls(d, params)
 

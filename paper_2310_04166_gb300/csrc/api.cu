@@ -139,14 +139,23 @@ static size_t eloc_plain_ws(const anqs_ham* H, uint64_t n_x, Arena& A, uint64_t*
 namespace anqs {
 // model kinds with a hand-written adjoint
 static int check_adjoint(const anqs_model* M) {
-  if (M->d.kind == ANQS_MODEL_MLP || M->d.kind == ANQS_MODEL_TF) return ANQS_OK;
+  if (M->d.kind == ANQS_MODEL_MLP || M->d.kind == ANQS_MODEL_TF || M->d.kind == ANQS_MODEL_NADE) return ANQS_OK;
   return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not available in this build", M->d.kind);
+}
+
+// model-specific adjoint workspace (bytes) beyond the two cotangent arrays
+static size_t vjp_ws_bytes(const anqs_model* M, uint64_t n_x) {
+  if (M->d.kind == ANQS_MODEL_TF) return tf_grad_workspace(M->tf, n_x);
+  if (M->d.kind == ANQS_MODEL_NADE) return nade_grad_partial_floats(M->nade, M->n_params, n_x) * sizeof(float);
+  return 0;
 }
 
 static int vjp_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, const float* cl,
                         const float* cp, float* grad, float* part, void* ws, size_t ws_bytes, cudaStream_t s) {
   if (M->d.kind == ANQS_MODEL_MLP) return launch_mlp_fp32_grad(M->mlp, H->v, x, n_x, cl, cp, grad, part, s);
   if (M->d.kind == ANQS_MODEL_TF) return launch_tf_fp32_grad(M->tf, H->v, x, n_x, cl, cp, grad, ws, ws_bytes, s);
+  if (M->d.kind == ANQS_MODEL_NADE)
+    return launch_nade_grad(M->nade, H->v, x, n_x, cl, cp, grad, M->n_params, static_cast<float*>(ws), s);
   return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not available in this build", M->d.kind);
 }
 }  // namespace anqs
@@ -673,7 +682,7 @@ int anqs_grad_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_
   A.take<float>(n_x);
   A.take<float>(n_x);
   if (M->d.kind == ANQS_MODEL_MLP) A.take<float>(mlp_fp32_grad_partial_floats(M->mlp, n_x));
-  if (M->d.kind == ANQS_MODEL_TF) A.take<char>(tf_grad_workspace(M->tf, n_x));
+  A.take<char>(vjp_ws_bytes(M, n_x));
   *bytes = A.off;
   return ANQS_OK;
 }
@@ -689,7 +698,7 @@ int anqs_grad(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const u
   float* cl = A.take<float>(n_x);
   float* cp = A.take<float>(n_x);
   float* part = (M->d.kind == ANQS_MODEL_MLP) ? A.take<float>(mlp_fp32_grad_partial_floats(M->mlp, n_x)) : nullptr;
-  const size_t tfb = (M->d.kind == ANQS_MODEL_TF) ? tf_grad_workspace(M->tf, n_x) : 0;
+  const size_t tfb = vjp_ws_bytes(M, n_x);
   void* tfws = tfb ? A.take<char>(tfb) : nullptr;
   if (!A.fits() || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", A.off);
   cudaStream_t s = (cudaStream_t)stream;
@@ -702,7 +711,7 @@ int anqs_grad(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const u
 int anqs_logpsi_vjp_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_x, size_t* bytes) {
   ANQS_TRY(check_pair(M, H));
   if (!bytes) return set_error(ANQS_ERR_ARG, "null output");
-  *bytes = (M->d.kind == ANQS_MODEL_TF) ? tf_grad_workspace(M->tf, n_x) : 0;
+  *bytes = vjp_ws_bytes(M, n_x);
   return ANQS_OK;
 }
 
@@ -712,7 +721,7 @@ int anqs_logpsi_vjp(const anqs_model* M, const anqs_ham* H, const uint64_t* x, u
   if (!grad) return set_error(ANQS_ERR_ARG, "null gradient output");
   if (n_x && (!x || !cl || !cp)) return set_error(ANQS_ERR_ARG, "null array argument");
   ANQS_TRY(check_adjoint(M));
-  const size_t need = (M->d.kind == ANQS_MODEL_TF) ? tf_grad_workspace(M->tf, n_x) : 0;
+  const size_t need = vjp_ws_bytes(M, n_x);
   if (ws_bytes < need || (need && !ws)) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
   cudaStream_t s = (cudaStream_t)stream;
   ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));

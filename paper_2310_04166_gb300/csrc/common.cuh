@@ -44,6 +44,7 @@ enum ProfId {
   PROF_TF_TC_SUFFIX,
   PROF_TF_TC_SLOT,
   PROF_NADE,
+  PROF_NADE_GRAD,
   PROF_COUNT
 };
 
@@ -321,6 +322,10 @@ int launch_nade_logpsi(const NadeView& m, const HamView& hv, const uint64_t* x, 
                        cudaStream_t s);
 int launch_nade_slot_logits(const NadeView& m, const HamView& hv, int p, const uint64_t* pre, const uint64_t* n_dev,
                             uint64_t max_rows, float* out8, cudaStream_t s);
+// part: nade_grad_partial_floats floats (null when that is 0); grad is overwritten
+int launch_nade_grad(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
+                     const float* cp, float* grad, uint64_t n_params, float* part, cudaStream_t s);
+size_t nade_grad_partial_floats(const NadeView& m, uint64_t n_params, uint64_t n_x);
 
 // api.cu
 int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, float* la,

@@ -268,4 +268,234 @@ int launch_nade_slot_logits(const NadeView& m, const HamView& hv, int p, const u
   return launch(m, hv, pre, Count{max_rows, n_dev, 1}, NADE_LOGITS, p, nullptr, nullptr, out8, s);
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint (vector-Jacobian product of the masked log psi).
+//
+// The masked NADE is normalised slot by slot on MU and DU levels alike, so the
+// slot log-softmax of the forward is identically zero and
+// log psi(x) = sum_i [Re z3_i(x_i) - LSE_{A_i}(2 Re z3_i) / 2 + i Im z3_i(x_i)],
+// with A_i qubit i's allowed values on the path x (both values on DU slots).
+// Only the branch a = x_2p of qubit 2p+1 enters.  For L = cl la + cp ph the
+// gradient of the complex output z3_i(k), as (dL/dRe, dL/dIm), is
+// (cl (delta_k,x_i - pi_k), cp delta_k,x_i) with pi the softmax of 2 Re z3 over
+// A_i; it is pulled back through the complex layers (W^H g for a linear map,
+// conj(1 - h1^2) g for tanh, the 1 / 0.01 slope per part for LeReLU) and the
+// parameter gradients are g conj(input) (the real bits for W1).
+//
+// CTA (g, i) handles qubit i for the row tiles g, g + G, ... and accumulates
+// qubit i's whole parameter block in shared memory (each entry owned by one
+// thread, rows in tile order: deterministic); with G > 1 the blocks go to a
+// per-g partial buffer that a second kernel sums in a fixed order.
+// ---------------------------------------------------------------------------
+namespace {
+
+__host__ __device__ inline uint32_t qubit_floats(uint32_t w, uint32_t i) { return 2u * (w * i + w + w * w + w + 2u * w + 2u); }
+
+template <int W>
+__global__ void __launch_bounds__(NT) nade_grad_kernel(NadeView m, HamView hv, const uint64_t* __restrict__ xs,
+                                                       Count rows_, const float* __restrict__ cl,
+                                                       const float* __restrict__ cp, float* __restrict__ out,
+                                                       uint64_t out_stride) {
+  ANQS_PDL_ENTRY();
+  constexpr int R = NT / W;
+  extern __shared__ float2 acc[];  // qubit i's parameter block (complex entries)
+  __shared__ float2 h1[R * W], h2[R * W], gz1[R * W], gz2[R * W], z3[R * 2], g3[R * 2];
+  __shared__ uint64_t xt[R];
+  const int i = blockIdx.y, p = i >> 1, sigma = i & 1;
+  const int r = threadIdx.x / W, u = threadIdx.x % W;
+  const uint32_t nc = qubit_floats(W, i) / 2;  // complex entries of the block
+  const uint32_t oW1 = 0, ob1 = W * i, oW2 = ob1 + W, ob2 = oW2 + W * W, oW3 = ob2 + W, ob3 = oW3 + 2 * W;
+  for (uint32_t e = threadIdx.x; e < nc; e += NT) acc[e] = make_float2(0.f, 0.f);
+  const QubitPtr q = qubit_ptrs(m, i);
+  const uint64_t rows = rows_.get();
+  for (uint64_t base = uint64_t(blockIdx.x) * R; base < rows; base += uint64_t(gridDim.x) * R) {
+    if (threadIdx.x < R) xt[threadIdx.x] = base + threadIdx.x < rows ? xs[base + threadIdx.x] : 0ull;
+    __syncthreads();
+    const uint64_t x = xt[r];
+    // forward of qubit i on the path (bits x_<i of row r)
+    float2 z = __ldg(q.b1 + u), lo = make_float2(0.f, 0.f);
+    for (int k = 0; k < i; ++k) {
+      if ((x >> k) & 1ull) {
+        const float2 wv = __ldg(q.W1 + size_t(u) * i + k);
+        float ex, ey;
+        z.x = two_sum(z.x, wv.x, ex);
+        z.y = two_sum(z.y, wv.y, ey);
+        lo.x += ex;
+        lo.y += ey;
+      }
+    }
+    h1[r * W + u] = ctanh(z.x, lo.x, z.y, lo.y);
+    __syncthreads();
+    z = __ldg(q.b2 + u);
+    for (int k = 0; k < W; ++k) {
+      const float2 t = cmul(__ldg(q.W2 + size_t(u) * W + k), h1[r * W + k]);
+      z.x += t.x;
+      z.y += t.y;
+    }
+    h2[r * W + u] = make_float2(lerelu(z.x), lerelu(z.y));
+    __syncthreads();
+    if (u < 2) {
+      z = __ldg(q.b3 + u);
+      for (int k = 0; k < W; ++k) {
+        const float2 t = cmul(__ldg(q.W3 + size_t(u) * W + k), h2[r * W + k]);
+        z.x += t.x;
+        z.y += t.y;
+      }
+      z3[r * 2 + u] = z;
+    }
+    __syncthreads();
+    if (u == 0) {  // cotangent of z3: allowed values of qubit i on the path, softmax of 2 Re z3 over them
+      unsigned allowed = 3u;
+      if (p < hv.mu_lv) {
+        const unsigned pm = prefix_mask(hv, p, x);
+        if (sigma == 0) {
+          allowed = ((pm | (pm >> 2)) & 1u) | (((pm >> 1) | (pm >> 3)) & 1u) << 1;
+        } else {
+          const int a = int((x >> (2 * p)) & 1ull);
+          allowed = ((pm >> a) & 1u) | ((pm >> (a + 2)) & 1u) << 1;
+        }
+      }
+      const int xi = int((x >> i) & 1ull);
+      float2 g0 = make_float2(0.f, 0.f), g1 = g0;
+      if (base + r < rows && ((allowed >> xi) & 1u)) {
+        const float r0 = (allowed & 1u) ? 2.f * z3[r * 2].x : -INFINITY;
+        const float r1 = (allowed & 2u) ? 2.f * z3[r * 2 + 1].x : -INFINITY;
+        const float mx = fmaxf(r0, r1);
+        const float e0 = expf(r0 - mx), e1 = expf(r1 - mx);
+        const float pi0 = e0 / (e0 + e1), pi1 = e1 / (e0 + e1);
+        const float c_l = cl[base + r], c_p = cp[base + r];
+        g0 = make_float2(c_l * ((xi == 0 ? 1.f : 0.f) - pi0), xi == 0 ? c_p : 0.f);
+        g1 = make_float2(c_l * ((xi == 1 ? 1.f : 0.f) - pi1), xi == 1 ? c_p : 0.f);
+      }
+      g3[r * 2] = g0;
+      g3[r * 2 + 1] = g1;
+    }
+    __syncthreads();
+    {  // z2 cotangent: conj(W3)^T g3, then the LeReLU slope of each part (sign of h2 = sign of z2)
+      const float2 w0 = __ldg(q.W3 + u), w1 = __ldg(q.W3 + W + u);
+      const float2 ga = g3[r * 2], gb = g3[r * 2 + 1];
+      const float gr = w0.x * ga.x + w0.y * ga.y + w1.x * gb.x + w1.y * gb.y;
+      const float gi = w0.x * ga.y - w0.y * ga.x + w1.x * gb.y - w1.y * gb.x;
+      const float2 hh = h2[r * W + u];
+      gz2[r * W + u] = make_float2(hh.x >= 0.f ? gr : 0.01f * gr, hh.y >= 0.f ? gi : 0.01f * gi);
+    }
+    __syncthreads();
+    {  // z1 cotangent: conj(W2)^T gz2, then tanh: conj(1 - h1^2) g
+      float gr = 0.f, gi = 0.f;
+      for (int j = 0; j < W; ++j) {
+        const float2 w = __ldg(q.W2 + size_t(j) * W + u);
+        const float2 g = gz2[r * W + j];
+        gr += w.x * g.x + w.y * g.y;
+        gi += w.x * g.y - w.y * g.x;
+      }
+      const float2 h = h1[r * W + u];
+      const float dr = 1.f - (h.x * h.x - h.y * h.y), di = -2.f * h.x * h.y;
+      gz1[r * W + u] = make_float2(dr * gr + di * gi, dr * gi - di * gr);
+    }
+    __syncthreads();
+    // parameter gradients of the tile's rows: g conj(input) per weight, g per bias
+    for (uint32_t e = threadIdx.x; e < nc; e += NT) {
+      float2 s = acc[e];
+      if (e < ob1) {  // W1[v][k]: real input bits
+        const uint32_t v = e / uint32_t(i), k = e % uint32_t(i);
+        for (int rr = 0; rr < R; ++rr)
+          if ((xt[rr] >> k) & 1ull) {
+            s.x += gz1[rr * W + v].x;
+            s.y += gz1[rr * W + v].y;
+          }
+      } else if (e < oW2) {  // b1
+        for (int rr = 0; rr < R; ++rr) {
+          s.x += gz1[rr * W + (e - ob1)].x;
+          s.y += gz1[rr * W + (e - ob1)].y;
+        }
+      } else if (e < ob2) {  // W2[v][k]
+        const uint32_t v = (e - oW2) / W, k = (e - oW2) % W;
+        for (int rr = 0; rr < R; ++rr) {
+          const float2 g = gz2[rr * W + v], h = h1[rr * W + k];
+          s.x += g.x * h.x + g.y * h.y;
+          s.y += g.y * h.x - g.x * h.y;
+        }
+      } else if (e < oW3) {  // b2
+        for (int rr = 0; rr < R; ++rr) {
+          s.x += gz2[rr * W + (e - ob2)].x;
+          s.y += gz2[rr * W + (e - ob2)].y;
+        }
+      } else if (e < ob3) {  // W3[k][j]
+        const uint32_t k = (e - oW3) / W, j = (e - oW3) % W;
+        for (int rr = 0; rr < R; ++rr) {
+          const float2 g = g3[rr * 2 + k], h = h2[rr * W + j];
+          s.x += g.x * h.x + g.y * h.y;
+          s.y += g.y * h.x - g.x * h.y;
+        }
+      } else {  // b3
+        for (int rr = 0; rr < R; ++rr) {
+          s.x += g3[rr * 2 + (e - ob3)].x;
+          s.y += g3[rr * 2 + (e - ob3)].y;
+        }
+      }
+      acc[e] = s;
+    }
+    __syncthreads();
+  }
+  (void)oW1;
+  float2* o = reinterpret_cast<float2*>(out + blockIdx.x * out_stride + m.qoff[i]);
+  for (uint32_t e = threadIdx.x; e < nc; e += NT) o[e] = acc[e];
+}
+
+__global__ void nade_partial_sum_kernel(const float* __restrict__ part, int G, uint64_t n, float* __restrict__ grad) {
+  ANQS_PDL_ENTRY();
+  for (uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += uint64_t(gridDim.x) * blockDim.x) {
+    float s = 0.f;
+    for (int g = 0; g < G; ++g) s += part[uint64_t(g) * n + j];
+    grad[j] = s;
+  }
+}
+
+// CTAs per qubit: about two CTAs per SM over all 2n qubits, at most one per row tile
+int grad_groups(const NadeView& m, uint64_t n_x) {
+  const uint64_t tiles = (n_x + (NT / m.w) - 1) / (NT / m.w);
+  uint64_t g = (2 * 152) / uint64_t(2 * m.n);
+  if (g < 1) g = 1;
+  if (g > tiles) g = tiles;
+  return int(g < 1 ? 1 : g);
+}
+
+template <int W>
+int grad_w(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl, const float* cp,
+           float* grad, uint64_t n_params, float* part, cudaStream_t s) {
+  const int G = grad_groups(m, n_x.n);
+  const size_t smem = size_t(qubit_floats(W, 2 * m.n - 1)) * sizeof(float);
+  ANQS_CUDA(cudaFuncSetAttribute(nade_grad_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  float* out = G > 1 ? part : grad;
+  if (G > 1 && !part) return set_error(ANQS_ERR_CAPACITY, "NADE adjoint needs its partial-sum workspace");
+  ProfScope ps(PROF_NADE_GRAD, s);
+  ANQS_CUDA_LAUNCH("nade_grad_kernel", launch_k(nade_grad_kernel<W>, dim3(G, 2 * m.n), dim3(NT), smem, s, m, hv, x,
+                                                n_x, cl, cp, out, G > 1 ? n_params : uint64_t(0)));
+  if (G > 1) {
+    uint64_t blocks = (n_params + 255) / 256;
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    ANQS_CUDA_LAUNCH("nade_partial_sum_kernel", launch_k(nade_partial_sum_kernel, dim3(unsigned(blocks)), dim3(256), 0,
+                                                         s, static_cast<const float*>(part), G, n_params, grad));
+  }
+  return ANQS_OK;
+}
+
+}  // namespace
+
+size_t nade_grad_partial_floats(const NadeView& m, uint64_t n_params, uint64_t n_x) {
+  const int G = grad_groups(m, n_x);
+  return G > 1 ? size_t(G) * n_params : 0;
+}
+
+int launch_nade_grad(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
+                     const float* cp, float* grad, uint64_t n_params, float* part, cudaStream_t s) {
+  if (n_x.n == 0) return ANQS_OK;
+  switch (m.w) {
+    case 32: return grad_w<32>(m, hv, x, n_x, cl, cp, grad, n_params, part, s);
+    case 64: return grad_w<64>(m, hv, x, n_x, cl, cp, grad, n_params, part, s);
+    case 128: return grad_w<128>(m, hv, x, n_x, cl, cp, grad, n_params, part, s);
+  }
+  return set_error(ANQS_ERR_UNSUPPORTED, "NADE width %d", m.w);
+}
+
 }  // namespace anqs
