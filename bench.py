@@ -138,7 +138,7 @@ def _cpu_baseline(w, sets=None, seconds=10.0, n_max=100000):
     samples; otherwise it cycles over the unique samples of one oracle
     sampling pass.  The value is unique samples per second over all the
     oracle's work."""
-    from oracle.anqs import MLPAnsatz, TFAnsatz
+    from oracle.anqs import MLPAnsatz, NADEAnsatz, TFAnsatz
     from oracle.hamiltonian import Hamiltonian as OHam
     from oracle.sampler import sample as osample
     from oracle.sector import molecular_isphys
@@ -146,8 +146,12 @@ def _cpu_baseline(w, sets=None, seconds=10.0, n_max=100000):
 
     oham = OHam(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
     ip = molecular_isphys(w["n"], w["n_alpha"], w["n_beta"])
-    om = MLPAnsatz(w["params_struct"], w["n"]) if w["kind"] == "mlp" else \
-        TFAnsatz(w["params_struct"], w["n"], w["n_heads"])
+    if w["kind"] == "mlp":
+        om = MLPAnsatz(w["params_struct"], w["n"])
+    elif w["kind"] == "nade":
+        om = NADEAnsatz(w["params_struct"], w["n"], ip)
+    else:
+        om = TFAnsatz(w["params_struct"], w["n"], w["n_heads"])
     k = 8
     if sets:
         done, busy, delta, notes = 0, 0.0, {}, []
@@ -203,8 +207,9 @@ def _reference_arm(args, w, ws, rank):
 
 
 def _config(w, args):
-    net = (f"per-slot MLP {w['n_hidden']}x{w['width']}" if w["kind"] == "mlp"
-           else f"transformer d{w['d_model']} h{w['n_heads']} L{w['n_layers']}")
+    net = {"mlp": lambda: f"per-slot MLP {w['n_hidden']}x{w['width']}",
+           "nade": lambda: f"per-qubit complex NADE (App. B.1) width {w['width']}",
+           "tf": lambda: f"transformer d{w['d_model']} h{w['n_heads']} L{w['n_layers']}"}[w["kind"]]()
     return {"workload": f"{args.workload}: n_orb={w['n']} N_a={w['n_alpha']} N_b={w['n_beta']} "
                         f"({2 * w['n']} qubits), {w['n_chol']} Cholesky vectors seed {w['seed']}, {net}, "
                         f"N_s={args.n_samples or w['n_samples']}",
@@ -228,6 +233,8 @@ TRAFFIC = {("h2o", "bf16"): {"mlp_fp32_grad_kernel": 1093120 + 44032, "mlp_tc_su
 def _make_model(A, w, params, form):
     if w["kind"] == "mlp":
         return A.Model.mlp(w["n"], w["width"], w["n_hidden"], params, form=form)
+    if w["kind"] == "nade":
+        return A.Model.nade(w["n"], w["width"], params)
     return A.Model.transformer(w["n"], w["d_model"], w["n_heads"], w["n_layers"], params, form=form)
 
 
@@ -491,6 +498,8 @@ def main():
         return
     ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
     params = torch.tensor(w["params"], device=dev)
+    if w["kind"] == "nade":  # the NADE has the FP32 form only
+        args.form, args.one_form = "fp32", True
     form = args.form
     if args.kernel_case:
         model = _make_model(A, w, params, form)
@@ -583,6 +592,8 @@ def _tc_work(A, ham, model, w, x):
     forward recomputed plus the two adjoint products); eloc bytes = per
     connected x': x' 8 + j 1 + H 8 + parent cache 8 + one 8-byte term per
     slot p > j."""
+    if w["kind"] == "nade":
+        return _nade_work(A, ham, w, x)
     if w["kind"] != "mlp":
         return _tf_work(A, ham, w, x)
     n, W, L = w["n"], w["width"], w["n_hidden"]
@@ -603,6 +614,27 @@ def _tc_work(A, ham, model, w, x):
             "connected_kernel": float(len(j) * (8 + 8 + 1) + len(x) * 8)}
 
 
+def _nade_work(A, ham, w, x):
+    """Algorithmic FLOP per step of the NADE kernels for the sample set x.
+    One evaluation of qubit i costs f(i) = 8 W^2 + 16 W + 2 i W (complex
+    W2 h1 and W3 h2 at 8 FLOP per complex multiply-add, the W1 columns of
+    the set bits counted as all i); a slot p costs f(2p) + 2 f(2p+1) (qubit
+    2p+1 for both values of qubit 2p).  nade_kernel = every slot of every
+    sample and of every connected x' (the FP32 form has no prefix reuse) plus
+    slot p of every distinct prefix at level p (sampler); nade_grad_kernel =
+    3 f(i) per (sample, qubit): the forward and the two adjoint products."""
+    n, W = w["n"], w["width"]
+    f = np.array([8 * W * W + 16 * W + 2 * i * W for i in range(2 * n)], dtype=np.float64)
+    slot = f[0::2] + 2 * f[1::2]
+    xs = x.cpu().numpy().astype(np.uint64)
+    rows = len(xs) * (1 + ham.n_connected)
+    samp = 0.0
+    for p in range(n):
+        pre = np.unique(xs & np.uint64((1 << (2 * p)) - 1)) if p else np.zeros(1, np.uint64)
+        samp += len(pre) * slot[p]
+    return {"nade_kernel": rows * slot.sum() + samp, "nade_grad_kernel": 3.0 * len(xs) * f.sum()}
+
+
 def _rooflines(prof, work, steps, peaks, src, traffic):
     """Roofline of every kernel family with a defined bound (work per step x
     steps / total event time) and the dominant one by time."""
@@ -618,7 +650,8 @@ def _rooflines(prof, work, steps, peaks, src, traffic):
             bound, unit, peak = "tensor", "TFLOP/s", peaks["bf16_tflops"]
             ach = per_launch / avg_s / 1e12
             note = f"dense bf16 {src} burst peak; FLOP with prefix reuse"
-        elif name in ("mlp_fp32_grad_kernel", "tf_fp32_grad_kernels", "tf_fp32_kernel"):
+        elif name in ("mlp_fp32_grad_kernel", "tf_fp32_grad_kernels", "tf_fp32_kernel", "nade_kernel",
+                      "nade_grad_kernel"):
             bound, unit, peak = "alu", "TFLOP/s", fp32_peak
             ach = per_launch / avg_s / 1e12
             note = f"FP32 SIMT peak derived: 152 SMs x 128 FMA lanes x 2 x {sm_mhz:.0f} MHz"

@@ -318,6 +318,8 @@ WORKLOADS = {
                 n_hidden=3, n_samples=100_000),
     "n2": dict(n=10, n_alpha=7, n_beta=7, seed=2, n_chol=20, kind="tf", d_model=64,
                n_heads=4, n_layers=2, n_samples=1_000_000),
+    "h2o_nade": dict(n=7, n_alpha=5, n_beta=5, seed=1, n_chol=14, kind="nade", width=64,
+                     n_samples=100_000),
     "large": dict(n=26, n_alpha=9, n_beta=9, seed=3, n_chol=52, kind="tf", d_model=128,
                   n_heads=8, n_layers=4, n_unique=4096),
 }
@@ -344,6 +346,9 @@ def workload(name: str, bias_std: float = 0.0):
     if w["kind"] == "mlp":
         w["params_struct"] = mlp_params(w["seed"], w["n"], w["width"], w["n_hidden"], bias_std)
         w["params"] = flatten_mlp(w["params_struct"])
+    elif w["kind"] == "nade":
+        w["params_struct"] = nade_params(w["seed"], w["n"], w["width"], bias_std)
+        w["params"] = flatten_nade(w["params_struct"])
     else:
         w["params_struct"] = tf_params(w["seed"], w["n"], w["d_model"], w["n_layers"], bias_std)
         w["params"] = flatten_tf(w["params_struct"])
