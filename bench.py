@@ -618,21 +618,26 @@ def _nade_work(A, ham, w, x):
     """Algorithmic FLOP per step of the NADE kernels for the sample set x.
     One evaluation of qubit i costs f(i) = 8 W^2 + 16 W + 2 i W (complex
     W2 h1 and W3 h2 at 8 FLOP per complex multiply-add, the W1 columns of
-    the set bits counted as all i); a slot p costs f(2p) + 2 f(2p+1) (qubit
-    2p+1 for both values of qubit 2p).  nade_kernel = every slot of every
-    sample and of every connected x' (the FP32 form has no prefix reuse) plus
-    slot p of every distinct prefix at level p (sampler); nade_grad_kernel =
-    3 f(i) per (sample, qubit): the forward and the two adjoint products."""
+    the set bits counted as all i).  parent = the 8 values of every slot of
+    every sample, f(2p) + 2 f(2p+1) per slot (qubit 2p+1 for both values of
+    qubit 2p); suffix = the path qubits 2p, 2p+1 of the slots p > j(x') of
+    every connected x'; slot (sampler) = slot p of every distinct prefix at
+    level p; grad = 3 f(i) per (sample, qubit): the forward and the two
+    adjoint products."""
     n, W = w["n"], w["width"]
     f = np.array([8 * W * W + 16 * W + 2 * i * W for i in range(2 * n)], dtype=np.float64)
     slot = f[0::2] + 2 * f[1::2]
+    path = f[0::2] + f[1::2]
+    cpath = np.concatenate([[0.0], np.cumsum(path)])  # cpath[p] = sum_{q<p} path[q]
+    _, _, js, _ = A.connected(ham, x)
+    j = js.reshape(-1).cpu().numpy().astype(np.int64)
     xs = x.cpu().numpy().astype(np.uint64)
-    rows = len(xs) * (1 + ham.n_connected)
     samp = 0.0
     for p in range(n):
         pre = np.unique(xs & np.uint64((1 << (2 * p)) - 1)) if p else np.zeros(1, np.uint64)
         samp += len(pre) * slot[p]
-    return {"nade_kernel": rows * slot.sum() + samp, "nade_grad_kernel": 3.0 * len(xs) * f.sum()}
+    return {"nade_parent_kernel": len(xs) * slot.sum(), "nade_suffix_kernel": float((cpath[n] - cpath[j + 1]).sum()),
+            "nade_slot_kernel": samp, "nade_grad_kernel": 3.0 * len(xs) * f.sum()}
 
 
 def _rooflines(prof, work, steps, peaks, src, traffic):
@@ -650,8 +655,7 @@ def _rooflines(prof, work, steps, peaks, src, traffic):
             bound, unit, peak = "tensor", "TFLOP/s", peaks["bf16_tflops"]
             ach = per_launch / avg_s / 1e12
             note = f"dense bf16 {src} burst peak; FLOP with prefix reuse"
-        elif name in ("mlp_fp32_grad_kernel", "tf_fp32_grad_kernels", "tf_fp32_kernel", "nade_kernel",
-                      "nade_grad_kernel"):
+        elif name in ("mlp_fp32_grad_kernel", "tf_fp32_grad_kernels", "tf_fp32_kernel") or name.startswith("nade_"):
             bound, unit, peak = "alu", "TFLOP/s", fp32_peak
             ach = per_launch / avg_s / 1e12
             note = f"FP32 SIMT peak derived: 152 SMs x 128 FMA lanes x 2 x {sm_mhz:.0f} MHz"

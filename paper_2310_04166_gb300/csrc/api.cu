@@ -620,9 +620,11 @@ int anqs_stats_combine(const double* stats_in, int world, double* stats_out, voi
 // local energy
 // ---------------------------------------------------------------------------
 
-static bool uses_tc_eloc(const anqs_model* M) { return M->d.form == ANQS_FORM_BF16; }
+// prefix-reuse local energy: the BF16 forms and the NADE
+static bool uses_tc_eloc(const anqs_model* M) { return M->d.form == ANQS_FORM_BF16 || M->d.kind == ANQS_MODEL_NADE; }
 
 static size_t tc_eloc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x) {
+  if (M->d.kind == ANQS_MODEL_NADE) return nade_eloc_workspace(H, n_x);
   return M->d.kind == ANQS_MODEL_TF ? tf_tc_eloc_workspace(M, H, n_x) : eloc_tc_workspace(M, H, n_x);
 }
 
@@ -653,7 +655,8 @@ int anqs_local_energy(const anqs_model* M, const anqs_ham* H, const uint64_t* x,
   if (uses_tc_eloc(M)) {
     size_t need = tc_eloc_workspace(M, H, n_x);
     if (ws_bytes < need || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
-    if (M->d.kind == ANQS_MODEL_TF) ANQS_TRY(run_eloc_tf_tc(M, H, x, nc, ere, eim, ws, ws_bytes, s));
+    if (M->d.kind == ANQS_MODEL_NADE) ANQS_TRY(run_eloc_nade(M, H, x, nc, ere, eim, ws, ws_bytes, s));
+    else if (M->d.kind == ANQS_MODEL_TF) ANQS_TRY(run_eloc_tf_tc(M, H, x, nc, ere, eim, ws, ws_bytes, s));
     else ANQS_TRY(run_eloc_tc(M, H, x, nc, ere, eim, ws, ws_bytes, s));
   } else {
     Arena A(ws, ws_bytes);

@@ -45,6 +45,9 @@ enum ProfId {
   PROF_TF_TC_SLOT,
   PROF_NADE,
   PROF_NADE_GRAD,
+  PROF_NADE_SLOT,
+  PROF_NADE_PARENT,
+  PROF_NADE_SUFFIX,
   PROF_COUNT
 };
 
@@ -326,6 +329,9 @@ int launch_nade_slot_logits(const NadeView& m, const HamView& hv, int p, const u
 int launch_nade_grad(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
                      const float* cp, float* grad, uint64_t n_params, float* part, cudaStream_t s);
 size_t nade_grad_partial_floats(const NadeView& m, uint64_t n_params, uint64_t n_x);
+size_t nade_eloc_workspace(const anqs_ham* H, uint64_t n_x);
+int run_eloc_nade(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,
+                  void* ws, size_t ws_bytes, cudaStream_t s);
 
 // api.cu
 int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, float* la,

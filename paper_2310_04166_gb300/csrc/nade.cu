@@ -6,17 +6,29 @@
 // = f3(z3)_{x_i}.
 //
 // Slot p groups qubits 2p (alpha) and 2p+1 (beta): psi_slot(a + 2b) =
-// psi_2p(a) psi_2p+1(b | a), so qubit 2p's network runs once and qubit 2p+1's
-// twice (a = 0, 1) per prefix.  MU masking (Sec. III.C) acts on each binary
+// psi_2p(a) psi_2p+1(b | a).  MU masking (Sec. III.C) acts on each binary
 // conditional: qubit 2p's allowed values are the a with an allowed (a, b) in
 // the slot mask, qubit 2p+1's the b with (a, b) allowed; the modulus is
 // renormalised over them, the phases kept; DU slots of an MU-d strategy mask
-// nothing.  The slot's 8 values l_v = log |psi_slot(v)|^2, phi_v =
-// arg psi_slot(v) are already a normalised distribution, so the slot-level
-// machinery (masked log-softmax, sampler, local energy) applies unchanged.
+// nothing.  A slot's 8 values l_v = log |psi_slot(v)|^2, phi_v =
+// arg psi_slot(v) are thus already a normalised distribution, and log psi(x)
+// is the sum over the qubits of x's own path of the masked qubit terms
+// Re z3_i(x_i) - LSE_{A_i}(2 Re z3_i) / 2 + i Im z3_i(x_i) (A_i the allowed
+// values): one evaluation per qubit, where the slot values need three per
+// slot (qubit 2p+1 for both values of qubit 2p).
 //
-// A CTA of 256 threads holds 256 / W rows; thread (r, u) owns hidden unit u of
-// row r (complex values in shared memory between the layers).
+// Tile engine: a CTA of 256 threads evaluates one qubit for a tile of
+// TR = 4096 / W rows.  The W2 product, the bulk of the work, is a complex
+// GEMM [TR x W] x [W x W]^T run from shared memory (W2 with row stride W + 1,
+// h1 transposed with row stride TR + 1) with a 4 x 4 register tile of
+// (row, unit) accumulators per thread; the input layer, tanh, LeReLU and the
+// 2-output head are elementwise or short reductions around it.
+//
+// Modes: LOGPSI (log psi of rows, path qubits only), RAW (the 8 slot values
+// of every slot of every row: the parent pass of the local energy), SUFFIX
+// (for each connected x', sorted by its first differing slot j, the path terms
+// of the slots p > j: prefix reuse, the slots <= j come from the parent), and
+// LOGITS (slot p's 8 values for the sampler's prefixes).
 #include <cmath>
 
 #include "common.cuh"
@@ -25,7 +37,6 @@ namespace anqs {
 namespace {
 
 constexpr int NT = 256;
-enum { NADE_LOGPSI = 0, NADE_LOGITS = 1 };
 
 // tanh(a + ib) = (sinh a cosh a + i sin b cos b) / (sinh^2 a + cos^2 b), for
 // z = (ah + al) + i (bh + bl) given as float-float pairs.  The denominator
@@ -74,59 +85,6 @@ __device__ __forceinline__ QubitPtr qubit_ptrs(const NadeView& m, int i) {
 
 __device__ __forceinline__ float2 cmul(float2 x, float2 y) { return make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x); }
 
-// Qubit i's network for the R rows of the tile: bits k < i of row r are the
-// bits of x[r] below bit min(i, 2p), and bit 2p (when i = 2p + 1) is `a`.
-// Writes f3(z3) (unmasked log psi_i(0), log psi_i(1)) to lq[r][0..1].
-template <int W>
-__device__ void qubit_forward(const NadeView& m, int i, int p, int a, const uint64_t* xs, float2* h1, float2* h2,
-                              float2* lq) {
-  const int r = threadIdx.x / W, u = threadIdx.x % W;
-  const QubitPtr q = qubit_ptrs(m, i);
-  const uint64_t x = xs[r];
-  // z1 as a float-float pair: the sum of the selected W1 columns is exact to
-  // about u^2, which matters only next to a pole of tanh
-  float2 z = __ldg(q.b1 + u), lo = make_float2(0.f, 0.f);
-  for (int k = 0; k < i; ++k) {
-    const int bit = k < 2 * p ? int((x >> k) & 1ull) : a;
-    if (bit) {
-      const float2 wv = __ldg(q.W1 + size_t(u) * i + k);
-      float ex, ey;
-      z.x = two_sum(z.x, wv.x, ex);
-      z.y = two_sum(z.y, wv.y, ey);
-      lo.x += ex;
-      lo.y += ey;
-    }
-  }
-  h1[r * W + u] = ctanh(z.x, lo.x, z.y, lo.y);
-  __syncthreads();
-  z = __ldg(q.b2 + u);
-  for (int k = 0; k < W; ++k) {
-    const float2 t = cmul(__ldg(q.W2 + size_t(u) * W + k), h1[r * W + k]);
-    z.x += t.x;
-    z.y += t.y;
-  }
-  h2[r * W + u] = make_float2(lerelu(z.x), lerelu(z.y));
-  __syncthreads();
-  if (u < 2) {
-    z = __ldg(q.b3 + u);
-    for (int k = 0; k < W; ++k) {
-      const float2 t = cmul(__ldg(q.W3 + size_t(u) * W + k), h2[r * W + k]);
-      z.x += t.x;
-      z.y += t.y;
-    }
-    lq[r * 2 + u] = z;
-  }
-  __syncthreads();
-  if (u == 0) {  // f3: log-normalise the two outputs
-    const float2 z0 = lq[r * 2], z1 = lq[r * 2 + 1];
-    const float mx = fmaxf(2.f * z0.x, 2.f * z1.x);
-    const float lse = 0.5f * (mx + logf(expf(2.f * z0.x - mx) + expf(2.f * z1.x - mx)));
-    lq[r * 2] = make_float2(z0.x - lse, z0.y);
-    lq[r * 2 + 1] = make_float2(z1.x - lse, z1.y);
-  }
-  __syncthreads();
-}
-
 // renormalise the modulus of a binary conditional over the allowed values
 __device__ __forceinline__ void mask2(float2& l0, float2& l1, unsigned allowed) {
   const float r0 = (allowed & 1u) ? l0.x : -INFINITY;
@@ -144,115 +102,334 @@ __device__ __forceinline__ unsigned prefix_mask(const HamView& hv, int p, uint64
   return slot_mask(hv, p, __popcll(x & pm & 0x5555555555555555ull), __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull), x);
 }
 
-// The 8 slot values of slot p for the tile's rows (into o8[r][8]).
+// allowed values (bit b = value b) of qubit i on the path x: from the slot
+// mask pm of slot p = i / 2 on MU slots, both values on DU slots
+__device__ __forceinline__ unsigned qubit_allowed(const HamView& hv, int i, uint64_t x, unsigned pm) {
+  const int p = i >> 1;
+  if (p >= hv.mu_lv) return 3u;
+  if ((i & 1) == 0) return ((pm | (pm >> 2)) & 1u) | (((pm >> 1) | (pm >> 3)) & 1u) << 1;
+  const int a = int((x >> (2 * p)) & 1ull);
+  return ((pm >> a) & 1u) | ((pm >> (a + 2)) & 1u) << 1;
+}
+
+// acc += w h (complex)
+__device__ __forceinline__ void cmac(float2& acc, float2 w, float2 h) {
+  acc.x = fmaf(w.x, h.x, acc.x);
+  acc.x = fmaf(-w.y, h.y, acc.x);
+  acc.y = fmaf(w.x, h.y, acc.y);
+  acc.y = fmaf(w.y, h.x, acc.y);
+}
+
+// ---------------------------------------------------------------------------
+// Tile engine
+// ---------------------------------------------------------------------------
 template <int W>
-__device__ void nade_slot(const NadeView& m, const HamView& hv, int p, const uint64_t* xs, float2* h1, float2* h2,
-                          float2* lq, float* o8) {
-  constexpr int R = NT / W;
-  float2* lq0 = lq;          // [R][2]
-  float2* lq1 = lq + 2 * R;  // [2][R][2]: a = 0, 1
-  qubit_forward<W>(m, 2 * p, p, 0, xs, h1, h2, lq0);
-  qubit_forward<W>(m, 2 * p + 1, p, 0, xs, h1, h2, lq1);
-  qubit_forward<W>(m, 2 * p + 1, p, 1, xs, h1, h2, lq1 + 2 * R);
-  if (threadIdx.x < R) {
-    const int r = threadIdx.x;
-    const unsigned pm = prefix_mask(hv, p, xs[r]);
-    float2 a0 = lq0[r * 2], a1 = lq0[r * 2 + 1];                  // qubit 2p: a = 0, 1
-    float2 b00 = lq1[r * 2], b01 = lq1[r * 2 + 1];                // qubit 2p+1 given a = 0: b = 0, 1
-    float2 b10 = lq1[2 * R + r * 2], b11 = lq1[2 * R + r * 2 + 1];  // given a = 1
-    if (p < hv.mu_lv) {
-      // v = a + 2b: a allowed if (a, 0) or (a, 1) is; b given a if (a, b) is
-      mask2(a0, a1, ((pm | (pm >> 2)) & 1u) | (((pm >> 1) | (pm >> 3)) & 1u) << 1);
-      mask2(b00, b01, (pm & 1u) | ((pm >> 2) & 1u) << 1);
-      mask2(b10, b11, ((pm >> 1) & 1u) | ((pm >> 3) & 1u) << 1);
+struct Tile {
+  static constexpr int TR = 4096 / W;    // rows per tile
+  static constexpr int NTX = W / 4;      // GEMM thread grid: NTX x NTY threads, 4 units x 4 rows each
+  static constexpr int NTY = TR / 4;
+  static constexpr int WS = W + 1;       // W2 row stride (float2)
+  static constexpr int HS = TR + 1;      // h row stride (float2)
+  static constexpr int KP = 128 / TR;    // k-parts of the head reduction
+  static constexpr int NZ = 3;           // evaluations kept for a slot (qubit 2p, qubit 2p+1 for a = 0, 1)
+  static constexpr size_t smem_floats2 = size_t(W) * WS + size_t(W) * HS + size_t(KP) * TR * 2 + size_t(NZ) * TR * 2;
+  static constexpr size_t smem_bytes = smem_floats2 * sizeof(float2);
+  static_assert(NTX * NTY == NT && TR * W == 4096, "tile shape");
+};
+
+struct TileSmem {
+  float2 *W2s, *H, *Z3p, *Z3;
+};
+
+template <int W>
+__device__ __forceinline__ TileSmem tile_smem(float2* base) {
+  using T = Tile<W>;
+  TileSmem s;
+  s.W2s = base;
+  s.H = s.W2s + size_t(W) * T::WS;
+  s.Z3p = s.H + size_t(W) * T::HS;
+  s.Z3 = s.Z3p + size_t(T::KP) * T::TR * 2;
+  return s;
+}
+
+// z3 of qubit i for the tile's rows into z3out[r][2].  Bit k < i of row r is
+// bit k of xt[r] for k < kx and `a` for k = kx (kx = i: all bits from x).
+// `staged` is the qubit whose W2 is in shared memory (uniform over the CTA).
+// Starts and ends with the CTA synchronised.
+template <int W>
+__device__ void eval_qubit(const NadeView& m, int i, int kx, int a, const uint64_t* xt, const TileSmem& S,
+                           float2* z3out, int& staged) {
+  using T = Tile<W>;
+  constexpr int TR = T::TR, WS = T::WS, HS = T::HS, NTX = T::NTX;
+  const int tid = threadIdx.x;
+  const QubitPtr q = qubit_ptrs(m, i);
+  if (staged != i) {  // W2 [u][k] -> W2s[u][k] (coalesced, conflict-free)
+    for (int e = tid; e < W * W; e += NT) S.W2s[(e / W) * WS + (e % W)] = __ldg(q.W2 + e);
+    staged = i;
+  }
+  {  // z1 (float-float) and tanh: lanes of a warp share the unit u and take consecutive rows
+    const int r = tid % TR;
+    const uint64_t x = xt[r];
+    for (int u = tid / TR; u < W; u += NT / TR) {
+      float2 z = __ldg(q.b1 + u), lo = make_float2(0.f, 0.f);
+      for (int k = 0; k < i; ++k) {
+        const int bit = k < kx ? int((x >> k) & 1ull) : a;
+        if (bit) {
+          const float2 wv = __ldg(q.W1 + size_t(u) * i + k);
+          float ex, ey;
+          z.x = two_sum(z.x, wv.x, ex);
+          z.y = two_sum(z.y, wv.y, ey);
+          lo.x += ex;
+          lo.y += ey;
+        }
+      }
+      S.H[u * HS + r] = ctanh(z.x, lo.x, z.y, lo.y);
     }
-    const float2 t[4] = {make_float2(a0.x + b00.x, a0.y + b00.y), make_float2(a1.x + b10.x, a1.y + b10.y),
-                         make_float2(a0.x + b01.x, a0.y + b01.y), make_float2(a1.x + b11.x, a1.y + b11.y)};
-    for (int v = 0; v < 4; ++v) {
-      o8[r * 8 + v] = 2.f * t[v].x;
-      o8[r * 8 + 4 + v] = t[v].y;
+  }
+  __syncthreads();
+  // z2[r][u] = sum_k W2[u][k] h1[r][k]: thread (tx, ty) owns units tx + NTX c and rows 4 ty + j
+  const int tx = tid % NTX, ty = tid / NTX;
+  float2 acc[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[j][c] = make_float2(0.f, 0.f);
+#pragma unroll 2
+  for (int k = 0; k < W; ++k) {
+    float2 w[4], h[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) w[c] = S.W2s[(tx + NTX * c) * WS + k];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = S.H[k * HS + 4 * ty + j];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) cmac(acc[j][c], w[c], h[j]);
+  }
+  __syncthreads();  // h1 fully consumed: h2 overwrites it
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int u = tx + NTX * c;
+    const float2 b = __ldg(q.b2 + u);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      S.H[u * HS + 4 * ty + j] = make_float2(lerelu(acc[j][c].x + b.x), lerelu(acc[j][c].y + b.y));
+  }
+  __syncthreads();
+  {  // head: z3[r][o] = b3[o] + sum_k W3[o][k] h2[r][k], the k range in KP parts
+    constexpr int KL = W / T::KP;
+    const int r = tid % TR, g = tid / TR, o = g & 1, part = g >> 1;
+    float2 z = make_float2(0.f, 0.f);
+    for (int k = part * KL; k < (part + 1) * KL; ++k) cmac(z, __ldg(q.W3 + o * W + k), S.H[k * HS + r]);
+    S.Z3p[(part * TR + r) * 2 + o] = z;
+  }
+  __syncthreads();
+  if (tid < 2 * TR) {
+    const int r = tid >> 1, o = tid & 1;
+    float2 z = __ldg(q.b3 + o);
+    for (int part = 0; part < T::KP; ++part) {
+      const float2 t = S.Z3p[(part * TR + r) * 2 + o];
+      z.x += t.x;
+      z.y += t.y;
     }
+    z3out[r * 2 + o] = z;
   }
   __syncthreads();
 }
 
-// NADE_LOGPSI: log psi of rows x (masked log-softmax over each slot's
-// normalising set, -inf outside the sector); NADE_LOGITS: the 8 values of
-// slot p for the sampler's prefixes.
-template <int W>
-__global__ void __launch_bounds__(NT) nade_kernel(NadeView m, HamView hv, const uint64_t* __restrict__ xs, Count rows_,
-                                                  int mode, int p_one, float* __restrict__ la_out,
-                                                  float* __restrict__ ph_out, float* __restrict__ out8) {
+// Masked path term of qubit i of row x from its z3 = (z0, z1): (Re, Im) of
+// log psi_i(x_i | x_<i) after masking; false when x_i (or, at the slot's
+// second qubit, the slot outcome) is not allowed.
+__device__ __forceinline__ bool path_term(const HamView& hv, int i, uint64_t x, float2 z0, float2 z1, float& tre,
+                                          float& tim) {
+  const int p = i >> 1, xi = int((x >> i) & 1ull);
+  const unsigned pm = prefix_mask(hv, p, x);
+  const unsigned allowed = qubit_allowed(hv, i, x, pm);
+  tim = xi ? z1.y : z0.y;
+  if (!((allowed >> xi) & 1u)) return false;
+  if ((i & 1) && !((pm >> int((x >> (2 * p)) & 3ull)) & 1u)) return false;
+  const float r0 = (allowed & 1u) ? 2.f * z0.x : -INFINITY;
+  const float r1 = (allowed & 2u) ? 2.f * z1.x : -INFINITY;
+  const float mx = fmaxf(r0, r1);
+  tre = (xi ? z1.x : z0.x) - 0.5f * (mx + logf(expf(r0 - mx) + expf(r1 - mx)));
+  return true;
+}
+
+// The 8 values of slot p for row r from the three evaluations in Z3
+// ([3][TR][2]: qubit 2p, qubit 2p+1 given a = 0, given a = 1).
+__device__ void slot_values(const HamView& hv, int p, uint64_t x, const float2* Z3, int r, int TR, float* o8) {
+  float2 l[3][2];
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {  // f3
+    const float2 z0 = Z3[(e * TR + r) * 2], z1 = Z3[(e * TR + r) * 2 + 1];
+    const float mx = fmaxf(2.f * z0.x, 2.f * z1.x);
+    const float lse = 0.5f * (mx + logf(expf(2.f * z0.x - mx) + expf(2.f * z1.x - mx)));
+    l[e][0] = make_float2(z0.x - lse, z0.y);
+    l[e][1] = make_float2(z1.x - lse, z1.y);
+  }
+  if (p < hv.mu_lv) {  // v = a + 2b: a allowed if (a, 0) or (a, 1) is; b given a if (a, b) is
+    const unsigned pm = prefix_mask(hv, p, x);
+    mask2(l[0][0], l[0][1], ((pm | (pm >> 2)) & 1u) | (((pm >> 1) | (pm >> 3)) & 1u) << 1);
+    mask2(l[1][0], l[1][1], (pm & 1u) | ((pm >> 2) & 1u) << 1);
+    mask2(l[2][0], l[2][1], ((pm >> 1) & 1u) | ((pm >> 3) & 1u) << 1);
+  }
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    const int a = v & 1, b = v >> 1;
+    o8[v] = 2.f * (l[0][a].x + l[1 + a][b].x);
+    o8[4 + v] = l[0][a].y + l[1 + a][b].y;
+  }
+}
+
+enum { MODE_LOGPSI = 0, MODE_RAW = 1, MODE_SUFFIX = 2, MODE_LOGITS = 3 };
+
+struct FwdArgs {
+  const uint64_t* x;        // rows (LOGPSI, RAW, LOGITS) or connected determinants (SUFFIX)
+  Count rows;               // row count (SUFFIX: bound on the connected rows; the count is offsets[n - 1])
+  int p;                    // LOGITS: the slot
+  float *la, *ph;           // LOGPSI: outputs
+  float* out8;              // RAW: [row][n][8]; LOGITS: [row][8]
+  const uint8_t* js;        // SUFFIX: first differing slot of each connected row
+  const uint32_t* perm;     // SUFFIX: connected rows in ascending js
+  const uint32_t* offsets;  // SUFFIX: offsets[p] = rows with js < p
+  float2* T;                // SUFFIX: [row][n] path terms of the slots > js
+};
+
+template <int W, int MODE>
+__global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, FwdArgs A) {
   ANQS_PDL_ENTRY();
-  constexpr int R = NT / W;
-  __shared__ float2 h1[R * W], h2[R * W], lq[6 * R];
-  __shared__ float o8[R * 8];
-  __shared__ uint64_t xt[R];
-  const uint64_t rows = rows_.get();
-  for (uint64_t base = uint64_t(blockIdx.x) * R; base < rows; base += uint64_t(gridDim.x) * R) {
-    if (threadIdx.x < R) xt[threadIdx.x] = base + threadIdx.x < rows ? xs[base + threadIdx.x] : 0ull;
-    __syncthreads();
-    if (mode == NADE_LOGITS) {
-      nade_slot<W>(m, hv, p_one, xt, h1, h2, lq, o8);
-      if (threadIdx.x < R * 8 && base + threadIdx.x / 8 < rows) out8[base * 8 + threadIdx.x] = o8[threadIdx.x];
-      __syncthreads();
-      continue;
+  constexpr int TR = Tile<W>::TR;
+  extern __shared__ float2 dsm[];
+  const TileSmem S = tile_smem<W>(dsm);
+  __shared__ uint64_t xt[TR];
+  __shared__ float la[TR], ph[TR], t0r[TR], t0i[TR];
+  __shared__ int dead[TR], jr[TR];
+  __shared__ uint32_t rid[TR];
+  const int n = m.n, tid = threadIdx.x;
+  const uint64_t rows = MODE == MODE_SUFFIX ? uint64_t(A.offsets[n - 1]) : A.rows.get();
+  int staged = -1;
+  for (uint64_t base = uint64_t(blockIdx.x) * TR; base < rows; base += uint64_t(gridDim.x) * TR) {
+    if (tid < TR) {
+      const uint64_t l = base + tid;
+      const bool valid = l < rows;
+      if (MODE == MODE_SUFFIX) {
+        const uint32_t row = valid ? A.perm[l] : 0u;
+        rid[tid] = row;
+        jr[tid] = valid ? int(A.js[row]) : n;  // j = n: no slot of the row is written
+        xt[tid] = valid ? A.x[row] : 0ull;
+      } else {
+        xt[tid] = valid ? A.x[l] : 0ull;
+      }
+      la[tid] = 0.f;
+      ph[tid] = 0.f;
+      dead[tid] = 0;
     }
-    float la = 0.f, ph = 0.f;
-    bool dead = false;
-    for (int p = 0; p < m.n; ++p) {
-      nade_slot<W>(m, hv, p, xt, h1, h2, lq, o8);
-      if (threadIdx.x < R) {
-        const uint64_t x = xt[threadIdx.x];
-        const unsigned pm = prefix_mask(hv, p, x);
-        const unsigned nm = norm_mask(hv, p, pm);
-        const int v = int((x >> (2 * p)) & 3ull);
-        const float* o = o8 + threadIdx.x * 8;
-        if (!((pm >> v) & 1u)) {
-          dead = true;
-        } else {
-          float mx = -INFINITY;
-          for (int u = 0; u < 4; ++u)
-            if ((nm >> u) & 1u) mx = fmaxf(mx, o[u]);
-          float s = 0.f;
-          for (int u = 0; u < 4; ++u)
-            if ((nm >> u) & 1u) s += expf(o[u] - mx);
-          la += 0.5f * (o[v] - mx - logf(s));
+    __syncthreads();
+    if (MODE == MODE_LOGPSI) {
+      for (int i = 0; i < 2 * n; ++i) {
+        eval_qubit<W>(m, i, i, 0, xt, S, S.Z3, staged);
+        if (tid < TR) {
+          float tr = 0.f, ti;
+          if (path_term(hv, i, xt[tid], S.Z3[tid * 2], S.Z3[tid * 2 + 1], tr, ti)) la[tid] += tr;
+          else dead[tid] = 1;
+          ph[tid] += ti;
         }
-        ph += o[4 + v];
       }
       __syncthreads();
-    }
-    if (threadIdx.x < R && base + threadIdx.x < rows) {
-      const uint64_t x = xt[threadIdx.x];
-      const bool out = dead || (hv.n < 32 && (x >> (2 * hv.n)) != 0);
-      la_out[base + threadIdx.x] = out ? -INFINITY : la;
-      ph_out[base + threadIdx.x] = ph;
+      if (tid < TR && base + tid < rows) {
+        const uint64_t x = xt[tid];
+        const bool out = dead[tid] || (n < 32 && (x >> (2 * n)) != 0);
+        A.la[base + tid] = out ? -INFINITY : la[tid];
+        A.ph[base + tid] = ph[tid];
+      }
+    } else if (MODE == MODE_SUFFIX) {
+      // rows are in ascending j: the tile's first row has the smallest, and
+      // every row needs the slots above its own j only
+      for (int i = 2 * (jr[0] + 1); i < 2 * n; ++i) {
+        eval_qubit<W>(m, i, i, 0, xt, S, S.Z3, staged);
+        const int p = i >> 1;
+        if (tid < TR && p > jr[tid]) {
+          float tr = 0.f, ti;
+          const bool ok = path_term(hv, i, xt[tid], S.Z3[tid * 2], S.Z3[tid * 2 + 1], tr, ti);
+          if ((i & 1) == 0) {
+            t0r[tid] = ok ? tr : -INFINITY;
+            t0i[tid] = ti;
+          } else {
+            A.T[uint64_t(rid[tid]) * n + p] = make_float2(ok ? t0r[tid] + tr : -INFINITY, t0i[tid] + ti);
+          }
+        }
+      }
+    } else {  // RAW, LOGITS
+      const int p_lo = MODE == MODE_RAW ? 0 : A.p, p_hi = MODE == MODE_RAW ? n : A.p + 1;
+      for (int p = p_lo; p < p_hi; ++p) {
+        eval_qubit<W>(m, 2 * p, 2 * p, 0, xt, S, S.Z3, staged);
+        eval_qubit<W>(m, 2 * p + 1, 2 * p, 0, xt, S, S.Z3 + 2 * TR, staged);
+        eval_qubit<W>(m, 2 * p + 1, 2 * p, 1, xt, S, S.Z3 + 4 * TR, staged);
+        if (tid < TR && base + tid < rows) {
+          float o8[8];
+          slot_values(hv, p, xt[tid], S.Z3, tid, TR, o8);
+          float* dst = MODE == MODE_RAW ? A.out8 + ((base + tid) * n + p) * 8 : A.out8 + (base + tid) * 8;
+#pragma unroll
+          for (int v = 0; v < 8; ++v) dst[v] = o8[v];
+        }
+      }
     }
     __syncthreads();
   }
 }
 
-template <int W>
-int launch_w(const NadeView& m, const HamView& hv, const uint64_t* x, Count rows, int mode, int p, float* la,
-             float* ph, float* out8, cudaStream_t s) {
-  constexpr int R = NT / W;
-  uint64_t blocks = (rows.n + R - 1) / R;
-  if (blocks > 152ull * 8) blocks = 152ull * 8;
-  ProfScope ps(PROF_NADE, s);
-  ANQS_CUDA_LAUNCH("nade_kernel", launch_k(nade_kernel<W>, dim3(unsigned(blocks ? blocks : 1)), dim3(NT), 0, s, m, hv,
-                                           x, rows, mode, p, la, ph, out8));
+template <int W, int MODE>
+int fwd_launch(const NadeView& m, const HamView& hv, const FwdArgs& a, uint64_t max_rows, int prof, cudaStream_t s) {
+  constexpr int TR = Tile<W>::TR;
+  const size_t smem = Tile<W>::smem_bytes;
+  auto kern = nade_fwd_kernel<W, MODE>;
+  ANQS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+  int occ = 0;
+  ANQS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
+  const uint64_t cap = 152ull * uint64_t(occ > 0 ? occ : 1);
+  uint64_t blocks = (max_rows + TR - 1) / TR;
+  if (blocks > cap) blocks = cap;
+  ProfScope ps(prof, s);
+  ANQS_CUDA_LAUNCH("nade_fwd_kernel", launch_k(kern, dim3(unsigned(blocks ? blocks : 1)), dim3(NT), smem, s, m, hv, a));
   return ANQS_OK;
 }
 
-int launch(const NadeView& m, const HamView& hv, const uint64_t* x, Count rows, int mode, int p, float* la, float* ph,
-           float* out8, cudaStream_t s) {
+template <int MODE>
+int fwd(const NadeView& m, const HamView& hv, const FwdArgs& a, uint64_t max_rows, int prof, cudaStream_t s) {
   switch (m.w) {
-    case 32: return launch_w<32>(m, hv, x, rows, mode, p, la, ph, out8, s);
-    case 64: return launch_w<64>(m, hv, x, rows, mode, p, la, ph, out8, s);
-    case 128: return launch_w<128>(m, hv, x, rows, mode, p, la, ph, out8, s);
+    case 32: return fwd_launch<32, MODE>(m, hv, a, max_rows, prof, s);
+    case 64: return fwd_launch<64, MODE>(m, hv, a, max_rows, prof, s);
+    case 128: return fwd_launch<128, MODE>(m, hv, a, max_rows, prof, s);
   }
   return set_error(ANQS_ERR_UNSUPPORTED, "NADE width %d", m.w);
+}
+
+// workspace of the local energy with prefix reuse
+struct NadeElocWs {
+  uint64_t* xp;
+  double *hv, *hd;
+  uint8_t* js;
+  float *la_x, *ph_x, *raw, *cache;
+  float2* T;
+  uint32_t *perm, *hist, *cursor, *offsets;
+};
+
+size_t plan_eloc(const anqs_ham* H, uint64_t n_x, Arena& A, NadeElocWs& w) {
+  const uint64_t m = n_x * H->v.K, n = uint64_t(H->v.n);
+  w.xp = A.take<uint64_t>(m);
+  w.hv = A.take<double>(m);
+  w.js = A.take<uint8_t>(m);
+  w.hd = A.take<double>(n_x);
+  w.la_x = A.take<float>(n_x);
+  w.ph_x = A.take<float>(n_x);
+  w.raw = A.take<float>(n_x * n * 8);
+  w.cache = A.take<float>(n_x * n * TC_CACHE_F);
+  w.T = A.take<float2>(m * n);
+  w.perm = A.take<uint32_t>(m);
+  w.hist = A.take<uint32_t>(ANQS_MAX_ORB);
+  w.cursor = A.take<uint32_t>(ANQS_MAX_ORB);
+  w.offsets = A.take<uint32_t>(ANQS_MAX_ORB + 1);
+  return A.off;
 }
 
 }  // namespace
@@ -260,12 +437,71 @@ int launch(const NadeView& m, const HamView& hv, const uint64_t* x, Count rows, 
 int launch_nade_logpsi(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, float* la, float* ph,
                        cudaStream_t s) {
   if (n_x.n == 0) return ANQS_OK;
-  return launch(m, hv, x, n_x, NADE_LOGPSI, 0, la, ph, nullptr, s);
+  FwdArgs a{};
+  a.x = x;
+  a.rows = n_x;
+  a.la = la;
+  a.ph = ph;
+  return fwd<MODE_LOGPSI>(m, hv, a, n_x.n, PROF_NADE, s);
 }
 
 int launch_nade_slot_logits(const NadeView& m, const HamView& hv, int p, const uint64_t* pre, const uint64_t* n_dev,
                             uint64_t max_rows, float* out8, cudaStream_t s) {
-  return launch(m, hv, pre, Count{max_rows, n_dev, 1}, NADE_LOGITS, p, nullptr, nullptr, out8, s);
+  FwdArgs a{};
+  a.x = pre;
+  a.rows = Count{max_rows, n_dev, 1};
+  a.p = p;
+  a.out8 = out8;
+  return fwd<MODE_LOGITS>(m, hv, a, max_rows, PROF_NADE_SLOT, s);
+}
+
+size_t nade_eloc_workspace(const anqs_ham* H, uint64_t n_x) {
+  Arena A(nullptr, 0);
+  NadeElocWs w;
+  return plan_eloc(H, n_x, A, w);
+}
+
+// Local energy with prefix reuse: the parents' slot values (RAW) give log psi(x)
+// and, per slot, the prefix sums and the slot's masked terms; each connected
+// x' then needs only the path terms of the slots above its first differing
+// slot j (SUFFIX, rows sorted by j); the assembly adds them up and sums
+// H_xx' psi(x')/psi(x) in FP64.
+int run_eloc_nade(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,
+                  void* ws, size_t ws_bytes, cudaStream_t s) {
+  Arena A(ws, ws_bytes);
+  NadeElocWs w;
+  plan_eloc(H, n_x.n, A, w);
+  if (!A.fits() || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", A.off);
+  const uint64_t K = H->v.K;
+  const Count mc = scaled(n_x, K);
+  if (mc.n > 0xffffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "more than 2^32 connected determinants per call");
+  ANQS_TRY(launch_connected(H->v, x, n_x, w.xp, w.hv, w.js, w.hd, s));
+  {
+    FwdArgs a{};
+    a.x = x;
+    a.rows = n_x;
+    a.out8 = w.raw;
+    ANQS_TRY(fwd<MODE_RAW>(M->nade, H->v, a, n_x.n, PROF_NADE_PARENT, s));
+    ProfScope ps(PROF_TC_FINALIZE, s);
+    ANQS_TRY(launch_tc_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
+  }
+  {
+    ProfScope ps(PROF_TC_SORT, s);
+    ANQS_TRY(launch_js_sort(w.js, mc, H->v.n, w.hist, w.cursor, w.offsets, w.perm, s));
+  }
+  {
+    FwdArgs a{};
+    a.x = w.xp;
+    a.rows = mc;
+    a.js = w.js;
+    a.perm = w.perm;
+    a.offsets = w.offsets;
+    a.T = w.T;
+    ANQS_TRY(fwd<MODE_SUFFIX>(M->nade, H->v, a, mc.n, PROF_NADE_SUFFIX, s));
+  }
+  ProfScope ps(PROF_TC_ELOC, s);
+  return launch_eloc_assemble(H->v.n, uint32_t(K), n_x, w.xp, w.js, w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x, ere, eim,
+                              s);
 }
 
 // ---------------------------------------------------------------------------

@@ -31,7 +31,8 @@ const char* kNames[PROF_COUNT] = {
     "tc_sort_kernels",        "eloc_assemble_kernel", "mlp_tc_slot_kernel",     "tf_fp32_kernel",
     "finalize_kernel",        "grad_partial_sum_kernel", "unused",              "tf_fp32_grad_kernels",
     "tf_tc_parent_kernel",    "tf_tc_suffix_kernel",  "tf_tc_slot_kernel",
-    "nade_kernel", "nade_grad_kernel"};
+    "nade_logpsi_kernel", "nade_grad_kernel", "nade_slot_kernel",
+    "nade_parent_kernel",    "nade_suffix_kernel"};
 
 cudaEvent_t get_event() {
   if (!g_pool.empty()) {
