@@ -18,11 +18,13 @@
 // slot (qubit 2p+1 for both values of qubit 2p).
 //
 // Tile engine: a CTA of 256 threads evaluates one qubit for a tile of
-// TR = 4096 / W rows.  The W2 product, the bulk of the work, is a complex
+// TR = RJ * 1024 / W rows.  The W2 product, the bulk of the work, is a complex
 // GEMM [TR x W] x [W x W]^T run from shared memory (W2 with row stride W + 1,
-// h1 transposed with row stride TR + 1) with a 4 x 4 register tile of
-// (row, unit) accumulators per thread; the input layer, tanh, LeReLU and the
-// 2-output head are elementwise or short reductions around it.
+// h1 transposed with row stride TR + 1) with a register tile of RJ rows x 4
+// units per thread; the input layer, tanh, LeReLU and the 2-output head are
+// elementwise or short reductions around it.  RJ = 4 for launches with
+// enough rows to fill the GPU, RJ = 1 (4x smaller tiles, 4x more CTAs) for
+// the latency-bound small ones (sampler levels, parent passes).
 //
 // Modes: LOGPSI (log psi of rows, path qubits only), RAW (the 8 slot values
 // of every slot of every row: the parent pass of the local energy), SUFFIX
@@ -123,27 +125,27 @@ __device__ __forceinline__ void cmac(float2& acc, float2 w, float2 h) {
 // ---------------------------------------------------------------------------
 // Tile engine
 // ---------------------------------------------------------------------------
-template <int W>
+template <int W, int RJ>
 struct Tile {
-  static constexpr int TR = 4096 / W;    // rows per tile
-  static constexpr int NTX = W / 4;      // GEMM thread grid: NTX x NTY threads, 4 units x 4 rows each
-  static constexpr int NTY = TR / 4;
+  static constexpr int NTX = W / 4;      // GEMM thread grid: NTX x NTY threads, 4 units x RJ rows each
+  static constexpr int NTY = NT / NTX;
+  static constexpr int TR = NTY * RJ;    // rows per tile
   static constexpr int WS = W + 1;       // W2 row stride (float2)
   static constexpr int HS = TR + 1;      // h row stride (float2)
   static constexpr int KP = 128 / TR;    // k-parts of the head reduction
   static constexpr int NZ = 3;           // evaluations kept for a slot (qubit 2p, qubit 2p+1 for a = 0, 1)
   static constexpr size_t smem_floats2 = size_t(W) * WS + size_t(W) * HS + size_t(KP) * TR * 2 + size_t(NZ) * TR * 2;
   static constexpr size_t smem_bytes = smem_floats2 * sizeof(float2);
-  static_assert(NTX * NTY == NT && TR * W == 4096, "tile shape");
+  static_assert(NTX * NTY == NT && NT % TR == 0 && W % KP == 0, "tile shape");
 };
 
 struct TileSmem {
   float2 *W2s, *H, *Z3p, *Z3;
 };
 
-template <int W>
+template <int W, int RJ>
 __device__ __forceinline__ TileSmem tile_smem(float2* base) {
-  using T = Tile<W>;
+  using T = Tile<W, RJ>;
   TileSmem s;
   s.W2s = base;
   s.H = s.W2s + size_t(W) * T::WS;
@@ -156,10 +158,10 @@ __device__ __forceinline__ TileSmem tile_smem(float2* base) {
 // bit k of xt[r] for k < kx and `a` for k = kx (kx = i: all bits from x).
 // `staged` is the qubit whose W2 is in shared memory (uniform over the CTA).
 // Starts and ends with the CTA synchronised.
-template <int W>
+template <int W, int RJ>
 __device__ void eval_qubit(const NadeView& m, int i, int kx, int a, const uint64_t* xt, const TileSmem& S,
                            float2* z3out, int& staged) {
-  using T = Tile<W>;
+  using T = Tile<W, RJ>;
   constexpr int TR = T::TR, WS = T::WS, HS = T::HS, NTX = T::NTX;
   const int tid = threadIdx.x;
   const QubitPtr q = qubit_ptrs(m, i);
@@ -187,22 +189,22 @@ __device__ void eval_qubit(const NadeView& m, int i, int kx, int a, const uint64
     }
   }
   __syncthreads();
-  // z2[r][u] = sum_k W2[u][k] h1[r][k]: thread (tx, ty) owns units tx + NTX c and rows 4 ty + j
+  // z2[r][u] = sum_k W2[u][k] h1[r][k]: thread (tx, ty) owns units tx + NTX c and rows RJ ty + j
   const int tx = tid % NTX, ty = tid / NTX;
-  float2 acc[4][4];
+  float2 acc[RJ][4];
 #pragma unroll
-  for (int j = 0; j < 4; ++j)
+  for (int j = 0; j < RJ; ++j)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[j][c] = make_float2(0.f, 0.f);
 #pragma unroll 2
   for (int k = 0; k < W; ++k) {
-    float2 w[4], h[4];
+    float2 w[4], h[RJ];
 #pragma unroll
     for (int c = 0; c < 4; ++c) w[c] = S.W2s[(tx + NTX * c) * WS + k];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) h[j] = S.H[k * HS + 4 * ty + j];
+    for (int j = 0; j < RJ; ++j) h[j] = S.H[k * HS + RJ * ty + j];
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < RJ; ++j)
 #pragma unroll
       for (int c = 0; c < 4; ++c) cmac(acc[j][c], w[c], h[j]);
   }
@@ -212,8 +214,8 @@ __device__ void eval_qubit(const NadeView& m, int i, int kx, int a, const uint64
     const int u = tx + NTX * c;
     const float2 b = __ldg(q.b2 + u);
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
-      S.H[u * HS + 4 * ty + j] = make_float2(lerelu(acc[j][c].x + b.x), lerelu(acc[j][c].y + b.y));
+    for (int j = 0; j < RJ; ++j)
+      S.H[u * HS + RJ * ty + j] = make_float2(lerelu(acc[j][c].x + b.x), lerelu(acc[j][c].y + b.y));
   }
   __syncthreads();
   {  // head: z3[r][o] = b3[o] + sum_k W3[o][k] h2[r][k], the k range in KP parts
@@ -295,12 +297,12 @@ struct FwdArgs {
   float2* T;                // SUFFIX: [row][n] path terms of the slots > js
 };
 
-template <int W, int MODE>
+template <int W, int RJ, int MODE>
 __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, FwdArgs A) {
   ANQS_PDL_ENTRY();
-  constexpr int TR = Tile<W>::TR;
+  constexpr int TR = Tile<W, RJ>::TR;
   extern __shared__ float2 dsm[];
-  const TileSmem S = tile_smem<W>(dsm);
+  const TileSmem S = tile_smem<W, RJ>(dsm);
   __shared__ uint64_t xt[TR];
   __shared__ float la[TR], ph[TR], t0r[TR], t0i[TR];
   __shared__ int dead[TR], jr[TR];
@@ -327,7 +329,7 @@ __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, Fw
     __syncthreads();
     if (MODE == MODE_LOGPSI) {
       for (int i = 0; i < 2 * n; ++i) {
-        eval_qubit<W>(m, i, i, 0, xt, S, S.Z3, staged);
+        eval_qubit<W, RJ>(m, i, i, 0, xt, S, S.Z3, staged);
         if (tid < TR) {
           float tr = 0.f, ti;
           if (path_term(hv, i, xt[tid], S.Z3[tid * 2], S.Z3[tid * 2 + 1], tr, ti)) la[tid] += tr;
@@ -346,7 +348,7 @@ __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, Fw
       // rows are in ascending j: the tile's first row has the smallest, and
       // every row needs the slots above its own j only
       for (int i = 2 * (jr[0] + 1); i < 2 * n; ++i) {
-        eval_qubit<W>(m, i, i, 0, xt, S, S.Z3, staged);
+        eval_qubit<W, RJ>(m, i, i, 0, xt, S, S.Z3, staged);
         const int p = i >> 1;
         if (tid < TR && p > jr[tid]) {
           float tr = 0.f, ti;
@@ -359,12 +361,12 @@ __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, Fw
           }
         }
       }
-    } else {  // RAW, LOGITS
-      const int p_lo = MODE == MODE_RAW ? 0 : A.p, p_hi = MODE == MODE_RAW ? n : A.p + 1;
+    } else {  // RAW (slot blockIdx.y), LOGITS (slot A.p)
+      const int p_lo = MODE == MODE_RAW ? int(blockIdx.y) : A.p, p_hi = p_lo + 1;
       for (int p = p_lo; p < p_hi; ++p) {
-        eval_qubit<W>(m, 2 * p, 2 * p, 0, xt, S, S.Z3, staged);
-        eval_qubit<W>(m, 2 * p + 1, 2 * p, 0, xt, S, S.Z3 + 2 * TR, staged);
-        eval_qubit<W>(m, 2 * p + 1, 2 * p, 1, xt, S, S.Z3 + 4 * TR, staged);
+        eval_qubit<W, RJ>(m, 2 * p, 2 * p, 0, xt, S, S.Z3, staged);
+        eval_qubit<W, RJ>(m, 2 * p + 1, 2 * p, 0, xt, S, S.Z3 + 2 * TR, staged);
+        eval_qubit<W, RJ>(m, 2 * p + 1, 2 * p, 1, xt, S, S.Z3 + 4 * TR, staged);
         if (tid < TR && base + tid < rows) {
           float o8[8];
           slot_values(hv, p, xt[tid], S.Z3, tid, TR, o8);
@@ -378,28 +380,41 @@ __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, Fw
   }
 }
 
-template <int W, int MODE>
+// Grid: ny slots (RAW: one per slot) x row tiles, at most one wave of
+// resident CTAs.  RJ = 4 when its tiles fill a wave, else RJ = 1.
+template <int W, int RJ, int MODE>
 int fwd_launch(const NadeView& m, const HamView& hv, const FwdArgs& a, uint64_t max_rows, int prof, cudaStream_t s) {
-  constexpr int TR = Tile<W>::TR;
-  const size_t smem = Tile<W>::smem_bytes;
-  auto kern = nade_fwd_kernel<W, MODE>;
+  constexpr int TR = Tile<W, RJ>::TR;
+  const size_t smem = Tile<W, RJ>::smem_bytes;
+  auto kern = nade_fwd_kernel<W, RJ, MODE>;
   ANQS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   int occ = 0;
   ANQS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
-  const uint64_t cap = 152ull * uint64_t(occ > 0 ? occ : 1);
+  const uint64_t ny = MODE == MODE_RAW ? uint64_t(m.n) : 1;
+  uint64_t cap = 152ull * uint64_t(occ > 0 ? occ : 1) / ny;
+  if (cap < 1) cap = 1;
   uint64_t blocks = (max_rows + TR - 1) / TR;
   if (blocks > cap) blocks = cap;
   ProfScope ps(prof, s);
-  ANQS_CUDA_LAUNCH("nade_fwd_kernel", launch_k(kern, dim3(unsigned(blocks ? blocks : 1)), dim3(NT), smem, s, m, hv, a));
+  ANQS_CUDA_LAUNCH("nade_fwd_kernel", launch_k(kern, dim3(unsigned(blocks ? blocks : 1), unsigned(ny)), dim3(NT), smem,
+                                               s, m, hv, a));
   return ANQS_OK;
+}
+
+template <int W, int MODE>
+int fwd_w(const NadeView& m, const HamView& hv, const FwdArgs& a, uint64_t max_rows, int prof, cudaStream_t s) {
+  const uint64_t ny = MODE == MODE_RAW ? uint64_t(m.n) : 1;
+  const uint64_t big_tiles = (max_rows + Tile<W, 4>::TR - 1) / Tile<W, 4>::TR;
+  if (big_tiles * ny >= 152) return fwd_launch<W, 4, MODE>(m, hv, a, max_rows, prof, s);
+  return fwd_launch<W, 1, MODE>(m, hv, a, max_rows, prof, s);
 }
 
 template <int MODE>
 int fwd(const NadeView& m, const HamView& hv, const FwdArgs& a, uint64_t max_rows, int prof, cudaStream_t s) {
   switch (m.w) {
-    case 32: return fwd_launch<32, MODE>(m, hv, a, max_rows, prof, s);
-    case 64: return fwd_launch<64, MODE>(m, hv, a, max_rows, prof, s);
-    case 128: return fwd_launch<128, MODE>(m, hv, a, max_rows, prof, s);
+    case 32: return fwd_w<32, MODE>(m, hv, a, max_rows, prof, s);
+    case 64: return fwd_w<64, MODE>(m, hv, a, max_rows, prof, s);
+    case 128: return fwd_w<128, MODE>(m, hv, a, max_rows, prof, s);
   }
   return set_error(ANQS_ERR_UNSUPPORTED, "NADE width %d", m.w);
 }
