@@ -55,8 +55,8 @@ __device__ __forceinline__ float2 ctanh(float ah, float al, float bh, float bl) 
   sincosf(bh, &sb, &cb);
   const float sa1 = fmaf(ca, al, sa), ca1 = fmaf(sa, al, ca);
   const float sb1 = fmaf(cb, bl, sb), cb1 = fmaf(-sb, bl, cb);
-  const float den = fmaf(sa1, sa1, cb1 * cb1);
-  return make_float2(sa1 * ca1 / den, sb1 * cb1 / den);
+  const float inv = __frcp_rn(fmaf(sa1, sa1, cb1 * cb1));
+  return make_float2(sa1 * ca1 * inv, sb1 * cb1 * inv);
 }
 
 // s + e = a + b exactly (Knuth's TwoSum)
@@ -131,25 +131,30 @@ struct Tile {
   static constexpr int NTY = NT / NTX;
   static constexpr int TR = NTY * RJ;    // rows per tile
   static constexpr int WS = W + 1;       // W2 row stride (float2)
-  static constexpr int HS = TR + 1;      // h row stride (float2)
+  static constexpr int HS = TR + 4;      // h row stride (floats; real and imaginary planes)
   static constexpr int KP = 128 / TR;    // k-parts of the head reduction
   static constexpr int NZ = 3;           // evaluations kept for a slot (qubit 2p, qubit 2p+1 for a = 0, 1)
-  static constexpr size_t smem_floats2 = size_t(W) * WS + size_t(W) * HS + size_t(KP) * TR * 2 + size_t(NZ) * TR * 2;
-  static constexpr size_t smem_bytes = smem_floats2 * sizeof(float2);
-  static_assert(NTX * NTY == NT && NT % TR == 0 && W % KP == 0, "tile shape");
+  static constexpr size_t w2_bytes = size_t(W) * WS * sizeof(float2);
+  static constexpr size_t h_bytes = 2 * size_t(W) * HS * sizeof(float);
+  static constexpr size_t smem_bytes = w2_bytes + h_bytes + (size_t(KP) * TR * 2 + size_t(NZ) * TR * 2) * sizeof(float2);
+  static_assert(NTX * NTY == NT && NT % TR == 0 && W % KP == 0 && TR % 4 == 0, "tile shape");
 };
 
 struct TileSmem {
-  float2 *W2s, *H, *Z3p, *Z3;
+  float2* W2;        // [W][WS]: W2[u][k] at u * WS + k
+  float *Hr, *Hi;    // [W][HS]: h[r][k] at k * HS + r
+  float2 *Z3p, *Z3;
 };
 
 template <int W, int RJ>
 __device__ __forceinline__ TileSmem tile_smem(float2* base) {
   using T = Tile<W, RJ>;
   TileSmem s;
-  s.W2s = base;
-  s.H = s.W2s + size_t(W) * T::WS;
-  s.Z3p = s.H + size_t(W) * T::HS;
+  char* p = reinterpret_cast<char*>(base);
+  s.W2 = reinterpret_cast<float2*>(p);
+  s.Hr = reinterpret_cast<float*>(p + T::w2_bytes);
+  s.Hi = s.Hr + size_t(W) * T::HS;
+  s.Z3p = reinterpret_cast<float2*>(s.Hi + size_t(W) * T::HS);
   s.Z3 = s.Z3p + size_t(T::KP) * T::TR * 2;
   return s;
 }
@@ -165,48 +170,68 @@ __device__ void eval_qubit(const NadeView& m, int i, int kx, int a, const uint64
   constexpr int TR = T::TR, WS = T::WS, HS = T::HS, NTX = T::NTX;
   const int tid = threadIdx.x;
   const QubitPtr q = qubit_ptrs(m, i);
-  if (staged != i) {  // W2 [u][k] -> W2s[u][k] (coalesced, conflict-free)
-    for (int e = tid; e < W * W; e += NT) S.W2s[(e / W) * WS + (e % W)] = __ldg(q.W2 + e);
+  if (staged != i) {  // W2 [u][k] -> shared [u][k] (coalesced, conflict-free)
+    for (int e = tid; e < W * W; e += NT) S.W2[(e / W) * WS + (e % W)] = __ldg(q.W2 + e);
     staged = i;
   }
-  {  // z1 (float-float) and tanh: lanes of a warp share the unit u and take consecutive rows
+  {  // z1 and tanh: lanes of a warp take consecutive rows of one unit
     const int r = tid % TR;
-    const uint64_t x = xt[r];
+    const uint64_t xr = xt[r];
+    // the input bits x_<i of the row: x's bits below kx, then a at kx
+    const uint64_t bits0 = (kx >= 64 ? xr : (xr & ((1ull << kx) - 1ull))) | (kx < i && a ? (1ull << kx) : 0ull);
     for (int u = tid / TR; u < W; u += NT / TR) {
-      float2 z = __ldg(q.b1 + u), lo = make_float2(0.f, 0.f);
+      // Kahan-compensated sum of the selected W1 columns: z + c carries the
+      // sum to about u^2, which matters only next to a pole of tanh
+      // (the loop runs over all k < i so that the lanes, which share u, load
+      // each W1 entry together)
+      const float2* w1 = q.W1 + size_t(u) * i;
+      float2 z = __ldg(q.b1 + u), c = make_float2(0.f, 0.f);
       for (int k = 0; k < i; ++k) {
-        const int bit = k < kx ? int((x >> k) & 1ull) : a;
-        if (bit) {
-          const float2 wv = __ldg(q.W1 + size_t(u) * i + k);
-          float ex, ey;
-          z.x = two_sum(z.x, wv.x, ex);
-          z.y = two_sum(z.y, wv.y, ey);
-          lo.x += ex;
-          lo.y += ey;
-        }
+        if (!((bits0 >> k) & 1ull)) continue;
+        const float2 wv = __ldg(w1 + k);
+        const float yx = wv.x - c.x, yy = wv.y - c.y;
+        const float tx = z.x + yx, ty = z.y + yy;
+        c.x = (tx - z.x) - yx;
+        c.y = (ty - z.y) - yy;
+        z.x = tx;
+        z.y = ty;
       }
-      S.H[u * HS + r] = ctanh(z.x, lo.x, z.y, lo.y);
+      const float2 h = ctanh(z.x, -c.x, z.y, -c.y);
+      S.Hr[u * HS + r] = h.x;
+      S.Hi[u * HS + r] = h.y;
     }
   }
   __syncthreads();
   // z2[r][u] = sum_k W2[u][k] h1[r][k]: thread (tx, ty) owns units tx + NTX c and rows RJ ty + j
   const int tx = tid % NTX, ty = tid / NTX;
-  float2 acc[RJ][4];
+  float2 z2[RJ][4];
 #pragma unroll
   for (int j = 0; j < RJ; ++j)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[j][c] = make_float2(0.f, 0.f);
+    for (int c = 0; c < 4; ++c) z2[j][c] = make_float2(0.f, 0.f);
 #pragma unroll 2
   for (int k = 0; k < W; ++k) {
     float2 w[4], h[RJ];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) w[c] = S.W2s[(tx + NTX * c) * WS + k];
+    for (int c = 0; c < 4; ++c) w[c] = S.W2[(tx + NTX * c) * WS + k];
+    if constexpr (RJ % 4 == 0) {
 #pragma unroll
-    for (int j = 0; j < RJ; ++j) h[j] = S.H[k * HS + RJ * ty + j];
+      for (int j = 0; j < RJ; j += 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(S.Hr + k * HS + RJ * ty + j);
+        const float4 b4 = *reinterpret_cast<const float4*>(S.Hi + k * HS + RJ * ty + j);
+        h[j] = make_float2(a4.x, b4.x);
+        h[j + 1] = make_float2(a4.y, b4.y);
+        h[j + 2] = make_float2(a4.z, b4.z);
+        h[j + 3] = make_float2(a4.w, b4.w);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < RJ; ++j) h[j] = make_float2(S.Hr[k * HS + RJ * ty + j], S.Hi[k * HS + RJ * ty + j]);
+    }
 #pragma unroll
     for (int j = 0; j < RJ; ++j)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) cmac(acc[j][c], w[c], h[j]);
+      for (int c = 0; c < 4; ++c) cmac(z2[j][c], w[c], h[j]);
   }
   __syncthreads();  // h1 fully consumed: h2 overwrites it
 #pragma unroll
@@ -214,15 +239,18 @@ __device__ void eval_qubit(const NadeView& m, int i, int kx, int a, const uint64
     const int u = tx + NTX * c;
     const float2 b = __ldg(q.b2 + u);
 #pragma unroll
-    for (int j = 0; j < RJ; ++j)
-      S.H[u * HS + RJ * ty + j] = make_float2(lerelu(acc[j][c].x + b.x), lerelu(acc[j][c].y + b.y));
+    for (int j = 0; j < RJ; ++j) {
+      S.Hr[u * HS + RJ * ty + j] = lerelu(z2[j][c].x + b.x);
+      S.Hi[u * HS + RJ * ty + j] = lerelu(z2[j][c].y + b.y);
+    }
   }
   __syncthreads();
   {  // head: z3[r][o] = b3[o] + sum_k W3[o][k] h2[r][k], the k range in KP parts
     constexpr int KL = W / T::KP;
     const int r = tid % TR, g = tid / TR, o = g & 1, part = g >> 1;
     float2 z = make_float2(0.f, 0.f);
-    for (int k = part * KL; k < (part + 1) * KL; ++k) cmac(z, __ldg(q.W3 + o * W + k), S.H[k * HS + r]);
+    for (int k = part * KL; k < (part + 1) * KL; ++k)
+      cmac(z, __ldg(q.W3 + o * W + k), make_float2(S.Hr[k * HS + r], S.Hi[k * HS + r]));
     S.Z3p[(part * TR + r) * 2 + o] = z;
   }
   __syncthreads();
