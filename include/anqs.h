@@ -91,7 +91,8 @@ enum { ANQS_MODEL_MLP = 0, ANQS_MODEL_TF = 1, ANQS_MODEL_TABLE = 2, ANQS_MODEL_N
 
 /* Arithmetic form of a model's network evaluation.
  * FP32: plain SIMT float32 kernels, every configuration evaluated over all
- *       slots (no prefix reuse).
+ *       slots (no prefix reuse), except the NADE, whose local energy reuses
+ *       the parent's slots for its connected determinants.
  * BF16: tensor-core (tcgen05, TMEM accumulators) bfloat16 GEMMs with float32
  *       accumulation, float32 activations/softmax/phase heads, and reuse of
  *       the parent determinant's slots for its connected determinants. */

@@ -223,3 +223,57 @@ def test_nade_has_no_bf16_form(A):
     n, w = 4, 32
     with pytest.raises(A.AnqsError, match="UNSUPPORTED"):
         A.Model(A.ModelDesc(3, 1, n, w, 0, 0, 0, 0), torch.zeros(nade_param_count(n, w), device="cuda"))
+
+
+@pytest.mark.parametrize("na,nb", [(1, 0), (1, 1), (0, 1)])
+def test_nade_single_orbital(A, na, nb):
+    """n = 1: one slot (two qubits), no slot past any first differing slot,
+    a one- or two-determinant sector."""
+    n, w = 1, 32
+    ham, model, om, ip, oham = _setup(A, n, na, nb, w, seed=50)
+    st = np.array(sector_states(n, na, nb), dtype=np.uint64)
+    la, ph = A.logpsi(model, ham, _dev(st))
+    rla, rph = log_psi(om, ip, st)
+    assert np.abs(la.cpu().numpy() - rla.numpy()).max() < _tol(n, w)
+    x, c = A.sample(model, ham, 1000, seed=1)
+    assert x.cpu().numpy().astype(np.uint64).tolist() == st.tolist() and int(c.sum()) == 1000
+    ere, eim, stats = A.local_energy(model, ham, x, c)
+    e_ref = local_energy(om, ip, oham, st)
+    assert np.allclose(ere.cpu().numpy(), e_ref.real, atol=1e-5) and np.allclose(eim.cpu().numpy(), e_ref.imag, atol=1e-5)
+    g = A.grad(model, ham, x, c, ere, eim, stats)
+    assert torch.isfinite(g).all()
+
+
+def test_nade_32_orbitals(A):
+    """n = 32 (64 qubits, bit 63 in use), one electron of each spin: log psi
+    over the whole 1024-determinant sector, local energies and the gradient
+    of three samples against the oracle."""
+    from oracle.vmc import gradient
+    n, na, nb, w = 32, 1, 1, 32
+    ham, model, om, ip, oham = _setup(A, n, na, nb, w, seed=72)
+    st = np.array(sorted((1 << (2 * i)) | (1 << (2 * j + 1)) for i in range(n) for j in range(n)), dtype=np.uint64)
+    la, ph = A.logpsi(model, ham, _dev(st))
+    rla, rph = log_psi(om, ip, st)
+    tol = _tol(n, w)
+    assert np.abs(la.cpu().numpy() - rla.numpy()).max() < tol
+    assert np.abs(_wrap(ph.cpu().numpy() - rph.numpy())).max() < tol
+    assert abs(np.exp(2 * la.double().cpu().numpy()).sum() - 1.0) < 1e-4
+    xs = st[[0, 517, 1023]]
+    on = np.array([3, 2, 1])
+    ere, eim, stats = A.local_energy(model, ham, _dev(xs), _dev(on))
+    e_ref = local_energy(om, ip, oham, xs)
+    lists = [oham.connected(int(v)) for v in xs]
+    K = len(lists[0])
+    xp = np.array([t[0] for L in lists for t in L], dtype=np.uint64)
+    hv = np.array([t[1] for L in lists for t in L]).reshape(-1, K)
+    lp, _ = log_psi(om, ip, xp)
+    r = np.exp(lp.numpy().reshape(-1, K) - rla.numpy()[np.searchsorted(st, xs)][:, None])
+    bound = (np.abs(hv) * r).sum(1) * (np.exp(2 * tol) - 1) + 1e-12
+    err = np.abs((ere.cpu().numpy() - e_ref.real) + 1j * (eim.cpu().numpy() - e_ref.imag))
+    assert np.all(err <= bound), (err / bound).max()
+    s_ref = energy_stats(e_ref, on)
+    g_ref = _flat_grad(gradient(om, ip, xs, on, e_ref, s_ref), n)
+    g = A.grad(model, ham, _dev(xs), _dev(on), torch.tensor(e_ref.real, device="cuda"),
+               torch.tensor(e_ref.imag, device="cuda"), torch.tensor(s_ref, device="cuda"))
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref) < 1e-4
