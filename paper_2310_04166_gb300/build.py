@@ -59,6 +59,11 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
             if verbose and (r.stdout or r.stderr):
                 print(r.stdout + r.stderr, file=sys.stderr)
             os.replace(obj + ".tmp", obj)
+        # objects of earlier versions of this source are not linked again
+        base = os.path.basename(src) + "."
+        for f in os.listdir(BUILD):
+            if f.startswith(base) and f.endswith(".o") and os.path.join(BUILD, f) != obj:
+                os.remove(os.path.join(BUILD, f))
         return obj
 
     with ThreadPoolExecutor(max_workers=jobs or min(16, os.cpu_count() or 4)) as ex:
