@@ -49,47 +49,69 @@ __global__ void eloc_sum_kernel(uint32_t K, Count n_x_, const double* __restrict
   }
 }
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  v = warp_sum(v);
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (w == 0) {
-    t = lane < int(blockDim.x >> 5) ? red[lane] : 0.0;
-    t = warp_sum(t);
-    if (lane == 0) red[0] = t;
-  }
-  __syncthreads();
-  return red[0];
-}
-
-// single CTA: S, E (complex) then Var in a second pass
-__global__ void stats_kernel(const double* __restrict__ ere, const double* __restrict__ eim,
-                             const uint64_t* __restrict__ counts, Count n_x_, double* __restrict__ stats) {
+// single CTA of STATS_T threads: S (integer), E (complex) then Var in a
+// second pass.  Few warps on purpose: a warp-wide FP64 add is slow on this
+// GPU, so the shuffle trees of many warps would cost more than the rows.
+constexpr int STATS_T = 256;
+__global__ void __launch_bounds__(STATS_T) stats_kernel(const double* __restrict__ ere, const double* __restrict__ eim,
+                                                        const uint64_t* __restrict__ counts, Count n_x_,
+                                                        double* __restrict__ stats) {
   ANQS_PDL_ENTRY();
-  __shared__ double red[32];
+  __shared__ double red_r[STATS_T / 32], red_i[STATS_T / 32];
+  __shared__ unsigned long long red_s[STATS_T / 32];
+  __shared__ double s_mean[3];
   const uint64_t n_x = n_x_.get();
-  double s = 0.0, sr = 0.0, si = 0.0;
-  for (uint64_t l = threadIdx.x; l < n_x; l += blockDim.x) {
-    double w = double(counts[l]);
-    s += w;
-    sr = fma(w, ere[l], sr);
-    si = fma(w, eim[l], si);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned long long cs = 0;
+  double sr = 0.0, si = 0.0;
+  for (uint64_t l = threadIdx.x; l < n_x; l += STATS_T) {
+    const uint64_t c = counts[l];
+    const double wt = double(c);
+    cs += c;
+    sr = fma(wt, ere[l], sr);
+    si = fma(wt, eim[l], si);
   }
-  s = block_sum(s, red);
-  sr = block_sum(sr, red);
-  si = block_sum(si, red);
-  const double Er = sr / s, Ei = si / s;
-  double v = 0.0;
-  for (uint64_t l = threadIdx.x; l < n_x; l += blockDim.x) {
-    double w = double(counts[l]);
-    double dr = ere[l] - Er, di = eim[l] - Ei;
-    v = fma(w, dr * dr + di * di, v);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    cs += __shfl_xor_sync(0xffffffffu, cs, o);
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
   }
-  v = block_sum(v, red);
+  if (lane == 0) {
+    red_s[w] = cs;
+    red_r[w] = sr;
+    red_i[w] = si;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
+    unsigned long long ts = 0;
+    double tr = 0.0, ti = 0.0;
+    for (int k = 0; k < STATS_T / 32; ++k) {
+      ts += red_s[k];
+      tr += red_r[k];
+      ti += red_i[k];
+    }
+    const double S = double(ts);
+    s_mean[0] = tr / S;
+    s_mean[1] = ti / S;
+    s_mean[2] = S;
+  }
+  __syncthreads();
+  const double Er = s_mean[0], Ei = s_mean[1], s = s_mean[2];
+  double v = 0.0;
+  for (uint64_t l = threadIdx.x; l < n_x; l += STATS_T) {
+    const double wt = double(counts[l]);
+    const double dr = ere[l] - Er, di = eim[l] - Ei;
+    v = fma(wt, dr * dr + di * di, v);
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red_r[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    v = 0.0;
+    for (int k = 0; k < STATS_T / 32; ++k) v += red_r[k];
     stats[0] = Er;
     stats[1] = Ei;
     stats[2] = v / s;
@@ -160,7 +182,7 @@ int launch_eloc_sum(const HamView& hv, Count n_x, const double* hval, const doub
 int launch_stats(const double* ere, const double* eim, const uint64_t* counts, Count n_x, double* stats,
                  cudaStream_t s) {
   ProfScope ps(PROF_STATS, s);
-  ANQS_CUDA_LAUNCH("stats_kernel", launch_k(stats_kernel, dim3(1), dim3(1024), 0, s, ere, eim, counts, n_x, stats));
+  ANQS_CUDA_LAUNCH("stats_kernel", launch_k(stats_kernel, dim3(1), dim3(STATS_T), 0, s, ere, eim, counts, n_x, stats));
   return ANQS_OK;
 }
 
