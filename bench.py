@@ -226,8 +226,7 @@ def _config(w, args):
 # workload (`ncu --set full -k regex:<kernel> -c 1 python bench.py
 # --kernel-case`, h2o, BF16 form): dram__bytes_read.sum + dram__bytes_write.sum
 TRAFFIC = {("h2o", "bf16"): {"mlp_fp32_grad_kernel": 1093120 + 44032, "mlp_tc_suffix_kernel": 1280768 + 5888,
-                             "mlp_tc_parent_kernel": 591616, "eloc_assemble_kernel": 4650496,
-                             "connected_kernel": 64256}}
+                             "mlp_tc_parent_kernel": 591616, "connected_kernel": 64256}}
 
 
 def _make_model(A, w, params, form):

@@ -488,24 +488,29 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_ws_kernel(TcView tv, HamView hv,
   teardown<W>(tv, s_tmem, s_abort);
 }
 
-// One warp per parent x: log psi(x') = parent prefix up to slot j + parent
-// slot-j term of v'_j + the terms T[x'][p] of the slots p > j; then
+// One CTA of AT threads per parent x (grid-stride over the parents), its
+// threads over the connected x': log psi(x') = parent prefix up to slot j +
+// parent slot-j term of v'_j + the terms T[x'][p] of the slots p > j; then
 // E_loc(x) = H_xx + sum H_xx' exp(log psi(x') - log psi(x)) with the ratio in
-// float32 and the sum in FP64.
-__global__ void eloc_assemble_kernel(int n, uint32_t K, Count n_x_, const uint64_t* __restrict__ xp,
-                                     const uint8_t* __restrict__ js, const float* __restrict__ cache,
-                                     const float2* __restrict__ T, const double* __restrict__ hval,
-                                     const double* __restrict__ hdiag, const float* __restrict__ la_x,
-                                     const float* __restrict__ ph_x, double* __restrict__ ere,
-                                     double* __restrict__ eim) {
+// float32 and the sum in FP64, reduced in a fixed order (deterministic).
+constexpr int AT = 128;
+__global__ void __launch_bounds__(AT) eloc_assemble_kernel(int n, uint32_t K, Count n_x_, const uint64_t* __restrict__ xp,
+                                                           const uint8_t* __restrict__ js,
+                                                           const float* __restrict__ cache,
+                                                           const float2* __restrict__ T,
+                                                           const double* __restrict__ hval,
+                                                           const double* __restrict__ hdiag,
+                                                           const float* __restrict__ la_x,
+                                                           const float* __restrict__ ph_x, double* __restrict__ ere,
+                                                           double* __restrict__ eim) {
   ANQS_PDL_ENTRY();
-  const int lane = threadIdx.x & 31;
+  __shared__ double red[2][AT / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t n_x = n_x_.get();
-  const uint64_t warps = uint64_t(gridDim.x) * (blockDim.x >> 5);
-  for (uint64_t l = blockIdx.x * uint64_t(blockDim.x >> 5) + (threadIdx.x >> 5); l < n_x; l += warps) {
+  for (uint64_t l = blockIdx.x; l < n_x; l += gridDim.x) {
     const float lx = la_x[l], px = ph_x[l];
     double re = 0.0, im = 0.0;
-    for (uint32_t k = lane; k < K; k += 32) {
+    for (uint32_t k = threadIdx.x; k < K; k += AT) {
       const uint64_t row = l * K + k;
       const int j = js[row];
       const uint64_t x = xp[row];
@@ -531,9 +536,21 @@ __global__ void eloc_assemble_kernel(int n, uint32_t K, Count n_x_, const uint64
       im += __shfl_xor_sync(0xffffffffu, im, o);
     }
     if (lane == 0) {
-      ere[l] = hdiag[l] + re;
-      eim[l] = im;
+      red[0][w] = re;
+      red[1][w] = im;
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sr = 0.0, si = 0.0;
+#pragma unroll
+      for (int q = 0; q < AT / 32; ++q) {
+        sr += red[0][q];
+        si += red[1][q];
+      }
+      ere[l] = hdiag[l] + sr;
+      eim[l] = si;
+    }
+    __syncthreads();
   }
 }
 
@@ -869,9 +886,9 @@ int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* hist, uint32_t*
 int launch_eloc_assemble(int n, uint32_t K, Count n_x, const uint64_t* xp, const uint8_t* js, const float* cache,
                          const float2* T, const double* hval, const double* hdiag, const float* la_x,
                          const float* ph_x, double* ere, double* eim, cudaStream_t s) {
-  uint64_t blocks = (n_x.n + 7) / 8;
+  uint64_t blocks = n_x.n;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  ANQS_CUDA_LAUNCH("eloc_assemble_kernel", launch_k(eloc_assemble_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(256), 0, s, n, K, n_x, xp, js, cache, T, hval, hdiag, la_x, ph_x, ere, eim));
+  ANQS_CUDA_LAUNCH("eloc_assemble_kernel", launch_k(eloc_assemble_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(AT), 0, s, n, K, n_x, xp, js, cache, T, hval, hdiag, la_x, ph_x, ere, eim));
   return ANQS_OK;
 }
 
@@ -915,9 +932,8 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count
   }
   {
     ProfScope ps(PROF_TC_ELOC, s);
-    uint64_t blocks = (n_x.n + 7) / 8;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    ANQS_CUDA_LAUNCH("eloc_assemble_kernel", launch_k(eloc_assemble_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(256), 0, s, H->v.n, uint32_t(K), n_x, w.xp, w.js, w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x, ere, eim));
+    ANQS_TRY(launch_eloc_assemble(H->v.n, uint32_t(K), n_x, w.xp, w.js, w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x, ere,
+                                  eim, s));
   }
   return ANQS_OK;
 }
