@@ -456,6 +456,7 @@ __global__ void scatter_kernel(int p, const uint64_t* __restrict__ pre, const ui
 // warp-segment aggregation into shared counters, compaction of the children.
 constexpr int SMALL_T = 256;
 constexpr int SMALL_F = 2048;  // largest frontier handled this way
+constexpr int RUN = 8;         // consecutive nodes or counters per thread in the scans
 constexpr size_t SMALL_DYN = size_t(SMALL_T) * 48;  // thresholds and window counts
 
 __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* sh, uint32_t* tot) {
@@ -517,13 +518,26 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
   const int nf = int(*n_front);
   const int lane = threadIdx.x & 31;
   const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
+  // draw-block offsets of the nodes: each thread scans a run of RUN
+  // consecutive nodes (their counts loaded together), one block scan per
+  // RUN * SMALL_T nodes
   uint32_t carry = 0;
-  for (int base = 0; base < nf; base += SMALL_T) {
-    const int i = base + threadIdx.x;
-    const uint32_t nb = i < nf ? uint32_t((cnt[i] + 3) / 4) : 0u;
+  for (int base = 0; base < nf; base += RUN * SMALL_T) {
+    const int i0 = base + RUN * threadIdx.x;
+    uint32_t nb[RUN], mine = 0;
+#pragma unroll
+    for (int e = 0; e < RUN; ++e) {
+      nb[e] = i0 + e < nf ? uint32_t((cnt[i0 + e] + 3) / 4) : 0u;
+      mine += nb[e];
+    }
     uint32_t tot;
-    const uint32_t ex = block_excl_scan_u32(nb, s_red, &tot);
-    if (i < nf) s_scan[i] = carry + ex;
+    uint32_t off = carry + block_excl_scan_u32(mine, s_red, &tot);
+#pragma unroll
+    for (int e = 0; e < RUN; ++e)
+      if (i0 + e < nf) {
+        s_scan[i0 + e] = off;
+        off += nb[e];
+      }
     carry += tot;
   }
   if (threadIdx.x == 0) s_scan[nf] = carry;
@@ -602,16 +616,28 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  // children in (node, outcome) order: runs of RUN consecutive counters per
+  // thread, loaded together, one block scan per RUN * SMALL_T counters
   carry = 0;
-  for (int base = 0; base < 4 * nf; base += SMALL_T) {
-    const int i = base + threadIdx.x;
-    const uint64_t c = i < 4 * nf ? __ldcg(child + i) : 0ull;
-    uint32_t tot;
-    const uint32_t ex = block_excl_scan_u32(c ? 1u : 0u, s_red, &tot);
-    if (c) {
-      pre_out[carry + ex] = pre[i >> 2] | (uint64_t(i & 3) << (2 * p));
-      cnt_out[carry + ex] = c;
+  for (int base = 0; base < 4 * nf; base += RUN * SMALL_T) {
+    const int i0 = base + RUN * threadIdx.x;
+    uint64_t c[RUN];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int e = 0; e < RUN; ++e) {
+      c[e] = i0 + e < 4 * nf ? __ldcg(child + i0 + e) : 0ull;
+      mine += c[e] ? 1u : 0u;
     }
+    uint32_t tot;
+    uint32_t off = carry + block_excl_scan_u32(mine, s_red, &tot);
+#pragma unroll
+    for (int e = 0; e < RUN; ++e)
+      if (c[e]) {
+        const int i = i0 + e;
+        pre_out[off] = pre[i >> 2] | (uint64_t(i & 3) << (2 * p));
+        cnt_out[off] = c[e];
+        ++off;
+      }
     carry += tot;
   }
   __syncthreads();
