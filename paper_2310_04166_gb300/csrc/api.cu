@@ -152,10 +152,13 @@ static size_t vjp_ws_bytes(const anqs_model* M, uint64_t n_x) {
 
 static int vjp_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, const float* cl,
                         const float* cp, float* grad, float* part, void* ws, size_t ws_bytes, cudaStream_t s) {
-  if (M->d.kind == ANQS_MODEL_MLP) return launch_mlp_fp32_grad(M->mlp, H->v, x, n_x, cl, cp, grad, part, s);
+  if (M->d.kind == ANQS_MODEL_MLP)
+    return launch_mlp_fp32_grad(M->mlp, H->v, x, n_x, CotSrc{cl, cp, nullptr, nullptr, nullptr, nullptr}, grad, part,
+                                s);
   if (M->d.kind == ANQS_MODEL_TF) return launch_tf_fp32_grad(M->tf, H->v, x, n_x, cl, cp, grad, ws, ws_bytes, s);
   if (M->d.kind == ANQS_MODEL_NADE)
-    return launch_nade_grad(M->nade, H->v, x, n_x, cl, cp, grad, M->n_params, static_cast<float*>(ws), s);
+    return launch_nade_grad(M->nade, H->v, x, n_x, CotSrc{cl, cp, nullptr, nullptr, nullptr, nullptr}, grad,
+                            M->n_params, static_cast<float*>(ws), s);
   return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not available in this build", M->d.kind);
 }
 }  // namespace anqs
@@ -707,6 +710,11 @@ int anqs_grad(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const u
   cudaStream_t s = (cudaStream_t)stream;
   if (!part) ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));
   const Count nc{n_x, n_x_dev, 1};
+  // the MLP and NADE adjoints compute each row's cotangents themselves
+  const CotSrc vmc{nullptr, nullptr, ere, eim, stats, counts};
+  if (M->d.kind == ANQS_MODEL_MLP) return launch_mlp_fp32_grad(M->mlp, H->v, x, nc, vmc, grad, part, s);
+  if (M->d.kind == ANQS_MODEL_NADE)
+    return launch_nade_grad(M->nade, H->v, x, nc, vmc, grad, M->n_params, static_cast<float*>(tfws), s);
   ANQS_TRY(launch_grad_cotangents(ere, eim, counts, stats, nc, cl, cp, s));
   return vjp_dispatch(M, H, x, nc, cl, cp, grad, part, tfws, tfb, s);
 }

@@ -160,6 +160,27 @@ __device__ __forceinline__ unsigned norm_mask(const HamView& hv, int p, unsigned
 }
 #endif
 
+// Cotangents of an adjoint: the given arrays cl, cp (log|psi|, arg psi per
+// row), or, when stats is set, those of the VMC gradient computed per row:
+// 2 (n_l / S) Re(E_loc,l - E) and 2 (n_l / S) Im(E_loc,l - E).
+struct CotSrc {
+  const float *cl, *cp;
+  const double *ere, *eim, *stats;
+  const uint64_t* counts;
+};
+#ifdef __CUDACC__
+__device__ __forceinline__ void cot_of(const CotSrc& c, uint64_t l, float& a, float& b) {
+  if (c.stats) {
+    const double w = double(c.counts[l]) / c.stats[3];
+    a = float(2.0 * w * (c.ere[l] - c.stats[0]));
+    b = float(2.0 * w * (c.eim[l] - c.stats[1]));
+  } else {
+    a = c.cl[l];
+    b = c.cp[l];
+  }
+}
+#endif
+
 // MLP parameters as seen by the kernels.
 struct MlpView {
   int n, width, n_hidden;
@@ -259,8 +280,8 @@ int launch_mlp_fp32_slot_logits(const MlpView& m, int p, const uint64_t* prefixe
                                 cudaStream_t s);
 // part: per-tile partial gradients (mlp_fp32_grad_partial_floats floats) or
 // null for atomic accumulation into grad (which must then be zeroed)
-int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x,
-                         const float* cot_la, const float* cot_ph, float* grad, float* part, cudaStream_t s);
+int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot,
+                         float* grad, float* part, cudaStream_t s);
 size_t mlp_fp32_grad_partial_floats(const MlpView& m, uint64_t n_x);
 
 // table.cu
@@ -326,8 +347,8 @@ int launch_nade_logpsi(const NadeView& m, const HamView& hv, const uint64_t* x, 
 int launch_nade_slot_logits(const NadeView& m, const HamView& hv, int p, const uint64_t* pre, const uint64_t* n_dev,
                             uint64_t max_rows, float* out8, cudaStream_t s);
 // part: nade_grad_partial_floats floats (null when that is 0); grad is overwritten
-int launch_nade_grad(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
-                     const float* cp, float* grad, uint64_t n_params, float* part, cudaStream_t s);
+int launch_nade_grad(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot,
+                     float* grad, uint64_t n_params, float* part, cudaStream_t s);
 size_t nade_grad_partial_floats(const NadeView& m, uint64_t n_params, uint64_t n_x);
 size_t nade_eloc_workspace(const anqs_ham* H, uint64_t n_x);
 int run_eloc_nade(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,

@@ -325,8 +325,7 @@ __device__ __forceinline__ void outer_accumulate(const float* dz, const float* h
 
 template <int W, int RG, bool PARTIAL, bool RESIDENT>
 __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const uint64_t* __restrict__ xs,
-                                                  Count n_x_, const float* __restrict__ cot_la,
-                                                  const float* __restrict__ cot_ph, float* __restrict__ grad,
+                                                  Count n_x_, CotSrc cot, float* __restrict__ grad,
                                                   uint64_t n_params) {
   ANQS_PDL_ENTRY();
   extern __shared__ float smem[];
@@ -345,8 +344,10 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
   if (threadIdx.x < RG) {
     bool ok = threadIdx.x < nrows;
     xt[threadIdx.x] = ok ? xs[base + threadIdx.x] : 0ull;
-    cl[threadIdx.x] = ok ? cot_la[base + threadIdx.x] : 0.f;
-    cp[threadIdx.x] = ok ? cot_ph[base + threadIdx.x] : 0.f;
+    float a = 0.f, b = 0.f;
+    if (ok) cot_of(cot, base + threadIdx.x, a, b);
+    cl[threadIdx.x] = a;
+    cp[threadIdx.x] = b;
   }
   __syncthreads();
   // hidden matrices of slot p resident in shared memory (row stride W + 1)
@@ -514,15 +515,15 @@ int logits_w(const MlpView& m, int p, const uint64_t* pre, const uint64_t* nr, u
 }
 
 template <int W, int RG, bool RES>
-int grad_launch(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
-                const float* cp, float* g, float* part, uint64_t n_params, size_t sm, cudaStream_t s) {
+int grad_launch(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot, float* g,
+                float* part, uint64_t n_params, size_t sm, cudaStream_t s) {
   dim3 grid(unsigned(std::max<uint64_t>((n_x.n + RG - 1) / RG, 1)), unsigned(m.n));
   if (part) {
     ANQS_TRY(set_smem(grad_kernel<W, RG, true, RES>, sm));
     {
       ProfScope ps(PROF_MLP_FP32_GRAD, s);
       ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, RG, true, RES>, dim3(grid), dim3(NT), sm, s, m, hv,
-                                                   x, n_x, cl, cp, part, n_params));
+                                                   x, n_x, cot, part, n_params));
     }
     ProfScope ps(PROF_GRAD_REDUCE, s);
     ANQS_CUDA_LAUNCH("mlp partial_sum_kernel",
@@ -532,7 +533,7 @@ int grad_launch(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_
     ANQS_TRY(set_smem(grad_kernel<W, RG, false, RES>, sm));
     ProfScope ps(PROF_MLP_FP32_GRAD, s);
     ANQS_CUDA_LAUNCH("mlp grad_kernel", launch_k(grad_kernel<W, RG, false, RES>, dim3(grid), dim3(NT), sm, s, m, hv,
-                                                 x, n_x, cl, cp, g, n_params));
+                                                 x, n_x, cot, g, n_params));
   }
   return ANQS_OK;
 }
@@ -540,24 +541,24 @@ int grad_launch(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_
 // The slot's hidden matrices stay in shared memory when they fit next to the
 // activations (widths 64 and 128); otherwise they stream in chunks.
 template <int W, int RG>
-int grad_rg(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
-            const float* cp, float* g, float* part, uint64_t n_params, cudaStream_t s) {
+int grad_rg(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot, float* g,
+            float* part, uint64_t n_params, cudaStream_t s) {
   const size_t sm = Smem<W, RG>::bytes(m.n_hidden + 1);
   const size_t res = sm + size_t(m.n_hidden - 1) * W * (W + 1) * sizeof(float);
-  if (res <= 227 * 1024) return grad_launch<W, RG, true>(m, hv, x, n_x, cl, cp, g, part, n_params, res, s);
+  if (res <= 227 * 1024) return grad_launch<W, RG, true>(m, hv, x, n_x, cot, g, part, n_params, res, s);
   if (sm > 227 * 1024)
     return set_error(ANQS_ERR_UNSUPPORTED, "FP32 MLP adjoint needs %zu bytes of shared memory", sm);
-  return grad_launch<W, RG, false>(m, hv, x, n_x, cl, cp, g, part, n_params, sm, s);
+  return grad_launch<W, RG, false>(m, hv, x, n_x, cot, g, part, n_params, sm, s);
 }
 
 template <int W>
-int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
-           const float* cp, float* g, float* part, uint64_t n_params, cudaStream_t s) {
+int grad_w(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot, float* g,
+           float* part, uint64_t n_params, cudaStream_t s) {
   switch (rg_for(m, n_x.n)) {
-    case 16: return grad_rg<W, 16>(m, hv, x, n_x, cl, cp, g, part, n_params, s);
-    case 24: return grad_rg<W, 24>(m, hv, x, n_x, cl, cp, g, part, n_params, s);
+    case 16: return grad_rg<W, 16>(m, hv, x, n_x, cot, g, part, n_params, s);
+    case 24: return grad_rg<W, 24>(m, hv, x, n_x, cot, g, part, n_params, s);
   }
-  return grad_rg<W, 32>(m, hv, x, n_x, cl, cp, g, part, n_params, s);
+  return grad_rg<W, 32>(m, hv, x, n_x, cot, g, part, n_params, s);
 }
 
 }  // namespace
@@ -587,14 +588,14 @@ size_t mlp_fp32_grad_partial_floats(const MlpView& m, uint64_t n_x) {
   return size_t((n_x + rg - 1) / rg) * m.slot_off[m.n];
 }
 
-int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
-                         const float* cp, float* g, float* part, cudaStream_t s) {
+int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot,
+                         float* g, float* part, cudaStream_t s) {
   if ((n_x.n + 15) / 16 > 0x7fffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "too many rows");
   const uint64_t np = m.slot_off[m.n];
   switch (m.width) {
-    case 64: return grad_w<64>(m, hv, x, n_x, cl, cp, g, part, np, s);
-    case 128: return grad_w<128>(m, hv, x, n_x, cl, cp, g, part, np, s);
-    case 256: return grad_w<256>(m, hv, x, n_x, cl, cp, g, part, np, s);
+    case 64: return grad_w<64>(m, hv, x, n_x, cot, g, part, np, s);
+    case 128: return grad_w<128>(m, hv, x, n_x, cot, g, part, np, s);
+    case 256: return grad_w<256>(m, hv, x, n_x, cot, g, part, np, s);
   }
   return set_error(ANQS_ERR_UNSUPPORTED, "width %d", m.width);
 }

@@ -572,8 +572,7 @@ __host__ __device__ inline uint32_t qubit_floats(uint32_t w, uint32_t i) { retur
 
 template <int W>
 __global__ void __launch_bounds__(NT) nade_grad_kernel(NadeView m, HamView hv, const uint64_t* __restrict__ xs,
-                                                       Count rows_, const float* __restrict__ cl,
-                                                       const float* __restrict__ cp, float* __restrict__ out,
+                                                       Count rows_, CotSrc cot, float* __restrict__ out,
                                                        uint64_t out_stride) {
   ANQS_PDL_ENTRY();
   constexpr int R = NT / W;
@@ -642,7 +641,8 @@ __global__ void __launch_bounds__(NT) nade_grad_kernel(NadeView m, HamView hv, c
         const float mx = fmaxf(r0, r1);
         const float e0 = expf(r0 - mx), e1 = expf(r1 - mx);
         const float pi0 = e0 / (e0 + e1), pi1 = e1 / (e0 + e1);
-        const float c_l = cl[base + r], c_p = cp[base + r];
+        float c_l, c_p;
+        cot_of(cot, base + r, c_l, c_p);
         g0 = make_float2(c_l * ((xi == 0 ? 1.f : 0.f) - pi0), xi == 0 ? c_p : 0.f);
         g1 = make_float2(c_l * ((xi == 1 ? 1.f : 0.f) - pi1), xi == 1 ? c_p : 0.f);
       }
@@ -740,8 +740,8 @@ int grad_groups(const NadeView& m, uint64_t n_x) {
 }
 
 template <int W>
-int grad_w(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl, const float* cp,
-           float* grad, uint64_t n_params, float* part, cudaStream_t s) {
+int grad_w(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot, float* grad,
+           uint64_t n_params, float* part, cudaStream_t s) {
   const int G = grad_groups(m, n_x.n);
   const size_t smem = size_t(qubit_floats(W, 2 * m.n - 1)) * sizeof(float);
   ANQS_CUDA(cudaFuncSetAttribute(nade_grad_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
@@ -749,7 +749,7 @@ int grad_w(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, c
   if (G > 1 && !part) return set_error(ANQS_ERR_CAPACITY, "NADE adjoint needs its partial-sum workspace");
   ProfScope ps(PROF_NADE_GRAD, s);
   ANQS_CUDA_LAUNCH("nade_grad_kernel", launch_k(nade_grad_kernel<W>, dim3(G, 2 * m.n), dim3(NT), smem, s, m, hv, x,
-                                                n_x, cl, cp, out, G > 1 ? n_params : uint64_t(0)));
+                                                n_x, cot, out, G > 1 ? n_params : uint64_t(0)));
   if (G > 1) {
     uint64_t blocks = (n_params + 255) / 256;
     if (blocks > 152 * 4) blocks = 152 * 4;
@@ -766,13 +766,13 @@ size_t nade_grad_partial_floats(const NadeView& m, uint64_t n_params, uint64_t n
   return G > 1 ? size_t(G) * n_params : 0;
 }
 
-int launch_nade_grad(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
-                     const float* cp, float* grad, uint64_t n_params, float* part, cudaStream_t s) {
+int launch_nade_grad(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot,
+                     float* grad, uint64_t n_params, float* part, cudaStream_t s) {
   if (n_x.n == 0) return ANQS_OK;
   switch (m.w) {
-    case 32: return grad_w<32>(m, hv, x, n_x, cl, cp, grad, n_params, part, s);
-    case 64: return grad_w<64>(m, hv, x, n_x, cl, cp, grad, n_params, part, s);
-    case 128: return grad_w<128>(m, hv, x, n_x, cl, cp, grad, n_params, part, s);
+    case 32: return grad_w<32>(m, hv, x, n_x, cot, grad, n_params, part, s);
+    case 64: return grad_w<64>(m, hv, x, n_x, cot, grad, n_params, part, s);
+    case 128: return grad_w<128>(m, hv, x, n_x, cot, grad, n_params, part, s);
   }
   return set_error(ANQS_ERR_UNSUPPORTED, "NADE width %d", m.w);
 }
