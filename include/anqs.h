@@ -337,6 +337,50 @@ ANQS_API int anqs_local_energy(const anqs_model* model, const anqs_ham* ham, con
                       size_t workspace_bytes, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Batched local energy (no counterpart in the paper, which treats one
+ * molecule at a time: many independent problems in one call)
+ *
+ * anqs_eloc_problem holds the arguments of one anqs_local_energy call.
+ * anqs_batched_local_energy computes every problem's local energies and
+ * statistics exactly as anqs_local_energy would, each problem on its own
+ * stream of the batch handle, forked from `stream` with an event and joined
+ * back into it with one event per problem: the problems run side by side,
+ * after the work queued on `stream` before the call and before the work
+ * queued after it.  The fork and join are ordinary event dependencies, so
+ * the call can be recorded into a CUDA graph by capturing `stream`.
+ * - Every problem is checked (model/Hamiltonian pair, n_x >= 1, arrays,
+ *   workspace size from anqs_local_energy_workspace_size) before anything is
+ *   queued; errors: ANQS_ERR_ARG, ANQS_ERR_CAPACITY (a workspace too small or
+ *   more problems than the handle's streams), ANQS_ERR_UNSUPPORTED, as for
+ *   anqs_local_energy.
+ * - Problems may share a model or a Hamiltonian (read only) but not their
+ *   outputs or workspaces.
+ * - The handle owns max_problems non-blocking streams and max_problems + 1
+ *   events on the device current at creation; a handle serves one call at a
+ *   time (calls on it are ordered by the caller).
+ * ------------------------------------------------------------------------- */
+typedef struct anqs_batch anqs_batch;
+
+typedef struct {
+  const anqs_model* model;
+  const anqs_ham* ham;
+  const uint64_t* x_dev;
+  const uint64_t* counts_dev;   /* or NULL (then no statistics) */
+  uint64_t n_x;
+  const uint64_t* n_x_dev;      /* or NULL */
+  double* eloc_re_dev;
+  double* eloc_im_dev;
+  double* stats_dev;            /* 4 doubles, required with counts_dev */
+  void* workspace_dev;
+  size_t workspace_bytes;
+} anqs_eloc_problem;
+
+ANQS_API int anqs_batch_create(anqs_batch** out, int max_problems);
+ANQS_API int anqs_batch_destroy(anqs_batch* batch);
+ANQS_API int anqs_batched_local_energy(anqs_batch* batch, const anqs_eloc_problem* problems_host, int n_problems,
+                                       void* stream);
+
+/* ---------------------------------------------------------------------------
  * VMC gradient (Eq. grad_def)
  *
  * grad = 2 Re{ E[eloc d ln psi*] - E[eloc] E[d ln psi*] } with expectations

@@ -21,7 +21,7 @@ import torch
 from . import _lib
 from ._lib import AnqsError, ModelDesc, check
 
-__all__ = ["Hamiltonian", "Model", "connected", "logpsi", "logpsi_vjp", "sample", "sample_into",
+__all__ = ["Hamiltonian", "Model", "EnergyBatch", "connected", "logpsi", "logpsi_vjp", "sample", "sample_into",
            "local_energy", "grad", "LogPsi", "AnqsError", "library_path"]
 
 
@@ -312,6 +312,51 @@ def local_energy(model: Model, ham: Hamiltonian, x: torch.Tensor, counts: torch.
                                         ere.data_ptr(), eim.data_ptr(), _ptr(stats), workspace.data_ptr(),
                                         workspace.numel(), _stream(stream)))
     return ere, eim, stats
+
+
+class EnergyBatch:
+    """Handle of anqs_batched_local_energy: one stream and one event per
+    problem slot (max_problems of them) on the current CUDA device."""
+
+    def __init__(self, max_problems: int):
+        h = C.c_void_p()
+        check(_lib.load().anqs_batch_create(C.byref(h), int(max_problems)))
+        self._h, self.max_problems = h, int(max_problems)
+
+    def __del__(self):
+        if getattr(self, "_h", None) is not None and _lib._lib is not None:
+            _lib._lib.anqs_batch_destroy(self._h)
+            self._h = None
+
+    def local_energy(self, items, stream=None):
+        """Local energies of several independent problems in one call, side
+        by side on the handle's streams, ordered on `stream` (capturable in a
+        CUDA graph).  items: dicts with model, ham, x and optionally counts,
+        n_dev, workspace, out=(eloc_re, eloc_im, stats).  Returns the
+        (eloc_re, eloc_im, stats) of each problem."""
+        probs = (_lib.ElocProblem * max(len(items), 1))()
+        keep, results = [], []
+        for k, it in enumerate(items):
+            model, ham, x = it["model"], it["ham"], _u64(it["x"])
+            counts = it.get("counts")
+            cnt = _u64(counts) if counts is not None else None
+            n_x = x.numel()
+            if it.get("out") is None:
+                ere = torch.empty(n_x, dtype=torch.float64, device=x.device)
+                eim = torch.empty_like(ere)
+                stats = torch.empty(4, dtype=torch.float64, device=x.device) if cnt is not None else None
+            else:
+                ere, eim, stats = it["out"]
+            ws = it.get("workspace")
+            if ws is None:
+                ws = _ws(local_energy_workspace_bytes(model, ham, n_x), x.device)
+            probs[k] = _lib.ElocProblem(model._m, ham.handle, x.data_ptr(), _ptr(cnt), n_x, _ptr(it.get("n_dev")),
+                                        ere.data_ptr(), eim.data_ptr(), _ptr(stats), ws.data_ptr(), ws.numel())
+            keep += [x, cnt, ws]
+            results.append((ere, eim, stats))
+        check(_lib.load().anqs_batched_local_energy(self._h, probs, len(items), _stream(stream)))
+        self._keep = keep  # inputs and workspaces stay alive until the next call
+        return results
 
 
 def grad_workspace_bytes(model, ham, n_x) -> int:

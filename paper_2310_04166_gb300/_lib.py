@@ -20,6 +20,14 @@ class ModelDesc(C.Structure):
                 ("n_layers", C.c_int32)]
 
 
+class ElocProblem(C.Structure):
+    """anqs_eloc_problem: the arguments of one anqs_local_energy call."""
+    _fields_ = [("model", C.c_void_p), ("ham", C.c_void_p), ("x_dev", C.c_void_p), ("counts_dev", C.c_void_p),
+                ("n_x", C.c_uint64), ("n_x_dev", C.c_void_p), ("eloc_re_dev", C.c_void_p),
+                ("eloc_im_dev", C.c_void_p), ("stats_dev", C.c_void_p), ("workspace_dev", C.c_void_p),
+                ("workspace_bytes", C.c_size_t)]
+
+
 class AnqsError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -59,6 +67,9 @@ SIGNATURES = {
     "anqs_grad_workspace_size": (C.c_int, [_VP, _VP, _U64, C.POINTER(_SZ)]),
     "anqs_grad": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "anqs_local_energy_static": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
+    "anqs_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int]),
+    "anqs_batch_destroy": (C.c_int, [_VP]),
+    "anqs_batched_local_energy": (C.c_int, [_VP, _VP, C.c_int, _VP]),
     "anqs_launch_count": (C.c_int, [C.POINTER(_U64)]),
     "anqs_profile_enable": (C.c_int, [C.c_int]),
     "anqs_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_char_p), C.POINTER(_U64), C.POINTER(C.c_double)]),

@@ -681,6 +681,98 @@ int anqs_local_energy(const anqs_model* M, const anqs_ham* H, const uint64_t* x,
 // gradient
 // ---------------------------------------------------------------------------
 
+// ---------------------------------------------------------------------------
+// batched local energy: one stream per problem, forked from and joined back
+// into the caller's stream with events
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+struct anqs_batch {
+  int device;
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t fork;
+};
+
+static void batch_release(anqs_batch* b) {
+  for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
+  for (cudaEvent_t e : b->done) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
+}
+
+// checks of one problem, before anything of the call is queued
+static int check_problem(const anqs_eloc_problem& q, int device) {
+  ANQS_TRY(check_pair(q.model, q.ham));
+  if (q.model->device != device) return set_error(ANQS_ERR_ARG, "problem on another device than the batch handle");
+  if (q.n_x == 0) return set_error(ANQS_ERR_ARG, "n_x must be >= 1");
+  if (!q.x_dev || !q.eloc_re_dev || !q.eloc_im_dev) return set_error(ANQS_ERR_ARG, "null array argument");
+  if (q.counts_dev && !q.stats_dev) return set_error(ANQS_ERR_ARG, "counts given without stats output");
+  size_t need = 0;
+  ANQS_TRY(anqs_local_energy_workspace_size(q.model, q.ham, q.n_x, &need));
+  if (q.workspace_bytes < need || !q.workspace_dev) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
+  if (uses_tc_eloc(q.model) && q.n_x * uint64_t(q.ham->v.K) > 0xffffffffull)
+    return set_error(ANQS_ERR_UNSUPPORTED, "more than 2^32 connected determinants per call");
+  return ANQS_OK;
+}
+
+extern "C" {
+
+int anqs_batch_create(anqs_batch** out, int max_problems) {
+  if (!out) return set_error(ANQS_ERR_ARG, "null output");
+  *out = nullptr;
+  if (max_problems < 1 || max_problems > 4096) return set_error(ANQS_ERR_ARG, "max_problems %d outside 1..4096", max_problems);
+  anqs_batch* b = new anqs_batch();
+  b->fork = nullptr;
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  for (int k = 0; e == cudaSuccess && k < max_problems; ++k) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->streams.push_back(st);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->done.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    batch_release(b);
+    return set_error(ANQS_ERR_CUDA, "batch handle: %s", cudaGetErrorString(e));
+  }
+  *out = b;
+  return ANQS_OK;
+}
+
+int anqs_batch_destroy(anqs_batch* b) {
+  if (!b) return ANQS_OK;
+  batch_release(b);
+  return ANQS_OK;
+}
+
+int anqs_batched_local_energy(anqs_batch* b, const anqs_eloc_problem* q, int n, void* stream) {
+  if (!b) return set_error(ANQS_ERR_ARG, "null batch handle");
+  if (n < 0 || (n > 0 && !q)) return set_error(ANQS_ERR_ARG, "invalid problem list");
+  if (n > int(b->streams.size()))
+    return set_error(ANQS_ERR_CAPACITY, "%d problems for a handle of %zu streams", n, b->streams.size());
+  ANQS_TRY(check_stream_device(b->device));
+  for (int k = 0; k < n; ++k) {
+    const int r = check_problem(q[k], b->device);
+    if (r != ANQS_OK) return r;
+  }
+  if (n == 0) return ANQS_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  ANQS_CUDA(cudaEventRecord(b->fork, s));
+  for (int k = 0; k < n; ++k) {
+    cudaStream_t sk = b->streams[k];
+    ANQS_CUDA(cudaStreamWaitEvent(sk, b->fork, 0));
+    ANQS_TRY(anqs_local_energy(q[k].model, q[k].ham, q[k].x_dev, q[k].counts_dev, q[k].n_x, q[k].n_x_dev,
+                               q[k].eloc_re_dev, q[k].eloc_im_dev, q[k].stats_dev, q[k].workspace_dev,
+                               q[k].workspace_bytes, sk));
+    ANQS_CUDA(cudaEventRecord(b->done[k], sk));
+  }
+  for (int k = 0; k < n; ++k) ANQS_CUDA(cudaStreamWaitEvent(s, b->done[k], 0));
+  return ANQS_OK;
+}
+
 int anqs_grad_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_x, size_t* bytes) {
   ANQS_TRY(check_pair(M, H));
   if (!bytes) return set_error(ANQS_ERR_ARG, "null output");

@@ -55,6 +55,14 @@ def test_param_counts_match_layouts(lib):
         k = C.c_uint64()
         assert lib.anqs_model_param_count(C.byref(d), C.byref(k)) == 0
         assert k.value == tf_param_count(n, dm, L)
+    from synthetic import nade_param_count
+    for n, w in [(1, 32), (7, 64), (32, 128)]:
+        d = ModelDesc(3, 0, n, w, 0, 0, 0, 0)
+        k = C.c_uint64()
+        assert lib.anqs_model_param_count(C.byref(d), C.byref(k)) == 0
+        assert k.value == nade_param_count(n, w)
+    for bad in (ModelDesc(3, 1, 4, 64, 0, 0, 0, 0), ModelDesc(3, 0, 4, 96, 0, 0, 0, 0)):  # BF16, width 96
+        assert lib.anqs_model_param_count(C.byref(bad), C.byref(C.c_uint64())) == -5
     d = ModelDesc(2, 0, 5, 0, 0, 0, 0, 0)
     k = C.c_uint64()
     assert lib.anqs_model_param_count(C.byref(d), C.byref(k)) == 0

@@ -50,3 +50,80 @@ def test_graph_of_problems_equals_each_problem_alone(A, form):
         assert torch.equal(a.ere[:k], b.ere[:k])
         assert torch.equal(a.g, b.g)
         assert int(a.ctr.item()) == int(b.ctr.item()) == 2
+
+
+def _mixed(A):
+    """Four problems of different models and sizes with their sample sets:
+    BF16 MLP (h2o shape), FP32 MLP (small), BF16 transformer (6 orbitals),
+    FP32 NADE (5 orbitals)."""
+    from synthetic import flatten_nade, flatten_tf, integrals, nade_params, tf_params, workload
+    out = []
+    for name, form in (("h2o", "bf16"), ("small", "fp32")):
+        w = workload(name, bias_std=0.2)
+        ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+        out.append((ham, A.Model.mlp(w["n"], w["width"], w["n_hidden"], torch.tensor(w["params"], device="cuda"),
+                                     form)))
+    h, g, e = integrals(21, 6, 6)
+    ham = A.Hamiltonian(h, g, e, 3, 2)
+    P = torch.tensor(flatten_tf(tf_params(21, 6, 64, 2, bias_std=0.2)), device="cuda")
+    out.append((ham, A.Model.transformer(6, 64, 4, 2, P, "bf16")))
+    h, g, e = integrals(22, 5, 5)
+    ham = A.Hamiltonian(h, g, e, 2, 3)
+    out.append((ham, A.Model.nade(5, 64, torch.tensor(flatten_nade(nade_params(22, 5, 64, bias_std=0.3)),
+                                                      device="cuda"))))
+    items = []
+    for k, (ham, model) in enumerate(out):
+        x, c = A.sample(model, ham, 50_000, seed=30 + k)
+        items.append(dict(model=model, ham=ham, x=x, counts=c))
+    return items
+
+
+def test_batched_local_energy_equals_each_call_alone(A):
+    """anqs_batched_local_energy runs each problem's anqs_local_energy on its
+    own stream: the same kernels on the same inputs, so the results are the
+    same bits; recorded in a CUDA graph and replayed, they are again."""
+    items = _mixed(A)
+    alone = [A.local_energy(it["model"], it["ham"], it["x"], it["counts"]) for it in items]
+    batch = A.EnergyBatch(len(items))
+    got = batch.local_energy(items)
+    torch.cuda.synchronize()
+    for (ar, ai, ast), (br, bi, bst) in zip(alone, got):
+        assert torch.equal(ar, br) and torch.equal(ai, bi) and torch.equal(ast, bst)
+    # the same call captured into a graph on a side stream, outputs cleared, replayed
+    outs = [(torch.empty_like(r), torch.empty_like(i), torch.empty_like(st)) for r, i, st in alone]
+    its = [dict(it, out=o) for it, o in zip(items, outs)]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        batch.local_energy(its, stream=side)  # workspaces allocated outside the capture
+        ws = [batch._keep[3 * k + 2] for k in range(len(its))]
+        its = [dict(it, workspace=w) for it, w in zip(its, ws)]
+        torch.cuda.synchronize()
+        with torch.cuda.graph(graph, stream=side):
+            batch.local_energy(its, stream=side)
+    for o in outs:
+        for t in o:
+            t.fill_(float("nan"))
+    graph.replay()
+    torch.cuda.synchronize()
+    for (ar, ai, ast), (br, bi, bst) in zip(alone, outs):
+        assert torch.equal(ar, br) and torch.equal(ai, bi) and torch.equal(ast, bst)
+
+
+def test_batched_local_energy_checks_before_queueing(A):
+    items = _mixed(A)[:3]
+    outs = [(torch.full((it["x"].numel(),), float("nan"), dtype=torch.float64, device="cuda"),
+             torch.full((it["x"].numel(),), float("nan"), dtype=torch.float64, device="cuda"),
+             torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")) for it in items]
+    its = [dict(it, out=o) for it, o in zip(items, outs)]
+    small = A.EnergyBatch(2)
+    with pytest.raises(A.AnqsError, match="CAPACITY"):
+        small.local_energy(its)
+    batch = A.EnergyBatch(3)
+    bad = dict(its[2], workspace=torch.empty(16, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(A.AnqsError, match="CAPACITY"):
+        batch.local_energy(its[:2] + [bad])
+    torch.cuda.synchronize()
+    for o in outs:  # nothing of the failed calls ran
+        assert all(torch.isnan(t).all() for t in o)
