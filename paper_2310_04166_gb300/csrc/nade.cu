@@ -33,6 +33,8 @@
 // LOGITS (slot p's 8 values for the sampler's prefixes).
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace anqs {
@@ -133,7 +135,7 @@ struct Tile {
   static constexpr int WS = W + 1;       // W2 row stride (float2)
   static constexpr int HS = TR + 4;      // h row stride (floats; real and imaginary planes)
   static constexpr int KP = 128 / TR;    // k-parts of the head reduction
-  static constexpr int NZ = 3;           // evaluations kept for a slot (qubit 2p, qubit 2p+1 for a = 0, 1)
+  static constexpr int NZ = 1;           // z3 tiles kept (one evaluation per CTA)
   static constexpr size_t w2_bytes = size_t(W) * WS * sizeof(float2);
   static constexpr size_t h_bytes = 2 * size_t(W) * HS * sizeof(float);
   static constexpr size_t smem_bytes = w2_bytes + h_bytes + (size_t(KP) * TR * 2 + size_t(NZ) * TR * 2) * sizeof(float2);
@@ -285,13 +287,13 @@ __device__ __forceinline__ bool path_term(const HamView& hv, int i, uint64_t x, 
   return true;
 }
 
-// The 8 values of slot p for row r from the three evaluations in Z3
-// ([3][TR][2]: qubit 2p, qubit 2p+1 given a = 0, given a = 1).
-__device__ void slot_values(const HamView& hv, int p, uint64_t x, const float2* Z3, int r, int TR, float* o8) {
+// The 8 values of slot p for row r from the three evaluations z[e] ([TR][2]
+// each: qubit 2p, qubit 2p+1 given a = 0, given a = 1).
+__device__ void slot_values(const HamView& hv, int p, uint64_t x, const float2* const (&z)[3], int r, float* o8) {
   float2 l[3][2];
 #pragma unroll
   for (int e = 0; e < 3; ++e) {  // f3
-    const float2 z0 = Z3[(e * TR + r) * 2], z1 = Z3[(e * TR + r) * 2 + 1];
+    const float2 z0 = z[e][r * 2], z1 = z[e][r * 2 + 1];
     const float mx = fmaxf(2.f * z0.x, 2.f * z1.x);
     const float lse = 0.5f * (mx + logf(expf(2.f * z0.x - mx) + expf(2.f * z1.x - mx)));
     l[e][0] = make_float2(z0.x - lse, z0.y);
@@ -389,20 +391,26 @@ __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, Fw
           }
         }
       }
-    } else {  // RAW (slot blockIdx.y), LOGITS (slot A.p)
-      const int p_lo = MODE == MODE_RAW ? int(blockIdx.y) : A.p, p_hi = p_lo + 1;
-      for (int p = p_lo; p < p_hi; ++p) {
-        eval_qubit<W, RJ>(m, 2 * p, 2 * p, 0, xt, S, S.Z3, staged);
-        eval_qubit<W, RJ>(m, 2 * p + 1, 2 * p, 0, xt, S, S.Z3 + 2 * TR, staged);
-        eval_qubit<W, RJ>(m, 2 * p + 1, 2 * p, 1, xt, S, S.Z3 + 4 * TR, staged);
-        if (tid < TR && base + tid < rows) {
-          float o8[8];
-          slot_values(hv, p, xt[tid], S.Z3, tid, TR, o8);
-          float* dst = MODE == MODE_RAW ? A.out8 + ((base + tid) * n + p) * 8 : A.out8 + (base + tid) * 8;
+    } else {
+      // RAW (slot blockIdx.y / 3), LOGITS (slot A.p): the three evaluations
+      // of the slot run in the three CTAs of a cluster (CTA e = blockIdx.y %
+      // 3: qubit 2p, qubit 2p+1 given a = 0, given a = 1); after a cluster
+      // barrier CTA 0 reads the other two z3 tiles from their shared memory
+      cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+      const int e = int(blockIdx.y % 3);
+      const int p = MODE == MODE_RAW ? int(blockIdx.y / 3) : A.p;
+      eval_qubit<W, RJ>(m, e == 0 ? 2 * p : 2 * p + 1, 2 * p, e == 2 ? 1 : 0, xt, S, S.Z3, staged);
+      cl.sync();
+      if (e == 0 && tid < TR && base + tid < rows) {
+        const float2* const z[3] = {S.Z3, cl.map_shared_rank(S.Z3, cl.block_rank() + 1),
+                                    cl.map_shared_rank(S.Z3, cl.block_rank() + 2)};
+        float o8[8];
+        slot_values(hv, p, xt[tid], z, tid, o8);
+        float* dst = MODE == MODE_RAW ? A.out8 + ((base + tid) * n + p) * 8 : A.out8 + (base + tid) * 8;
 #pragma unroll
-          for (int v = 0; v < 8; ++v) dst[v] = o8[v];
-        }
+        for (int v = 0; v < 8; ++v) dst[v] = o8[v];
       }
+      cl.sync();  // the peers' z3 stay until CTA 0 has read them
     }
     __syncthreads();
   }
@@ -410,6 +418,11 @@ __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, Fw
 
 // Grid: ny slots (RAW: one per slot) x row tiles, at most one wave of
 // resident CTAs.  RJ = 4 when its tiles fill a wave, else RJ = 1.
+// CTAs along y: RAW 3 per slot, LOGITS 3 (clusters of three, one per
+// evaluation of the slot), else 1
+template <int MODE>
+constexpr bool clustered() { return MODE == MODE_RAW || MODE == MODE_LOGITS; }
+
 template <int W, int RJ, int MODE>
 int fwd_launch(const NadeView& m, const HamView& hv, const FwdArgs& a, uint64_t max_rows, int prof, cudaStream_t s) {
   constexpr int TR = Tile<W, RJ>::TR;
@@ -418,20 +431,35 @@ int fwd_launch(const NadeView& m, const HamView& hv, const FwdArgs& a, uint64_t 
   ANQS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   int occ = 0;
   ANQS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
-  const uint64_t ny = MODE == MODE_RAW ? uint64_t(m.n) : 1;
+  const uint64_t ny = MODE == MODE_RAW ? 3ull * uint64_t(m.n) : (clustered<MODE>() ? 3ull : 1ull);
   uint64_t cap = 152ull * uint64_t(occ > 0 ? occ : 1) / ny;
   if (cap < 1) cap = 1;
   uint64_t blocks = (max_rows + TR - 1) / TR;
   if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
   ProfScope ps(prof, s);
-  ANQS_CUDA_LAUNCH("nade_fwd_kernel", launch_k(kern, dim3(unsigned(blocks ? blocks : 1), unsigned(ny)), dim3(NT), smem,
-                                               s, m, hv, a));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(blocks), unsigned(ny));
+  cfg.blockDim = dim3(NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = 1;
+  attr[1].val.clusterDim.y = clustered<MODE>() ? 3 : 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  note_launch();
+  ANQS_CUDA_LAUNCH("nade_fwd_kernel", cudaLaunchKernelEx(&cfg, kern, m, hv, a));
   return ANQS_OK;
 }
 
 template <int W, int MODE>
 int fwd_w(const NadeView& m, const HamView& hv, const FwdArgs& a, uint64_t max_rows, int prof, cudaStream_t s) {
-  const uint64_t ny = MODE == MODE_RAW ? uint64_t(m.n) : 1;
+  const uint64_t ny = MODE == MODE_RAW ? 3ull * uint64_t(m.n) : (clustered<MODE>() ? 3ull : 1ull);
   const uint64_t big_tiles = (max_rows + Tile<W, 4>::TR - 1) / Tile<W, 4>::TR;
   if (big_tiles * ny >= 152) return fwd_launch<W, 4, MODE>(m, hv, a, max_rows, prof, s);
   return fwd_launch<W, 1, MODE>(m, hv, a, max_rows, prof, s);
