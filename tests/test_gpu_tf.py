@@ -241,3 +241,35 @@ def test_tf_grad_large_central_differences(A):
         assert abs(g[i] - fd) <= 1e-4 * max(1.0, abs(fd)) + 1e-4 * np.linalg.norm(ref) / np.sqrt(len(ref)), \
             (i, g[i], fd, ref[i])
     assert checked == 16 and tried < 64, (checked, tried)
+
+
+def test_tf_local_energy_fp32_large_shape(A):
+    """26 slots, 9+9 electrons, 33,507 connected determinants per sample: the
+    oracle cannot evaluate that many amplitudes per sample in the time bound,
+    so E_loc is checked against its definition assembled in FP64 from the
+    library's connected set (bit-exact against the oracle, see
+    test_gpu_parity) and log psi (against the oracle at this shape above).
+    The library forms each ratio psi(x')/psi(x) in float32 (exp and sincos of
+    the float32 log differences) and sums in FP64, so the two agree to a few
+    float32 ulps per term: |dE| <= 1e-6 sum_k |H_k r_k| (about 17 ulps); a
+    wrong term would show as an error of order |H_k r_k|."""
+    w = workload("large", bias_std=0.2)
+    ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    model = A.Model.transformer(w["n"], w["d_model"], w["n_heads"], w["n_layers"],
+                                torch.tensor(w["params"], device="cuda"))
+    x, c = A.sample(model, ham, 2000, seed=5)
+    x, c = x[:3], c[:3]
+    ere, eim, stats = A.local_energy(model, ham, x, c)
+    xp, hv, js, hd = A.connected(ham, x)
+    assert xp.shape[1] == 33507
+    lx, px = A.logpsi(model, ham, x)
+    lp, pp = A.logpsi(model, ham, xp.reshape(-1))
+    K = ham.n_connected
+    r = torch.exp((lp.double().reshape(-1, K) - lx.double()[:, None])
+                  + 1j * (pp.double().reshape(-1, K) - px.double()[:, None]))
+    e = hd + (hv * r).sum(1)
+    bound = 1e-6 * (hv.abs() * r.abs()).sum(1)
+    assert ((e.real - ere).abs() <= bound).all()
+    assert ((e.imag - eim).abs() <= bound).all()
+    wts = c.double() / c.double().sum()
+    assert abs(float((wts * ere).sum()) - float(stats[0])) <= 1e-12 * float(ere.abs().max())
