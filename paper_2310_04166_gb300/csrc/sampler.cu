@@ -507,7 +507,6 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
                                                              uint64_t* __restrict__ pre_out,
                                                              uint64_t* __restrict__ cnt_out,
                                                              uint64_t* __restrict__ n_out) {
-  ANQS_PDL_ENTRY();
   __shared__ uint32_t s_scan[SMALL_F + 1];
   extern __shared__ __align__(16) unsigned char s_dyn[];
   uint64_t(*s_thr)[4] = reinterpret_cast<uint64_t(*)[4]>(s_dyn);                  // SMALL_T x 4
@@ -515,9 +514,12 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
   __shared__ uint8_t s_mk[SMALL_T];
   __shared__ uint32_t s_red[33];
   __shared__ bool s_last;
+  // Prologue (before the wait on the slot-logits kernel): the frontier and
+  // its counts were written two kernels back (the previous level's split, or
+  // the initial/shard kernel), so the node offsets can be scanned while the
+  // logits kernel finishes.
   const int nf = int(*n_front);
   const int lane = threadIdx.x & 31;
-  const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
   // draw-block offsets of the nodes: each thread scans a run of RUN
   // consecutive nodes (their counts loaded together), one block scan per
   // RUN * SMALL_T nodes
@@ -541,6 +543,9 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
     carry += tot;
   }
   if (threadIdx.x == 0) s_scan[nf] = carry;
+  ANQS_PDL_WAIT();
+  ANQS_PDL_TRIGGER();
+  const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
   __syncthreads();
   const uint32_t total = carry;
   auto node_of = [&](uint32_t t) {
