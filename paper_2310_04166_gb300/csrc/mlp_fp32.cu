@@ -327,7 +327,6 @@ template <int W, int RG, bool PARTIAL, bool RESIDENT>
 __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const uint64_t* __restrict__ xs,
                                                   Count n_x_, CotSrc cot, float* __restrict__ grad,
                                                   uint64_t n_params) {
-  ANQS_PDL_ENTRY();
   extern __shared__ float smem[];
   const int L = m.n_hidden;
   float* act = smem;                       // L buffers [RG][W]: h_1..h_L
@@ -337,6 +336,22 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
   __shared__ uint64_t xt[RG];
   __shared__ float cl[RG], cp[RG];
   const int p = blockIdx.y;
+  // Prologue, before the wait on the previous kernel: the hidden matrices of
+  // slot p into shared memory (row stride W + 1).  No library kernel writes
+  // the parameters, so their last update has completed before any library
+  // kernel can let this one start; rows, counts and energies are read after
+  // the wait.
+  float* wres = RESIDENT ? dh + RG * W : nullptr;
+  if (RESIDENT) {
+    const MlpPtr Pw = slot_ptrs(m, p);
+    for (int l = 0; l < L - 1; ++l) {
+      const float* src = Pw.Wk + size_t(l) * (size_t(W) * W + W);
+      float* dst = wres + size_t(l) * W * (W + 1);
+      for (int idx = threadIdx.x; idx < W * W; idx += NT) dst[(idx / W) * (W + 1) + idx % W] = __ldg(src + idx);
+    }
+  }
+  ANQS_PDL_WAIT();
+  ANQS_PDL_TRIGGER();
   const uint64_t n_x = n_x_.get();
   const uint64_t base = uint64_t(blockIdx.x) * RG;
   if (base >= n_x) return;
@@ -350,16 +365,6 @@ __global__ void __launch_bounds__(NT) grad_kernel(MlpView m, HamView hv, const u
     cp[threadIdx.x] = b;
   }
   __syncthreads();
-  // hidden matrices of slot p resident in shared memory (row stride W + 1)
-  float* wres = RESIDENT ? dh + RG * W : nullptr;
-  if (RESIDENT) {
-    const MlpPtr Pw = slot_ptrs(m, p);
-    for (int l = 0; l < L - 1; ++l) {
-      const float* src = Pw.Wk + size_t(l) * (size_t(W) * W + W);
-      float* dst = wres + size_t(l) * W * (W + 1);
-      for (int idx = threadIdx.x; idx < W * W; idx += NT) dst[(idx / W) * (W + 1) + idx % W] = __ldg(src + idx);
-    }
-  }
   const int last = slot_forward<W, RG>(m, p, xt, nrows, act, L, ws, out8, wres);
   const MlpPtr P = slot_ptrs(m, p);
   float* gbase = grad + (P.W1 - m.params) + (PARTIAL ? uint64_t(blockIdx.x) * n_params : 0ull);
