@@ -566,9 +566,13 @@ __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Cou
     const uint64_t x = xs[l];
     float la = 0.f, ph = 0.f;
     bool dead = (n < 32) && ((x >> (2 * n)) != 0);
-    int a = 0, b = 0;
+    // prefix electron counts from popcounts (not a running sum), so that the
+    // slots' loads do not wait on one another
+#pragma unroll 4
     for (int p = 0; p < n; ++p) {
       const float* o = raw + (l * n + p) * 8;
+      const uint64_t below = (1ull << (2 * p)) - 1ull;  // p < 32
+      const int a = __popcll(x & below & 0x5555555555555555ull), b = __popcll(x & below & 0xAAAAAAAAAAAAAAAAull);
       const unsigned pmk = slot_mask(hv, p, a, b, x), mk = norm_mask(hv, p, pmk);
       float mx = -INFINITY;
       for (int u = 0; u < 4; ++u)
@@ -590,8 +594,6 @@ __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Cou
       if (!((pmk >> v) & 1u)) dead = true;
       if (!dead) la += 0.5f * (o[v] - lse);
       ph += o[4 + v];
-      a += v & 1;
-      b += v >> 1;
     }
     la_out[l] = dead ? -INFINITY : la;
     ph_out[l] = ph;
