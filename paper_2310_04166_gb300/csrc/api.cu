@@ -71,11 +71,6 @@ struct IsPhysTable {
   }
 };
 
-static uint64_t sat_mul(uint64_t a, uint64_t b) {
-  if (a == 0 || b == 0) return 0;
-  if (a > UINT64_MAX / b) return UINT64_MAX;
-  return a * b;
-}
 static uint64_t sat_add(uint64_t a, uint64_t b) { return (a > UINT64_MAX - b) ? UINT64_MAX : a + b; }
 static uint64_t binom(int n, int k) {
   if (k < 0 || k > n) return 0;

@@ -61,14 +61,6 @@ __device__ __forceinline__ float2 ctanh(float ah, float al, float bh, float bl) 
   return make_float2(sa1 * ca1 * inv, sb1 * cb1 * inv);
 }
 
-// s + e = a + b exactly (Knuth's TwoSum)
-__device__ __forceinline__ float two_sum(float a, float b, float& e) {
-  const float s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-  return s;
-}
-
 __device__ __forceinline__ float lerelu(float x) { return x >= 0.f ? x : 0.01f * x; }
 
 struct QubitPtr {
@@ -122,6 +114,26 @@ __device__ __forceinline__ void cmac(float2& acc, float2 w, float2 h) {
   acc.x = fmaf(-w.y, h.y, acc.x);
   acc.y = fmaf(w.x, h.y, acc.y);
   acc.y = fmaf(w.y, h.x, acc.y);
+}
+
+// h1 = tanh z1 of one hidden unit: z1 = b1 + the sum of the W1 columns k < i
+// whose input bit is set (w1 = the unit's row of W1).  The sum is
+// Kahan-compensated: z + c carries it to about u^2, which matters only next
+// to a pole of tanh.  The loop runs over all k < i so that lanes sharing the
+// unit load each W1 entry together.
+__device__ __forceinline__ float2 input_layer(const float2* __restrict__ w1, float2 b1, uint64_t bits, int i) {
+  float2 z = b1, c = make_float2(0.f, 0.f);
+  for (int k = 0; k < i; ++k) {
+    if (!((bits >> k) & 1ull)) continue;
+    const float2 wv = __ldg(w1 + k);
+    const float yx = wv.x - c.x, yy = wv.y - c.y;
+    const float tx = z.x + yx, ty = z.y + yy;
+    c.x = (tx - z.x) - yx;
+    c.y = (ty - z.y) - yy;
+    z.x = tx;
+    z.y = ty;
+  }
+  return ctanh(z.x, -c.x, z.y, -c.y);
 }
 
 // ---------------------------------------------------------------------------
@@ -182,23 +194,7 @@ __device__ void eval_qubit(const NadeView& m, int i, int kx, int a, const uint64
     // the input bits x_<i of the row: x's bits below kx, then a at kx
     const uint64_t bits0 = (kx >= 64 ? xr : (xr & ((1ull << kx) - 1ull))) | (kx < i && a ? (1ull << kx) : 0ull);
     for (int u = tid / TR; u < W; u += NT / TR) {
-      // Kahan-compensated sum of the selected W1 columns: z + c carries the
-      // sum to about u^2, which matters only next to a pole of tanh
-      // (the loop runs over all k < i so that the lanes, which share u, load
-      // each W1 entry together)
-      const float2* w1 = q.W1 + size_t(u) * i;
-      float2 z = __ldg(q.b1 + u), c = make_float2(0.f, 0.f);
-      for (int k = 0; k < i; ++k) {
-        if (!((bits0 >> k) & 1ull)) continue;
-        const float2 wv = __ldg(w1 + k);
-        const float yx = wv.x - c.x, yy = wv.y - c.y;
-        const float tx = z.x + yx, ty = z.y + yy;
-        c.x = (tx - z.x) - yx;
-        c.y = (ty - z.y) - yy;
-        z.x = tx;
-        z.y = ty;
-      }
-      const float2 h = ctanh(z.x, -c.x, z.y, -c.y);
+      const float2 h = input_layer(q.W1 + size_t(u) * i, __ldg(q.b1 + u), bits0, i);
       S.Hr[u * HS + r] = h.x;
       S.Hi[u * HS + r] = h.y;
     }
@@ -607,7 +603,7 @@ __global__ void __launch_bounds__(NT) nade_grad_kernel(NadeView m, HamView hv, c
   extern __shared__ float2 acc[];  // qubit i's parameter block (complex entries)
   __shared__ float2 h1[R * W], h2[R * W], gz1[R * W], gz2[R * W], z3[R * 2], g3[R * 2];
   __shared__ uint64_t xt[R];
-  const int i = blockIdx.y, p = i >> 1, sigma = i & 1;
+  const int i = blockIdx.y, p = i >> 1;
   const int r = threadIdx.x / W, u = threadIdx.x % W;
   const uint32_t nc = qubit_floats(W, i) / 2;  // complex entries of the block
   const uint32_t oW1 = 0, ob1 = W * i, oW2 = ob1 + W, ob2 = oW2 + W * W, oW3 = ob2 + W, ob3 = oW3 + 2 * W;
@@ -619,20 +615,9 @@ __global__ void __launch_bounds__(NT) nade_grad_kernel(NadeView m, HamView hv, c
     __syncthreads();
     const uint64_t x = xt[r];
     // forward of qubit i on the path (bits x_<i of row r)
-    float2 z = __ldg(q.b1 + u), lo = make_float2(0.f, 0.f);
-    for (int k = 0; k < i; ++k) {
-      if ((x >> k) & 1ull) {
-        const float2 wv = __ldg(q.W1 + size_t(u) * i + k);
-        float ex, ey;
-        z.x = two_sum(z.x, wv.x, ex);
-        z.y = two_sum(z.y, wv.y, ey);
-        lo.x += ex;
-        lo.y += ey;
-      }
-    }
-    h1[r * W + u] = ctanh(z.x, lo.x, z.y, lo.y);
+    h1[r * W + u] = input_layer(q.W1 + size_t(u) * i, __ldg(q.b1 + u), x, i);
     __syncthreads();
-    z = __ldg(q.b2 + u);
+    float2 z = __ldg(q.b2 + u);
     for (int k = 0; k < W; ++k) {
       const float2 t = cmul(__ldg(q.W2 + size_t(u) * W + k), h1[r * W + k]);
       z.x += t.x;
@@ -651,16 +636,7 @@ __global__ void __launch_bounds__(NT) nade_grad_kernel(NadeView m, HamView hv, c
     }
     __syncthreads();
     if (u == 0) {  // cotangent of z3: allowed values of qubit i on the path, softmax of 2 Re z3 over them
-      unsigned allowed = 3u;
-      if (p < hv.mu_lv) {
-        const unsigned pm = prefix_mask(hv, p, x);
-        if (sigma == 0) {
-          allowed = ((pm | (pm >> 2)) & 1u) | (((pm >> 1) | (pm >> 3)) & 1u) << 1;
-        } else {
-          const int a = int((x >> (2 * p)) & 1ull);
-          allowed = ((pm >> a) & 1u) | ((pm >> (a + 2)) & 1u) << 1;
-        }
-      }
+      const unsigned allowed = qubit_allowed(hv, i, x, prefix_mask(hv, p, x));
       const int xi = int((x >> i) & 1ull);
       float2 g0 = make_float2(0.f, 0.f), g1 = g0;
       if (base + r < rows && ((allowed >> xi) & 1u)) {
