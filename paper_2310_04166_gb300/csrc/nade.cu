@@ -725,6 +725,274 @@ __global__ void __launch_bounds__(NT) nade_grad_kernel(NadeView m, HamView hv, c
   for (uint32_t e = threadIdx.x; e < nc; e += NT) o[e] = acc[e];
 }
 
+// Tiled adjoint (widths 32 and 64): CTA (g, i) takes qubit i for the row
+// tiles g, g + G, ... of TR = 4096 / W rows.  The qubit's W2 is staged in
+// shared memory once; per tile the forward keeps h1 and h2 (real and
+// imaginary planes [unit][row]), and the backward runs the two W x W
+// contractions of the adjoint, gh1 = W2^H gz2 and dW2 += gz2^T conj(h1), with
+// register tiles.  The qubit's parameter block accumulates in shared memory,
+// every entry owned by one thread and the rows taken in tile order
+// (deterministic), as in the kernel above.
+__device__ __forceinline__ void cmac_conj(float2& acc, float2 a, float2 b) {  // acc += conj(a) b
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
+template <int W>
+struct GradTile {
+  using T = Tile<W, 4>;
+  static constexpr int TR = T::TR, WS = T::WS, HS = T::HS, KP = T::KP;
+  static constexpr int UK = W / 16;  // dW2 register tile: UK units x UK inputs per thread (16 x 16 threads)
+  static size_t smem_bytes(int n) {
+    return size_t(W) * WS * sizeof(float2) + 4 * size_t(W) * HS * sizeof(float) +
+           size_t(KP) * TR * 2 * sizeof(float2) + size_t(qubit_floats(W, 2 * n - 1)) * sizeof(float);
+  }
+};
+
+template <int W>
+__global__ void __launch_bounds__(NT) nade_grad_tile_kernel(NadeView m, HamView hv, const uint64_t* __restrict__ xs,
+                                                            Count rows_, CotSrc cot, float* __restrict__ out,
+                                                            uint64_t out_stride) {
+  using G = GradTile<W>;
+  constexpr int TR = G::TR, WS = G::WS, HS = G::HS, KP = G::KP, NTX = W / 4, UK = G::UK;
+  extern __shared__ float4 dsm4[];
+  float2* W2s = reinterpret_cast<float2*>(dsm4);  // [W][WS]
+  float* H1r = reinterpret_cast<float*>(W2s + size_t(W) * WS);
+  float* H1i = H1r + W * HS;                       // h1 planes [W][HS]
+  float* Gr = H1i + W * HS;
+  float* Gi = Gr + W * HS;                         // h2, then gz2, then gz1
+  float2* Z3p = reinterpret_cast<float2*>(Gi + W * HS);
+  float2* acc = Z3p + KP * TR * 2;                 // the qubit's parameter block (complex entries)
+  __shared__ uint64_t xt[TR];
+  __shared__ float2 z3[TR * 2], g3[TR * 2];
+  const int i = blockIdx.y, p = i >> 1, tid = threadIdx.x;
+  const QubitPtr q = qubit_ptrs(m, i);
+  const uint32_t nc = qubit_floats(W, i) / 2;
+  const uint32_t ob1 = W * i, oW2 = ob1 + W, ob2 = oW2 + W * W, oW3 = ob2 + W;  // b3 follows W3 at oW3 + 2W
+  // prologue: the parameters are written before any library kernel runs
+  for (uint32_t e = tid; e < nc; e += NT) acc[e] = make_float2(0.f, 0.f);
+  for (int e = tid; e < W * W; e += NT) W2s[(e / W) * WS + (e % W)] = __ldg(q.W2 + e);
+  ANQS_PDL_WAIT();
+  ANQS_PDL_TRIGGER();
+  const uint64_t rows = rows_.get();
+  const int tx = tid % NTX, ty = tid / NTX;
+  for (uint64_t base = uint64_t(blockIdx.x) * TR; base < rows; base += uint64_t(gridDim.x) * TR) {
+    if (tid < TR) xt[tid] = base + tid < rows ? xs[base + tid] : 0ull;
+    __syncthreads();
+    {  // h1 = tanh(z1) of the path x_<i
+      const int r = tid % TR;
+      for (int u = tid / TR; u < W; u += NT / TR) {
+        const float2 h = input_layer(q.W1 + size_t(u) * i, __ldg(q.b1 + u), xt[r], i);
+        H1r[u * HS + r] = h.x;
+        H1i[u * HS + r] = h.y;
+      }
+    }
+    __syncthreads();
+    {  // z2 = W2 h1 + b2, h2 = LeReLU parts -> G planes
+      float2 z2[4][4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) z2[j][c] = make_float2(0.f, 0.f);
+#pragma unroll 2
+      for (int k = 0; k < W; ++k) {
+        float2 w[4], h[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) w[c] = W2s[(tx + NTX * c) * WS + k];
+        const float4 a4 = *reinterpret_cast<const float4*>(H1r + k * HS + 4 * ty);
+        const float4 b4 = *reinterpret_cast<const float4*>(H1i + k * HS + 4 * ty);
+        h[0] = make_float2(a4.x, b4.x);
+        h[1] = make_float2(a4.y, b4.y);
+        h[2] = make_float2(a4.z, b4.z);
+        h[3] = make_float2(a4.w, b4.w);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) cmac(z2[j][c], w[c], h[j]);
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int u = tx + NTX * c;
+        const float2 b = __ldg(q.b2 + u);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          Gr[u * HS + 4 * ty + j] = lerelu(z2[j][c].x + b.x);
+          Gi[u * HS + 4 * ty + j] = lerelu(z2[j][c].y + b.y);
+        }
+      }
+    }
+    __syncthreads();
+    {  // head: z3[r][o] = b3[o] + sum_k W3[o][k] h2[r][k]
+      constexpr int KL = W / KP;
+      const int r = tid % TR, g = tid / TR, o = g & 1, part = g >> 1;
+      float2 z = make_float2(0.f, 0.f);
+      for (int k = part * KL; k < (part + 1) * KL; ++k)
+        cmac(z, __ldg(q.W3 + o * W + k), make_float2(Gr[k * HS + r], Gi[k * HS + r]));
+      Z3p[(part * TR + r) * 2 + o] = z;
+    }
+    __syncthreads();
+    if (tid < 2 * TR) {
+      const int r = tid >> 1, o = tid & 1;
+      float2 z = __ldg(q.b3 + o);
+      for (int part = 0; part < KP; ++part) {
+        const float2 t = Z3p[(part * TR + r) * 2 + o];
+        z.x += t.x;
+        z.y += t.y;
+      }
+      z3[r * 2 + o] = z;
+    }
+    __syncthreads();
+    if (tid < TR) {  // cotangent of z3: the path's masked softmax (see the kernel above)
+      const int r = tid;
+      const uint64_t x = xt[r];
+      const unsigned allowed = qubit_allowed(hv, i, x, prefix_mask(hv, p, x));
+      const int xi = int((x >> i) & 1ull);
+      float2 g0 = make_float2(0.f, 0.f), g1 = g0;
+      if (base + r < rows && ((allowed >> xi) & 1u)) {
+        const float r0 = (allowed & 1u) ? 2.f * z3[r * 2].x : -INFINITY;
+        const float r1 = (allowed & 2u) ? 2.f * z3[r * 2 + 1].x : -INFINITY;
+        const float mx = fmaxf(r0, r1);
+        const float e0 = expf(r0 - mx), e1 = expf(r1 - mx);
+        const float pi0 = e0 / (e0 + e1), pi1 = e1 / (e0 + e1);
+        float c_l, c_p;
+        cot_of(cot, base + r, c_l, c_p);
+        g0 = make_float2(c_l * ((xi == 0 ? 1.f : 0.f) - pi0), xi == 0 ? c_p : 0.f);
+        g1 = make_float2(c_l * ((xi == 1 ? 1.f : 0.f) - pi1), xi == 1 ? c_p : 0.f);
+      }
+      g3[r * 2] = g0;
+      g3[r * 2 + 1] = g1;
+    }
+    __syncthreads();
+    // W3, b3: sum_r g3[r][o] conj(h2[r][j]), sum_r g3[r][o]
+    if (tid < 2 * W + 2) {
+      float2 sacc = acc[oW3 + tid];
+      if (tid < 2 * W) {
+        const int o = tid / W, j = tid % W;
+        for (int r = 0; r < TR; ++r) cmac_conj(sacc, make_float2(Gr[j * HS + r], Gi[j * HS + r]), g3[r * 2 + o]);
+      } else {
+        for (int r = 0; r < TR; ++r) {
+          sacc.x += g3[r * 2 + (tid - 2 * W)].x;
+          sacc.y += g3[r * 2 + (tid - 2 * W)].y;
+        }
+      }
+      acc[oW3 + tid] = sacc;
+    }
+    __syncthreads();
+    // gz2 = LeReLU'(z2) (conj(W3)^T g3), in place of h2 (sign of h2 = sign of z2)
+    for (int e = tid; e < TR * W; e += NT) {
+      const int u = e / TR, r = e % TR;
+      const float2 w0 = __ldg(q.W3 + u), w1 = __ldg(q.W3 + W + u);
+      const float2 ga = g3[r * 2], gb = g3[r * 2 + 1];
+      const float gr = w0.x * ga.x + w0.y * ga.y + w1.x * gb.x + w1.y * gb.y;
+      const float gi = w0.x * ga.y - w0.y * ga.x + w1.x * gb.y - w1.y * gb.x;
+      Gr[u * HS + r] = Gr[u * HS + r] >= 0.f ? gr : 0.01f * gr;
+      Gi[u * HS + r] = Gi[u * HS + r] >= 0.f ? gi : 0.01f * gi;
+    }
+    __syncthreads();
+    if (tid < W) {  // b2
+      float2 sacc = acc[ob2 + tid];
+      for (int r = 0; r < TR; ++r) {
+        sacc.x += Gr[tid * HS + r];
+        sacc.y += Gi[tid * HS + r];
+      }
+      acc[ob2 + tid] = sacc;
+    }
+    {  // W2[u][k] += sum_r gz2[r][u] conj(h1[r][k]): thread owns a UK x UK block of (u, k)
+      const int u0 = (tid / 16) * UK, k0 = (tid % 16) * UK;
+      float2 s[UK][UK];
+#pragma unroll
+      for (int a = 0; a < UK; ++a)
+#pragma unroll
+        for (int b = 0; b < UK; ++b) s[a][b] = make_float2(0.f, 0.f);
+      for (int r = 0; r < TR; r += 2) {
+        float2 gr2[UK], gi2[UK], hr2[UK], hi2[UK];
+#pragma unroll
+        for (int a = 0; a < UK; ++a) {
+          gr2[a] = *reinterpret_cast<const float2*>(Gr + (u0 + a) * HS + r);
+          gi2[a] = *reinterpret_cast<const float2*>(Gi + (u0 + a) * HS + r);
+          hr2[a] = *reinterpret_cast<const float2*>(H1r + (k0 + a) * HS + r);
+          hi2[a] = *reinterpret_cast<const float2*>(H1i + (k0 + a) * HS + r);
+        }
+#pragma unroll
+        for (int a = 0; a < UK; ++a)
+#pragma unroll
+          for (int b = 0; b < UK; ++b) {
+            cmac_conj(s[a][b], make_float2(hr2[b].x, hi2[b].x), make_float2(gr2[a].x, gi2[a].x));
+            cmac_conj(s[a][b], make_float2(hr2[b].y, hi2[b].y), make_float2(gr2[a].y, gi2[a].y));
+          }
+      }
+#pragma unroll
+      for (int a = 0; a < UK; ++a)
+#pragma unroll
+        for (int b = 0; b < UK; ++b) {
+          float2& d = acc[oW2 + (u0 + a) * W + k0 + b];
+          d.x += s[a][b].x;
+          d.y += s[a][b].y;
+        }
+    }
+    // gh1[r][k] = sum_u conj(W2[u][k]) gz2[r][u]: thread (tx, ty) owns inputs tx + NTX c, rows 4 ty + j
+    float2 gh[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) gh[j][c] = make_float2(0.f, 0.f);
+#pragma unroll 2
+    for (int u = 0; u < W; ++u) {
+      float2 w[4], g[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) w[c] = W2s[u * WS + tx + NTX * c];
+      const float4 a4 = *reinterpret_cast<const float4*>(Gr + u * HS + 4 * ty);
+      const float4 b4 = *reinterpret_cast<const float4*>(Gi + u * HS + 4 * ty);
+      g[0] = make_float2(a4.x, b4.x);
+      g[1] = make_float2(a4.y, b4.y);
+      g[2] = make_float2(a4.z, b4.z);
+      g[3] = make_float2(a4.w, b4.w);
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cmac_conj(gh[j][c], w[c], g[j]);
+    }
+    __syncthreads();  // gz2 and the b2 sums are done with the G planes
+    // gz1 = conj(1 - h1^2) gh1 -> G planes
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int k = tx + NTX * c, r = 4 * ty + j;
+        const float hr = H1r[k * HS + r], hi = H1i[k * HS + r];
+        const float dr = 1.f - (hr * hr - hi * hi), di = -2.f * hr * hi;
+        const float2 g = gh[j][c];
+        Gr[k * HS + r] = dr * g.x + di * g.y;
+        Gi[k * HS + r] = dr * g.y - di * g.x;
+      }
+    __syncthreads();
+    // W1[u][k] (real input bits) and b1[u]: sums of gz1 over the rows
+    for (uint32_t e = tid; e < uint32_t(W) * (i + 1); e += NT) {
+      float2 sacc = acc[e];
+      if (e < ob1) {
+        const uint32_t u = e / uint32_t(i), k = e % uint32_t(i);
+        for (int r = 0; r < TR; ++r)
+          if ((xt[r] >> k) & 1ull) {
+            sacc.x += Gr[u * HS + r];
+            sacc.y += Gi[u * HS + r];
+          }
+      } else {
+        const uint32_t u = e - ob1;
+        for (int r = 0; r < TR; ++r) {
+          sacc.x += Gr[u * HS + r];
+          sacc.y += Gi[u * HS + r];
+        }
+      }
+      acc[e] = sacc;
+    }
+    __syncthreads();
+  }
+  float2* o = reinterpret_cast<float2*>(out + blockIdx.x * out_stride + m.qoff[i]);
+  for (uint32_t e = tid; e < nc; e += NT) o[e] = acc[e];
+}
+
 __global__ void nade_partial_sum_kernel(const float* __restrict__ part, int G, uint64_t n, float* __restrict__ grad) {
   ANQS_PDL_ENTRY();
   for (uint64_t j = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n; j += uint64_t(gridDim.x) * blockDim.x) {
@@ -734,10 +1002,14 @@ __global__ void nade_partial_sum_kernel(const float* __restrict__ part, int G, u
   }
 }
 
-// CTAs per qubit: about two CTAs per SM over all 2n qubits, at most one per row tile
+// CTAs per qubit: over all 2n qubits about one CTA per SM for the tiled
+// adjoint (widths 32, 64; tiles of 4096 / W rows), two for the one of width
+// 128 (tiles of 256 / W rows); at most one per row tile
 int grad_groups(const NadeView& m, uint64_t n_x) {
-  const uint64_t tiles = (n_x + (NT / m.w) - 1) / (NT / m.w);
-  uint64_t g = (2 * 152) / uint64_t(2 * m.n);
+  const bool tiled = m.w <= 64;
+  const uint64_t tr = tiled ? uint64_t(4096 / m.w) : uint64_t(NT / m.w);
+  const uint64_t tiles = (n_x + tr - 1) / tr;
+  uint64_t g = (tiled ? 152 : 2 * 152) / uint64_t(2 * m.n);
   if (g < 1) g = 1;
   if (g > tiles) g = tiles;
   return int(g < 1 ? 1 : g);
@@ -747,13 +1019,20 @@ template <int W>
 int grad_w(const NadeView& m, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot, float* grad,
            uint64_t n_params, float* part, cudaStream_t s) {
   const int G = grad_groups(m, n_x.n);
-  const size_t smem = size_t(qubit_floats(W, 2 * m.n - 1)) * sizeof(float);
-  ANQS_CUDA(cudaFuncSetAttribute(nade_grad_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
   float* out = G > 1 ? part : grad;
   if (G > 1 && !part) return set_error(ANQS_ERR_CAPACITY, "NADE adjoint needs its partial-sum workspace");
   ProfScope ps(PROF_NADE_GRAD, s);
-  ANQS_CUDA_LAUNCH("nade_grad_kernel", launch_k(nade_grad_kernel<W>, dim3(G, 2 * m.n), dim3(NT), smem, s, m, hv, x,
-                                                n_x, cot, out, G > 1 ? n_params : uint64_t(0)));
+  if constexpr (W <= 64) {
+    const size_t smem = GradTile<W>::smem_bytes(m.n);
+    ANQS_CUDA(cudaFuncSetAttribute(nade_grad_tile_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    ANQS_CUDA_LAUNCH("nade_grad_tile_kernel", launch_k(nade_grad_tile_kernel<W>, dim3(G, 2 * m.n), dim3(NT), smem, s, m,
+                                                       hv, x, n_x, cot, out, G > 1 ? n_params : uint64_t(0)));
+  } else {
+    const size_t smem = size_t(qubit_floats(W, 2 * m.n - 1)) * sizeof(float);
+    ANQS_CUDA(cudaFuncSetAttribute(nade_grad_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)));
+    ANQS_CUDA_LAUNCH("nade_grad_kernel", launch_k(nade_grad_kernel<W>, dim3(G, 2 * m.n), dim3(NT), smem, s, m, hv, x,
+                                                  n_x, cot, out, G > 1 ? n_params : uint64_t(0)));
+  }
   if (G > 1) {
     uint64_t blocks = (n_params + 255) / 256;
     if (blocks > 152 * 4) blocks = 152 * 4;
