@@ -154,6 +154,14 @@ struct Tile {
   static_assert(NTX * NTY == NT && NT % TR == 0 && W % KP == 0 && TR % 4 == 0, "tile shape");
 };
 
+// asynchronous global -> shared copy of 8 bytes (both 8-byte aligned)
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(smem_dst));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 struct TileSmem {
   float2* W2;        // [W][WS]: W2[u][k] at u * WS + k
   float *Hr, *Hi;    // [W][HS]: h[r][k] at k * HS + r
@@ -175,15 +183,23 @@ __device__ __forceinline__ TileSmem tile_smem(float2* base) {
 
 // z3 of qubit i for the tile's rows into z3out[r][2].  Bit k < i of row r is
 // bit k of xt[r] for k < kx and `a` for k = kx (kx = i: all bits from x).
-// `staged` is the qubit whose W2 is in shared memory (uniform over the CTA).
+// `staged` is the qubit whose W2 is in shared memory or on its way there
+// (`pending`: asynchronous copies in flight), uniform over the CTA.  With
+// next >= 0, qubit next's W2 is copied in asynchronously as soon as this
+// evaluation's GEMM is done with the buffer, so the copy overlaps the head,
+// the caller's row work and the next evaluation's input layer.
 // Starts and ends with the CTA synchronised.
 template <int W, int RJ>
 __device__ void eval_qubit(const NadeView& m, int i, int kx, int a, const uint64_t* xt, const TileSmem& S,
-                           float2* z3out, int& staged) {
+                           float2* z3out, int& staged, bool& pending, int next) {
   using T = Tile<W, RJ>;
   constexpr int TR = T::TR, WS = T::WS, HS = T::HS, NTX = T::NTX;
   const int tid = threadIdx.x;
   const QubitPtr q = qubit_ptrs(m, i);
+  if (pending) {  // this thread's copies land before the barrier that ends the input layer
+    cp_async_wait_all();
+    pending = false;
+  }
   if (staged != i) {  // W2 [u][k] -> shared [u][k] (coalesced, conflict-free)
     for (int e = tid; e < W * W; e += NT) S.W2[(e / W) * WS + (e % W)] = __ldg(q.W2 + e);
     staged = i;
@@ -231,7 +247,14 @@ __device__ void eval_qubit(const NadeView& m, int i, int kx, int a, const uint64
 #pragma unroll
       for (int c = 0; c < 4; ++c) cmac(z2[j][c], w[c], h[j]);
   }
-  __syncthreads();  // h1 fully consumed: h2 overwrites it
+  __syncthreads();  // h1 fully consumed: h2 overwrites it; W2 no longer read
+  if (next >= 0 && next != i) {
+    const float2* src = qubit_ptrs(m, next).W2;
+    for (int e = tid; e < W * W; e += NT) cp_async8(S.W2 + (e / W) * WS + (e % W), src + e);
+    cp_async_commit();
+    staged = next;
+    pending = true;
+  }
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const int u = tx + NTX * c;
@@ -336,6 +359,7 @@ __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, Fw
   const int n = m.n, tid = threadIdx.x;
   const uint64_t rows = MODE == MODE_SUFFIX ? uint64_t(A.offsets[n - 1]) : A.rows.get();
   int staged = -1;
+  bool pending = false;
   for (uint64_t base = uint64_t(blockIdx.x) * TR; base < rows; base += uint64_t(gridDim.x) * TR) {
     if (tid < TR) {
       const uint64_t l = base + tid;
@@ -355,7 +379,7 @@ __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, Fw
     __syncthreads();
     if (MODE == MODE_LOGPSI) {
       for (int i = 0; i < 2 * n; ++i) {
-        eval_qubit<W, RJ>(m, i, i, 0, xt, S, S.Z3, staged);
+        eval_qubit<W, RJ>(m, i, i, 0, xt, S, S.Z3, staged, pending, i + 1 < 2 * n ? i + 1 : -1);
         if (tid < TR) {
           float tr = 0.f, ti;
           if (path_term(hv, i, xt[tid], S.Z3[tid * 2], S.Z3[tid * 2 + 1], tr, ti)) la[tid] += tr;
@@ -374,7 +398,7 @@ __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, Fw
       // rows are in ascending j: the tile's first row has the smallest, and
       // every row needs the slots above its own j only
       for (int i = 2 * (jr[0] + 1); i < 2 * n; ++i) {
-        eval_qubit<W, RJ>(m, i, i, 0, xt, S, S.Z3, staged);
+        eval_qubit<W, RJ>(m, i, i, 0, xt, S, S.Z3, staged, pending, i + 1 < 2 * n ? i + 1 : -1);
         const int p = i >> 1;
         if (tid < TR && p > jr[tid]) {
           float tr = 0.f, ti;
@@ -395,7 +419,7 @@ __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, Fw
       cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
       const int e = int(blockIdx.y % 3);
       const int p = MODE == MODE_RAW ? int(blockIdx.y / 3) : A.p;
-      eval_qubit<W, RJ>(m, e == 0 ? 2 * p : 2 * p + 1, 2 * p, e == 2 ? 1 : 0, xt, S, S.Z3, staged);
+      eval_qubit<W, RJ>(m, e == 0 ? 2 * p : 2 * p + 1, 2 * p, e == 2 ? 1 : 0, xt, S, S.Z3, staged, pending, -1);
       cl.sync();
       if (e == 0 && tid < TR && base + tid < rows) {
         const float2* const z[3] = {S.Z3, cl.map_shared_rank(S.Z3, cl.block_rank() + 1),
@@ -410,6 +434,7 @@ __global__ void __launch_bounds__(NT) nade_fwd_kernel(NadeView m, HamView hv, Fw
     }
     __syncthreads();
   }
+  if (pending) cp_async_wait_all();  // no copy outlives the CTA
 }
 
 // Grid: ny slots (RAW: one per slot) x row tiles, at most one wave of
