@@ -423,12 +423,14 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_ws_kernel(TcView tv, HamView hv,
   c.bar_m = tc::smem_u32(&bars[2 + wg]);
   c.wg = wg;
   c.t = t;
-  // partition of the grid among the slots (same result in every CTA)
-  uint64_t tiles[ANQS_MAX_ORB];
+  // partition of the grid among the slots (same result in every CTA); the
+  // slots' tile counts go to shared memory once, not to every thread's stack
+  __shared__ uint32_t tiles[ANQS_MAX_ORB];
+  if (threadIdx.x < n) tiles[threadIdx.x] = uint32_t((uint64_t(offsets[threadIdx.x]) + MT - 1) / MT);
+  __syncthreads();
   uint64_t total = 0;
   int S = 0;
   for (int p = 0; p < n; ++p) {
-    tiles[p] = (uint64_t(offsets[p]) + MT - 1) / MT;
     total += tiles[p];
     S += tiles[p] ? 1 : 0;
   }
