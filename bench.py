@@ -225,7 +225,7 @@ def _config(w, args):
 # DRAM bytes per launch from one ncu capture of the same kernel build and
 # workload (`ncu --set full -k regex:<kernel> -c 1 python bench.py
 # --kernel-case`, h2o, BF16 form): dram__bytes_read.sum + dram__bytes_write.sum
-TRAFFIC = {("h2o", "bf16"): {"mlp_fp32_grad_kernel": 1101824 + 43520, "mlp_tc_suffix_kernel": 1280000 + 6912,
+TRAFFIC = {("h2o", "bf16"): {"mlp_fp32_grad_kernel": 1101824 + 43520, "mlp_tc_suffix_kernel": 1273088 + 256,
                              "mlp_tc_parent_kernel": 591616, "eloc_assemble_kernel": 4649472,
                              "connected_kernel": 64256}}
 
