@@ -89,3 +89,13 @@ def test_shard_and_combine_arguments_rejected_on_host(lib):
     buf = C.create_string_buffer(8 * 8)
     assert lib.anqs_stats_combine(buf, 0, buf, None) == -1
     assert lib.anqs_sample_shard(None, None, 10, 0, 0, None, 0, 2, 1, None, None, 0, None, None, 0, None) == -1
+
+
+def test_batch_arguments_rejected_on_host(lib):
+    """The batched local energy's argument checks come before any CUDA call."""
+    h = C.c_void_p()
+    assert lib.anqs_batch_create(None, 4) == -1
+    assert lib.anqs_batch_create(C.byref(h), 0) == -1 and not h.value
+    assert lib.anqs_batch_create(C.byref(h), 5000) == -1 and not h.value
+    assert lib.anqs_batch_destroy(None) == 0
+    assert lib.anqs_batched_local_energy(None, None, 0, None) == -1
