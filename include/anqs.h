@@ -143,7 +143,7 @@ ANQS_API int anqs_hamiltonian_destroy(anqs_ham* ham);
 
 /* Pruning strategy of unphysical subtrees (Sec. III.C, Fig. 1C): MU-d with
  * d = du_levels, i.e. MU on the first n_orb - d slots and DU on the last d
- * (slot levels of this build's 4-way tree).  d = 0 (the default) is MU:
+ * (slot levels of the library's 4-way tree).  d = 0 (the default) is MU:
  * conditionals are renormalised over the allowed outcomes and no sample is
  * lost.  d = n_orb is DU: on a DU level the conditional is the network's
  * softmax over all four outcomes, and samples drawn into an unphysical child

@@ -227,7 +227,7 @@ class NADEAnsatz:
     z - 1/2 LSE(2 Re z) over its two outputs, so that
     log psi_i(x_i | x_<i) = f3(z)_{x_i}.
 
-    The slot formulation of this build groups qubits 2p (alpha) and 2p + 1
+    The slot formulation used here groups qubits 2p (alpha) and 2p + 1
     (beta): the slot conditional of v = a + 2b is psi_{2p}(a) psi_{2p+1}(b | a).
     MU masking acts on each qubit's binary conditional (Sec. III.C): the
     allowed values of qubit 2p are those a with some allowed (a, b) in the

@@ -13,7 +13,7 @@ TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
 Qubit order (Appendix A): 1-based odd qubits carry spin up.  In 0-based terms
 qubit q = 2 p + sigma with p the spatial orbital and sigma = 0 for alpha.  The
-autoregressive unit of this build is the spatial orbital ("slot"): slot p
+autoregressive unit used here is the spatial orbital ("slot"): slot p
 takes the value v = x_{2p} + 2 x_{2p+1}, and outcome v is allowed when the
 qubit-level IsPhys of the prefix extended by both qubits is True.
 

@@ -110,7 +110,7 @@ int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, C
     case ANQS_MODEL_NADE:
       return launch_nade_logpsi(M->nade, H->v, x, n_x, la, ph, s);
     default:
-      return set_error(ANQS_ERR_UNSUPPORTED, "model kind %d not available in this build", M->d.kind);
+      return set_error(ANQS_ERR_UNSUPPORTED, "model kind %d not supported by this library", M->d.kind);
   }
 }
 }  // namespace anqs
@@ -135,7 +135,7 @@ namespace anqs {
 // model kinds with a hand-written adjoint
 static int check_adjoint(const anqs_model* M) {
   if (M->d.kind == ANQS_MODEL_MLP || M->d.kind == ANQS_MODEL_TF || M->d.kind == ANQS_MODEL_NADE) return ANQS_OK;
-  return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not available in this build", M->d.kind);
+  return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not supported by this library", M->d.kind);
 }
 
 // model-specific adjoint workspace (bytes) beyond the two cotangent arrays
@@ -154,7 +154,7 @@ static int vjp_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* 
   if (M->d.kind == ANQS_MODEL_NADE)
     return launch_nade_grad(M->nade, H->v, x, n_x, CotSrc{cl, cp, nullptr, nullptr, nullptr, nullptr}, grad,
                             M->n_params, static_cast<float*>(ws), s);
-  return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not available in this build", M->d.kind);
+  return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not supported by this library", M->d.kind);
 }
 }  // namespace anqs
 

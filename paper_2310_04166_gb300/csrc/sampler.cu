@@ -816,7 +816,7 @@ int logits_dispatch(const anqs_model* M, const anqs_ham* H, int p, const uint64_
     case ANQS_MODEL_NADE:
       return launch_nade_slot_logits(M->nade, H->v, p, pre, n_dev, max_rows, out8, s);
     default:
-      return set_error(ANQS_ERR_UNSUPPORTED, "sampling for model kind %d not available in this build", M->d.kind);
+      return set_error(ANQS_ERR_UNSUPPORTED, "sampling for model kind %d not supported by this library", M->d.kind);
   }
 }
 
