@@ -404,8 +404,10 @@ ANQS_API int anqs_grad(const anqs_model* model, const anqs_ham* ham, const uint6
  * + cot_phase_dev[l] arg psi(x_l)].  anqs_grad is this product with the
  * cotangents 2 (n_l/S) Re(eloc_l - E) and 2 (n_l/S) Im(eloc_l - E).
  * The transformer's adjoint keeps every forward activation of the n_x
- * determinants in the workspace (anqs_logpsi_vjp_workspace_size); the MLP's
- * needs none (workspace may be null). */
+ * determinants in the workspace (anqs_logpsi_vjp_workspace_size); the NADE's
+ * uses it for per-CTA partial gradients when its rows span several tile
+ * groups; the MLP's needs none (workspace may be null).  The table model has
+ * no adjoint: ANQS_ERR_UNSUPPORTED before anything is queued. */
 ANQS_API int anqs_logpsi_vjp_workspace_size(const anqs_model* model, const anqs_ham* ham, uint64_t n_x,
                                             size_t* bytes);
 ANQS_API int anqs_logpsi_vjp(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev, uint64_t n_x,
