@@ -389,6 +389,50 @@ def _run_form(A, lib, args, w, form, ham, params, dev, rank, dist, stream_clocks
             "clocks": clk.summary()}
 
 
+def _large(args, dev):
+    """Config-4 shape (26 orbitals, 9+9 electrons, transformer d128 h8 L4,
+    33,507 connected determinants per sample): local energies per second of
+    anqs_local_energy over a bounded sample (the 64 most frequent unique
+    samples of one 2000-sample pass), FP32 form, since the tensor-core
+    transformer covers d = 64 only.  An auxiliary line, not the headline
+    workload; it prints one JSON line."""
+    import paper_2310_04166_gb300 as A
+    from synthetic import workload
+    w = workload("large")
+    ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    model = A.Model.transformer(w["n"], w["d_model"], w["n_heads"], w["n_layers"],
+                                torch.tensor(w["params"], device=dev))
+    x, c = A.sample(model, ham, 2000, seed=1234)
+    keep = torch.argsort(c, descending=True, stable=True)[:64]
+    x, c = x[keep].contiguous(), c[keep].contiguous()
+    ws = A._ws(A.local_energy_workspace_bytes(model, ham, x.numel()), dev)
+    out = (torch.empty(x.numel(), dtype=torch.float64, device=dev),
+           torch.empty(x.numel(), dtype=torch.float64, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
+    for _ in range(args.warmup):
+        A.local_energy(model, ham, x, c, workspace=ws, out=out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(dev.index or 0) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            A.local_energy(model, ham, x, c, workspace=ws, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    K = ham.n_connected
+    print(json.dumps({"metric": METRIC, "value": x.numel() / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f32 network / f64 E_loc", "data": "synthetic",
+                      "config": {"workload": f"large: n_orb={w['n']} N_a={w['n_alpha']} N_b={w['n_beta']}, "
+                                             f"transformer d{w['d_model']} h{w['n_heads']} L{w['n_layers']}, "
+                                             f"{x.numel()} unique samples x {K} connected determinants per step",
+                                 "form": "fp32", "timed": "anqs_local_energy only (connected set, amplitudes of "
+                                                          "every connected determinant, E_loc, statistics)",
+                                 "l2": f"working set above L2 ({x.numel() * K} connected determinants)"},
+                      "clocks": clk.summary()}), flush=True)
+
+
 def _batch32(args, dev):
     """32 independent problems (seeds 100..131, n in [6, 14], MLP 3x128 each,
     N_s = 1e5 each): the BF16 form with all passes in one CUDA graph (one
@@ -495,6 +539,9 @@ def main():
     dev = torch.device("cuda", local)
     if args.workload == "batch32":
         _batch32(args, dev)
+        return
+    if args.workload == "large":
+        _large(args, dev)
         return
     ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
     params = torch.tensor(w["params"], device=dev)
