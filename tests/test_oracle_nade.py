@@ -80,3 +80,56 @@ def test_each_qubit_conditional_is_normalised():
         bits = torch.tensor(rng.integers(0, 2, (7, i)).astype(np.float64))
         lq = om._qubit(i, bits)
         assert torch.allclose(torch.exp(2 * lq.real).sum(1), torch.ones(7, dtype=torch.float64), atol=1e-13)
+
+
+def test_nade_gradient_matches_central_differences():
+    """The oracle's NADE gradient (autograd through log psi, which the GPU
+    adjoint is tested against) equals FP64 central differences of
+    L = sum_l [c_l log|psi(x_l)| + c'_l arg psi(x_l)] on 12 random real and
+    imaginary weight parts.  L is piecewise smooth (LeReLU), so a parameter
+    is used only where the differences with steps h and h/2 agree to their
+    rounding, i.e. no kink lies within the stencil."""
+    import torch
+    n, na, nb, w = 3, 2, 1, 8
+    qubits = nade_params(9, n, w, bias_std=0.4)
+    ip = molecular_isphys(n, na, nb)
+    om = NADEAnsatz(qubits, n, ip)
+    st = np.array(sector_states(n, na, nb), dtype=np.uint64)
+    rng = np.random.default_rng(3)
+    ca, cp = torch.tensor(rng.normal(size=len(st))), torch.tensor(rng.normal(size=len(st)))
+    ps = om.parameters()
+    for t in ps:
+        t.requires_grad_(True)
+    la, ph = log_psi(om, ip, st)
+    grads = torch.autograd.grad((ca * la).sum() + (cp * ph).sum(), ps, allow_unused=True)
+    for t in ps:
+        t.requires_grad_(False)
+
+    def loss():
+        a, b = log_psi(om, ip, st)
+        return float((ca * a).sum() + (cp * b).sum())
+
+    sizes = [t.numel() for t in ps]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    h, checked = 1e-4, 0
+    for i in rng.permutation(offs[-1]):
+        if checked == 12:
+            break
+        k = int(np.searchsorted(offs, i, side="right") - 1)
+        flat = ps[k].view(-1)
+        j = int(i - offs[k])
+        old = float(flat[j])
+        d = {}
+        for step in (h, h / 2):
+            flat[j] = old + step
+            lp = loss()
+            flat[j] = old - step
+            lm = loss()
+            flat[j] = old
+            d[step] = (lp - lm) / (2 * step)
+        if abs(d[h] - d[h / 2]) > 1e-9 * max(1.0, abs(d[h])):
+            continue  # a LeReLU kink within the stencil
+        g = float(grads[k].view(-1)[j]) if grads[k] is not None else 0.0
+        assert abs(g - d[h / 2]) <= 1e-7 * max(1.0, abs(g)), (k, j, g, d)
+        checked += 1
+    assert checked == 12
