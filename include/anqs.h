@@ -352,7 +352,8 @@ ANQS_API int anqs_local_energy(const anqs_model* model, const anqs_ham* ham, con
  *   workspace size from anqs_local_energy_workspace_size) before anything is
  *   queued; errors: ANQS_ERR_ARG, ANQS_ERR_CAPACITY (a workspace too small or
  *   more problems than the handle's streams), ANQS_ERR_UNSUPPORTED, as for
- *   anqs_local_energy.
+ *   anqs_local_energy.  A CUDA error while queueing (ANQS_ERR_CUDA) still
+ *   joins the work already queued into `stream`.
  * - Problems may share a model or a Hamiltonian (read only) but not their
  *   outputs or workspaces.
  * - The handle owns max_problems non-blocking streams and max_problems + 1

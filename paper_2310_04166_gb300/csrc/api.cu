@@ -756,16 +756,25 @@ int anqs_batched_local_energy(anqs_batch* b, const anqs_eloc_problem* q, int n, 
   if (n == 0) return ANQS_OK;
   cudaStream_t s = (cudaStream_t)stream;
   ANQS_CUDA(cudaEventRecord(b->fork, s));
-  for (int k = 0; k < n; ++k) {
+  int queued = 0, r = ANQS_OK;
+  for (int k = 0; k < n && r == ANQS_OK; ++k) {
     cudaStream_t sk = b->streams[k];
-    ANQS_CUDA(cudaStreamWaitEvent(sk, b->fork, 0));
-    ANQS_TRY(anqs_local_energy(q[k].model, q[k].ham, q[k].x_dev, q[k].counts_dev, q[k].n_x, q[k].n_x_dev,
-                               q[k].eloc_re_dev, q[k].eloc_im_dev, q[k].stats_dev, q[k].workspace_dev,
-                               q[k].workspace_bytes, sk));
-    ANQS_CUDA(cudaEventRecord(b->done[k], sk));
+    if (cudaStreamWaitEvent(sk, b->fork, 0) != cudaSuccess) {
+      r = set_error(ANQS_ERR_CUDA, "batched local energy: stream fork failed");
+      break;
+    }
+    r = anqs_local_energy(q[k].model, q[k].ham, q[k].x_dev, q[k].counts_dev, q[k].n_x, q[k].n_x_dev,
+                          q[k].eloc_re_dev, q[k].eloc_im_dev, q[k].stats_dev, q[k].workspace_dev,
+                          q[k].workspace_bytes, sk);
+    // join whatever this problem queued, even on an error, so that the
+    // caller's stream stays ordered after it
+    if (cudaEventRecord(b->done[k], sk) == cudaSuccess) ++queued;
+    else if (r == ANQS_OK) r = set_error(ANQS_ERR_CUDA, "batched local energy: event record failed");
   }
-  for (int k = 0; k < n; ++k) ANQS_CUDA(cudaStreamWaitEvent(s, b->done[k], 0));
-  return ANQS_OK;
+  for (int k = 0; k < queued; ++k)
+    if (cudaStreamWaitEvent(s, b->done[k], 0) != cudaSuccess && r == ANQS_OK)
+      r = set_error(ANQS_ERR_CUDA, "batched local energy: stream join failed");
+  return r;
 }
 
 int anqs_grad_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_x, size_t* bytes) {
