@@ -54,29 +54,92 @@ def _peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """SM clocks and throttle reasons sampled during a region.
+
+    NVML is read directly (libnvidia-ml through ctypes) every millisecond
+    from a helper thread, so that even a timed region of a few milliseconds
+    holds samples; nvidia-smi at its 20 ms period is the fallback when the
+    library cannot be loaded.  Only reads: no setting of the GPU is changed."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    # NVML clock event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
+        self.samples = []  # (time, sm_mhz, max_mhz, reason bits) from NVML
+        self.nvml = None
+        self.stop = threading.Event()
+        self.source = "none"
+
+    def _nvml_handle(self):
+        import ctypes as C
+        lib = C.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            return None
+        h = C.c_void_p()
+        # the CUDA device's own UUID first (NVML ignores CUDA_VISIBLE_DEVICES)
+        try:
+            u = str(torch.cuda.get_device_properties(self.index).uuid)
+        except Exception:
+            u = ""
+        for cand in ([u, "GPU-" + u] if u else []):
+            if lib.nvmlDeviceGetHandleByUUID(cand.encode(), C.byref(h)) == 0:
+                return lib, h
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        ids = [s.strip() for s in vis.split(",") if s.strip()]
+        idx = self.index
+        if self.index < len(ids):
+            if ids[self.index].isdigit():
+                idx = int(ids[self.index])
+            elif lib.nvmlDeviceGetHandleByUUID(ids[self.index].encode(), C.byref(h)) == 0:
+                return lib, h
+        if lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(idx), C.byref(h)) == 0:
+            return lib, h
+        return None
+
+    def _poll(self):
+        import ctypes as C
+        lib, h = self.nvml
+        mhz, mx, bits = C.c_uint(), C.c_uint(), C.c_ulonglong()
+        get_reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        while not self.stop.is_set():
+            if (lib.nvmlDeviceGetClockInfo(h, 1, C.byref(mhz)) == 0 and
+                    lib.nvmlDeviceGetMaxClockInfo(h, 1, C.byref(mx)) == 0 and get_reasons(h, C.byref(bits)) == 0):
+                self.samples.append((time.perf_counter(), float(mhz.value), float(mx.value), int(bits.value)))
+            time.sleep(0.001)
 
     def __enter__(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "20"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
-            t0 = time.perf_counter()  # the sampler is running before the region starts
-            while not self.lines and time.perf_counter() - t0 < 5.0:
-                time.sleep(0.01)
+            self.nvml = self._nvml_handle()
         except OSError:
-            self.proc = None
+            self.nvml = None
+        if self.nvml:
+            self.source = "nvml 1 ms"
+            self.t = threading.Thread(target=self._poll, daemon=True)
+            self.t.start()
+            t0 = time.perf_counter()
+            while not self.samples and time.perf_counter() - t0 < 2.0:
+                time.sleep(0.001)
+        else:
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                              "--format=csv,noheader,nounits", "-lms", "20"],
+                                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                self.source = "nvidia-smi 20 ms"
+                self.t = threading.Thread(target=self._read, daemon=True)
+                self.t.start()
+                t0 = time.perf_counter()  # the sampler is running before the region starts
+                while not self.lines and time.perf_counter() - t0 < 5.0:
+                    time.sleep(0.01)
+            except OSError:
+                self.proc = None
         self.t_begin = time.perf_counter()
         return self
 
@@ -86,6 +149,9 @@ class Clocks:
 
     def __exit__(self, *a):
         self.t_end = time.perf_counter()
+        self.stop.set()
+        if self.nvml:
+            self.t.join(timeout=1.0)
         if self.proc:
             self.proc.terminate()
             try:
@@ -95,26 +161,36 @@ class Clocks:
 
     def summary(self):
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        inside = [ln for t, ln in self.lines if self.t_begin <= t <= self.t_end]
-        if not inside:  # region shorter than the sampling period: the first sample after its start
-            inside = [ln for t, ln in self.lines if t >= self.t_begin][:1]
-        for ln in inside:
-            f = [t.strip() for t in ln.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
-            except ValueError:
-                continue
-            for nm, val in zip(names, f[5:9]):
-                if val.lower() == "active":
-                    reasons.add(nm)
+        if self.nvml:
+            inside = [s for s in self.samples if self.t_begin <= s[0] <= self.t_end]
+            for _, a, b, bits in inside:
+                sm.append(a)
+                mx.append(b)
+                for bit, nm in self.REASONS.items():
+                    if bits & bit:
+                        reasons.add(nm)
+        else:
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            inside = [ln for t, ln in self.lines if self.t_begin <= t <= self.t_end]
+            if not inside:  # region shorter than the sampling period: the first sample after its start
+                inside = [ln for t, ln in self.lines if t >= self.t_begin][:1]
+            for ln in inside:
+                f = [t.strip() for t in ln.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    mx.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, f[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
         if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0,
+                    "source": self.source}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": self.source}
 
 
 def _dist():
@@ -223,11 +299,17 @@ def _config(w, args):
 
 
 # DRAM bytes per launch from one ncu capture of the same kernel build and
-# workload (`ncu --set full -k regex:<kernel> -c 1 python bench.py
-# --kernel-case`, h2o, BF16 form): dram__bytes_read.sum + dram__bytes_write.sum
+# workload (`ncu --set full --clock-control none -k regex:<kernel> -c 1
+# python bench.py --kernel-case`, h2o, BF16 form): dram__bytes_read.sum +
+# dram__bytes_write.sum
 TRAFFIC = {("h2o", "bf16"): {"mlp_fp32_grad_kernel": 1101824 + 43520, "mlp_tc_suffix_kernel": 1273088 + 256,
                              "mlp_tc_parent_kernel": 591616, "eloc_assemble_kernel": 4649472,
                              "connected_kernel": 64256}}
+
+
+# kernel families that evaluate the connected determinants' amplitudes, in
+# order of preference for the headline roofline
+AMPLITUDE_FAMILIES = ("mlp_tc_suffix_kernel", "tf_tc_suffix_kernel", "nade_suffix_kernel", "tf_fp32_kernel")
 
 
 def _make_model(A, w, params, form):
@@ -363,7 +445,8 @@ def _run_form(A, lib, args, w, form, ham, params, dev, rank, dist, stream_clocks
         total_ms, total_u = float(tm[0]), float(t[1])
     value = total_u / (total_ms / 1e3)
     k_last = int(nu.item())
-    last = {"x": x[:k_last].clone(), "cnt": cnt[:k_last].cpu().numpy(), "stats": stats.cpu().numpy().copy()}
+    last = {"x": x[:k_last].clone(), "cnt": cnt[:k_last].cpu().numpy(), "stats": stats.cpu().numpy().copy(),
+            "ere": ere[:k_last].cpu().numpy().copy()}
 
     # end to end through the public API: host parameters in, host energy
     # statistics and gradient out, around each graph replay
@@ -387,6 +470,66 @@ def _run_form(A, lib, args, w, form, ham, params, dev, rank, dist, stream_clocks
                     "d2h_bytes_per_step": int(4 * 8 + model.n_params * 4 + 8)},
             "launches_per_step": launches_per_step, "prof": prof, "n_prof": n_prof, "last": last,
             "clocks": clk.summary()}
+
+
+def _oracle_subset(w, last, m=48, seed=7):
+    """|E_gpu - E_oracle| estimated from m samples of the step's unique set,
+    drawn with probability proportional to their counts: the mean of
+    E_loc,gpu - E_loc,oracle over the draws is an unbiased estimate of the
+    count-weighted energy difference (its standard error beside it).  For
+    sample sets too large for the FP64 oracle to evaluate whole within the
+    bench's time bound."""
+    from oracle.anqs import MLPAnsatz, TFAnsatz
+    from oracle.hamiltonian import Hamiltonian as OHam
+    from oracle.sector import molecular_isphys
+    from oracle.vmc import local_energy
+    oham = OHam(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    ip = molecular_isphys(w["n"], w["n_alpha"], w["n_beta"])
+    om = MLPAnsatz(w["params_struct"], w["n"]) if w["kind"] == "mlp" else TFAnsatz(w["params_struct"], w["n"],
+                                                                                    w["n_heads"])
+    xs = last["x"].cpu().numpy().astype(np.uint64)
+    cnt = np.asarray(last["cnt"], dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    pick = rng.choice(len(xs), size=min(m, len(xs)), replace=True, p=cnt / cnt.sum())
+    uniq, inv = np.unique(pick, return_inverse=True)
+    t0 = time.perf_counter()
+    e_ref = np.concatenate([local_energy(om, ip, oham, xs[uniq[a:a + 8]]) for a in range(0, len(uniq), 8)]).real
+    d = (last["ere"][uniq] - e_ref)[inv]
+    return {"abs_dE_ha_estimate": abs(float(d.mean())), "stderr_ha": float(d.std(ddof=1) / np.sqrt(len(d))),
+            "max_abs_dEloc_ha": float(np.abs(d).max()), "draws": int(len(d)), "oracle_s": time.perf_counter() - t0,
+            "how": f"{len(d)} draws (proportional to counts) of the {len(xs)} unique samples, FP64 oracle E_loc"}
+
+
+def _sub_workload(A, lib, args, name, dev, rank, dist, steps):
+    """Both forms of another workload, timed as the headline one (graph replay
+    of the whole step, L2 flushed between steps), with the amplitude
+    contraction's roofline and the oracle comparison on a count-weighted
+    subset of each form's last sample set."""
+    import copy
+    from synthetic import workload
+    w = workload(name)
+    a = copy.copy(args)
+    a.steps, a.n_samples, a.binomial = steps, 0, False
+    ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    params = torch.tensor(w["params"], device=dev)
+    out = {"config": _config(w, a)["workload"], "steps": steps}
+    peaks, src = _peaks()
+    for form in ("bf16", "fp32"):
+        r = _run_form(A, lib, a, w, form, ham, params, dev, rank, dist, True)
+        work = _tc_work(A, ham, r["model"], w, r["last"]["x"])
+        roof, _ = _rooflines(r["prof"], work, r["n_prof"], peaks, src, {})
+        f = {"value": r["value"], "ms_per_step": r["ms_per_step"], "n_unique_per_step": r["n_unique"],
+             "E_ha": float(r["last"]["stats"][0]), "clocks": r["clocks"]}
+        if roof:
+            f["roofline"] = {k: roof[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac",
+                                                  "avg_launch_us")}
+        if not args.no_cpu_baseline:
+            f["oracle"] = _oracle_subset(w, r["last"])
+        out[form] = f
+        del r
+        torch.cuda.empty_cache()
+    out["bf16_over_fp32"] = out["bf16"]["value"] / out["fp32"]["value"]
+    return out
 
 
 def _large(args, dev):
@@ -514,6 +657,7 @@ def main():
     ap.add_argument("--workload", default="h2o")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--one-form", action="store_true", help="time only --form (default: both forms)")
+    ap.add_argument("--no-extra", action="store_true", help="h2o only: leave out the n2 sub-workload")
     ap.add_argument("--binomial", action="store_true", help="binomial statistics sampling (chained binomials per node)")
     ap.add_argument("--n-samples", type=float, default=0, help="N_s of the sampling pass (default: the workload's)")
     ap.add_argument("--kernel-case", action="store_true",
@@ -598,6 +742,9 @@ def main():
             "roofline": roof, "rooflines": roofs, "top_kernel_family": top, "clocks": r["clocks"]}
     if cpu:
         line["cpu_baseline"] = cpu
+    if args.workload == "h2o" and not args.no_extra and ws == 1:
+        # the N2-shaped transformer workload in the same line, fewer steps (its FP32 form takes ~0.75 s a step)
+        line["workloads"] = {"n2": _sub_workload(A, lib, args, "n2", dev, rank, dist, min(args.steps, 10))}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -713,8 +860,12 @@ def _rooflines(prof, work, steps, peaks, src, traffic):
         out[name] = {"kernel": name, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
                      "frac": ach / peak, "traffic": traffic.get(name), "avg_launch_us": avg_s * 1e6,
                      "work_per_launch": per_launch, "note": note}
-    dominant = max(out.values(), key=lambda r: prof[r["kernel"]][1]) if out else None
-    return dominant, out
+    # the headline is the amplitude contraction of the connected determinants
+    # (the bulk of the tensor work); the other families stay under `rooflines`
+    headline = next((out[k] for k in AMPLITUDE_FAMILIES if k in out), None)
+    if headline is None and out:
+        headline = max(out.values(), key=lambda r: prof[r["kernel"]][1])
+    return headline, out
 
 
 if __name__ == "__main__":
