@@ -536,44 +536,84 @@ def _large(args, dev):
     """Config-4 shape (26 orbitals, 9+9 electrons, transformer d128 h8 L4,
     33,507 connected determinants per sample): local energies per second of
     anqs_local_energy over a bounded sample (the 64 most frequent unique
-    samples of one 2000-sample pass), FP32 form, since the tensor-core
-    transformer covers d = 64 only.  An auxiliary line, not the headline
-    workload; it prints one JSON line."""
+    samples of one 2000-sample pass), BF16 tensor-core form (keys and values
+    of the parent reused) against the plain FP32 form on the same samples,
+    with the amplitude kernel's roofline and the BF16 form's local-energy
+    deviation from the FP32 form (which is checked against its FP64 definition
+    at this shape).  An auxiliary line, not the headline workload."""
+    import ctypes as C
     import paper_2310_04166_gb300 as A
+    from paper_2310_04166_gb300 import _lib
     from synthetic import workload
+    lib = _lib.load()
     w = workload("large")
     ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
-    model = A.Model.transformer(w["n"], w["d_model"], w["n_heads"], w["n_layers"],
-                                torch.tensor(w["params"], device=dev))
-    x, c = A.sample(model, ham, 2000, seed=1234)
+    params = torch.tensor(w["params"], device=dev)
+    models = {f: A.Model.transformer(w["n"], w["d_model"], w["n_heads"], w["n_layers"], params, form=f)
+              for f in ("bf16", "fp32")}
+    x, c = A.sample(models["fp32"], ham, 2000, seed=1234)
     keep = torch.argsort(c, descending=True, stable=True)[:64]
     x, c = x[keep].contiguous(), c[keep].contiguous()
-    ws = A._ws(A.local_energy_workspace_bytes(model, ham, x.numel()), dev)
-    out = (torch.empty(x.numel(), dtype=torch.float64, device=dev),
-           torch.empty(x.numel(), dtype=torch.float64, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
-    for _ in range(args.warmup):
-        A.local_energy(model, ham, x, c, workspace=ws, out=out)
-    torch.cuda.synchronize()
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(dev.index or 0) as clk:
-        e0.record(stream)
-        for _ in range(args.steps):
+    ws = A._ws(max(A.local_energy_workspace_bytes(m, ham, x.numel()) for m in models.values()), dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    res, outs = {}, {}
+    peaks, src = _peaks()
+    for form, model in models.items():
+        out = (torch.empty(x.numel(), dtype=torch.float64, device=dev),
+               torch.empty(x.numel(), dtype=torch.float64, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
+        steps = args.steps if form == "bf16" else max(1, min(args.steps, 2))
+        for _ in range(args.warmup if form == "bf16" else 1):
             A.local_energy(model, ham, x, c, workspace=ws, out=out)
-        e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+        lib.anqs_profile_enable(1)
+        A.local_energy(model, ham, x, c, workspace=ws, out=out)
+        torch.cuda.synchronize()
+        prof = {}
+        for pid in range(64):
+            nm, n_l, ms = C.c_char_p(), C.c_uint64(), C.c_double()
+            if lib.anqs_profile_read(pid, C.byref(nm), C.byref(n_l), C.byref(ms)) != 0:
+                break
+            if n_l.value:
+                prof[nm.value.decode()] = (n_l.value, ms.value)
+        lib.anqs_profile_enable(0)
+        stream = torch.cuda.current_stream()
+        times = []
+        with Clocks(dev.index or 0) as clk:
+            for i in range(steps):
+                flush.fill_(i & 0xFF)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                A.local_energy(model, ham, x, c, workspace=ws, out=out)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+        ms = sum(times) / len(times)
+        work = _tf_work(A, ham, w, x)
+        roof, _ = _rooflines(prof, work, 1, peaks, src, {})
+        res[form] = {"value": x.numel() / (ms / 1e3), "ms_per_step": ms, "steps": steps, "clocks": clk.summary(),
+                     "roofline": roof, "status": model.status()}
+        outs[form] = (out[0].clone(), out[2].clone())
+    d = (outs["bf16"][0] - outs["fp32"][0]).abs()
     K = ham.n_connected
-    print(json.dumps({"metric": METRIC, "value": x.numel() / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                      "scaling": "weak", "vs_baseline": None, "dtype": "f32 network / f64 E_loc", "data": "synthetic",
+    r = res["bf16"]
+    print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["steps"],
+                      "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "bf16 GEMM / f32 heads / f64 E_loc",
+                      "data": "synthetic",
                       "config": {"workload": f"large: n_orb={w['n']} N_a={w['n_alpha']} N_b={w['n_beta']}, "
                                              f"transformer d{w['d_model']} h{w['n_heads']} L{w['n_layers']}, "
                                              f"{x.numel()} unique samples x {K} connected determinants per step",
-                                 "form": "fp32", "timed": "anqs_local_energy only (connected set, amplitudes of "
-                                                          "every connected determinant, E_loc, statistics)",
-                                 "l2": f"working set above L2 ({x.numel() * K} connected determinants)"},
-                      "clocks": clk.summary()}), flush=True)
+                                 "timed": "anqs_local_energy only (connected set, amplitudes, E_loc, statistics)",
+                                 "l2": f"flushed between timed steps; working set above L2 ({x.numel() * K} "
+                                       "connected determinants)"},
+                      "roofline": r["roofline"], "clocks": r["clocks"],
+                      "forms": {"bf16": res["bf16"], "fp32": res["fp32"],
+                                "bf16_over_fp32": res["bf16"]["value"] / res["fp32"]["value"],
+                                "bf16_vs_fp32": {"max_abs_dEloc_ha": float(d.max()),
+                                                 "abs_dE_ha": abs(float(outs["bf16"][1][0] - outs["fp32"][1][0])),
+                                                 "note": "FP32 form = E_loc definition within 1e-6 relative "
+                                                         "(tests/test_gpu_tf.py)"}}}), flush=True)
 
 
 def _batch32(args, dev):

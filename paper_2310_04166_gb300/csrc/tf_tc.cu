@@ -35,6 +35,18 @@
 #include "tc_ptx.cuh"
 
 namespace anqs {
+
+// d_model 128 (tf_tc128.cu)
+bool tf128_supported(const anqs_model* M);
+size_t tf128_packed_bytes(const anqs_model* M);
+int tf128_pack(anqs_model* M, cudaStream_t s);
+int tf128_status_offset(const anqs_model* M);
+int launch_tf128_full(const anqs_model* M, const HamView& hv, const uint64_t* x, Count n_seq, int P, int last_only,
+                      float* raw, __nv_bfloat16* kv_out, int prof, cudaStream_t s);
+int launch_tf128_suffix(const anqs_model* M, const HamView& hv, const uint64_t* xp, const uint32_t* perm,
+                        const uint32_t* offsets, uint32_t K, const __nv_bfloat16* kv_in, float2* T, uint64_t m_max,
+                        int prof, cudaStream_t s);
+
 namespace {
 
 constexpr int D = 64;
@@ -661,17 +673,18 @@ size_t plan(const anqs_model* M, const anqs_ham* H, uint64_t n_x, Arena& A, TfEl
   w.hist = A.take<uint32_t>(ANQS_MAX_ORB);
   w.cursor = A.take<uint32_t>(ANQS_MAX_ORB);
   w.offsets = A.take<uint32_t>(ANQS_MAX_ORB + 1);
-  w.kv = A.take<__nv_bfloat16>(n_x * uint64_t(M->d.n_layers) * n * 2 * D);
+  w.kv = A.take<__nv_bfloat16>(n_x * uint64_t(M->d.n_layers) * n * 2 * uint64_t(M->d.d_model));
   return A.off;
 }
 
 }  // namespace
 
 int tf_tc_pack_alloc(anqs_model* M) {
-  if (M->d.d_model != D) return set_error(ANQS_ERR_UNSUPPORTED, "BF16 transformer form supports d_model 64");
-  if (D / M->d.n_heads != 16 && D / M->d.n_heads != 32)
+  if (M->d.d_model != D && M->d.d_model != 128)
+    return set_error(ANQS_ERR_UNSUPPORTED, "BF16 transformer form supports d_model 64 or 128");
+  if (M->d.d_model / M->d.n_heads != 16 && M->d.d_model / M->d.n_heads != 32)
     return set_error(ANQS_ERR_UNSUPPORTED, "BF16 transformer form supports head width 16 or 32");
-  M->packed_bytes = size_t(M->d.n_layers) * LAYER_BYTES + 256;
+  M->packed_bytes = M->d.d_model == 128 ? tf128_packed_bytes(M) : size_t(M->d.n_layers) * LAYER_BYTES + 256;
   ANQS_CUDA(cudaMalloc(&M->packed, M->packed_bytes));
   ANQS_CUDA(cudaMemset(M->packed, 0, M->packed_bytes));
   M->tc_raw_rows = 32768;
@@ -680,6 +693,7 @@ int tf_tc_pack_alloc(anqs_model* M) {
 }
 
 int tf_tc_pack(anqs_model* M, cudaStream_t s) {
+  if (M->d.d_model == 128) return tf128_pack(M, s);
   ANQS_CUDA_LAUNCH("tf_pack_kernel", launch_k(tf_pack_kernel, dim3(152), dim3(256), 0, s, M->params, M->d.n_orb,
                                               M->d.n_layers, static_cast<unsigned char*>(M->packed)));
   return ANQS_OK;
@@ -687,8 +701,8 @@ int tf_tc_pack(anqs_model* M, cudaStream_t s) {
 
 int tf_tc_status(const anqs_model* M, int* status) {
   int v = 0;
-  ANQS_CUDA(cudaMemcpy(&v, static_cast<const unsigned char*>(M->packed) + size_t(M->d.n_layers) * LAYER_BYTES,
-                       sizeof(int), cudaMemcpyDeviceToHost));
+  const size_t off = M->d.d_model == 128 ? size_t(tf128_status_offset(M)) : size_t(M->d.n_layers) * LAYER_BYTES;
+  ANQS_CUDA(cudaMemcpy(&v, static_cast<const unsigned char*>(M->packed) + off, sizeof(int), cudaMemcpyDeviceToHost));
   *status = v;
   return ANQS_OK;
 }
@@ -698,8 +712,12 @@ int launch_tf_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t* 
   const int n = M->d.n_orb;
   for (uint64_t off = 0; off < n_x; off += M->tc_raw_rows) {
     const uint64_t k = std::min<uint64_t>(M->tc_raw_rows, n_x - off);
-    Args a = full_args(x + off, host_count(k), n, 0, M->tc_raw, nullptr, hv);
-    ANQS_TRY(launch(M, a, (k + MT / n - 1) / (MT / n), PROF_TF_TC_PARENT, s));
+    if (M->d.d_model == 128) {
+      ANQS_TRY(launch_tf128_full(M, hv, x + off, host_count(k), n, 0, M->tc_raw, nullptr, PROF_TF_TC_PARENT, s));
+    } else {
+      Args a = full_args(x + off, host_count(k), n, 0, M->tc_raw, nullptr, hv);
+      ANQS_TRY(launch(M, a, (k + MT / n - 1) / (MT / n), PROF_TF_TC_PARENT, s));
+    }
     ProfScope ps(PROF_TC_FINALIZE, s);
     ANQS_TRY(launch_tc_finalize(hv, x + off, host_count(k), M->tc_raw, la + off, ph + off, nullptr, s));
   }
@@ -709,6 +727,8 @@ int launch_tf_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t* 
 int launch_tf_tc_slot_logits(const anqs_model* M, int p, const uint64_t* pre, const uint64_t* n_dev,
                              uint64_t max_rows, float* out8, cudaStream_t s) {
   HamView hv{};
+  if (M->d.d_model == 128)
+    return launch_tf128_full(M, hv, pre, Count{max_rows, n_dev, 1}, p + 1, 1, out8, nullptr, PROF_TF_TC_SLOT, s);
   Args a = full_args(pre, Count{max_rows, n_dev, 1}, p + 1, 1, out8, nullptr, hv);
   const uint64_t S = MT / (p + 1);
   return launch(M, a, (max_rows + S - 1) / S, PROF_TF_TC_SLOT, s);
@@ -732,8 +752,12 @@ int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Co
   if (mc.n > 0xffffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "more than 2^32 connected determinants per call");
   ANQS_TRY(launch_connected(H->v, x, n_x, w.xp, w.hv, w.js, w.hd, s));
   {
-    Args a = full_args(x, n_x, n, 0, w.raw, w.kv, H->v);
-    ANQS_TRY(launch(M, a, (n_x.n + MT / n - 1) / (MT / n), PROF_TF_TC_PARENT, s));
+    if (M->d.d_model == 128) {
+      ANQS_TRY(launch_tf128_full(M, H->v, x, n_x, n, 0, w.raw, w.kv, PROF_TF_TC_PARENT, s));
+    } else {
+      Args a = full_args(x, n_x, n, 0, w.raw, w.kv, H->v);
+      ANQS_TRY(launch(M, a, (n_x.n + MT / n - 1) / (MT / n), PROF_TF_TC_PARENT, s));
+    }
     ProfScope ps(PROF_TC_FINALIZE, s);
     ANQS_TRY(launch_tc_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
   }
@@ -741,7 +765,10 @@ int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Co
     ProfScope ps(PROF_TC_SORT, s);
     ANQS_TRY(launch_js_sort(w.js, mc, n, w.hist, w.cursor, w.offsets, w.perm, s));
   }
-  {
+  if (M->d.d_model == 128) {
+    ANQS_TRY(launch_tf128_suffix(M, H->v, w.xp, w.perm, w.offsets, uint32_t(K), w.kv, w.T, mc.n, PROF_TF_TC_SUFFIX,
+                                 s));
+  } else {
     Args a{};
     a.mode = MODE_SUFFIX;
     a.hv = H->v;
