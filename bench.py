@@ -700,6 +700,8 @@ def main():
     ap.add_argument("--no-extra", action="store_true", help="h2o only: leave out the n2 sub-workload")
     ap.add_argument("--binomial", action="store_true", help="binomial statistics sampling (chained binomials per node)")
     ap.add_argument("--n-samples", type=float, default=0, help="N_s of the sampling pass (default: the workload's)")
+    ap.add_argument("--kernel-samples", type=int, default=0,
+                    help="--kernel-case: keep only the K most frequent samples and leave out the gradient call")
     ap.add_argument("--kernel-case", action="store_true",
                     help="one FP32-form sampling pass, then one local-energy and one gradient call in the "
                          "chosen form (the launch sequence to capture with ncu), then exit")
@@ -724,20 +726,24 @@ def main():
     if args.workload == "batch32":
         _batch32(args, dev)
         return
-    if args.workload == "large":
-        _large(args, dev)
-        return
     ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
     params = torch.tensor(w["params"], device=dev)
     if w["kind"] == "nade":  # the NADE has the FP32 form only
         args.form, args.one_form = "fp32", True
     form = args.form
+    if args.workload == "large" and not args.kernel_case:
+        _large(args, dev)
+        return
     if args.kernel_case:
         model = _make_model(A, w, params, form)
         m32 = _make_model(A, w, params, "fp32")
-        xk, nk = A.sample(m32, ham, w["n_samples"], seed=99)
+        xk, nk = A.sample(m32, ham, w.get("n_samples", 2000), seed=99)
+        if args.kernel_samples:  # the most frequent few (a small case of the same kernels)
+            keep = torch.argsort(nk, descending=True, stable=True)[:args.kernel_samples]
+            xk, nk = xk[keep].contiguous(), nk[keep].contiguous()
         ek = A.local_energy(model, ham, xk, nk)
-        A.grad(model, ham, xk, nk, ek[0], ek[1], ek[2])
+        if not args.kernel_samples:
+            A.grad(model, ham, xk, nk, ek[0], ek[1], ek[2])
         torch.cuda.synchronize()
         print(json.dumps({"kernel_case": args.workload, "form": form, "n_unique": xk.numel(),
                           "E": float(ek[2][0])}))

@@ -389,17 +389,13 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
 #pragma unroll
         for (int e = 0; e < DH; ++e) acc[e] = 0.f;
         const int upto = valid ? pos : -1;
-#pragma unroll 1
-        for (int u = 0; u <= upto; ++u) {
-          const uint4* kp;
-          if (u < tl.t0) kp = reinterpret_cast<const uint4*>(pkv + size_t(u) * (2 * D));
-          else kp = reinterpret_cast<const uint4*>(sKV + (row0 + u - tl.t0) * KV_STRIDE);
-          // score as two interleaved partial sums (packed f32x2 FMAs)
+        // one key: score, online-softmax update of (m, lsum, acc)
+        auto step = [&](const uint4 (&kw)[DH / 8], const uint4 (&vw)[DH / 8]) {
           float s0 = 0.f, s1 = 0.f;
 #pragma unroll
           for (int e8 = 0; e8 < DH; e8 += 8) {
             float kf[8];
-            bf16x8_to_f32(kp[(hd * DH + e8) / 8], kf);
+            bf16x8_to_f32(kw[e8 / 8], kf);
 #pragma unroll
             for (int e = 0; e < 8; e += 2) tc::fma_f32x2(q[e8 + e], q[e8 + e + 1], kf[e], kf[e + 1], s0, s1, s0, s1);
           }
@@ -410,15 +406,52 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
 #pragma unroll
           for (int e8 = 0; e8 < DH; e8 += 8) {
             float vf[8];
-            bf16x8_to_f32(kp[(D + hd * DH + e8) / 8], vf);
+            bf16x8_to_f32(vw[e8 / 8], vf);
 #pragma unroll
-            for (int e = 0; e < 8; e += 2) {  // acc = acc corr + p v, two elements per instruction
+            for (int e = 0; e < 8; e += 2) {
               float p0, p1;
               tc::fma_f32x2(p, p, vf[e], vf[e + 1], 0.f, 0.f, p0, p1);
               tc::fma_f32x2(acc[e8 + e], acc[e8 + e + 1], corr, corr, p0, p1, acc[e8 + e], acc[e8 + e + 1]);
             }
           }
           m = mn;
+        };
+        // keys of positions < t0 from the parent cache (global memory; the
+        // next key's words are loaded before this key's arithmetic), then
+        // the tile's own keys from shared memory
+        const int n_par = min(upto + 1, tl.t0);
+        if (n_par > 0) {
+          const uint4* gp = reinterpret_cast<const uint4*>(pkv);
+          uint4 kw[DH / 8], vw[DH / 8];
+#pragma unroll
+          for (int e = 0; e < DH / 8; ++e) {
+            kw[e] = __ldg(gp + (hd * DH) / 8 + e);
+            vw[e] = __ldg(gp + (D + hd * DH) / 8 + e);
+          }
+#pragma unroll 1
+          for (int u = 0; u < n_par; ++u) {
+            uint4 kn[DH / 8], vn[DH / 8];
+            const uint4* np = gp + size_t(u + 1 < n_par ? u + 1 : u) * (2 * D / 8);
+#pragma unroll
+            for (int e = 0; e < DH / 8; ++e) {
+              kn[e] = __ldg(np + (hd * DH) / 8 + e);
+              vn[e] = __ldg(np + (D + hd * DH) / 8 + e);
+            }
+            step(kw, vw);
+#pragma unroll
+            for (int e = 0; e < DH / 8; ++e) kw[e] = kn[e], vw[e] = vn[e];
+          }
+        }
+#pragma unroll 1
+        for (int u = tl.t0; u <= upto; ++u) {
+          const uint4* sp = reinterpret_cast<const uint4*>(sKV + (row0 + u - tl.t0) * KV_STRIDE);
+          uint4 kw[DH / 8], vw[DH / 8];
+#pragma unroll
+          for (int e = 0; e < DH / 8; ++e) {
+            kw[e] = sp[(hd * DH) / 8 + e];
+            vw[e] = sp[(D + hd * DH) / 8 + e];
+          }
+          step(kw, vw);
         }
         const float inv = valid ? 1.0f / lsum : 0.f;
 #pragma unroll

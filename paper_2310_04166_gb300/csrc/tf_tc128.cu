@@ -74,7 +74,9 @@ constexpr uint32_t OFF_KV = OFF_A + A_BYTES;
 constexpr uint32_t OFF_HEAD = OFF_KV + KV_BYTES;              // head [8][D] f32 + bias [8]
 constexpr uint32_t OFF_RED = OFF_HEAD + (8 * D + 8) * 4;      // exchange [2 slots][2 halves][128] f32
 constexpr uint32_t OFF_HX = OFF_RED + 2 * 2 * MT * 4;         // head partials of half 1 [128][8] f32
-constexpr uint32_t SMEM_BYTES = OFF_HX + MT * 8 * 4;
+constexpr uint32_t OFF_LP = OFF_HX + MT * 8 * 4;              // the layer's LayerNorm parameters and biases
+constexpr uint32_t LP_FLOATS = 14 * D;                         // ln1 g,b | bq bk bv bo | ln2 g,b | b1 (4D) | b2
+constexpr uint32_t SMEM_BYTES = OFF_LP + LP_FLOATS * 4;
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int MODE_FULL = 0, MODE_SUFFIX = 1;
 // chunk indices within a layer
@@ -110,19 +112,46 @@ struct LayerP {
 
 __host__ __device__ inline size_t layer_floats() { return 12 * size_t(D) * D + 13 * D; }
 
-__device__ __forceinline__ LayerP layer_p(const float* params, int n, int l) {
+// The small parameters of block l (LayerNorms and biases, 14 D floats) are
+// copied to shared memory at the start of the block; lp points there.
+__device__ __forceinline__ const float* layer_small(const float* params, int n, int l, int part) {
+  // part: 0 ln1 g, 1 ln1 b, 2 bq, 3 bk, 4 bv, 5 bo, 6 ln2 g, 7 ln2 b, 8 b1 (4 D), 9 b2
   const float* b = params + 5 * D + size_t(n) * D + size_t(l) * layer_floats();
+  switch (part) {
+    case 0: return b;
+    case 1: return b + D;
+    case 2: return b + 2 * D + D * D;
+    case 3: return b + 2 * D + 2 * D * D + D;
+    case 4: return b + 2 * D + 3 * D * D + 2 * D;
+    case 5: return b + 2 * D + 4 * D * D + 3 * D;
+    case 6: return b + 2 * D + 4 * D * D + 4 * D;
+    case 7: return b + 2 * D + 4 * D * D + 5 * D;
+    case 8: return b + 2 * D + 4 * D * D + 6 * D + 4 * D * D;
+    default: return b + 2 * D + 4 * D * D + 6 * D + 4 * D * D + 4 * D + 4 * D * D;
+  }
+}
+
+__device__ __forceinline__ void stage_layer(const float* params, int n, int l, float* s_lp) {
+  for (int i = threadIdx.x; i < int(LP_FLOATS); i += blockDim.x) {
+    const int r = i / D;
+    const int part = r < 8 ? r : (r < 12 ? 8 : 9);
+    const int off = r < 8 ? i % D : (r < 12 ? i - 8 * D : i - 12 * D);
+    s_lp[i] = layer_small(params, n, l, part)[off];
+  }
+}
+
+__device__ __forceinline__ LayerP staged_p(const float* s_lp) {
   LayerP P;
-  P.ln1_g = b;
-  P.ln1_b = b + D;
-  P.bq = b + 2 * D + D * D;
-  P.bk = P.bq + D + D * D;
-  P.bv = P.bk + D + D * D;
-  P.bo = P.bv + D + D * D;
-  P.ln2_g = P.bo + D;
-  P.ln2_b = P.ln2_g + D;
-  P.b1 = P.ln2_b + D + 4 * D * D;
-  P.b2 = P.b1 + 4 * D + 4 * D * D;
+  P.ln1_g = s_lp;
+  P.ln1_b = s_lp + D;
+  P.bq = s_lp + 2 * D;
+  P.bk = s_lp + 3 * D;
+  P.bv = s_lp + 4 * D;
+  P.bo = s_lp + 5 * D;
+  P.ln2_g = s_lp + 6 * D;
+  P.ln2_b = s_lp + 7 * D;
+  P.b1 = s_lp + 8 * D;
+  P.b2 = s_lp + 12 * D;
   return P;
 }
 
@@ -216,10 +245,10 @@ __device__ __forceinline__ void ln_store(const float (&hh)[HD], const float* __r
   const int cb = h * HD;
 #pragma unroll
   for (int c0 = 0; c0 < HD; c0 += 8) {
-    const float4 g0 = __ldg(reinterpret_cast<const float4*>(g + cb + c0));
-    const float4 g1 = __ldg(reinterpret_cast<const float4*>(g + cb + c0 + 4));
-    const float4 b0 = __ldg(reinterpret_cast<const float4*>(b + cb + c0));
-    const float4 b1 = __ldg(reinterpret_cast<const float4*>(b + cb + c0 + 4));
+    const float4 g0 = *reinterpret_cast<const float4*>(g + cb + c0);
+    const float4 g1 = *reinterpret_cast<const float4*>(g + cb + c0 + 4);
+    const float4 b0 = *reinterpret_cast<const float4*>(b + cb + c0);
+    const float4 b1 = *reinterpret_cast<const float4*>(b + cb + c0 + 4);
     const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
     const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
     uint32_t w[4];
@@ -375,6 +404,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
     const uint32_t a_addr = tc::smem_u32(sA);
     Xch xc{reinterpret_cast<float*>(smem + OFF_RED), 0};
     float* s_hx = reinterpret_cast<float*>(smem + OFF_HX);
+    float* s_lp = reinterpret_cast<float*>(smem + OFF_LP);
     const bool issuer = threadIdx.x == 0;
     const uint64_t my_tiles = total > blockIdx.x ? (total - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     Ring ring{w_addr, bar_full, bar_empty, a.img, L, 0, 0, my_tiles * uint64_t(L) * NCH};
@@ -433,7 +463,10 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
         }
       }
       for (int l = 0; ok && l < L; ++l) {
-        const LayerP lp = layer_p(a.params, n, l);
+        csync();  // the previous block's readers of the staged parameters are done
+        stage_layer(a.params, n, l, s_lp);
+        csync();
+        const LayerP lp = staged_p(s_lp);
         ln_store(hh, lp.ln1_g, lp.ln1_b, sA, h, t, xc);
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -460,7 +493,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
             const float* bias = (kv == 0 ? lp.bk : lp.bv) + cb + c0;
             uint32_t w[16];
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) w[i / 2] = tc::pack_bf16x2(v[i] + __ldg(bias + i), v[i + 1] + __ldg(bias + i + 1));
+            for (int i = 0; i < 32; i += 2) w[i / 2] = tc::pack_bf16x2(v[i] + bias[i], v[i + 1] + bias[i + 1]);
             const int off = kv * D + cb + c0;  // element offset within the k|v row
             uint4* dst = reinterpret_cast<uint4*>(sKV + t * KV_STRIDE + off * 2);
 #pragma unroll
@@ -485,21 +518,18 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
             tc::tmem_ld32(tmem + lane_base + uint32_t(hd * DH), q);
           }
 #pragma unroll
-          for (int e = 0; e < DH; ++e) q[e] = (q[e] + __ldg(lp.bq + hd * DH + e)) * scale;
+          for (int e = 0; e < DH; ++e) q[e] = (q[e] + lp.bq[hd * DH + e]) * scale;
           float m = -INFINITY, lsum = 0.f, acc[DH];
 #pragma unroll
           for (int e = 0; e < DH; ++e) acc[e] = 0.f;
           const int upto = valid ? pos : -1;
-#pragma unroll 1
-          for (int u = 0; u <= upto; ++u) {
-            const uint4* kp;
-            if (u < tl.t0) kp = reinterpret_cast<const uint4*>(pkv + size_t(u) * (2 * D));
-            else kp = reinterpret_cast<const uint4*>(sKV + (row0 + u - tl.t0) * KV_STRIDE);
+          // one key: score, online-softmax update of (m, lsum, acc)
+          auto step = [&](const uint4 (&kw)[DH / 8], const uint4 (&vw)[DH / 8]) {
             float s0 = 0.f, s1 = 0.f;
 #pragma unroll
             for (int e8 = 0; e8 < DH; e8 += 8) {
               float kf[8];
-              bf16x8_to_f32(kp[(hd * DH + e8) / 8], kf);
+              bf16x8_to_f32(kw[e8 / 8], kf);
 #pragma unroll
               for (int e = 0; e < 8; e += 2) tc::fma_f32x2(q[e8 + e], q[e8 + e + 1], kf[e], kf[e + 1], s0, s1, s0, s1);
             }
@@ -510,7 +540,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
 #pragma unroll
             for (int e8 = 0; e8 < DH; e8 += 8) {
               float vf[8];
-              bf16x8_to_f32(kp[(D + hd * DH + e8) / 8], vf);
+              bf16x8_to_f32(vw[e8 / 8], vf);
 #pragma unroll
               for (int e = 0; e < 8; e += 2) {
                 float p0, p1;
@@ -519,6 +549,43 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
               }
             }
             m = mn;
+          };
+          // keys of positions < t0 from the parent cache (global memory; the
+          // next key's words are loaded before this key's arithmetic), then
+          // the tile's own keys from shared memory
+          const int n_par = min(upto + 1, tl.t0);
+          if (n_par > 0) {
+            const uint4* gp = reinterpret_cast<const uint4*>(pkv);
+            uint4 kw[DH / 8], vw[DH / 8];
+#pragma unroll
+            for (int e = 0; e < DH / 8; ++e) {
+              kw[e] = __ldg(gp + (hd * DH) / 8 + e);
+              vw[e] = __ldg(gp + (D + hd * DH) / 8 + e);
+            }
+#pragma unroll 1
+            for (int u = 0; u < n_par; ++u) {
+              uint4 kn[DH / 8], vn[DH / 8];
+              const uint4* np = gp + size_t(u + 1 < n_par ? u + 1 : u) * (2 * D / 8);
+#pragma unroll
+              for (int e = 0; e < DH / 8; ++e) {
+                kn[e] = __ldg(np + (hd * DH) / 8 + e);
+                vn[e] = __ldg(np + (D + hd * DH) / 8 + e);
+              }
+              step(kw, vw);
+#pragma unroll
+              for (int e = 0; e < DH / 8; ++e) kw[e] = kn[e], vw[e] = vn[e];
+            }
+          }
+#pragma unroll 1
+          for (int u = tl.t0; u <= upto; ++u) {
+            const uint4* sp = reinterpret_cast<const uint4*>(sKV + (row0 + u - tl.t0) * KV_STRIDE);
+            uint4 kw[DH / 8], vw[DH / 8];
+#pragma unroll
+            for (int e = 0; e < DH / 8; ++e) {
+              kw[e] = sp[(hd * DH) / 8 + e];
+              vw[e] = sp[(D + hd * DH) / 8 + e];
+            }
+            step(kw, vw);
           }
           const float inv = valid ? 1.0f / lsum : 0.f;
 #pragma unroll
@@ -546,7 +613,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
           float v[32];
           tc::tmem_ld32(tmem + lane_base + uint32_t(cb + c0), v);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) hh[c0 + i] += v[i] + __ldg(lp.bo + cb + c0 + i);
+          for (int i = 0; i < 32; ++i) hh[c0 + i] += v[i] + lp.bo[cb + c0 + i];
         }
         ln_store(hh, lp.ln2_g, lp.ln2_b, sA, h, t, xc);
         tc::fence_async_smem();
@@ -584,7 +651,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 const int i = q8 + 2 * e;
-                w[e] = tc::pack_bf16x2(fmaxf(v[i] + __ldg(b1 + i), 0.f), fmaxf(v[i + 1] + __ldg(b1 + i + 1), 0.f));
+                w[e] = tc::pack_bf16x2(fmaxf(v[i] + b1[i], 0.f), fmaxf(v[i + 1] + b1[i + 1], 0.f));
               }
               *reinterpret_cast<uint4*>(sH + tc::canon_off(t, cb + c0 + q8, D)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
@@ -613,7 +680,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
           float v[32];
           tc::tmem_ld32(tmem + lane_base + uint32_t(384 + cb + c0), v);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) hh[c0 + i] += v[i] + __ldg(lp.b2 + cb + c0 + i);
+          for (int i = 0; i < 32; ++i) hh[c0 + i] += v[i] + lp.b2[cb + c0 + i];
         }
       }
       if (!ok) break;
