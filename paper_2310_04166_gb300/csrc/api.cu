@@ -222,6 +222,67 @@ static int build_sector(anqs_ham* H) {
   return ANQS_OK;
 }
 
+// The sampler's prefix table: all physical prefixes of levels 0..n-1 by a
+// breadth-first walk of the slot masks (children in ascending outcome, as the
+// sampler emits them), when there are at most kPrefixTable of them and no
+// level holds more than kPrefixLevel.  Uploads it to the device.
+constexpr size_t kPrefixTable = 16384, kPrefixLevel = 2048;
+
+static int build_prefix_table(anqs_ham* H) {
+  const HamView& v = H->v;
+  const int n = v.n;
+  cudaFree(H->d_pt_x);
+  cudaFree(H->d_pt_child);
+  H->d_pt_x = nullptr;
+  H->d_pt_child = nullptr;
+  H->pt_x.clear();
+  H->pt_off.clear();
+  H->pt_child.clear();
+  uint64_t total = 0;
+  for (int p = 0; p < n; ++p) {
+    if (H->phys_prefix[p] > kPrefixLevel) return ANQS_OK;
+    total += H->phys_prefix[p];
+  }
+  if (total > kPrefixTable) return ANQS_OK;
+  std::vector<uint64_t> x{0ull};
+  std::vector<uint32_t> off{0u, 1u};
+  std::vector<int32_t> child;
+  for (int p = 0; p < n; ++p) {
+    const uint64_t below = (1ull << (2 * p)) - 1ull;
+    for (uint32_t i = off[p]; i < off[p + 1]; ++i) {
+      const uint64_t xi = x[i];
+      const int a = __builtin_popcountll(xi & below & 0x5555555555555555ull);
+      const int b = __builtin_popcountll(xi & below & 0xAAAAAAAAAAAAAAAAull);
+      int z = 0;
+      for (int j = 0; j < v.nz; ++j) z |= (__builtin_popcountll(xi & below & v.zmask[j]) & 1) << j;
+      const unsigned m = (a <= v.na && b <= v.nb) ? H->mask_host[mask_index(v, p, a, b, z)] : 0u;
+      for (int u = 0; u < 4; ++u) {
+        if (((m >> u) & 1u) && p + 1 < n) {
+          child.push_back(int32_t(x.size()));
+          x.push_back(xi | (uint64_t(u) << (2 * p)));
+        } else {
+          child.push_back(-1);
+        }
+      }
+    }
+    if (p + 1 < n) off.push_back(uint32_t(x.size()));
+  }
+  if (off.size() != size_t(n) + 1 || x.size() != total) return ANQS_OK;  // counts disagree: no table
+  if (cudaMalloc(&H->d_pt_x, x.size() * sizeof(uint64_t)) != cudaSuccess ||
+      cudaMalloc(&H->d_pt_child, child.size() * sizeof(int32_t)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(H->d_pt_x);
+    H->d_pt_x = nullptr;
+    return set_error(ANQS_ERR_CUDA, "cudaMalloc failed for the prefix table");
+  }
+  ANQS_CUDA(cudaMemcpy(H->d_pt_x, x.data(), x.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+  ANQS_CUDA(cudaMemcpy(H->d_pt_child, child.data(), child.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+  H->pt_x.swap(x);
+  H->pt_off.swap(off);
+  H->pt_child.swap(child);
+  return ANQS_OK;
+}
+
 extern "C" {
 
 const char* anqs_version(void) { return "anqs 0.1 (sm_103a)"; }
@@ -285,6 +346,10 @@ int anqs_hamiltonian_create(anqs_ham** out, int n, int na, int nb, const double*
   v.g = H->d_g;
   v.mask = H->d_mask;
   v.mu_lv = n;
+  if (build_prefix_table(H) != ANQS_OK) {
+    anqs_hamiltonian_destroy(H);
+    return ANQS_ERR_CUDA;
+  }
   *out = H;
   return ANQS_OK;
 }
@@ -318,7 +383,7 @@ int anqs_hamiltonian_set_z2(anqs_ham* H, int nz, const uint64_t* qubit_masks) {
   cudaFree(H->d_mask);
   H->d_mask = d;
   H->v.mask = d;
-  return ANQS_OK;
+  return build_prefix_table(H);
 }
 
 int anqs_hamiltonian_set_pruning(anqs_ham* H, int du_levels) {
@@ -334,6 +399,8 @@ int anqs_hamiltonian_destroy(anqs_ham* H) {
   cudaFree(H->d_h);
   cudaFree(H->d_g);
   cudaFree(H->d_mask);
+  cudaFree(H->d_pt_x);
+  cudaFree(H->d_pt_child);
   delete H;
   return ANQS_OK;
 }

@@ -224,6 +224,16 @@ struct anqs_ham {
   uint64_t sector_dim;
   std::vector<uint8_t> mask_host;
   std::vector<uint64_t> phys_prefix;  // [p] physical prefixes holding slots < p (saturated)
+  // Every physical prefix of the levels 0..n-1 when there are few (the
+  // sampler's prefix table): prefixes of level p at [pt_off[p], pt_off[p+1])
+  // in the order the sampler emits them, and per (prefix, outcome) the index
+  // of the child prefix in the next level (-1: unphysical, or the last level).
+  // Empty when the sector has too many prefixes.
+  std::vector<uint64_t> pt_x;
+  std::vector<uint32_t> pt_off;
+  std::vector<int32_t> pt_child;
+  uint64_t* d_pt_x;
+  int32_t* d_pt_child;
   double* d_h;
   double* d_g;
   uint8_t* d_mask;
@@ -319,6 +329,8 @@ int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t*
                          float* ph, cudaStream_t s);
 int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, const uint64_t* pre,
                               const uint64_t* n_dev, uint64_t max_rows, float* out8, cudaStream_t s);
+// slot-p outputs of every prefix of the prefix table (level p's rows use slot p), one launch
+int launch_mlp_tc_prefix_logits(const anqs_model* M, const anqs_ham* H, float* out8, cudaStream_t s);
 int mlp_tc_status(const anqs_model* M, int* status);
 // pieces of the tensor-core local-energy pipeline shared by the MLP and transformer forms
 constexpr int TC_CACHE_F = 10;  // floats per (parent, slot): prefix la, ph, 4 masked terms, 4 phases

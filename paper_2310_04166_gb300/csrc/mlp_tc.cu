@@ -149,6 +149,8 @@ struct TileArgs {
   int p_lo, p_hi;              // SLOTS: slots [p_lo, p_hi)
   float* raw;                  // SLOTS output [row][p_hi - p_lo][8]
   int tpi;                     // SLOTS: 128-row tiles per work item (1..NWG; warpgroups >= tpi idle)
+  int levels;                  // LEVELS: rows [lv_off[p], lv_off[p+1]) take slot p (p < levels), raw [row][8]
+  uint32_t lv_off[ANQS_MAX_ORB + 1];
 };
 
 constexpr int NWG = kNwg;     // warpgroups per CTA, one 128-row tile each in flight
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
   // prologue: the packed images were written before the previous kernel.
   int loaded = -1;     // slot whose image is in shared memory (or on its way)
   bool pending = false;
-  if (np == 1) {
+  if (np == 1 && !ta.levels) {
     if (threadIdx.x == 0) load_slot(tv, ta.p_lo, tc::smem_u32(s_img), bar_w, W, tv.L);
     loaded = ta.p_lo;
     pending = true;
@@ -356,17 +358,43 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
   const int tpi = ta.tpi;
   const uint64_t n_groups = (n_rows + uint64_t(tpi) * MT - 1) / (uint64_t(tpi) * MT);
   const uint64_t n_items = n_groups * uint64_t(np);
-  for (uint64_t it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int p = ta.p_lo + int(it / n_groups);
-    const uint64_t grp = it % n_groups;
+  // LEVELS: items are (level p, group of its rows), levels in order
+  uint64_t n_items_lv = 0;
+  if (ta.levels)
+    for (int q = 0; q < ta.levels; ++q)
+      n_items_lv += (uint64_t(ta.lv_off[q + 1] - ta.lv_off[q]) + uint64_t(tpi) * MT - 1) / (uint64_t(tpi) * MT);
+  for (uint64_t it = blockIdx.x; it < (ta.levels ? n_items_lv : n_items); it += gridDim.x) {
+    int p = ta.p_lo + int(it / n_groups);
+    uint64_t grp = it % n_groups, row_lo = 0, row_hi = n_rows;
+    if (ta.levels) {
+      uint64_t acc = 0;
+      for (int q = 0; q < ta.levels; ++q) {
+        const uint64_t g = (uint64_t(ta.lv_off[q + 1] - ta.lv_off[q]) + uint64_t(tpi) * MT - 1) / (uint64_t(tpi) * MT);
+        if (it < acc + g) {
+          p = q;
+          grp = it - acc;
+          row_lo = ta.lv_off[q];
+          row_hi = ta.lv_off[q + 1];
+          break;
+        }
+        acc += g;
+      }
+    }
     const SlotLayout S = slot_layout(p, W, tv.L, tv.lo);
     if (p != loaded) {
+      // a copy still in flight into the buffer lands before the next one is issued
+      if (pending) {
+        if (!__syncthreads_and(wait_bar(bar_w, ph_w))) s_abort = 1;
+        ph_w ^= 1;
+        pending = false;
+        if (s_abort) break;
+      }
       if (threadIdx.x == 0) load_slot(tv, p, tc::smem_u32(s_img), bar_w, W, tv.L);
       loaded = p;
       pending = true;
     }
-    const uint64_t r = (grp * tpi + wg) * MT + t;
-    const bool valid = wg < tpi && r < n_rows;
+    const uint64_t r = row_lo + (grp * tpi + wg) * MT + t;
+    const bool valid = wg < tpi && r < row_hi;
     const uint64_t x = valid ? ta.x[r] : 0ull;
     bool ok = true;
     if (pending) {
@@ -375,11 +403,11 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
       pending = false;
     }
     float out[8];
-    if (ok && wg < tpi && (grp * tpi + wg) * MT < n_rows)
+    if (ok && wg < tpi && row_lo + (grp * tpi + wg) * MT < row_hi)
       ok = tile_slot<W>(c, ph_m, p, x, S, tc::smem_u32(s_img), s_img, out);
     if (!ok) s_abort = 1;
     if (ok && valid) {
-      float4* dst = reinterpret_cast<float4*>(ta.raw + (r * np + (p - ta.p_lo)) * 8);
+      float4* dst = reinterpret_cast<float4*>(ta.raw + (ta.levels ? r : r * np + (p - ta.p_lo)) * 8);
       dst[0] = make_float4(out[0], out[1], out[2], out[3]);
       dst[1] = make_float4(out[4], out[5], out[6], out[7]);
     }
@@ -727,10 +755,20 @@ int launch_slots_w(const TcView& tv, const TileArgs& ta, cudaStream_t s) {
   const size_t sm = smem_bytes(tv, 1);
   // one 128-row tile per CTA (its warpgroup alone on the SM) while the
   // tiles of all slots fit in one wave, else NWG tiles per CTA
-  const uint64_t np = uint64_t(ta.p_hi - ta.p_lo), tiles = (max_rows + MT - 1) / MT;
+  const uint64_t np = uint64_t(ta.p_hi - ta.p_lo);
+  uint64_t tiles = (max_rows + MT - 1) / MT * np;
+  if (ta.levels) {
+    tiles = 0;
+    for (int q = 0; q < ta.levels; ++q) tiles += (uint64_t(ta.lv_off[q + 1] - ta.lv_off[q]) + MT - 1) / MT;
+  }
   TileArgs a = ta;
-  a.tpi = tiles * np <= uint64_t(num_sms()) ? 1 : NWG;
-  const uint64_t items = (max_rows + uint64_t(a.tpi) * MT - 1) / (uint64_t(a.tpi) * MT) * np;
+  a.tpi = tiles <= uint64_t(num_sms()) ? 1 : NWG;
+  uint64_t items = (max_rows + uint64_t(a.tpi) * MT - 1) / (uint64_t(a.tpi) * MT) * np;
+  if (ta.levels) {
+    items = 0;
+    for (int q = 0; q < ta.levels; ++q)
+      items += (uint64_t(ta.lv_off[q + 1] - ta.lv_off[q]) + uint64_t(a.tpi) * MT - 1) / (uint64_t(a.tpi) * MT);
+  }
   const unsigned grid = unsigned(std::min<uint64_t>(items ? items : 1, uint64_t(num_sms())));
   TcView v1 = tv;
   v1.nbuf = 1;
@@ -854,6 +892,19 @@ int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t*
     ANQS_TRY(launch_finalize(hv, x + off, host_count(k), M->tc_raw, la + off, ph + off, nullptr, s));
   }
   return ANQS_OK;
+}
+
+int launch_mlp_tc_prefix_logits(const anqs_model* M, const anqs_ham* H, float* out8, cudaStream_t s) {
+  const int n = H->v.n;
+  TileArgs ta{};
+  ta.x = H->d_pt_x;
+  ta.rows = host_count(H->pt_x.size());
+  ta.p_lo = 0;
+  ta.p_hi = 1;
+  ta.raw = out8;
+  ta.levels = n;
+  for (int q = 0; q <= n; ++q) ta.lv_off[q] = H->pt_off[q];
+  return launch_slots(M, ta, s, PROF_TC_SLOT);
 }
 
 int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, const uint64_t* pre,

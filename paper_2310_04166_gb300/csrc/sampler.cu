@@ -57,8 +57,9 @@ struct Philox {
 };
 
 __global__ void init_kernel(uint64_t* pre, uint64_t* cnt, uint64_t* n_front, uint64_t n_samples, unsigned* done,
-                            uint64_t* child) {
+                            uint64_t* child, uint32_t* idx0) {
   ANQS_PDL_ENTRY();
+  if (idx0) idx0[0] = 0;  // prefix-table mode: the root is table row 0
   pre[0] = 0;
   cnt[0] = n_samples;
   n_front[0] = 1;
@@ -499,14 +500,16 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* sh
 // No CTA waits on another.
 __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, uint64_t seed, uint64_t counter0,
                                                              const uint64_t* __restrict__ counter_dev,
-                                                             const uint64_t* __restrict__ pre,
-                                                             const uint64_t* __restrict__ cnt,
-                                                             const uint64_t* __restrict__ n_front,
+                                                             const uint64_t* pre, const uint64_t* cnt,
+                                                             const uint64_t* n_front,
                                                              const float* __restrict__ logits,
                                                              uint64_t* __restrict__ child, unsigned* __restrict__ done,
                                                              uint64_t* __restrict__ pre_out,
                                                              uint64_t* __restrict__ cnt_out,
-                                                             uint64_t* __restrict__ n_out) {
+                                                             uint64_t* __restrict__ n_out,
+                                                             const uint32_t* idx_in,
+                                                             uint32_t* __restrict__ idx_out,
+                                                             const int32_t* __restrict__ pt_child, int early) {
   __shared__ uint32_t s_scan[SMALL_F + 1];
   extern __shared__ __align__(16) unsigned char s_dyn[];
   uint64_t(*s_thr)[4] = reinterpret_cast<uint64_t(*)[4]>(s_dyn);                  // SMALL_T x 4
@@ -514,11 +517,17 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
   __shared__ uint8_t s_mk[SMALL_T];
   __shared__ uint32_t s_red[33];
   __shared__ bool s_last;
-  // Prologue (before the wait on the slot-logits kernel): the frontier and
-  // its counts were written two kernels back (the previous level's split, or
-  // the initial/shard kernel), so the node offsets can be scanned while the
-  // logits kernel finishes.
-  const int nf = int(*n_front);
+  // Prologue (before the wait on the slot-logits kernel, with `early`): the
+  // frontier and its counts were written two kernels back (the previous
+  // level's split, or the initial/shard kernel), so the node offsets can be
+  // scanned while the logits kernel finishes.  Without `early` (prefix-table
+  // mode, where the previous kernel is the previous level's split itself)
+  // the scan waits for the previous kernel first.
+  // The frontier is read through L2 (__ldcg), never through the read-only
+  // cache: in prefix-table mode it was written by the kernel just before
+  // this one, which may still have been running when this grid started.
+  if (!early) ANQS_PDL_WAIT();
+  const int nf = int(__ldcg(n_front));
   const int lane = threadIdx.x & 31;
   // draw-block offsets of the nodes: each thread scans a run of RUN
   // consecutive nodes (their counts loaded together), one block scan per
@@ -529,7 +538,7 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
     uint32_t nb[RUN], mine = 0;
 #pragma unroll
     for (int e = 0; e < RUN; ++e) {
-      nb[e] = i0 + e < nf ? uint32_t((cnt[i0 + e] + 3) / 4) : 0u;
+      nb[e] = i0 + e < nf ? uint32_t((__ldcg(cnt + i0 + e) + 3) / 4) : 0u;
       mine += nb[e];
     }
     uint32_t tot;
@@ -564,9 +573,11 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
     if (threadIdx.x <= n_hi - n_lo) {
       const int i = n_lo + threadIdx.x;
       for (int v = 0; v < 4; ++v) s_cnt[threadIdx.x][v] = 0;
-      const uint64_t x = pre[i];
+      const uint64_t x = __ldcg(pre + i);
       const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p), x), mk = norm_mask(hv, p, pm);
-      split_thresholds(logits + uint64_t(i) * 8, mk, s_thr[threadIdx.x]);
+      // prefix-table mode: the node's logits sit at its table row
+      const uint64_t row = idx_in ? uint64_t(__ldcg(idx_in + i)) : uint64_t(i);
+      split_thresholds(logits + row * 8, mk, s_thr[threadIdx.x]);
       s_mk[threadIdx.x] = uint8_t(mk | (pm << 4));
     }
     __syncthreads();
@@ -577,9 +588,9 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
       node = node_of(t);
       const int li = node - n_lo;
       const uint64_t ib = t - s_scan[node];
-      const uint64_t c = cnt[node];
+      const uint64_t c = __ldcg(cnt + node);
       uint64_t w[4];
-      Philox::block(pre[node], ib, uint64_t(p), counter, seed, 0ull, w);
+      Philox::block(__ldcg(pre + node), ib, uint64_t(p), counter, seed, 0ull, w);
       const unsigned mk = s_mk[li] & 0xFu, pm = s_mk[li] >> 4;
       int last = 3;
       while (last > 0 && !((mk >> last) & 1u)) --last;
@@ -639,8 +650,9 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
     for (int e = 0; e < RUN; ++e)
       if (c[e]) {
         const int i = i0 + e;
-        pre_out[off] = pre[i >> 2] | (uint64_t(i & 3) << (2 * p));
+        pre_out[off] = __ldcg(pre + (i >> 2)) | (uint64_t(i & 3) << (2 * p));
         cnt_out[off] = c[e];
+        if (idx_out) idx_out[off] = uint32_t(pt_child[uint64_t(__ldcg(idx_in + (i >> 2))) * 4 + (i & 3)]);
         ++off;
       }
     carry += tot;
@@ -683,6 +695,8 @@ struct Plan {
   uint64_t F;  // max frontier
   uint64_t *pre[2], *cnt[2], *nblk, *nblk_scan, *child, *flags, *pos, *partial, *n_front;
   float* logits;
+  float* plog;         // prefix-table mode: slot outputs of every table row [rows][8]
+  uint32_t* idx[2];    // prefix-table mode: table row of each frontier node
   uint64_t* thr;
   uint8_t* allowed;
   unsigned* done;
@@ -712,6 +726,9 @@ void plan_ws(const anqs_ham* H, uint64_t n_samples, Arena& A, Plan& P) {
   P.partial = A.take<uint64_t>((F * 4 + 1) / SCAN_CHUNK + 2);
   P.n_front = A.take<uint64_t>(2);
   P.done = A.take<unsigned>(1);
+  const uint64_t rows = H->pt_x.size();
+  P.plog = rows ? A.take<float>(rows * 8) : nullptr;
+  for (int b = 0; b < 2; ++b) P.idx[b] = rows ? A.take<uint32_t>(F) : nullptr;
 }
 
 int scan(const uint64_t* in, const uint64_t* n_dev, uint64_t mult, uint64_t max_n, uint64_t* partial,
@@ -748,7 +765,17 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
   const int n = H->v.n;
   {
     ProfScope ps(PROF_SAMPLER, s);
-    ANQS_CUDA_LAUNCH("sampler init_kernel", launch_k(init_kernel, dim3(1), dim3(1), 0, s, P.pre[0], P.cnt[0], P.n_front, n_samples, P.done, P.child));
+    ANQS_CUDA_LAUNCH("sampler init_kernel", launch_k(init_kernel, dim3(1), dim3(1), 0, s, P.pre[0], P.cnt[0], P.n_front, n_samples, P.done, P.child, P.idx[0]));
+  }
+  // Prefix-table mode (BF16 MLP, small sectors, multinomial splits on one
+  // rank): the network's slot outputs of every physical prefix of every level
+  // in one launch, then per level only the split; the frontier carries each
+  // node's table row.  The draws and their order are those of the per-level
+  // path, so the samples are the same bit for bit.
+  const bool table = !binom && world == 1 && P.plog && M->d.kind == ANQS_MODEL_MLP &&
+                     M->d.form == ANQS_FORM_BF16 && n_samples < (1ull << 31);
+  if (table) {
+    ANQS_TRY(launch_mlp_tc_prefix_logits(M, H, P.plog, s));
   }
   bool prev_large = false;
   for (int p = 0; p < n; ++p) {
@@ -761,7 +788,7 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
       ANQS_CUDA_LAUNCH("sampler shard_kernel",
                        launch_k(shard_kernel, dim3(1), dim3(SMALL_T), 0, s, P.pre[cur], P.cnt[cur], nf, rank, world));
     }
-    ANQS_TRY(logits_dispatch(M, H, p, P.pre[cur], nf, Fp, P.logits, s));
+    if (!table) ANQS_TRY(logits_dispatch(M, H, p, P.pre[cur], nf, Fp, P.logits, s));
     ProfScope ps(PROF_SAMPLER, s);
     const bool last = (p == n - 1);
     if (binom) {
@@ -772,7 +799,7 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
       ANQS_CUDA_LAUNCH("sampler scatter_kernel", launch_k(scatter_kernel, dim3(blocks_for(Fp * 4, 256, 152 * 8)), dim3(256), 0, s, p, P.pre[cur], P.child, nf, P.pos, last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt]));
       continue;
     }
-    const bool small = Fp <= uint64_t(SMALL_F) && n_samples < (1ull << 31);
+    const bool small = (Fp <= uint64_t(SMALL_F) && n_samples < (1ull << 31)) || table;
     if (small && prev_large) {
       // the multi-kernel path leaves its counters set; the small path expects them cleared
       ANQS_CUDA(cudaMemsetAsync(P.child, 0, Fp * 4 * sizeof(uint64_t), s));
@@ -781,7 +808,7 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
     if (small) {
       const uint64_t blocks = ((n_samples + 3) / 4 + Fp + SMALL_T - 1) / SMALL_T;
       ANQS_CUDA(cudaFuncSetAttribute(draw_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(SMALL_DYN)));
-      ANQS_CUDA_LAUNCH("sampler draw_small_kernel", launch_k(draw_small_kernel, dim3(blocks_for(blocks, 1, 152)), dim3(SMALL_T), SMALL_DYN, s, H->v, p, seed, counter, counter_dev, P.pre[cur], P.cnt[cur], nf, P.logits, P.child, P.done, last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt], last ? n_unique : P.n_front + nxt));
+      ANQS_CUDA_LAUNCH("sampler draw_small_kernel", launch_k(draw_small_kernel, dim3(blocks_for(blocks, 1, 152)), dim3(SMALL_T), SMALL_DYN, s, H->v, p, seed, counter, counter_dev, P.pre[cur], P.cnt[cur], nf, table ? P.plog : P.logits, P.child, P.done, last ? x_out : P.pre[nxt], last ? n_out : P.cnt[nxt], last ? n_unique : P.n_front + nxt, table ? P.idx[cur] : nullptr, table && !last ? P.idx[nxt] : nullptr, H->d_pt_child, (table && p > 0) ? 0 : 1));
       continue;
     }
     ANQS_CUDA_LAUNCH("sampler prep_kernel", launch_k(prep_kernel, dim3(blocks_for(Fp, 256, 152 * 8)), dim3(256), 0, s, H->v, p, P.pre[cur], P.cnt[cur], nf, P.logits, P.thr, P.allowed, P.nblk, P.child));

@@ -6,7 +6,10 @@ wait on one another).  Bars: the union of the shards is the unsharded sample
 set, bit for bit, for every split level; the combined statistics equal the
 unsharded ones to FP64 summation-order rounding; the summed gradient equals
 the unsharded one to float32 summation-order rounding; the sharded sets also
-match the oracle's own shards.
+match the oracle's own shards.  For the BF16 MLP on h2o the unsharded pass
+takes the prefix-table path (every physical prefix evaluated in one launch)
+and the shards the per-level path, so the first test also pins the two paths
+to each other bit for bit.
 """
 import numpy as np
 import pytest
