@@ -57,9 +57,11 @@ struct Philox {
 };
 
 __global__ void init_kernel(uint64_t* pre, uint64_t* cnt, uint64_t* n_front, uint64_t n_samples, unsigned* done,
-                            uint64_t* child, uint32_t* idx0) {
+                            uint64_t* child, uint32_t* idx0, int* barrier) {
   ANQS_PDL_ENTRY();
   if (idx0) idx0[0] = 0;  // prefix-table mode: the root is table row 0
+  if (barrier)            // the persistent launch's grid barrier: count, rounds, error
+    for (int k = 0; k < 4; ++k) barrier[k] = 0;
   pre[0] = 0;
   cnt[0] = n_samples;
   n_front[0] = 1;
@@ -666,7 +668,255 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
   }
 }
 
-// Keeps the nodes i with i % world == rank of a device-sized list, in order
+// ---- every level in one persistent launch (prefix-table mode) -----------------
+// The grid is co-resident (cooperative launch) and passes one grid-wide
+// barrier per level.  Each CTA keeps its own copy of the frontier (prefix,
+// count, table row) in shared memory: after the barrier of level p every CTA
+// reads the child counters of level p and compacts them into its copy of
+// the level-(p+1) frontier, so no frontier goes through global memory and no
+// CTA waits for another's compaction.  The child counters rotate over three
+// buffers: level p adds into buffer p % 3 and, before its barrier, the grid
+// clears buffer (p + 1) % 3, which every CTA finished reading before the
+// barrier of level p - 1.  The draws and their order are those of
+// draw_small_kernel, so the samples are the same bit for bit.
+constexpr int PER_F = 2048;                          // largest frontier (the prefix table's level bound)
+constexpr size_t PER_DYN = size_t(2) * PER_F * (8 + 4 + 4)   // frontier copies: prefix, count, table row
+                           + size_t(PER_F + 1) * 4            // draw-block offsets
+                           + size_t(SMALL_T) * (32 + 16);     // window thresholds and counts
+constexpr uint64_t kBarrierNs = 2000000000ull;
+
+struct GridBarrier {
+  unsigned count;  // CTAs arrived in the current round
+  unsigned gen;    // rounds completed
+  int err;         // a CTA gave up waiting
+  int pad;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Barrier over the co-resident grid: the last CTA to arrive resets the count
+// and opens the next round; the others wait (bounded by kBarrierNs, after
+// which they set the error word and every CTA leaves).  Writes before the
+// barrier are visible to every CTA after it.  `gen` is thread 0's count of
+// rounds passed.
+__device__ bool grid_barrier(GridBarrier* gb, unsigned& gen, int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      const uint64_t t0 = gtimer();
+      while (ld_acquire_u32(&gb->gen) == gen) {
+        if (*reinterpret_cast<volatile int*>(&gb->err) || gtimer() - t0 > kBarrierNs) {
+          atomicExch(&gb->err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ++gen;
+    *s_ok = ok && !*reinterpret_cast<volatile int*>(&gb->err);
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+__global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int n, uint64_t n_samples, uint64_t seed,
+                                                                uint64_t counter0,
+                                                                const uint64_t* __restrict__ counter_dev,
+                                                                const float* __restrict__ logits,
+                                                                const int32_t* __restrict__ pt_child,
+                                                                uint64_t* child, uint64_t child_stride,
+                                                                GridBarrier* gb, uint64_t* __restrict__ x_out,
+                                                                uint64_t* __restrict__ n_out,
+                                                                uint64_t* __restrict__ n_unique, int* status) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  uint64_t* fr_pre = reinterpret_cast<uint64_t*>(s_dyn);                        // [2][PER_F]
+  uint32_t* fr_cnt = reinterpret_cast<uint32_t*>(fr_pre + 2 * PER_F);            // [2][PER_F]
+  uint32_t* fr_idx = fr_cnt + 2 * PER_F;                                         // [2][PER_F]
+  uint32_t* s_scan = fr_idx + 2 * PER_F;                                         // [PER_F + 1]
+  uint64_t(*s_thr)[4] = reinterpret_cast<uint64_t(*)[4]>(s_scan + PER_F + 4);    // [SMALL_T][4]
+  uint32_t(*s_cnt)[4] = reinterpret_cast<uint32_t(*)[4]>(s_thr + SMALL_T);       // [SMALL_T][4]
+  __shared__ uint8_t s_mk[SMALL_T];
+  __shared__ uint32_t s_red[33];
+  __shared__ int s_ok;
+  ANQS_PDL_WAIT();  // the prefix table's logits and the cleared counters come from the kernels before
+  const int lane = threadIdx.x & 31;
+  const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
+  unsigned gen = 0;  // the initial kernel zeroed the barrier
+  if (threadIdx.x == 0) {
+    fr_pre[0] = 0;
+    fr_cnt[0] = uint32_t(n_samples);
+    fr_idx[0] = 0;
+  }
+  int nf = 1;
+  bool ok = true;
+  for (int p = 0; p < n && ok; ++p) {
+    const int cur = p & 1, nxt = cur ^ 1;
+    const uint64_t* pre = fr_pre + cur * PER_F;
+    const uint32_t* cnt = fr_cnt + cur * PER_F;
+    const uint32_t* idx = fr_idx + cur * PER_F;
+    uint64_t* ch = child + uint64_t(p % 3) * child_stride;
+    // clear the counters of level p + 1 (last read before the barrier of level p - 1)
+    {
+      uint64_t* nc = child + uint64_t((p + 1) % 3) * child_stride;
+      for (uint64_t i = blockIdx.x * uint64_t(SMALL_T) + threadIdx.x; i < child_stride;
+           i += uint64_t(gridDim.x) * SMALL_T)
+        nc[i] = 0;
+    }
+    __syncthreads();  // this level's frontier copy is complete
+    // draw-block offsets of the nodes
+    uint32_t carry = 0;
+    for (int base = 0; base < nf; base += RUN * SMALL_T) {
+      const int i0 = base + RUN * threadIdx.x;
+      uint32_t nb[RUN], mine = 0;
+#pragma unroll
+      for (int e = 0; e < RUN; ++e) {
+        nb[e] = i0 + e < nf ? (cnt[i0 + e] + 3u) / 4u : 0u;
+        mine += nb[e];
+      }
+      uint32_t tot;
+      uint32_t off = carry + block_excl_scan_u32(mine, s_red, &tot);
+#pragma unroll
+      for (int e = 0; e < RUN; ++e)
+        if (i0 + e < nf) {
+          s_scan[i0 + e] = off;
+          off += nb[e];
+        }
+      carry += tot;
+    }
+    if (threadIdx.x == 0) s_scan[nf] = carry;
+    __syncthreads();
+    const uint32_t total = carry;
+    auto node_of = [&](uint32_t t) {
+      int lo = 0, hi = nf - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_scan[mid] <= t) lo = mid;
+        else hi = mid - 1;
+      }
+      return lo;
+    };
+    for (uint32_t t0 = blockIdx.x * SMALL_T; t0 < total; t0 += gridDim.x * SMALL_T) {
+      const uint32_t t_end = min(total, t0 + SMALL_T);
+      const int n_lo = node_of(t0), n_hi = node_of(t_end - 1);
+      __syncthreads();  // previous window's thresholds are no longer read
+      if (threadIdx.x <= n_hi - n_lo) {
+        const int i = n_lo + threadIdx.x;
+        for (int v = 0; v < 4; ++v) s_cnt[threadIdx.x][v] = 0;
+        const uint64_t x = pre[i];
+        const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p), x), mk = norm_mask(hv, p, pm);
+        split_thresholds(logits + uint64_t(idx[i]) * 8, mk, s_thr[threadIdx.x]);
+        s_mk[threadIdx.x] = uint8_t(mk | (pm << 4));
+      }
+      __syncthreads();
+      const uint32_t t = t0 + threadIdx.x;
+      int node = -1;
+      uint32_t packed = 0;
+      if (t < t_end) {
+        node = node_of(t);
+        const int li = node - n_lo;
+        const uint64_t ib = t - s_scan[node];
+        const uint64_t c = cnt[node];
+        uint64_t w[4];
+        Philox::block(pre[node], ib, uint64_t(p), counter, seed, 0ull, w);
+        const unsigned mk = s_mk[li] & 0xFu, pm = s_mk[li] >> 4;
+        int last = 3;
+        while (last > 0 && !((mk >> last) & 1u)) --last;
+        for (int k = 0; k < 4; ++k) {
+          if (ib * 4 + k >= c) break;
+          const int v = draw_outcome(w[k], s_thr[li], mk, last);
+          if ((pm >> v) & 1u) packed += 1u << (8 * v);
+        }
+      }
+      const int prev = __shfl_up_sync(0xffffffffu, node, 1);
+      const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || prev != node);
+      const int seg_start = 31 - __clz(heads & ((2u << lane) - 1u));
+      uint32_t v = packed;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t other = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane - o >= seg_start) v += other;
+      }
+      const bool tail = (lane == 31) || ((heads >> (lane + 1)) & 1u);
+      if (tail && node >= 0)
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t ck = (v >> (8 * k)) & 0xffu;
+          if (ck) atomicAdd(&s_cnt[node - n_lo][k], ck);
+        }
+      __syncthreads();
+      if (threadIdx.x <= n_hi - n_lo)
+        for (int k = 0; k < 4; ++k) {
+          const uint32_t ck = s_cnt[threadIdx.x][k];
+          if (ck)
+            atomicAdd(reinterpret_cast<unsigned long long*>(ch + uint64_t(n_lo + threadIdx.x) * 4 + k),
+                      (unsigned long long)ck);
+        }
+    }
+    // every CTA's counts of level p are in `ch`
+    ok = grid_barrier(gb, gen, &s_ok);
+    if (!ok) break;
+    // children in (node, outcome) order -> this CTA's copy of the next frontier
+    // (the last level: the output, written by CTA 0)
+    const bool last = (p == n - 1);
+    carry = 0;
+    for (int base = 0; base < 4 * nf; base += RUN * SMALL_T) {
+      const int i0 = base + RUN * threadIdx.x;
+      uint64_t c[RUN];
+      uint32_t mine = 0;
+#pragma unroll
+      for (int e = 0; e < RUN; ++e) {
+        c[e] = i0 + e < 4 * nf ? __ldcg(ch + i0 + e) : 0ull;
+        mine += c[e] ? 1u : 0u;
+      }
+      uint32_t tot;
+      uint32_t off = carry + block_excl_scan_u32(mine, s_red, &tot);
+#pragma unroll
+      for (int e = 0; e < RUN; ++e)
+        if (c[e]) {
+          const int i = i0 + e;
+          const uint64_t xc = pre[i >> 2] | (uint64_t(i & 3) << (2 * p));
+          if (!last) {
+            if (off < uint32_t(PER_F)) {
+              fr_pre[nxt * PER_F + off] = xc;
+              fr_cnt[nxt * PER_F + off] = uint32_t(c[e]);
+              fr_idx[nxt * PER_F + off] = uint32_t(pt_child[uint64_t(idx[i >> 2]) * 4 + (i & 3)]);
+            }
+          } else if (blockIdx.x == 0) {
+            x_out[off] = xc;
+            n_out[off] = c[e];
+          }
+          ++off;
+        }
+      carry += tot;
+    }
+    if (last && blockIdx.x == 0 && threadIdx.x == 0) *n_unique = carry;
+    if (!last && carry > uint32_t(PER_F)) {  // cannot happen with the prefix table's level bound
+      if (threadIdx.x == 0) atomicExch(&gb->err, 1);
+      ok = false;
+    }
+    nf = int(carry);
+  }
+  if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(&gb->err)) atomicExch(status, 1);
+}
+
+
 // and in place (one CTA, chunk by chunk: each chunk is read before any of
 // its compacted entries is written).
 __global__ void __launch_bounds__(SMALL_T) shard_kernel(uint64_t* __restrict__ pre, uint64_t* __restrict__ cnt,
@@ -697,6 +947,7 @@ struct Plan {
   float* logits;
   float* plog;         // prefix-table mode: slot outputs of every table row [rows][8]
   uint32_t* idx[2];    // prefix-table mode: table row of each frontier node
+  GridBarrier* barrier;  // prefix-table mode: the persistent launch's grid barrier
   uint64_t* thr;
   uint8_t* allowed;
   unsigned* done;
@@ -720,7 +971,7 @@ void plan_ws(const anqs_ham* H, uint64_t n_samples, Arena& A, Plan& P) {
   P.allowed = A.take<uint8_t>(F);
   P.nblk = A.take<uint64_t>(F);
   P.nblk_scan = A.take<uint64_t>(F + 1);
-  P.child = A.take<uint64_t>(F * 4);
+  P.child = A.take<uint64_t>(F * 4 * (H->pt_x.empty() ? 1 : 3));  // prefix-table mode: three rotating buffers
   P.flags = A.take<uint64_t>(F * 4);
   P.pos = A.take<uint64_t>(F * 4 + 1);
   P.partial = A.take<uint64_t>((F * 4 + 1) / SCAN_CHUNK + 2);
@@ -729,6 +980,7 @@ void plan_ws(const anqs_ham* H, uint64_t n_samples, Arena& A, Plan& P) {
   const uint64_t rows = H->pt_x.size();
   P.plog = rows ? A.take<float>(rows * 8) : nullptr;
   for (int b = 0; b < 2; ++b) P.idx[b] = rows ? A.take<uint32_t>(F) : nullptr;
+  P.barrier = rows ? A.take<GridBarrier>(1) : nullptr;
 }
 
 int scan(const uint64_t* in, const uint64_t* n_dev, uint64_t mult, uint64_t max_n, uint64_t* partial,
@@ -765,7 +1017,7 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
   const int n = H->v.n;
   {
     ProfScope ps(PROF_SAMPLER, s);
-    ANQS_CUDA_LAUNCH("sampler init_kernel", launch_k(init_kernel, dim3(1), dim3(1), 0, s, P.pre[0], P.cnt[0], P.n_front, n_samples, P.done, P.child, P.idx[0]));
+    ANQS_CUDA_LAUNCH("sampler init_kernel", launch_k(init_kernel, dim3(1), dim3(1), 0, s, P.pre[0], P.cnt[0], P.n_front, n_samples, P.done, P.child, P.idx[0], reinterpret_cast<int*>(P.barrier)));
   }
   // Prefix-table mode (BF16 MLP, small sectors, multinomial splits on one
   // rank): the network's slot outputs of every physical prefix of every level
@@ -776,6 +1028,37 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
                      M->d.form == ANQS_FORM_BF16 && n_samples < (1ull << 31);
   if (table) {
     ANQS_TRY(launch_mlp_tc_prefix_logits(M, H, P.plog, s));
+    // all levels in one cooperative launch (one CTA per SM at most, each CTA
+    // one window of draw blocks per round)
+    int occ = 0;
+    ANQS_CUDA(cudaFuncSetAttribute(sample_levels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(PER_DYN)));
+    ANQS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sample_levels_kernel, SMALL_T, PER_DYN));
+    int dev = 0, sms = 0;
+    ANQS_CUDA(cudaGetDevice(&dev));
+    ANQS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (occ >= 1) {
+      uint64_t F = 1;
+      for (int q = 0; q <= n; ++q) F = std::max(F, level_cap(H, n_samples, q));
+      const unsigned grid = blocks_for(((n_samples + 3) / 4 + F + SMALL_T - 1) / SMALL_T, 1, uint64_t(sms));
+      int* status = reinterpret_cast<int*>(static_cast<unsigned char*>(M->packed) + M->pack_off[n]);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(grid);
+      cfg.blockDim = dim3(SMALL_T);
+      cfg.dynamicSmemBytes = PER_DYN;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      ProfScope ps(PROF_SAMPLER, s);
+      note_launch();
+      ANQS_CUDA_LAUNCH("sampler sample_levels_kernel",
+                       cudaLaunchKernelEx(&cfg, sample_levels_kernel, H->v, n, n_samples, seed, counter, counter_dev,
+                                          static_cast<const float*>(P.plog), static_cast<const int32_t*>(H->d_pt_child),
+                                          P.child, F * 4, P.barrier, x_out, n_out, n_unique, status));
+      return ANQS_OK;
+    }
   }
   bool prev_large = false;
   for (int p = 0; p < n; ++p) {
