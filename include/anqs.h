@@ -93,9 +93,14 @@ enum { ANQS_MODEL_MLP = 0, ANQS_MODEL_TF = 1, ANQS_MODEL_TABLE = 2, ANQS_MODEL_N
  * FP32: plain SIMT float32 kernels, every configuration evaluated over all
  *       slots (no prefix reuse), except the NADE, whose local energy reuses
  *       the parent's slots for its connected determinants.
- * BF16: tensor-core (tcgen05, TMEM accumulators) bfloat16 GEMMs with float32
+ * BF16: tensor-core (tcgen05, TMEM accumulators) 16-bit GEMMs with float32
  *       accumulation, float32 activations/softmax/phase heads, and reuse of
- *       the parent determinant's slots for its connected determinants. */
+ *       the parent determinant's slots for its connected determinants.  The
+ *       MLP's operands are bfloat16 (its layer-1 weights as two bf16 parts);
+ *       the transformer's operands and stored keys/values are fp16 (the same
+ *       MMA instruction and rate, three more significand bits for its
+ *       activations; conversions saturate at +-65504).  MLP width 64 or 128,
+ *       transformer d_model 64 or 128 with head width 16 or 32. */
 enum { ANQS_FORM_FP32 = 0, ANQS_FORM_BF16 = 1 };
 
 typedef struct anqs_ham anqs_ham;
@@ -153,6 +158,20 @@ ANQS_API int anqs_hamiltonian_destroy(anqs_ham* ham);
  * every later call with this Hamiltonian (sampling, log psi, local energy,
  * gradient).  ANQS_ERR_ARG unless 0 <= du_levels <= n_orb. */
 ANQS_API int anqs_hamiltonian_set_pruning(anqs_ham* ham, int du_levels);
+
+/* Sampler events recorded on the device for this Hamiltonian since its
+ * creation or the last clear, as a bit set:
+ *   ANQS_HAM_BINOMIAL_REJECT  a binomial draw of anqs_sample_binomial left
+ *                             the BTRS rejection loop (Hormann 1993) after 256
+ *                             rejections and took the mode;
+ *   ANQS_HAM_BINOMIAL_CAP     a pmf-inversion walk (n q < 10) stopped at
+ *                             k = 4096.
+ * Both have negligible probability; either makes that one draw biased.
+ * Synchronous (reads one word); clear != 0 resets the word.  ANQS_ERR_ARG
+ * for a null pointer. */
+#define ANQS_HAM_BINOMIAL_REJECT 1
+#define ANQS_HAM_BINOMIAL_CAP 2
+ANQS_API int anqs_hamiltonian_status(const anqs_ham* ham, int* status, int clear);
 
 /* Z2 symmetries of H (Sec. IV.A: Pauli-Z strings that commute with H, such
  * as the images of the abelian point-group operations under the
@@ -213,7 +232,7 @@ ANQS_API int anqs_model_param_count(const anqs_model_desc* desc, uint64_t* n_par
 
 /* Creates a model over params_dev (n_params floats, caller-owned device
  * memory that must outlive the model; the library keeps the pointer).  The
- * BF16 form keeps packed bfloat16 copies of the weights: call
+ * BF16 form keeps packed 16-bit copies of the weights: call
  * anqs_model_sync() after changing params_dev.  Synchronous.
  * Errors: ANQS_ERR_ARG, ANQS_ERR_UNSUPPORTED (sizes outside the ranges of
  * anqs_model_desc), ANQS_ERR_CUDA. */
@@ -419,8 +438,9 @@ ANQS_API int anqs_logpsi_vjp(const anqs_model* model, const anqs_ham* ham, const
  * Local energy without caller workspace (the paper has no counterpart: this
  * is an interface for callers that cannot allocate device memory)
  *
- * Same computation and outputs as anqs_local_energy for FP32-form MLP and
- * table models, but the scratch memory lives in a fixed 16 MiB array inside
+ * Same computation and outputs as anqs_local_energy for FP32-form models
+ * (MLP, transformer, table, NADE), but the scratch memory lives in a fixed
+ * 16 MiB array inside
  * the library (one per GPU that loads it, kept until the process exits)
  * instead of a caller-provided workspace, and nothing is allocated.  Meant
  * for callers that cannot hand out device memory at run time, e.g. plug-ins
@@ -428,9 +448,12 @@ ANQS_API int anqs_logpsi_vjp(const anqs_model* model, const anqs_ham* ham, const
  * call cudaMalloc after start-up.
  * - Needs n_x * n_connected * 24 + n_x * 16 bytes (plus alignment) to fit in
  *   16 MiB; larger requests fail with ANQS_ERR_CAPACITY before any work is
- *   queued.  Other forms and kinds: ANQS_ERR_UNSUPPORTED.
+ *   queued.  BF16 forms: ANQS_ERR_UNSUPPORTED.
  * - The first call on a device looks up the array's device address (with
  *   that device current); make that first call before any stream capture.
+ *   A context made anew on the device (e.g. after cudaDeviceReset) makes the
+ *   next call look the address up again, so make that call outside capture
+ *   too.
  * - All calls on a device share the array: calls that may run concurrently
  *   on the GPU race and must be ordered by the caller.  Every scratch
  *   element is written before it is read, so no clearing is needed.

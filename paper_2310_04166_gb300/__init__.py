@@ -68,6 +68,12 @@ class Hamiltonian:
     def handle(self):
         return self._h
 
+    def status(self, clear: bool = False) -> int:
+        """Sampler event bits recorded on the device (anqs_hamiltonian_status)."""
+        v = C.c_int()
+        check(_lib.load().anqs_hamiltonian_status(self._h, C.byref(v), int(bool(clear))))
+        return v.value
+
     def set_pruning(self, du_levels: int) -> "Hamiltonian":
         """MU-d (Sec. III.C): MU on the first n_orb - du_levels slots, DU on the rest."""
         check(_lib.load().anqs_hamiltonian_set_pruning(self._h, int(du_levels)))

@@ -59,6 +59,7 @@ SIGNATURES = {
     "anqs_sample_shard": (C.c_int, [_VP, _VP, _U64, _U64, _U64, _VP, C.c_int, C.c_int, C.c_int, _VP, _VP, _U64, _VP,
                                      _VP, _SZ, _VP]),
     "anqs_hamiltonian_set_pruning": (C.c_int, [_VP, C.c_int]),
+    "anqs_hamiltonian_status": (C.c_int, [_VP, C.POINTER(C.c_int), C.c_int]),
     "anqs_hamiltonian_set_z2": (C.c_int, [_VP, C.c_int, _VP]),
     "anqs_model_status": (C.c_int, [_VP, C.POINTER(C.c_int)]),
     "anqs_stats_combine": (C.c_int, [_VP, C.c_int, _VP, _VP]),

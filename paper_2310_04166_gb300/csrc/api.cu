@@ -334,7 +334,8 @@ int anqs_hamiltonian_create(anqs_ham** out, int n, int na, int nb, const double*
   size_t hn = size_t(n) * n, gn = hn * hn;
   if (cudaMalloc(&H->d_h, hn * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&H->d_g, gn * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&H->d_mask, H->mask_host.size()) != cudaSuccess) {
+      cudaMalloc(&H->d_mask, H->mask_host.size()) != cudaSuccess ||
+      cudaMalloc(&H->d_status, sizeof(unsigned)) != cudaSuccess) {
     cudaGetLastError();
     anqs_hamiltonian_destroy(H);
     return set_error(ANQS_ERR_CUDA, "cudaMalloc failed for Hamiltonian tables");
@@ -342,6 +343,8 @@ int anqs_hamiltonian_create(anqs_ham** out, int n, int na, int nb, const double*
   ANQS_CUDA(cudaMemcpy(H->d_h, h_host, hn * sizeof(double), cudaMemcpyHostToDevice));
   ANQS_CUDA(cudaMemcpy(H->d_g, g_host, gn * sizeof(double), cudaMemcpyHostToDevice));
   ANQS_CUDA(cudaMemcpy(H->d_mask, H->mask_host.data(), H->mask_host.size(), cudaMemcpyHostToDevice));
+  ANQS_CUDA(cudaMemset(H->d_status, 0, sizeof(unsigned)));
+  v.status = H->d_status;
   v.h = H->d_h;
   v.g = H->d_g;
   v.mask = H->d_mask;
@@ -401,7 +404,18 @@ int anqs_hamiltonian_destroy(anqs_ham* H) {
   cudaFree(H->d_mask);
   cudaFree(H->d_pt_x);
   cudaFree(H->d_pt_child);
+  cudaFree(H->d_status);
   delete H;
+  return ANQS_OK;
+}
+
+int anqs_hamiltonian_status(const anqs_ham* H, int* status, int clear) {
+  if (!H || !status) return set_error(ANQS_ERR_ARG, "null argument");
+  ANQS_TRY(check_stream_device(H->device));
+  unsigned v = 0;
+  ANQS_CUDA(cudaMemcpy(&v, H->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost));
+  if (clear) ANQS_CUDA(cudaMemset(H->d_status, 0, sizeof(unsigned)));
+  *status = int(v);
   return ANQS_OK;
 }
 

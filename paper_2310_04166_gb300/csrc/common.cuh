@@ -130,6 +130,7 @@ struct HamView {
   int mu_lv;           // slots p < mu_lv are masked (MU), slots p >= mu_lv discard (DU): MU-d, d = n - mu_lv
   int nz;              // Z2 symmetries (Pauli-Z strings commuting with H), 0..ANQS_MAX_Z2
   uint64_t zmask[4];   // their qubit supports (bit q = qubit q)
+  unsigned* status;    // sampler events (ANQS_HAM_* bits of anqs.h), set with atomicOr
 };
 
 // slot mask table entry of (slot p, a alpha and b beta electrons, Z2 parity
@@ -234,6 +235,7 @@ struct anqs_ham {
   std::vector<int32_t> pt_child;
   uint64_t* d_pt_x;
   int32_t* d_pt_child;
+  unsigned* d_status;  // HamView::status
   double* d_h;
   double* d_g;
   uint8_t* d_mask;

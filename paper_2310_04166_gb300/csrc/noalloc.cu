@@ -32,19 +32,52 @@ static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBy
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {nullptr};
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};
 
-// Device address of the array on the current device, looked up once per
-// device (the host-side symbol is only a stand-in and must never be passed
-// to a kernel).
+// Identifier of the current CUDA context (the driver's cuCtxGetCurrent and
+// cuCtxGetId, reached through the runtime's entry-point query so that the
+// library does not link the driver library); 0 when unavailable.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void**);
+  using GetId = int (*)(void*, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static bool looked_up = false;
+  if (!looked_up) {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+    cudaGetLastError();
+    looked_up = true;
+  }
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current && get_id && get_current(&ctx) == 0 && ctx && get_id(ctx, &id) == 0) return id;
+  return 0;
+}
+
+// Device address of the array in the current context, looked up once per
+// (device, context) (the host-side symbol is only a stand-in and must never
+// be passed to a kernel).  A context made anew on a device (for example
+// after cudaDeviceReset) loads the module again and may place the array
+// elsewhere, so a new context id triggers a new lookup.
 int scratch_address(int device, void** out) {
   if (device < 0 || device >= kMaxDevices)
     return set_error(ANQS_ERR_UNSUPPORTED, "device ordinal %d beyond %d", device, kMaxDevices);
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_scratch_ptr[device]) {
+  const unsigned long long ctx = current_context_id();
+  if (!g_scratch_ptr[device] || ctx != g_scratch_ctx[device]) {
     void* p = nullptr;
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess) return cuda_error(e, "cudaGetSymbolAddress(g_static_scratch)", __FILE__, __LINE__);
     g_scratch_ptr[device] = p;
+    g_scratch_ctx[device] = ctx;
   }
   *out = g_scratch_ptr[device];
   return ANQS_OK;
@@ -60,8 +93,8 @@ extern "C" int anqs_local_energy_static(const anqs_model* M, const anqs_ham* H, 
                                         double* stats, void* stream) {
   if (!M || !H) return set_error(ANQS_ERR_ARG, "null model or Hamiltonian");
   if (M->d.n_orb != H->v.n) return set_error(ANQS_ERR_ARG, "model and Hamiltonian sizes differ");
-  if (M->d.form != ANQS_FORM_FP32 || (M->d.kind != ANQS_MODEL_MLP && M->d.kind != ANQS_MODEL_TABLE))
-    return set_error(ANQS_ERR_UNSUPPORTED, "the static-scratch local energy serves FP32-form MLP and table models");
+  if (M->d.form != ANQS_FORM_FP32)
+    return set_error(ANQS_ERR_UNSUPPORTED, "the static-scratch local energy serves FP32-form models");
   if (n_x == 0) return set_error(ANQS_ERR_ARG, "n_x must be >= 1");
   if (!x || !ere || !eim) return set_error(ANQS_ERR_ARG, "null array argument");
   if (counts && !stats) return set_error(ANQS_ERR_ARG, "counts given without stats output");

@@ -347,7 +347,10 @@ __device__ __forceinline__ double lgamma_stirling(double x) {
 }
 
 // one draw of B(n, q)
-__device__ uint64_t binomial(uint64_t n, double q, Uniforms& U) {
+// Sets bit 1 of *events when an inversion walk stops at k = 4096 and bit 0
+// when the BTRS loop gives up after 256 rejections (returning the mode); both
+// have negligible probability, and either makes that draw biased.
+__device__ uint64_t binomial(uint64_t n, double q, Uniforms& U, unsigned* events) {
   if (n == 0 || !(q > 0.0)) return 0;
   if (q >= 1.0) return n;
   const bool flip = q > 0.5;
@@ -362,6 +365,7 @@ __device__ uint64_t binomial(uint64_t n, double q, Uniforms& U) {
       ++k;
       r *= a / double(k) - s;
     }
+    if (u > r && k < n) *events |= 2u;
   } else {
     // BTRS: transformed rejection with squeeze (Hormann 1993)
     const double spq = sqrt(nd * p * qq);
@@ -370,21 +374,24 @@ __device__ uint64_t binomial(uint64_t n, double q, Uniforms& U) {
     const double m = floor((nd + 1.0) * p);
     const double h = lgamma_stirling(m + 1.0) + lgamma_stirling(nd - m + 1.0);
     k = uint64_t(m);
-    for (int it = 0; it < 256; ++it) {  // acceptance is above 0.8 per iteration
+    bool accepted = false;
+    for (int it = 0; it < 256 && !accepted; ++it) {  // acceptance is above 0.8 per iteration
       const double u = U.next() - 0.5, v = U.next();
       const double us = 0.5 - fabs(u);
       const double kf = floor((2.0 * a / us + b) * u + c);
       if (kf < 0.0 || kf > nd) continue;
       if (us >= 0.07 && v <= vr) {
         k = uint64_t(kf);
-        break;
+        accepted = true;
+        continue;
       }
       const double lv = log(v * alpha / (a / (us * us) + b));
       if (lv <= h - lgamma_stirling(kf + 1.0) - lgamma_stirling(nd - kf + 1.0) + (kf - m) * lpq) {
         k = uint64_t(kf);
-        break;
+        accepted = true;
       }
     }
+    if (!accepted) *events |= 1u;
   }
   return flip ? n - k : k;
 }
@@ -394,6 +401,7 @@ __global__ void binom_kernel(HamView hv, int p, uint64_t seed, uint64_t counter0
                              const uint64_t* __restrict__ cnt, const uint64_t* __restrict__ n_front,
                              const float* __restrict__ logits, uint64_t* __restrict__ child) {
   ANQS_PDL_ENTRY();
+  unsigned events = 0;
   const uint64_t nf = *n_front;
   const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < nf; i += uint64_t(gridDim.x) * blockDim.x) {
@@ -420,7 +428,7 @@ __global__ void binom_kernel(HamView hv, int p, uint64_t seed, uint64_t counter0
         } else {
           const double pv = double(__fdiv_rn(e[v], s));
           Uniforms U{x, uint64_t(v), uint64_t(p), counter, seed, 0, {0, 0, 0, 0}, 4};
-          k = binomial(rest, tail > 0.0 ? fmin(pv / tail, 1.0) : 1.0, U);
+          k = binomial(rest, tail > 0.0 ? fmin(pv / tail, 1.0) : 1.0, U, &events);
           tail -= pv;
         }
       }
@@ -428,6 +436,7 @@ __global__ void binom_kernel(HamView hv, int p, uint64_t seed, uint64_t counter0
       rest -= k;
     }
   }
+  if (events && hv.status) atomicOr(hv.status, events);
 }
 
 __global__ void flag_kernel(const uint64_t* __restrict__ child, const uint64_t* __restrict__ n_front,

@@ -1,6 +1,7 @@
-// BF16 tensor-core form of the causal-transformer ansatz at d_model = 128
+// 16-bit tensor-core form of the causal-transformer ansatz at d_model = 128
 // (tcgen05 MMAs with TMEM accumulators), with reuse of the parent
-// determinant's keys and values for its connected determinants.
+// determinant's keys and values for its connected determinants.  GEMM
+// operands and stored keys and values are fp16 (see tf_tc.cu for why).
 //
 // The network is the one of the FP32 form (decoder-only, pre-LayerNorm, eps
 // 1e-5, causal multi-head attention, ReLU FFN of width 4d, head d -> 8 whose
@@ -12,7 +13,7 @@
 // model dimensions of every row: its 64 residual-stream values in
 // registers, its 64 columns of every epilogue, its half of the attention
 // heads.  LayerNorm statistics and the head's partial sums cross between the
-// halves through shared memory.  A layer's weights (384 KB in bf16) do not
+// halves through shared memory.  A layer's weights (384 KB in fp16) do not
 // fit in shared memory: they are cut into twelve [128 out][128 in] chunks
 // (q, k, v, o, the four W1 row blocks and the four W2 column blocks, stored
 // in the order the MMAs consume them) that stream through a ring of three
@@ -26,12 +27,12 @@
 // output projection reuses q's columns), the two FFN hidden-chunk
 // accumulators at 128 and 256 (after k and v are consumed), the FFN output
 // accumulator at 384.  Per block:
-//   LN1 -> A (bf16)        MMA q, k, v = A W^T
+//   LN1 -> A (fp16)        MMA q, k, v = A W^T
 //   k, v (+ bias) -> shared memory and the parent cache; causal attention of
 //   each row over keys 0..t on the CUDA cores (online softmax, f32) -> A
 //   MMA o = A Wo^T         h += o + bo;  LN2 -> A
 //   FFN chunk c: MMA f1_c = A W1_c^T (issued one chunk ahead), ReLU -> H_c
-//   (bf16, two buffers in the key/value region), MMA acc2 += H_c W2_c^T
+//   (fp16, two buffers in the key/value region), MMA acc2 += H_c W2_c^T
 //   h += acc2 + b2
 // then LNf and the f32 head.
 //
@@ -42,7 +43,7 @@
 //   SUFFIX  connected determinants x' grouped by first differing slot j:
 //           positions j+1..n-1 only, keys and values of positions <= j from
 //           the parent cache; writes the masked slot terms T[x'][t].
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -61,7 +62,7 @@ constexpr int D = 128;
 constexpr int MT = 128;
 constexpr int HD = D / 2;                       // model dimensions per warpgroup
 constexpr int NT = 256;                         // two warpgroups
-constexpr uint32_t CHUNK = D * D * 2;           // one weight chunk, [128][128] bf16 canonical K-major
+constexpr uint32_t CHUNK = D * D * 2;           // one weight chunk, [128][128] fp16 canonical K-major
 constexpr int NCH = 12;                         // chunks per layer, in consumption order
 constexpr uint32_t LAYER_BYTES = NCH * CHUNK;
 constexpr int NS = 3;                           // ring stages
@@ -85,7 +86,7 @@ static_assert(2 * A_BYTES <= KV_BYTES, "hidden chunks live in the k|v region");
 static_assert(SMEM_BYTES <= 227 * 1024, "shared memory");
 
 struct Args {
-  const unsigned char* img;  // packed bf16 chunks, LAYER_BYTES per layer
+  const unsigned char* img;  // packed fp16 chunks, LAYER_BYTES per layer
   const float* params;       // f32 parameters (tok, pos, LayerNorms, biases, head)
   int n, L;
   HamView hv;
@@ -95,13 +96,13 @@ struct Args {
   Count n_seq;
   int P, last_only;
   float* raw;
-  __nv_bfloat16* kv_out;
+  __half* kv_out;
   // SUFFIX
   const uint64_t* xp;
   const uint32_t* perm;
   const uint32_t* offsets;
   uint32_t K;
-  const __nv_bfloat16* kv_in;
+  const __half* kv_in;
   float2* T;
   int* status;
 };
@@ -155,7 +156,7 @@ __device__ __forceinline__ LayerP staged_p(const float* s_lp) {
   return P;
 }
 
-// ---- packing: f32 parameters -> per-layer bf16 chunks --------------------------
+// ---- packing: f32 parameters -> per-layer fp16 chunks --------------------------
 __global__ void tf128_pack_kernel(const float* __restrict__ params, int n, int L, unsigned char* __restrict__ img) {
   ANQS_PDL_ENTRY();
   const uint32_t per_layer = LAYER_BYTES / 2;  // elements
@@ -187,7 +188,7 @@ __global__ void tf128_pack_kernel(const float* __restrict__ params, int n, int L
       }
     }
     *reinterpret_cast<uint16_t*>(img + size_t(l) * LAYER_BYTES + size_t(ch) * CHUNK + tc::canon_off(r, k, D)) =
-        __bfloat16_as_ushort(__float2bfloat16_rn(v));
+        __half_as_ushort(__float2half_rn(v));
   }
 }
 
@@ -230,7 +231,7 @@ struct Xch {
 };
 
 // LayerNorm (eps 1e-5, biased variance) of the row whose half-h dimensions
-// this thread holds -> bf16 into its 64 columns of the canonical K-major
+// this thread holds -> fp16 into its 64 columns of the canonical K-major
 // [128][128] operand
 __device__ __forceinline__ void ln_store(const float (&hh)[HD], const float* __restrict__ g,
                                          const float* __restrict__ b, unsigned char* sA, int h, int t, Xch& xc) {
@@ -254,18 +255,19 @@ __device__ __forceinline__ void ln_store(const float (&hh)[HD], const float* __r
     uint32_t w[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      w[e] = tc::pack_bf16x2(fmaf((hh[c0 + 2 * e] - mean) * rs, gg[2 * e], bb[2 * e]),
+      w[e] = tc::pack_f16x2(fmaf((hh[c0 + 2 * e] - mean) * rs, gg[2 * e], bb[2 * e]),
                              fmaf((hh[c0 + 2 * e + 1] - mean) * rs, gg[2 * e + 1], bb[2 * e + 1]));
     *reinterpret_cast<uint4*>(sA + tc::canon_off(t, cb + c0, D)) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
-__device__ __forceinline__ void bf16x8_to_f32(const uint4 u, float (&f)[8]) {
+__device__ __forceinline__ void f16x8_to_f32(const uint4 u, float (&f)[8]) {
   const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
   for (int e = 0; e < 4; ++e) {
-    f[2 * e] = __uint_as_float(w[e] << 16);
-    f[2 * e + 1] = __uint_as_float(w[e] & 0xffff0000u);
+    const float2 v = __half22float2(*reinterpret_cast<const __half2*>(&w[e]));
+    f[2 * e] = v.x;
+    f[2 * e + 1] = v.y;
   }
 }
 
@@ -319,7 +321,7 @@ struct Ring {
   // D (+)= A W_chunk^T over K = 128 for the next chunk of the stream; its
   // stage is released (empty) when these MMAs complete.  False on time-out.
   __device__ __forceinline__ bool gemm(uint32_t d_tmem, uint32_t a_addr, uint32_t accumulate) {
-    constexpr uint32_t IDESC = tc::idesc_bf16_f32(MT, D);
+    constexpr uint32_t IDESC = tc::idesc_f16_f32(MT, D);
     if (!pump(true)) return false;
     const uint32_t st = uint32_t(g % NS), ph = uint32_t((g / NS) & 1);
     if (!wait_bar(full + 8u * st, ph)) return false;
@@ -328,7 +330,7 @@ struct Ring {
     const uint32_t b_addr = w_addr + st * CHUNK;
 #pragma unroll
     for (uint32_t ks = 0; ks < D / 16; ++ks)
-      tc::mma_bf16(d_tmem, tc::sdesc(a_addr + ks * 256u, 128u, D * 16u), tc::sdesc(b_addr + ks * 256u, 128u, D * 16u),
+      tc::mma_f16(d_tmem, tc::sdesc(a_addr + ks * 256u, 128u, D * 16u), tc::sdesc(b_addr + ks * 256u, 128u, D * 16u),
                    IDESC, (accumulate || ks > 0) ? 1u : 0u);
     tc::mma_commit(empty + 8u * st);
     return pump(false);
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
             const float* bias = (kv == 0 ? lp.bk : lp.bv) + cb + c0;
             uint32_t w[16];
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) w[i / 2] = tc::pack_bf16x2(v[i] + bias[i], v[i + 1] + bias[i + 1]);
+            for (int i = 0; i < 32; i += 2) w[i / 2] = tc::pack_f16x2(v[i] + bias[i], v[i + 1] + bias[i + 1]);
             const int off = kv * D + cb + c0;  // element offset within the k|v row
             uint4* dst = reinterpret_cast<uint4*>(sKV + t * KV_STRIDE + off * 2);
 #pragma unroll
@@ -507,7 +509,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
         }
         csync();
         // causal attention of this row over the keys 0..pos, this half's heads
-        const __nv_bfloat16* pkv = a.kv_in ? a.kv_in + (parent * L + l) * size_t(n) * (2 * D) : nullptr;
+        const __half* pkv = a.kv_in ? a.kv_in + (parent * L + l) * size_t(n) * (2 * D) : nullptr;
 #pragma unroll 1
         for (int hq = 0; hq < HPH; ++hq) {
           const int hd = h * HPH + hq;
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
 #pragma unroll
             for (int e8 = 0; e8 < DH; e8 += 8) {
               float kf[8];
-              bf16x8_to_f32(kw[e8 / 8], kf);
+              f16x8_to_f32(kw[e8 / 8], kf);
 #pragma unroll
               for (int e = 0; e < 8; e += 2) tc::fma_f32x2(q[e8 + e], q[e8 + e + 1], kf[e], kf[e + 1], s0, s1, s0, s1);
             }
@@ -540,7 +542,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
 #pragma unroll
             for (int e8 = 0; e8 < DH; e8 += 8) {
               float vf[8];
-              bf16x8_to_f32(vw[e8 / 8], vf);
+              f16x8_to_f32(vw[e8 / 8], vf);
 #pragma unroll
               for (int e = 0; e < 8; e += 2) {
                 float p0, p1;
@@ -592,7 +594,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
           for (int e8 = 0; e8 < DH; e8 += 8) {
             uint32_t w[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) w[e] = tc::pack_bf16x2(acc[e8 + 2 * e] * inv, acc[e8 + 2 * e + 1] * inv);
+            for (int e = 0; e < 4; ++e) w[e] = tc::pack_f16x2(acc[e8 + 2 * e] * inv, acc[e8 + 2 * e + 1] * inv);
             *reinterpret_cast<uint4*>(sA + tc::canon_off(t, hd * DH + e8, D)) = make_uint4(w[0], w[1], w[2], w[3]);
           }
         }
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
                 const int i = q8 + 2 * e;
-                w[e] = tc::pack_bf16x2(fmaxf(v[i] + b1[i], 0.f), fmaxf(v[i + 1] + b1[i + 1], 0.f));
+                w[e] = tc::pack_f16x2(fmaxf(v[i] + b1[i], 0.f), fmaxf(v[i + 1] + b1[i + 1], 0.f));
               }
               *reinterpret_cast<uint4*>(sH + tc::canon_off(t, cb + c0 + q8, D)) = make_uint4(w[0], w[1], w[2], w[3]);
             }
@@ -783,7 +785,7 @@ int launch(const anqs_model* M, Args a, uint64_t max_tiles, int prof, cudaStream
   return ANQS_OK;
 }
 
-Args full_args(const uint64_t* x, Count n_seq, int P, int last_only, float* raw, __nv_bfloat16* kv_out,
+Args full_args(const uint64_t* x, Count n_seq, int P, int last_only, float* raw, __half* kv_out,
                const HamView& hv) {
   Args a{};
   a.mode = MODE_FULL;
@@ -815,14 +817,14 @@ int tf128_pack(anqs_model* M, cudaStream_t s) {
 int tf128_status_offset(const anqs_model* M) { return int(size_t(M->d.n_layers) * LAYER_BYTES); }
 
 int launch_tf128_full(const anqs_model* M, const HamView& hv, const uint64_t* x, Count n_seq, int P, int last_only,
-                      float* raw, __nv_bfloat16* kv_out, int prof, cudaStream_t s) {
+                      float* raw, __half* kv_out, int prof, cudaStream_t s) {
   Args a = full_args(x, n_seq, P, last_only, raw, kv_out, hv);
   const uint64_t S = MT / P;
   return launch(M, a, (n_seq.n + S - 1) / S, prof, s);
 }
 
 int launch_tf128_suffix(const anqs_model* M, const HamView& hv, const uint64_t* xp, const uint32_t* perm,
-                        const uint32_t* offsets, uint32_t K, const __nv_bfloat16* kv_in, float2* T, uint64_t m_max,
+                        const uint32_t* offsets, uint32_t K, const __half* kv_in, float2* T, uint64_t m_max,
                         int prof, cudaStream_t s) {
   Args a{};
   a.mode = MODE_SUFFIX;

@@ -54,6 +54,7 @@ def test_binomial_sampler_follows_born_distribution(A, n, na, nb, Ns):
     keep = prob * Ns > 5
     stat = ((full[keep] - Ns * prob[keep]) ** 2 / (Ns * prob[keep])).sum()
     assert stat < chi2.ppf(1 - 1e-6, keep.sum() - 1)
+    assert ham.status() == 0  # no binomial draw left its rejection loop or its inversion walk early
 
 
 @pytest.mark.parametrize("N", [12, 10 ** 8])
@@ -75,6 +76,7 @@ def test_binomial_node_has_multinomial_moments(A, N):
         x, c = A.sample(model, ham, N, seed=5, counter=r, binomial=True)
         counts[r, (x.cpu().numpy() & 3).astype(int)] = c.cpu().numpy()
     assert np.all(counts.sum(1) == N)
+    assert ham.status(clear=True) == 0 and ham.status() == 0
     mean, var = counts.mean(0), counts.var(0, ddof=1)
     sd = np.sqrt(N * pf * (1 - pf))
     assert np.all(np.abs(mean - N * pf) < 5 * sd / np.sqrt(R))

@@ -4,7 +4,7 @@ oracle.
 
 The bound is the one of the d = 64 form: the synthetic weights are
 bf16-representable, so only activations are rounded (every GEMM operand and
-the stored keys and values carry a relative error of at most u = 2^-9;
+the stored keys and values carry a relative error of at most u = 2^-12 (fp16 operands);
 accumulation, softmax, LayerNorm statistics and the head are f32).  Each
 slot's logits move by O(u) and log psi, a sum of n slot terms, by at most
 TOL = 4 u n.  Reusing the parent's keys and values is exact: positions <= j
@@ -21,7 +21,7 @@ from oracle.sector import molecular_isphys, sector_states
 from synthetic import flatten_tf, integrals, tf_params, workload
 
 pytestmark = pytest.mark.gpu
-U = 2.0 ** -9
+U = 2.0 ** -12  # fp16 operands: unit roundoff of an 11-bit significand
 
 
 @pytest.fixture(scope="module")

@@ -4,7 +4,7 @@ against the FP64 oracle.
 The synthetic weights are bf16-representable, so only activations are
 rounded: every GEMM operand (LayerNorm outputs, attention outputs, FFN hidden
 units) and the stored keys and values carry a relative error of at most
-u = 2^-9; accumulation, softmax, LayerNorm statistics and the head are f32.
+u = 2^-12 (fp16 operands); accumulation, softmax, LayerNorm statistics and the head are f32.
 As for the MLP form, each slot's logits move by O(u) and log psi, a sum of n
 slot terms, by at most TOL = 4 u n; a local energy moves by at most
 sum_k |H_k psi(x'_k)/psi(x)| (e^{2 TOL} - 1).  Reusing the parent's keys and
@@ -25,7 +25,7 @@ from oracle.vmc import energy_stats, local_energy
 from synthetic import flatten_tf, integrals, tf_params, workload
 
 pytestmark = pytest.mark.gpu
-U = 2.0 ** -9
+U = 2.0 ** -12  # fp16 operands: unit roundoff of an 11-bit significand
 
 
 @pytest.fixture(scope="module")
