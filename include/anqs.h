@@ -414,6 +414,14 @@ ANQS_API int anqs_batched_local_energy(anqs_batch* batch, const anqs_eloc_proble
  * ------------------------------------------------------------------------- */
 ANQS_API int anqs_grad_workspace_size(const anqs_model* model, const anqs_ham* ham, uint64_t n_x,
                              size_t* bytes);
+/* The smallest workspace anqs_grad accepts.  For the transformer it holds
+ * only each block's input rows: given less than anqs_grad_workspace_size,
+ * the adjoint recomputes a block's activations from its input just before
+ * that block's backward (one more forward pass; about a third of the memory
+ * at 4 blocks of width 128).  Equal to anqs_grad_workspace_size for the other
+ * kinds. */
+ANQS_API int anqs_grad_workspace_size_min(const anqs_model* model, const anqs_ham* ham, uint64_t n_x,
+                                          size_t* bytes);
 ANQS_API int anqs_grad(const anqs_model* model, const anqs_ham* ham, const uint64_t* x_dev,
               const uint64_t* counts_dev, uint64_t n_x, const uint64_t* n_x_dev,
               const double* eloc_re_dev, const double* eloc_im_dev, const double* stats_dev,
@@ -424,7 +432,10 @@ ANQS_API int anqs_grad(const anqs_model* model, const anqs_ham* ham, const uint6
  * + cot_phase_dev[l] arg psi(x_l)].  anqs_grad is this product with the
  * cotangents 2 (n_l/S) Re(eloc_l - E) and 2 (n_l/S) Im(eloc_l - E).
  * The transformer's adjoint keeps every forward activation of the n_x
- * determinants in the workspace (anqs_logpsi_vjp_workspace_size); the NADE's
+ * determinants in the workspace (anqs_logpsi_vjp_workspace_size), or, when
+ * given less, only the block inputs, recomputing each block's activations
+ * before its backward (the least it accepts is the size anqs_grad needs
+ * beyond its cotangents, see anqs_grad_workspace_size_min); the NADE's
  * uses it for per-CTA partial gradients when its rows span several tile
  * groups; the MLP's needs none (workspace may be null).  The table model has
  * no adjoint: ANQS_ERR_UNSUPPORTED before anything is queued. */

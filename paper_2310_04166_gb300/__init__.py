@@ -365,9 +365,12 @@ class EnergyBatch:
         return results
 
 
-def grad_workspace_bytes(model, ham, n_x) -> int:
+def grad_workspace_bytes(model, ham, n_x, least: bool = False) -> int:
+    """Workspace of anqs_grad; with least=True the smallest it accepts (the
+    transformer's adjoint then recomputes each block's activations)."""
     b = C.c_size_t()
-    check(_lib.load().anqs_grad_workspace_size(model._m, ham.handle, n_x, C.byref(b)))
+    fn = _lib.load().anqs_grad_workspace_size_min if least else _lib.load().anqs_grad_workspace_size
+    check(fn(model._m, ham.handle, n_x, C.byref(b)))
     return b.value
 
 

@@ -66,6 +66,7 @@ SIGNATURES = {
     "anqs_local_energy_workspace_size": (C.c_int, [_VP, _VP, _U64, C.POINTER(_SZ)]),
     "anqs_local_energy": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "anqs_grad_workspace_size": (C.c_int, [_VP, _VP, _U64, C.POINTER(_SZ)]),
+    "anqs_grad_workspace_size_min": (C.c_int, [_VP, _VP, _U64, C.POINTER(_SZ)]),
     "anqs_grad": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),
     "anqs_local_energy_static": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP]),
     "anqs_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int]),

@@ -138,9 +138,11 @@ static int check_adjoint(const anqs_model* M) {
   return set_error(ANQS_ERR_UNSUPPORTED, "adjoint for model kind %d not supported by this library", M->d.kind);
 }
 
-// model-specific adjoint workspace (bytes) beyond the two cotangent arrays
-static size_t vjp_ws_bytes(const anqs_model* M, uint64_t n_x) {
-  if (M->d.kind == ANQS_MODEL_TF) return tf_grad_workspace(M->tf, n_x);
+// model-specific adjoint workspace (bytes) beyond the two cotangent arrays;
+// with `least`, the smallest the adjoint accepts (the transformer then
+// recomputes each block's activations from the block's input)
+static size_t vjp_ws_bytes(const anqs_model* M, uint64_t n_x, bool least = false) {
+  if (M->d.kind == ANQS_MODEL_TF) return tf_grad_workspace(M->tf, n_x, least);
   if (M->d.kind == ANQS_MODEL_NADE) return nade_grad_partial_floats(M->nade, M->n_params, n_x) * sizeof(float);
   return 0;
 }
@@ -858,15 +860,26 @@ int anqs_batched_local_energy(anqs_batch* b, const anqs_eloc_problem* q, int n, 
   return r;
 }
 
-int anqs_grad_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_x, size_t* bytes) {
-  ANQS_TRY(check_pair(M, H));
-  if (!bytes) return set_error(ANQS_ERR_ARG, "null output");
+static size_t grad_ws_bytes(const anqs_model* M, uint64_t n_x, bool least) {
   Arena A(nullptr, 0);
   A.take<float>(n_x);
   A.take<float>(n_x);
   if (M->d.kind == ANQS_MODEL_MLP) A.take<float>(mlp_fp32_grad_partial_floats(M->mlp, n_x));
-  A.take<char>(vjp_ws_bytes(M, n_x));
-  *bytes = A.off;
+  A.take<char>(vjp_ws_bytes(M, n_x, least));
+  return A.off;
+}
+
+int anqs_grad_workspace_size(const anqs_model* M, const anqs_ham* H, uint64_t n_x, size_t* bytes) {
+  ANQS_TRY(check_pair(M, H));
+  if (!bytes) return set_error(ANQS_ERR_ARG, "null output");
+  *bytes = grad_ws_bytes(M, n_x, false);
+  return ANQS_OK;
+}
+
+int anqs_grad_workspace_size_min(const anqs_model* M, const anqs_ham* H, uint64_t n_x, size_t* bytes) {
+  ANQS_TRY(check_pair(M, H));
+  if (!bytes) return set_error(ANQS_ERR_ARG, "null output");
+  *bytes = grad_ws_bytes(M, n_x, true);
   return ANQS_OK;
 }
 
@@ -881,8 +894,14 @@ int anqs_grad(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const u
   float* cl = A.take<float>(n_x);
   float* cp = A.take<float>(n_x);
   float* part = (M->d.kind == ANQS_MODEL_MLP) ? A.take<float>(mlp_fp32_grad_partial_floats(M->mlp, n_x)) : nullptr;
-  const size_t tfb = vjp_ws_bytes(M, n_x);
+  size_t tfb = vjp_ws_bytes(M, n_x);
+  const size_t off0 = A.off;
   void* tfws = tfb ? A.take<char>(tfb) : nullptr;
+  if (!A.fits() && tfb) {  // too small for every activation: the recomputing adjoint
+    A.off = off0;
+    tfb = vjp_ws_bytes(M, n_x, true);
+    tfws = A.take<char>(tfb);
+  }
   if (!A.fits() || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", A.off);
   cudaStream_t s = (cudaStream_t)stream;
   if (!part) ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));
@@ -909,7 +928,7 @@ int anqs_logpsi_vjp(const anqs_model* M, const anqs_ham* H, const uint64_t* x, u
   if (!grad) return set_error(ANQS_ERR_ARG, "null gradient output");
   if (n_x && (!x || !cl || !cp)) return set_error(ANQS_ERR_ARG, "null array argument");
   ANQS_TRY(check_adjoint(M));
-  const size_t need = vjp_ws_bytes(M, n_x);
+  const size_t need = vjp_ws_bytes(M, n_x, true);  // with less than vjp_ws_bytes(M, n_x) the transformer recomputes
   if (ws_bytes < need || (need && !ws)) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
   cudaStream_t s = (cudaStream_t)stream;
   ANQS_CUDA(cudaMemsetAsync(grad, 0, M->n_params * sizeof(float), s));

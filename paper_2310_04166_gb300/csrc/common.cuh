@@ -301,7 +301,7 @@ int launch_tf_fp32_logpsi(const TfView& m, const HamView& hv, const uint64_t* x,
                           cudaStream_t s);
 int launch_tf_fp32_slot_logits(const TfView& m, int p, const uint64_t* pre, const uint64_t* nr, uint64_t max_rows,
                                float* out, cudaStream_t s);
-size_t tf_grad_workspace(const TfView& m, uint64_t n_x);
+size_t tf_grad_workspace(const TfView& m, uint64_t n_x, bool recompute);  // recompute: block inputs only
 int launch_tf_fp32_grad(const TfView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,
                         const float* cp, float* grad, void* ws, size_t ws_bytes, cudaStream_t s);
 int launch_table_logpsi(const anqs_model* md, const HamView& hv, const uint64_t* x, Count n_x,

@@ -5,7 +5,9 @@
 //
 // The unique samples are few (thousands) while each has n positions, so the
 // adjoint runs as batched passes over all R = n_x * n rows (sample,
-// position) with every activation of the forward stored in the workspace:
+// position) with every activation of the forward stored in the workspace
+// (or, when the workspace is too small for that, only the block inputs, each
+// block's activations being recomputed from its input before its backward):
 // embedding; per block LN1, q|k|v, causal attention (probabilities kept),
 // output projection + residual, LN2, FFN (pre-activation kept) + residual;
 // final LN and head.  The backward walks the same steps in reverse.  Matrix
@@ -434,10 +436,14 @@ struct Acts {
   float *Xhf, *Af, *RSf, *out8, *dout8, *dH, *dA, *dHm, *dF, *dQ, *dK, *dV, *dO;
 };
 
-size_t plan(const TfView& m, uint64_t nx, Arena& Ar, Acts& a) {
+// Full storage keeps every block's activations; with `ckpt` (activation
+// recomputation) only the block inputs H[l] are kept and one set of block
+// activations is shared by all blocks: the backward recomputes block l's
+// forward from H[l] just before its own backward.
+size_t plan(const TfView& m, uint64_t nx, Arena& Ar, Acts& a, bool ckpt = false) {
   const uint64_t R = nx * m.n, D = m.d;
   for (int l = 0; l <= m.L; ++l) a.H[l] = Ar.take<float>(R * D);
-  for (int l = 0; l < m.L; ++l) {
+  for (int l = 0; l < (ckpt ? 1 : m.L); ++l) {
     a.Xh1[l] = Ar.take<float>(R * D);
     a.A1[l] = Ar.take<float>(R * D);
     a.RS1[l] = Ar.take<float>(R);
@@ -451,6 +457,11 @@ size_t plan(const TfView& m, uint64_t nx, Arena& Ar, Acts& a) {
     a.A2[l] = Ar.take<float>(R * D);
     a.RS2[l] = Ar.take<float>(R);
     a.F[l] = Ar.take<float>(R * 4 * D);
+  }
+  for (int l = 1; ckpt && l < m.L; ++l) {
+    a.Xh1[l] = a.Xh1[0], a.A1[l] = a.A1[0], a.RS1[l] = a.RS1[0], a.Q[l] = a.Q[0], a.K[l] = a.K[0];
+    a.V[l] = a.V[0], a.P[l] = a.P[0], a.O[l] = a.O[0], a.Hm[l] = a.Hm[0], a.Xh2[l] = a.Xh2[0];
+    a.A2[l] = a.A2[0], a.RS2[l] = a.RS2[0], a.F[l] = a.F[0];
   }
   a.Xhf = Ar.take<float>(R * D);
   a.Af = Ar.take<float>(R * D);
@@ -519,7 +530,15 @@ int run(const TfView& m, const HamView& hv, const uint64_t* x, Count nx, const f
   Arena Ar(ws, ws_bytes);
   Acts a;
   plan(m, nx.n, Ar, a);
-  if (!Ar.fits()) return set_error(ANQS_ERR_CAPACITY, "transformer adjoint workspace needs %zu bytes", Ar.off);
+  bool ckpt = false;
+  if (!Ar.fits()) {  // too little workspace for every activation: recompute each block's
+    Arena Ac(ws, ws_bytes);
+    plan(m, nx.n, Ac, a, true);
+    if (!Ac.fits())
+      return set_error(ANQS_ERR_CAPACITY, "transformer adjoint workspace needs %zu bytes (%zu with recomputation)",
+                       Ar.off, Ac.off);
+    ckpt = true;
+  }
   const int n = m.n, L = m.L, H = m.H;
   const Count rows = scaled(nx, n);
   const uint64_t R = rows.n;
@@ -528,7 +547,9 @@ int run(const TfView& m, const HamView& hv, const uint64_t* x, Count nx, const f
   ProfScope ps(PROF_TF_GRAD, s);
   const unsigned eg = grid_for(R * D, 256, 152 * 16), lg = grid_for(R * 32, 256, 152 * 16);
   ANQS_CUDA_LAUNCH("tf embed_kernel", launch_k(embed_kernel, dim3(eg), dim3(256), 0, s, m, x, rows, a.H[0]));
-  for (int l = 0; l < L; ++l) {
+  // forward of block l from H[l]: its activations and H[l + 1] (deterministic,
+  // so a recomputation reproduces them bit for bit)
+  auto fwd_block = [&](int l) -> int {
     const LayerOff o = layer_off(m, l);
     ANQS_CUDA_LAUNCH("tf ln_fwd_kernel", launch_k(ln_fwd_kernel<D>, dim3(lg), dim3(256), 0, s, a.H[l], P + o.ln1_g,
                                                   P + o.ln1_b, a.Xh1[l], a.A1[l], a.RS1[l], rows));
@@ -565,7 +586,9 @@ int run(const TfView& m, const HamView& hv, const uint64_t* x, Count nx, const f
       g.ldcin = D;
       ANQS_TRY(gemm_nt(g, R, 4 * D, s));
     }
-  }
+    return ANQS_OK;
+  };
+  for (int l = 0; l < L; ++l) ANQS_TRY(fwd_block(l));
   const size_t tail = 5 * size_t(D) + size_t(n) * D + size_t(L) * (12 * size_t(D) * D + 13 * size_t(D));
   const size_t lnf_g = tail, lnf_b = tail + D, head_w = tail + 2 * D, head_b = tail + 10 * D;
   ANQS_CUDA_LAUNCH("tf ln_fwd_kernel", launch_k(ln_fwd_kernel<D>, dim3(lg), dim3(256), 0, s, a.H[L], P + lnf_g,
@@ -600,6 +623,7 @@ int run(const TfView& m, const HamView& hv, const uint64_t* x, Count nx, const f
                             (const float*)nullptr, a.dH, grad + lnf_g, grad + lnf_b, rows));
   for (int l = L - 1; l >= 0; --l) {
     const LayerOff o = layer_off(m, l);
+    if (ckpt && l + 1 < L) ANQS_TRY(fwd_block(l));  // the shared activations hold block L-1's after the forward
     ANQS_TRY(wgrad(a.dH, D, a.F[l], 4 * D, D, 4 * D, grad + o.w2, 1));
     ANQS_TRY(colsum(a.dH, D, grad + o.b2));
     {
@@ -649,10 +673,10 @@ int run(const TfView& m, const HamView& hv, const uint64_t* x, Count nx, const f
 
 }  // namespace
 
-size_t tf_grad_workspace(const TfView& m, uint64_t n_x) {
+size_t tf_grad_workspace(const TfView& m, uint64_t n_x, bool recompute) {
   Arena Ar(nullptr, 0);
   Acts a;
-  return plan(m, n_x, Ar, a);
+  return plan(m, n_x, Ar, a, recompute);
 }
 
 int launch_tf_fp32_grad(const TfView& m, const HamView& hv, const uint64_t* x, Count n_x, const float* cl,

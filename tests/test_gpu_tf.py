@@ -273,3 +273,31 @@ def test_tf_local_energy_fp32_large_shape(A):
     assert ((e.imag - eim).abs() <= bound).all()
     wts = c.double() / c.double().sum()
     assert abs(float((wts * ere).sum()) - float(stats[0])) <= 1e-12 * float(ere.abs().max())
+
+
+@pytest.mark.parametrize("name,n_samples", [("n2", 20_000), ("large", 2000)])
+def test_tf_grad_with_recomputation_equals_full_storage(A, name, n_samples):
+    """The adjoint given only the smallest workspace (block inputs stored,
+    each block's activations recomputed before its backward) against the one
+    that stores every activation: the recomputed forward is bit-identical, so
+    the gradients differ only by the summation order of the split-K weight
+    products (float32 atomics)."""
+    w = workload(name, bias_std=0.2)
+    ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    model = A.Model.transformer(w["n"], w["d_model"], w["n_heads"], w["n_layers"],
+                                torch.tensor(w["params"], device="cuda"))
+    x, c = A.sample(model, ham, n_samples, seed=13)
+    if name == "large":
+        x, c = x[:16].contiguous(), c[:16].contiguous()
+    ere, eim, stats = A.local_energy(model, ham, x, c)
+    full = A.grad_workspace_bytes(model, ham, x.numel())
+    least = A.grad_workspace_bytes(model, ham, x.numel(), least=True)
+    assert least < (full / 2 if name == "large" else full)  # 4 blocks of width 128: under half
+    g_full = A.grad(model, ham, x, c, ere, eim, stats, workspace=A._ws(full, "cuda"))
+    g_rec = A.grad(model, ham, x, c, ere, eim, stats, workspace=A._ws(least, "cuda"))
+    torch.cuda.synchronize()
+    assert torch.isfinite(g_rec).all()
+    rel = float((g_rec - g_full).norm() / g_full.norm())
+    assert rel < 1e-5, rel
+    with pytest.raises(Exception):  # below the least size: capacity error before anything is queued
+        A.grad(model, ham, x, c, ere, eim, stats, workspace=A._ws(least - 4096, "cuda"))
