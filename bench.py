@@ -244,7 +244,8 @@ def _cpu_baseline(w, sets=None, seconds=10.0, n_max=100000):
             notes.append(f"{m} of the {len(xs)} unique samples of the {form} form's last step")
             if m == len(xs):
                 ref = energy_stats(np.concatenate(es), st["cnt"])
-                delta[form] = {"E_oracle_ha": float(ref[0]), "abs_dE_ha": abs(float(st["stats"][0]) - ref[0])}
+                delta[form] = {"E_oracle_ha": float(ref[0]), "abs_dE_ha": abs(float(st["stats"][0]) - ref[0]),
+                               "_e_ref": np.concatenate(es)}
             else:
                 delta[form] = {"abs_dE_ha": None, "note": "oracle did not finish the set in the time bound"}
         return {"value": done / busy, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
@@ -472,32 +473,59 @@ def _run_form(A, lib, args, w, form, ham, params, dev, rank, dist, stream_clocks
             "clocks": clk.summary()}
 
 
-def _oracle_subset(w, last, m=48, seed=7):
+def _oracle_model(w):
+    from oracle.anqs import MLPAnsatz, TFAnsatz
+    from oracle.sector import molecular_isphys
+    ip = molecular_isphys(w["n"], w["n_alpha"], w["n_beta"])
+    om = MLPAnsatz(w["params_struct"], w["n"]) if w["kind"] == "mlp" else TFAnsatz(w["params_struct"], w["n"],
+                                                                                    w["n_heads"])
+    return om, ip
+
+
+def _grad_vs_oracle(A, model, ham, w, x, cnt, e_ref):
+    """Relative L2 distance between the form's VMC gradient (Eq. grad_def) on
+    the samples x with counts cnt (its own local energies and statistics, all
+    through the library) and the FP64 oracle's gradient on the same samples
+    from the oracle's local energies e_ref."""
+    from oracle.vmc import energy_stats, gradient
+    om, ip = _oracle_model(w)
+    c = torch.as_tensor(np.asarray(cnt, dtype=np.int64), device=x.device)
+    ere, eim, st = A.local_energy(model, ham, x, c)
+    g = A.grad(model, ham, x, c, ere, eim, st).cpu().numpy().astype(np.float64)
+    xs = x.cpu().numpy().astype(np.uint64)
+    s_ref = energy_stats(e_ref, cnt)
+    g_ref = np.concatenate([t.reshape(-1).numpy() for t in gradient(om, ip, xs, cnt, e_ref, s_ref)])
+    return float(np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref))
+
+
+def _oracle_subset(w, last, m=48, seed=7, A=None, model=None, ham=None):
     """|E_gpu - E_oracle| estimated from m samples of the step's unique set,
     drawn with probability proportional to their counts: the mean of
     E_loc,gpu - E_loc,oracle over the draws is an unbiased estimate of the
     count-weighted energy difference (its standard error beside it).  For
     sample sets too large for the FP64 oracle to evaluate whole within the
     bench's time bound."""
-    from oracle.anqs import MLPAnsatz, TFAnsatz
     from oracle.hamiltonian import Hamiltonian as OHam
-    from oracle.sector import molecular_isphys
     from oracle.vmc import local_energy
     oham = OHam(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
-    ip = molecular_isphys(w["n"], w["n_alpha"], w["n_beta"])
-    om = MLPAnsatz(w["params_struct"], w["n"]) if w["kind"] == "mlp" else TFAnsatz(w["params_struct"], w["n"],
-                                                                                    w["n_heads"])
+    om, ip = _oracle_model(w)
     xs = last["x"].cpu().numpy().astype(np.uint64)
     cnt = np.asarray(last["cnt"], dtype=np.float64)
     rng = np.random.default_rng(seed)
     pick = rng.choice(len(xs), size=min(m, len(xs)), replace=True, p=cnt / cnt.sum())
     uniq, inv = np.unique(pick, return_inverse=True)
     t0 = time.perf_counter()
-    e_ref = np.concatenate([local_energy(om, ip, oham, xs[uniq[a:a + 8]]) for a in range(0, len(uniq), 8)]).real
-    d = (last["ere"][uniq] - e_ref)[inv]
-    return {"abs_dE_ha_estimate": abs(float(d.mean())), "stderr_ha": float(d.std(ddof=1) / np.sqrt(len(d))),
-            "max_abs_dEloc_ha": float(np.abs(d).max()), "draws": int(len(d)), "oracle_s": time.perf_counter() - t0,
-            "how": f"{len(d)} draws (proportional to counts) of the {len(xs)} unique samples, FP64 oracle E_loc"}
+    e_c = np.concatenate([local_energy(om, ip, oham, xs[uniq[a:a + 8]]) for a in range(0, len(uniq), 8)])
+    d = (last["ere"][uniq] - e_c.real)[inv]
+    out = {"abs_dE_ha_estimate": abs(float(d.mean())), "stderr_ha": float(d.std(ddof=1) / np.sqrt(len(d))),
+           "max_abs_dEloc_ha": float(np.abs(d).max()), "draws": int(len(d)), "oracle_s": time.perf_counter() - t0,
+           "how": f"{len(d)} draws (proportional to counts) of the {len(xs)} unique samples, FP64 oracle E_loc"}
+    if A is not None:  # the gradient restricted to the drawn samples (their counts in the step's set)
+        sel = torch.as_tensor(uniq, device=last["x"].device)
+        out["grad_rel_l2"] = _grad_vs_oracle(A, model, ham, w, last["x"][sel].contiguous(), cnt[uniq], e_c)
+        out["grad_how"] = (f"gradient on the {len(uniq)} distinct drawn samples with their step counts: library "
+                           "(own local energies) against the FP64 oracle")
+    return out
 
 
 def _sub_workload(A, lib, args, name, dev, rank, dist, steps):
@@ -509,7 +537,7 @@ def _sub_workload(A, lib, args, name, dev, rank, dist, steps):
     from synthetic import workload
     w = workload(name)
     a = copy.copy(args)
-    a.steps, a.n_samples, a.binomial = steps, 0, False
+    a.steps, a.n_samples, a.binomial, a.workload = steps, 0, False, name
     ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
     params = torch.tensor(w["params"], device=dev)
     out = {"config": _config(w, a)["workload"], "steps": steps}
@@ -524,7 +552,8 @@ def _sub_workload(A, lib, args, name, dev, rank, dist, steps):
             f["roofline"] = {k: roof[k] for k in ("kernel", "bound", "achieved", "peak", "unit", "frac",
                                                   "avg_launch_us")}
         if not args.no_cpu_baseline:  # more draws for the 16-bit form, whose per-sample deviations are larger
-            f["oracle"] = _oracle_subset(w, r["last"], m=256 if form == "bf16" else 64)
+            f["oracle"] = _oracle_subset(w, r["last"], m=256 if form == "bf16" else 64, A=A, model=r["model"],
+                                         ham=ham)
         out[form] = f
         del r
         torch.cuda.empty_cache()
@@ -599,7 +628,7 @@ def _large(args, dev):
     r = res["bf16"]
     print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["steps"],
                       "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
-                      "scaling": "weak", "vs_baseline": None, "dtype": "bf16 GEMM / f32 heads / f64 E_loc",
+                      "scaling": "weak", "vs_baseline": None, "dtype": "fp16-operand tcgen05 GEMM (kind::f16, f32 accumulate) / f32 heads / f64 E_loc",
                       "data": "synthetic",
                       "config": {"workload": f"large: n_orb={w['n']} N_a={w['n_alpha']} N_b={w['n_beta']}, "
                                              f"transformer d{w['d_model']} h{w['n_heads']} L{w['n_layers']}, "
@@ -673,7 +702,7 @@ def _batch32(args, dev):
     res["fp32"] = timed(plain, probs, args.steps)
     line = {"metric": METRIC, "value": res["bf16"][0], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": res["bf16"][1], "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16 GEMM / f32 heads / f64 E_loc", "data": "synthetic",
+            "vs_baseline": None, "dtype": "fp16-operand tcgen05 GEMM (kind::f16, f32 accumulate) / f32 heads / f64 E_loc", "data": "synthetic",
             "config": {"workload": "batch32: 32 problems, seeds 100..131, n in [6, 14], N_a = N_b in [1, n-1], "
                                    "2n Cholesky vectors, per-slot MLP 3x128 each, N_s = 1e5 each",
                        "l2": "flushed between timed steps (256 MiB write)",
@@ -772,13 +801,18 @@ def main():
                  "n_unique_per_step": v["n_unique"], "E_ha": float(v["last"]["stats"][0])} for f, v in runs.items()}
     if cpu:
         for f, d in cpu.pop("delta_E", {}).items():
+            e_ref = d.pop("_e_ref", None)
             forms[f].update(d)
+            if e_ref is not None:  # the whole set evaluated by the oracle: the gradient on it too
+                v = runs[f]
+                forms[f]["grad_rel_l2"] = _grad_vs_oracle(A, v["model"], ham, w, v["last"]["x"], v["last"]["cnt"],
+                                                          e_ref)
     if "fp32" in runs and "bf16" in runs:
         forms["bf16_over_fp32"] = runs["bf16"]["value"] / runs["fp32"]["value"]
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16 GEMM / f32 heads / f64 E_loc" if form == "bf16" else "f32 network / f64 E_loc",
+            "dtype": "fp16-operand tcgen05 GEMM (kind::f16, f32 accumulate) / f32 heads / f64 E_loc" if form == "bf16" else "f32 network / f64 E_loc",
             "data": "synthetic", "config": _config(w, args), "n_unique_per_step": r["n_unique"],
             "e2e": r["e2e"], "forms": forms,
             "gpu_launches": r["launches_per_step"] * args.steps,

@@ -93,14 +93,17 @@ enum { ANQS_MODEL_MLP = 0, ANQS_MODEL_TF = 1, ANQS_MODEL_TABLE = 2, ANQS_MODEL_N
  * FP32: plain SIMT float32 kernels, every configuration evaluated over all
  *       slots (no prefix reuse), except the NADE, whose local energy reuses
  *       the parent's slots for its connected determinants.
- * BF16: tensor-core (tcgen05, TMEM accumulators) 16-bit GEMMs with float32
- *       accumulation, float32 activations/softmax/phase heads, and reuse of
- *       the parent determinant's slots for its connected determinants.  The
- *       MLP's operands are bfloat16 (its layer-1 weights as two bf16 parts);
- *       the transformer's operands and stored keys/values are fp16 (the same
- *       MMA instruction and rate, three more significand bits for its
- *       activations; conversions saturate at +-65504).  MLP width 64 or 128,
- *       transformer d_model 64 or 128 with head width 16 or 32. */
+ * BF16: the 16-bit form: tensor-core (tcgen05, TMEM accumulators) 16-bit
+ *       GEMMs with float32 accumulation, float32 activations/softmax/phase
+ *       heads, and reuse of the parent determinant's slots for its connected
+ *       determinants.  GEMM operands are fp16, the same MMA instruction and
+ *       rate as bfloat16 with three more significand bits (the bf16 rounding
+ *       of activations put the gradient's error above 1e-3 relative L2):
+ *       the MLP's weights (layer 1 as two fp16 parts) and tanh activations,
+ *       the transformer's activations and stored keys/values (its weights are
+ *       bf16-representable, hence exact in fp16).  Conversions saturate at
+ *       +-65504.  MLP width 64 or 128, transformer d_model 64 or 128 with
+ *       head width 16 or 32. */
 enum { ANQS_FORM_FP32 = 0, ANQS_FORM_BF16 = 1 };
 
 typedef struct anqs_ham anqs_ham;

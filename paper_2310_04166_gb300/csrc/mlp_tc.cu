@@ -1,14 +1,21 @@
-// BF16 tensor-core form of the per-slot MLP ansatz (tcgen05 MMA, TMEM
+// 16-bit tensor-core form of the per-slot MLP ansatz (tcgen05 MMA, TMEM
 // accumulators, bulk-copied weight images), with reuse of the parent
 // determinant's slots for its connected determinants.
+//
+// Operands are fp16 (kind::f16, the rate of bf16): the weights are rounded to
+// an 11-bit significand instead of 8, and so are the hidden activations (tanh
+// values in [-1, 1], where fp16's narrower exponent range costs nothing).
+// With bf16 operands the per-sample local-energy deviation reached 2e-2 Ha on
+// the 7-orbital workload and the VMC gradient's relative L2 error 1.6e-3;
+// fp16 operands make both about eight times smaller.
 //
 // A CTA of 128 threads owns a tile of 128 rows (one row per thread and per
 // TMEM lane).  For each slot p the CTA bulk-copies slot p's packed weight
 // image into shared memory, writes the one-hot input of v_<p as the A
 // operand, and runs the layers as M=128 x N=W x K GEMMs on the tensor cores
-// (bf16 operands, f32 accumulation in TMEM).  Epilogues read the
+// (fp16 operands, f32 accumulation in TMEM).  Epilogues read the
 // accumulator from TMEM, add the bias and apply tanh in f32, and write the
-// bf16 activations back as the next A operand; the last hidden layer feeds
+// fp16 activations back as the next A operand; the last hidden layer feeds
 // the f32 head (8 outputs) on the CUDA cores, then the masked log-softmax
 // (Appendix B.1 f3 with MU masking, Sec. III.C) in f32.
 //
@@ -23,7 +30,7 @@
 //           one slot for the whole launch.
 //   LOGPSI  rows = arbitrary determinants, all slots, log psi only.
 //   LOGITS  rows = sampler frontier prefixes, one slot, the 8 raw outputs.
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cmath>
@@ -47,10 +54,10 @@ enum { ST_TIMEOUT = 1 };
 // Layout of one slot's packed image (byte offsets from the image base).
 struct SlotLayout {
   uint32_t k1;      // padded input width of layer 1 (multiple of 16, 0 for slot 0)
-  uint32_t w1;      // layer-1 matrix [W][k1] bf16, canonical K-major
-  uint32_t w1lo;    // its rounding residual W1 - bf16(W1), same layout, or 0 bytes when the split is
-                    // off (the one-hot input is exact, so hi + lo makes layer 1 exact to 2^-16 relative)
-  uint32_t wk;      // hidden matrices [L-1][W][W] bf16, canonical, each W*W*2 bytes
+  uint32_t w1;      // layer-1 matrix [W][k1] fp16, canonical K-major
+  uint32_t w1lo;    // its rounding residual W1 - fp16(W1), same layout, or 0 bytes when the split is
+                    // off (the one-hot input is exact, so hi + lo makes layer 1 exact to about 2^-22 relative)
+  uint32_t wk;      // hidden matrices [L-1][W][W] fp16, canonical, each W*W*2 bytes
   uint32_t bias;    // [L][W] f32
   uint32_t head;    // head [W][8] f32 (transposed: the 8 outputs of input k are adjacent)
   uint32_t hbias;   // [8] f32
@@ -92,7 +99,11 @@ struct TcView {
   int* status;
 };
 
-// ---- packing: f32 parameters -> per-slot bf16/f32 images --------------------
+// ---- packing: f32 parameters -> per-slot fp16/f32 images --------------------
+
+// f32 -> fp16 bits, round to nearest, saturating at the largest finite value
+__device__ __forceinline__ uint16_t f16_bits(float v) { return uint16_t(tc::pack_f16x2(v, 0.f) & 0xFFFFu); }
+__device__ __forceinline__ float f16_value(uint16_t b) { return __half2float(__ushort_as_half(b)); }
 __global__ void pack_kernel(MlpView m, TcView tv, unsigned char* img) {
   ANQS_PDL_ENTRY();
   const int p = blockIdx.y;
@@ -111,16 +122,14 @@ __global__ void pack_kernel(MlpView m, TcView tv, unsigned char* img) {
     if (t < n1) {
       uint32_t r = t / S.k1, k = t % S.k1;
       float v = (k < 4u * p) ? W1[size_t(r) * 4 * p + k] : 0.f;
-      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      *reinterpret_cast<uint16_t*>(base + S.w1 + tc::canon_off(r, k, S.k1)) = __bfloat16_as_ushort(hi);
+      const uint16_t hi = f16_bits(v);
+      *reinterpret_cast<uint16_t*>(base + S.w1 + tc::canon_off(r, k, S.k1)) = hi;
       if (tv.lo)
-        *reinterpret_cast<uint16_t*>(base + S.w1lo + tc::canon_off(r, k, S.k1)) =
-            __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(hi)));
+        *reinterpret_cast<uint16_t*>(base + S.w1lo + tc::canon_off(r, k, S.k1)) = f16_bits(v - f16_value(hi));
     } else if (t < n1 + nk) {
       uint32_t u = t - n1, l = u / (W * W), e = u % (W * W), r = e / W, k = e % W;
       float v = Wk[size_t(l) * (size_t(W) * W + W) + size_t(r) * W + k];
-      *reinterpret_cast<uint16_t*>(base + S.wk + l * W * W * 2u + tc::canon_off(r, k, W)) =
-          __bfloat16_as_ushort(__float2bfloat16_rn(v));
+      *reinterpret_cast<uint16_t*>(base + S.wk + l * W * W * 2u + tc::canon_off(r, k, W)) = f16_bits(v);
     } else if (t < n1 + nk + uint32_t(L) * W) {
       uint32_t u = t - n1 - nk, l = u / W, o = u % W;
       const float* bl = (l == 0) ? b1 : (Wk + size_t(l - 1) * (size_t(W) * W + W) + size_t(W) * W);
@@ -189,7 +198,7 @@ __device__ __forceinline__ bool wg_all(int wg, bool v) {
 template <int W>
 __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const SlotLayout& S, uint32_t img_addr,
                           const unsigned char* img, float (&out)[8]) {
-  constexpr uint32_t IDESC = tc::idesc_bf16_f32(MT, W);
+  constexpr uint32_t IDESC = tc::idesc_f16_f32(MT, W);
   const int L = c.tv->L;
   // layer-1 input: one-hot of v_<p (K = k1 columns)
   for (uint32_t k = 0; k < S.k1; k += 8) {
@@ -198,8 +207,8 @@ __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const
     for (int e = 0; e < 4; ++e) {
       uint32_t lo = 0, hi = 0;
       const uint32_t k0 = k + 2 * e, k1 = k0 + 1;
-      if (k0 < 4u * p && ((x >> (2 * (k0 >> 2))) & 3ull) == (k0 & 3u)) lo = 0x3F80u;
-      if (k1 < 4u * p && ((x >> (2 * (k1 >> 2))) & 3ull) == (k1 & 3u)) hi = 0x3F80u;
+      if (k0 < 4u * p && ((x >> (2 * (k0 >> 2))) & 3ull) == (k0 & 3u)) lo = 0x3C00u;  // fp16 1.0
+      if (k1 < 4u * p && ((x >> (2 * (k1 >> 2))) & 3ull) == (k1 & 3u)) hi = 0x3C00u;
       w4[e] = lo | (hi << 16);
     }
     *reinterpret_cast<uint4*>(c.s_a + tc::canon_off(c.t, k, S.k1)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
@@ -222,13 +231,13 @@ __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const
         const uint32_t b_addr = img_addr + (layer == 0 ? S.w1 : S.wk + uint32_t(layer - 1) * W * W * 2u);
 #pragma unroll 1
         for (uint32_t ks = 0; ks < K / 16; ++ks)
-          tc::mma_bf16(c.tmem, tc::sdesc(c.a_addr + ks * 256u, 128u, K * 16u),
-                       tc::sdesc(b_addr + ks * 256u, 128u, K * 16u), IDESC, ks > 0 ? 1u : 0u);
-        if (layer == 0 && c.tv->lo) {  // + one-hot x (W1 - bf16(W1))
+          tc::mma_f16(c.tmem, tc::sdesc(c.a_addr + ks * 256u, 128u, K * 16u),
+                      tc::sdesc(b_addr + ks * 256u, 128u, K * 16u), IDESC, ks > 0 ? 1u : 0u);
+        if (layer == 0 && c.tv->lo) {  // + one-hot x (W1 - fp16(W1))
 #pragma unroll 1
           for (uint32_t ks = 0; ks < K / 16; ++ks)
-            tc::mma_bf16(c.tmem, tc::sdesc(c.a_addr + ks * 256u, 128u, K * 16u),
-                         tc::sdesc(img_addr + S.w1lo + ks * 256u, 128u, K * 16u), IDESC, 1u);
+            tc::mma_f16(c.tmem, tc::sdesc(c.a_addr + ks * 256u, 128u, K * 16u),
+                        tc::sdesc(img_addr + S.w1lo + ks * 256u, 128u, K * 16u), IDESC, 1u);
         }
         tc::mma_commit(c.bar_m);
       }
@@ -254,14 +263,14 @@ __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const
         tc::add_f32x2(v[i], v[i + 1], bb.x, bb.y, v[i], v[i + 1]);
       }
       if (!last) {
-        // next GEMM operand: f32 tanh, rounded to bf16 (a bf16x2 tanh would add
-        // its own approximation error to the bf16 rounding)
+        // next GEMM operand: f32 tanh, rounded to fp16 (a half-precision tanh
+        // would add its own approximation error to the rounding)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           uint32_t u[4];
 #pragma unroll
           for (int e = 0; e < 4; ++e)
-            u[e] = tc::pack_bf16x2(tc::tanh_fast(v[8 * q + 2 * e]), tc::tanh_fast(v[8 * q + 2 * e + 1]));
+            u[e] = tc::pack_f16x2(tc::tanh_fast(v[8 * q + 2 * e]), tc::tanh_fast(v[8 * q + 2 * e + 1]));
           *reinterpret_cast<uint4*>(c.s_a + tc::canon_off(c.t, c0 + 8 * q, W)) = make_uint4(u[0], u[1], u[2], u[3]);
         }
       } else {

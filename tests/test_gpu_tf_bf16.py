@@ -4,9 +4,9 @@ against the FP64 oracle.
 The synthetic weights are bf16-representable, so only activations are
 rounded: every GEMM operand (LayerNorm outputs, attention outputs, FFN hidden
 units) and the stored keys and values carry a relative error of at most
-u = 2^-12 (fp16 operands); accumulation, softmax, LayerNorm statistics and the head are f32.
+u = 2^-11 (fp16 operands); accumulation, softmax, LayerNorm statistics and the head are f32.
 As for the MLP form, each slot's logits move by O(u) and log psi, a sum of n
-slot terms, by at most TOL = 4 u n; a local energy moves by at most
+slot terms, by at most TOL = 2 u n; a local energy moves by at most
 sum_k |H_k psi(x'_k)/psi(x)| (e^{2 TOL} - 1).  Reusing the parent's keys and
 values is exact: a connected determinant's positions <= j see bit-identical
 rows in the parent's tile, so E_loc with reuse equals E_loc assembled from
@@ -25,7 +25,7 @@ from oracle.vmc import energy_stats, local_energy
 from synthetic import flatten_tf, integrals, tf_params, workload
 
 pytestmark = pytest.mark.gpu
-U = 2.0 ** -12  # fp16 operands: unit roundoff of an 11-bit significand
+U = 2.0 ** -11  # fp16 operands: unit roundoff of an 11-bit significand
 
 
 @pytest.fixture(scope="module")
@@ -64,7 +64,7 @@ def test_tf_bf16_logpsi_within_roundoff_bound(A, n, na, nb, H, L):
     st = np.array(sector_states(n, na, nb), dtype=np.uint64)
     la, ph = A.logpsi(model, ham, _dev(st))
     rla, rph = log_psi(om, ip, st)
-    tol = 4 * U * n
+    tol = 2 * U * n
     assert np.abs(la.cpu().numpy() - rla.numpy()).max() < tol
     assert np.abs(ph.cpu().numpy() - rph.numpy()).max() < tol
     # the masked BF16 ansatz is still normalised on the sector (f32 softmax)
@@ -97,7 +97,7 @@ def test_tf_bf16_local_energy_against_oracle(A):
     ox, on = ox[keep], on[keep]
     ere, eim, stats = A.local_energy(model, ham, _dev(ox), _dev(on))
     e_ref = local_energy(om, ip, oham, ox)
-    tol = 4 * U * w["n"]
+    tol = 2 * U * w["n"]
     la, _ = log_psi(om, ip, ox)
     lists = [oham.connected(int(v)) for v in ox]
     K = len(lists[0])
