@@ -378,9 +378,34 @@ ANQS_API int anqs_local_energy(const anqs_model* model, const anqs_ham* ham, con
  *   joins the work already queued into `stream`.
  * - Problems may share a model or a Hamiltonian (read only) but not their
  *   outputs or workspaces.
- * - The handle owns max_problems non-blocking streams and max_problems + 1
- *   events on the device current at creation; a handle serves one call at a
- *   time (calls on it are ordered by the caller).
+ * - Persistent launch: the 16-bit MLP problems of one width (the width of
+ *   the first such problem, at most 32 of them) share one launch for their
+ *   amplitude stage, the connected determinants' slots (the bulk of the
+ *   work).  Their earlier stages (connected set, parents, sort by first
+ *   slot) run on their streams; the caller's stream then waits for all of
+ *   them and runs one plan kernel and one persistent kernel of one CTA per
+ *   SM over every (problem, slot, tile); each problem's assembly and
+ *   statistics then run on its stream again.  Results are bit-identical to
+ *   anqs_local_energy's.  Other problems run whole on their streams.
+ * - Schedule of the persistent launch (anqs_batch_set_schedule).  The
+ *   128-row tiles of every (problem, slot) form one sequence in
+ *   problem-major order.  ANQS_BATCH_STATIC: CTA i of G takes the tiles
+ *   [i T / G, (i + 1) T / G) (chunk unused).  ANQS_BATCH_DYNAMIC (the
+ *   default, chunk 8): work items of `chunk` tiles of one (problem, slot)
+ *   taken from a global counter.  ANQS_BATCH_STREAMS: every problem whole on
+ *   its own stream (no persistent launch).
+ * - anqs_batch_autotune times the persistent launch on the given problems
+ *   for each candidate schedule (STATIC, then DYNAMIC with chunk 8, 16, 32,
+ *   64, 128, 256, 512; times_ms, if not NULL, receives the 8 times in ms,
+ *   CUDA events on `stream`) and keeps the fastest in the handle.  It runs the
+ *   batched call 9 times (outputs are overwritten, inputs unchanged) and
+ *   synchronises `stream`; it must not be called while `stream` is being
+ *   captured (ANQS_ERR_ARG), and returns ANQS_ERR_UNSUPPORTED when no
+ *   problem would use the persistent launch.
+ * - The handle owns max_problems non-blocking streams, 2 max_problems + 4
+ *   events and 16 KB of device memory (the persistent launch's work groups)
+ *   on the device current at creation; a handle serves one call at a time
+ *   (calls on it are ordered by the caller).
  * ------------------------------------------------------------------------- */
 typedef struct anqs_batch anqs_batch;
 
@@ -402,6 +427,12 @@ ANQS_API int anqs_batch_create(anqs_batch** out, int max_problems);
 ANQS_API int anqs_batch_destroy(anqs_batch* batch);
 ANQS_API int anqs_batched_local_energy(anqs_batch* batch, const anqs_eloc_problem* problems_host, int n_problems,
                                        void* stream);
+
+enum { ANQS_BATCH_STREAMS = 0, ANQS_BATCH_STATIC = 1, ANQS_BATCH_DYNAMIC = 2 };
+ANQS_API int anqs_batch_set_schedule(anqs_batch* batch, int mode, int chunk);
+ANQS_API int anqs_batch_get_schedule(const anqs_batch* batch, int* mode, int* chunk);
+ANQS_API int anqs_batch_autotune(anqs_batch* batch, const anqs_eloc_problem* problems_host, int n_problems,
+                                 void* stream, float* times_ms);
 
 /* ---------------------------------------------------------------------------
  * VMC gradient (Eq. grad_def)

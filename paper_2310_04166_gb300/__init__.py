@@ -320,6 +320,10 @@ def local_energy(model: Model, ham: Hamiltonian, x: torch.Tensor, counts: torch.
     return ere, eim, stats
 
 
+AUTOTUNE_CANDIDATES = [(_lib.ANQS_BATCH_STATIC, 1)] + \
+    [(_lib.ANQS_BATCH_DYNAMIC, c) for c in (8, 16, 32, 64, 128, 256, 512)]
+
+
 class EnergyBatch:
     """Handle of anqs_batched_local_energy: one stream and one event per
     problem slot (max_problems of them) on the current CUDA device."""
@@ -334,12 +338,7 @@ class EnergyBatch:
             _lib._lib.anqs_batch_destroy(self._h)
             self._h = None
 
-    def local_energy(self, items, stream=None):
-        """Local energies of several independent problems in one call, side
-        by side on the handle's streams, ordered on `stream` (capturable in a
-        CUDA graph).  items: dicts with model, ham, x and optionally counts,
-        n_dev, workspace, out=(eloc_re, eloc_im, stats).  Returns the
-        (eloc_re, eloc_im, stats) of each problem."""
+    def _problems(self, items):
         probs = (_lib.ElocProblem * max(len(items), 1))()
         keep, results = [], []
         for k, it in enumerate(items):
@@ -360,9 +359,42 @@ class EnergyBatch:
                                         ere.data_ptr(), eim.data_ptr(), _ptr(stats), ws.data_ptr(), ws.numel())
             keep += [x, cnt, ws]
             results.append((ere, eim, stats))
+        return probs, keep, results
+
+    def local_energy(self, items, stream=None):
+        """Local energies of several independent problems in one call, side
+        by side on the handle's streams, the 16-bit MLP problems' amplitude
+        stage in one persistent launch, ordered on `stream` (capturable in a
+        CUDA graph).  items: dicts with model, ham, x and optionally counts,
+        n_dev, workspace, out=(eloc_re, eloc_im, stats).  Returns the
+        (eloc_re, eloc_im, stats) of each problem."""
+        probs, keep, results = self._problems(items)
         check(_lib.load().anqs_batched_local_energy(self._h, probs, len(items), _stream(stream)))
         self._keep = keep  # inputs and workspaces stay alive until the next call
         return results
+
+    def set_schedule(self, mode: int, chunk: int = 8):
+        """Schedule of the persistent launch: _lib.ANQS_BATCH_STATIC or
+        ANQS_BATCH_DYNAMIC with `chunk` tiles per work item, or
+        ANQS_BATCH_STREAMS (every problem whole on its own stream)."""
+        check(_lib.load().anqs_batch_set_schedule(self._h, int(mode), int(chunk)))
+
+    @property
+    def schedule(self):
+        mode, chunk = C.c_int(), C.c_int()
+        check(_lib.load().anqs_batch_get_schedule(self._h, C.byref(mode), C.byref(chunk)))
+        return mode.value, chunk.value
+
+    def autotune(self, items, stream=None):
+        """Time every candidate schedule of the persistent launch on these
+        problems (outside any capture) and keep the fastest.  Returns the 8
+        times in ms of AUTOTUNE_CANDIDATES: STATIC, then DYNAMIC with chunk
+        8 .. 512."""
+        probs, keep, _ = self._problems(items)
+        times = (C.c_float * 8)()
+        check(_lib.load().anqs_batch_autotune(self._h, probs, len(items), _stream(stream), times))
+        self._keep = keep
+        return list(times)
 
 
 def grad_workspace_bytes(model, ham, n_x, least: bool = False) -> int:

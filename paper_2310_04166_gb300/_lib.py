@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(HERE, "lib", "libanqs.so")
 ANQS_OK = 0
 ANQS_MODEL_MLP, ANQS_MODEL_TF, ANQS_MODEL_TABLE, ANQS_MODEL_NADE = 0, 1, 2, 3
 ANQS_FORM_FP32, ANQS_FORM_BF16 = 0, 1
+ANQS_BATCH_STREAMS, ANQS_BATCH_STATIC, ANQS_BATCH_DYNAMIC = 0, 1, 2
 ERRORS = {-1: "ANQS_ERR_ARG", -2: "ANQS_ERR_CAPACITY", -3: "ANQS_ERR_SECTOR", -4: "ANQS_ERR_CUDA",
           -5: "ANQS_ERR_UNSUPPORTED"}
 
@@ -72,6 +73,9 @@ SIGNATURES = {
     "anqs_batch_create": (C.c_int, [C.POINTER(_VP), C.c_int]),
     "anqs_batch_destroy": (C.c_int, [_VP]),
     "anqs_batched_local_energy": (C.c_int, [_VP, _VP, C.c_int, _VP]),
+    "anqs_batch_set_schedule": (C.c_int, [_VP, C.c_int, C.c_int]),
+    "anqs_batch_get_schedule": (C.c_int, [_VP, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "anqs_batch_autotune": (C.c_int, [_VP, _VP, C.c_int, _VP, C.POINTER(C.c_float)]),
     "anqs_launch_count": (C.c_int, [C.POINTER(_U64)]),
     "anqs_profile_enable": (C.c_int, [C.c_int]),
     "anqs_profile_read": (C.c_int, [C.c_int, C.POINTER(C.c_char_p), C.POINTER(_U64), C.POINTER(C.c_double)]),

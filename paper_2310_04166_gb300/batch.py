@@ -4,17 +4,21 @@ Each problem's VMC pass (sampling, local energies with their statistics,
 gradient) runs on its own CUDA stream; the passes of all problems are
 captured into one CUDA graph (fork from the capturing stream, join back), so
 one replay launches every problem's kernels and the GPU runs problems of
-different sizes side by side.  All sizes stay on the device (unique counts,
-Philox counters), as for a single problem.  Argument marshalling only: every
-step runs in the library's kernels.
+different sizes side by side.  With `persistent=True` the local energies of
+all problems come from one anqs_batched_local_energy call between the
+samplers and the gradients: the 16-bit MLP problems' amplitude stage then
+runs as one persistent launch over every (problem, slot, tile), with the
+schedule the handle's autotuner picked.  All sizes stay on the device
+(unique counts, Philox counters), as for a single problem.  Argument
+marshalling only: every step runs in the library's kernels.
 """
 from __future__ import annotations
 
 import torch
 
 from . import _lib
-from . import (Hamiltonian, Model, grad, grad_workspace_bytes, local_energy, local_energy_workspace_bytes,
-               sample_into, sample_workspace_bytes, _ws)
+from . import (EnergyBatch, Hamiltonian, Model, grad, grad_workspace_bytes, local_energy,
+               local_energy_workspace_bytes, sample_into, sample_workspace_bytes, _ws)
 
 
 class Problem:
@@ -33,38 +37,64 @@ class Problem:
         self.ws_e = _ws(local_energy_workspace_bytes(model, ham, cap), dev)
         self.ws_g = _ws(grad_workspace_bytes(model, ham, cap), dev)
 
-    def step(self, stream=None):
-        """One pass on the current (or given) stream; the counter advances on the device."""
+    def sample(self, stream=None):
         m = self.model
         if m.desc.form == _lib.ANQS_FORM_BF16:
             m.sync(stream)
         sample_into(m, self.ham, self.n_samples, self.seed, 0, self.x, self.cnt, self.nu, self.ws_s, stream,
                     counter_dev=self.ctr)
-        local_energy(m, self.ham, self.x, self.cnt, workspace=self.ws_e, stream=stream, n_dev=self.nu,
-                     out=(self.ere, self.eim, self.stats))
-        grad(m, self.ham, self.x, self.cnt, self.ere, self.eim, self.stats, workspace=self.ws_g, stream=stream,
-             n_dev=self.nu, out=self.g)
+
+    def energy_item(self) -> dict:
+        """This problem's arguments of a batched local-energy call."""
+        return dict(model=self.model, ham=self.ham, x=self.x, counts=self.cnt, n_dev=self.nu, workspace=self.ws_e,
+                    out=(self.ere, self.eim, self.stats))
+
+    def gradient(self, stream=None):
+        grad(self.model, self.ham, self.x, self.cnt, self.ere, self.eim, self.stats, workspace=self.ws_g,
+             stream=stream, n_dev=self.nu, out=self.g)
         s = torch.cuda.current_stream() if stream is None else stream
         with torch.cuda.stream(s):
             self.ctr.add_(1)
 
+    def step(self, stream=None):
+        """One pass on the current (or given) stream; the counter advances on the device."""
+        self.sample(stream)
+        local_energy(self.model, self.ham, self.x, self.cnt, workspace=self.ws_e, stream=stream, n_dev=self.nu,
+                     out=(self.ere, self.eim, self.stats))
+        self.gradient(stream)
+
 
 class BatchedStep:
-    """All problems' passes in one CUDA graph (one stream per problem)."""
+    """All problems' passes in one CUDA graph (one stream per problem; with
+    persistent=True the local energies in one batched call)."""
 
-    def __init__(self, problems: list[Problem]):
+    def __init__(self, problems: list[Problem], persistent: bool = False):
         self.problems = problems
         self.streams = [torch.cuda.Stream() for _ in problems]
         self.graph = None
+        self.energy = EnergyBatch(len(problems)) if persistent else None
 
-    def _fork_join(self):
+    def _each(self, fn):
         main = torch.cuda.current_stream()
         for p, s in zip(self.problems, self.streams):
             s.wait_stream(main)
             with torch.cuda.stream(s):
-                p.step(s)
+                fn(p, s)
         for s in self.streams:
             main.wait_stream(s)
+
+    def _fork_join(self):
+        if self.energy is None:
+            self._each(lambda p, s: p.step(s))
+            return
+        self._each(lambda p, s: p.sample(s))
+        self.energy.local_energy([p.energy_item() for p in self.problems])
+        self._each(lambda p, s: p.gradient(s))
+
+    def autotune(self):
+        """Pick the persistent launch's schedule on the current sample sets
+        (run one eager pass first so that they exist)."""
+        return self.energy.autotune([p.energy_item() for p in self.problems])
 
     def eager(self):
         self._fork_join()

@@ -768,15 +768,43 @@ int anqs_local_energy(const anqs_model* M, const anqs_ham* H, const uint64_t* x,
 struct anqs_batch {
   int device;
   std::vector<cudaStream_t> streams;
-  std::vector<cudaEvent_t> done;
-  cudaEvent_t fork;
+  std::vector<cudaEvent_t> done;  // problem k's work is queued
+  std::vector<cudaEvent_t> pre;   // problem k's stages before the persistent launch are queued
+  cudaEvent_t fork = nullptr, mid = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;  // around the persistent launch (autotuner)
+  bool timing = false;
+  void* groups = nullptr;  // work groups of the persistent launch (device)
+  uint32_t* ctl = nullptr;  // its counters (device)
+  int mode = ANQS_BATCH_DYNAMIC, chunk = 8;
 };
 
 static void batch_release(anqs_batch* b) {
   for (cudaStream_t st : b->streams) cudaStreamDestroy(st);
   for (cudaEvent_t e : b->done) cudaEventDestroy(e);
-  if (b->fork) cudaEventDestroy(b->fork);
+  for (cudaEvent_t e : b->pre) cudaEventDestroy(e);
+  for (cudaEvent_t e : {b->fork, b->mid, b->t0, b->t1})
+    if (e) cudaEventDestroy(e);
+  if (b->groups) cudaFree(b->groups);
+  if (b->ctl) cudaFree(b->ctl);
   delete b;
+}
+
+// problems whose suffix stage can join the persistent multi-problem launch:
+// 16-bit MLPs of one width (the width of the first such problem), at most
+// mlp_tc_multi_max() of them
+static std::vector<char> fusable(const anqs_batch* b, const anqs_eloc_problem* q, int n) {
+  std::vector<char> f(size_t(n), 0);
+  if (b->mode == ANQS_BATCH_STREAMS) return f;
+  int width = 0, taken = 0;
+  for (int k = 0; k < n && taken < mlp_tc_multi_max(); ++k) {
+    const anqs_model* M = q[k].model;
+    if (M->d.kind != ANQS_MODEL_MLP || M->d.form != ANQS_FORM_BF16) continue;
+    if (!width) width = M->d.width;
+    if (M->d.width != width) continue;
+    f[size_t(k)] = 1;
+    ++taken;
+  }
+  return f;
 }
 
 // checks of one problem, before anything of the call is queued
@@ -801,16 +829,22 @@ int anqs_batch_create(anqs_batch** out, int max_problems) {
   *out = nullptr;
   if (max_problems < 1 || max_problems > 4096) return set_error(ANQS_ERR_ARG, "max_problems %d outside 1..4096", max_problems);
   anqs_batch* b = new anqs_batch();
-  b->fork = nullptr;
   cudaError_t e = cudaGetDevice(&b->device);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->mid, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&b->t1);
+  if (e == cudaSuccess) e = cudaMalloc(&b->groups, mlp_tc_multi_groups_bytes());
+  if (e == cudaSuccess) e = cudaMalloc(&b->ctl, 4 * sizeof(uint32_t));
   for (int k = 0; e == cudaSuccess && k < max_problems; ++k) {
     cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr, ep = nullptr;
     e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
     if (e == cudaSuccess) b->streams.push_back(st);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e == cudaSuccess) b->done.push_back(ev);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ep, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->pre.push_back(ep);
   }
   if (e != cudaSuccess) {
     batch_release(b);
@@ -838,26 +872,141 @@ int anqs_batched_local_energy(anqs_batch* b, const anqs_eloc_problem* q, int n, 
   }
   if (n == 0) return ANQS_OK;
   cudaStream_t s = (cudaStream_t)stream;
+  const std::vector<char> fused = fusable(b, q, n);
+  std::vector<MultiEloc> multi;
+  for (int k = 0; k < n; ++k)
+    if (fused[size_t(k)])
+      multi.push_back(MultiEloc{q[k].model, q[k].ham, q[k].n_x, q[k].workspace_dev, q[k].workspace_bytes});
   ANQS_CUDA(cudaEventRecord(b->fork, s));
-  int queued = 0, r = ANQS_OK;
+  // join[k]: the last event recorded on problem k's stream (0 none, 1 pre, 2 done)
+  std::vector<int> join(size_t(n), 0);
+  int r = ANQS_OK;
+  auto fail = [&](const char* what) {
+    if (r == ANQS_OK) r = set_error(ANQS_ERR_CUDA, "batched local energy: %s failed", what);
+  };
   for (int k = 0; k < n && r == ANQS_OK; ++k) {
     cudaStream_t sk = b->streams[k];
     if (cudaStreamWaitEvent(sk, b->fork, 0) != cudaSuccess) {
-      r = set_error(ANQS_ERR_CUDA, "batched local energy: stream fork failed");
+      fail("stream fork");
       break;
     }
-    r = anqs_local_energy(q[k].model, q[k].ham, q[k].x_dev, q[k].counts_dev, q[k].n_x, q[k].n_x_dev,
-                          q[k].eloc_re_dev, q[k].eloc_im_dev, q[k].stats_dev, q[k].workspace_dev,
-                          q[k].workspace_bytes, sk);
-    // join whatever this problem queued, even on an error, so that the
-    // caller's stream stays ordered after it
-    if (cudaEventRecord(b->done[k], sk) == cudaSuccess) ++queued;
-    else if (r == ANQS_OK) r = set_error(ANQS_ERR_CUDA, "batched local energy: event record failed");
+    const Count nc{q[k].n_x, q[k].n_x_dev, 1};
+    if (fused[size_t(k)]) {
+      r = eloc_tc_pre(q[k].model, q[k].ham, q[k].x_dev, nc, q[k].workspace_dev, q[k].workspace_bytes, sk);
+      if (cudaEventRecord(b->pre[k], sk) == cudaSuccess) join[k] = 1;
+      else fail("event record");
+    } else {
+      r = anqs_local_energy(q[k].model, q[k].ham, q[k].x_dev, q[k].counts_dev, q[k].n_x, q[k].n_x_dev,
+                            q[k].eloc_re_dev, q[k].eloc_im_dev, q[k].stats_dev, q[k].workspace_dev,
+                            q[k].workspace_bytes, sk);
+      // joined even on an error, so that the caller's stream stays ordered after it
+      if (cudaEventRecord(b->done[k], sk) == cudaSuccess) join[k] = 2;
+      else fail("event record");
+    }
   }
-  for (int k = 0; k < queued; ++k)
-    if (cudaStreamWaitEvent(s, b->done[k], 0) != cudaSuccess && r == ANQS_OK)
-      r = set_error(ANQS_ERR_CUDA, "batched local energy: stream join failed");
+  if (!multi.empty()) {
+    // the persistent launch waits for every fused problem's first stages
+    bool all_pre = true;
+    for (int k = 0; k < n; ++k)
+      if (fused[size_t(k)]) {
+        if (join[k] != 1) all_pre = false;
+        else if (cudaStreamWaitEvent(s, b->pre[k], 0) != cudaSuccess) fail("stream join");
+      }
+    if (r == ANQS_OK && all_pre) {
+      if (b->timing && cudaEventRecord(b->t0, s) != cudaSuccess) fail("timing event");
+      if (r == ANQS_OK)
+        r = launch_mlp_tc_multi(multi.data(), int(multi.size()), b->chunk, b->mode == ANQS_BATCH_DYNAMIC, b->groups,
+                                b->ctl, s);
+      if (b->timing && r == ANQS_OK && cudaEventRecord(b->t1, s) != cudaSuccess) fail("timing event");
+      if (cudaEventRecord(b->mid, s) != cudaSuccess) fail("event record");
+      // the last stages of every fused problem, back on its own stream
+      for (int k = 0; k < n && r == ANQS_OK; ++k) {
+        if (!fused[size_t(k)]) continue;
+        cudaStream_t sk = b->streams[k];
+        if (cudaStreamWaitEvent(sk, b->mid, 0) != cudaSuccess) {
+          fail("stream fork");
+          break;
+        }
+        const Count nc{q[k].n_x, q[k].n_x_dev, 1};
+        r = eloc_tc_post(q[k].ham, nc, q[k].eloc_re_dev, q[k].eloc_im_dev, q[k].workspace_dev, q[k].workspace_bytes,
+                         sk);
+        if (r == ANQS_OK && q[k].counts_dev)
+          r = launch_stats(q[k].eloc_re_dev, q[k].eloc_im_dev, q[k].counts_dev, nc, q[k].stats_dev, sk);
+        if (cudaEventRecord(b->done[k], sk) == cudaSuccess) join[k] = 2;
+        else fail("event record");
+      }
+    }
+  }
+  for (int k = 0; k < n; ++k) {
+    if (!join[k]) continue;
+    if (cudaStreamWaitEvent(s, join[k] == 2 ? b->done[k] : b->pre[k], 0) != cudaSuccess) fail("stream join");
+  }
   return r;
+}
+
+int anqs_batch_set_schedule(anqs_batch* b, int mode, int chunk) {
+  if (!b) return set_error(ANQS_ERR_ARG, "null batch handle");
+  if (mode != ANQS_BATCH_STREAMS && mode != ANQS_BATCH_STATIC && mode != ANQS_BATCH_DYNAMIC)
+    return set_error(ANQS_ERR_ARG, "unknown schedule mode %d", mode);
+  if (chunk < 1 || chunk > 1024) return set_error(ANQS_ERR_ARG, "chunk %d outside 1..1024", chunk);
+  b->mode = mode;
+  b->chunk = chunk;
+  return ANQS_OK;
+}
+
+int anqs_batch_get_schedule(const anqs_batch* b, int* mode, int* chunk) {
+  if (!b || !mode || !chunk) return set_error(ANQS_ERR_ARG, "null argument");
+  *mode = b->mode;
+  *chunk = b->chunk;
+  return ANQS_OK;
+}
+
+int anqs_batch_autotune(anqs_batch* b, const anqs_eloc_problem* q, int n, void* stream, float* times_ms) {
+  if (!b) return set_error(ANQS_ERR_ARG, "null batch handle");
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  ANQS_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return set_error(ANQS_ERR_ARG, "autotuning cannot run inside a capture");
+  const int mode0 = b->mode, chunk0 = b->chunk;
+  if (b->mode == ANQS_BATCH_STREAMS) b->mode = ANQS_BATCH_DYNAMIC;
+  bool any = false;
+  for (char f : fusable(b, q, n)) any = any || f;
+  if (!any) {
+    b->mode = mode0;
+    return set_error(ANQS_ERR_UNSUPPORTED, "no problem of the batch runs in the persistent launch");
+  }
+  // candidates: STATIC (contiguous tile ranges; chunk unused), then DYNAMIC
+  // with 8 .. 512 tiles per work item
+  static const int kChunks[8] = {1, 8, 16, 32, 64, 128, 256, 512};
+  float best = -1.f;
+  int best_mode = b->mode, best_chunk = b->chunk, r = ANQS_OK;
+  b->timing = true;
+  r = anqs_batched_local_energy(b, q, n, stream);  // warm-up (module loading, caches)
+  for (int c = 0; c < 8 && r == ANQS_OK; ++c) {
+    b->mode = c == 0 ? ANQS_BATCH_STATIC : ANQS_BATCH_DYNAMIC;
+    b->chunk = kChunks[c];
+    r = anqs_batched_local_energy(b, q, n, stream);
+    float ms = 0.f;
+    if (r == ANQS_OK && (cudaEventSynchronize(b->t1) != cudaSuccess ||
+                         cudaEventElapsedTime(&ms, b->t0, b->t1) != cudaSuccess))
+      r = set_error(ANQS_ERR_CUDA, "autotuner timing failed");
+    if (times_ms) times_ms[c] = ms;
+    if (r == ANQS_OK && (best < 0.f || ms < best)) {
+      best = ms;
+      best_mode = b->mode;
+      best_chunk = b->chunk;
+    }
+  }
+  b->timing = false;
+  if (r != ANQS_OK) {
+    b->mode = mode0;
+    b->chunk = chunk0;
+    return r;
+  }
+  b->mode = best_mode;
+  b->chunk = best_chunk;
+  ANQS_CUDA(cudaStreamSynchronize(s));
+  return ANQS_OK;
 }
 
 static size_t grad_ws_bytes(const anqs_model* M, uint64_t n_x, bool least) {

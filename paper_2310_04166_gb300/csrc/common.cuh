@@ -325,6 +325,22 @@ int launch_grad_cotangents(const double* ere, const double* eim, const uint64_t*
 int mlp_tc_pack_alloc(anqs_model* m);
 int mlp_tc_pack(anqs_model* m, cudaStream_t s);
 size_t eloc_tc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x);
+// 16-bit MLP local energy in stages (pre: connected set, parents, sort; post:
+// assembly) and the suffix stage of many problems in one persistent launch
+struct MultiEloc {
+  const anqs_model* model;
+  const anqs_ham* ham;
+  uint64_t n_x;  // the host bound of the problem's rows (workspace layout)
+  void* ws;
+  size_t ws_bytes;
+};
+int eloc_tc_pre(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, void* ws, size_t ws_bytes,
+                cudaStream_t s);
+int eloc_tc_post(const anqs_ham* H, Count n_x, double* ere, double* eim, void* ws, size_t ws_bytes, cudaStream_t s);
+int mlp_tc_multi_max();
+size_t mlp_tc_multi_groups_bytes();
+int launch_mlp_tc_multi(const MultiEloc* q, int n, int chunk, int dynamic, void* groups, uint32_t* ctl,
+                        cudaStream_t s);
 int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere,
                 double* eim, void* ws, size_t ws_bytes, cudaStream_t s);
 int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la,

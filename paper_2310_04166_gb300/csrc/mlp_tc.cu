@@ -163,6 +163,7 @@ struct TileArgs {
 };
 
 constexpr int NWG = kNwg;     // warpgroups per CTA, one 128-row tile each in flight
+constexpr int kMaxBatch = 32;  // problems of one persistent multi-problem launch
 constexpr int NT = NWG * MT;
 
 struct Ctx {
@@ -429,6 +430,45 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
   teardown<W>(tv, s_tmem, s_abort);
 }
 
+// One 128-row tile of the suffix work of slot p (one warpgroup): rows
+// perm[tile*128 + t] of the connected determinants with first differing slot
+// j < p (the first `rows` entries of the sorted order); writes each row's
+// masked slot-p term T[row][p] = (log|psi_p(v_p)|, phase).  Returns false if a
+// wait timed out.  Loads of the sort's outputs go through L2: they are written
+// by kernels that may have been launched just before this one.
+template <int W>
+__device__ __forceinline__ bool suffix_tile(const Ctx& c, uint32_t& ph_m, int p, int n, uint64_t tile, uint64_t rows,
+                                            const uint32_t* perm, const uint64_t* xp, const HamView& hv,
+                                            const SlotLayout& Sl, uint32_t img_addr, const unsigned char* img,
+                                            float2* T) {
+  const uint64_t r = tile * MT + c.t;
+  const bool valid = r < rows;
+  const uint32_t row = valid ? __ldcg(perm + r) : 0u;
+  const uint64_t x = valid ? __ldcg(reinterpret_cast<const unsigned long long*>(xp) + row) : 0ull;
+  float out[8];
+  const bool ok = tile_slot<W>(c, ph_m, p, x, Sl, img_addr, img, out);
+  if (ok && valid) {
+    const uint64_t pm = (1ull << (2 * p)) - 1ull;
+    const int a = __popcll(x & pm & 0x5555555555555555ull);
+    const int bb = __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull);
+    const unsigned pmk = slot_mask(hv, p, a, bb, x), mk = norm_mask(hv, p, pmk);
+    float mx = -INFINITY;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if ((mk >> u) & 1u) mx = fmaxf(mx, out[u]);
+    float sum = 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if ((mk >> u) & 1u) sum += __expf(out[u] - mx);
+    const int v = int((x >> (2 * p)) & 3ull);
+    const float ov = (v == 0) ? out[0] : (v == 1) ? out[1] : (v == 2) ? out[2] : out[3];
+    const float pv = (v == 0) ? out[4] : (v == 1) ? out[5] : (v == 2) ? out[6] : out[7];
+    const float lse = mx + __logf(sum);  // same expression order as finalize_kernel
+    T[uint64_t(row) * n + p] = make_float2(((pmk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY, pv);
+  }
+  return ok;
+}
+
 // SUFFIX (weight-stationary): the connected determinants sorted by first
 // differing slot j make, for every slot p, the rows that need slot p (those
 // with j < p) a prefix of the sorted order.  The grid is split among the
@@ -495,36 +535,187 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_ws_kernel(TcView tv, HamView hv,
     bool ok = __syncthreads_and(wait_bar(tc::smem_u32(&bars[0]), 0));
     const uint64_t rows = offsets[p];
     uint32_t ph_m = 0;
-    for (uint64_t tile = li + gp * wg; ok && tile < tiles[p]; tile += gp * NWG) {
-      const uint64_t r = tile * MT + t;
-      const bool valid = r < rows;
-      const uint32_t row = valid ? perm[r] : 0u;
-      const uint64_t x = valid ? xp[row] : 0ull;
-      float out[8];
-      ok = tile_slot<W>(c, ph_m, p, x, Sl, img_addr, smem, out);
-      if (ok && valid) {
-        const uint64_t pm = (1ull << (2 * p)) - 1ull;
-        const int a = __popcll(x & pm & 0x5555555555555555ull);
-        const int bb = __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull);
-        const unsigned pmk = slot_mask(hv, p, a, bb, x), mk = norm_mask(hv, p, pmk);
-        float mx = -INFINITY;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if ((mk >> u) & 1u) mx = fmaxf(mx, out[u]);
-        float sum = 0.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if ((mk >> u) & 1u) sum += __expf(out[u] - mx);
-        const int v = int((x >> (2 * p)) & 3ull);
-        const float ov = (v == 0) ? out[0] : (v == 1) ? out[1] : (v == 2) ? out[2] : out[3];
-        const float pv = (v == 0) ? out[4] : (v == 1) ? out[5] : (v == 2) ? out[6] : out[7];
-        const float lse = mx + __logf(sum);  // same expression order as finalize_kernel
-        T[uint64_t(row) * n + p] = make_float2(((pmk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY, pv);
-      }
-    }
+    for (uint64_t tile = li + gp * wg; ok && tile < tiles[p]; tile += gp * NWG)
+      ok = suffix_tile<W>(c, ph_m, p, n, tile, rows, perm, xp, hv, Sl, img_addr, smem, T);
     if (!ok) s_abort = 1;
   }
   teardown<W>(tv, s_tmem, s_abort);
+}
+
+// ---- many problems in one persistent launch ---------------------------------
+//
+// The suffix work of up to kMaxBatch independent problems (each its own
+// Hamiltonian, MLP and connected set, all of width W) in one launch of one
+// CTA per SM.  A plan kernel turns the problems' sorted row counts into
+// groups (problem b, slot p, tiles of slot p) in problem-major order; the
+// tiles of all groups form one sequence.  Two schedules:
+//   static   CTA i of G takes the contiguous tile range [i T / G, (i+1) T / G)
+//            of the sequence: every CTA gets the same number of tiles, and it
+//            synchronises and reloads the weight image only where its range
+//            crosses into the next group;
+//   dynamic  the groups are cut into work items of `chunk` tiles that CTAs
+//            take from a global counter (the next item is fetched while the
+//            current one runs); a CTA synchronises after every item and
+//            reloads the image when the item's group differs.
+// In both, the CTA's warpgroups share the tiles round-robin.  `chunk` and
+// the schedule are what the batch autotuner chooses.  Every tile computes
+// exactly what the single-problem launch computes for it, so the results are
+// bit-identical.
+struct MultiProblem {
+  TcView tv;
+  HamView hv;
+  const uint64_t* xp;
+  const uint32_t* perm;
+  const uint32_t* offsets;
+  float2* T;
+};
+
+struct MultiGroup {
+  uint32_t bp;     // problem << 8 | slot
+  uint32_t tiles;  // 128-row tiles of the slot
+  uint32_t item0;  // first work item of the group (dynamic schedule)
+  uint32_t tile0;  // first tile of the group in the sequence (static schedule)
+};
+
+struct MultiArgs {
+  int n_prob, chunk, dynamic, pad;
+  uint32_t max_img, kmax;
+  MultiGroup* groups;  // [kMaxBatch * ANQS_MAX_ORB]
+  uint32_t* ctl;       // [0] groups, [1] items, [2] next item (dynamic), [3] tiles
+  MultiProblem prob[kMaxBatch];
+};
+static_assert(sizeof(MultiArgs) <= 32000, "kernel parameter block too large");
+
+__global__ void multi_plan_kernel(const __grid_constant__ MultiArgs a) {
+  ANQS_PDL_ENTRY();
+  __shared__ uint32_t tiles[kMaxBatch][ANQS_MAX_ORB];
+  for (int i = threadIdx.x; i < kMaxBatch * ANQS_MAX_ORB; i += blockDim.x) {
+    const int b = i / ANQS_MAX_ORB, p = i % ANQS_MAX_ORB;
+    uint32_t t = 0;
+    if (b < a.n_prob && p < a.prob[b].tv.n) t = (__ldcg(a.prob[b].offsets + p) + MT - 1) / MT;
+    tiles[b][p] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t g = 0, items = 0, t0 = 0;
+    for (int b = 0; b < a.n_prob; ++b)
+      for (int p = 0; p < a.prob[b].tv.n; ++p)
+        if (tiles[b][p]) {
+          a.groups[g] = MultiGroup{uint32_t(b) << 8 | uint32_t(p), tiles[b][p], items, t0};
+          items += (tiles[b][p] + uint32_t(a.chunk) - 1) / uint32_t(a.chunk);
+          t0 += tiles[b][p];
+          ++g;
+        }
+    a.ctl[0] = g;
+    a.ctl[1] = items;
+    a.ctl[2] = 0;
+    a.ctl[3] = t0;
+  }
+}
+
+// Last group g with key(g) <= v (keys ascending; group 0 has key 0), found by
+// warp 0 and returned to every thread.  Contains a CTA barrier.
+__device__ __forceinline__ uint32_t multi_find(const MultiGroup* groups, uint32_t n_groups, uint32_t v,
+                                               bool by_tile, uint32_t* s_out) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    uint32_t best = 0;
+    for (uint32_t g0 = 0; g0 < n_groups; g0 += 32) {
+      const uint32_t g = g0 + lane;
+      const bool le = g < n_groups && __ldcg(by_tile ? &groups[g].tile0 : &groups[g].item0) <= v;
+      const unsigned m = __ballot_sync(0xffffffffu, le);
+      if (m) best = g0 + 31 - __clz(m);
+      if (m != 0xffffffffu) break;
+    }
+    if (lane == 0) *s_out = best;
+  }
+  __syncthreads();
+  return *s_out;
+}
+
+template <int W>
+__global__ void __launch_bounds__(NT, 1) mlp_tc_multi_kernel(const __grid_constant__ MultiArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[2 + NWG];
+  __shared__ uint32_t s_tmem, s_item[2], s_group;
+  __shared__ int s_abort;
+  const int wg = threadIdx.x / MT, t = threadIdx.x % MT;
+  setup<W>(bars, &s_tmem, &s_abort);
+  ANQS_PDL_WAIT();
+  ANQS_PDL_TRIGGER();
+  Ctx c;
+  c.tv = &a.prob[0].tv;
+  c.s_a = smem + round_up(a.max_img, 1024u) + wg * (MT * a.kmax * 2u);
+  c.a_addr = tc::smem_u32(c.s_a);
+  c.tmem = s_tmem + uint32_t(wg) * W;
+  c.lane_base = uint32_t(t & ~31) << 16;
+  c.bar_m = tc::smem_u32(&bars[2 + wg]);
+  c.wg = wg;
+  c.t = t;
+  const uint32_t img_addr = tc::smem_u32(smem), bar_w = tc::smem_u32(&bars[0]);
+  const uint32_t n_groups = __ldcg(a.ctl), n_items = __ldcg(a.ctl + 1), n_tiles = __ldcg(a.ctl + 3);
+  uint32_t ph_w = 0, ph_m = 0, loaded = 0xffffffffu;
+  // the tiles [t_lo, t_hi) of group g (positions within the group); false on a timed-out wait
+  auto run = [&](uint32_t g, uint32_t t_lo, uint32_t t_hi) -> bool {
+    const uint32_t bp = __ldcg(&a.groups[g].bp);
+    const int b = int(bp >> 8), p = int(bp & 0xffu);
+    const MultiProblem& P = a.prob[b];
+    c.tv = &P.tv;
+    const SlotLayout Sl = slot_layout(p, W, P.tv.L, P.tv.lo);
+    if (bp != loaded) {  // every warpgroup is past its last read of the old image (barrier before)
+      if (threadIdx.x == 0) load_slot(P.tv, p, img_addr, bar_w, W, P.tv.L);
+      const bool ok = __syncthreads_and(wait_bar(bar_w, ph_w));
+      ph_w ^= 1;
+      loaded = bp;
+      if (!ok) return false;
+    }
+    const uint64_t rows = __ldcg(P.offsets + p);
+    bool ok = true;
+    for (uint32_t tile = t_lo + wg; ok && tile < t_hi; tile += NWG)
+      ok = suffix_tile<W>(c, ph_m, p, P.tv.n, tile, rows, P.perm, P.xp, P.hv, Sl, img_addr, smem, P.T);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    return __syncthreads_and(ok);
+  };
+  if (!a.dynamic) {
+    const uint32_t lo = uint32_t(uint64_t(n_tiles) * blockIdx.x / gridDim.x),
+                   hi = uint32_t(uint64_t(n_tiles) * (blockIdx.x + 1) / gridDim.x);
+    if (lo < hi) {
+      for (uint32_t g = multi_find(a.groups, n_groups, lo, true, &s_group); g < n_groups; ++g) {
+        const uint32_t g0 = __ldcg(&a.groups[g].tile0), gt = __ldcg(&a.groups[g].tiles);
+        if (g0 >= hi) break;
+        if (!run(g, (lo > g0 ? lo : g0) - g0, (hi < g0 + gt ? hi : g0 + gt) - g0)) {
+          s_abort = 1;
+          break;
+        }
+      }
+    }
+  } else {
+    if (threadIdx.x == 0) s_item[0] = atomicAdd(a.ctl + 2, 1u);
+    uint32_t g = 0, g_item0 = 1, g_item1 = 0;  // current group and its items [g_item0, g_item1)
+    for (uint32_t k = 0;; ++k) {
+      __syncthreads();
+      const uint32_t item = s_item[k & 1];
+      if (item >= n_items) break;
+      if (threadIdx.x == 0) s_item[(k + 1) & 1] = atomicAdd(a.ctl + 2, 1u);  // read after the next barrier
+      if (item < g_item0 || item >= g_item1) {
+        g = multi_find(a.groups, n_groups, item, false, &s_group);
+        g_item0 = __ldcg(&a.groups[g].item0);
+        g_item1 = g_item0 + (__ldcg(&a.groups[g].tiles) + uint32_t(a.chunk) - 1) / uint32_t(a.chunk);
+      }
+      const uint32_t gt = __ldcg(&a.groups[g].tiles);
+      const uint32_t t0 = (item - g_item0) * uint32_t(a.chunk), t1 = min(t0 + uint32_t(a.chunk), gt);
+      if (!run(g, t0, t1)) {
+        s_abort = 1;
+        break;
+      }
+    }
+  }
+  if (s_abort && threadIdx.x < a.n_prob) atomicExch(a.prob[threadIdx.x].tv.status, ST_TIMEOUT);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (threadIdx.x < 32) tc::tmem_dealloc(s_tmem, NWG * W);
 }
 
 // One CTA of AT threads per parent x (grid-stride over the parents), its
@@ -963,16 +1154,25 @@ size_t eloc_tc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x) {
   return plan_eloc(H, n_x, A, w);
 }
 
-int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,
-                void* ws, size_t ws_bytes, cudaStream_t s) {
+// The local energy of one problem in three stages, so that a batch can run
+// the middle one for many problems in one launch.
+//   pre:    connected set, parents' slots and caches, sort by first slot
+//   suffix: the connected determinants' slots p > j (mlp_tc_ws_kernel)
+//   post:   E_loc assembly
+static int plan_ws(const anqs_ham* H, Count n_x, void* ws, size_t ws_bytes, ElocWs& w) {
   Arena A(ws, ws_bytes);
-  ElocWs w;
   plan_eloc(H, n_x.n, A, w);
   if (!A.fits()) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", A.off);
-  const uint64_t K = H->v.K;
-  const Count mc = scaled(n_x, K);
-  const uint64_t m = mc.n;
-  if (m > 0xffffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "more than 2^32 connected determinants per call");
+  if (n_x.n * H->v.K > 0xffffffffull)
+    return set_error(ANQS_ERR_UNSUPPORTED, "more than 2^32 connected determinants per call");
+  return ANQS_OK;
+}
+
+int eloc_tc_pre(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, void* ws, size_t ws_bytes,
+                cudaStream_t s) {
+  ElocWs w;
+  ANQS_TRY(plan_ws(H, n_x, ws, ws_bytes, w));
+  const Count mc = scaled(n_x, H->v.K);
   ANQS_TRY(launch_connected(H->v, x, n_x, w.xp, w.hv, w.js, w.hd, s));
   {
     TileArgs ta{};
@@ -985,19 +1185,74 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count
     ProfScope ps(PROF_TC_FINALIZE, s);
     ANQS_TRY(launch_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
   }
-  {
-    ProfScope ps(PROF_TC_SORT, s);
-    ANQS_TRY(launch_js_sort(w.js, mc, H->v.n, w.hist, w.cursor, w.offsets, w.perm, s));
-  }
+  ProfScope ps(PROF_TC_SORT, s);
+  return launch_js_sort(w.js, mc, H->v.n, w.hist, w.cursor, w.offsets, w.perm, s);
+}
+
+int eloc_tc_post(const anqs_ham* H, Count n_x, double* ere, double* eim, void* ws, size_t ws_bytes,
+                 cudaStream_t s) {
+  ElocWs w;
+  ANQS_TRY(plan_ws(H, n_x, ws, ws_bytes, w));
+  ProfScope ps(PROF_TC_ELOC, s);
+  return launch_eloc_assemble(H->v.n, uint32_t(H->v.K), n_x, w.xp, w.js, w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x,
+                              ere, eim, s);
+}
+
+int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,
+                void* ws, size_t ws_bytes, cudaStream_t s) {
+  ElocWs w;
+  ANQS_TRY(plan_ws(H, n_x, ws, ws_bytes, w));
+  ANQS_TRY(eloc_tc_pre(M, H, x, n_x, ws, ws_bytes, s));
   {
     TcView tv = make_view(M);
     ProfScope ps(PROF_TC_SUFFIX, s);
     ANQS_TRY(tv.W == 128 ? launch_ws_w<128>(tv, H->v, w, s) : launch_ws_w<64>(tv, H->v, w, s));
   }
-  {
-    ProfScope ps(PROF_TC_ELOC, s);
-    ANQS_TRY(launch_eloc_assemble(H->v.n, uint32_t(K), n_x, w.xp, w.js, w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x, ere,
-                                  eim, s));
+  return eloc_tc_post(H, n_x, ere, eim, ws, ws_bytes, s);
+}
+
+int mlp_tc_multi_max() { return kMaxBatch; }
+
+size_t mlp_tc_multi_groups_bytes() { return size_t(kMaxBatch) * ANQS_MAX_ORB * sizeof(MultiGroup); }
+
+// The suffix stage of n problems (16-bit MLPs of one width, each after its
+// pre stage) in one plan launch and one persistent launch on s.
+int launch_mlp_tc_multi(const MultiEloc* q, int n, int chunk, int dynamic, void* groups, uint32_t* ctl,
+                        cudaStream_t s) {
+  if (n < 1 || n > kMaxBatch) return set_error(ANQS_ERR_ARG, "%d problems for one multi-problem launch", n);
+  if (chunk < 1) return set_error(ANQS_ERR_ARG, "chunk must be >= 1");
+  MultiArgs a{};
+  a.n_prob = n;
+  a.chunk = chunk;
+  a.dynamic = dynamic ? 1 : 0;
+  a.groups = static_cast<MultiGroup*>(groups);
+  a.ctl = ctl;
+  int W = 0;
+  for (int k = 0; k < n; ++k) {
+    const TcView tv = make_view(q[k].model);
+    if (k == 0) W = tv.W;
+    if (tv.W != W) return set_error(ANQS_ERR_ARG, "multi-problem launch needs one network width");
+    ElocWs w;
+    ANQS_TRY(plan_ws(q[k].ham, host_count(q[k].n_x), q[k].ws, q[k].ws_bytes, w));
+    a.prob[k].tv = tv;
+    a.prob[k].hv = q[k].ham->v;
+    a.prob[k].xp = w.xp;
+    a.prob[k].perm = w.perm;
+    a.prob[k].offsets = w.offsets;
+    a.prob[k].T = w.T;
+    a.max_img = std::max(a.max_img, tv.max_img);
+    a.kmax = std::max(a.kmax, tv.kmax);
+  }
+  const size_t sm = size_t(round_up(a.max_img, 1024u)) + size_t(NWG) * MT * a.kmax * 2u;
+  if (sm > kSmemLimit) return set_error(ANQS_ERR_UNSUPPORTED, "multi-problem launch needs %zu bytes of shared memory", sm);
+  ProfScope ps(PROF_TC_SUFFIX, s);
+  ANQS_CUDA_LAUNCH("multi_plan_kernel", launch_k(multi_plan_kernel, dim3(1), dim3(256), 0, s, a));
+  if (W == 128) {
+    ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_multi_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+    ANQS_CUDA_LAUNCH("mlp_tc_multi_kernel", launch_k(mlp_tc_multi_kernel<128>, dim3(num_sms()), dim3(NT), sm, s, a));
+  } else {
+    ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_multi_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+    ANQS_CUDA_LAUNCH("mlp_tc_multi_kernel", launch_k(mlp_tc_multi_kernel<64>, dim3(num_sms()), dim3(NT), sm, s, a));
   }
   return ANQS_OK;
 }

@@ -127,3 +127,100 @@ def test_batched_local_energy_checks_before_queueing(A):
     torch.cuda.synchronize()
     for o in outs:  # nothing of the failed calls ran
         assert all(torch.isnan(t).all() for t in o)
+
+
+def _mlp_items(A, ks, n_samples=20_000):
+    """16-bit MLP problems of the 32-problem workload (different orbital and
+    electron counts, width 128) with their sample sets, plus one 16-bit MLP
+    of width 64 (runs on its stream: the persistent launch takes one width)."""
+    from synthetic import workload
+    items = []
+    for k in ks:
+        p = batch32_problem(k)
+        ham = A.Hamiltonian(p["h"], p["g"], p["e_nuc"], p["n_alpha"], p["n_beta"])
+        params = torch.tensor(flatten_mlp(mlp_params(p["seed"], p["n"], p["width"], p["n_hidden"])), device="cuda")
+        model = A.Model.mlp(p["n"], p["width"], p["n_hidden"], params, "bf16")
+        x, c = A.sample(model, ham, n_samples, seed=40 + k)
+        items.append(dict(model=model, ham=ham, x=x, counts=c))
+    w = workload("small", bias_std=0.2)
+    ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    model = A.Model.mlp(w["n"], w["width"], w["n_hidden"], torch.tensor(w["params"], device="cuda"), "bf16")
+    x, c = A.sample(model, ham, 10_000, seed=3)
+    items.insert(2, dict(model=model, ham=ham, x=x, counts=c))
+    return items
+
+
+def test_persistent_launch_every_schedule_equals_each_call_alone(A):
+    """The persistent multi-problem launch computes every tile exactly as the
+    single-problem launch does: for every schedule (static and dynamic, 4 to
+    32 tiles per work item) and for plain streams, the local energies and
+    statistics are the same bits as anqs_local_energy's."""
+    from paper_2310_04166_gb300 import _lib
+    items = _mlp_items(A, [0, 3, 5, 9, 14, 20, 27])
+    alone = [A.local_energy(it["model"], it["ham"], it["x"], it["counts"]) for it in items]
+    batch = A.EnergyBatch(len(items))
+    assert batch.schedule == (_lib.ANQS_BATCH_DYNAMIC, 8)
+    for mode in (_lib.ANQS_BATCH_STATIC, _lib.ANQS_BATCH_DYNAMIC, _lib.ANQS_BATCH_STREAMS):
+        for chunk in (1, 3, 8, 32, 512):
+            batch.set_schedule(mode, chunk)
+            got = batch.local_energy(items)
+            torch.cuda.synchronize()
+            for (ar, ai, ast), (br, bi, bst) in zip(alone, got):
+                assert torch.equal(ar, br) and torch.equal(ai, bi) and torch.equal(ast, bst), (mode, chunk)
+    for it in items:
+        assert it["model"].status() == 0
+
+
+def test_autotune_keeps_the_fastest_schedule(A):
+    from paper_2310_04166_gb300 import _lib
+    items = _mlp_items(A, [1, 4, 8, 12])
+    batch = A.EnergyBatch(len(items))
+    times = batch.autotune(items)
+    assert len(times) == 8 and all(t > 0 for t in times)
+    mode, chunk = batch.schedule
+    best = min(range(8), key=lambda i: times[i])
+    assert (mode, chunk) == A.AUTOTUNE_CANDIDATES[best]
+    alone = [A.local_energy(it["model"], it["ham"], it["x"], it["counts"]) for it in items]
+    got = batch.local_energy(items)
+    torch.cuda.synchronize()
+    for (ar, ai, ast), (br, bi, bst) in zip(alone, got):
+        assert torch.equal(ar, br) and torch.equal(ai, bi) and torch.equal(ast, bst)
+    # refused while the stream is being captured (nothing is queued)
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with pytest.raises(A.AnqsError, match="capture"):
+            with torch.cuda.graph(graph, stream=side):
+                batch.autotune(items, stream=side)
+    # no 16-bit MLP problem: nothing to tune
+    w_items = [it for it in _mixed(A) if not (it["model"].desc.kind == _lib.ANQS_MODEL_MLP
+                                              and it["model"].desc.form == _lib.ANQS_FORM_BF16)]
+    with pytest.raises(A.AnqsError, match="UNSUPPORTED"):
+        A.EnergyBatch(len(w_items)).autotune(w_items)
+
+
+def test_batched_step_with_persistent_launch_equals_each_problem_alone(A):
+    """The 32-problem workload's step shape (samplers on their streams, one
+    batched local-energy call, gradients on their streams) in one CUDA graph
+    gives every problem the pass it gets alone, bit for bit."""
+    from paper_2310_04166_gb300.batch import BatchedStep
+    ks = [2, 6, 11, 19, 23]
+    batched = _problems(A, ks, "bf16", 20_000)
+    alone = _problems(A, ks, "bf16", 20_000)
+    bs = BatchedStep(batched, persistent=True)
+    bs.eager()
+    bs.autotune()
+    bs.capture()
+    bs.replay()
+    for p in alone:
+        for _ in range(3):
+            p.step()
+    torch.cuda.synchronize()
+    for a, b in zip(batched, alone):
+        k = int(a.nu.item())
+        assert k == int(b.nu.item()) and k > 0
+        assert torch.equal(a.x[:k], b.x[:k]) and torch.equal(a.cnt[:k], b.cnt[:k])
+        assert torch.equal(a.stats, b.stats)
+        assert torch.equal(a.ere[:k], b.ere[:k])
+        assert torch.equal(a.g, b.g)
+        assert int(a.ctr.item()) == int(b.ctr.item()) == 3
