@@ -56,12 +56,22 @@ struct Philox {
   }
 };
 
+// Grid barrier of the persistent launch: one arrival counter per level
+// (zeroed by the initial kernel, never reset), so a level's barrier is one
+// reduction per CTA and a poll until the count reaches the grid size.
+struct GridBarrier {
+  unsigned arrive[ANQS_MAX_ORB + 1];
+  int err;  // a CTA gave up waiting
+  int pad[2];
+};
+constexpr int kBarrierWords = int(sizeof(GridBarrier) / 4);
+
 __global__ void init_kernel(uint64_t* pre, uint64_t* cnt, uint64_t* n_front, uint64_t n_samples, unsigned* done,
                             uint64_t* child, uint32_t* idx0, int* barrier) {
   ANQS_PDL_ENTRY();
   if (idx0) idx0[0] = 0;  // prefix-table mode: the root is table row 0
-  if (barrier)            // the persistent launch's grid barrier: count, rounds, error
-    for (int k = 0; k < 4; ++k) barrier[k] = 0;
+  if (barrier)            // the persistent launch's grid barrier: arrivals per level, error
+    for (int k = 0; k < kBarrierWords; ++k) barrier[k] = 0;
   pre[0] = 0;
   cnt[0] = n_samples;
   n_front[0] = 1;
@@ -688,17 +698,23 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
 // clears buffer (p + 1) % 3, which every CTA finished reading before the
 // barrier of level p - 1.  The draws and their order are those of
 // draw_small_kernel, so the samples are the same bit for bit.
+//
+// When the table has at most kStageRows rows, every CTA first stages, for
+// every row, the split thresholds of its conditional, its outcome masks and
+// its children's rows in shared memory (the masks and children before the
+// programmatic-dependency wait, the thresholds from the slot outputs after
+// it), so that a level reads nothing from global memory but the child counts
+// after its barrier.
 constexpr int PER_F = 2048;                          // largest frontier (the prefix table's level bound)
 constexpr size_t PER_DYN = size_t(2) * PER_F * (8 + 4 + 4)   // frontier copies: prefix, count, table row
                            + size_t(PER_F + 1) * 4            // draw-block offsets
                            + size_t(SMALL_T) * (32 + 16);     // window thresholds and counts
+constexpr int kStageRows = 1024;
+constexpr size_t STAGE_DYN = size_t(kStageRows) * (32 + 16 + 1);  // thresholds, child rows, masks
 constexpr uint64_t kBarrierNs = 2000000000ull;
 
-struct GridBarrier {
-  unsigned count;  // CTAs arrived in the current round
-  unsigned gen;    // rounds completed
-  int err;         // a CTA gave up waiting
-  int pad;
+struct LevelOffsets {
+  uint32_t off[ANQS_MAX_ORB + 1];  // table rows of level p: [off[p], off[p + 1])
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
@@ -713,33 +729,28 @@ __device__ __forceinline__ uint64_t gtimer() {
   return t;
 }
 
-// Barrier over the co-resident grid: the last CTA to arrive resets the count
-// and opens the next round; the others wait (bounded by kBarrierNs, after
-// which they set the error word and every CTA leaves).  Writes before the
-// barrier are visible to every CTA after it.  `gen` is thread 0's count of
-// rounds passed.
-__device__ bool grid_barrier(GridBarrier* gb, unsigned& gen, int* s_ok) {
+// Barrier of level p over the co-resident grid: thread 0 of every CTA makes
+// the CTA's writes visible and adds one to the level's arrival counter, then
+// polls it until every CTA has arrived (bounded by kBarrierNs, after which it
+// sets the error word and every CTA leaves).  Writes before the barrier are
+// visible to every CTA after it.
+__device__ bool level_barrier(GridBarrier* gb, int p, int* s_ok) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(&gb->arrive[p]) : "memory");
     int ok = 1;
-    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
+    if (ld_acquire_u32(&gb->arrive[p]) < gridDim.x) {
       const uint64_t t0 = gtimer();
-      while (ld_acquire_u32(&gb->gen) == gen) {
+      while (ld_acquire_u32(&gb->arrive[p]) < gridDim.x) {
         if (*reinterpret_cast<volatile int*>(&gb->err) || gtimer() - t0 > kBarrierNs) {
           atomicExch(&gb->err, 1);
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
-    __threadfence();
-    ++gen;
     *s_ok = ok && !*reinterpret_cast<volatile int*>(&gb->err);
   }
   __syncthreads();
@@ -747,11 +758,10 @@ __device__ bool grid_barrier(GridBarrier* gb, unsigned& gen, int* s_ok) {
 }
 
 __global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int n, uint64_t n_samples, uint64_t seed,
-                                                                uint64_t counter0,
-                                                                const uint64_t* __restrict__ counter_dev,
-                                                                const float* __restrict__ logits,
-                                                                const int32_t* __restrict__ pt_child,
-                                                                uint64_t* child, uint64_t child_stride,
+                                                                uint64_t counter0, const uint64_t* counter_dev,
+                                                                const float* logits, const uint64_t* pt_x,
+                                                                const int32_t* pt_child, LevelOffsets lvo,
+                                                                int staged, uint64_t* child, uint64_t child_stride,
                                                                 GridBarrier* gb, uint64_t* __restrict__ x_out,
                                                                 uint64_t* __restrict__ n_out,
                                                                 uint64_t* __restrict__ n_unique, int* status) {
@@ -762,13 +772,37 @@ __global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int 
   uint32_t* s_scan = fr_idx + 2 * PER_F;                                         // [PER_F + 1]
   uint64_t(*s_thr)[4] = reinterpret_cast<uint64_t(*)[4]>(s_scan + PER_F + 4);    // [SMALL_T][4]
   uint32_t(*s_cnt)[4] = reinterpret_cast<uint32_t(*)[4]>(s_thr + SMALL_T);       // [SMALL_T][4]
+  uint64_t(*st_thr)[4] = reinterpret_cast<uint64_t(*)[4]>(s_cnt + SMALL_T);      // staged: [kStageRows][4]
+  int32_t(*st_child)[4] = reinterpret_cast<int32_t(*)[4]>(st_thr + kStageRows);  // staged: [kStageRows][4]
+  uint8_t* st_mk = reinterpret_cast<uint8_t*>(st_child + kStageRows);           // staged: [kStageRows]
   __shared__ uint8_t s_mk[SMALL_T];
   __shared__ uint32_t s_red[33];
   __shared__ int s_ok;
+  __shared__ uint32_t s_off[ANQS_MAX_ORB + 1];
+  if (threadIdx.x <= n) s_off[threadIdx.x] = lvo.off[threadIdx.x];
+  __syncthreads();
+  const int n_rows = int(s_off[n]);
+  if (staged) {  // rows' masks and children: fixed by the Hamiltonian
+    for (int r = threadIdx.x; r < n_rows; r += SMALL_T) {
+      int p = 0;
+      while (p + 1 < n && uint32_t(r) >= s_off[p + 1]) ++p;
+      const uint64_t x = pt_x[r];
+      const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p), x), mk = norm_mask(hv, p, pm);
+      st_mk[r] = uint8_t(mk | (pm << 4));
+      for (int v = 0; v < 4; ++v) st_child[r][v] = pt_child[uint64_t(r) * 4 + v];
+    }
+  }
   ANQS_PDL_WAIT();  // the prefix table's logits and the cleared counters come from the kernels before
+  if (staged) {  // rows' split thresholds from the slot outputs just written
+    __syncthreads();
+    for (int r = threadIdx.x; r < n_rows; r += SMALL_T) {
+      float l[4];
+      for (int v = 0; v < 4; ++v) l[v] = __ldcg(logits + uint64_t(r) * 8 + v);
+      split_thresholds(l, st_mk[r] & 0xFu, st_thr[r]);
+    }
+  }
   const int lane = threadIdx.x & 31;
   const uint64_t counter = counter0 + (counter_dev ? *counter_dev : 0ull);
-  unsigned gen = 0;  // the initial kernel zeroed the barrier
   if (threadIdx.x == 0) {
     fr_pre[0] = 0;
     fr_cnt[0] = uint32_t(n_samples);
@@ -790,6 +824,38 @@ __global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int 
         nc[i] = 0;
     }
     __syncthreads();  // this level's frontier copy is complete
+    if (p == n - 1) {
+      // The last slot: where every node has a single allowed outcome (always
+      // so under MU masking, the electron counts fix the last orbital) every
+      // draw goes to it, so the children are the nodes with that outcome and
+      // their counts: written without draws or a barrier, in the order the
+      // split would emit them.
+      bool forced = true;
+      for (int i = threadIdx.x; i < nf; i += SMALL_T) {
+        unsigned mkb;
+        if (staged) {
+          mkb = st_mk[idx[i]];
+        } else {
+          const uint64_t x = pre[i];
+          const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p), x);
+          mkb = norm_mask(hv, p, pm) | (pm << 4);
+        }
+        if (__popc(mkb & 0xFu) != 1 || !((mkb >> 4) & mkb & 0xFu)) forced = false;
+      }
+      if (__syncthreads_and(forced)) {
+        if (blockIdx.x == 0) {
+          for (int i = threadIdx.x; i < nf; i += SMALL_T) {
+            const unsigned mk = staged ? st_mk[idx[i]] & 0xFu
+                                       : norm_mask(hv, p, slot_mask(hv, p, popc_alpha(pre[i], p),
+                                                                    popc_beta(pre[i], p), pre[i]));
+            x_out[i] = pre[i] | (uint64_t(__ffs(mk) - 1) << (2 * p));
+            n_out[i] = cnt[i];
+          }
+          if (threadIdx.x == 0) *n_unique = uint64_t(nf);
+        }
+        break;
+      }
+    }
     // draw-block offsets of the nodes
     uint32_t carry = 0;
     for (int base = 0; base < nf; base += RUN * SMALL_T) {
@@ -829,10 +895,14 @@ __global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int 
       if (threadIdx.x <= n_hi - n_lo) {
         const int i = n_lo + threadIdx.x;
         for (int v = 0; v < 4; ++v) s_cnt[threadIdx.x][v] = 0;
-        const uint64_t x = pre[i];
-        const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p), x), mk = norm_mask(hv, p, pm);
-        split_thresholds(logits + uint64_t(idx[i]) * 8, mk, s_thr[threadIdx.x]);
-        s_mk[threadIdx.x] = uint8_t(mk | (pm << 4));
+        if (!staged) {
+          const uint64_t x = pre[i];
+          const unsigned pm = slot_mask(hv, p, popc_alpha(x, p), popc_beta(x, p), x), mk = norm_mask(hv, p, pm);
+          float l[4];
+          for (int v = 0; v < 4; ++v) l[v] = __ldcg(logits + uint64_t(idx[i]) * 8 + v);
+          split_thresholds(l, mk, s_thr[threadIdx.x]);
+          s_mk[threadIdx.x] = uint8_t(mk | (pm << 4));
+        }
       }
       __syncthreads();
       const uint32_t t = t0 + threadIdx.x;
@@ -845,12 +915,15 @@ __global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int 
         const uint64_t c = cnt[node];
         uint64_t w[4];
         Philox::block(pre[node], ib, uint64_t(p), counter, seed, 0ull, w);
-        const unsigned mk = s_mk[li] & 0xFu, pm = s_mk[li] >> 4;
+        const uint32_t row = idx[node];
+        const unsigned mkb = staged ? st_mk[row] : s_mk[li];
+        const uint64_t* thr = staged ? st_thr[row] : s_thr[li];
+        const unsigned mk = mkb & 0xFu, pm = mkb >> 4;
         int last = 3;
         while (last > 0 && !((mk >> last) & 1u)) --last;
         for (int k = 0; k < 4; ++k) {
           if (ib * 4 + k >= c) break;
-          const int v = draw_outcome(w[k], s_thr[li], mk, last);
+          const int v = draw_outcome(w[k], thr, mk, last);
           if ((pm >> v) & 1u) packed += 1u << (8 * v);
         }
       }
@@ -879,7 +952,7 @@ __global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int 
         }
     }
     // every CTA's counts of level p are in `ch`
-    ok = grid_barrier(gb, gen, &s_ok);
+    ok = level_barrier(gb, p, &s_ok);
     if (!ok) break;
     // children in (node, outcome) order -> this CTA's copy of the next frontier
     // (the last level: the output, written by CTA 0)
@@ -905,7 +978,8 @@ __global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int 
             if (off < uint32_t(PER_F)) {
               fr_pre[nxt * PER_F + off] = xc;
               fr_cnt[nxt * PER_F + off] = uint32_t(c[e]);
-              fr_idx[nxt * PER_F + off] = uint32_t(pt_child[uint64_t(idx[i >> 2]) * 4 + (i & 3)]);
+              fr_idx[nxt * PER_F + off] =
+                  uint32_t(staged ? st_child[idx[i >> 2]][i & 3] : pt_child[uint64_t(idx[i >> 2]) * 4 + (i & 3)]);
             }
           } else if (blockIdx.x == 0) {
             x_out[off] = xc;
@@ -1039,9 +1113,14 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
     ANQS_TRY(launch_mlp_tc_prefix_logits(M, H, P.plog, s));
     // all levels in one cooperative launch (one CTA per SM at most, each CTA
     // one window of draw blocks per round)
+    // rows' thresholds, masks and children staged in shared memory when they fit
+    LevelOffsets lvo{};
+    for (int q = 0; q <= n; ++q) lvo.off[q] = H->pt_off[q];
+    const int staged = H->pt_off[n] <= uint32_t(kStageRows) ? 1 : 0;
+    const size_t dyn = PER_DYN + (staged ? STAGE_DYN : 0);
     int occ = 0;
-    ANQS_CUDA(cudaFuncSetAttribute(sample_levels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(PER_DYN)));
-    ANQS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sample_levels_kernel, SMALL_T, PER_DYN));
+    ANQS_CUDA(cudaFuncSetAttribute(sample_levels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn)));
+    ANQS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sample_levels_kernel, SMALL_T, dyn));
     int dev = 0, sms = 0;
     ANQS_CUDA(cudaGetDevice(&dev));
     ANQS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1053,7 +1132,7 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(grid);
       cfg.blockDim = dim3(SMALL_T);
-      cfg.dynamicSmemBytes = PER_DYN;
+      cfg.dynamicSmemBytes = dyn;
       cfg.stream = s;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeCooperative;
@@ -1064,8 +1143,9 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
       note_launch();
       ANQS_CUDA_LAUNCH("sampler sample_levels_kernel",
                        cudaLaunchKernelEx(&cfg, sample_levels_kernel, H->v, n, n_samples, seed, counter, counter_dev,
-                                          static_cast<const float*>(P.plog), static_cast<const int32_t*>(H->d_pt_child),
-                                          P.child, F * 4, P.barrier, x_out, n_out, n_unique, status));
+                                          static_cast<const float*>(P.plog), static_cast<const uint64_t*>(H->d_pt_x),
+                                          static_cast<const int32_t*>(H->d_pt_child), lvo, staged, P.child, F * 4,
+                                          P.barrier, x_out, n_out, n_unique, status));
       return ANQS_OK;
     }
   }
