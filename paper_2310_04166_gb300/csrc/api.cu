@@ -149,9 +149,14 @@ static size_t vjp_ws_bytes(const anqs_model* M, uint64_t n_x, bool least = false
 
 static int vjp_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, const float* cl,
                         const float* cp, float* grad, float* part, void* ws, size_t ws_bytes, cudaStream_t s) {
-  if (M->d.kind == ANQS_MODEL_MLP)
-    return launch_mlp_fp32_grad(M->mlp, H->v, x, n_x, CotSrc{cl, cp, nullptr, nullptr, nullptr, nullptr}, grad, part,
-                                s);
+  if (M->d.kind == ANQS_MODEL_MLP) {
+    const CotSrc c{cl, cp, nullptr, nullptr, nullptr, nullptr};
+    // the tensor-core adjoint writes per-tile partial gradients (anqs_grad's
+    // workspace); anqs_logpsi_vjp, which has none for the MLP, stays in FP32
+    if (part && M->d.form == ANQS_FORM_BF16 && mlp_tc_grad_supported(M))
+      return launch_mlp_tc_grad(M, H->v, x, n_x, c, grad, part, s);
+    return launch_mlp_fp32_grad(M->mlp, H->v, x, n_x, c, grad, part, s);
+  }
   if (M->d.kind == ANQS_MODEL_TF) return launch_tf_fp32_grad(M->tf, H->v, x, n_x, cl, cp, grad, ws, ws_bytes, s);
   if (M->d.kind == ANQS_MODEL_NADE)
     return launch_nade_grad(M->nade, H->v, x, n_x, CotSrc{cl, cp, nullptr, nullptr, nullptr, nullptr}, grad,
@@ -1057,7 +1062,11 @@ int anqs_grad(const anqs_model* M, const anqs_ham* H, const uint64_t* x, const u
   const Count nc{n_x, n_x_dev, 1};
   // the MLP and NADE adjoints compute each row's cotangents themselves
   const CotSrc vmc{nullptr, nullptr, ere, eim, stats, counts};
-  if (M->d.kind == ANQS_MODEL_MLP) return launch_mlp_fp32_grad(M->mlp, H->v, x, nc, vmc, grad, part, s);
+  if (M->d.kind == ANQS_MODEL_MLP) {
+    if (M->d.form == ANQS_FORM_BF16 && mlp_tc_grad_supported(M))  // 16-bit forward and adjoint on the tensor cores
+      return launch_mlp_tc_grad(M, H->v, x, nc, vmc, grad, part, s);
+    return launch_mlp_fp32_grad(M->mlp, H->v, x, nc, vmc, grad, part, s);
+  }
   if (M->d.kind == ANQS_MODEL_NADE)
     return launch_nade_grad(M->nade, H->v, x, nc, vmc, grad, M->n_params, static_cast<float*>(tfws), s);
   ANQS_TRY(launch_grad_cotangents(ere, eim, counts, stats, nc, cl, cp, s));

@@ -48,6 +48,7 @@ enum ProfId {
   PROF_NADE_SLOT,
   PROF_NADE_PARENT,
   PROF_NADE_SUFFIX,
+  PROF_MLP_TC_GRAD,
   PROF_COUNT
 };
 
@@ -292,6 +293,11 @@ int launch_mlp_fp32_slot_logits(const MlpView& m, int p, const uint64_t* prefixe
                                 cudaStream_t s);
 // part: per-tile partial gradients (mlp_fp32_grad_partial_floats floats) or
 // null for atomic accumulation into grad (which must then be zeroed)
+int launch_grad_partial_sum(const float* part, Count n_x, uint64_t n_params, int rows_per_tile, float* g,
+                            cudaStream_t s);
+bool mlp_tc_grad_supported(const anqs_model* M);
+int launch_mlp_tc_grad(const anqs_model* M, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot,
+                       float* grad, float* part, cudaStream_t s);
 int launch_mlp_fp32_grad(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot,
                          float* grad, float* part, cudaStream_t s);
 size_t mlp_fp32_grad_partial_floats(const MlpView& m, uint64_t n_x);

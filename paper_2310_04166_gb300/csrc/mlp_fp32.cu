@@ -588,6 +588,15 @@ int launch_mlp_fp32_slot_logits(const MlpView& m, int p, const uint64_t* pre, co
   return set_error(ANQS_ERR_UNSUPPORTED, "width %d", m.width);
 }
 
+int launch_grad_partial_sum(const float* part, Count n_x, uint64_t n_params, int rows_per_tile, float* g,
+                            cudaStream_t s) {
+  ProfScope ps(PROF_GRAD_REDUCE, s);
+  ANQS_CUDA_LAUNCH("mlp partial_sum_kernel",
+                   launch_k(partial_sum_kernel, dim3(unsigned(std::min<uint64_t>((n_params + 255) / 256, 152 * 8))),
+                            dim3(256), 0, s, part, n_x, n_params, rows_per_tile, g));
+  return ANQS_OK;
+}
+
 size_t mlp_fp32_grad_partial_floats(const MlpView& m, uint64_t n_x) {
   const int rg = rg_for(m, n_x);
   return size_t((n_x + rg - 1) / rg) * m.slot_off[m.n];

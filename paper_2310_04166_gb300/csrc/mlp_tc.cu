@@ -718,6 +718,397 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_multi_kernel(const __grid_consta
   if (threadIdx.x < 32) tc::tmem_dealloc(s_tmem, NWG * W);
 }
 
+// ---- the adjoint (Eq. grad_def) on the tensor cores ------------------------
+//
+// One CTA of 128 threads per (128-row tile of the samples, slot p); thread t
+// owns sample row t and TMEM lane t.  It recomputes slot p's forward pass in
+// the 16-bit form (layer 1 from the hi part of W1), turns the cotangents of
+// log|psi| and arg psi into the head's adjoint, and runs the backward pass:
+//   data GEMMs    dh_{k-1} = dz_k W_k           (A: dz_k per row, B: W_k)
+//   weight GEMMs  dW_k = dz_k^T h_{k-1}, dW_1 = dz_1^T u, dW_h = dout^T h_L
+// The weight GEMMs reduce over the tile's rows, so their operands are the
+// same per-row tiles read as MN-major matrices (K = rows), and the data GEMMs
+// read the forward weight image as an MN-major B operand: no transposed copy
+// of anything is made.  Operands are fp16; the cotangents of each tile are
+// scaled by a power of two that puts their largest magnitude at 2^8 (the
+// gradient is linear in them; the scale is divided out, exactly, when the
+// tile's partial gradient is written).  Biases' gradients are column sums of
+// the dz tiles on the CUDA cores.  Each tile writes its slot's block of a
+// per-tile partial gradient; a reduction over the tiles follows.
+__device__ __forceinline__ int popc_alpha_tc(uint64_t x, int p) {
+  return __popcll(x & ((1ull << (2 * p)) - 1ull) & 0x5555555555555555ull);
+}
+__device__ __forceinline__ int popc_beta_tc(uint64_t x, int p) {
+  return __popcll(x & ((1ull << (2 * p)) - 1ull) & 0xAAAAAAAAAAAAAAAAull);
+}
+
+// offsets of slot p's parameter blocks in the flat parameter vector
+struct MlpPtrTc {
+  uint64_t W1, b1, Wk, Wh, bh;
+};
+__device__ __forceinline__ MlpPtrTc slot_ptrs_tc(const MlpView& m, int p) {
+  MlpPtrTc r;
+  const uint64_t w = uint64_t(m.width);
+  r.W1 = m.slot_off[p];
+  r.b1 = r.W1 + w * 4u * uint64_t(p);
+  r.Wk = r.b1 + w;
+  r.Wh = r.Wk + uint64_t(m.n_hidden - 1) * (w * w + w);
+  r.bh = r.Wh + 8u * w;
+  return r;
+}
+
+struct GradArgs {
+  TcView tv;
+  MlpView m;
+  HamView hv;
+  const uint64_t* xs;
+  Count n_x;
+  CotSrc cot;
+  float* part;  // [tiles][n_params]
+  uint64_t n_params;
+  uint32_t img_bytes, kmax1;  // image region (without W1's lo part), widest layer-1 input
+};
+
+// MN-major view of a tile stored per row in the canonical K-major layout with
+// `cols` columns: the MMA's K runs over the rows (16 per step), M or N over
+// the columns.
+__device__ __forceinline__ uint64_t mn_desc(uint32_t base, uint32_t cols, uint32_t ks) {
+  return tc::sdesc(base + ks * 2u * cols * 16u, cols * 16u, 128u);
+}
+
+__host__ __device__ constexpr uint32_t idesc_f16_mn(int M, int N, bool a_mn, bool b_mn) {
+  return tc::idesc_f16_f32(M, N) | (a_mn ? (1u << 15) : 0u) | (b_mn ? (1u << 16) : 0u);
+}
+
+template <int W>
+__global__ void __launch_bounds__(MT, 1) mlp_tc_grad_kernel(const __grid_constant__ GradArgs a) {
+  static_assert(W == 128, "the weight GEMMs put the layer width on the MMA's M = 128");
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bars[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ float s_max[4], s_bh[4][8];
+  __shared__ int s_abort;
+  constexpr uint32_t TILE = MT * W * 2u;
+  constexpr uint32_t C_ACC = 0, C_DW = W, C_DWH = 2 * W, C_DW1 = 2 * W + 32, NCOL = W == 128 ? 512 : 256;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int p = blockIdx.y, L = a.m.n_hidden;
+  const SlotLayout S = slot_layout(p, W, L, a.tv.lo);
+  const uint32_t k1 = S.k1, lo_bytes = S.wk - S.w1lo;
+  // shared memory: image (W1 hi | hidden | bias | head) | H_1..H_{L-1} | P1 | P2 | U | dout
+  unsigned char* img = smem;
+  const uint32_t o_wk = S.w1lo, o_bias = S.bias - lo_bytes, o_head = S.head - lo_bytes, o_hb = S.hbias - lo_bytes;
+  unsigned char* Hb = smem + a.img_bytes;
+  unsigned char* P1 = Hb + uint32_t(L - 1) * TILE;
+  unsigned char* P2 = P1 + TILE;
+  unsigned char* U = P2 + TILE;
+  unsigned char* DO = U + MT * a.kmax1 * 2u;
+  const uint32_t bar_w = tc::smem_u32(&bars[0]), bar_m = tc::smem_u32(&bars[1]);
+  if (t == 0) {
+    tc::mbar_init(bar_w, 1);
+    tc::mbar_init(bar_m, 1);
+    tc::fence_mbar_init();
+    s_abort = 0;
+    // the image, written by the packing kernel several launches back
+    const unsigned char* src = a.tv.img + a.tv.img_off[p];
+    tc::mbar_arrive_expect_tx(bar_w, S.w1lo + (S.bytes - S.wk));
+    if (S.w1lo) tc::bulk_g2s(tc::smem_u32(img), src, S.w1lo, bar_w);
+    tc::bulk_g2s(tc::smem_u32(img + o_wk), src + S.wk, S.bytes - S.wk, bar_w);
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_u32(&s_tmem), NCOL);
+    tc::tmem_relinquish();
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  ANQS_PDL_WAIT();
+  ANQS_PDL_TRIGGER();
+  const uint32_t tm = s_tmem, lb = uint32_t(t & ~31) << 16;
+  const uint64_t n_x = a.n_x.get();
+  const uint64_t row = uint64_t(blockIdx.x) * MT + t;
+  const bool valid = row < n_x;
+  const uint64_t x = valid ? a.xs[row] : 0ull;
+  float cla = 0.f, cph = 0.f;
+  if (valid) cot_of(a.cot, row, cla, cph);
+  // scale of the tile's cotangents: a power of two, largest magnitude -> 2^8
+  {
+    float mx = fmaxf(fabsf(cla), fabsf(cph));
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_max[warp] = mx;
+  }
+  // one-hot input of v_<p (layer 1's A operand and dW_1's B operand)
+  for (uint32_t k = 0; k < k1; k += 8) {
+    uint32_t w4[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint32_t lo = 0, hi = 0;
+      const uint32_t k0 = k + 2 * e, kk = k0 + 1;
+      if (k0 < 4u * p && ((x >> (2 * (k0 >> 2))) & 3ull) == (k0 & 3u)) lo = 0x3C00u;
+      if (kk < 4u * p && ((x >> (2 * (kk >> 2))) & 3ull) == (kk & 3u)) hi = 0x3C00u;
+      w4[e] = lo | (hi << 16);
+    }
+    *reinterpret_cast<uint4*>(U + tc::canon_off(t, k, k1)) = make_uint4(w4[0], w4[1], w4[2], w4[3]);
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  float mx = fmaxf(fmaxf(s_max[0], s_max[1]), fmaxf(s_max[2], s_max[3]));
+  int e2 = 0;
+  if (mx > 0.f) {
+    frexpf(mx, &e2);  // mx in [2^(e2-1), 2^e2)
+    e2 = 8 - e2;
+  }
+  const float sc = ldexpf(1.f, e2), inv_sc = ldexpf(1.f, -e2);
+  bool ok = __syncthreads_and(wait_bar(bar_w, 0));
+  uint32_t ph = 0;
+  auto mma_wait = [&]() -> bool {
+    const bool r = __syncthreads_and(wait_bar(bar_m, ph));
+    ph ^= 1;
+    tc::fence_after_sync();
+    return r;
+  };
+  const float* bias = reinterpret_cast<const float*>(img + o_bias);
+  const float4* head = reinterpret_cast<const float4*>(img + o_head);
+  const float* hbias = reinterpret_cast<const float*>(img + o_hb);
+  const uint32_t img_a = tc::smem_u32(img);
+  // ---- forward: h_1 .. h_{L-1} to their tiles, z_L left in TMEM ----
+  for (int layer = 0; ok && layer < L; ++layer) {
+    const uint32_t K = layer == 0 ? k1 : uint32_t(W);
+    if (K > 0) {
+      if (t == 0) {
+        tc::fence_after_sync();
+        const uint32_t a_addr = layer == 0 ? tc::smem_u32(U) : tc::smem_u32(Hb + uint32_t(layer - 1) * TILE);
+        const uint32_t b_addr = img_a + (layer == 0 ? 0u : o_wk + uint32_t(layer - 1) * W * W * 2u);
+        for (uint32_t ks = 0; ks < K / 16; ++ks)
+          tc::mma_f16(tm + C_ACC, tc::sdesc(a_addr + ks * 256u, 128u, K * 16u),
+                      tc::sdesc(b_addr + ks * 256u, 128u, K * 16u), tc::idesc_f16_f32(MT, W), ks > 0 ? 1u : 0u);
+        tc::mma_commit(bar_m);
+      }
+      ok = mma_wait();
+    }
+    if (!ok || layer == L - 1) break;
+    unsigned char* dst = Hb + uint32_t(layer) * TILE;
+    for (int c0 = 0; c0 < W; c0 += 32) {
+      float v[32];
+      if (K > 0) {
+        tc::tmem_ld32(tm + lb + C_ACC + uint32_t(c0), v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t u4[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int i = 8 * q + 2 * e;
+          u4[e] = tc::pack_f16x2(tc::tanh_fast(v[i] + bias[layer * W + c0 + i]),
+                                 tc::tanh_fast(v[i + 1] + bias[layer * W + c0 + i + 1]));
+        }
+        *reinterpret_cast<uint4*>(dst + tc::canon_off(t, c0 + 8 * q, W)) = make_uint4(u4[0], u4[1], u4[2], u4[3]);
+      }
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  const bool kL = (L == 1 ? k1 : uint32_t(W)) > 0;  // z_L is in TMEM (else it is zero)
+  // ---- head (f32) and the adjoint of its 8 outputs ----
+  float dout[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (ok) {
+    float out[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) out[o] = 0.f;
+    for (int c0 = 0; c0 < W; c0 += 32) {
+      float v[32];
+      if (kL) {
+        tc::tmem_ld32(tm + lb + C_ACC + uint32_t(c0), v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+#pragma unroll
+      for (int i = 0; i < 32; ++i) {
+        const float h = tc::tanh_fast(v[i] + bias[(L - 1) * W + c0 + i]);
+        const float4 w0 = head[(c0 + i) * 2], w1 = head[(c0 + i) * 2 + 1];
+        out[0] = fmaf(w0.x, h, out[0]);
+        out[1] = fmaf(w0.y, h, out[1]);
+        out[2] = fmaf(w0.z, h, out[2]);
+        out[3] = fmaf(w0.w, h, out[3]);
+        out[4] = fmaf(w1.x, h, out[4]);
+        out[5] = fmaf(w1.y, h, out[5]);
+        out[6] = fmaf(w1.z, h, out[6]);
+        out[7] = fmaf(w1.w, h, out[7]);
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 8; ++o) out[o] += hbias[o];
+    // d l_u = cot_la 1/2 (delta_uv - p~_u) over the allowed u; d phi_u = cot_ph delta_uv
+    if (valid) {
+      const unsigned pm = slot_mask(a.hv, p, popc_alpha_tc(x, p), popc_beta_tc(x, p), x), mk = norm_mask(a.hv, p, pm);
+      const int v = int((x >> (2 * p)) & 3ull);
+      if ((pm >> v) & 1u) {
+        float m = -INFINITY;
+        for (int u = 0; u < 4; ++u)
+          if ((mk >> u) & 1u) m = fmaxf(m, out[u]);
+        float ex[4], sum = 0.f;
+        for (int u = 0; u < 4; ++u) {
+          ex[u] = ((mk >> u) & 1u) ? __expf(out[u] - m) : 0.f;
+          sum += ex[u];
+        }
+        const float c = 0.5f * cla * sc;
+        for (int u = 0; u < 4; ++u) dout[u] = ((mk >> u) & 1u) ? c * ((u == v ? 1.f : 0.f) - ex[u] / sum) : 0.f;
+        dout[4 + v] = cph * sc;
+      }
+    }
+    // dout tile (fp16, 16 columns, 8..15 zero): B operand of dW_h
+    uint32_t d4[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) d4[e] = tc::pack_f16x2(dout[2 * e], dout[2 * e + 1]);
+    *reinterpret_cast<uint4*>(DO + tc::canon_off(t, 0, 16)) = make_uint4(d4[0], d4[1], d4[2], d4[3]);
+    *reinterpret_cast<uint4*>(DO + tc::canon_off(t, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
+    // h_L (fp16) to P1, dz_L = (W_h^T dout) (1 - h_L^2) to P2
+    for (int c0 = 0; c0 < W; c0 += 32) {
+      float v[32];
+      if (kL) {
+        tc::tmem_ld32(tm + lb + C_ACC + uint32_t(c0), v);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t hu[4], zu[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          float hh[2], zz[2];
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const int i = 8 * q + 2 * e + j, k = c0 + i;
+            const float h = tc::tanh_fast(v[i] + bias[(L - 1) * W + k]);
+            const float4 w0 = head[k * 2], w1 = head[k * 2 + 1];
+            float dh = w0.x * dout[0];
+            dh = fmaf(w0.y, dout[1], dh);
+            dh = fmaf(w0.z, dout[2], dh);
+            dh = fmaf(w0.w, dout[3], dh);
+            dh = fmaf(w1.x, dout[4], dh);
+            dh = fmaf(w1.y, dout[5], dh);
+            dh = fmaf(w1.z, dout[6], dh);
+            dh = fmaf(w1.w, dout[7], dh);
+            hh[j] = h;
+            zz[j] = dh * (1.f - h * h);
+          }
+          hu[e] = tc::pack_f16x2(hh[0], hh[1]);
+          zu[e] = tc::pack_f16x2(zz[0], zz[1]);
+        }
+        *reinterpret_cast<uint4*>(P1 + tc::canon_off(t, c0 + 8 * q, W)) = make_uint4(hu[0], hu[1], hu[2], hu[3]);
+        *reinterpret_cast<uint4*>(P2 + tc::canon_off(t, c0 + 8 * q, W)) = make_uint4(zu[0], zu[1], zu[2], zu[3]);
+      }
+    }
+  }
+  // d b_h: column sums of dout over the rows (f32, warp shuffles)
+#pragma unroll
+  for (int o = 0; o < 8; ++o) {
+    float sum = dout[o];
+    for (int d = 16; d; d >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, d);
+    if (lane == 0) s_bh[warp][o] = sum;
+  }
+  tc::fence_async_smem();
+  tc::fence_before_sync();
+  __syncthreads();
+  const MlpPtrTc P = slot_ptrs_tc(a.m, p);
+  float* gbase = a.part + uint64_t(blockIdx.x) * a.n_params;
+  if (t < 8) gbase[P.bh + t] = (s_bh[0][t] + s_bh[1][t] + s_bh[2][t] + s_bh[3][t]) * inv_sc;
+  // ---- backward: step k = L .. 1; dz_k in Z, the next dz into the other buffer ----
+  unsigned char* Z = P2;
+  unsigned char* Zn = P1;
+  for (int k = L; ok && k >= 1; --k) {
+    const bool first = (k == L);
+    // dW_k's B operand: h_{k-1} (U for k = 1); it has k1 columns at k = 1
+    const uint32_t hprev = k == 1 ? tc::smem_u32(U) : tc::smem_u32(Hb + uint32_t(k - 2) * TILE);
+    const uint32_t ncols = k == 1 ? k1 : uint32_t(W);
+    if (t == 0) {
+      tc::fence_after_sync();
+      const uint32_t z = tc::smem_u32(Z);
+      if (first)  // dW_h^T[k][o] = sum_r h_L[r][k] dout[r][o]
+        for (uint32_t ks = 0; ks < MT / 16; ++ks)
+          tc::mma_f16(tm + C_DWH, mn_desc(tc::smem_u32(P1), W, ks), mn_desc(tc::smem_u32(DO), 16, ks),
+                      idesc_f16_mn(MT, 16, true, true), ks > 0 ? 1u : 0u);
+      if (k >= 2)  // dh_{k-1} = dz_k W_k
+        for (uint32_t ks = 0; ks < W / 16; ++ks)
+          tc::mma_f16(tm + C_ACC, tc::sdesc(z + ks * 256u, 128u, W * 16u),
+                      mn_desc(img_a + o_wk + uint32_t(k - 2) * W * W * 2u, W, ks),
+                      idesc_f16_mn(MT, W, false, true), ks > 0 ? 1u : 0u);
+      if (ncols > 0)  // dW_k = dz_k^T h_{k-1}
+        for (uint32_t ks = 0; ks < MT / 16; ++ks)
+          tc::mma_f16(tm + (k == 1 ? C_DW1 : C_DW), mn_desc(z, W, ks), mn_desc(hprev, ncols, ks),
+                      idesc_f16_mn(MT, int(ncols), true, true), ks > 0 ? 1u : 0u);
+      tc::mma_commit(bar_m);
+    }
+    ok = mma_wait();
+    if (!ok) break;
+    // dz_{k-1} = dh_{k-1} (1 - h_{k-1}^2), h_{k-1} from its tile
+    if (k >= 2) {
+      const unsigned char* hp = Hb + uint32_t(k - 2) * TILE;
+      for (int c0 = 0; c0 < W; c0 += 32) {
+        float v[32];
+        tc::tmem_ld32(tm + lb + C_ACC + uint32_t(c0), v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint4 h4 = *reinterpret_cast<const uint4*>(hp + tc::canon_off(t, c0 + 8 * q, W));
+          const uint32_t hw[4] = {h4.x, h4.y, h4.z, h4.w};
+          uint32_t zu[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 h2 = __half22float2(*reinterpret_cast<const __half2*>(&hw[e]));
+            zu[e] = tc::pack_f16x2(v[8 * q + 2 * e] * (1.f - h2.x * h2.x), v[8 * q + 2 * e + 1] * (1.f - h2.y * h2.y));
+          }
+          *reinterpret_cast<uint4*>(Zn + tc::canon_off(t, c0 + 8 * q, W)) = make_uint4(zu[0], zu[1], zu[2], zu[3]);
+        }
+      }
+    }
+    // dW_k (lane t = output unit t), unscaled, to the tile's partial gradient
+    if (ncols > 0) {
+      float* gw = gbase + (k == 1 ? P.W1 : P.Wk + uint64_t(k - 2) * (uint64_t(W) * W + W)) + uint64_t(t) * (k == 1 ? 4u * p : W);
+      const uint32_t nvalid = k == 1 ? 4u * p : uint32_t(W);
+      for (uint32_t c0 = 0; c0 < ncols; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tm + lb + (k == 1 ? C_DW1 : C_DW) + c0, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (c0 + i < nvalid) gw[c0 + i] = v[i] * inv_sc;
+      }
+    }
+    if (first) {  // dW_h[o][t]
+      float v[8];
+      tc::tmem_ld8(tm + lb + C_DWH, v);
+#pragma unroll
+      for (int o = 0; o < 8; ++o) gbase[P.Wh + uint64_t(o) * W + t] = v[o] * inv_sc;
+    }
+    // d b_k: column sums of dz_k (unit t)
+    if (t < W) {
+      float sum = 0.f;
+      for (int r = 0; r < MT; r += 8) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+          sum += __half2float(*reinterpret_cast<const __half*>(Z + tc::canon_off(r + j, t, W)));
+      }
+      gbase[(k == 1 ? P.b1 : P.Wk + uint64_t(k - 2) * (uint64_t(W) * W + W) + uint64_t(W) * W) + t] = sum * inv_sc;
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    unsigned char* tmp = Z;
+    Z = Zn;
+    Zn = tmp;
+  }
+  if (!ok && t == 0) atomicExch(a.tv.status, ST_TIMEOUT);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tm, NCOL);
+}
+
 // One CTA of AT threads per parent x (grid-stride over the parents), its
 // threads over the connected x': log psi(x') = parent prefix up to slot j +
 // parent slot-j term of v'_j + the terms T[x'][p] of the slots p > j; then
@@ -1209,6 +1600,55 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count
     ANQS_TRY(tv.W == 128 ? launch_ws_w<128>(tv, H->v, w, s) : launch_ws_w<64>(tv, H->v, w, s));
   }
   return eloc_tc_post(H, n_x, ere, eim, ws, ws_bytes, s);
+}
+
+// Shared memory of the tensor-core adjoint of model M (0 when it does not
+// apply: width other than 128, more than 3 hidden layers, or too large).
+static size_t tc_grad_smem(const anqs_model* M, uint32_t* img_bytes, uint32_t* kmax1) {
+  const int n = M->d.n_orb, W = M->d.width, L = M->d.n_hidden;
+  if (W != 128 || L < 1 || L > 3) return 0;
+  const int lo = use_w1_split(n, W, L);
+  uint32_t img = 0, k1 = 0;
+  for (int p = 0; p < n; ++p) {
+    const SlotLayout S = slot_layout(p, W, L, lo);
+    img = std::max(img, S.w1lo + (S.bytes - S.wk));
+    k1 = std::max(k1, S.k1);
+  }
+  img = round_up(img, 1024u);
+  if (img_bytes) *img_bytes = img;
+  if (kmax1) *kmax1 = k1;
+  const size_t tile = size_t(MT) * W * 2;
+  const size_t sm = size_t(img) + size_t(L - 1) * tile + 2 * tile + size_t(MT) * k1 * 2 + size_t(MT) * 16 * 2;
+  return sm <= kSmemLimit ? sm : 0;
+}
+
+bool mlp_tc_grad_supported(const anqs_model* M) { return tc_grad_smem(M, nullptr, nullptr) > 0; }
+
+// The VMC gradient of a 16-bit MLP on the tensor cores: per-tile partial
+// gradients in `part` ([tiles][n_params], tiles of 128 rows), then their sum.
+int launch_mlp_tc_grad(const anqs_model* M, const HamView& hv, const uint64_t* x, Count n_x, const CotSrc& cot,
+                       float* grad, float* part, cudaStream_t s) {
+  GradArgs a{};
+  const size_t sm = tc_grad_smem(M, &a.img_bytes, &a.kmax1);
+  if (!sm) return set_error(ANQS_ERR_UNSUPPORTED, "tensor-core adjoint does not apply to this model");
+  if (!part) return set_error(ANQS_ERR_ARG, "tensor-core adjoint needs the partial-gradient workspace");
+  a.tv = make_view(M);
+  a.m = M->mlp;
+  a.hv = hv;
+  a.xs = x;
+  a.n_x = n_x;
+  a.cot = cot;
+  a.part = part;
+  a.n_params = M->mlp.slot_off[M->mlp.n];
+  const uint64_t tiles = std::max<uint64_t>((n_x.n + MT - 1) / MT, 1);
+  if (tiles > 0x7fffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "too many rows");
+  ANQS_CUDA(cudaFuncSetAttribute(mlp_tc_grad_kernel<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm)));
+  {
+    ProfScope ps(PROF_MLP_TC_GRAD, s);
+    ANQS_CUDA_LAUNCH("mlp_tc_grad_kernel", launch_k(mlp_tc_grad_kernel<128>, dim3(unsigned(tiles), unsigned(M->d.n_orb)),
+                                                    dim3(MT), sm, s, a));
+  }
+  return launch_grad_partial_sum(part, n_x, a.n_params, MT, grad, s);
 }
 
 int mlp_tc_multi_max() { return kMaxBatch; }

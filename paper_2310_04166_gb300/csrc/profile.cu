@@ -32,7 +32,7 @@ const char* kNames[PROF_COUNT] = {
     "finalize_kernel",        "grad_partial_sum_kernel", "unused",              "tf_fp32_grad_kernels",
     "tf_tc_parent_kernel",    "tf_tc_suffix_kernel",  "tf_tc_slot_kernel",
     "nade_logpsi_kernel", "nade_grad_kernel", "nade_slot_kernel",
-    "nade_parent_kernel",    "nade_suffix_kernel"};
+    "nade_parent_kernel",    "nade_suffix_kernel",   "mlp_tc_grad_kernel"};
 
 cudaEvent_t get_event() {
   if (!g_pool.empty()) {

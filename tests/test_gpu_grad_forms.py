@@ -69,3 +69,67 @@ def test_16bit_form_gradient_against_oracle(A, name, Ns, keep):
     rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
     d = np.abs(ere.cpu().numpy() - e_ref.real)
     assert rel < BAR, (rel, d.max(), np.sqrt(s_ref[2]))
+
+
+def _batch_problem(A, k, n_samples):
+    from synthetic import batch32_problem, flatten_mlp, mlp_params
+    p = batch32_problem(k)
+    ham = A.Hamiltonian(p["h"], p["g"], p["e_nuc"], p["n_alpha"], p["n_beta"])
+    P = mlp_params(p["seed"], p["n"], p["width"], p["n_hidden"], 0.2)
+    model = A.Model.mlp(p["n"], p["width"], p["n_hidden"], torch.tensor(flatten_mlp(P), device="cuda"), "bf16")
+    om = MLPAnsatz(P, p["n"])
+    ip = molecular_isphys(p["n"], p["n_alpha"], p["n_beta"])
+    oham = OHam(p["h"], p["g"], p["e_nuc"], p["n_alpha"], p["n_beta"])
+    return ham, model, om, ip, oham
+
+
+@pytest.mark.parametrize("case", ["h2o", "batch14", "batch0"])
+def test_tensor_core_adjoint_against_oracle(A, case):
+    """The 16-bit MLP's adjoint (tcgen05, fp16 operands, per-tile scaled
+    cotangents) with the oracle's own local energies as input, so that only
+    the adjoint's arithmetic differs: relative L2 error below 5e-4 (the CPU
+    emulation of its rounding gives about 2e-4 on h2o).  h2o: 441 rows, four
+    tiles, the last one partial; problem 14 of the 32-problem workload (7
+    orbitals); problem 0 (12 orbitals, 10+10 electrons: the widest layer-1
+    input the kernel takes)."""
+    if case == "h2o":
+        w, ham, model, om, ip, oham = _problem(A, "h2o")
+        Ns = 100_000
+    else:
+        ham, model, om, ip, oham = _batch_problem(A, int(case[5:]), 20_000)
+        Ns = 20_000
+    x, c = A.sample(model, ham, Ns, seed=31)
+    if x.numel() > 600:
+        order = torch.argsort(c.cpu(), descending=True, stable=True)[:600].to(x.device)
+        x, c = x[order].contiguous(), c[order].contiguous()
+    xs, cs = x.cpu().numpy().astype(np.uint64), c.cpu().numpy()
+    e_ref = local_energy(om, ip, oham, xs)
+    s_ref = energy_stats(e_ref, cs)
+    g = A.grad(model, ham, x, c, torch.tensor(e_ref.real, device="cuda"), torch.tensor(e_ref.imag, device="cuda"),
+               torch.tensor(s_ref, device="cuda")).cpu().numpy().astype(np.float64)
+    assert model.status() == 0
+    g_ref = np.concatenate([t.reshape(-1).numpy() for t in gradient(om, ip, xs, cs, e_ref, s_ref)])
+    rel = np.linalg.norm(g - g_ref) / np.linalg.norm(g_ref)
+    assert rel < 5e-4, rel
+    # every parameter block is written: slot 0's first-layer bias and the heads too
+    assert np.isfinite(g).all()
+
+
+def test_tensor_core_adjoint_with_device_row_count(A):
+    """The bench's shape: capacity rows on the host, the unique count on the
+    device; tiles past the count contribute nothing."""
+    w, ham, model, om, ip, oham = _problem(A, "h2o")
+    x, c = A.sample(model, ham, 100_000, seed=32)
+    k = x.numel()
+    cap = k + 300
+    xb = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    cb = torch.zeros(cap, dtype=torch.int64, device="cuda")
+    xb[:k], cb[:k] = x, c
+    ere, eim, st = A.local_energy(model, ham, x, c)
+    erb = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    eib = torch.zeros(cap, dtype=torch.float64, device="cuda")
+    erb[:k], eib[:k] = ere, eim
+    g1 = A.grad(model, ham, x, c, ere, eim, st)
+    nd = torch.tensor([k], dtype=torch.int64, device="cuda")
+    g2 = A.grad(model, ham, xb, cb, erb, eib, st, n_dev=nd)
+    assert torch.equal(g1, g2)
