@@ -732,9 +732,10 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_multi_kernel(const __grid_consta
 // of anything is made.  Operands are fp16; the cotangents of each tile are
 // scaled by a power of two that puts their largest magnitude at 2^8 (the
 // gradient is linear in them; the scale is divided out, exactly, when the
-// tile's partial gradient is written).  Biases' gradients are column sums of
-// the dz tiles on the CUDA cores.  Each tile writes its slot's block of a
-// per-tile partial gradient; a reduction over the tiles follows.
+// tile's partial gradient is written).  Biases' gradients are the column sums
+// of the dz tiles, one more small MMA per layer against the dout tile, whose
+// column 8 holds ones.  Each tile writes its slot's block of a per-tile
+// partial gradient; a reduction over the tiles follows.
 __device__ __forceinline__ int popc_alpha_tc(uint64_t x, int p) {
   return __popcll(x & ((1ull << (2 * p)) - 1ull) & 0x5555555555555555ull);
 }
@@ -789,12 +790,13 @@ __global__ void __launch_bounds__(MT, 1) mlp_tc_grad_kernel(const __grid_constan
   __shared__ float s_max[4], s_bh[4][8];
   __shared__ int s_abort;
   constexpr uint32_t TILE = MT * W * 2u;
-  constexpr uint32_t C_ACC = 0, C_DW = W, C_DWH = 2 * W, C_DW1 = 2 * W + 32, NCOL = W == 128 ? 512 : 256;
+  constexpr uint32_t C_ACC = 0, C_DW = W, C_DWH = 2 * W, C_DB = 2 * W + 16, C_DW1 = 2 * W + 32,
+                     NCOL = W == 128 ? 512 : 256;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int p = blockIdx.y, L = a.m.n_hidden;
   const SlotLayout S = slot_layout(p, W, L, a.tv.lo);
   const uint32_t k1 = S.k1, lo_bytes = S.wk - S.w1lo;
-  // shared memory: image (W1 hi | hidden | bias | head) | H_1..H_{L-1} | P1 | P2 | U | dout
+  // shared memory: image (W1 hi | hidden | bias | head) | H_1..H_{L-1} | P1 | P2 | U | dout (and ones)
   unsigned char* img = smem;
   const uint32_t o_wk = S.w1lo, o_bias = S.bias - lo_bytes, o_head = S.head - lo_bytes, o_hb = S.hbias - lo_bytes;
   unsigned char* Hb = smem + a.img_bytes;
@@ -961,12 +963,13 @@ __global__ void __launch_bounds__(MT, 1) mlp_tc_grad_kernel(const __grid_constan
         dout[4 + v] = cph * sc;
       }
     }
-    // dout tile (fp16, 16 columns, 8..15 zero): B operand of dW_h
+    // dout tile (fp16, 16 columns: dout, then a one in column 8): B operand of
+    // dW_h and of the bias sums
     uint32_t d4[4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) d4[e] = tc::pack_f16x2(dout[2 * e], dout[2 * e + 1]);
     *reinterpret_cast<uint4*>(DO + tc::canon_off(t, 0, 16)) = make_uint4(d4[0], d4[1], d4[2], d4[3]);
-    *reinterpret_cast<uint4*>(DO + tc::canon_off(t, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
+    *reinterpret_cast<uint4*>(DO + tc::canon_off(t, 8, 16)) = make_uint4(0x3C00u, 0u, 0u, 0u);
     // h_L (fp16) to P1, dz_L = (W_h^T dout) (1 - h_L^2) to P2
     for (int c0 = 0; c0 < W; c0 += 32) {
       float v[32];
@@ -1043,6 +1046,9 @@ __global__ void __launch_bounds__(MT, 1) mlp_tc_grad_kernel(const __grid_constan
         for (uint32_t ks = 0; ks < MT / 16; ++ks)
           tc::mma_f16(tm + (k == 1 ? C_DW1 : C_DW), mn_desc(z, W, ks), mn_desc(hprev, ncols, ks),
                       idesc_f16_mn(MT, int(ncols), true, true), ks > 0 ? 1u : 0u);
+      for (uint32_t ks = 0; ks < MT / 16; ++ks)  // db_k = dz_k^T 1 (column 8)
+        tc::mma_f16(tm + C_DB, mn_desc(z, W, ks), mn_desc(tc::smem_u32(DO), 16, ks), idesc_f16_mn(MT, 16, true, true),
+                    ks > 0 ? 1u : 0u);
       tc::mma_commit(bar_m);
     }
     ok = mma_wait();
@@ -1085,15 +1091,10 @@ __global__ void __launch_bounds__(MT, 1) mlp_tc_grad_kernel(const __grid_constan
 #pragma unroll
       for (int o = 0; o < 8; ++o) gbase[P.Wh + uint64_t(o) * W + t] = v[o] * inv_sc;
     }
-    // d b_k: column sums of dz_k (unit t)
-    if (t < W) {
-      float sum = 0.f;
-      for (int r = 0; r < MT; r += 8) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-          sum += __half2float(*reinterpret_cast<const __half*>(Z + tc::canon_off(r + j, t, W)));
-      }
-      gbase[(k == 1 ? P.b1 : P.Wk + uint64_t(k - 2) * (uint64_t(W) * W + W) + uint64_t(W) * W) + t] = sum * inv_sc;
+    {  // d b_k[t]
+      float v[8];
+      tc::tmem_ld8(tm + lb + C_DB + 8u, v);
+      gbase[(k == 1 ? P.b1 : P.Wk + uint64_t(k - 2) * (uint64_t(W) * W + W) + uint64_t(W) * W) + t] = v[0] * inv_sc;
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
