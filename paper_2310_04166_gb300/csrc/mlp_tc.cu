@@ -1073,16 +1073,33 @@ __global__ void __launch_bounds__(MT, 1) mlp_tc_grad_kernel(const __grid_constan
         }
       }
     }
-    // dW_k (lane t = output unit t), unscaled, to the tile's partial gradient
+    // dW_k (lane t = output unit t), unscaled, to the tile's partial gradient:
+    // 32 columns at a time through shared memory (dz_k's tile, free now), so
+    // that each warp store covers 32 consecutive columns of one row
     if (ncols > 0) {
-      float* gw = gbase + (k == 1 ? P.W1 : P.Wk + uint64_t(k - 2) * (uint64_t(W) * W + W)) + uint64_t(t) * (k == 1 ? 4u * p : W);
-      const uint32_t nvalid = k == 1 ? 4u * p : uint32_t(W);
-      for (uint32_t c0 = 0; c0 < ncols; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tm + lb + (k == 1 ? C_DW1 : C_DW) + c0, v);
+      float* gw = gbase + (k == 1 ? P.W1 : P.Wk + uint64_t(k - 2) * (uint64_t(W) * W + W));
+      const uint32_t ld = k == 1 ? 4u * p : uint32_t(W), nvalid = ld;
+      float* stage = reinterpret_cast<float*>(Z);  // [128][33]
+      for (uint32_t c0 = 0; c0 < ncols; c0 += 32) {
+        float v[32];
+        if (c0 + 32 <= ncols) {
+          tc::tmem_ld32(tm + lb + (k == 1 ? C_DW1 : C_DW) + c0, v);
+        } else {
+          float v16[16];
+          tc::tmem_ld16(tm + lb + (k == 1 ? C_DW1 : C_DW) + c0, v16);
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (c0 + i < nvalid) gw[c0 + i] = v[i] * inv_sc;
+          for (int i = 0; i < 16; ++i) {
+            v[i] = v16[i];
+            v[16 + i] = 0.f;
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) stage[t * 33 + i] = v[i];
+        __syncthreads();
+        const uint32_t c = c0 + uint32_t(lane);
+        if (c < nvalid)
+          for (int r = warp; r < MT; r += 4) gw[uint64_t(r) * ld + c] = stage[r * 33 + lane] * inv_sc;
+        __syncthreads();
       }
     }
     if (first) {  // dW_h[o][t]
