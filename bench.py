@@ -949,7 +949,7 @@ def _tc_work(A, ham, model, w, x):
         slot += len(pre) * f[p]
     eloc_bytes = float((8 + 1 + 8 + 8 + 8 * (n - 1 - j)).sum())
     return {"mlp_tc_suffix_kernel": suffix, "mlp_tc_parent_kernel": parent, "mlp_tc_slot_kernel": slot,
-            "mlp_fp32_grad_kernel": 3.0 * parent, "eloc_assemble_kernel": eloc_bytes,
+            "mlp_fp32_grad_kernel": 3.0 * parent, "mlp_tc_grad_kernel": 3.0 * parent, "eloc_assemble_kernel": eloc_bytes,
             "connected_kernel": float(len(j) * (8 + 8 + 1) + len(x) * 8)}
 
 
