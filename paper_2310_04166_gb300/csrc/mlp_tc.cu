@@ -1198,18 +1198,23 @@ __global__ void __launch_bounds__(AT) eloc_assemble_kernel(int n, uint32_t K, Co
 __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x_,
                                 const float* __restrict__ raw, float* __restrict__ la_out, float* __restrict__ ph_out,
                                 float* __restrict__ cache) {
+  // one warp per row, lane p = slot p (n <= 32): the slots' loads go out
+  // together; the prefix sums are passed from lane to lane in slot order, so
+  // they are added in the same order as a running sum over the slots
   ANQS_PDL_ENTRY();
-  const int n = hv.n;
+  const int n = hv.n, lane = threadIdx.x & 31;
   const uint64_t n_x = n_x_.get();
-  for (uint64_t l = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; l < n_x; l += uint64_t(gridDim.x) * blockDim.x) {
+  const uint64_t w0 = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nw = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t l = w0; l < n_x; l += nw) {
     const uint64_t x = xs[l];
-    float la = 0.f, ph = 0.f;
-    bool dead = (n < 32) && ((x >> (2 * n)) != 0);
-    // prefix electron counts from popcounts (not a running sum), so that the
-    // slots' loads do not wait on one another
-#pragma unroll 4
-    for (int p = 0; p < n; ++p) {
-      const float* o = raw + (l * n + p) * 8;
+    const int p = lane;
+    float tla = 0.f, tph = 0.f;
+    bool ok = true;
+    if (p < n) {
+      const float4* o4 = reinterpret_cast<const float4*>(raw + (l * n + p) * 8);
+      const float4 q0 = o4[0], q1 = o4[1];
+      const float o[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
       const uint64_t below = (1ull << (2 * p)) - 1ull;  // p < 32
       const int a = __popcll(x & below & 0x5555555555555555ull), b = __popcll(x & below & 0xAAAAAAAAAAAAAAAAull);
       const unsigned pmk = slot_mask(hv, p, a, b, x), mk = norm_mask(hv, p, pmk);
@@ -1222,20 +1227,43 @@ __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Cou
       const float lse = mx + __logf(s);
       if (cache) {
         float* cc = cache + (l * n + p) * CACHE_F;
-        cc[0] = la;
-        cc[1] = ph;
         for (int u = 0; u < 4; ++u) {
           cc[2 + u] = ((pmk >> u) & 1u) ? 0.5f * (o[u] - lse) : -INFINITY;
           cc[6 + u] = o[4 + u];
         }
       }
       const int v = int((x >> (2 * p)) & 3ull);
-      if (!((pmk >> v) & 1u)) dead = true;
-      if (!dead) la += 0.5f * (o[v] - lse);
-      ph += o[4 + v];
+      ok = (pmk >> v) & 1u;
+      if (ok) tla = 0.5f * (o[v] - lse);
+      tph = o[4 + v];
     }
-    la_out[l] = dead ? -INFINITY : la;
-    ph_out[l] = ph;
+    // a row is dead from its first unphysical slot on (from the start if it
+    // has bits above its 2n qubits): its later slots add nothing to la
+    const bool high = (n < 32) && ((x >> (2 * n)) != 0);
+    const unsigned bad = __ballot_sync(0xffffffffu, !ok);
+    const int first_bad = high ? 0 : bad ? __ffs(bad) - 1 : 32;
+    if (p >= first_bad) tla = 0.f;
+    float run_la = 0.f, run_ph = 0.f;  // sum over the slots before p
+    for (int k = 1; k < n; ++k) {
+      const float il = __shfl_sync(0xffffffffu, run_la + tla, k - 1);
+      const float ip = __shfl_sync(0xffffffffu, run_ph + tph, k - 1);
+      if (lane == k) {
+        run_la = il;
+        run_ph = ip;
+      }
+    }
+    if (cache && p < n) {
+      float* cc = cache + (l * n + p) * CACHE_F;
+      cc[0] = run_la;
+      cc[1] = run_ph;
+    }
+    const float tot_la = __shfl_sync(0xffffffffu, run_la + tla, n - 1);
+    const float tot_ph = __shfl_sync(0xffffffffu, run_ph + tph, n - 1);
+    if (lane == 0) {
+      const bool dead = bad != 0 || high;
+      la_out[l] = dead ? -INFINITY : tot_la;
+      ph_out[l] = tot_ph;
+    }
   }
 }
 
@@ -1395,8 +1423,8 @@ int launch_slots(const anqs_model* M, const TileArgs& ta, cudaStream_t s, int pr
 
 int launch_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
                     float* cache, cudaStream_t s) {
-  uint64_t blocks = (n_x.n + 127) / 128;
-  if (blocks > 152 * 8) blocks = 152 * 8;
+  uint64_t blocks = (n_x.n + 3) / 4;  // four rows (warps) per CTA of 128 threads
+  if (blocks > 152 * 16) blocks = 152 * 16;
   ANQS_CUDA_LAUNCH("finalize_kernel", launch_k(finalize_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(128), 0, s, hv, x, n_x, raw, la, ph, cache));
   return ANQS_OK;
 }
