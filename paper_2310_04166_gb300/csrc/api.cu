@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace anqs {
@@ -882,6 +884,10 @@ int anqs_batched_local_energy(anqs_batch* b, const anqs_eloc_problem* q, int n, 
   for (int k = 0; k < n; ++k)
     if (fused[size_t(k)])
       multi.push_back(MultiEloc{q[k].model, q[k].ham, q[k].n_x, q[k].workspace_dev, q[k].workspace_bytes});
+  // Host-side fault injection for tests of this error path: ANQS_BATCH_FAIL_AT=k
+  // makes problem k fail as a queueing error would, after its stream was forked.
+  int fail_at = -1;
+  if (const char* e = getenv("ANQS_BATCH_FAIL_AT")) fail_at = atoi(e);
   ANQS_CUDA(cudaEventRecord(b->fork, s));
   // join[k]: the last event recorded on problem k's stream (0 none, 1 pre, 2 done)
   std::vector<int> join(size_t(n), 0);
@@ -896,7 +902,10 @@ int anqs_batched_local_energy(anqs_batch* b, const anqs_eloc_problem* q, int n, 
       break;
     }
     const Count nc{q[k].n_x, q[k].n_x_dev, 1};
-    if (fused[size_t(k)]) {
+    if (k == fail_at) {
+      r = set_error(ANQS_ERR_CUDA, "batched local energy: injected failure at problem %d", k);
+      if (cudaEventRecord(b->done[k], sk) == cudaSuccess) join[k] = 2;
+    } else if (fused[size_t(k)]) {
       r = eloc_tc_pre(q[k].model, q[k].ham, q[k].x_dev, nc, q[k].workspace_dev, q[k].workspace_bytes, sk);
       if (cudaEventRecord(b->pre[k], sk) == cudaSuccess) join[k] = 1;
       else fail("event record");

@@ -224,3 +224,52 @@ def test_batched_step_with_persistent_launch_equals_each_problem_alone(A):
         assert torch.equal(a.ere[:k], b.ere[:k])
         assert torch.equal(a.g, b.g)
         assert int(a.ctr.item()) == int(b.ctr.item()) == 3
+
+
+@pytest.mark.parametrize("fail_at", [1, 3])
+def test_batched_local_energy_error_after_fork_joins_every_stream(A, fail_at, monkeypatch):
+    """A problem that fails after its stream was forked (a host-side injected
+    error, ANQS_BATCH_FAIL_AT): the call returns ANQS_ERR_CUDA, the problems
+    queued before it complete, and the caller's stream is joined to every
+    forked stream, eagerly and inside a CUDA-graph capture (which then ends
+    without unjoined work)."""
+    items = _mlp_items(A, [0, 3, 5], n_samples=10_000)  # 16-bit MLPs (persistent launch) and one width-64 MLP
+    alone = [A.local_energy(it["model"], it["ham"], it["x"], it["counts"]) for it in items]
+    outs = [(torch.full_like(r, float("nan")), torch.full_like(i, float("nan")), torch.full_like(st, float("nan")))
+            for r, i, st in alone]
+    its = [dict(it, out=o) for it, o in zip(items, outs)]
+    batch = A.EnergyBatch(len(its))
+    batch.set_schedule(_lib_mode(A, "streams"), 8)
+    monkeypatch.setenv("ANQS_BATCH_FAIL_AT", str(fail_at))
+    with pytest.raises(A.AnqsError, match="injected failure"):
+        batch.local_energy(its)
+    torch.cuda.synchronize()
+    for k in range(fail_at):  # queued before the failure: complete and right
+        assert torch.equal(outs[k][0], alone[k][0])
+    # the persistent path: the failure stops the launch; nothing is left running
+    batch.set_schedule(_lib_mode(A, "dynamic"), 8)
+    with pytest.raises(A.AnqsError, match="injected failure"):
+        batch.local_energy(its)
+    torch.cuda.synchronize()
+    # inside a capture: the error is raised, and the capture ends cleanly
+    ws = [A._ws(A.local_energy_workspace_bytes(it["model"], it["ham"], it["x"].numel()), it["x"].device) for it in its]
+    its_ws = [dict(it, workspace=w) for it, w in zip(its, ws)]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(side):
+        with pytest.raises(A.AnqsError, match="injected failure"):
+            with torch.cuda.graph(graph, stream=side):
+                batch.local_energy(its_ws, stream=side)
+    torch.cuda.synchronize()
+    monkeypatch.delenv("ANQS_BATCH_FAIL_AT")
+    got = batch.local_energy(its_ws)  # the handle still works
+    torch.cuda.synchronize()
+    for (ar, ai, ast), (br, bi, bst) in zip(alone, got):
+        assert torch.equal(ar, br) and torch.equal(ai, bi) and torch.equal(ast, bst)
+
+
+def _lib_mode(A, name):
+    from paper_2310_04166_gb300 import _lib
+    return {"streams": _lib.ANQS_BATCH_STREAMS, "static": _lib.ANQS_BATCH_STATIC,
+            "dynamic": _lib.ANQS_BATCH_DYNAMIC}[name]
