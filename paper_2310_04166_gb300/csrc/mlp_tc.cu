@@ -16,8 +16,9 @@
 // (fp16 operands, f32 accumulation in TMEM).  Epilogues read the
 // accumulator from TMEM, add the bias and apply tanh in f32, and write the
 // fp16 activations back as the next A operand; the last hidden layer feeds
-// the f32 head (8 outputs) on the CUDA cores, then the masked log-softmax
-// (Appendix B.1 f3 with MU masking, Sec. III.C) in f32.
+// the head (8 outputs) as one more MMA with N = 16 and the head's weights as
+// fp16 hi + lo parts, then the masked log-softmax (Appendix B.1 f3 with MU
+// masking, Sec. III.C) in f32.
 //
 // Modes
 //   PARENT  rows = unique samples x, all slots; writes log psi(x) and, per
@@ -61,6 +62,7 @@ struct SlotLayout {
   uint32_t bias;    // [L][W] f32
   uint32_t head;    // head [W][8] f32 (transposed: the 8 outputs of input k are adjacent)
   uint32_t hbias;   // [8] f32
+  uint32_t head16;  // head as an MMA operand: [16][W] fp16 hi then [16][W] lo (rows 8..15 zero), canonical
   uint32_t bytes;   // total, multiple of 128
 };
 
@@ -75,7 +77,8 @@ __host__ __device__ inline SlotLayout slot_layout(int p, int W, int L, int lo) {
   s.bias = round_up(s.wk + uint32_t(L - 1) * W * W * 2u, 128u);
   s.head = round_up(s.bias + uint32_t(L) * W * 4u, 128u);
   s.hbias = round_up(s.head + 8u * W * 4u, 128u);
-  s.bytes = round_up(s.hbias + 8u * 4u, 128u);
+  s.head16 = round_up(s.hbias + 8u * 4u, 128u);
+  s.bytes = round_up(s.head16 + 2u * 16u * W * 2u, 128u);
   return s;
 }
 
@@ -117,7 +120,7 @@ __global__ void pack_kernel(MlpView m, TcView tv, unsigned char* img) {
   const float* bh = Wh + 8 * W;
   const uint32_t n1 = uint32_t(W) * S.k1;
   const uint32_t nk = uint32_t(L - 1) * W * W;
-  const uint32_t total = n1 + nk + uint32_t(L) * W + 8u * W + 8u;
+  const uint32_t total = n1 + nk + uint32_t(L) * W + 8u * W + 8u + 16u * W;
   for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
     if (t < n1) {
       uint32_t r = t / S.k1, k = t % S.k1;
@@ -137,9 +140,15 @@ __global__ void pack_kernel(MlpView m, TcView tv, unsigned char* img) {
     } else if (t < n1 + nk + uint32_t(L) * W + 8u * W) {
       uint32_t u = t - n1 - nk - uint32_t(L) * W, o = u / W, k = u % W;
       reinterpret_cast<float*>(base + S.head)[k * 8 + o] = Wh[o * W + k];
-    } else {
+    } else if (t < n1 + nk + uint32_t(L) * W + 8u * W + 8u) {
       uint32_t u = t - n1 - nk - uint32_t(L) * W - 8u * W;
       reinterpret_cast<float*>(base + S.hbias)[u] = bh[u];
+    } else {  // head as an MMA operand, hi and lo fp16 parts
+      uint32_t u = t - n1 - nk - uint32_t(L) * W - 8u * W - 8u, o = u / W, k = u % W;
+      const float v = o < 8 ? Wh[o * W + k] : 0.f;
+      const uint16_t hi = f16_bits(v);
+      *reinterpret_cast<uint16_t*>(base + S.head16 + tc::canon_off(o, k, W)) = hi;
+      *reinterpret_cast<uint16_t*>(base + S.head16 + 16u * W * 2u + tc::canon_off(o, k, W)) = f16_bits(v - f16_value(hi));
     }
   }
 }
@@ -218,11 +227,7 @@ __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const
   tc::fence_before_sync();
   wg_sync(c.wg);
   const float* bias = reinterpret_cast<const float*>(img + S.bias);
-  const float4* head = reinterpret_cast<const float4*>(img + S.head);  // [W][8] as 2 float4 per input
   const float* hbias = reinterpret_cast<const float*>(img + S.hbias);
-  float acc[8];
-#pragma unroll
-  for (int o = 0; o < 8; ++o) acc[o] = 0.f;
   bool ok = true;
   for (int layer = 0; layer < L; ++layer) {
     const uint32_t K = layer == 0 ? S.k1 : uint32_t(W);
@@ -247,7 +252,6 @@ __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const
       if (!ok) return false;
       tc::fence_after_sync();
     }
-    const bool last = (layer == L - 1);
     const float* b = bias + layer * W;
 #pragma unroll 1
     for (int c0 = 0; c0 < W; c0 += 32) {
@@ -263,36 +267,46 @@ __device__ bool tile_slot(const Ctx& c, uint32_t& ph_m, int p, uint64_t x, const
         const float2 bb = *reinterpret_cast<const float2*>(b + c0 + i);
         tc::add_f32x2(v[i], v[i + 1], bb.x, bb.y, v[i], v[i + 1]);
       }
-      if (!last) {
-        // next GEMM operand: f32 tanh, rounded to fp16 (a half-precision tanh
-        // would add its own approximation error to the rounding)
+      // the next GEMM's operand (after the last layer, the head's): f32 tanh,
+      // rounded to fp16 (a half-precision tanh would add its own
+      // approximation error to the rounding)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          uint32_t u[4];
+      for (int q = 0; q < 4; ++q) {
+        uint32_t u[4];
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            u[e] = tc::pack_f16x2(tc::tanh_fast(v[8 * q + 2 * e]), tc::tanh_fast(v[8 * q + 2 * e + 1]));
-          *reinterpret_cast<uint4*>(c.s_a + tc::canon_off(c.t, c0 + 8 * q, W)) = make_uint4(u[0], u[1], u[2], u[3]);
-        }
-      } else {
-        // last hidden layer in f32 feeding the f32 head: acc[o] += head[k][o] h[k]
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float h = tc::tanh_fast(v[i]);
-          const float4 w0 = head[(c0 + i) * 2], w1 = head[(c0 + i) * 2 + 1];
-          tc::fma_f32x2(w0.x, w0.y, h, h, acc[0], acc[1], acc[0], acc[1]);
-          tc::fma_f32x2(w0.z, w0.w, h, h, acc[2], acc[3], acc[2], acc[3]);
-          tc::fma_f32x2(w1.x, w1.y, h, h, acc[4], acc[5], acc[4], acc[5]);
-          tc::fma_f32x2(w1.z, w1.w, h, h, acc[6], acc[7], acc[6], acc[7]);
-        }
+        for (int e = 0; e < 4; ++e)
+          u[e] = tc::pack_f16x2(tc::tanh_fast(v[8 * q + 2 * e]), tc::tanh_fast(v[8 * q + 2 * e + 1]));
+        *reinterpret_cast<uint4*>(c.s_a + tc::canon_off(c.t, c0 + 8 * q, W)) = make_uint4(u[0], u[1], u[2], u[3]);
       }
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
     wg_sync(c.wg);
   }
+  // head: the 8 outputs as one MMA with N = 16 (weights as fp16 hi + lo parts,
+  // rows 8..15 zero), into the accumulator's first columns (all of them were
+  // read before the barrier above)
+  if (c.t == 0) {
+    tc::fence_after_sync();
+    constexpr uint32_t IDESC_H = tc::idesc_f16_f32(MT, 16);
+#pragma unroll 1
+    for (uint32_t ks = 0; ks < uint32_t(W) / 16; ++ks)
+      tc::mma_f16(c.tmem, tc::sdesc(c.a_addr + ks * 256u, 128u, W * 16u),
+                  tc::sdesc(img_addr + S.head16 + ks * 256u, 128u, W * 16u), IDESC_H, ks > 0 ? 1u : 0u);
+#pragma unroll 1
+    for (uint32_t ks = 0; ks < uint32_t(W) / 16; ++ks)
+      tc::mma_f16(c.tmem, tc::sdesc(c.a_addr + ks * 256u, 128u, W * 16u),
+                  tc::sdesc(img_addr + S.head16 + 16u * W * 2u + ks * 256u, 128u, W * 16u), IDESC_H, 1u);
+    tc::mma_commit(c.bar_m);
+  }
+  ok = wg_all(c.wg, wait_bar(c.bar_m, ph_m));
+  ph_m ^= 1;
+  if (!ok) return false;
+  tc::fence_after_sync();
+  float v8[8];
+  tc::tmem_ld8(c.tmem + c.lane_base, v8);
 #pragma unroll
-  for (int o = 0; o < 8; ++o) out[o] = acc[o] + hbias[o];
+  for (int o = 0; o < 8; ++o) out[o] = v8[o] + hbias[o];
   return true;
 }
 
@@ -796,7 +810,7 @@ __global__ void __launch_bounds__(MT, 1) mlp_tc_grad_kernel(const __grid_constan
   const int p = blockIdx.y, L = a.m.n_hidden;
   const SlotLayout S = slot_layout(p, W, L, a.tv.lo);
   const uint32_t k1 = S.k1, lo_bytes = S.wk - S.w1lo;
-  // shared memory: image (W1 hi | hidden | bias | head) | H_1..H_{L-1} | P1 | P2 | U | dout (and ones)
+  // shared memory: image (W1 hi | hidden | bias | f32 head) | H_1..H_{L-1} | P1 | P2 | U | dout (and ones)
   unsigned char* img = smem;
   const uint32_t o_wk = S.w1lo, o_bias = S.bias - lo_bytes, o_head = S.head - lo_bytes, o_hb = S.hbias - lo_bytes;
   unsigned char* Hb = smem + a.img_bytes;
@@ -812,9 +826,9 @@ __global__ void __launch_bounds__(MT, 1) mlp_tc_grad_kernel(const __grid_constan
     s_abort = 0;
     // the image, written by the packing kernel several launches back
     const unsigned char* src = a.tv.img + a.tv.img_off[p];
-    tc::mbar_arrive_expect_tx(bar_w, S.w1lo + (S.bytes - S.wk));
+    tc::mbar_arrive_expect_tx(bar_w, S.w1lo + (S.head16 - S.wk));
     if (S.w1lo) tc::bulk_g2s(tc::smem_u32(img), src, S.w1lo, bar_w);
-    tc::bulk_g2s(tc::smem_u32(img + o_wk), src + S.wk, S.bytes - S.wk, bar_w);
+    tc::bulk_g2s(tc::smem_u32(img + o_wk), src + S.wk, S.head16 - S.wk, bar_w);
   }
   if (warp == 0) {
     tc::tmem_alloc(tc::smem_u32(&s_tmem), NCOL);
@@ -1657,7 +1671,7 @@ static size_t tc_grad_smem(const anqs_model* M, uint32_t* img_bytes, uint32_t* k
   uint32_t img = 0, k1 = 0;
   for (int p = 0; p < n; ++p) {
     const SlotLayout S = slot_layout(p, W, L, lo);
-    img = std::max(img, S.w1lo + (S.bytes - S.wk));
+    img = std::max(img, S.w1lo + (S.head16 - S.wk));
     k1 = std::max(k1, S.k1);
   }
   img = round_up(img, 1024u);
