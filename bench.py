@@ -300,12 +300,13 @@ def _config(w, args):
 
 
 # DRAM bytes per launch from one ncu capture of the same kernel build and
-# workload (`ncu --set full --clock-control none -k regex:<kernel> -c 1
-# python bench.py --kernel-case`, h2o, BF16 form): dram__bytes_read.sum +
-# dram__bytes_write.sum
-TRAFFIC = {("h2o", "bf16"): {"mlp_fp32_grad_kernel": 1101824 + 43520, "mlp_tc_suffix_kernel": 1273088 + 256,
-                             "mlp_tc_parent_kernel": 591616, "eloc_assemble_kernel": 4649472,
-                             "connected_kernel": 64256}}
+# workload (`ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+# --clock-control none -c 80 --csv python bench.py --kernel-case`, h2o, 16-bit
+# form): dram__bytes_read.sum + dram__bytes_write.sum.  A kernel changed since
+# that capture has no entry (traffic null).
+TRAFFIC = {("h2o", "bf16"): {"mlp_tc_parent_kernel": 657408, "mlp_tc_grad_kernel": 608512,
+                             "eloc_assemble_kernel": 4649728, "connected_kernel": 64000,
+                             "grad_partial_sum_kernel": 4009472}}
 
 
 # kernel families that evaluate the connected determinants' amplitudes, in

@@ -447,25 +447,46 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
 // One 128-row tile of the suffix work of slot p (one warpgroup): rows
 // perm[tile*128 + t] of the connected determinants with first differing slot
 // j < p (the first `rows` entries of the sorted order); writes each row's
-// masked slot-p term T[row][p] = (log|psi_p(v_p)|, phase).  Returns false if a
-// wait timed out.  Loads of the sort's outputs go through L2: they are written
-// by kernels that may have been launched just before this one.
+// masked slot-p term T[row][p] = (log|psi_p(v_p)|, phase).  The caller loads
+// the row index and its determinant (suffix_row), ahead of time where it can.
+// The slot's mask is read before the MMAs start so that its latency overlaps
+// them.  Returns false if a wait timed out.
+struct SuffixRow {
+  uint32_t row;
+  uint64_t x;
+};
+
+// Loads of the sort's outputs go through L2: they are written by kernels that
+// may have been launched just before this one.
+__device__ __forceinline__ SuffixRow suffix_row(uint64_t tile, uint64_t rows, int t, const uint32_t* perm,
+                                                const uint64_t* xp) {
+  const uint64_t r = tile * MT + t;
+  SuffixRow s{0u, 0ull};
+  if (r < rows) {
+    s.row = __ldcg(perm + r);
+    s.x = __ldcg(reinterpret_cast<const unsigned long long*>(xp) + s.row);
+  }
+  return s;
+}
+
 template <int W>
 __device__ __forceinline__ bool suffix_tile(const Ctx& c, uint32_t& ph_m, int p, int n, uint64_t tile, uint64_t rows,
-                                            const uint32_t* perm, const uint64_t* xp, const HamView& hv,
-                                            const SlotLayout& Sl, uint32_t img_addr, const unsigned char* img,
-                                            float2* T) {
-  const uint64_t r = tile * MT + c.t;
-  const bool valid = r < rows;
-  const uint32_t row = valid ? __ldcg(perm + r) : 0u;
-  const uint64_t x = valid ? __ldcg(reinterpret_cast<const unsigned long long*>(xp) + row) : 0ull;
-  float out[8];
-  const bool ok = tile_slot<W>(c, ph_m, p, x, Sl, img_addr, img, out);
-  if (ok && valid) {
+                                            SuffixRow sr, const HamView& hv, const SlotLayout& Sl, uint32_t img_addr,
+                                            const unsigned char* img, float2* T) {
+  const bool valid = tile * MT + c.t < rows;
+  const uint32_t row = sr.row;
+  const uint64_t x = sr.x;
+  unsigned pmk = 0, mk = 0;
+  if (valid) {
     const uint64_t pm = (1ull << (2 * p)) - 1ull;
     const int a = __popcll(x & pm & 0x5555555555555555ull);
     const int bb = __popcll(x & pm & 0xAAAAAAAAAAAAAAAAull);
-    const unsigned pmk = slot_mask(hv, p, a, bb, x), mk = norm_mask(hv, p, pmk);
+    pmk = slot_mask(hv, p, a, bb, x);
+    mk = norm_mask(hv, p, pmk);
+  }
+  float out[8];
+  const bool ok = tile_slot<W>(c, ph_m, p, x, Sl, img_addr, img, out);
+  if (ok && valid) {
     float mx = -INFINITY;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -549,8 +570,14 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_ws_kernel(TcView tv, HamView hv,
     bool ok = __syncthreads_and(wait_bar(tc::smem_u32(&bars[0]), 0));
     const uint64_t rows = offsets[p];
     uint32_t ph_m = 0;
-    for (uint64_t tile = li + gp * wg; ok && tile < tiles[p]; tile += gp * NWG)
-      ok = suffix_tile<W>(c, ph_m, p, n, tile, rows, perm, xp, hv, Sl, img_addr, smem, T);
+    // the next tile's rows are loaded while this tile runs
+    uint64_t tile = li + gp * wg;
+    SuffixRow nx = tile < tiles[p] ? suffix_row(tile, rows, t, perm, xp) : SuffixRow{0u, 0ull};
+    for (; ok && tile < tiles[p]; tile += gp * NWG) {
+      const SuffixRow cur = nx;
+      if (tile + gp * NWG < tiles[p]) nx = suffix_row(tile + gp * NWG, rows, t, perm, xp);
+      ok = suffix_tile<W>(c, ph_m, p, n, tile, rows, cur, hv, Sl, img_addr, smem, T);
+    }
     if (!ok) s_abort = 1;
   }
   teardown<W>(tv, s_tmem, s_abort);
@@ -686,7 +713,8 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_multi_kernel(const __grid_consta
     const uint64_t rows = __ldcg(P.offsets + p);
     bool ok = true;
     for (uint32_t tile = t_lo + wg; ok && tile < t_hi; tile += NWG)
-      ok = suffix_tile<W>(c, ph_m, p, P.tv.n, tile, rows, P.perm, P.xp, P.hv, Sl, img_addr, smem, P.T);
+      ok = suffix_tile<W>(c, ph_m, p, P.tv.n, tile, rows, suffix_row(tile, rows, c.t, P.perm, P.xp), P.hv, Sl, img_addr,
+                          smem, P.T);
     tc::fence_async_smem();
     tc::fence_before_sync();
     return __syncthreads_and(ok);
