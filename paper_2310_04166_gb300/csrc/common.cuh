@@ -364,7 +364,7 @@ int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* hist, uint32_t*
                    uint32_t* perm, cudaStream_t s);
 int launch_eloc_assemble(int n, uint32_t K, Count n_x, const uint64_t* xp, const uint8_t* js, const float* cache,
                          const float2* T, const double* hval, const double* hdiag, const float* la_x,
-                         const float* ph_x, double* ere, double* eim, cudaStream_t s);
+                         const float* ph_x, double* ere, double* eim, cudaStream_t s, bool tsum = false);
 // BF16 transformer form
 int tf_tc_pack_alloc(anqs_model* m);
 int tf_tc_pack(anqs_model* m, cudaStream_t s);

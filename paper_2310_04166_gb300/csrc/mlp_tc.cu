@@ -1173,7 +1173,10 @@ __global__ void __launch_bounds__(MT, 1) mlp_tc_grad_kernel(const __grid_constan
 // threads over the connected x': log psi(x') = parent prefix up to slot j +
 // parent slot-j term of v'_j + the terms T[x'][p] of the slots p > j; then
 // E_loc(x) = H_xx + sum H_xx' exp(log psi(x') - log psi(x)) with the ratio in
-// float32 and the sum in FP64, reduced in a fixed order (deterministic).
+// float32 and the sum in FP64, reduced in a fixed order (deterministic).  The
+// suffix terms come per (x', slot) (T[x'][p], MLP and NADE) or already summed
+// per x' (T[x'], `tsum`: the transformer, whose suffix kernel holds a
+// sequence's positions in one tile).
 constexpr int AT = 128;
 __global__ void __launch_bounds__(AT) eloc_assemble_kernel(int n, uint32_t K, Count n_x_, const uint64_t* __restrict__ xp,
                                                            const uint8_t* __restrict__ js,
@@ -1183,7 +1186,7 @@ __global__ void __launch_bounds__(AT) eloc_assemble_kernel(int n, uint32_t K, Co
                                                            const double* __restrict__ hdiag,
                                                            const float* __restrict__ la_x,
                                                            const float* __restrict__ ph_x, double* __restrict__ ere,
-                                                           double* __restrict__ eim) {
+                                                           double* __restrict__ eim, int tsum) {
   ANQS_PDL_ENTRY();
   __shared__ double red[2][AT / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1198,10 +1201,18 @@ __global__ void __launch_bounds__(AT) eloc_assemble_kernel(int n, uint32_t K, Co
       const float* cc = cache + (l * n + j) * CACHE_F;
       const int vj = int((x >> (2 * j)) & 3ull);
       float la = cc[0] + cc[2 + vj], ph = cc[1] + cc[6 + vj];
-      for (int p = j + 1; p < n; ++p) {
-        const float2 tv = T[row * n + p];
-        la += tv.x;
-        ph += tv.y;
+      if (tsum) {
+        if (j + 1 < n) {  // determinants with j = n - 1 have no suffix positions (and no T entry)
+          const float2 tv = T[row];
+          la += tv.x;
+          ph += tv.y;
+        }
+      } else {
+        for (int p = j + 1; p < n; ++p) {
+          const float2 tv = T[row * n + p];
+          la += tv.x;
+          ph += tv.y;
+        }
       }
       const double h = hval[row];
       const float r = expf(la - lx);
@@ -1619,10 +1630,10 @@ int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* hist, uint32_t*
 
 int launch_eloc_assemble(int n, uint32_t K, Count n_x, const uint64_t* xp, const uint8_t* js, const float* cache,
                          const float2* T, const double* hval, const double* hdiag, const float* la_x,
-                         const float* ph_x, double* ere, double* eim, cudaStream_t s) {
+                         const float* ph_x, double* ere, double* eim, cudaStream_t s, bool tsum) {
   uint64_t blocks = n_x.n;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  ANQS_CUDA_LAUNCH("eloc_assemble_kernel", launch_k(eloc_assemble_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(AT), 0, s, n, K, n_x, xp, js, cache, T, hval, hdiag, la_x, ph_x, ere, eim));
+  ANQS_CUDA_LAUNCH("eloc_assemble_kernel", launch_k(eloc_assemble_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(AT), 0, s, n, K, n_x, xp, js, cache, T, hval, hdiag, la_x, ph_x, ere, eim, tsum ? 1 : 0));
   return ANQS_OK;
 }
 

@@ -33,7 +33,9 @@
 //   SUFFIX  connected determinants x', grouped by first differing slot j:
 //           positions t = j+1..n-1 only (positions <= j see the same tokens as
 //           in the parent x, Eq. anqs_def); keys and values of positions <= j
-//           come from the parent cache; writes the masked slot terms T[x'][t].
+//           come from the parent cache; writes the sum over those positions of
+//           the masked slot terms, one (log|psi|, phase) pair T[x'] per
+//           connected determinant (a sequence's positions are rows of one tile).
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -628,8 +630,23 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
           const float ov = (v == 0) ? out[0] : (v == 1) ? out[1] : (v == 2) ? out[2] : out[3];
           const float pv = (v == 0) ? out[4] : (v == 1) ? out[5] : (v == 2) ? out[6] : out[7];
           const float lse = mx + __logf(sum);
-          a.T[seq * n + pos] = make_float2(((pmk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY, pv);
+          // the row's term to shared memory (the k|v region is free now); the
+          // sequence's first row adds its positions' terms below
+          reinterpret_cast<float2*>(sKV)[t] = make_float2(((pmk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY, pv);
         }
+      }
+    }
+    if (a.mode == MODE_SUFFIX) {
+      // one sum per connected determinant, over its positions in order: T[x']
+      __syncthreads();
+      if (valid && pos == tl.t0) {
+        const float2* tr = reinterpret_cast<const float2*>(sKV) + t;
+        float sl = 0.f, sp = 0.f;
+        for (int i = 0; i < tl.P; ++i) {
+          sl += tr[i].x;
+          sp += tr[i].y;
+        }
+        a.T[seq] = make_float2(sl, sp);
       }
     }
     __syncthreads();  // shared k|v and hidden buffers are rewritten by the next tile
@@ -710,7 +727,7 @@ size_t plan(const anqs_model* M, const anqs_ham* H, uint64_t n_x, Arena& A, TfEl
   w.ph_x = A.take<float>(n_x);
   w.raw = A.take<float>(n_x * n * 8);
   w.cache = A.take<float>(n_x * n * TC_CACHE_F);
-  w.T = A.take<float2>(m * n);
+  w.T = A.take<float2>(m);  // one sum of the suffix positions' terms per connected determinant
   w.perm = A.take<uint32_t>(m);
   w.hist = A.take<uint32_t>(ANQS_MAX_ORB);
   w.cursor = A.take<uint32_t>(ANQS_MAX_ORB);
@@ -827,7 +844,7 @@ int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Co
   {
     ProfScope ps(PROF_TC_ELOC, s);
     ANQS_TRY(launch_eloc_assemble(n, uint32_t(K), n_x, w.xp, w.js, w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x, ere,
-                                  eim, s));
+                                  eim, s, true));
   }
   return ANQS_OK;
 }

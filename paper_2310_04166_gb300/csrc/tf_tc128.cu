@@ -739,8 +739,24 @@ __global__ void __launch_bounds__(NT, 1) tf128_kernel(Args a) {
             const float ov = (v == 0) ? out[0] : (v == 1) ? out[1] : (v == 2) ? out[2] : out[3];
             const float pv = (v == 0) ? out[4] : (v == 1) ? out[5] : (v == 2) ? out[6] : out[7];
             const float lse = mx + __logf(sum);
-            a.T[seq * n + pos] = make_float2(((pmk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY, pv);
+            // the row's term to its own exchange slot (read above); the
+            // sequence's first row adds its positions' terms below
+            reinterpret_cast<float2*>(s_hx + t * 8)[0] =
+                make_float2(((pmk >> v) & 1u) ? 0.5f * (ov - lse) : -INFINITY, pv);
           }
+        }
+      }
+      if (a.mode == MODE_SUFFIX) {
+        // one sum per connected determinant, over its positions in order: T[x']
+        csync();
+        if (h == 0 && valid && pos == tl.t0) {
+          float sl = 0.f, sp = 0.f;
+          for (int i = 0; i < tl.P; ++i) {
+            const float2 tv = reinterpret_cast<const float2*>(s_hx + (t + i) * 8)[0];
+            sl += tv.x;
+            sp += tv.y;
+          }
+          a.T[seq] = make_float2(sl, sp);
         }
       }
       csync();  // shared k|v, hidden buffers and exchange slots are rewritten by the next tile
