@@ -795,10 +795,22 @@ __global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int 
   ANQS_PDL_WAIT();  // the prefix table's logits and the cleared counters come from the kernels before
   if (staged) {  // rows' split thresholds from the slot outputs just written
     __syncthreads();
-    for (int r = threadIdx.x; r < n_rows; r += SMALL_T) {
-      float l[4];
-      for (int v = 0; v < 4; ++v) l[v] = __ldcg(logits + uint64_t(r) * 8 + v);
-      split_thresholds(l, st_mk[r] & 0xFu, st_thr[r]);
+    // all of a thread's rows' outputs are loaded before any is used (one L2
+    // round trip instead of one per row): at most kStageRows / SMALL_T rows
+    constexpr int RPT = kStageRows / SMALL_T;
+    float4 l4[RPT];
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int r = threadIdx.x + k * SMALL_T;
+      l4[k] = r < n_rows ? __ldcg(reinterpret_cast<const float4*>(logits + uint64_t(r) * 8)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < RPT; ++k) {
+      const int r = threadIdx.x + k * SMALL_T;
+      if (r < n_rows) {
+        const float l[4] = {l4[k].x, l4[k].y, l4[k].z, l4[k].w};
+        split_thresholds(l, st_mk[r] & 0xFu, st_thr[r]);
+      }
     }
   }
   const int lane = threadIdx.x & 31;
