@@ -562,7 +562,7 @@ def _sub_workload(A, lib, args, name, dev, rank, dist, steps):
     return out
 
 
-def _large(args, dev):
+def _large(args, dev, quick=False):
     """Config-4 shape (26 orbitals, 9+9 electrons, transformer d128 h8 L4,
     33,507 connected determinants per sample): local energies per second of
     anqs_local_energy over a bounded sample (the 64 most frequent unique
@@ -591,7 +591,7 @@ def _large(args, dev):
     for form, model in models.items():
         out = (torch.empty(x.numel(), dtype=torch.float64, device=dev),
                torch.empty(x.numel(), dtype=torch.float64, device=dev), torch.empty(4, dtype=torch.float64, device=dev))
-        steps = args.steps if form == "bf16" else max(1, min(args.steps, 2))
+        steps = (min(args.steps, 3) if quick else args.steps) if form == "bf16" else max(1, min(args.steps, 1 if quick else 2))
         for _ in range(args.warmup if form == "bf16" else 1):
             A.local_energy(model, ham, x, c, workspace=ws, out=out)
         torch.cuda.synchronize()
@@ -627,7 +627,7 @@ def _large(args, dev):
     d = (outs["bf16"][0] - outs["fp32"][0]).abs()
     K = ham.n_connected
     r = res["bf16"]
-    print(json.dumps({"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["steps"],
+    return ({"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": r["steps"],
                       "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
                       "scaling": "weak", "vs_baseline": None, "dtype": "fp16-operand tcgen05 GEMM (kind::f16, f32 accumulate) / f32 heads / f64 E_loc",
                       "data": "synthetic",
@@ -643,10 +643,10 @@ def _large(args, dev):
                                 "bf16_vs_fp32": {"max_abs_dEloc_ha": float(d.max()),
                                                  "abs_dE_ha": abs(float(outs["bf16"][1][0] - outs["fp32"][1][0])),
                                                  "note": "FP32 form = E_loc definition within 1e-6 relative "
-                                                         "(tests/test_gpu_tf.py)"}}}), flush=True)
+                                                         "(tests/test_gpu_tf.py)"}}})
 
 
-def _batch32(args, dev):
+def _batch32(args, dev, quick=False):
     """32 independent problems (seeds 100..131, n in [6, 14], MLP 3x128 each,
     N_s = 1e5 each), every arm one CUDA-graph replay of all 32 passes
     (sampling, local energies, gradient) per timed step:
@@ -665,7 +665,7 @@ def _batch32(args, dev):
     from synthetic import batch32_problem, flatten_mlp, mlp_params
     specs = [batch32_problem(k) for k in range(32)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    steps = max(1, min(args.steps, 20))
+    steps = max(1, min(args.steps, 3 if quick else 20))
 
     def build(form):
         out = []
@@ -692,8 +692,8 @@ def _batch32(args, dev):
         return {"value": uniq / (sum(times) / 1e3), "ms_per_step": sum(times) / n, "n_unique_per_step": uniq / n}
 
     def graph_arm(form, persistent):
-        # the FP32 arms take about 13 s a step: one warm-up pass and 3 timed steps
-        warm, n_timed = (args.warmup, steps) if form == "bf16" else (1, max(1, min(steps, 3)))
+        # the FP32 arms take about 13 s a step: one warm-up pass and 3 timed steps (1 in the quick form)
+        warm, n_timed = (args.warmup, steps) if form == "bf16" else (1, 1 if quick else max(1, min(steps, 3)))
         probs = build(form)
         bs = BatchedStep(probs, persistent=persistent)
         for _ in range(warm):
@@ -719,7 +719,7 @@ def _batch32(args, dev):
 
     res = {}
     res["bf16_persistent"], probs = graph_arm("bf16", True)
-    oracle = None if args.no_cpu_baseline else _batch32_oracle(specs, probs)
+    oracle = None if args.no_cpu_baseline else _batch32_oracle(specs, probs, 10.0 if quick else 20.0)
     del probs
     torch.cuda.empty_cache()
     res["bf16_streams"], probs = graph_arm("bf16", False)
@@ -730,8 +730,9 @@ def _batch32(args, dev):
     def plain():
         for p in probs:
             p.step()
-    plain()
-    res["fp32_separate"] = timed(plain, probs, max(1, min(steps, 3)))
+    if not quick:  # 32 eager FP32 passes (left out of the default line: the graph arm above times the same work)
+        plain()
+        res["fp32_separate"] = timed(plain, probs, max(1, min(steps, 3)))
     head = res["bf16_persistent"]
     line = {"metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": steps,
             "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -746,11 +747,12 @@ def _batch32(args, dev):
             "n_unique_per_step": head["n_unique_per_step"],
             "forms": dict(res, bf16_persistent_over_fp32_streams=head["value"] / res["fp32_streams"]["value"],
                           bf16_persistent_over_bf16_streams=head["value"] / res["bf16_streams"]["value"],
-                          bf16_persistent_over_fp32_separate=head["value"] / res["fp32_separate"]["value"]),
+                          **({"bf16_persistent_over_fp32_separate": head["value"] / res["fp32_separate"]["value"]}
+                             if "fp32_separate" in res else {})),
             "clocks": head["clocks"]}
     if oracle:
         line["oracle"] = oracle
-    print(json.dumps(line), flush=True)
+    return line
 
 
 def _batch32_oracle(specs, probs, seconds=20.0):
@@ -792,7 +794,7 @@ def main():
     ap.add_argument("--workload", default="h2o")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--one-form", action="store_true", help="time only --form (default: both forms)")
-    ap.add_argument("--no-extra", action="store_true", help="h2o only: leave out the n2 sub-workload")
+    ap.add_argument("--no-extra", action="store_true", help="h2o only: leave out the n2, batch32 and large sub-workloads")
     ap.add_argument("--binomial", action="store_true", help="binomial statistics sampling (chained binomials per node)")
     ap.add_argument("--n-samples", type=float, default=0, help="N_s of the sampling pass (default: the workload's)")
     ap.add_argument("--kernel-samples", type=int, default=0,
@@ -819,7 +821,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if args.workload == "batch32":
-        _batch32(args, dev)
+        print(json.dumps(_batch32(args, dev)), flush=True)
         return
     ham = A.Hamiltonian(w["h"], w["g"], w["e_nuc"], w["n_alpha"], w["n_beta"])
     params = torch.tensor(w["params"], device=dev)
@@ -827,7 +829,7 @@ def main():
         args.form, args.one_form = "fp32", True
     form = args.form
     if args.workload == "large" and not args.kernel_case:
-        _large(args, dev)
+        print(json.dumps(_large(args, dev)), flush=True)
         return
     if args.kernel_case:
         model = _make_model(A, w, params, form)
@@ -891,9 +893,20 @@ def main():
     if args.workload == "h2o" and not args.no_extra and ws == 1:
         # the N2-shaped transformer workload in the same line, fewer steps (its FP32 form takes ~0.75 s a step)
         line["workloads"] = {"n2": _sub_workload(A, lib, args, "n2", dev, rank, dist, min(args.steps, 10))}
+        torch.cuda.empty_cache()
+        # the 32-problem batch (persistent launch, autotuned) and the 26-orbital transformer, in short forms
+        line["workloads"]["batch32"] = _compact(_batch32(args, dev, quick=True))
+        torch.cuda.empty_cache()
+        line["workloads"]["large"] = _compact(_large(args, dev, quick=True))
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _compact(sub):
+    """A workload's own line without the keys the enclosing line already has."""
+    return {k: v for k, v in sub.items() if k not in ("metric", "unit", "n_gpus", "higher_is_better", "scaling",
+                                                        "vs_baseline", "data")}
 
 
 def _tf_work(A, ham, w, x):
