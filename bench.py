@@ -707,6 +707,20 @@ def _batch32(args, dev, quick=False):
             extra["autotuner"] = {"times_ms": {nm: round(v, 4) for nm, v in zip(names, t)},
                                   "chosen": {"mode": "static" if mode == _lib.ANQS_BATCH_STATIC else "dynamic",
                                              "chunk": chunk}}
+            # roofline of the persistent amplitude launch: the suffix FLOP (with prefix
+            # reuse) of the sample sets the autotuner timed, over its fastest time
+            flop = 0.0
+            for sp, pr in zip(specs, probs):
+                nu = int(pr.nu.item())
+                flop += _tc_work(A, pr.ham, pr.model, sp, pr.x[:nu].contiguous())["mlp_tc_suffix_kernel"]
+            peaks, src = _peaks()
+            best = min(t)
+            ach = flop / (best / 1e3) / 1e12
+            extra["roofline"] = {"kernel": "mlp_tc_multi_kernel", "bound": "tensor", "achieved": ach,
+                                 "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"],
+                                 "traffic": None, "avg_launch_us": best * 1e3, "work_per_launch": flop,
+                                 "note": f"dense bf16 {src} burst peak; suffix FLOP with prefix reuse of the 32 "
+                                         "problems over the autotuner's fastest launch time"}
         bs.capture()
         for _ in range(warm):
             bs.replay()
@@ -745,6 +759,7 @@ def _batch32(args, dev, quick=False):
                                  "local energies and statistics, gradient); fp32_separate: 32 eager passes one "
                                  "after the other"},
             "n_unique_per_step": head["n_unique_per_step"],
+            "roofline": head.get("roofline"),
             "forms": dict(res, bf16_persistent_over_fp32_streams=head["value"] / res["fp32_streams"]["value"],
                           bf16_persistent_over_bf16_streams=head["value"] / res["bf16_streams"]["value"],
                           **({"bf16_persistent_over_fp32_separate": head["value"] / res["fp32_separate"]["value"]}
