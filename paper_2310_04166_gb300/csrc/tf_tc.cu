@@ -75,7 +75,10 @@ constexpr uint32_t OFF_WA = 0, OFF_WF = WA_BYTES, OFF_WG = WA_BYTES + WF_BYTES;
 constexpr uint32_t WG_BYTES = A_BYTES + KV_BYTES;
 constexpr uint32_t OFF_TP = OFF_WG + NWG * WG_BYTES;
 constexpr uint32_t OFF_HEAD = OFF_TP + TP_FLOATS * 4;
-constexpr uint32_t SMEM_BYTES = OFF_HEAD + (8 * D + 8) * 4;
+constexpr int kMaxL = 4;                                   // blocks of the 16-bit d-64 form
+constexpr uint32_t LP_FLOATS = 13 * D;                     // per block: ln1 g,b | bq bk bv bo | ln2 g,b | b1 (4D) | b2
+constexpr uint32_t OFF_LP = OFF_HEAD + (8 * D + 8) * 4;    // every block's, then the final LayerNorm's g, b
+constexpr uint32_t SMEM_BYTES = OFF_LP + (kMaxL * LP_FLOATS + 2 * D) * 4;
 constexpr uint32_t TMEM_WG = 256;  // columns per warpgroup: [0,192) qkv / o / f1 buffers, [192,256) acc2
 constexpr uint64_t kWaitNs = 2000000000ull;
 constexpr int MODE_FULL = 0, MODE_SUFFIX = 1;
@@ -178,8 +181,8 @@ __device__ __forceinline__ void load_half(const Args& a, int layer, bool ffn, ui
 
 // LayerNorm of the thread's row (eps 1e-5, biased variance) -> fp16 row t of
 // a canonical K-major [128][64] operand
-__device__ __forceinline__ void ln_store(const float (&h)[D], const float* __restrict__ g,
-                                         const float* __restrict__ b, unsigned char* sA, int t) {
+__device__ __forceinline__ void ln_store(const float (&h)[D], const float* g, const float* b, unsigned char* sA,
+                                         int t) {
   float s = 0.f;
 #pragma unroll
   for (int c = 0; c < D; ++c) s += h[c];
@@ -190,8 +193,8 @@ __device__ __forceinline__ void ln_store(const float (&h)[D], const float* __res
   const float rs = 1.0f / sqrtf(q * (1.0f / D) + 1e-5f);
 #pragma unroll
   for (int c0 = 0; c0 < D; c0 += 8) {
-    const float4 g0 = __ldg(reinterpret_cast<const float4*>(g + c0)), g1 = __ldg(reinterpret_cast<const float4*>(g + c0 + 4));
-    const float4 b0 = __ldg(reinterpret_cast<const float4*>(b + c0)), b1 = __ldg(reinterpret_cast<const float4*>(b + c0 + 4));
+    const float4 g0 = *reinterpret_cast<const float4*>(g + c0), g1 = *reinterpret_cast<const float4*>(g + c0 + 4);
+    const float4 b0 = *reinterpret_cast<const float4*>(b + c0), b1 = *reinterpret_cast<const float4*>(b + c0 + 4);
     const float gg[8] = {g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w};
     const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
     uint32_t w[4];
@@ -252,10 +255,29 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
   ANQS_PDL_TRIGGER();
   float* s_tp = reinterpret_cast<float*>(smem + OFF_TP);
   float* s_head = reinterpret_cast<float*>(smem + OFF_HEAD);
+  float* s_lp = reinterpret_cast<float*>(smem + OFF_LP);
   {
     const size_t tail = 5 * size_t(D) + size_t(n) * D + size_t(L) * (12 * size_t(D) * D + 13 * D);
     for (int i = threadIdx.x; i < (5 + n) * D; i += NT) s_tp[i] = a.params[i];
     for (int i = threadIdx.x; i < 8 * D + 8; i += NT) s_head[i] = a.params[tail + 2 * D + i];
+    // every block's LayerNorm parameters and biases, and the final LayerNorm's
+    for (int l = 0; l < L; ++l) {
+      const LayerP g = layer_p(a.params, n, l);
+      float* d = s_lp + l * LP_FLOATS;
+      for (int i = threadIdx.x; i < D; i += NT) {
+        d[i] = g.ln1_g[i];
+        d[D + i] = g.ln1_b[i];
+        d[2 * D + i] = g.bq[i];
+        d[3 * D + i] = g.bk[i];
+        d[4 * D + i] = g.bv[i];
+        d[5 * D + i] = g.bo[i];
+        d[6 * D + i] = g.ln2_g[i];
+        d[7 * D + i] = g.ln2_b[i];
+        d[12 * D + i] = g.b2[i];
+      }
+      for (int i = threadIdx.x; i < 4 * D; i += NT) d[8 * D + i] = g.b1[i];
+    }
+    for (int i = threadIdx.x; i < 2 * D; i += NT) s_lp[kMaxL * LP_FLOATS + i] = a.params[tail + i];
   }
   // work: FULL one group; SUFFIX the groups j = 0..n-2 (P = n-1-j positions)
   uint64_t total = 0;
@@ -342,7 +364,20 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
       for (int c = 0; c < D; ++c) h[c] = s_tp[token * D + c] + s_tp[(5 + pos) * D + c];
     }
     for (int l = 0; ok && l < L; ++l) {
-      const LayerP lp = layer_p(a.params, n, l);
+      LayerP lp;  // this block's small parameters, staged in shared memory
+      {
+        const float* d = s_lp + l * LP_FLOATS;
+        lp.ln1_g = d;
+        lp.ln1_b = d + D;
+        lp.bq = d + 2 * D;
+        lp.bk = d + 3 * D;
+        lp.bv = d + 4 * D;
+        lp.bo = d + 5 * D;
+        lp.ln2_g = d + 6 * D;
+        lp.ln2_b = d + 7 * D;
+        lp.b1 = d + 8 * D;
+        lp.b2 = d + 12 * D;
+      }
       ln_store(h, lp.ln1_g, lp.ln1_b, sA, t);
       tc::fence_async_smem();
       tc::fence_before_sync();
@@ -373,7 +408,7 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
         const float* bias = c0 < 2 * D ? lp.bk + (c0 - D) : lp.bv + (c0 - 2 * D);
         uint32_t w[16];
 #pragma unroll
-        for (int i = 0; i < 32; i += 2) w[i / 2] = tc::pack_f16x2(v[i] + __ldg(bias + i), v[i + 1] + __ldg(bias + i + 1));
+        for (int i = 0; i < 32; i += 2) w[i / 2] = tc::pack_f16x2(v[i] + bias[i], v[i + 1] + bias[i + 1]);
         uint4* dst = reinterpret_cast<uint4*>(sKV + t * KV_STRIDE + (c0 - D) * 2);
 #pragma unroll
         for (int q = 0; q < 4; ++q) dst[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
@@ -395,7 +430,7 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
           tc::tmem_ld32(tmem + lane_base + uint32_t(hd * DH), q);
         }
 #pragma unroll
-        for (int e = 0; e < DH; ++e) q[e] = (q[e] + __ldg(lp.bq + hd * DH + e)) * scale;
+        for (int e = 0; e < DH; ++e) q[e] = (q[e] + lp.bq[hd * DH + e]) * scale;
         float m = -INFINITY, lsum = 0.f, acc[DH];
 #pragma unroll
         for (int e = 0; e < DH; ++e) acc[e] = 0.f;
@@ -496,7 +531,7 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
         float v[32];
         tc::tmem_ld32(tmem + lane_base + uint32_t(c0), v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) h[c0 + i] += v[i] + __ldg(lp.bo + c0 + i);
+        for (int i = 0; i < 32; ++i) h[c0 + i] += v[i] + lp.bo[c0 + i];
       }
       ln_store(h, lp.ln2_g, lp.ln2_b, sA, t);
       tc::fence_async_smem();
@@ -544,8 +579,8 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
               const int i = q8 + 2 * e;
-              w[e] = tc::pack_f16x2(fmaxf(v[i] + __ldg(lp.b1 + c * D + c0 + i), 0.f),
-                                     fmaxf(v[i + 1] + __ldg(lp.b1 + c * D + c0 + i + 1), 0.f));
+              w[e] = tc::pack_f16x2(fmaxf(v[i] + lp.b1[c * D + c0 + i], 0.f),
+                                     fmaxf(v[i + 1] + lp.b1[c * D + c0 + i + 1], 0.f));
             }
             *reinterpret_cast<uint4*>(sH + tc::canon_off(t, c0 + q8, D)) = make_uint4(w[0], w[1], w[2], w[3]);
           }
@@ -580,14 +615,13 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
         float v[32];
         tc::tmem_ld32(tmem + lane_base + uint32_t(3 * D + c0), v);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) h[c0 + i] += v[i] + __ldg(lp.b2 + c0 + i);
+        for (int i = 0; i < 32; ++i) h[c0 + i] += v[i] + lp.b2[c0 + i];
       }
     }
     if (!ok) break;
     // final LayerNorm and head
     {
-      const size_t tail = 5 * size_t(D) + size_t(n) * D + size_t(L) * (12 * size_t(D) * D + 13 * D);
-      const float* g = a.params + tail;
+      const float* g = s_lp + kMaxL * LP_FLOATS;
       const float* b = g + D;
       float s = 0.f;
 #pragma unroll
@@ -602,7 +636,7 @@ __global__ void __launch_bounds__(NT, 1) tf_tc_kernel(Args a) {
       for (int o = 0; o < 8; ++o) out[o] = s_head[8 * D + o];
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        const float y = fmaf((h[c] - mean) * rs, __ldg(g + c), __ldg(b + c));
+        const float y = fmaf((h[c] - mean) * rs, g[c], b[c]);
 #pragma unroll
         for (int o = 0; o < 8; ++o) out[o] = fmaf(y, s_head[o * D + c], out[o]);
       }
@@ -743,6 +777,8 @@ int tf_tc_pack_alloc(anqs_model* M) {
     return set_error(ANQS_ERR_UNSUPPORTED, "BF16 transformer form supports d_model 64 or 128");
   if (M->d.d_model / M->d.n_heads != 16 && M->d.d_model / M->d.n_heads != 32)
     return set_error(ANQS_ERR_UNSUPPORTED, "BF16 transformer form supports head width 16 or 32");
+  if (M->d.d_model == D && M->d.n_layers > kMaxL)
+    return set_error(ANQS_ERR_UNSUPPORTED, "BF16 transformer form at d_model 64 supports up to %d blocks", kMaxL);
   M->packed_bytes = M->d.d_model == 128 ? tf128_packed_bytes(M) : size_t(M->d.n_layers) * LAYER_BYTES + 256;
   ANQS_CUDA(cudaMalloc(&M->packed, M->packed_bytes));
   ANQS_CUDA(cudaMemset(M->packed, 0, M->packed_bytes));
