@@ -102,8 +102,8 @@ enum { ANQS_MODEL_MLP = 0, ANQS_MODEL_TF = 1, ANQS_MODEL_TABLE = 2, ANQS_MODEL_N
  *       the MLP's weights (layer 1 as two fp16 parts) and tanh activations,
  *       the transformer's activations and stored keys/values (its weights are
  *       bf16-representable, hence exact in fp16).  Conversions saturate at
- *       +-65504.  MLP width 64 or 128, transformer d_model 64 or 128 with
- *       head width 16 or 32. */
+ *       +-65504.  MLP width 64 or 128, transformer d_model 64 (at most 4
+ *       blocks) or 128 with head width 16 or 32. */
 enum { ANQS_FORM_FP32 = 0, ANQS_FORM_BF16 = 1 };
 
 typedef struct anqs_ham anqs_ham;
