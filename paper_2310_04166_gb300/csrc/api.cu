@@ -743,9 +743,12 @@ int anqs_local_energy(const anqs_model* M, const anqs_ham* H, const uint64_t* x,
   if (uses_tc_eloc(M)) {
     size_t need = tc_eloc_workspace(M, H, n_x);
     if (ws_bytes < need || !ws) return set_error(ANQS_ERR_CAPACITY, "workspace needs %zu bytes", need);
-    if (M->d.kind == ANQS_MODEL_NADE) ANQS_TRY(run_eloc_nade(M, H, x, nc, ere, eim, ws, ws_bytes, s));
-    else if (M->d.kind == ANQS_MODEL_TF) ANQS_TRY(run_eloc_tf_tc(M, H, x, nc, ere, eim, ws, ws_bytes, s));
-    else ANQS_TRY(run_eloc_tc(M, H, x, nc, ere, eim, ws, ws_bytes, s));
+    // the assembly kernel also writes the statistics (counts set)
+    if (M->d.kind == ANQS_MODEL_NADE) ANQS_TRY(run_eloc_nade(M, H, x, nc, ere, eim, counts, stats, ws, ws_bytes, s));
+    else if (M->d.kind == ANQS_MODEL_TF)
+      ANQS_TRY(run_eloc_tf_tc(M, H, x, nc, ere, eim, counts, stats, ws, ws_bytes, s));
+    else ANQS_TRY(run_eloc_tc(M, H, x, nc, ere, eim, counts, stats, ws, ws_bytes, s));
+    return ANQS_OK;
   } else {
     Arena A(ws, ws_bytes);
     uint64_t* xp;
@@ -942,10 +945,8 @@ int anqs_batched_local_energy(anqs_batch* b, const anqs_eloc_problem* q, int n, 
           break;
         }
         const Count nc{q[k].n_x, q[k].n_x_dev, 1};
-        r = eloc_tc_post(q[k].ham, nc, q[k].eloc_re_dev, q[k].eloc_im_dev, q[k].workspace_dev, q[k].workspace_bytes,
-                         sk);
-        if (r == ANQS_OK && q[k].counts_dev)
-          r = launch_stats(q[k].eloc_re_dev, q[k].eloc_im_dev, q[k].counts_dev, nc, q[k].stats_dev, sk);
+        r = eloc_tc_post(q[k].ham, nc, q[k].eloc_re_dev, q[k].eloc_im_dev, q[k].counts_dev, q[k].stats_dev,
+                         q[k].workspace_dev, q[k].workspace_bytes, sk);
         if (cudaEventRecord(b->done[k], sk) == cudaSuccess) join[k] = 2;
         else fail("event record");
       }

@@ -119,6 +119,96 @@ struct Count {
 inline Count host_count(uint64_t n) { return Count{n, nullptr, 1}; }
 inline Count scaled(const Count& c, uint64_t k) { return Count{c.n * k, c.dev, c.mult * k}; }
 
+#ifdef __CUDACC__
+// Count-weighted statistics of a sample set (Eq. energy_est): S = sum_l n_l,
+// E = sum_l n_l E_loc(l) / S (complex) and Var = sum_l n_l |E_loc(l) - E|^2 / S
+// over the rows l < n_x, written as stats = {Re E, Im E, Var, S}.  One CTA of
+// NT threads, one pass over the rows with the shift K = E_loc(0):
+//   A = sum_l n_l (E_loc(l) - K),  Q = sum_l n_l |E_loc(l) - K|^2,
+//   E = K + A / S,  Var = Q / S - |A / S|^2  (clamped at 0),
+// which equals the two-pass form up to rounding (the shift keeps |A / S| of
+// the order of the spread, so the difference loses no significant digits).
+// The reduction order is fixed (strided per-thread sums with RPT rows' loads
+// issued together, a shuffle tree per warp, the warps' partials in warp order):
+// the result is deterministic.  The loads go through L2, so a caller may
+// reduce rows that other CTAs of its own grid wrote (after a fence).
+template <int NT>
+__device__ void cta_energy_stats(const double* ere, const double* eim, const uint64_t* counts, uint64_t n_x,
+                                 double* stats) {
+  constexpr int RPT = 4;
+  __shared__ double red[4][NT / 32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned long long* cnt = reinterpret_cast<const unsigned long long*>(counts);
+  const double kr = n_x ? __ldcg(ere) : 0.0, ki = n_x ? __ldcg(eim) : 0.0;
+  double cs = 0.0, ar = 0.0, ai = 0.0, q = 0.0;  // counts below 2^53 add exactly in FP64
+  for (uint64_t l0 = 0; l0 < n_x; l0 += uint64_t(NT) * RPT) {
+    double c[RPT], er[RPT], ei[RPT];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const uint64_t l = l0 + uint64_t(r) * NT + threadIdx.x;
+      const bool in = l < n_x;
+      c[r] = in ? double(__ldcg(cnt + l)) : 0.0;
+      er[r] = in ? __ldcg(ere + l) : kr;
+      ei[r] = in ? __ldcg(eim + l) : ki;
+    }
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+      const double dr = er[r] - kr, di = ei[r] - ki;
+      cs += c[r];
+      ar = fma(c[r], dr, ar);
+      ai = fma(c[r], di, ai);
+      q = fma(c[r], fma(dr, dr, di * di), q);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    cs += __shfl_xor_sync(0xffffffffu, cs, o);
+    ar += __shfl_xor_sync(0xffffffffu, ar, o);
+    ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    q += __shfl_xor_sync(0xffffffffu, q, o);
+  }
+  if (lane == 0) {
+    red[0][w] = cs;
+    red[1][w] = ar;
+    red[2][w] = ai;
+    red[3][w] = q;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double S = 0.0, tr = 0.0, ti = 0.0, tq = 0.0;
+    for (int k = 0; k < NT / 32; ++k) {
+      S += red[0][k];
+      tr += red[1][k];
+      ti += red[2][k];
+      tq += red[3][k];
+    }
+    const double mr = tr / S, mi = ti / S;
+    stats[0] = kr + mr;
+    stats[1] = ki + mi;
+    stats[2] = fmax(0.0, tq / S - fma(mr, mr, mi * mi));
+    stats[3] = S;
+  }
+}
+#endif
+
+// Control words of one tensor-core local-energy call, in its workspace: the
+// histogram of the connected rows' first differing slots (the sort), the
+// sort's ticket and the assembly's statistics ticket.  The parents' finalize
+// zeroes them, so the later kernels of the call need no memset.
+constexpr int TC_CTL_WORDS = ANQS_MAX_ORB + 2;
+constexpr int TC_CTL_SORT_TICKET = ANQS_MAX_ORB;
+constexpr int TC_CTL_STATS_TICKET = ANQS_MAX_ORB + 1;
+
+// Where the local-energy assembly writes the statistics of the sample set
+// (counts null: none).  ticket is a zeroed word (TC_CTL_STATS_TICKET); the
+// assembly's CTAs take a ticket each when their rows are written and the last
+// one reduces.
+struct StatsOut {
+  const uint64_t* counts;
+  double* stats;
+  uint32_t* ticket;
+};
+
 // Hamiltonian as seen by the kernels (passed by value).
 struct HamView {
   int n, na, nb;
@@ -342,13 +432,14 @@ struct MultiEloc {
 };
 int eloc_tc_pre(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, void* ws, size_t ws_bytes,
                 cudaStream_t s);
-int eloc_tc_post(const anqs_ham* H, Count n_x, double* ere, double* eim, void* ws, size_t ws_bytes, cudaStream_t s);
+int eloc_tc_post(const anqs_ham* H, Count n_x, double* ere, double* eim, const uint64_t* counts, double* stats,
+                 void* ws, size_t ws_bytes, cudaStream_t s);
 int mlp_tc_multi_max();
 size_t mlp_tc_multi_groups_bytes();
 int launch_mlp_tc_multi(const MultiEloc* q, int n, int chunk, int dynamic, void* groups, uint32_t* ctl,
                         cudaStream_t s);
 int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere,
-                double* eim, void* ws, size_t ws_bytes, cudaStream_t s);
+                double* eim, const uint64_t* counts, double* stats, void* ws, size_t ws_bytes, cudaStream_t s);
 int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la,
                          float* ph, cudaStream_t s);
 int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, const uint64_t* pre,
@@ -358,20 +449,23 @@ int launch_mlp_tc_prefix_logits(const anqs_model* M, const anqs_ham* H, float* o
 int mlp_tc_status(const anqs_model* M, int* status);
 // pieces of the tensor-core local-energy pipeline shared by the MLP and transformer forms
 constexpr int TC_CACHE_F = 10;  // floats per (parent, slot): prefix la, ph, 4 masked terms, 4 phases
+// ctl (optional): the call's TC_CTL_WORDS control words, set to zero
 int launch_tc_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
-                       float* cache, cudaStream_t s);
-int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* hist, uint32_t* cursor, uint32_t* offsets,
+                       float* cache, cudaStream_t s, uint32_t* ctl = nullptr);
+// ctl: the call's control words, zeroed by the finalize before it
+int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* ctl, uint32_t* cursor, uint32_t* offsets,
                    uint32_t* perm, cudaStream_t s);
 int launch_eloc_assemble(int n, uint32_t K, Count n_x, const uint64_t* xp, const uint8_t* js, const float* cache,
                          const float2* T, const double* hval, const double* hdiag, const float* la_x,
-                         const float* ph_x, double* ere, double* eim, cudaStream_t s, bool tsum = false);
+                         const float* ph_x, double* ere, double* eim, const StatsOut& so, cudaStream_t s,
+                         bool tsum = false);
 // BF16 transformer form
 int tf_tc_pack_alloc(anqs_model* m);
 int tf_tc_pack(anqs_model* m, cudaStream_t s);
 int tf_tc_status(const anqs_model* M, int* status);
 size_t tf_tc_eloc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x);
 int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,
-                   void* ws, size_t ws_bytes, cudaStream_t s);
+                   const uint64_t* counts, double* stats, void* ws, size_t ws_bytes, cudaStream_t s);
 int launch_tf_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t* x, uint64_t n_x, float* la,
                         float* ph, cudaStream_t s);
 int launch_tf_tc_slot_logits(const anqs_model* M, int p, const uint64_t* pre, const uint64_t* n_dev,
@@ -388,7 +482,7 @@ int launch_nade_grad(const NadeView& m, const HamView& hv, const uint64_t* x, Co
 size_t nade_grad_partial_floats(const NadeView& m, uint64_t n_params, uint64_t n_x);
 size_t nade_eloc_workspace(const anqs_ham* H, uint64_t n_x);
 int run_eloc_nade(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,
-                  void* ws, size_t ws_bytes, cudaStream_t s);
+                  const uint64_t* counts, double* stats, void* ws, size_t ws_bytes, cudaStream_t s);
 
 // api.cu
 int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, float* la,

@@ -49,74 +49,15 @@ __global__ void eloc_sum_kernel(uint32_t K, Count n_x_, const double* __restrict
   }
 }
 
-// single CTA of STATS_T threads: S (integer), E (complex) then Var in a
-// second pass.  Few warps on purpose: a warp-wide FP64 add is slow on this
-// GPU, so the shuffle trees of many warps would cost more than the rows.
+// single CTA of STATS_T threads: S, E (complex) and Var in one shifted pass
+// (cta_energy_stats).  Few warps on purpose: a warp-wide FP64 add is slow on
+// this GPU, so the shuffle trees of many warps would cost more than the rows.
 constexpr int STATS_T = 256;
 __global__ void __launch_bounds__(STATS_T) stats_kernel(const double* __restrict__ ere, const double* __restrict__ eim,
                                                         const uint64_t* __restrict__ counts, Count n_x_,
                                                         double* __restrict__ stats) {
   ANQS_PDL_ENTRY();
-  __shared__ double red_r[STATS_T / 32], red_i[STATS_T / 32];
-  __shared__ unsigned long long red_s[STATS_T / 32];
-  __shared__ double s_mean[3];
-  const uint64_t n_x = n_x_.get();
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned long long cs = 0;
-  double sr = 0.0, si = 0.0;
-  for (uint64_t l = threadIdx.x; l < n_x; l += STATS_T) {
-    const uint64_t c = counts[l];
-    const double wt = double(c);
-    cs += c;
-    sr = fma(wt, ere[l], sr);
-    si = fma(wt, eim[l], si);
-  }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) {
-    cs += __shfl_xor_sync(0xffffffffu, cs, o);
-    sr += __shfl_xor_sync(0xffffffffu, sr, o);
-    si += __shfl_xor_sync(0xffffffffu, si, o);
-  }
-  if (lane == 0) {
-    red_s[w] = cs;
-    red_r[w] = sr;
-    red_i[w] = si;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long ts = 0;
-    double tr = 0.0, ti = 0.0;
-    for (int k = 0; k < STATS_T / 32; ++k) {
-      ts += red_s[k];
-      tr += red_r[k];
-      ti += red_i[k];
-    }
-    const double S = double(ts);
-    s_mean[0] = tr / S;
-    s_mean[1] = ti / S;
-    s_mean[2] = S;
-  }
-  __syncthreads();
-  const double Er = s_mean[0], Ei = s_mean[1], s = s_mean[2];
-  double v = 0.0;
-  for (uint64_t l = threadIdx.x; l < n_x; l += STATS_T) {
-    const double wt = double(counts[l]);
-    const double dr = ere[l] - Er, di = eim[l] - Ei;
-    v = fma(wt, dr * dr + di * di, v);
-  }
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red_r[w] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    v = 0.0;
-    for (int k = 0; k < STATS_T / 32; ++k) v += red_r[k];
-    stats[0] = Er;
-    stats[1] = Ei;
-    stats[2] = v / s;
-    stats[3] = s;
-  }
+  cta_energy_stats<STATS_T>(ere, eim, counts, n_x_.get(), stats);
 }
 
 // cot_la = 2 w Re(eloc - E), cot_ph = 2 w Im(eloc - E), w = n / S

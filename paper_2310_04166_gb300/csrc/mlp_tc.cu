@@ -1176,7 +1176,8 @@ __global__ void __launch_bounds__(MT, 1) mlp_tc_grad_kernel(const __grid_constan
 // float32 and the sum in FP64, reduced in a fixed order (deterministic).  The
 // suffix terms come per (x', slot) (T[x'][p], MLP and NADE) or already summed
 // per x' (T[x'], `tsum`: the transformer, whose suffix kernel holds a
-// sequence's positions in one tile).
+// sequence's positions in one tile).  With so.counts set, the last CTA to
+// finish also reduces the statistics of the sample set over every row.
 constexpr int AT = 128;
 __global__ void __launch_bounds__(AT) eloc_assemble_kernel(int n, uint32_t K, Count n_x_, const uint64_t* __restrict__ xp,
                                                            const uint8_t* __restrict__ js,
@@ -1186,9 +1187,10 @@ __global__ void __launch_bounds__(AT) eloc_assemble_kernel(int n, uint32_t K, Co
                                                            const double* __restrict__ hdiag,
                                                            const float* __restrict__ la_x,
                                                            const float* __restrict__ ph_x, double* __restrict__ ere,
-                                                           double* __restrict__ eim, int tsum) {
+                                                           double* __restrict__ eim, int tsum, StatsOut so) {
   ANQS_PDL_ENTRY();
   __shared__ double red[2][AT / 32];
+  __shared__ int s_last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint64_t n_x = n_x_.get();
   for (uint64_t l = blockIdx.x; l < n_x; l += gridDim.x) {
@@ -1244,17 +1246,29 @@ __global__ void __launch_bounds__(AT) eloc_assemble_kernel(int n, uint32_t K, Co
     }
     __syncthreads();
   }
+  if (so.counts) {
+    if (threadIdx.x == 0) {
+      __threadfence();  // this CTA's rows (written by thread 0) before its ticket
+      s_last = atomicAdd(so.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      cta_energy_stats<AT>(ere, eim, so.counts, n_x, so.stats);
+    }
+  }
 }
 
 // Per row: masked half-log-probabilities from the raw slot outputs, prefix
 // sums and log psi (and the parent cache when requested).
 __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x_,
                                 const float* __restrict__ raw, float* __restrict__ la_out, float* __restrict__ ph_out,
-                                float* __restrict__ cache) {
+                                float* __restrict__ cache, uint32_t* __restrict__ ctl) {
   // one warp per row, lane p = slot p (n <= 32): the slots' loads go out
   // together; the prefix sums are passed from lane to lane in slot order, so
   // they are added in the same order as a running sum over the slots
   ANQS_PDL_ENTRY();
+  if (ctl && blockIdx.x == 0 && threadIdx.x < TC_CTL_WORDS) ctl[threadIdx.x] = 0u;
   const int n = hv.n, lane = threadIdx.x & 31;
   const uint64_t n_x = n_x_.get();
   const uint64_t w0 = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
@@ -1321,9 +1335,14 @@ __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Cou
 }
 
 // ---- sort of connected rows by first differing slot ---------------------------
-__global__ void js_hist_kernel(const uint8_t* __restrict__ js, Count m_, int n, uint32_t* __restrict__ hist) {
+// Histogram of the first slots into ctl[0, n) (zero on entry); the last CTA
+// to finish then writes cursor[i] = offsets[i] = rows with first slot < i
+// (exclusive prefix sums) and offsets[n] = rows.
+__global__ void js_hist_kernel(const uint8_t* __restrict__ js, Count m_, int n, uint32_t* __restrict__ ctl,
+                               uint32_t* __restrict__ cursor, uint32_t* __restrict__ offsets) {
   ANQS_PDL_ENTRY();
   __shared__ uint32_t h[ANQS_MAX_ORB];
+  __shared__ int s_last;
   const uint64_t m = m_.get();
   for (int i = threadIdx.x; i < n; i += blockDim.x) h[i] = 0;
   __syncthreads();
@@ -1331,21 +1350,26 @@ __global__ void js_hist_kernel(const uint8_t* __restrict__ js, Count m_, int n, 
     atomicAdd(&h[js[t]], 1u);
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x)
-    if (h[i]) atomicAdd(&hist[i], h[i]);
-}
-
-// cursor[i] = offsets[i] = rows with first slot < i (exclusive prefix sums)
-__global__ void js_offsets_kernel(const uint32_t* __restrict__ hist, int n, uint32_t* __restrict__ cursor,
-                                  uint32_t* __restrict__ offsets) {
-  ANQS_PDL_ENTRY();
-  if (threadIdx.x == 0) {
-    uint32_t acc = 0;
-    for (int i = 0; i < n; ++i) {
-      cursor[i] = acc;
-      offsets[i] = acc;
-      acc += hist[i];
+    if (h[i]) atomicAdd(&ctl[i], h[i]);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&ctl[TC_CTL_SORT_TICKET], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (s_last && threadIdx.x < 32) {  // one warp, lane i = slot i (n <= 32): an inclusive scan
+    __threadfence();
+    const int i = threadIdx.x;
+    const uint32_t h_i = i < n ? __ldcg(ctl + i) : 0u;
+    uint32_t inc = h_i;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (i >= o) inc += v;
     }
-    offsets[n] = acc;
+    if (i < n) {
+      cursor[i] = inc - h_i;
+      offsets[i] = inc - h_i;
+    }
+    if (i == n - 1) offsets[n] = inc;
   }
 }
 
@@ -1475,10 +1499,10 @@ int launch_slots(const anqs_model* M, const TileArgs& ta, cudaStream_t s, int pr
 }
 
 int launch_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
-                    float* cache, cudaStream_t s) {
+                    float* cache, cudaStream_t s, uint32_t* ctl = nullptr) {
   uint64_t blocks = (n_x.n + 3) / 4;  // four rows (warps) per CTA of 128 threads
   if (blocks > 152 * 16) blocks = 152 * 16;
-  ANQS_CUDA_LAUNCH("finalize_kernel", launch_k(finalize_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(128), 0, s, hv, x, n_x, raw, la, ph, cache));
+  ANQS_CUDA_LAUNCH("finalize_kernel", launch_k(finalize_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(128), 0, s, hv, x, n_x, raw, la, ph, cache, ctl));
   return ANQS_OK;
 }
 
@@ -1489,7 +1513,7 @@ struct ElocWs {
   double* hd;
   float *la_x, *ph_x, *raw, *cache;
   float2* T;
-  uint32_t *perm, *hist, *cursor, *offsets;
+  uint32_t *perm, *hist, *cursor, *offsets, *ticket;
 };
 
 size_t plan_eloc(const anqs_ham* H, uint64_t n_x, Arena& A, ElocWs& w) {
@@ -1504,9 +1528,10 @@ size_t plan_eloc(const anqs_ham* H, uint64_t n_x, Arena& A, ElocWs& w) {
   w.cache = A.take<float>(n_x * H->v.n * CACHE_F);
   w.T = A.take<float2>(m * H->v.n);
   w.perm = A.take<uint32_t>(m);
-  w.hist = A.take<uint32_t>(ANQS_MAX_ORB);
   w.cursor = A.take<uint32_t>(ANQS_MAX_ORB);
   w.offsets = A.take<uint32_t>(ANQS_MAX_ORB + 1);
+  w.hist = A.take<uint32_t>(TC_CTL_WORDS);
+  w.ticket = w.hist + TC_CTL_STATS_TICKET;
   return A.off;
 }
 
@@ -1610,30 +1635,29 @@ int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, con
 }
 
 int launch_tc_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
-                       float* cache, cudaStream_t s) {
-  return launch_finalize(hv, x, n_x, raw, la, ph, cache, s);
+                       float* cache, cudaStream_t s, uint32_t* ctl) {
+  return launch_finalize(hv, x, n_x, raw, la, ph, cache, s, ctl);
 }
 
-int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* hist, uint32_t* cursor, uint32_t* offsets,
+int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* ctl, uint32_t* cursor, uint32_t* offsets,
                    uint32_t* perm, cudaStream_t s) {
   if (mc.n <= JS_SMALL) {
     ANQS_CUDA_LAUNCH("js_sort_small_kernel", launch_k(js_sort_small_kernel, dim3(1), dim3(1024), 0, s, js, mc, n, offsets, perm));
     return ANQS_OK;
   }
-  ANQS_CUDA(cudaMemsetAsync(hist, 0, ANQS_MAX_ORB * sizeof(uint32_t), s));
   const unsigned g = unsigned(std::min<uint64_t>((mc.n + 255) / 256, 152 * 4));
-  ANQS_CUDA_LAUNCH("js_hist_kernel", launch_k(js_hist_kernel, dim3(g ? g : 1), dim3(256), 0, s, js, mc, n, hist));
-  ANQS_CUDA_LAUNCH("js_offsets_kernel", launch_k(js_offsets_kernel, dim3(1), dim3(32), 0, s, hist, n, cursor, offsets));
+  ANQS_CUDA_LAUNCH("js_hist_kernel", launch_k(js_hist_kernel, dim3(g ? g : 1), dim3(256), 0, s, js, mc, n, ctl, cursor, offsets));
   ANQS_CUDA_LAUNCH("js_scatter_kernel", launch_k(js_scatter_kernel, dim3(g ? g : 1), dim3(256), 0, s, js, mc, cursor, perm));
   return ANQS_OK;
 }
 
 int launch_eloc_assemble(int n, uint32_t K, Count n_x, const uint64_t* xp, const uint8_t* js, const float* cache,
                          const float2* T, const double* hval, const double* hdiag, const float* la_x,
-                         const float* ph_x, double* ere, double* eim, cudaStream_t s, bool tsum) {
+                         const float* ph_x, double* ere, double* eim, const StatsOut& so, cudaStream_t s,
+                         bool tsum) {
   uint64_t blocks = n_x.n;
   if (blocks > 152 * 16) blocks = 152 * 16;
-  ANQS_CUDA_LAUNCH("eloc_assemble_kernel", launch_k(eloc_assemble_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(AT), 0, s, n, K, n_x, xp, js, cache, T, hval, hdiag, la_x, ph_x, ere, eim, tsum ? 1 : 0));
+  ANQS_CUDA_LAUNCH("eloc_assemble_kernel", launch_k(eloc_assemble_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(AT), 0, s, n, K, n_x, xp, js, cache, T, hval, hdiag, la_x, ph_x, ere, eim, tsum ? 1 : 0, so));
   return ANQS_OK;
 }
 
@@ -1673,23 +1697,23 @@ int eloc_tc_pre(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count
     ta.raw = w.raw;
     ANQS_TRY(launch_slots(M, ta, s, PROF_TC_PARENT));
     ProfScope ps(PROF_TC_FINALIZE, s);
-    ANQS_TRY(launch_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
+    ANQS_TRY(launch_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s, w.hist));
   }
   ProfScope ps(PROF_TC_SORT, s);
   return launch_js_sort(w.js, mc, H->v.n, w.hist, w.cursor, w.offsets, w.perm, s);
 }
 
-int eloc_tc_post(const anqs_ham* H, Count n_x, double* ere, double* eim, void* ws, size_t ws_bytes,
-                 cudaStream_t s) {
+int eloc_tc_post(const anqs_ham* H, Count n_x, double* ere, double* eim, const uint64_t* counts, double* stats,
+                 void* ws, size_t ws_bytes, cudaStream_t s) {
   ElocWs w;
   ANQS_TRY(plan_ws(H, n_x, ws, ws_bytes, w));
   ProfScope ps(PROF_TC_ELOC, s);
   return launch_eloc_assemble(H->v.n, uint32_t(H->v.K), n_x, w.xp, w.js, w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x,
-                              ere, eim, s);
+                              ere, eim, StatsOut{counts, stats, w.ticket}, s);
 }
 
 int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,
-                void* ws, size_t ws_bytes, cudaStream_t s) {
+                const uint64_t* counts, double* stats, void* ws, size_t ws_bytes, cudaStream_t s) {
   ElocWs w;
   ANQS_TRY(plan_ws(H, n_x, ws, ws_bytes, w));
   ANQS_TRY(eloc_tc_pre(M, H, x, n_x, ws, ws_bytes, s));
@@ -1698,7 +1722,7 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count
     ProfScope ps(PROF_TC_SUFFIX, s);
     ANQS_TRY(tv.W == 128 ? launch_ws_w<128>(tv, H->v, w, s) : launch_ws_w<64>(tv, H->v, w, s));
   }
-  return eloc_tc_post(H, n_x, ere, eim, ws, ws_bytes, s);
+  return eloc_tc_post(H, n_x, ere, eim, counts, stats, ws, ws_bytes, s);
 }
 
 // Shared memory of the tensor-core adjoint of model M (0 when it does not

@@ -503,7 +503,7 @@ struct NadeElocWs {
   uint8_t* js;
   float *la_x, *ph_x, *raw, *cache;
   float2* T;
-  uint32_t *perm, *hist, *cursor, *offsets;
+  uint32_t *perm, *hist, *cursor, *offsets, *ticket;
 };
 
 size_t plan_eloc(const anqs_ham* H, uint64_t n_x, Arena& A, NadeElocWs& w) {
@@ -518,9 +518,10 @@ size_t plan_eloc(const anqs_ham* H, uint64_t n_x, Arena& A, NadeElocWs& w) {
   w.cache = A.take<float>(n_x * n * TC_CACHE_F);
   w.T = A.take<float2>(m * n);
   w.perm = A.take<uint32_t>(m);
-  w.hist = A.take<uint32_t>(ANQS_MAX_ORB);
   w.cursor = A.take<uint32_t>(ANQS_MAX_ORB);
   w.offsets = A.take<uint32_t>(ANQS_MAX_ORB + 1);
+  w.hist = A.take<uint32_t>(TC_CTL_WORDS);
+  w.ticket = w.hist + TC_CTL_STATS_TICKET;
   return A.off;
 }
 
@@ -559,7 +560,7 @@ size_t nade_eloc_workspace(const anqs_ham* H, uint64_t n_x) {
 // slot j (SUFFIX, rows sorted by j); the assembly adds them up and sums
 // H_xx' psi(x')/psi(x) in FP64.
 int run_eloc_nade(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,
-                  void* ws, size_t ws_bytes, cudaStream_t s) {
+                  const uint64_t* counts, double* stats, void* ws, size_t ws_bytes, cudaStream_t s) {
   Arena A(ws, ws_bytes);
   NadeElocWs w;
   plan_eloc(H, n_x.n, A, w);
@@ -575,7 +576,7 @@ int run_eloc_nade(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Cou
     a.out8 = w.raw;
     ANQS_TRY(fwd<MODE_RAW>(M->nade, H->v, a, n_x.n, PROF_NADE_PARENT, s));
     ProfScope ps(PROF_TC_FINALIZE, s);
-    ANQS_TRY(launch_tc_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
+    ANQS_TRY(launch_tc_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s, w.hist));
   }
   {
     ProfScope ps(PROF_TC_SORT, s);
@@ -593,7 +594,7 @@ int run_eloc_nade(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Cou
   }
   ProfScope ps(PROF_TC_ELOC, s);
   return launch_eloc_assemble(H->v.n, uint32_t(K), n_x, w.xp, w.js, w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x, ere, eim,
-                              s);
+                              StatsOut{counts, stats, w.ticket}, s);
 }
 
 // ---------------------------------------------------------------------------

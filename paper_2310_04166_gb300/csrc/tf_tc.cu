@@ -747,7 +747,7 @@ struct TfElocWs {
   double* hd;
   float *la_x, *ph_x, *raw, *cache;
   float2* T;
-  uint32_t *perm, *hist, *cursor, *offsets;
+  uint32_t *perm, *hist, *cursor, *offsets, *ticket;
   __half* kv;
 };
 
@@ -763,9 +763,10 @@ size_t plan(const anqs_model* M, const anqs_ham* H, uint64_t n_x, Arena& A, TfEl
   w.cache = A.take<float>(n_x * n * TC_CACHE_F);
   w.T = A.take<float2>(m);  // one sum of the suffix positions' terms per connected determinant
   w.perm = A.take<uint32_t>(m);
-  w.hist = A.take<uint32_t>(ANQS_MAX_ORB);
   w.cursor = A.take<uint32_t>(ANQS_MAX_ORB);
   w.offsets = A.take<uint32_t>(ANQS_MAX_ORB + 1);
+  w.hist = A.take<uint32_t>(TC_CTL_WORDS);
+  w.ticket = w.hist + TC_CTL_STATS_TICKET;
   w.kv = A.take<__half>(n_x * uint64_t(M->d.n_layers) * n * 2 * uint64_t(M->d.d_model));
   return A.off;
 }
@@ -836,7 +837,7 @@ size_t tf_tc_eloc_workspace(const anqs_model* M, const anqs_ham* H, uint64_t n_x
 }
 
 int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, double* ere, double* eim,
-                   void* ws, size_t ws_bytes, cudaStream_t s) {
+                   const uint64_t* counts, double* stats, void* ws, size_t ws_bytes, cudaStream_t s) {
   Arena A(ws, ws_bytes);
   TfElocWs w;
   plan(M, H, n_x.n, A, w);
@@ -854,7 +855,7 @@ int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Co
       ANQS_TRY(launch(M, a, (n_x.n + MT / n - 1) / (MT / n), PROF_TF_TC_PARENT, s));
     }
     ProfScope ps(PROF_TC_FINALIZE, s);
-    ANQS_TRY(launch_tc_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
+    ANQS_TRY(launch_tc_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s, w.hist));
   }
   {
     ProfScope ps(PROF_TC_SORT, s);
@@ -880,7 +881,7 @@ int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Co
   {
     ProfScope ps(PROF_TC_ELOC, s);
     ANQS_TRY(launch_eloc_assemble(n, uint32_t(K), n_x, w.xp, w.js, w.cache, w.T, w.hv, w.hd, w.la_x, w.ph_x, ere,
-                                  eim, s, true));
+                                  eim, StatsOut{counts, stats, w.ticket}, s, true));
   }
   return ANQS_OK;
 }

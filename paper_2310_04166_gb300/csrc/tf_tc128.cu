@@ -53,8 +53,6 @@
 
 namespace anqs {
 
-int launch_tc_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
-                       float* cache, cudaStream_t s);
 
 namespace {
 
