@@ -299,14 +299,18 @@ def _config(w, args):
                             "gradient all-reduce per step" if args.gpus > 1 else "single GPU")}
 
 
-# DRAM bytes per launch from one ncu capture of the same kernel build and
-# workload (`ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
-# --clock-control none -c 80 --csv python bench.py --kernel-case`, h2o, 16-bit
-# form): dram__bytes_read.sum + dram__bytes_write.sum.  A kernel changed since
-# that capture has no entry (traffic null).
-TRAFFIC = {("h2o", "bf16"): {"mlp_tc_suffix_kernel": 1321728, "mlp_tc_parent_kernel": 657408,
-                             "mlp_tc_grad_kernel": 609792, "eloc_assemble_kernel": 4651264,
-                             "connected_kernel": 64512, "grad_partial_sum_kernel": 4009984}}
+# DRAM bytes per launch from ncu captures of the same kernel build and
+# workload (h2o, 16-bit form): dram__bytes_read.sum + dram__bytes_write.sum.
+# The suffix from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum
+# --clock-control none -k regex:'mlp_tc_ws|eloc_assemble|js_hist' -s 6 -c 3 --csv
+# python bench.py --steps 2 --warmup 3 --no-cpu-baseline --one-form --no-extra`
+# (the third step's launch); the others from `ncu --metrics
+# dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+# --clock-control none -c 80 --csv python bench.py --kernel-case`.  A kernel
+# changed since its capture has no entry (traffic null).
+TRAFFIC = {("h2o", "bf16"): {"mlp_tc_suffix_kernel": 1327104, "mlp_tc_parent_kernel": 657408,
+                             "mlp_tc_grad_kernel": 609792, "connected_kernel": 64512,
+                             "grad_partial_sum_kernel": 4009984}}
 
 
 # kernel families that evaluate the connected determinants' amplitudes, in
