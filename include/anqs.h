@@ -332,9 +332,20 @@ ANQS_API int anqs_stats_combine(const double* stats_in_dev, int world, double* s
 
 /* Device-side status of the model's BF16 tensor-core kernels (synchronous):
  * 0, or 1 when a bounded wait inside a kernel (weight copy or MMA completion,
- * 2 s each) gave up since the model was created; the kernel then stopped and
- * the outputs of that call are invalid.  Always 0 for the FP32 forms. */
+ * 2 s each) or the persistent sampler's grid barrier (2 s per level) gave up
+ * since the model was created; the kernel then stopped and the outputs of
+ * that call are invalid (a sampling pass that gave up returns n_unique = 0).
+ * Always 0 for the FP32 forms. */
 ANQS_API int anqs_model_status(const anqs_model* model, int* status);
+
+/* Test hook for failure detection without a GPU fault (process-wide, not
+ * thread-safe; set it only while no sampling call is being queued).  With
+ * extra_arrivals > 0 every grid barrier of the persistent sampler waits for
+ * that many CTAs more than its grid has, an arrival that never comes, and
+ * gives up after limit_ns (0: the default 2 s): every CTA leaves, the model's
+ * status word is set and the pass returns no samples.  extra_arrivals = 0 and
+ * limit_ns = 0 restore the defaults.  Always ANQS_OK. */
+ANQS_API int anqs_test_sampler_barrier(unsigned extra_arrivals, uint64_t limit_ns);
 
 /* ---------------------------------------------------------------------------
  * Local energy and energy statistics (Eq. local_energy_def, Eq. energy_est)

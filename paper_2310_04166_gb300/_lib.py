@@ -63,6 +63,7 @@ SIGNATURES = {
     "anqs_hamiltonian_status": (C.c_int, [_VP, C.POINTER(C.c_int), C.c_int]),
     "anqs_hamiltonian_set_z2": (C.c_int, [_VP, C.c_int, _VP]),
     "anqs_model_status": (C.c_int, [_VP, C.POINTER(C.c_int)]),
+    "anqs_test_sampler_barrier": (C.c_int, [C.c_uint, _U64]),
     "anqs_stats_combine": (C.c_int, [_VP, C.c_int, _VP, _VP]),
     "anqs_local_energy_workspace_size": (C.c_int, [_VP, _VP, _U64, C.POINTER(_SZ)]),
     "anqs_local_energy": (C.c_int, [_VP, _VP, _VP, _VP, _U64, _VP, _VP, _VP, _VP, _VP, _SZ, _VP]),

@@ -608,6 +608,11 @@ int anqs_model_sync(anqs_model* M, void* stream) {
   return ANQS_OK;
 }
 
+int anqs_test_sampler_barrier(unsigned extra_arrivals, uint64_t limit_ns) {
+  sampler_test_barrier(extra_arrivals, limit_ns);
+  return ANQS_OK;
+}
+
 int anqs_model_status(const anqs_model* M, int* status) {
   if (!M || !status) return set_error(ANQS_ERR_ARG, "null argument");
   *status = 0;

@@ -490,6 +490,8 @@ int logpsi_dispatch(const anqs_model* M, const anqs_ham* H, const uint64_t* x, C
 
 // sampler.cu
 size_t sampler_workspace(const anqs_ham* ham, uint64_t n_samples);
+// anqs_test_sampler_barrier: the persistent sampler's barrier target and limit
+void sampler_test_barrier(unsigned extra_arrivals, uint64_t limit_ns);
 int run_sampler(const anqs_model* md, const anqs_ham* ham, uint64_t n_samples, uint64_t seed,
                 uint64_t counter, const uint64_t* counter_dev, uint64_t* x_out, uint64_t* n_out,
                 uint64_t* n_unique, void* ws, size_t ws_bytes, cudaStream_t s, int rank = 0, int world = 1,

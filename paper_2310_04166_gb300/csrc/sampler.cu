@@ -713,6 +713,15 @@ constexpr int kStageRows = 1024;
 constexpr size_t STAGE_DYN = size_t(kStageRows) * (32 + 16 + 1);  // thresholds, child rows, masks
 constexpr uint64_t kBarrierNs = 2000000000ull;
 
+// The grid barrier's arrival target (gridDim.x + extra) and time limit.  extra
+// is 0 and the limit kBarrierNs except under anqs_test_sampler_barrier, which
+// makes every barrier wait for an arrival that never comes.
+struct BarrierCfg {
+  unsigned extra;
+  uint64_t limit_ns;
+};
+BarrierCfg g_barrier_cfg{0u, kBarrierNs};
+
 struct LevelOffsets {
   uint32_t off[ANQS_MAX_ORB + 1];  // table rows of level p: [off[p], off[p + 1])
 };
@@ -734,16 +743,17 @@ __device__ __forceinline__ uint64_t gtimer() {
 // polls it until every CTA has arrived (bounded by kBarrierNs, after which it
 // sets the error word and every CTA leaves).  Writes before the barrier are
 // visible to every CTA after it.
-__device__ bool level_barrier(GridBarrier* gb, int p, int* s_ok) {
+__device__ bool level_barrier(GridBarrier* gb, int p, int* s_ok, const BarrierCfg& bc) {
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     asm volatile("red.relaxed.gpu.global.add.u32 [%0], 1;" ::"l"(&gb->arrive[p]) : "memory");
     int ok = 1;
-    if (ld_acquire_u32(&gb->arrive[p]) < gridDim.x) {
+    const unsigned target = gridDim.x + bc.extra;
+    if (ld_acquire_u32(&gb->arrive[p]) < target) {
       const uint64_t t0 = gtimer();
-      while (ld_acquire_u32(&gb->arrive[p]) < gridDim.x) {
-        if (*reinterpret_cast<volatile int*>(&gb->err) || gtimer() - t0 > kBarrierNs) {
+      while (ld_acquire_u32(&gb->arrive[p]) < target) {
+        if (*reinterpret_cast<volatile int*>(&gb->err) || gtimer() - t0 > bc.limit_ns) {
           atomicExch(&gb->err, 1);
           ok = 0;
           break;
@@ -764,7 +774,8 @@ __global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int 
                                                                 int staged, uint64_t* child, uint64_t child_stride,
                                                                 GridBarrier* gb, uint64_t* __restrict__ x_out,
                                                                 uint64_t* __restrict__ n_out,
-                                                                uint64_t* __restrict__ n_unique, int* status) {
+                                                                uint64_t* __restrict__ n_unique, int* status,
+                                                                BarrierCfg bc) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   uint64_t* fr_pre = reinterpret_cast<uint64_t*>(s_dyn);                        // [2][PER_F]
   uint32_t* fr_cnt = reinterpret_cast<uint32_t*>(fr_pre + 2 * PER_F);            // [2][PER_F]
@@ -964,7 +975,7 @@ __global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int 
         }
     }
     // every CTA's counts of level p are in `ch`
-    ok = level_barrier(gb, p, &s_ok);
+    ok = level_barrier(gb, p, &s_ok, bc);
     if (!ok) break;
     // children in (node, outcome) order -> this CTA's copy of the next frontier
     // (the last level: the output, written by CTA 0)
@@ -1008,7 +1019,10 @@ __global__ void __launch_bounds__(SMALL_T) sample_levels_kernel(HamView hv, int 
     }
     nf = int(carry);
   }
-  if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(&gb->err)) atomicExch(status, 1);
+  if (threadIdx.x == 0 && *reinterpret_cast<volatile int*>(&gb->err)) {
+    atomicExch(status, 1);
+    if (blockIdx.x == 0) *n_unique = 0;  // a pass that gave up returns no samples
+  }
 }
 
 
@@ -1157,7 +1171,7 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
                        cudaLaunchKernelEx(&cfg, sample_levels_kernel, H->v, n, n_samples, seed, counter, counter_dev,
                                           static_cast<const float*>(P.plog), static_cast<const uint64_t*>(H->d_pt_x),
                                           static_cast<const int32_t*>(H->d_pt_child), lvo, staged, P.child, F * 4,
-                                          P.barrier, x_out, n_out, n_unique, status));
+                                          P.barrier, x_out, n_out, n_unique, status, g_barrier_cfg));
       return ANQS_OK;
     }
   }
@@ -1229,6 +1243,11 @@ int logits_dispatch(const anqs_model* M, const anqs_ham* H, int p, const uint64_
     default:
       return set_error(ANQS_ERR_UNSUPPORTED, "sampling for model kind %d not supported by this library", M->d.kind);
   }
+}
+
+void sampler_test_barrier(unsigned extra_arrivals, uint64_t limit_ns) {
+  g_barrier_cfg.extra = extra_arrivals;
+  g_barrier_cfg.limit_ns = limit_ns ? limit_ns : kBarrierNs;
 }
 
 }  // namespace anqs
