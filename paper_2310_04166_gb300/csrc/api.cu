@@ -552,7 +552,7 @@ int anqs_model_create(anqs_model** out, const anqs_model_desc* d, const float* p
     if (d->form == ANQS_FORM_BF16) {
       int r = mlp_tc_pack_alloc(M);
       if (r != ANQS_OK) {
-        delete M;
+        anqs_model_destroy(M);
         return r;
       }
       r = mlp_tc_pack(M, 0);
@@ -596,6 +596,9 @@ int anqs_model_destroy(anqs_model* M) {
   if (!M) return ANQS_OK;
   if (M->packed) cudaFree(M->packed);
   if (M->tc_raw) cudaFree(M->tc_raw);
+  if (M->ev_fork) cudaEventDestroy(M->ev_fork);
+  if (M->ev_join) cudaEventDestroy(M->ev_join);
+  if (M->side) cudaStreamDestroy(M->side);
   delete M;
   return ANQS_OK;
 }

@@ -193,8 +193,8 @@ __device__ void cta_energy_stats(const double* ere, const double* eim, const uin
 
 // Control words of one tensor-core local-energy call, in its workspace: the
 // histogram of the connected rows' first differing slots (the sort), the
-// sort's ticket and the assembly's statistics ticket.  The parents' finalize
-// zeroes them, so the later kernels of the call need no memset.
+// sort's ticket and the assembly's statistics ticket.  The call's connected-set
+// kernel zeroes them, so the later kernels of the call need no memset.
 constexpr int TC_CTL_WORDS = ANQS_MAX_ORB + 2;
 constexpr int TC_CTL_SORT_TICKET = ANQS_MAX_ORB;
 constexpr int TC_CTL_STATS_TICKET = ANQS_MAX_ORB + 1;
@@ -346,6 +346,10 @@ struct anqs_model {
   std::vector<uint64_t> pack_off;  // per slot byte offset of its image
   float* tc_raw;                   // BF16 form: raw slot outputs of one chunk of anqs_logpsi rows
   uint64_t tc_raw_rows;
+  // BF16 MLP: a second stream and its fork and join events, so that one local
+  // energy call runs the parents' slots beside the connected set and its sort
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 // ---- launchers implemented in the kernel translation units ----
@@ -372,8 +376,9 @@ inline cudaError_t launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, siz
 
 
 // connect.cu
+// ctl (optional): a tensor-core local energy's control words, set to zero
 int launch_connected(const HamView& hv, const uint64_t* x, Count n_x, uint64_t* xp, double* hval,
-                     uint8_t* first_slot, double* hdiag, cudaStream_t s);
+                     uint8_t* first_slot, double* hdiag, cudaStream_t s, uint32_t* ctl = nullptr);
 
 // mlp_fp32.cu
 int launch_mlp_fp32_logpsi(const MlpView& m, const HamView& hv, const uint64_t* x, Count n_x,
@@ -430,8 +435,10 @@ struct MultiEloc {
   void* ws;
   size_t ws_bytes;
 };
+// fork: run the parents' slots and finalize on the model's second stream,
+// beside the connected set and the sort (joined back into s before returning)
 int eloc_tc_pre(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, void* ws, size_t ws_bytes,
-                cudaStream_t s);
+                cudaStream_t s, bool fork = false);
 int eloc_tc_post(const anqs_ham* H, Count n_x, double* ere, double* eim, const uint64_t* counts, double* stats,
                  void* ws, size_t ws_bytes, cudaStream_t s);
 int mlp_tc_multi_max();
@@ -449,10 +456,9 @@ int launch_mlp_tc_prefix_logits(const anqs_model* M, const anqs_ham* H, float* o
 int mlp_tc_status(const anqs_model* M, int* status);
 // pieces of the tensor-core local-energy pipeline shared by the MLP and transformer forms
 constexpr int TC_CACHE_F = 10;  // floats per (parent, slot): prefix la, ph, 4 masked terms, 4 phases
-// ctl (optional): the call's TC_CTL_WORDS control words, set to zero
 int launch_tc_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
-                       float* cache, cudaStream_t s, uint32_t* ctl = nullptr);
-// ctl: the call's control words, zeroed by the finalize before it
+                       float* cache, cudaStream_t s);
+// ctl: the call's control words, zeroed by the connected-set kernel before it
 int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* ctl, uint32_t* cursor, uint32_t* offsets,
                    uint32_t* perm, cudaStream_t s);
 int launch_eloc_assemble(int n, uint32_t K, Count n_x, const uint64_t* xp, const uint8_t* js, const float* cache,

@@ -154,10 +154,18 @@ __device__ __forceinline__ void connected_body(const HamView& hv, const uint64_t
   }
 }
 
+// The tensor-core local energy's control words (TC_CTL_WORDS, optional) are
+// zeroed by block 0 of the call's first kernel, on the stream of the kernels
+// that use them (sort histogram, statistics ticket).
+__device__ __forceinline__ void zero_ctl(uint32_t* ctl) {
+  if (ctl && blockIdx.x == 0 && threadIdx.x < TC_CTL_WORDS) ctl[threadIdx.x] = 0u;
+}
+
 __global__ void connected_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x,
                                  uint64_t* __restrict__ xp_out, double* __restrict__ h_out,
-                                 uint8_t* __restrict__ j_out) {
+                                 uint8_t* __restrict__ j_out, uint32_t* __restrict__ ctl) {
   ANQS_PDL_ENTRY();
+  zero_ctl(ctl);
   connected_body(hv, xs, n_x, xp_out, h_out, j_out, blockIdx.x, gridDim.x);
 }
 
@@ -201,8 +209,10 @@ __device__ __forceinline__ void diagonal_body(const HamView& hv, const uint64_t*
   }
 }
 
-__global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x, double* __restrict__ hdiag) {
+__global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x, double* __restrict__ hdiag,
+                                uint32_t* __restrict__ ctl) {
   ANQS_PDL_ENTRY();
+  zero_ctl(ctl);
   diagonal_body(hv, xs, n_x, hdiag, blockIdx.x, gridDim.x);
 }
 
@@ -210,8 +220,10 @@ __global__ void diagonal_kernel(HamView hv, const uint64_t* __restrict__ xs, Cou
 // launch
 __global__ void connected_diag_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x,
                                       uint64_t* __restrict__ xp_out, double* __restrict__ h_out,
-                                      uint8_t* __restrict__ j_out, double* __restrict__ hdiag, unsigned nb_c) {
+                                      uint8_t* __restrict__ j_out, double* __restrict__ hdiag, unsigned nb_c,
+                                      uint32_t* __restrict__ ctl) {
   ANQS_PDL_ENTRY();
+  zero_ctl(ctl);
   if (blockIdx.x < nb_c) connected_body(hv, xs, n_x, xp_out, h_out, j_out, blockIdx.x, nb_c);
   else diagonal_body(hv, xs, n_x, hdiag, blockIdx.x - nb_c, gridDim.x - nb_c);
 }
@@ -219,7 +231,7 @@ __global__ void connected_diag_kernel(HamView hv, const uint64_t* __restrict__ x
 }  // namespace
 
 int launch_connected(const HamView& hv, const uint64_t* x, Count n_x, uint64_t* xp, double* hval,
-                     uint8_t* first_slot, double* hdiag, cudaStream_t s) {
+                     uint8_t* first_slot, double* hdiag, cudaStream_t s, uint32_t* ctl) {
   const int threads = 256;
   uint64_t total = n_x.n * hv.K;
   if (total && hdiag) {
@@ -227,21 +239,22 @@ int launch_connected(const HamView& hv, const uint64_t* x, Count n_x, uint64_t* 
     if (bc > 152ull * 64) bc = 152ull * 64;
     if (bd > 152ull * 16) bd = 152ull * 16;
     ProfScope ps(PROF_CONNECT, s);
-    ANQS_CUDA_LAUNCH("connected_diag_kernel", launch_k(connected_diag_kernel, dim3(unsigned(bc + bd)), dim3(threads), 0, s, hv, x, n_x, xp, hval, first_slot, hdiag, unsigned(bc)));
+    ANQS_CUDA_LAUNCH("connected_diag_kernel", launch_k(connected_diag_kernel, dim3(unsigned(bc + bd)), dim3(threads), 0, s, hv, x, n_x, xp, hval, first_slot, hdiag, unsigned(bc), ctl));
     return ANQS_OK;
   }
   if (total) {
     uint64_t blocks = (total + threads - 1) / threads;
     if (blocks > 152ull * 64) blocks = 152ull * 64;
     ProfScope ps(PROF_CONNECT, s);
-    ANQS_CUDA_LAUNCH("connected_kernel", launch_k(connected_kernel, dim3(unsigned(blocks)), dim3(threads), 0, s, hv, x, n_x, xp, hval, first_slot));
+    ANQS_CUDA_LAUNCH("connected_kernel", launch_k(connected_kernel, dim3(unsigned(blocks)), dim3(threads), 0, s, hv, x, n_x, xp, hval, first_slot, ctl));
+    ctl = nullptr;
   }
   if (hdiag) {
     uint64_t blocks = (n_x.n + 7) / 8;  // 8 warps per CTA
     if (blocks > 152ull * 16) blocks = 152ull * 16;
     if (blocks == 0) blocks = 1;
     ProfScope ps(PROF_DIAGONAL, s);
-    ANQS_CUDA_LAUNCH("diagonal_kernel", launch_k(diagonal_kernel, dim3(unsigned(blocks)), dim3(threads), 0, s, hv, x, n_x, hdiag));
+    ANQS_CUDA_LAUNCH("diagonal_kernel", launch_k(diagonal_kernel, dim3(unsigned(blocks)), dim3(threads), 0, s, hv, x, n_x, hdiag, ctl));
   }
   return ANQS_OK;
 }

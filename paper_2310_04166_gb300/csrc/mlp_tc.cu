@@ -1263,12 +1263,11 @@ __global__ void __launch_bounds__(AT) eloc_assemble_kernel(int n, uint32_t K, Co
 // sums and log psi (and the parent cache when requested).
 __global__ void finalize_kernel(HamView hv, const uint64_t* __restrict__ xs, Count n_x_,
                                 const float* __restrict__ raw, float* __restrict__ la_out, float* __restrict__ ph_out,
-                                float* __restrict__ cache, uint32_t* __restrict__ ctl) {
+                                float* __restrict__ cache) {
   // one warp per row, lane p = slot p (n <= 32): the slots' loads go out
   // together; the prefix sums are passed from lane to lane in slot order, so
   // they are added in the same order as a running sum over the slots
   ANQS_PDL_ENTRY();
-  if (ctl && blockIdx.x == 0 && threadIdx.x < TC_CTL_WORDS) ctl[threadIdx.x] = 0u;
   const int n = hv.n, lane = threadIdx.x & 31;
   const uint64_t n_x = n_x_.get();
   const uint64_t w0 = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
@@ -1499,10 +1498,10 @@ int launch_slots(const anqs_model* M, const TileArgs& ta, cudaStream_t s, int pr
 }
 
 int launch_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
-                    float* cache, cudaStream_t s, uint32_t* ctl = nullptr) {
+                    float* cache, cudaStream_t s) {
   uint64_t blocks = (n_x.n + 3) / 4;  // four rows (warps) per CTA of 128 threads
   if (blocks > 152 * 16) blocks = 152 * 16;
-  ANQS_CUDA_LAUNCH("finalize_kernel", launch_k(finalize_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(128), 0, s, hv, x, n_x, raw, la, ph, cache, ctl));
+  ANQS_CUDA_LAUNCH("finalize_kernel", launch_k(finalize_kernel, dim3(unsigned(blocks ? blocks : 1)), dim3(128), 0, s, hv, x, n_x, raw, la, ph, cache));
   return ANQS_OK;
 }
 
@@ -1573,6 +1572,9 @@ int mlp_tc_pack_alloc(anqs_model* M) {
   ANQS_CUDA(cudaMemset(M->packed, 0, M->packed_bytes));
   M->tc_raw_rows = 32768;
   ANQS_CUDA(cudaMalloc(&M->tc_raw, M->tc_raw_rows * n * 8 * sizeof(float)));
+  ANQS_CUDA(cudaStreamCreateWithFlags(&M->side, cudaStreamNonBlocking));
+  ANQS_CUDA(cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming));
+  ANQS_CUDA(cudaEventCreateWithFlags(&M->ev_join, cudaEventDisableTiming));
   return ANQS_OK;
 }
 
@@ -1635,8 +1637,8 @@ int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, con
 }
 
 int launch_tc_finalize(const HamView& hv, const uint64_t* x, Count n_x, const float* raw, float* la, float* ph,
-                       float* cache, cudaStream_t s, uint32_t* ctl) {
-  return launch_finalize(hv, x, n_x, raw, la, ph, cache, s, ctl);
+                       float* cache, cudaStream_t s) {
+  return launch_finalize(hv, x, n_x, raw, la, ph, cache, s);
 }
 
 int launch_js_sort(const uint8_t* js, Count mc, int n, uint32_t* ctl, uint32_t* cursor, uint32_t* offsets,
@@ -1682,25 +1684,46 @@ static int plan_ws(const anqs_ham* H, Count n_x, void* ws, size_t ws_bytes, Eloc
   return ANQS_OK;
 }
 
+// Two independent chains: the connected set and its sort by first slot (on
+// s), the parents' slot outputs and finalize (on sp: the model's second
+// stream when forking).  The control words are zeroed by the connected-set
+// kernel, on the stream of the histogram and the assembly that use them.
 int eloc_tc_pre(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count n_x, void* ws, size_t ws_bytes,
-                cudaStream_t s) {
+                cudaStream_t s, bool fork) {
   ElocWs w;
   ANQS_TRY(plan_ws(H, n_x, ws, ws_bytes, w));
   const Count mc = scaled(n_x, H->v.K);
-  ANQS_TRY(launch_connected(H->v, x, n_x, w.xp, w.hv, w.js, w.hd, s));
-  {
+  cudaStream_t sp = s;
+  if (fork && M->side) {
+    ANQS_CUDA(cudaEventRecord(M->ev_fork, s));
+    ANQS_CUDA(cudaStreamWaitEvent(M->side, M->ev_fork, 0));
+    sp = M->side;
+  }
+  int r = launch_connected(H->v, x, n_x, w.xp, w.hv, w.js, w.hd, s, w.hist);
+  if (r == ANQS_OK) {
     TileArgs ta{};
     ta.x = x;
     ta.rows = n_x;
     ta.p_lo = 0;
     ta.p_hi = H->v.n;
     ta.raw = w.raw;
-    ANQS_TRY(launch_slots(M, ta, s, PROF_TC_PARENT));
-    ProfScope ps(PROF_TC_FINALIZE, s);
-    ANQS_TRY(launch_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s, w.hist));
+    r = launch_slots(M, ta, sp, PROF_TC_PARENT);
+    if (r == ANQS_OK) {
+      ProfScope ps(PROF_TC_FINALIZE, sp);
+      r = launch_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, sp);
+    }
   }
-  ProfScope ps(PROF_TC_SORT, s);
-  return launch_js_sort(w.js, mc, H->v.n, w.hist, w.cursor, w.offsets, w.perm, s);
+  if (r == ANQS_OK) {
+    ProfScope ps(PROF_TC_SORT, s);
+    r = launch_js_sort(w.js, mc, H->v.n, w.hist, w.cursor, w.offsets, w.perm, s);
+  }
+  if (sp != s) {  // join, also after an error, so that no work of the call is left outside s
+    if (cudaEventRecord(M->ev_join, sp) != cudaSuccess || cudaStreamWaitEvent(s, M->ev_join, 0) != cudaSuccess) {
+      cudaGetLastError();
+      if (r == ANQS_OK) r = set_error(ANQS_ERR_CUDA, "stream join");
+    }
+  }
+  return r;
 }
 
 int eloc_tc_post(const anqs_ham* H, Count n_x, double* ere, double* eim, const uint64_t* counts, double* stats,
@@ -1716,7 +1739,7 @@ int run_eloc_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Count
                 const uint64_t* counts, double* stats, void* ws, size_t ws_bytes, cudaStream_t s) {
   ElocWs w;
   ANQS_TRY(plan_ws(H, n_x, ws, ws_bytes, w));
-  ANQS_TRY(eloc_tc_pre(M, H, x, n_x, ws, ws_bytes, s));
+  ANQS_TRY(eloc_tc_pre(M, H, x, n_x, ws, ws_bytes, s, true));
   {
     TcView tv = make_view(M);
     ProfScope ps(PROF_TC_SUFFIX, s);

@@ -568,7 +568,7 @@ int run_eloc_nade(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Cou
   const uint64_t K = H->v.K;
   const Count mc = scaled(n_x, K);
   if (mc.n > 0xffffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "more than 2^32 connected determinants per call");
-  ANQS_TRY(launch_connected(H->v, x, n_x, w.xp, w.hv, w.js, w.hd, s));
+  ANQS_TRY(launch_connected(H->v, x, n_x, w.xp, w.hv, w.js, w.hd, s, w.hist));
   {
     FwdArgs a{};
     a.x = x;
@@ -576,7 +576,7 @@ int run_eloc_nade(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Cou
     a.out8 = w.raw;
     ANQS_TRY(fwd<MODE_RAW>(M->nade, H->v, a, n_x.n, PROF_NADE_PARENT, s));
     ProfScope ps(PROF_TC_FINALIZE, s);
-    ANQS_TRY(launch_tc_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s, w.hist));
+    ANQS_TRY(launch_tc_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
   }
   {
     ProfScope ps(PROF_TC_SORT, s);

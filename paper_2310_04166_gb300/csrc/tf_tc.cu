@@ -846,7 +846,7 @@ int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Co
   const uint64_t K = H->v.K;
   const Count mc = scaled(n_x, K);
   if (mc.n > 0xffffffffull) return set_error(ANQS_ERR_UNSUPPORTED, "more than 2^32 connected determinants per call");
-  ANQS_TRY(launch_connected(H->v, x, n_x, w.xp, w.hv, w.js, w.hd, s));
+  ANQS_TRY(launch_connected(H->v, x, n_x, w.xp, w.hv, w.js, w.hd, s, w.hist));
   {
     if (M->d.d_model == 128) {
       ANQS_TRY(launch_tf128_full(M, H->v, x, n_x, n, 0, w.raw, w.kv, PROF_TF_TC_PARENT, s));
@@ -855,7 +855,7 @@ int run_eloc_tf_tc(const anqs_model* M, const anqs_ham* H, const uint64_t* x, Co
       ANQS_TRY(launch(M, a, (n_x.n + MT / n - 1) / (MT / n), PROF_TF_TC_PARENT, s));
     }
     ProfScope ps(PROF_TC_FINALIZE, s);
-    ANQS_TRY(launch_tc_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s, w.hist));
+    ANQS_TRY(launch_tc_finalize(H->v, x, n_x, w.raw, w.la_x, w.ph_x, w.cache, s));
   }
   {
     ProfScope ps(PROF_TC_SORT, s);
