@@ -89,7 +89,9 @@ struct ProfScope {
 // So the part of a kernel placed before ANQS_PDL_WAIT() (its prologue) runs
 // while the previous kernel may still execute, but after the kernel before
 // that has completed: a prologue may read data written two or more kernels
-// earlier (e.g. packed weights) and set up TMEM and shared memory.
+// earlier and set up TMEM and shared memory.  The weight-packing kernels do
+// not trigger at all (their dependents start when they have completed), so a
+// prologue may always read packed weight images.
 #define ANQS_PDL_TRIGGER() asm volatile("griddepcontrol.launch_dependents;" ::: "memory")
 #define ANQS_PDL_WAIT() asm volatile("griddepcontrol.wait;" ::: "memory")
 #define ANQS_PDL_ENTRY() \

@@ -108,7 +108,10 @@ struct TcView {
 __device__ __forceinline__ uint16_t f16_bits(float v) { return uint16_t(tc::pack_f16x2(v, 0.f) & 0xFFFFu); }
 __device__ __forceinline__ float f16_value(uint16_t b) { return __half2float(__ushort_as_half(b)); }
 __global__ void pack_kernel(MlpView m, TcView tv, unsigned char* img) {
-  ANQS_PDL_ENTRY();
+  // no early trigger: a later kernel's prologue may read the packed images
+  // before its own dependency wait, so the images are complete before any
+  // dependent launch starts
+  ANQS_PDL_WAIT();
   const int p = blockIdx.y;
   const int W = m.width, L = m.n_hidden;
   const SlotLayout S = slot_layout(p, W, L, tv.lo);

@@ -130,7 +130,10 @@ __device__ __forceinline__ LayerP layer_p(const float* params, int n, int l) {
 
 // ---- packing: f32 parameters -> per-block fp16 canonical images ---------------
 __global__ void tf_pack_kernel(const float* __restrict__ params, int n, int L, unsigned char* __restrict__ img) {
-  ANQS_PDL_ENTRY();
+  // no early trigger: a later kernel's prologue may read the packed images
+  // before its own dependency wait, so the images are complete before any
+  // dependent launch starts
+  ANQS_PDL_WAIT();
   const size_t per = 12 * size_t(D) * D + 13 * D;
   const uint32_t per_layer = LAYER_BYTES / 2;  // elements
   for (uint64_t e = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; e < uint64_t(L) * per_layer;
