@@ -133,3 +133,25 @@ def test_tensor_core_adjoint_with_device_row_count(A):
     nd = torch.tensor([k], dtype=torch.int64, device="cuda")
     g2 = A.grad(model, ham, xb, cb, erb, eib, st, n_dev=nd)
     assert torch.equal(g1, g2)
+
+
+def test_tensor_core_adjoint_directly_after_a_repack(A):
+    """The adjoint kernel bulk-copies the packed weight images before its
+    dependency wait.  The packing kernel never lets a dependent launch start
+    early, so a gradient queued directly after a repack (no other kernel in
+    between: preallocated output and workspace) sees the new weights."""
+    w, ham, model, om, ip, oham = _problem(A, "h2o")
+    x, c = A.sample(model, ham, 100_000, seed=34)
+    ere, eim, st = A.local_energy(model, ham, x, c)
+    ws = A._ws(A.grad_workspace_bytes(model, ham, x.numel()), x.device)
+    g1 = torch.empty(model.n_params, dtype=torch.float32, device=x.device)
+    g2 = torch.empty_like(g1)
+    model.params.mul_(1.25)
+    torch.cuda.synchronize()
+    model.sync()
+    A.grad(model, ham, x, c, ere, eim, st, workspace=ws, out=g1)
+    torch.cuda.synchronize()
+    A.grad(model, ham, x, c, ere, eim, st, workspace=ws, out=g2)
+    torch.cuda.synchronize()
+    assert model.status() == 0
+    assert torch.equal(g1, g2)
