@@ -361,6 +361,12 @@ ANQS_API int anqs_test_sampler_barrier(unsigned extra_arrivals, uint64_t limit_n
  * capacity that sizes launches and the workspace; e.g. pass the sampler's
  * n_unique_dev so that sampling, local energy and gradient can be captured
  * in one CUDA graph.  Outputs beyond *n_x_dev are left untouched.
+ * The statistics are reduced in a fixed order (deterministic), in one pass
+ * shifted by eloc_0 (equal to the two-pass form up to rounding).
+ * The 16-bit MLP form runs part of the call on a second stream owned by the
+ * model, forked from `stream` and joined back into it with events: the call
+ * still orders with the work queued on `stream` and can be captured in a
+ * CUDA graph, but one model must not be used by several host threads at once.
  * ------------------------------------------------------------------------- */
 ANQS_API int anqs_local_energy_workspace_size(const anqs_model* model, const anqs_ham* ham,
                                      uint64_t n_x, size_t* bytes);
