@@ -454,7 +454,14 @@ int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t*
 int launch_mlp_tc_slot_logits(const anqs_model* M, const HamView& hv, int p, const uint64_t* pre,
                               const uint64_t* n_dev, uint64_t max_rows, float* out8, cudaStream_t s);
 // slot-p outputs of every prefix of the prefix table (level p's rows use slot p), one launch
-int launch_mlp_tc_prefix_logits(const anqs_model* M, const anqs_ham* H, float* out8, cudaStream_t s);
+// Words that a launch sets to zero (block 0, after its dependency wait), for
+// the kernel after it: up to two ranges of 32-bit words.
+struct ZeroWords {
+  uint32_t* p[2];
+  int n[2];
+};
+int launch_mlp_tc_prefix_logits(const anqs_model* M, const anqs_ham* H, float* out8, cudaStream_t s,
+                                ZeroWords zero = ZeroWords{});
 int mlp_tc_status(const anqs_model* M, int* status);
 // pieces of the tensor-core local-energy pipeline shared by the MLP and transformer forms
 constexpr int TC_CACHE_F = 10;  // floats per (parent, slot): prefix la, ph, 4 masked terms, 4 phases

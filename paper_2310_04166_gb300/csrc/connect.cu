@@ -53,8 +53,16 @@ __device__ __forceinline__ void connected_body(const HamView& hv, const uint64_t
   const uint64_t total = n_x.get() * K;
   const int n = hv.n;
   for (uint64_t t = bid * blockDim.x + threadIdx.x; t < total; t += nb * blockDim.x) {
-    uint64_t l = t / K;
-    uint32_t k = uint32_t(t - l * K);
+    uint64_t l;
+    uint32_t k;
+    if (total <= 0xffffffffull) {  // the usual case: a 32-bit division instead of a 64-bit one
+      const uint32_t t32 = uint32_t(t), l32 = t32 / uint32_t(K);
+      l = l32;
+      k = t32 - l32 * uint32_t(K);
+    } else {
+      l = t / K;
+      k = uint32_t(t - l * K);
+    }
     uint64_t x = __ldg(xs + l);
     uint32_t oa = spin_occ(x, 0, n), ob = spin_occ(x, 1, n);
     uint32_t full = (n == 32) ? 0xffffffffu : ((1u << n) - 1u);

@@ -172,6 +172,7 @@ struct TileArgs {
   int tpi;                     // SLOTS: 128-row tiles per work item (1..NWG; warpgroups >= tpi idle)
   int levels;                  // LEVELS: rows [lv_off[p], lv_off[p+1]) take slot p (p < levels), raw [row][8]
   uint32_t lv_off[ANQS_MAX_ORB + 1];
+  ZeroWords zero;              // cleared by block 0 for the next kernel
 };
 
 constexpr int NWG = kNwg;     // warpgroups per CTA, one 128-row tile each in flight
@@ -381,6 +382,9 @@ __global__ void __launch_bounds__(NT, 1) mlp_tc_slots_kernel(TcView tv, TileArgs
   }
   ANQS_PDL_WAIT();
   ANQS_PDL_TRIGGER();
+  if (blockIdx.x == 0)
+    for (int r = 0; r < 2; ++r)
+      for (int i = threadIdx.x; i < ta.zero.n[r]; i += NT) ta.zero.p[r][i] = 0u;
   const uint64_t n_rows = ta.rows.get();
   const int tpi = ta.tpi;
   const uint64_t n_groups = (n_rows + uint64_t(tpi) * MT - 1) / (uint64_t(tpi) * MT);
@@ -1213,10 +1217,17 @@ __global__ void __launch_bounds__(AT) eloc_assemble_kernel(int n, uint32_t K, Co
           ph += tv.y;
         }
       } else {
-        for (int p = j + 1; p < n; ++p) {
-          const float2 tv = T[row * n + p];
-          la += tv.x;
-          ph += tv.y;
+        // the terms of slots j+1 .. n-1, eight loads in flight at a time,
+        // added in slot order (the padding adds zeros)
+        for (int p0 = j + 1; p0 < n; p0 += 8) {
+          float2 tv[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) tv[e] = p0 + e < n ? T[row * n + p0 + e] : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            la += tv[e].x;
+            ph += tv[e].y;
+          }
         }
       }
       const double h = hval[row];
@@ -1614,9 +1625,11 @@ int launch_mlp_tc_logpsi(const anqs_model* M, const HamView& hv, const uint64_t*
   return ANQS_OK;
 }
 
-int launch_mlp_tc_prefix_logits(const anqs_model* M, const anqs_ham* H, float* out8, cudaStream_t s) {
+int launch_mlp_tc_prefix_logits(const anqs_model* M, const anqs_ham* H, float* out8, cudaStream_t s,
+                                ZeroWords zero) {
   const int n = H->v.n;
   TileArgs ta{};
+  ta.zero = zero;
   ta.x = H->d_pt_x;
   ta.rows = host_count(H->pt_x.size());
   ta.p_lo = 0;

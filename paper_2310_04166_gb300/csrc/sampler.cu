@@ -1124,10 +1124,6 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
   plan_ws(H, n_samples, A, P);
   if (!A.fits()) return set_error(ANQS_ERR_CAPACITY, "sampler workspace needs %zu bytes", A.off);
   const int n = H->v.n;
-  {
-    ProfScope ps(PROF_SAMPLER, s);
-    ANQS_CUDA_LAUNCH("sampler init_kernel", launch_k(init_kernel, dim3(1), dim3(1), 0, s, P.pre[0], P.cnt[0], P.n_front, n_samples, P.done, P.child, P.idx[0], reinterpret_cast<int*>(P.barrier)));
-  }
   // Prefix-table mode (BF16 MLP, small sectors, multinomial splits on one
   // rank): the network's slot outputs of every physical prefix of every level
   // in one launch, then per level only the split; the frontier carries each
@@ -1135,22 +1131,40 @@ int run_sampler(const anqs_model* M, const anqs_ham* H, uint64_t n_samples, uint
   // path, so the samples are the same bit for bit.
   const bool table = !binom && world == 1 && P.plog && M->d.kind == ANQS_MODEL_MLP &&
                      M->d.form == ANQS_FORM_BF16 && n_samples < (1ull << 31);
+  // all levels in one cooperative launch when its CTAs can all be resident
+  // (one CTA per SM at most, each CTA one window of draw blocks per round);
+  // rows' thresholds, masks and children staged in shared memory when they fit
+  LevelOffsets lvo{};
+  int staged = 0, occ = 0, sms = 0;
+  size_t dyn = 0;
   if (table) {
-    ANQS_TRY(launch_mlp_tc_prefix_logits(M, H, P.plog, s));
-    // all levels in one cooperative launch (one CTA per SM at most, each CTA
-    // one window of draw blocks per round)
-    // rows' thresholds, masks and children staged in shared memory when they fit
-    LevelOffsets lvo{};
     for (int q = 0; q <= n; ++q) lvo.off[q] = H->pt_off[q];
-    const int staged = H->pt_off[n] <= uint32_t(kStageRows) ? 1 : 0;
-    const size_t dyn = PER_DYN + (staged ? STAGE_DYN : 0);
-    int occ = 0;
+    staged = H->pt_off[n] <= uint32_t(kStageRows) ? 1 : 0;
+    dyn = PER_DYN + (staged ? STAGE_DYN : 0);
     ANQS_CUDA(cudaFuncSetAttribute(sample_levels_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(dyn)));
     ANQS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sample_levels_kernel, SMALL_T, dyn));
-    int dev = 0, sms = 0;
+    int dev = 0;
     ANQS_CUDA(cudaGetDevice(&dev));
     ANQS_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    if (occ >= 1) {
+  }
+  const bool persistent = table && occ >= 1;
+  if (!persistent) {
+    ProfScope ps(PROF_SAMPLER, s);
+    ANQS_CUDA_LAUNCH("sampler init_kernel", launch_k(init_kernel, dim3(1), dim3(1), 0, s, P.pre[0], P.cnt[0], P.n_front, n_samples, P.done, P.child, P.idx[0], reinterpret_cast<int*>(P.barrier)));
+  }
+  if (table) {
+    // the persistent kernel needs only its grid barrier and the first
+    // level's child counters cleared: the slot launch before it does that
+    // instead of the initial kernel
+    ZeroWords z{};
+    if (persistent) {
+      z.p[0] = reinterpret_cast<uint32_t*>(P.barrier);
+      z.n[0] = kBarrierWords;
+      z.p[1] = reinterpret_cast<uint32_t*>(P.child);
+      z.n[1] = 8;  // child[0..3], uint64
+    }
+    ANQS_TRY(launch_mlp_tc_prefix_logits(M, H, P.plog, s, z));
+    if (persistent) {
       uint64_t F = 1;
       for (int q = 0; q <= n; ++q) F = std::max(F, level_cap(H, n_samples, q));
       const unsigned grid = blocks_for(((n_samples + 3) / 4 + F + SMALL_T - 1) / SMALL_T, 1, uint64_t(sms));
