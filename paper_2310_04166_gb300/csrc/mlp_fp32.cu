@@ -477,8 +477,18 @@ __global__ void partial_sum_kernel(const float* __restrict__ part, Count n_x_, u
   const uint64_t tiles = (n_x_.get() + rg - 1) / rg;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < n_params;
        i += uint64_t(gridDim.x) * blockDim.x) {
+    // four tiles' loads in flight at a time, added in tile order
     float s = 0.f;
-    for (uint64_t t = 0; t < tiles; ++t) s += part[t * n_params + i];
+    uint64_t t = 0;
+    for (; t + 4 <= tiles; t += 4) {
+      const float a0 = part[t * n_params + i], a1 = part[(t + 1) * n_params + i],
+                  a2 = part[(t + 2) * n_params + i], a3 = part[(t + 3) * n_params + i];
+      s += a0;
+      s += a1;
+      s += a2;
+      s += a3;
+    }
+    for (; t < tiles; ++t) s += part[t * n_params + i];
     grad[i] = s;
   }
 }
