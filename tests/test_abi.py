@@ -99,3 +99,10 @@ def test_batch_arguments_rejected_on_host(lib):
     assert lib.anqs_batch_create(C.byref(h), 5000) == -1 and not h.value
     assert lib.anqs_batch_destroy(None) == 0
     assert lib.anqs_batched_local_energy(None, None, 0, None) == -1
+
+
+def test_sampler_barrier_test_hook_is_host_only(lib):
+    """The failure-detection hook only sets host-side launch parameters: it
+    needs no GPU, always succeeds, and (0, 0) restores the defaults."""
+    assert lib.anqs_test_sampler_barrier(1, 20_000_000) == 0
+    assert lib.anqs_test_sampler_barrier(0, 0) == 0
