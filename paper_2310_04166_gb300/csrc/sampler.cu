@@ -57,8 +57,9 @@ struct Philox {
 };
 
 // Grid barrier of the persistent launch: one arrival counter per level
-// (zeroed by the initial kernel, never reset), so a level's barrier is one
-// reduction per CTA and a poll until the count reaches the grid size.
+// (zeroed by the kernel launched just before it, never reset within a pass),
+// so a level's barrier is one reduction per CTA and a poll until the count
+// reaches the grid size.
 struct GridBarrier {
   unsigned arrive[ANQS_MAX_ORB + 1];
   int err;  // a CTA gave up waiting
@@ -696,8 +697,9 @@ __global__ void __launch_bounds__(SMALL_T) draw_small_kernel(HamView hv, int p, 
 // CTA waits for another's compaction.  The child counters rotate over three
 // buffers: level p adds into buffer p % 3 and, before its barrier, the grid
 // clears buffer (p + 1) % 3, which every CTA finished reading before the
-// barrier of level p - 1.  The draws and their order are those of
-// draw_small_kernel, so the samples are the same bit for bit.
+// barrier of level p - 1 (level 0's counters and the barrier are cleared by
+// the prefix-table slot launch before this one).  The draws and their order
+// are those of draw_small_kernel, so the samples are the same bit for bit.
 //
 // When the table has at most kStageRows rows, every CTA first stages, for
 // every row, the split thresholds of its conditional, its outcome masks and
