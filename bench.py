@@ -300,17 +300,21 @@ def _config(w, args):
 
 
 # DRAM bytes per launch from ncu captures of the same kernel build and
-# workload (h2o, 16-bit form): dram__bytes_read.sum + dram__bytes_write.sum.
-# The suffix from `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum
-# --clock-control none -k regex:'mlp_tc_ws|eloc_assemble|js_hist' -s 6 -c 3 --csv
-# python bench.py --steps 2 --warmup 3 --no-cpu-baseline --one-form --no-extra`
-# (the third step's launch); the others from `ncu --metrics
-# dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+# workload (h2o, 16-bit form): dram__bytes_read.sum + dram__bytes_write.sum,
+# each from the third step's launch of
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none
+#       -k regex:<kernels> -s <2 steps of them> -c <1 step of them> --csv
+#       python bench.py --steps 2 --warmup 3 --no-cpu-baseline --one-form --no-extra
+# (the suffix with regex 'mlp_tc_ws|eloc_assemble|js_hist'; the slot launches,
+# connected set, assembly and partial sum with
+# 'connected_diag|mlp_tc_slots|eloc_assemble|partial_sum'); the adjoint from
+# `ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
 # --clock-control none -c 80 --csv python bench.py --kernel-case`.  A kernel
 # changed since its capture has no entry (traffic null).
-TRAFFIC = {("h2o", "bf16"): {"mlp_tc_suffix_kernel": 1327104, "mlp_tc_parent_kernel": 657408,
-                             "mlp_tc_grad_kernel": 609792, "connected_kernel": 64512,
-                             "grad_partial_sum_kernel": 4009984}}
+TRAFFIC = {("h2o", "bf16"): {"mlp_tc_suffix_kernel": 1327104, "mlp_tc_parent_kernel": 660480,
+                             "mlp_tc_slot_kernel": 663808, "mlp_tc_grad_kernel": 609792,
+                             "eloc_assemble_kernel": 4674560, "connected_kernel": 64512,
+                             "grad_partial_sum_kernel": 4014336}}
 
 
 # kernel families that evaluate the connected determinants' amplitudes, in
