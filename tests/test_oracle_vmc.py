@@ -140,3 +140,23 @@ def test_gradient_equals_exact_energy_gradient():
         t[j] = old
         fd = (fp - fm) / 2e-5
         assert abs(fd - g[flat_i]) < 1e-7 * max(1.0, abs(fd))
+
+
+def test_energy_stats_equal_the_statistics_of_the_expanded_sample_list():
+    """Eq. energy_est over unique samples with occurrence numbers equals the
+    plain mean over the N_s individual samples; the variance (reading: the
+    count-weighted population variance with the complex mean) equals numpy's
+    population variance of the expanded list, real and imaginary parts added."""
+    rng = np.random.default_rng(7)
+    e = -75.0 + rng.normal(size=40) * 1.3 + 1j * rng.normal(size=40) * 1e-2
+    n = rng.integers(1, 50, size=40)
+    st = energy_stats(e, n)
+    full = np.repeat(e, n)
+    assert st[3] == n.sum() == full.size
+    assert abs(st[0] - full.real.mean()) <= 1e-12 * abs(full.real.mean())
+    assert abs(st[1] - full.imag.mean()) <= 1e-12
+    var = full.real.var() + full.imag.var()
+    assert abs(st[2] - var) <= 1e-10 * var
+    # a single sample has zero variance; equal energies too
+    assert energy_stats(e[:1], n[:1])[2] == 0.0
+    assert energy_stats(np.full(5, -3.0 + 0j), np.arange(1, 6))[2] == 0.0
