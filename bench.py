@@ -914,16 +914,28 @@ def main():
     if cpu:
         line["cpu_baseline"] = cpu
     if args.workload == "h2o" and not args.no_extra and ws == 1:
-        # the N2-shaped transformer workload in the same line, fewer steps (its FP32 form takes ~0.75 s a step)
-        line["workloads"] = {"n2": _sub_workload(A, lib, args, "n2", dev, rank, dist, min(args.steps, 10))}
-        torch.cuda.empty_cache()
-        # the 32-problem batch (persistent launch, autotuned) and the 26-orbital transformer, in short forms
-        line["workloads"]["batch32"] = _compact(_batch32(args, dev, quick=True))
-        torch.cuda.empty_cache()
-        line["workloads"]["large"] = _compact(_large(args, dev, quick=True))
+        # the N2-shaped transformer workload in the same line, fewer steps (its FP32 form takes ~0.75 s a step),
+        # then the 32-problem batch (persistent launch, autotuned) and the 26-orbital transformer in short forms;
+        # a sub-workload that fails records its error and the line still prints
+        subs = (("n2", lambda: _sub_workload(A, lib, args, "n2", dev, rank, dist, min(args.steps, 10))),
+                ("batch32", lambda: _compact(_batch32(args, dev, quick=True))),
+                ("large", lambda: _compact(_large(args, dev, quick=True))))
+        line["workloads"] = {}
+        for name, run in subs:
+            line["workloads"][name] = _guarded(run)
+            _guarded(torch.cuda.empty_cache)
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def _guarded(run):
+    """run(), or {"error": ...} if it raises: one sub-workload's failure
+    must not take the headline line with it."""
+    try:
+        return run()
+    except Exception as e:  # noqa: BLE001 (any failure of a sub-workload is reported, not raised)
+        return {"error": f"{type(e).__name__}: {e}"[:400]}
 
 
 def _compact(sub):
