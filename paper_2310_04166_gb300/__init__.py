@@ -103,7 +103,11 @@ class Hamiltonian:
 
 
 class Model:
-    """Autoregressive ansatz over caller-owned float32 CUDA parameters."""
+    """Autoregressive ansatz over caller-owned float32 CUDA parameters.
+
+    A model's calls may be queued on any stream, but not from several host
+    threads at once: the 16-bit MLP keeps scratch rows and a second stream of
+    its own (forked from and joined back into the caller's stream)."""
 
     def __init__(self, desc: ModelDesc, params: torch.Tensor):
         lib = _lib.load()
